@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of the RPBA hot path on GB300 (one JSON line on stdout).
+
+Workload: the 1,000-camera / 100k-point / ~600k-observation block with 8
+uneven sub-blocks (60..200 cameras), nadir + 30 deg oblique views, 0.5 px
+noise, 2 % outliers (seeded synthetic data).
+
+A step is one pass of the whole hot path over that block: one lock-step
+Levenberg-Marquardt iteration of every sub-block (residuals, Jacobians,
+normal equations with the TP control term, Schur complement, RCS solve,
+back-substitution, trial cost, accept/reject), the exchange, the robust
+weights (per-camera MAD) and the intersection of all tie points with their
+covariance-derived weights. value = observations processed per second per
+LM iteration.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to oracle-matched RMS (s) & obs/s per LM iter, chosen vs plain form"
+WORKLOAD = "rpba-1000cam-100kpt-600kobs-8sub (25x40 grid, nadir+30deg oblique, 0.5px, 2% outliers)"
+TARGETS = os.path.join(ROOT, "tests", "golden", "oracle_targets.json")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--config", type=int, default=2)
+    p.add_argument("--precision", type=int, default=1)
+    p.add_argument("--solver", type=int, default=0)
+    p.add_argument("--no-extras", action="store_true", help="skip e2e / time-to-RMS / cpu legs")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0])); smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------
+def fp64_peak_gflops():
+    """Nominal dense FP64 rate of a GB300 (1.25 TFLOP/s, 152 SMs at 2.07 GHz)."""
+    return 1250.0
+
+
+def cholesky_update_flops(sub_sizes, tile=64):
+    """Algorithmic FP64 flops of the trailing updates of one blocked factorisation
+    of every sub-block RCS: sum_k 64 * m_k (m_k + 1), m_k = n - 64 (k + 1)."""
+    tot = 0
+    for n in sub_sizes:
+        k = 0
+        while n - tile * (k + 1) > 0:
+            m = n - tile * (k + 1)
+            tot += tile * m * (m + 1)
+            k += 1
+    return tot
+
+
+def roofline(prof, steps, n_sub_sizes, K, peaks, mem_bound_bytes):
+    # dominant kernel = largest summed event time over the timed region
+    name, (launches, ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    per_launch_s = ms / 1e3 / max(launches, 1)
+    if name == "k_syrk_update":
+        work = cholesky_update_flops(n_sub_sizes) * steps / max(launches, 1)
+        achieved = work / per_launch_s / 1e12
+        peak = fp64_peak_gflops() / 1e3
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "nominal FP64 1.25 TFLOP/s (no measured FP64 peak)",
+                "launches": launches, "avg_launch_ms": per_launch_s * 1e3}
+    bytes_per_launch = mem_bound_bytes.get(name)
+    if bytes_per_launch is None:
+        return {"kernel": name, "bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": None, "traffic": None, "launches": launches, "avg_launch_ms": per_launch_s * 1e3}
+    achieved = bytes_per_launch / per_launch_s / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": "measured",
+            "launches": launches, "avg_launch_ms": per_launch_s * 1e3}
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+def bench_options(precision, solver, max_inner):
+    return dict(precision=precision, solver=solver, robust=1, robust_from_start=1, max_inner=max_inner)
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle
+# ---------------------------------------------------------------------------
+def oracle_step_sample(prob):
+    """One bounded sample of the step on the CPU oracle: one LM iteration of
+    every sub-block, the exchange, robust weights and the TP intersection."""
+    import oracle
+    o = oracle.Oracle(prob)
+    o.intersect()
+    t0 = time.perf_counter()
+    for l in range(o.L):
+        o.lm_step(l, 1e-4)
+    o.robust_weights()
+    o.intersect(tp_only=True)
+    dt = time.perf_counter() - t0
+    _, act = o.points()
+    k_act = int(act[prob["obs_point"]].sum())
+    return dt, k_act
+
+
+def run_reference(args, rank, world):
+    from paper_1910_08138_gb300 import synth
+    if rank != 0:
+        return
+    prob = synth.config(args.config)
+    for _ in range(max(args.warmup, 0) and 1):
+        oracle_step_sample(prob)
+    times, kk = [], 0
+    for _ in range(args.steps):
+        dt, kk = oracle_step_sample(prob)
+        times.append(dt)
+    ms = 1e3 * float(np.mean(times))
+    value = kk / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "obs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "obs/s", "cores": 1, "kind": "oracle",
+                             "sample": "one LM iteration of all 8 sub-blocks + robust weights + TP intersection, "
+                                       "whole block, single thread, per step"},
+            "e2e": {"value": value, "unit": "obs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import torch
+
+    from paper_1910_08138_gb300 import rpba, synth
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    prob = synth.config(args.config)
+    peaks = load_peaks()
+    ctx = rpba.Rpba(prob, stream=stream, **bench_options(args.precision, args.solver, 1))
+    ctx.intersect()
+    n_sub = [6 * len(ctx.sub_cameras(l)) for l in range(ctx.L)]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    for _ in range(args.warmup):
+        ctx.iterate(1)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ctx.profile_enable(True)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    times = []
+    k_act = None
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep = ctx.iterate(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        k_act = rep["active_obs"]
+    clk = clocks.stop()
+    prof, launches = ctx.profile_read()
+    ctx.profile_enable(False)
+    total_ms = float(np.sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    ms = total_ms / args.steps
+    value = world * k_act * args.steps / (total_ms / 1e3)
+    # algorithmic bytes of the HBM-bound kernels per launch (FP32 form: 20 B/obs
+    # of observation data + per-observation 3x6 blocks written and read)
+    K = k_act
+    rs = 4 if args.precision == 1 else 8
+    mem_bytes = {
+        "k_linearize": K * (4 + 4 + 16 + 8 + 2 * 18 * rs),
+        "k_camera_blocks": K * (4 + 4 + 16 + 8 + 2 * 18 * rs + 24),
+        "k_inst_cost": K * (4 + 16 + 8) + ctx.P * 24,
+        "k_backsub": K * (4 + 18 * rs) + ctx.P * (24 * 2 + 9 * rs),
+    }
+    roof = roofline(prof, args.steps, n_sub, K, peaks, mem_bytes)
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    line = {"metric": METRIC, "value": value, "unit": "obs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == 1 else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "mixed FP32/FP64" if args.precision == 1 else "FP64",
+                       "solver": "dense Cholesky" if args.solver == 0 else "block-Jacobi PCG",
+                       "l2": "flushed between steps (256 MB write)", "n_obs": K, "subblocks": ctx.L,
+                       "step": "1 LM iteration of all sub-blocks + exchange + robust weights + TP intersection",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "gpu_launches": launches // args.steps * args.steps,
+            "gpu_launches_per_step": launches / args.steps, "clocks": clk, "kernels": kernels}
+    if rank == 0 and not args.no_extras:
+        line.update(extras(args, prob, ctx, stream, K))
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def extras(args, prob, ctx, stream, K):
+    import torch
+
+    from paper_1910_08138_gb300 import rpba
+    out = {}
+    # e2e through the C ABI with host buffers: state H2D, one step, state D2H
+    cams = np.ascontiguousarray(ctx.cameras())
+    X, act = ctx.points()
+    times = []
+    for s in range(max(3, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.set_cameras(cams)
+        ctx.set_points(X, act)
+        rep = ctx.iterate(1)
+        cams = ctx.cameras()
+        X, act = ctx.points()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    h2d = cams.nbytes + X.nbytes + act.nbytes
+    d2h = h2d
+    out["e2e"] = {"value": K / float(np.mean(times)), "unit": "obs/s", "h2d_bytes_per_step": int(h2d),
+                  "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * float(np.mean(times))}
+    # time to the oracle's final RMS, chosen form vs plain all-FP64 form
+    target = None
+    try:
+        target = json.load(open(TARGETS))[f"config{args.config}"]["rms"]
+    except Exception:
+        pass
+    ttr = {}
+    for form, prec in (("chosen", args.precision), ("plain", 0)):
+        g = rpba.Rpba(prob, stream=stream, **bench_options(prec, args.solver, 20))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.intersect()
+        rep = g.iterate()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        ttr[form] = {"seconds": dt, "final_rms": rep["rms"], "outer": rep["outer"],
+                     "lm_iterations": rep["lm_launches"],
+                     "matches_oracle": (target is not None and rep["rms"] <= target + 1e-3)}
+        g.close()
+    ttr["oracle_final_rms"] = target
+    if ttr["plain"]["seconds"] > 0:
+        ttr["chosen_speedup_vs_plain"] = ttr["plain"]["seconds"] / ttr["chosen"]["seconds"]
+    out["time_to_oracle_rms"] = ttr
+    # CPU oracle on a bounded sample of the same workload
+    dt, kk = oracle_step_sample(prob)
+    out["cpu_baseline"] = {"value": kk / dt, "unit": "obs/s", "cores": 1, "kind": "oracle",
+                           "sample": "one LM iteration of all 8 sub-blocks + robust weights + TP intersection "
+                                     f"({kk} obs), single thread, {dt:.1f} s"}
+    return out
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * rpba.h -- C ABI of the GB300 (sm_103a) implementation of the RPBA hot path:
+ * covariance-weighted parallel bundle adjustment by sub-blocks (Mayer,
+ * "RPBA - Robust Parallel Bundle Adjustment Based on Covariance Information").
+ *
+ * Problem statement (Sec. 2; Sec. 4, sub-block split): M cameras P_i (pose:
+ * angle-axis omega and translation t, X_c = R(omega) X + t; fixed pinhole
+ * intrinsics f, cx, cy), N 3D points X_j, K image observations x_k of point j
+ * in camera i with 2x2 weight C_k^-1. Every camera belongs to exactly one
+ * sub-block; a point observed from cameras of several sub-blocks is a tie
+ * point (TP). The method alternates the adjustment of every sub-block with its
+ * TPs as weighted control points (Eq. bact) and the intersection of the TPs
+ * with all cameras fixed (Eq. bars), which yields the TP positions, their
+ * covariances and the per-sub-block weights W^l (Sec. 5.1).
+ *
+ * Conventions for every call
+ *   - All array arguments are HOST pointers owned by the caller; the library
+ *     copies what it needs and never keeps a caller pointer past the call.
+ *   - Row-major, tightly packed; indices are 0-based int32.
+ *   - sym3 = 6 doubles (a00, a01, a02, a11, a12, a22).
+ *   - Every call returns an rpba_status; on error the context keeps a message
+ *     (rpba_last_error) and the state is left as it was before the failing
+ *     kernel (device state may be partially updated after RPBA_ERR_CUDA).
+ *   - The library owns all device memory (cudaMalloc, or the caller's
+ *     allocator hook in rpba_options) and runs every kernel on the stream
+ *     given at creation. Calls on one context must not overlap.
+ *   - No CPU fallback: without a usable sm_103a device rpba_create fails with
+ *     RPBA_ERR_CUDA.
+ */
+#ifndef RPBA_H
+#define RPBA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rpba_ctx rpba_ctx;
+
+typedef enum {
+  RPBA_OK = 0,
+  RPBA_ERR_INVALID_ARG = 1,   /* bad size, index out of range, NULL where required */
+  RPBA_ERR_OOM = 2,           /* device allocation failed */
+  RPBA_ERR_CUDA = 3,          /* a CUDA runtime error (message has the CUDA text) */
+  RPBA_ERR_NOT_CONVERGED = 4, /* iteration cap reached (state is still valid) */
+  RPBA_ERR_DEVICE_TIMEOUT = 5,/* a bounded device-side wait ran out */
+  RPBA_ERR_NUMERIC = 6,       /* non-finite values where finite ones are required */
+  RPBA_ERR_STATE = 7          /* call out of order (e.g. sub-block index >= L) */
+} rpba_status;
+
+/* Input block (Sec. 2). cam_pose n_cams x 6 (omega rad, t); cam_intr
+ * n_cams x 3 (f, cx, cy); points n_points x 3; obs_cam/obs_point n_obs;
+ * obs_xy n_obs x 2 pixels; obs_winv n_obs x 3 (w11, w12, w22) of C_k^-1 or
+ * NULL for identity; cam_subblock n_cams (global sub-block ids 0..L-1, every
+ * id used); cam_block n_cams or NULL: id of the independent block a camera
+ * belongs to (only used for reporting; independent blocks are simply
+ * sub-blocks that share no point). A point needs two observations to be
+ * estimated; points with fewer stay inactive. */
+typedef struct {
+  int32_t n_cams, n_points, n_obs;
+  const double *cam_pose;
+  const double *cam_intr;
+  const double *points;
+  const int32_t *obs_cam;
+  const int32_t *obs_point;
+  const double *obs_xy;
+  const double *obs_winv;
+  const int32_t *cam_subblock;
+  const int32_t *cam_block;
+} rpba_problem;
+
+/* Options; rpba_default_options fills the paper's values (Sec. 5.3, 5.5). */
+typedef struct {
+  double lambda0;        /* LM damping N + lambda diag(N), 1e-4 (Sec. 5.5) */
+  double t_v;            /* robust threshold on sqrt(v^T C^-1 v)/sigma_cam, 4 (Sec. 5.3) */
+  double downweight;     /* weight of a detected outlier, 1e-4 (Sec. 5.3) */
+  double stop_ratio;     /* best/current ratio that ends a loop, 1.01 (Sec. 5.5) */
+  int32_t grace;         /* iterations allowed below the ratio, 1 (Sec. 5.5) */
+  int32_t max_outer;     /* cap on bact/bars iterations, 30 */
+  int32_t max_inner;     /* cap on LM iterations per sub-block per bact, 20 */
+  int32_t max_reject;    /* rejected LM steps in a row that end a bact, 6 */
+  int32_t robust;        /* 1: robust stage (Sec. 5.3, parallel variant) */
+  int32_t robust_from_start; /* 1: robust weights from the first intersection on */
+  int32_t isect_max_iter;/* Gauss-Newton iterations of the intersection, 10 */
+  double isect_tol;      /* ||dX|| <= tol (1 + ||X||) ends it, 1e-10 (FP64) */
+  double cond_max;       /* Frobenius condition number that drops a point, 1e12 */
+  int32_t precision;     /* 0: all FP64 ("plain"); 1: FP32 bulk, FP64 solve/reductions */
+  int32_t solver;        /* 0: dense Cholesky of the RCS; 1: block-Jacobi PCG */
+  double pcg_tol;        /* relative residual of the PCG solve, 1e-8 */
+  int32_t pcg_max_iter;  /* PCG iteration cap, 500 */
+  /* optional device allocator (NULL: cudaMalloc / cudaFree) */
+  void *(*dev_alloc)(size_t bytes, void *user);
+  void (*dev_free)(void *ptr, void *user);
+  void *alloc_user;
+} rpba_options;
+
+typedef struct {
+  double sigma0;          /* final sigma_0 (Eq. sigma0, weights C^-1) */
+  double rms;             /* RMS image residual [px] over active, not down-weighted obs */
+  double sigma0_initial;  /* sigma_0 after the initial intersection */
+  int32_t outer;          /* bact/bars iterations done */
+  int32_t inner_total;    /* LM iterations summed over sub-blocks */
+  int32_t lm_launches;    /* lock-step LM iterations (all sub-blocks together) */
+  int32_t deleted_points; /* points eliminated or dropped since creation */
+  int32_t active_points;
+  int32_t active_obs;
+  int32_t robust_started_at; /* outer iteration where the robust stage began, -1 never */
+  double sigma0_hist[128];
+} rpba_report;
+
+void rpba_default_options(rpba_options *opt);
+
+/* Creates a context: validates and copies the block to the device, builds the
+ * sub-block topology (point instances, CSR orders by instance and by camera,
+ * RCS layout). `cuda_stream` is a cudaStream_t (NULL = default stream).
+ * Errors: INVALID_ARG (sizes, ids out of range, a duplicate (camera, point)
+ * observation), OOM, CUDA. */
+rpba_status rpba_create(const rpba_problem *prob, const rpba_options *opt, void *cuda_stream,
+                        rpba_ctx **out);
+void rpba_destroy(rpba_ctx *ctx);
+const char *rpba_last_error(const rpba_ctx *ctx);
+
+/* Intersection of every active point with all cameras fixed (Eq. bars, the
+ * start values for the first bact): Gauss-Newton on X_j, then W^l_j = N_j -
+ * N_j^(l) for every instance (Sec. 5.1). Points that do not converge are
+ * dropped (Sec. 5.5). */
+rpba_status rpba_intersect(rpba_ctx *ctx);
+
+/* The RPBA iteration (Sec. 5): up to max_outer (<= 0: options.max_outer)
+ * alternations of the LM adjustment of every sub-block (Eq. bact; all
+ * sub-blocks advance together, one launch per step) and the TP intersection
+ * (Eq. bars), with the robust stage of Sec. 5.3 when enabled. Runs
+ * rpba_intersect first if it has not been run. `report` may be NULL. */
+rpba_status rpba_iterate(rpba_ctx *ctx, int32_t max_outer, rpba_report *report);
+
+/* C_j = N_j^-1 of the listed points at the current state (Eq. bars), out is
+ * n x 9 row-major; inactive points give NaN. */
+rpba_status rpba_covariance(rpba_ctx *ctx, const int32_t *point_ids, int32_t n, double *out9);
+
+rpba_status rpba_get_cameras(rpba_ctx *ctx, double *pose /* n_cams x 6 */);
+rpba_status rpba_get_points(rpba_ctx *ctx, double *X /* n_points x 3 */, uint8_t *active /* nullable */);
+
+/* ---- state access and single steps (used by the parity tests) ---------- */
+
+rpba_status rpba_info(rpba_ctx *ctx, int32_t *n_subblocks, int32_t *n_instances);
+/* cameras of sub-block l in RCS row order (ascending global id); n_out = count */
+rpba_status rpba_sub_cameras(rpba_ctx *ctx, int32_t l, int32_t *cams, int32_t *n_out);
+rpba_status rpba_set_cameras(rpba_ctx *ctx, const double *pose);
+rpba_status rpba_set_points(rpba_ctx *ctx, const double *X, const uint8_t *active /* nullable */);
+/* instances sorted by (sub-block, point): point id, sub-block id, X^l (P x 3),
+ * W^l (P x 6 sym3); any output may be NULL */
+rpba_status rpba_get_instances(rpba_ctx *ctx, int32_t *inst_point, int32_t *inst_sub, double *Xl,
+                               double *Wl);
+rpba_status rpba_set_instances(rpba_ctx *ctx, const double *Xl, const double *Wl);
+/* robust weights w_k, in the caller's observation order */
+rpba_status rpba_get_weights(rpba_ctx *ctx, double *w);
+rpba_status rpba_set_weights(rpba_ctx *ctx, const double *w);
+/* v_k = g_k(P_i, X_j) - x_k at the global state (Sec. 2), n_obs x 2 */
+rpba_status rpba_residuals(rpba_ctx *ctx, double *v);
+/* Jc (n_obs x 2 x 6, d/d(dw, dt), dw left-multiplied) and Jx (n_obs x 2 x 3) (Eq. ta) */
+rpba_status rpba_jacobians(rpba_ctx *ctx, double *Jc, double *Jx);
+/* sigma_0 (Eq. sigma0) and RMS at the global state */
+rpba_status rpba_sigma0(rpba_ctx *ctx, double *sigma0, double *rms);
+/* per-camera 1.4826 * MAD of the whitened residual components (Sec. 5.3) */
+rpba_status rpba_camera_scale(rpba_ctx *ctx, double *sigma /* n_cams */);
+/* robust weights from that scale; n_down = number down-weighted (Sec. 5.3) */
+rpba_status rpba_robust_weights(rpba_ctx *ctx, int32_t *n_down);
+/* intersection of all active points (tp_only = 0) or of the TPs only */
+rpba_status rpba_intersect_points(rpba_ctx *ctx, int32_t tp_only, int32_t *n_dropped);
+/* F_l of every sub-block at the current state (Eq. bact), n_subblocks values */
+rpba_status rpba_sub_costs(rpba_ctx *ctx, double *F);
+/* damped RCS of sub-block l (Sec. 2, 5.5): S (n x n, lower triangle valid,
+ * n = 6 x cameras of l) and y (n), at the current state */
+rpba_status rpba_rcs(rpba_ctx *ctx, int32_t l, double lambda, double *S, double *y);
+/* one LM step of every sub-block with damping lambda: solve, trial, accept
+ * if F_l decreases. Outputs per sub-block (nullable): accepted (1/0/-1 solve
+ * failed), F before, F of the trial; dc = camera updates in RCS order of all
+ * sub-blocks concatenated (6 x n_cams), dx = instance updates (P x 3). */
+rpba_status rpba_lm_step(rpba_ctx *ctx, double lambda, int32_t *accepted, double *F_before,
+                         double *F_trial, double *dc, double *dx);
+
+/* ---- measurement ------------------------------------------------------- */
+
+/* Resets the per-kernel counters; enable != 0 also times every kernel launch
+ * with a pair of CUDA events on the context stream (adds two event records
+ * per launch; leave it off outside measurements). */
+rpba_status rpba_profile_enable(rpba_ctx *ctx, int32_t enable);
+/* Kernel launches since the last rpba_profile_enable, per kernel name (names:
+ * max_kernels slots of 48 chars), their summed event time in ms (0 when
+ * timing was off), the number of distinct kernels and of launches. */
+rpba_status rpba_profile_read(rpba_ctx *ctx, int32_t max_kernels, char *names, double *ms,
+                              int64_t *launches, int32_t *n_kernels, int64_t *total_launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

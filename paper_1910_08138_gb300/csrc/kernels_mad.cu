@@ -1,0 +1,102 @@
+// kernels_mad.cu -- per-camera robust scale (Sec. 5.3): 1.4826 times the
+// median absolute deviation of the whitened residual components of every
+// observation of the camera. One CTA per camera; the 2 K_i components are
+// sorted in shared memory (bitonic network, padded to a power of two with
+// +inf), the median is read off, the absolute deviations are sorted again.
+#include <cuda_runtime.h>
+#include <float.h>
+
+#include "rpba_internal.cuh"
+
+namespace rpba {
+
+__device__ static void bitonic_sort(double *a, int n2) {
+  for (int size = 2; size <= n2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int idx = threadIdx.x; idx < (n2 >> 1); idx += blockDim.x) {
+        int i = 2 * stride * (idx / stride) + (idx % stride);
+        int j = i + stride;
+        bool up = (i & size) == 0;
+        double x = a[i], y = a[j];
+        if ((x > y) == up) {
+          a[i] = y;
+          a[j] = x;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__device__ static double sorted_median(const double *a, int n) {
+  return (n & 1) ? a[n / 2] : 0.5 * (a[n / 2 - 1] + a[n / 2]);
+}
+
+__global__ void k_camera_mad(int M, const double *R, const double *t, const double *intr, const double *X,
+                             const uint8_t *active, const int *cam_obs_ptr, const int *cam_obs, const int *obs_pt,
+                             const double *obs_xy, const double *obs_winv, int has_winv, double *sigma) {
+  extern __shared__ double sh[];
+  __shared__ int count;
+  int i = blockIdx.x;
+  if (i >= M) return;
+  if (threadIdx.x == 0) count = 0;
+  __syncthreads();
+  int p0 = cam_obs_ptr[i], p1 = cam_obs_ptr[i + 1];
+  const double *Ri = R + 9 * i, *ti = t + 3 * i;
+  double f = intr[3 * i], cx = intr[3 * i + 1], cy = intr[3 * i + 2];
+  for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    int k = cam_obs[p];
+    int j = obs_pt[k];
+    if (!active[j]) continue;
+    const double *Xj = X + 3 * j;
+    double Xc[3];
+    for (int r = 0; r < 3; r++) Xc[r] = Ri[3 * r] * Xj[0] + Ri[3 * r + 1] * Xj[1] + Ri[3 * r + 2] * Xj[2] + ti[r];
+    double iz = 1.0 / Xc[2];
+    double r0 = f * Xc[0] * iz + cx - obs_xy[2 * k];
+    double r1 = f * Xc[1] * iz + cy - obs_xy[2 * k + 1];
+    double W0 = 1, W1 = 0, W2 = 1;
+    if (has_winv) { W0 = obs_winv[3 * k]; W1 = obs_winv[3 * k + 1]; W2 = obs_winv[3 * k + 2]; }
+    double a = sqrt(W0);
+    double e0 = a * r0 + (W1 / a) * r1;
+    double e1 = sqrt(W2 - W1 * W1 / W0) * r1;
+    int slot = atomicAdd(&count, 2);
+    sh[slot] = e0;
+    sh[slot + 1] = e1;
+  }
+  __syncthreads();
+  int n = count;
+  if (n == 0) {
+    if (threadIdx.x == 0) sigma[i] = 0.0;
+    return;
+  }
+  int n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  for (int e = n + threadIdx.x; e < n2; e += blockDim.x) sh[e] = DBL_MAX;
+  __syncthreads();
+  bitonic_sort(sh, n2);
+  double med = sorted_median(sh, n);
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += blockDim.x) sh[e] = fabs(sh[e] - med);
+  __syncthreads();
+  bitonic_sort(sh, n2);
+  if (threadIdx.x == 0) sigma[i] = 1.4826 * sorted_median(sh, n);
+}
+
+rpba_status launch_camera_scale(Ctx *ctx) {
+  if (ctx->M == 0) return RPBA_OK;
+  int n2 = 1;
+  while (n2 < 2 * ctx->max_cam_obs) n2 <<= 1;
+  size_t smem = (size_t)n2 * sizeof(double);
+  if (smem > 200 * 1024) {
+    ctx->err = "camera with too many observations for the shared-memory median";
+    return RPBA_ERR_INVALID_ARG;
+  }
+  if (smem > 48 * 1024)
+    RPBA_CUDA(cudaFuncSetAttribute(k_camera_mad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  RPBA_KERNEL(ctx, "k_camera_mad", k_camera_mad<<<ctx->M, 512, smem, ctx->stream>>>(ctx->M, ctx->R, ctx->t, ctx->intr, ctx->X, ctx->active,
+                                                   ctx->cam_obs_ptr, ctx->cam_obs, ctx->obs_pt, ctx->obs_xy,
+                                                   ctx->obs_winv, ctx->has_winv, ctx->cam_sigma));
+  return RPBA_OK;
+}
+
+}  // namespace rpba

@@ -1,0 +1,909 @@
+// kernels_obs.cu -- observation-, instance-, point- and camera-level kernels
+// of the RPBA hot path on sm_103a:
+//   residuals and Jacobians (Sec. 2, Eq. ta), weighted cost and sigma_0
+//   (Eq. v2, normalw, sigma0), intersection of points with the cameras fixed
+//   and the refined TP weights (Eq. bars, Sec. 5.1), normal equations of a
+//   sub-block with the TP control term and LM damping (Eq. bact, Sec. 5.5),
+//   Schur complement onto the cameras (Sec. 2, 5.5), back-substitution and
+//   trial update, robust weights (Sec. 5.3).
+//
+// Compute precision T is double for the all-FP64 form and float for the
+// mixed form; positions, rotations, costs and the RCS stay double.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "rpba_internal.cuh"
+
+namespace rpba {
+
+// ---------------------------------------------------------------------------
+// views
+// ---------------------------------------------------------------------------
+struct View {
+  int M, N, K, L, P, has_winv;
+  const double *R, *t, *intr;
+  double *Rt, *tt;
+  const int *cam_sub, *cam_local, *sub_cam_ptr, *sub_cam, *cam_obs_ptr, *cam_obs;
+  double *X;
+  uint8_t *active;
+  const int *pt_inst_ptr, *pt_inst;
+  const int *inst_pt, *inst_sub, *inst_obs_ptr, *sub_inst_ptr;
+  double *Xl, *Xlt, *Wl, *inst_cost;
+  const int *obs_cam, *obs_inst, *obs_user, *obs_pt;
+  const double *obs_xy, *obs_winv;
+  double *obs_w;
+  double *S, *y, *dC;
+  const long long *S_off;
+  const int *npad, *ycam_off;
+};
+
+static View make_view(Ctx *c) {
+  View v;
+  v.M = c->M; v.N = c->N; v.K = c->K; v.L = c->L; v.P = c->P; v.has_winv = c->has_winv;
+  v.R = c->R; v.t = c->t; v.intr = c->intr; v.Rt = c->Rt; v.tt = c->tt;
+  v.cam_sub = c->cam_sub; v.cam_local = c->cam_local; v.sub_cam_ptr = c->sub_cam_ptr;
+  v.sub_cam = c->sub_cam; v.cam_obs_ptr = c->cam_obs_ptr; v.cam_obs = c->cam_obs;
+  v.X = c->X; v.active = c->active; v.pt_inst_ptr = c->pt_inst_ptr; v.pt_inst = c->pt_inst;
+  v.inst_pt = c->inst_pt; v.inst_sub = c->inst_sub; v.inst_obs_ptr = c->inst_obs_ptr;
+  v.sub_inst_ptr = c->sub_inst_ptr; v.Xl = c->Xl; v.Xlt = c->Xlt; v.Wl = c->Wl;
+  v.inst_cost = c->inst_cost; v.obs_cam = c->obs_cam; v.obs_inst = c->obs_inst;
+  v.obs_user = c->obs_user; v.obs_pt = c->obs_pt; v.obs_xy = c->obs_xy; v.obs_winv = c->obs_winv;
+  v.obs_w = c->obs_w; v.S = c->S; v.y = c->y; v.dC = c->dC; v.S_off = c->S_off; v.npad = c->npad;
+  v.ycam_off = c->ycam_off;
+  return v;
+}
+
+rpba_status check_launch(Ctx *ctx, const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return RPBA_ERR_CUDA;
+  }
+  return RPBA_OK;
+}
+
+static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
+
+// camera i and point X in the compute precision: Xc = R (X - C), RX = Xc - t.
+// The difference X - C is formed in double so that large coordinates keep
+// their precision before the cast.
+template <typename T>
+struct CamPt {
+  T R[9], Xc[3], RX[3], f, cx, cy;
+};
+
+template <typename T>
+__device__ inline void cam_point(const double *R, const double *t, const double *intr,
+                                 const double X[3], CamPt<T> &o) {
+  if (sizeof(T) == sizeof(double)) {
+    // plain form: exactly R X + t
+    for (int r = 0; r < 3; r++) {
+      double rx = R[3 * r] * X[0] + R[3 * r + 1] * X[1] + R[3 * r + 2] * X[2];
+      o.RX[r] = (T)rx;
+      o.Xc[r] = (T)(rx + t[r]);
+    }
+    for (int e = 0; e < 9; e++) o.R[e] = (T)R[e];
+  } else {
+    // camera centre C = -R^T t
+    double C[3];
+    for (int c = 0; c < 3; c++) C[c] = -(R[c] * t[0] + R[3 + c] * t[1] + R[6 + c] * t[2]);
+    T d[3] = {(T)(X[0] - C[0]), (T)(X[1] - C[1]), (T)(X[2] - C[2])};
+    for (int e = 0; e < 9; e++) o.R[e] = (T)R[e];
+    for (int r = 0; r < 3; r++) {
+      o.Xc[r] = o.R[3 * r] * d[0] + o.R[3 * r + 1] * d[1] + o.R[3 * r + 2] * d[2];
+      o.RX[r] = o.Xc[r] - (T)t[r];
+    }
+  }
+  o.f = (T)intr[0]; o.cx = (T)intr[1]; o.cy = (T)intr[2];
+}
+
+template <typename T>
+__device__ inline void load_winv(const View &v, int k, T W[3]) {
+  if (v.has_winv) {
+    W[0] = (T)v.obs_winv[3 * k]; W[1] = (T)v.obs_winv[3 * k + 1]; W[2] = (T)v.obs_winv[3 * k + 2];
+  } else {
+    W[0] = 1; W[1] = 0; W[2] = 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// residuals, Jacobians (diagnostics / parity) at the global state
+// ---------------------------------------------------------------------------
+__global__ void k_residuals(View v, double *out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= v.K) return;
+  int i = v.obs_cam[k], j = v.obs_pt[k];
+  const double *R = v.R + 9 * i, *t = v.t + 3 * i, *X = v.X + 3 * j;
+  double Xc[3];
+  for (int r = 0; r < 3; r++) Xc[r] = R[3 * r] * X[0] + R[3 * r + 1] * X[1] + R[3 * r + 2] * X[2] + t[r];
+  double f = v.intr[3 * i], iz = 1.0 / Xc[2];
+  int u = v.obs_user[k];
+  out[2 * u] = f * Xc[0] * iz + v.intr[3 * i + 1] - v.obs_xy[2 * k];
+  out[2 * u + 1] = f * Xc[1] * iz + v.intr[3 * i + 2] - v.obs_xy[2 * k + 1];
+}
+
+template <typename T>
+__global__ void k_jacobians(View v, double *Jc, double *Jx) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= v.K) return;
+  int i = v.obs_cam[k], j = v.obs_pt[k];
+  CamPt<T> cp;
+  cam_point<T>(v.R + 9 * i, v.t + 3 * i, v.intr + 3 * i, v.X + 3 * j, cp);
+  ProjJac<T> pj;
+  project_jac<T>(cp.R, cp.Xc, cp.RX, cp.f, cp.cx, cp.cy, pj);
+  int u = v.obs_user[k];
+  for (int e = 0; e < 12; e++) Jc[12 * u + e] = (double)pj.Jc[e];
+  for (int e = 0; e < 6; e++) Jx[6 * u + e] = (double)pj.Jx[e];
+}
+
+rpba_status launch_residuals(Ctx *ctx, double *v_dev) {
+  if (ctx->K == 0) return RPBA_OK;
+  RPBA_KERNEL(ctx, "k_residuals", k_residuals<<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(make_view(ctx), v_dev));
+  return RPBA_OK;
+}
+
+rpba_status launch_jacobians(Ctx *ctx, double *Jc, double *Jx) {
+  if (ctx->K == 0) return RPBA_OK;
+  if (ctx->opt.precision == 1)
+    RPBA_KERNEL(ctx, "k_jacobians", k_jacobians<float><<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(make_view(ctx), Jc, Jx));
+  else
+    RPBA_KERNEL(ctx, "k_jacobians", k_jacobians<double><<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(make_view(ctx), Jc, Jx));
+  return RPBA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// deterministic block reductions
+// ---------------------------------------------------------------------------
+template <int NV>
+__device__ inline void block_reduce_store(double (&val)[NV], double *out_block) {
+  __shared__ double sh[NV][32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int e = 0; e < NV; e++) {
+    double x = val[e];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[e][wid] = x;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int e = 0; e < NV; e++) {
+      double x = lane < nw ? sh[e][lane] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) out_block[e] = x;
+    }
+  }
+}
+
+// sum of `nb` rows of NV partials, one block
+template <int NV>
+__global__ void k_sum_partials(const double *part, int nb, double *out) {
+  double acc[NV];
+#pragma unroll
+  for (int e = 0; e < NV; e++) acc[e] = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+    for (int e = 0; e < NV; e++) acc[e] += part[(size_t)b * NV + e];
+  block_reduce_store<NV>(acc, out);
+}
+
+// sigma_0 / RMS sums: [sum w v^T W v, n_active_obs, sum |v|^2 (w == 1), n (w == 1)]
+__global__ void k_obs_sigma(View v, double *part) {
+  double acc[4] = {0, 0, 0, 0};
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < v.K; k += gridDim.x * blockDim.x) {
+    int j = v.obs_pt[k];
+    if (!v.active[j]) continue;
+    int i = v.obs_cam[k];
+    const double *R = v.R + 9 * i, *t = v.t + 3 * i, *X = v.X + 3 * j;
+    double Xc[3];
+    for (int r = 0; r < 3; r++) Xc[r] = R[3 * r] * X[0] + R[3 * r + 1] * X[1] + R[3 * r + 2] * X[2] + t[r];
+    double f = v.intr[3 * i], iz = 1.0 / Xc[2];
+    double r0 = f * Xc[0] * iz + v.intr[3 * i + 1] - v.obs_xy[2 * k];
+    double r1 = f * Xc[1] * iz + v.intr[3 * i + 2] - v.obs_xy[2 * k + 1];
+    double W0 = 1, W1 = 0, W2 = 1;
+    if (v.has_winv) { W0 = v.obs_winv[3 * k]; W1 = v.obs_winv[3 * k + 1]; W2 = v.obs_winv[3 * k + 2]; }
+    double w = v.obs_w[k];
+    acc[0] += w * (W0 * r0 * r0 + 2.0 * W1 * r0 * r1 + W2 * r1 * r1);
+    acc[1] += 1.0;
+    if (w == 1.0) {
+      acc[2] += r0 * r0 + r1 * r1;
+      acc[3] += 1.0;
+    }
+  }
+  block_reduce_store<4>(acc, part + 4 * blockIdx.x);
+}
+
+__global__ void k_count_active(View v, double *part) {
+  double acc[1] = {0};
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < v.N; j += gridDim.x * blockDim.x)
+    acc[0] += v.active[j] ? 1.0 : 0.0;
+  block_reduce_store<1>(acc, part + blockIdx.x);
+}
+
+rpba_status launch_sigma0(Ctx *ctx, double *sigma0, double *rms) {
+  View v = make_view(ctx);
+  int nb = ctx->red_blocks;
+  RPBA_KERNEL(ctx, "k_obs_sigma", k_obs_sigma<<<nb, 256, 0, ctx->stream>>>(v, ctx->red));
+  RPBA_KERNEL(ctx, "k_sum_partials", k_sum_partials<4><<<1, 256, 0, ctx->stream>>>(ctx->red, nb, ctx->red + 4 * nb));
+  RPBA_KERNEL(ctx, "k_count_active", k_count_active<<<nb, 256, 0, ctx->stream>>>(v, ctx->red + 4 * nb + 4));
+  RPBA_KERNEL(ctx, "k_sum_partials", k_sum_partials<1><<<1, 256, 0, ctx->stream>>>(ctx->red + 4 * nb + 4, nb, ctx->red + 5 * nb + 4));
+  double h[6];
+  RPBA_CUDA(cudaMemcpyAsync(h, ctx->red + 4 * nb, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  RPBA_CUDA(cudaMemcpyAsync(h + 4, ctx->red + 5 * nb + 4, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  RPBA_CUDA(cudaStreamSynchronize(ctx->stream));
+  double red = 2.0 * h[1] - 6.0 * ctx->M - 3.0 * h[4] + 7.0;
+  if (red < 1.0) red = 1.0;
+  if (sigma0) *sigma0 = sqrt(h[0] / red);
+  if (rms) *rms = h[3] > 0 ? sqrt(h[2] / (2.0 * h[3])) : 0.0;
+  return RPBA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// intersection (Eq. bars) and refined weights (Sec. 5.1)
+// ---------------------------------------------------------------------------
+// per instance of a running point: partial normal matrix N^(l) (sym3) and
+// gradient g^(l) at the current X_j, cameras fixed. flag bit: behind camera.
+template <typename T>
+__global__ void k_isect_inst(View v, const int *state, double *part) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= v.P) return;
+  int j = v.inst_pt[q];
+  if (state[j] != 1) return;
+  double Xj[3] = {v.X[3 * j], v.X[3 * j + 1], v.X[3 * j + 2]};
+  T N[6] = {0, 0, 0, 0, 0, 0}, g[3] = {0, 0, 0};
+  double behind = 0.0;
+  for (int k = v.inst_obs_ptr[q]; k < v.inst_obs_ptr[q + 1]; k++) {
+    int i = v.obs_cam[k];
+    CamPt<T> cp;
+    cam_point<T>(v.R + 9 * i, v.t + 3 * i, v.intr + 3 * i, Xj, cp);
+    if (!(cp.Xc[2] > T(0))) { behind = 1.0; continue; }
+    ProjJac<T> pj;
+    project_jac<T>(cp.R, cp.Xc, cp.RX, cp.f, cp.cx, cp.cy, pj);
+    T r0 = pj.u - (T)v.obs_xy[2 * k], r1 = pj.v - (T)v.obs_xy[2 * k + 1];
+    T W[3];
+    load_winv<T>(v, k, W);
+    T w = (T)v.obs_w[k];
+    // WA = w W Jx (2x3)
+    T a0[3], a1[3];
+    for (int c = 0; c < 3; c++) {
+      a0[c] = w * (W[0] * pj.Jx[c] + W[1] * pj.Jx[3 + c]);
+      a1[c] = w * (W[1] * pj.Jx[c] + W[2] * pj.Jx[3 + c]);
+    }
+    for (int r = 0; r < 3; r++) {
+      for (int c = r; c < 3; c++) N[s3idx(r, c)] += pj.Jx[r] * a0[c] + pj.Jx[3 + r] * a1[c];
+      g[r] += a0[r] * r0 + a1[r] * r1;
+    }
+  }
+  double *o = part + 10 * (size_t)q;
+  for (int e = 0; e < 6; e++) o[e] = (double)N[e];
+  for (int e = 0; e < 3; e++) o[6 + e] = (double)g[e];
+  o[9] = behind;
+}
+
+// per running point: sum the instance parts, Gauss-Newton update, checks,
+// and on convergence W^l = N - N^(l) for every instance.
+__global__ void k_isect_point(View v, int *state, int *iter, const double *part, int max_iter,
+                              double tol, double cond_max, int last) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= v.N || state[j] != 1) return;
+  int q0 = v.pt_inst_ptr[j], q1 = v.pt_inst_ptr[j + 1];
+  double N[6] = {0, 0, 0, 0, 0, 0}, g[3] = {0, 0, 0};
+  bool behind = false;
+  for (int a = q0; a < q1; a++) {
+    const double *o = part + 10 * (size_t)v.pt_inst[a];
+    for (int e = 0; e < 6; e++) N[e] += o[e];
+    for (int e = 0; e < 3; e++) g[e] += o[6 + e];
+    behind |= o[9] != 0.0;
+  }
+  bool fail = behind;
+  double inv[6];
+  if (!fail) {
+    double det = sym3_inv<double>(N, inv);
+    fail = !(det > 0.0) || !(sym3_frob<double>(N) * sym3_frob<double>(inv) <= cond_max);
+  }
+  bool conv = false;
+  if (!fail) {
+    double d[3];
+    for (int r = 0; r < 3; r++)
+      d[r] = inv[s3idx(r, 0)] * g[0] + inv[s3idx(r, 1)] * g[1] + inv[s3idx(r, 2)] * g[2];
+    double Xn[3];
+    for (int r = 0; r < 3; r++) Xn[r] = v.X[3 * j + r] - d[r];
+    for (int r = 0; r < 3; r++) v.X[3 * j + r] = Xn[r];
+    double nd = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double nx = sqrt(Xn[0] * Xn[0] + Xn[1] * Xn[1] + Xn[2] * Xn[2]);
+    conv = nd <= tol * (1.0 + nx);
+  }
+  int it = ++iter[j];
+  if (!fail && !conv && (it >= max_iter || last)) fail = true;
+  if (fail) {
+    state[j] = 3;
+    v.active[j] = 0;
+    for (int a = q0; a < q1; a++)
+      for (int e = 0; e < 6; e++) v.Wl[6 * (size_t)v.pt_inst[a] + e] = 0.0;
+  } else if (conv) {
+    state[j] = 2;
+    bool tp = (q1 - q0) >= 2;
+    for (int a = q0; a < q1; a++) {
+      int q = v.pt_inst[a];
+      const double *o = part + 10 * (size_t)q;
+      for (int e = 0; e < 6; e++) v.Wl[6 * (size_t)q + e] = tp ? N[e] - o[e] : 0.0;
+    }
+  }
+}
+
+__global__ void k_isect_start(View v, int *state, int *iter, int tp_only, int *count) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= v.N) return;
+  int nq = v.pt_inst_ptr[j + 1] - v.pt_inst_ptr[j];
+  int s = (v.active[j] && (!tp_only || nq >= 2)) ? 1 : 0;
+  state[j] = s;
+  iter[j] = 0;
+  if (s) atomicAdd(count, 1);
+}
+
+__global__ void k_isect_count(const int *state, int n, int *running, int *failed) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  if (state[j] == 1) atomicAdd(running, 1);
+  if (state[j] == 3) atomicAdd(failed, 1);
+}
+
+rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped) {
+  View v = make_view(ctx);
+  if (ctx->N == 0) { if (n_dropped) *n_dropped = 0; return RPBA_OK; }
+  RPBA_CUDA(cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(int), ctx->stream));
+  RPBA_KERNEL(ctx, "k_isect_start", k_isect_start<<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(v, ctx->isect_state, ctx->isect_iter, tp_only,
+                                                          ctx->counters));
+  int maxit = ctx->opt.isect_max_iter;
+  double tol = ctx->opt.isect_tol;
+  if (ctx->opt.precision == 1 && tol < 1e-6) tol = 1e-6;  // FP32 residuals cannot resolve less
+  for (int it = 0; it < maxit; it++) {
+    if (ctx->opt.precision == 1)
+      RPBA_KERNEL(ctx, "k_isect_inst", k_isect_inst<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, ctx->isect_state, ctx->isect_N));
+    else
+      RPBA_KERNEL(ctx, "k_isect_inst", k_isect_inst<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, ctx->isect_state, ctx->isect_N));
+    RPBA_KERNEL(ctx, "k_isect_point", k_isect_point<<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(v, ctx->isect_state, ctx->isect_iter, ctx->isect_N,
+                                                             maxit, tol, ctx->opt.cond_max, it == maxit - 1));
+  }
+  RPBA_CUDA(cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(int), ctx->stream));
+  RPBA_KERNEL(ctx, "k_isect_count", k_isect_count<<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(ctx->isect_state, ctx->N, ctx->counters,
+                                                          ctx->counters + 1));
+  int h[2];
+  RPBA_CUDA(cudaMemcpyAsync(h, ctx->counters, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RPBA_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (n_dropped) *n_dropped = h[1];
+  return RPBA_OK;
+}
+
+// exchange after bact: points seen in one sub-block take that sub-block's copy
+__global__ void k_exchange(View v) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= v.N || !v.active[j]) return;
+  int q0 = v.pt_inst_ptr[j];
+  if (v.pt_inst_ptr[j + 1] - q0 != 1) return;
+  int q = v.pt_inst[q0];
+  for (int e = 0; e < 3; e++) v.X[3 * j + e] = v.Xl[3 * (size_t)q + e];
+}
+
+// sub-block copies restart at the intersected position
+__global__ void k_tp_copies(View v, int tp_only) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= v.P) return;
+  int j = v.inst_pt[q];
+  if (tp_only && v.pt_inst_ptr[j + 1] - v.pt_inst_ptr[j] < 2) return;
+  for (int e = 0; e < 3; e++) v.Xl[3 * (size_t)q + e] = v.X[3 * j + e];
+}
+
+rpba_status launch_exchange(Ctx *ctx) {
+  if (ctx->N == 0) return RPBA_OK;
+  RPBA_KERNEL(ctx, "k_exchange", k_exchange<<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(make_view(ctx)));
+  return RPBA_OK;
+}
+
+rpba_status launch_tp_copies(Ctx *ctx, int tp_only) {
+  if (ctx->P == 0) return RPBA_OK;
+  RPBA_KERNEL(ctx, "k_tp_copies", k_tp_copies<<<nblk(ctx->P, 256), 256, 0, ctx->stream>>>(make_view(ctx), tp_only));
+  return RPBA_OK;
+}
+
+// robust weights from the per-camera scale (Sec. 5.3)
+__global__ void k_robust_weights(View v, const double *sigma, double t_v, double dw, int *count) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= v.K) return;
+  int j = v.obs_pt[k];
+  if (!v.active[j]) return;
+  int i = v.obs_cam[k];
+  const double *R = v.R + 9 * i, *t = v.t + 3 * i, *X = v.X + 3 * j;
+  double Xc[3];
+  for (int r = 0; r < 3; r++) Xc[r] = R[3 * r] * X[0] + R[3 * r + 1] * X[1] + R[3 * r + 2] * X[2] + t[r];
+  double f = v.intr[3 * i], iz = 1.0 / Xc[2];
+  double r0 = f * Xc[0] * iz + v.intr[3 * i + 1] - v.obs_xy[2 * k];
+  double r1 = f * Xc[1] * iz + v.intr[3 * i + 2] - v.obs_xy[2 * k + 1];
+  double W0 = 1, W1 = 0, W2 = 1;
+  if (v.has_winv) { W0 = v.obs_winv[3 * k]; W1 = v.obs_winv[3 * k + 1]; W2 = v.obs_winv[3 * k + 2]; }
+  double nr = sqrt(W0 * r0 * r0 + 2.0 * W1 * r0 * r1 + W2 * r1 * r1);
+  double s = sigma[i];
+  bool out = (s > 0.0) && (nr / s > t_v);
+  v.obs_w[k] = out ? dw : 1.0;
+  if (out) atomicAdd(count, 1);
+}
+
+rpba_status launch_robust_weights(Ctx *ctx, int *n_down) {
+  RPBA_TRY(launch_camera_scale(ctx));
+  RPBA_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(int), ctx->stream));
+  if (ctx->K)
+    RPBA_KERNEL(ctx, "k_robust_weights", k_robust_weights<<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(make_view(ctx), ctx->cam_sigma, ctx->opt.t_v,
+                                                                ctx->opt.downweight, ctx->counters));
+  if (n_down) {
+    RPBA_CUDA(cudaMemcpyAsync(ctx->h_pinned_counter, ctx->counters, sizeof(int), cudaMemcpyDeviceToHost,
+                              ctx->stream));
+    RPBA_CUDA(cudaStreamSynchronize(ctx->stream));
+    *n_down = ctx->h_pinned_counter[0];
+  }
+  return RPBA_OK;
+}
+
+__global__ void k_eliminate(View v) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= v.K) return;
+  if (v.obs_w[k] != 1.0) v.active[v.obs_pt[k]] = 0;
+}
+
+rpba_status launch_eliminate(Ctx *ctx) {
+  if (!ctx->K) return RPBA_OK;
+  RPBA_KERNEL(ctx, "k_eliminate", k_eliminate<<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(make_view(ctx)));
+  return RPBA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// sub-block cost F_l (Eq. bact) per instance, then per sub-block
+// ---------------------------------------------------------------------------
+// trial = 1 evaluates the trial cameras/instances of running sub-blocks
+template <typename T>
+__global__ void k_inst_cost(View v, int trial, const int *run) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= v.P) return;
+  int l = v.inst_sub[q];
+  int j = v.inst_pt[q];
+  if ((run && !run[l]) || !v.active[j]) { v.inst_cost[q] = 0.0; return; }
+  const double *R = trial ? v.Rt : v.R;
+  const double *tt = trial ? v.tt : v.t;
+  const double *Xq = (trial ? v.Xlt : v.Xl) + 3 * (size_t)q;
+  double Xd[3] = {Xq[0], Xq[1], Xq[2]};
+  double F = 0.0;
+  bool behind = false;
+  for (int k = v.inst_obs_ptr[q]; k < v.inst_obs_ptr[q + 1]; k++) {
+    int i = v.obs_cam[k];
+    CamPt<T> cp;
+    cam_point<T>(R + 9 * i, tt + 3 * i, v.intr + 3 * i, Xd, cp);
+    if (!(cp.Xc[2] > T(0))) { behind = true; continue; }
+    T iz = T(1) / cp.Xc[2];
+    T r0 = cp.f * cp.Xc[0] * iz + cp.cx - (T)v.obs_xy[2 * k];
+    T r1 = cp.f * cp.Xc[1] * iz + cp.cy - (T)v.obs_xy[2 * k + 1];
+    T W[3];
+    load_winv<T>(v, k, W);
+    F += v.obs_w[k] * (double)(W[0] * r0 * r0 + T(2) * W[1] * r0 * r1 + W[2] * r1 * r1);
+  }
+  // TP control term (X^l - X_TP)^T W^l (X^l - X_TP)
+  const double *W = v.Wl + 6 * (size_t)q;
+  double d[3] = {Xd[0] - v.X[3 * j], Xd[1] - v.X[3 * j + 1], Xd[2] - v.X[3 * j + 2]};
+  F += W[0] * d[0] * d[0] + W[3] * d[1] * d[1] + W[5] * d[2] * d[2] +
+       2.0 * (W[1] * d[0] * d[1] + W[2] * d[0] * d[2] + W[4] * d[1] * d[2]);
+  v.inst_cost[q] = behind ? INFINITY : F;
+}
+
+// one block per sub-block: deterministic sum over its instance range
+__global__ void k_sub_sum(View v, const int *run, double *F) {
+  int l = blockIdx.x;
+  if (run && !run[l]) return;
+  double acc[1] = {0.0};
+  for (int q = v.sub_inst_ptr[l] + threadIdx.x; q < v.sub_inst_ptr[l + 1]; q += blockDim.x)
+    acc[0] += v.inst_cost[q];
+  __shared__ double out[1];
+  block_reduce_store<1>(acc, out);
+  __syncthreads();
+  if (threadIdx.x == 0) F[l] = out[0];
+}
+
+static rpba_status sub_costs_impl(Ctx *ctx, int trial, const int *run, double *F_dev) {
+  View v = make_view(ctx);
+  if (ctx->P) {
+    if (ctx->opt.precision == 1)
+      RPBA_KERNEL(ctx, "k_inst_cost", k_inst_cost<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, trial, run));
+    else
+      RPBA_KERNEL(ctx, "k_inst_cost", k_inst_cost<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, trial, run));
+  }
+  RPBA_KERNEL(ctx, "k_sub_sum", k_sub_sum<<<ctx->L, 256, 0, ctx->stream>>>(v, run, F_dev));
+  return RPBA_OK;
+}
+
+rpba_status launch_sub_costs(Ctx *ctx, int trial, double *F_dev) {
+  return sub_costs_impl(ctx, trial, trial ? ctx->lm_run : nullptr, F_dev);
+}
+
+// ---------------------------------------------------------------------------
+// normal equations of the sub-blocks and the Schur complement (Sec. 2, 5.5)
+// ---------------------------------------------------------------------------
+// per instance: N_XX (+ W^l, damped), g_X, Ninv; per observation N_XC = w A_X^T W A_C
+// and Z = Ninv N_XC (both 3x6 row-major)
+template <typename T>
+__global__ void k_linearize(View v, const double *lambda, const int *run, T *NXC, T *Z, T *Ninv_out,
+                            T *gX_out) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= v.P) return;
+  int l = v.inst_sub[q];
+  if (!run[l]) return;
+  int j = v.inst_pt[q];
+  int k0 = v.inst_obs_ptr[q], k1 = v.inst_obs_ptr[q + 1];
+  if (!v.active[j]) {
+    for (int e = 0; e < 6; e++) Ninv_out[6 * (size_t)q + e] = 0;
+    for (int e = 0; e < 3; e++) gX_out[3 * (size_t)q + e] = 0;
+    for (int k = k0; k < k1; k++)
+      for (int e = 0; e < 18; e++) { NXC[18 * (size_t)k + e] = 0; Z[18 * (size_t)k + e] = 0; }
+    return;
+  }
+  double Xd[3] = {v.Xl[3 * (size_t)q], v.Xl[3 * (size_t)q + 1], v.Xl[3 * (size_t)q + 2]};
+  T N[6] = {0, 0, 0, 0, 0, 0}, g[3] = {0, 0, 0};
+  for (int k = k0; k < k1; k++) {
+    int i = v.obs_cam[k];
+    CamPt<T> cp;
+    cam_point<T>(v.R + 9 * i, v.t + 3 * i, v.intr + 3 * i, Xd, cp);
+    ProjJac<T> pj;
+    project_jac<T>(cp.R, cp.Xc, cp.RX, cp.f, cp.cx, cp.cy, pj);
+    T r0 = pj.u - (T)v.obs_xy[2 * k], r1 = pj.v - (T)v.obs_xy[2 * k + 1];
+    T W[3];
+    load_winv<T>(v, k, W);
+    T w = (T)v.obs_w[k];
+    T a0[3], a1[3];  // rows of w W A_X, transposed use
+    for (int c = 0; c < 3; c++) {
+      a0[c] = w * (W[0] * pj.Jx[c] + W[1] * pj.Jx[3 + c]);
+      a1[c] = w * (W[1] * pj.Jx[c] + W[2] * pj.Jx[3 + c]);
+    }
+    for (int r = 0; r < 3; r++) {
+      for (int c = r; c < 3; c++) N[s3idx(r, c)] += pj.Jx[r] * a0[c] + pj.Jx[3 + r] * a1[c];
+      g[r] += a0[r] * r0 + a1[r] * r1;
+    }
+    // N_XC = (w W A_X)^T A_C : row r (point coord) = a0[r] Jc[0,:] + a1[r] Jc[1,:]
+    T *o = NXC + 18 * (size_t)k;
+    for (int r = 0; r < 3; r++)
+      for (int c = 0; c < 6; c++) o[6 * r + c] = a0[r] * pj.Jc[c] + a1[r] * pj.Jc[6 + c];
+  }
+  // TP control term
+  const double *Wq = v.Wl + 6 * (size_t)q;
+  double d[3] = {Xd[0] - v.X[3 * j], Xd[1] - v.X[3 * j + 1], Xd[2] - v.X[3 * j + 2]};
+  for (int e = 0; e < 6; e++) N[e] += (T)Wq[e];
+  for (int r = 0; r < 3; r++)
+    g[r] += (T)(Wq[s3idx(r, 0)] * d[0] + Wq[s3idx(r, 1)] * d[1] + Wq[s3idx(r, 2)] * d[2]);
+  // damping of the point block
+  T lam = (T)lambda[l];
+  N[0] += lam * N[0]; N[3] += lam * N[3]; N[5] += lam * N[5];
+  T inv[6];
+  sym3_inv<T>(N, inv);
+  for (int e = 0; e < 6; e++) Ninv_out[6 * (size_t)q + e] = inv[e];
+  for (int e = 0; e < 3; e++) gX_out[3 * (size_t)q + e] = g[e];
+  for (int k = k0; k < k1; k++) {
+    const T *B = NXC + 18 * (size_t)k;
+    T *o = Z + 18 * (size_t)k;
+    for (int r = 0; r < 3; r++)
+      for (int c = 0; c < 6; c++)
+        o[6 * r + c] = inv[s3idx(r, 0)] * B[c] + inv[s3idx(r, 1)] * B[6 + c] + inv[s3idx(r, 2)] * B[12 + c];
+  }
+}
+
+// one warp per camera of a running sub-block: diagonal RCS block
+//   S_ii = U_ii + lambda diag(U_ii) - sum_k N_XC,k^T Z_k,  U_ii = sum_k w A_C^T W A_C
+// and right-hand side y_i = -sum_k w A_C^T W v + sum_k Z_k^T g_X
+template <typename T>
+__global__ void k_camera_blocks(View v, const double *lambda, const int *run, const T *NXC, const T *Z,
+                                const T *gX) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= v.M) return;
+  int i = warp;
+  int l = v.cam_sub[i];
+  if (!run[l]) return;
+  T U[21], gc[6], SZ[21], yz[6];
+  for (int e = 0; e < 21; e++) { U[e] = 0; SZ[e] = 0; }
+  for (int e = 0; e < 6; e++) { gc[e] = 0; yz[e] = 0; }
+  for (int p = v.cam_obs_ptr[i] + lane; p < v.cam_obs_ptr[i + 1]; p += 32) {
+    int k = v.cam_obs[p];
+    int q = v.obs_inst[k];
+    int j = v.inst_pt[q];
+    if (!v.active[j]) continue;
+    double Xd[3] = {v.Xl[3 * (size_t)q], v.Xl[3 * (size_t)q + 1], v.Xl[3 * (size_t)q + 2]};
+    CamPt<T> cp;
+    cam_point<T>(v.R + 9 * i, v.t + 3 * i, v.intr + 3 * i, Xd, cp);
+    ProjJac<T> pj;
+    project_jac<T>(cp.R, cp.Xc, cp.RX, cp.f, cp.cx, cp.cy, pj);
+    T r0 = pj.u - (T)v.obs_xy[2 * k], r1 = pj.v - (T)v.obs_xy[2 * k + 1];
+    T W[3];
+    load_winv<T>(v, k, W);
+    T w = (T)v.obs_w[k];
+    T b0[6], b1[6];  // w W A_C
+    for (int c = 0; c < 6; c++) {
+      b0[c] = w * (W[0] * pj.Jc[c] + W[1] * pj.Jc[6 + c]);
+      b1[c] = w * (W[1] * pj.Jc[c] + W[2] * pj.Jc[6 + c]);
+    }
+    const T *B = NXC + 18 * (size_t)k, *Zk = Z + 18 * (size_t)k, *gq = gX + 3 * (size_t)q;
+    int e = 0;
+    for (int r = 0; r < 6; r++) {
+      gc[r] += b0[r] * r0 + b1[r] * r1;
+      yz[r] += Zk[r] * gq[0] + Zk[6 + r] * gq[1] + Zk[12 + r] * gq[2];
+      for (int c = r; c < 6; c++, e++) {
+        U[e] += pj.Jc[r] * b0[c] + pj.Jc[6 + r] * b1[c];
+        SZ[e] += B[r] * Zk[c] + B[6 + r] * Zk[6 + c] + B[12 + r] * Zk[12 + c];
+      }
+    }
+  }
+  // warp reductions
+  for (int e = 0; e < 21; e++)
+    for (int o = 16; o > 0; o >>= 1) {
+      U[e] += __shfl_down_sync(0xffffffffu, U[e], o);
+      SZ[e] += __shfl_down_sync(0xffffffffu, SZ[e], o);
+    }
+  for (int e = 0; e < 6; e++)
+    for (int o = 16; o > 0; o >>= 1) {
+      gc[e] += __shfl_down_sync(0xffffffffu, gc[e], o);
+      yz[e] += __shfl_down_sync(0xffffffffu, yz[e], o);
+    }
+  if (lane == 0) {
+    double lam = lambda[l];
+    int li = v.cam_local[i];
+    int np = v.npad[l];
+    double *S = v.S + v.S_off[l];
+    int e = 0;
+    for (int r = 0; r < 6; r++)
+      for (int c = r; c < 6; c++, e++) {
+        double val = (double)U[e] - (double)SZ[e];
+        if (r == c) val += lam * (double)U[e];
+        S[(size_t)(6 * li + r) * np + 6 * li + c] = val;
+        S[(size_t)(6 * li + c) * np + 6 * li + r] = val;
+      }
+    double *yv = v.y + v.ycam_off[l];
+    for (int r = 0; r < 6; r++) yv[6 * li + r] = -(double)gc[r] + (double)yz[r];
+  }
+}
+
+// off-diagonal Schur blocks: one thread per (pair, row r):
+//   S[(6 ia + r), 6 ib + c] -= sum_e N_XC,a[e][r] Z_b[e][c]    (ia > ib)
+template <typename T>
+__global__ void k_schur_pairs(View v, const int *run, const int *pa, const int *pb, long long npairs,
+                              const T *NXC, const T *Z) {
+  long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= npairs * 6) return;
+  long long p = tid / 6;
+  int r = (int)(tid - p * 6);
+  int a = pa[p], b = pb[p];
+  int q = v.obs_inst[a];
+  int l = v.inst_sub[q];
+  if (!run[l] || !v.active[v.inst_pt[q]]) return;
+  int ia = v.cam_local[v.obs_cam[a]], ib = v.cam_local[v.obs_cam[b]];
+  const T *A = NXC + 18 * (size_t)a, *Zb = Z + 18 * (size_t)b;
+  T x0 = A[r], x1 = A[6 + r], x2 = A[12 + r];
+  double *row = v.S + v.S_off[l] + (size_t)(6 * ia + r) * v.npad[l] + 6 * ib;
+#pragma unroll
+  for (int c = 0; c < 6; c++) {
+    T val = x0 * Zb[c] + x1 * Zb[6 + c] + x2 * Zb[12 + c];
+    atomicAdd(row + c, -(double)val);
+  }
+}
+
+// zero the RCS of running sub-blocks, identity on the padding
+__global__ void k_rcs_clear(View v, const int *run, int L) {
+  int l = blockIdx.y;
+  if (l >= L || !run[l]) return;
+  int np = v.npad[l];
+  int n = 6 * (v.sub_cam_ptr[l + 1] - v.sub_cam_ptr[l]);
+  double *S = v.S + v.S_off[l];
+  size_t tot = (size_t)np * np;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    size_t r = e / np, c = e - r * np;
+    S[e] = (r == c && (int)r >= n) ? 1.0 : 0.0;
+  }
+  double *yv = v.y + v.ycam_off[l];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < np; e += gridDim.x * blockDim.x)
+    if (e >= n) yv[e] = 0.0;
+}
+
+rpba_status launch_build_rcs(Ctx *ctx, const double *lambda_dev, const int *run_dev) {
+  View v = make_view(ctx);
+  dim3 gclr(64, ctx->L);
+  RPBA_KERNEL(ctx, "k_rcs_clear", k_rcs_clear<<<gclr, 256, 0, ctx->stream>>>(v, run_dev, ctx->L));
+  if (ctx->P == 0) return RPBA_OK;
+  if (ctx->opt.precision == 1) {
+    float *NXC = (float *)ctx->NXC, *Z = (float *)ctx->Z;
+    RPBA_KERNEL(ctx, "k_linearize", k_linearize<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, lambda_dev, run_dev, NXC, Z,
+                                                                   (float *)ctx->Ninv, (float *)ctx->gX));
+    RPBA_KERNEL(ctx, "k_camera_blocks", k_camera_blocks<float><<<nblk((long long)ctx->M * 32, 128), 128, 0, ctx->stream>>>(
+        v, lambda_dev, run_dev, NXC, Z, (const float *)ctx->gX));
+    if (ctx->n_pairs)
+      RPBA_KERNEL(ctx, "k_schur_pairs", k_schur_pairs<float><<<nblk(ctx->n_pairs * 6, 256), 256, 0, ctx->stream>>>(
+          v, run_dev, ctx->pair_a, ctx->pair_b, ctx->n_pairs, NXC, Z));
+  } else {
+    double *NXC = (double *)ctx->NXC, *Z = (double *)ctx->Z;
+    RPBA_KERNEL(ctx, "k_linearize", k_linearize<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, lambda_dev, run_dev, NXC, Z,
+                                                                    (double *)ctx->Ninv, (double *)ctx->gX));
+    RPBA_KERNEL(ctx, "k_camera_blocks", k_camera_blocks<double><<<nblk((long long)ctx->M * 32, 128), 128, 0, ctx->stream>>>(
+        v, lambda_dev, run_dev, NXC, Z, (const double *)ctx->gX));
+    if (ctx->n_pairs)
+      RPBA_KERNEL(ctx, "k_schur_pairs", k_schur_pairs<double><<<nblk(ctx->n_pairs * 6, 256), 256, 0, ctx->stream>>>(
+          v, run_dev, ctx->pair_a, ctx->pair_b, ctx->n_pairs, NXC, Z));
+  }
+  return RPBA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// back-substitution, trial state
+// ---------------------------------------------------------------------------
+// dX = Ninv (-g_X - sum_k N_XC,k dC_i(k)); X^l trial = X^l + dX
+template <typename T>
+__global__ void k_backsub(View v, const int *run, const T *NXC, const T *Ninv, const T *gX) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= v.P) return;
+  int l = v.inst_sub[q];
+  if (!run[l]) return;
+  const double *Xq = v.Xl + 3 * (size_t)q;
+  double *Xt = v.Xlt + 3 * (size_t)q;
+  if (!v.active[v.inst_pt[q]]) {
+    for (int e = 0; e < 3; e++) Xt[e] = Xq[e];
+    return;
+  }
+  const double *dC = v.dC + v.ycam_off[l];
+  T rhs[3] = {-gX[3 * (size_t)q], -gX[3 * (size_t)q + 1], -gX[3 * (size_t)q + 2]};
+  for (int k = v.inst_obs_ptr[q]; k < v.inst_obs_ptr[q + 1]; k++) {
+    const double *dc = dC + 6 * v.cam_local[v.obs_cam[k]];
+    const T *B = NXC + 18 * (size_t)k;
+    for (int r = 0; r < 3; r++) {
+      T s = 0;
+      for (int c = 0; c < 6; c++) s += B[6 * r + c] * (T)dc[c];
+      rhs[r] -= s;
+    }
+  }
+  const T *iv = Ninv + 6 * (size_t)q;
+  for (int r = 0; r < 3; r++)
+    Xt[r] = Xq[r] + (double)(iv[s3idx(r, 0)] * rhs[0] + iv[s3idx(r, 1)] * rhs[1] + iv[s3idx(r, 2)] * rhs[2]);
+}
+
+// trial cameras: R' = exp([dw]x) R, t' = t + dt
+__global__ void k_cam_trial(View v, const int *run) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= v.M) return;
+  int l = v.cam_sub[i];
+  const double *R = v.R + 9 * i;
+  double *Rt = v.Rt + 9 * i;
+  if (!run[l]) {
+    for (int e = 0; e < 9; e++) Rt[e] = R[e];
+    for (int e = 0; e < 3; e++) v.tt[3 * i + e] = v.t[3 * i + e];
+    return;
+  }
+  const double *dc = v.dC + v.ycam_off[l] + 6 * v.cam_local[i];
+  double dR[9];
+  rodrigues(dc, dR);
+  for (int r = 0; r < 3; r++)
+    for (int c = 0; c < 3; c++)
+      Rt[3 * r + c] = dR[3 * r] * R[c] + dR[3 * r + 1] * R[3 + c] + dR[3 * r + 2] * R[6 + c];
+  for (int e = 0; e < 3; e++) v.tt[3 * i + e] = v.t[3 * i + e] + dc[3 + e];
+}
+
+rpba_status launch_backsub_trial(Ctx *ctx, const int *run_dev) {
+  View v = make_view(ctx);
+  if (ctx->P) {
+    if (ctx->opt.precision == 1)
+      RPBA_KERNEL(ctx, "k_backsub", k_backsub<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, run_dev, (const float *)ctx->NXC,
+                                                                   (const float *)ctx->Ninv, (const float *)ctx->gX));
+    else
+      RPBA_KERNEL(ctx, "k_backsub", k_backsub<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, run_dev, (const double *)ctx->NXC,
+                                                                    (const double *)ctx->Ninv, (const double *)ctx->gX));
+  }
+  if (ctx->M) RPBA_KERNEL(ctx, "k_cam_trial", k_cam_trial<<<nblk(ctx->M, 128), 128, 0, ctx->stream>>>(v, run_dev));
+  return sub_costs_impl(ctx, 1, run_dev, ctx->lm_Ft);
+}
+
+// ---------------------------------------------------------------------------
+// LM control per sub-block (Sec. 5.5 and the stopping reading)
+// ---------------------------------------------------------------------------
+__global__ void k_lm_init(View v, const int *sub_nc, double lambda0, int grace, double *lam, double *F,
+                          double *best, int *gr, int *rej, int *it, int *run, const double *F0) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= v.L) return;
+  lam[l] = lambda0;
+  F[l] = F0[l];
+  best[l] = F0[l];
+  gr[l] = grace;
+  rej[l] = 0;
+  it[l] = 0;
+  run[l] = (v.sub_cam_ptr[l + 1] - v.sub_cam_ptr[l]) > 0;
+}
+
+__global__ void k_lm_decide(int L, double lambda0, double stop_ratio, int max_inner, int max_reject,
+                            double *lam, double *F, const double *Ft, double *best, int *gr, int *rej, int *it,
+                            int *run, int *acc, const int *fail, int *n_running) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= L) return;
+  acc[l] = 0;
+  if (!run[l]) return;
+  it[l] += 1;
+  double ft = Ft[l];
+  bool ok = !fail[l] && isfinite(ft) && ft < F[l];
+  bool stop = false;
+  if (!ok) {
+    lam[l] *= 10.0;
+    if (++rej[l] > max_reject) stop = true;
+  } else {
+    acc[l] = 1;
+    rej[l] = 0;
+    double ratio = best[l] / (ft > 1e-300 ? ft : 1e-300);
+    F[l] = ft;
+    double nl = lam[l] / 10.0;
+    lam[l] = nl > lambda0 ? nl : lambda0;
+    if (ft < best[l]) best[l] = ft;
+    if (ratio < stop_ratio) {
+      if (gr[l] > 0) gr[l] -= 1;
+      else stop = true;
+    }
+  }
+  if (it[l] >= max_inner) stop = true;
+  if (stop) run[l] = 0;
+  else atomicAdd(n_running, 1);
+}
+
+// copy the trial state of accepted sub-blocks
+__global__ void k_lm_apply_cams(View v, const int *acc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= v.M || !acc[v.cam_sub[i]]) return;
+  double *R = const_cast<double *>(v.R) + 9 * i;
+  double *t = const_cast<double *>(v.t) + 3 * i;
+  for (int e = 0; e < 9; e++) R[e] = v.Rt[9 * i + e];
+  for (int e = 0; e < 3; e++) t[e] = v.tt[3 * i + e];
+}
+
+__global__ void k_lm_apply_inst(View v, const int *acc) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= v.P || !acc[v.inst_sub[q]]) return;
+  for (int e = 0; e < 3; e++) v.Xl[3 * (size_t)q + e] = v.Xlt[3 * (size_t)q + e];
+}
+
+rpba_status launch_lm_apply(Ctx *ctx, const int *acc_dev) {
+  View v = make_view(ctx);
+  if (ctx->M) RPBA_KERNEL(ctx, "k_lm_apply_cams", k_lm_apply_cams<<<nblk(ctx->M, 128), 128, 0, ctx->stream>>>(v, acc_dev));
+  if (ctx->P) RPBA_KERNEL(ctx, "k_lm_apply_inst", k_lm_apply_inst<<<nblk(ctx->P, 256), 256, 0, ctx->stream>>>(v, acc_dev));
+  return RPBA_OK;
+}
+
+rpba_status launch_lm_init(Ctx *ctx) {
+  RPBA_TRY(sub_costs_impl(ctx, 0, nullptr, ctx->lm_Ft));
+  RPBA_KERNEL(ctx, "k_lm_init", k_lm_init<<<nblk(ctx->L, 128), 128, 0, ctx->stream>>>(make_view(ctx), nullptr, ctx->opt.lambda0, ctx->opt.grace,
+                                                        ctx->lm_lambda, ctx->lm_F, ctx->lm_best, ctx->lm_grace,
+                                                        ctx->lm_rej, ctx->lm_it, ctx->lm_run, ctx->lm_Ft));
+  return RPBA_OK;
+}
+
+rpba_status launch_lm_decide(Ctx *ctx) {
+  RPBA_KERNEL(ctx, "k_lm_decide", k_lm_decide<<<nblk(ctx->L, 128), 128, 0, ctx->stream>>>(
+      ctx->L, ctx->opt.lambda0, ctx->opt.stop_ratio, ctx->opt.max_inner, ctx->opt.max_reject, ctx->lm_lambda,
+      ctx->lm_F, ctx->lm_Ft, ctx->lm_best, ctx->lm_grace, ctx->lm_rej, ctx->lm_it, ctx->lm_run, ctx->lm_acc,
+      ctx->lm_cholfail, ctx->counters));
+  return RPBA_OK;
+}
+
+__global__ void k_fill_int(int *p, int n, int val) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) p[e] = val;
+}
+__global__ void k_fill_double(double *p, long long n, double val) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) p[e] = val;
+}
+rpba_status launch_fill_int(Ctx *ctx, int *p, int n, int v) {
+  if (n <= 0) return RPBA_OK;
+  RPBA_KERNEL(ctx, "k_fill_int", k_fill_int<<<nblk(n, 256), 256, 0, ctx->stream>>>(p, n, v));
+  return RPBA_OK;
+}
+rpba_status launch_fill_double(Ctx *ctx, double *p, long long n, double v) {
+  if (n <= 0) return RPBA_OK;
+  RPBA_KERNEL(ctx, "k_fill_double", k_fill_double<<<nblk(n, 256), 256, 0, ctx->stream>>>(p, n, v));
+  return RPBA_OK;
+}
+
+}  // namespace rpba

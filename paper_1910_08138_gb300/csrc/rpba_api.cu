@@ -1,0 +1,881 @@
+// rpba_api.cu -- C ABI of the GB300 RPBA library (include/rpba.h): context
+// creation (validation, sub-block topology, device layout), state access, and
+// the host driver of the iteration of Sec. 5 (bact of all sub-blocks in lock
+// step, exchange, bars, convergence, robust stage).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <numeric>
+
+#include "rpba_internal.cuh"
+
+using namespace rpba;
+
+struct rpba_ctx {
+  Ctx c;
+};
+
+namespace rpba {
+
+// ---------------------------------------------------------------------------
+// pose <-> rotation, covariance
+// ---------------------------------------------------------------------------
+__global__ void k_pose_to_R(int M, const double *pose, double *R, double *t) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  double w[3] = {pose[6 * i], pose[6 * i + 1], pose[6 * i + 2]};
+  rodrigues(w, R + 9 * i);
+  for (int e = 0; e < 3; e++) t[3 * i + e] = pose[6 * i + 3 + e];
+}
+
+// angle-axis vector of R (log map; axis from the symmetric part near pi)
+__global__ void k_R_to_pose(int M, const double *R, const double *t, double *pose) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const double *Q = R + 9 * i;
+  double c = 0.5 * (Q[0] + Q[4] + Q[8] - 1.0);
+  c = fmin(1.0, fmax(-1.0, c));
+  double th = acos(c);
+  double v[3] = {Q[7] - Q[5], Q[2] - Q[6], Q[3] - Q[1]};
+  double w[3];
+  if (th < 1e-6) {
+    for (int e = 0; e < 3; e++) w[e] = 0.5 * v[e];
+  } else if (th < 3.14159265358979323846 - 1e-4) {
+    double s = th / (2.0 * sin(th));
+    for (int e = 0; e < 3; e++) w[e] = s * v[e];
+  } else {
+    double B[3] = {(Q[0] - c) / (1.0 - c), (Q[4] - c) / (1.0 - c), (Q[8] - c) / (1.0 - c)};
+    int k = 0;
+    if (B[1] > B[k]) k = 1;
+    if (B[2] > B[k]) k = 2;
+    double a[3];
+    a[k] = sqrt(fmax(B[k], 0.0));
+    for (int e = 0; e < 3; e++)
+      if (e != k) a[e] = (Q[3 * k + e] + Q[3 * e + k]) / (2.0 * (1.0 - c) * a[k]);
+    double n = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    double sg = (a[0] * v[0] + a[1] * v[1] + a[2] * v[2]) < 0.0 ? -1.0 : 1.0;
+    for (int e = 0; e < 3; e++) w[e] = sg * th * a[e] / n;
+  }
+  for (int e = 0; e < 3; e++) {
+    pose[6 * i + e] = w[e];
+    pose[6 * i + 3 + e] = t[3 * i + e];
+  }
+}
+
+// C_j = N_j^-1 with N_j = sum_k w A_X^T W A_X over all observations of j
+__global__ void k_covariance(int n, const int *ids, const double *R, const double *t, const double *intr,
+                             const double *X, const uint8_t *active, const int *pt_inst_ptr, const int *pt_inst,
+                             const int *inst_obs_ptr, const int *obs_cam, const double *obs_winv, int has_winv,
+                             const double *obs_w, int N, double *out) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  int j = ids[a];
+  bool ok = j >= 0 && j < N && active[j];
+  double Nm[6] = {0, 0, 0, 0, 0, 0};
+  if (ok) {
+    const double *Xj = X + 3 * j;
+    for (int s = pt_inst_ptr[j]; s < pt_inst_ptr[j + 1] && ok; s++) {
+      int q = pt_inst[s];
+      for (int k = inst_obs_ptr[q]; k < inst_obs_ptr[q + 1]; k++) {
+        int i = obs_cam[k];
+        double Rl[9], Xc[3], RX[3];
+        for (int e = 0; e < 9; e++) Rl[e] = R[9 * i + e];
+        for (int r = 0; r < 3; r++) {
+          RX[r] = Rl[3 * r] * Xj[0] + Rl[3 * r + 1] * Xj[1] + Rl[3 * r + 2] * Xj[2];
+          Xc[r] = RX[r] + t[3 * i + r];
+        }
+        if (!(Xc[2] > 0.0)) { ok = false; break; }
+        ProjJac<double> pj;
+        project_jac<double>(Rl, Xc, RX, intr[3 * i], intr[3 * i + 1], intr[3 * i + 2], pj);
+        double W0 = 1, W1 = 0, W2 = 1;
+        if (has_winv) { W0 = obs_winv[3 * k]; W1 = obs_winv[3 * k + 1]; W2 = obs_winv[3 * k + 2]; }
+        double w = obs_w[k];
+        for (int r = 0; r < 3; r++)
+          for (int c = r; c < 3; c++) {
+            double a0 = W0 * pj.Jx[c] + W1 * pj.Jx[3 + c], a1 = W1 * pj.Jx[c] + W2 * pj.Jx[3 + c];
+            Nm[s3idx(r, c)] += w * (pj.Jx[r] * a0 + pj.Jx[3 + r] * a1);
+          }
+      }
+    }
+  }
+  double inv[6];
+  if (ok) ok = sym3_inv<double>(Nm, inv) > 0.0;
+  for (int r = 0; r < 3; r++)
+    for (int c = 0; c < 3; c++) out[9 * a + 3 * r + c] = ok ? inv[s3idx(r, c)] : NAN;
+}
+
+}  // namespace rpba
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+static rpba_status dev_alloc(Ctx *ctx, void **p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  void *q = nullptr;
+  if (ctx->opt.dev_alloc) {
+    q = ctx->opt.dev_alloc(bytes, ctx->opt.alloc_user);
+    if (!q) {
+      ctx->err = "device allocator hook returned NULL";
+      return RPBA_ERR_OOM;
+    }
+  } else {
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+      ctx->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+      return e == cudaErrorMemoryAllocation ? RPBA_ERR_OOM : RPBA_ERR_CUDA;
+    }
+  }
+  ctx->allocs.push_back(q);
+  *p = q;
+  return RPBA_OK;
+}
+
+template <typename T>
+static rpba_status alloc_n(Ctx *ctx, T **p, size_t n) {
+  return dev_alloc(ctx, (void **)p, n * sizeof(T));
+}
+
+template <typename T>
+static rpba_status upload(Ctx *ctx, T **p, const T *host, size_t n) {
+  RPBA_TRY(alloc_n(ctx, p, n));
+  if (n) RPBA_CUDA(cudaMemcpyAsync(*p, host, n * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+  return RPBA_OK;
+}
+
+static rpba_status sync(Ctx *ctx) {
+  RPBA_CUDA(cudaStreamSynchronize(ctx->stream));
+  return RPBA_OK;
+}
+
+static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
+
+extern "C" void rpba_default_options(rpba_options *o) {
+  memset(o, 0, sizeof(*o));
+  o->lambda0 = 1e-4;
+  o->t_v = 4.0;
+  o->downweight = 1e-4;
+  o->stop_ratio = 1.01;
+  o->grace = 1;
+  o->max_outer = 30;
+  o->max_inner = 20;
+  o->max_reject = 6;
+  o->robust = 0;
+  o->robust_from_start = 0;
+  o->isect_max_iter = 10;
+  o->isect_tol = 1e-10;
+  o->cond_max = 1e12;
+  o->precision = 0;
+  o->solver = 0;
+  o->pcg_tol = 1e-8;
+  o->pcg_max_iter = 500;
+}
+
+extern "C" const char *rpba_last_error(const rpba_ctx *ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
+
+extern "C" void rpba_destroy(rpba_ctx *h) {
+  if (!h) return;
+  Ctx *ctx = &h->c;
+  cudaStreamSynchronize(ctx->stream);
+  for (void *p : ctx->allocs) {
+    if (ctx->opt.dev_free) ctx->opt.dev_free(p, ctx->opt.alloc_user);
+    else cudaFree(p);
+  }
+  if (ctx->h_pinned_counter) cudaFreeHost(ctx->h_pinned_counter);
+  if (ctx->h_pinned_d) cudaFreeHost(ctx->h_pinned_d);
+  delete h;
+}
+
+// ---------------------------------------------------------------------------
+// creation: validation and topology
+// ---------------------------------------------------------------------------
+static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
+  const int M = pb->n_cams, N = pb->n_points, K = pb->n_obs;
+  ctx->M = M; ctx->N = N; ctx->K = K;
+  if (M < 0 || N < 0 || K < 0 || (M && (!pb->cam_pose || !pb->cam_intr || !pb->cam_subblock)) ||
+      (N && !pb->points) || (K && (!pb->obs_cam || !pb->obs_point || !pb->obs_xy))) {
+    ctx->err = "invalid sizes or NULL input arrays";
+    return RPBA_ERR_INVALID_ARG;
+  }
+  int L = 0;
+  for (int i = 0; i < M; i++) {
+    int s = pb->cam_subblock[i];
+    if (s < 0 || s >= (1 << 20)) { ctx->err = "cam_subblock out of range"; return RPBA_ERR_INVALID_ARG; }
+    L = std::max(L, s + 1);
+  }
+  ctx->L = L;
+  for (int k = 0; k < K; k++) {
+    if (pb->obs_cam[k] < 0 || pb->obs_cam[k] >= M || pb->obs_point[k] < 0 || pb->obs_point[k] >= N) {
+      ctx->err = "observation index out of range";
+      return RPBA_ERR_INVALID_ARG;
+    }
+  }
+  for (long long e = 0; e < 6LL * M; e++)
+    if (!isfinite(pb->cam_pose[e])) { ctx->err = "non-finite camera pose"; return RPBA_ERR_NUMERIC; }
+  for (long long e = 0; e < 3LL * N; e++)
+    if (!isfinite(pb->points[e])) { ctx->err = "non-finite point"; return RPBA_ERR_NUMERIC; }
+  for (long long e = 0; e < 2LL * K; e++)
+    if (!isfinite(pb->obs_xy[e])) { ctx->err = "non-finite observation"; return RPBA_ERR_NUMERIC; }
+  ctx->has_winv = pb->obs_winv != nullptr;
+  if (ctx->has_winv)
+    for (int k = 0; k < K; k++) {
+      const double *W = pb->obs_winv + 3 * k;
+      if (!(W[0] > 0.0) || !(W[0] * W[2] - W[1] * W[1] > 0.0)) {
+        ctx->err = "obs_winv not positive definite";
+        return RPBA_ERR_INVALID_ARG;
+      }
+    }
+  // cameras by (sub-block, id)
+  std::vector<int> &scp = ctx->h_sub_cam_ptr, &sc = ctx->h_sub_cam;
+  scp.assign(L + 1, 0);
+  for (int i = 0; i < M; i++) scp[pb->cam_subblock[i] + 1]++;
+  for (int l = 0; l < L; l++) scp[l + 1] += scp[l];
+  sc.resize(M);
+  std::vector<int> cam_local(M), fill(scp.begin(), scp.end() - 1);
+  for (int i = 0; i < M; i++) {
+    int p = fill[pb->cam_subblock[i]]++;
+    sc[p] = i;
+    cam_local[i] = p - scp[pb->cam_subblock[i]];
+  }
+  // observations sorted by (sub-block, point), stable: two counting sorts
+  std::vector<int> by_pt(K), order(K);
+  {
+    std::vector<int> cnt(N + 1, 0);
+    for (int k = 0; k < K; k++) cnt[pb->obs_point[k] + 1]++;
+    for (int j = 0; j < N; j++) cnt[j + 1] += cnt[j];
+    for (int k = 0; k < K; k++) by_pt[cnt[pb->obs_point[k]]++] = k;
+  }
+  // duplicate (camera, point) check on the point-sorted list
+  {
+    std::vector<int> seen(M, -1);
+    for (int p = 0; p < K; p++) {
+      int k = by_pt[p];
+      int i = pb->obs_cam[k], j = pb->obs_point[k];
+      if (seen[i] == j) { ctx->err = "duplicate (camera, point) observation"; return RPBA_ERR_INVALID_ARG; }
+      seen[i] = j;
+    }
+  }
+  {
+    std::vector<int> cnt(L + 1, 0);
+    for (int k = 0; k < K; k++) cnt[pb->cam_subblock[pb->obs_cam[k]] + 1]++;
+    for (int l = 0; l < L; l++) cnt[l + 1] += cnt[l];
+    for (int p = 0; p < K; p++) {
+      int k = by_pt[p];
+      order[cnt[pb->cam_subblock[pb->obs_cam[k]]]++] = k;
+    }
+  }
+  // instances
+  std::vector<int> obs_inst(K), inst_obs_ptr(1, 0), inst_pt, inst_sub;
+  for (int p = 0; p < K; p++) {
+    int k = order[p];
+    int l = pb->cam_subblock[pb->obs_cam[k]], j = pb->obs_point[k];
+    if (inst_pt.empty() || inst_pt.back() != j || inst_sub.back() != l) {
+      if (!inst_pt.empty()) inst_obs_ptr.push_back(p);
+      inst_pt.push_back(j);
+      inst_sub.push_back(l);
+    }
+    obs_inst[p] = (int)inst_pt.size() - 1;
+  }
+  int P = (int)inst_pt.size();
+  inst_obs_ptr.push_back(K);
+  if (P == 0) inst_obs_ptr.assign(1, 0);
+  ctx->P = P;
+  ctx->h_inst_pt = inst_pt;
+  ctx->h_inst_sub = inst_sub;
+  ctx->h_obs_user = order;
+  std::vector<int> sip(L + 1, 0);
+  for (int q = 0; q < P; q++) sip[inst_sub[q] + 1]++;
+  for (int l = 0; l < L; l++) sip[l + 1] += sip[l];
+  ctx->h_sub_inst_ptr = sip;
+  // point -> instances
+  std::vector<int> pip(N + 1, 0), pin(P);
+  for (int q = 0; q < P; q++) pip[inst_pt[q] + 1]++;
+  for (int j = 0; j < N; j++) pip[j + 1] += pip[j];
+  {
+    std::vector<int> f(pip.begin(), pip.end() - 1);
+    for (int q = 0; q < P; q++) pin[f[inst_pt[q]]++] = q;
+  }
+  // camera -> observation positions
+  std::vector<int> cop(M + 1, 0), cob(K);
+  for (int p = 0; p < K; p++) cop[pb->obs_cam[order[p]] + 1]++;
+  for (int i = 0; i < M; i++) cop[i + 1] += cop[i];
+  {
+    std::vector<int> f(cop.begin(), cop.end() - 1);
+    for (int p = 0; p < K; p++) cob[f[pb->obs_cam[order[p]]]++] = p;
+  }
+  int mco = 0;
+  for (int i = 0; i < M; i++) mco = std::max(mco, cop[i + 1] - cop[i]);
+  ctx->max_cam_obs = mco;
+  // Schur pairs inside each instance: local(cam a) > local(cam b)
+  std::vector<int> pa, pb_;
+  for (int q = 0; q < P; q++)
+    for (int a = inst_obs_ptr[q]; a < inst_obs_ptr[q + 1]; a++)
+      for (int b = inst_obs_ptr[q]; b < inst_obs_ptr[q + 1]; b++) {
+        int la = cam_local[pb->obs_cam[order[a]]], lb = cam_local[pb->obs_cam[order[b]]];
+        if (la > lb) { pa.push_back(a); pb_.push_back(b); }
+      }
+  ctx->n_pairs = (long long)pa.size();
+  // RCS layout
+  std::vector<long long> soff(L);
+  std::vector<int> npad(L), yoff(L), ntiles(L);
+  long long stot = 0;
+  int yt = 0, maxT = 0;
+  for (int l = 0; l < L; l++) {
+    int n = 6 * (scp[l + 1] - scp[l]);
+    int T = (n + RPBA_TILE - 1) / RPBA_TILE;
+    npad[l] = T * RPBA_TILE;
+    ntiles[l] = T;
+    maxT = std::max(maxT, T);
+    soff[l] = stot;
+    stot += (long long)npad[l] * npad[l];
+    yoff[l] = yt;
+    yt += npad[l];
+  }
+  ctx->h_S_off = soff;
+  ctx->h_npad = npad;
+  ctx->S_total = stot;
+  ctx->max_tiles = maxT;
+  // per-observation arrays in GPU order
+  std::vector<int> ocam(K), opt(K);
+  std::vector<double> oxy(2 * (size_t)K), ow(3 * (size_t)(ctx->has_winv ? K : 0));
+  for (int p = 0; p < K; p++) {
+    int k = order[p];
+    ocam[p] = pb->obs_cam[k];
+    opt[p] = pb->obs_point[k];
+    oxy[2 * p] = pb->obs_xy[2 * k];
+    oxy[2 * p + 1] = pb->obs_xy[2 * k + 1];
+    if (ctx->has_winv)
+      for (int e = 0; e < 3; e++) ow[3 * (size_t)p + e] = pb->obs_winv[3 * (size_t)k + e];
+  }
+  std::vector<uint8_t> active(N);
+  int nact = 0;
+  {
+    std::vector<int> cnt(N, 0);
+    for (int k = 0; k < K; k++) cnt[pb->obs_point[k]]++;
+    for (int j = 0; j < N; j++) { active[j] = cnt[j] >= 2; nact += active[j]; }
+    ctx->h_pt_nobs = cnt;
+  }
+  ctx->h_pinned_d = nullptr;
+  // device uploads
+  double *pose_d = nullptr;
+  RPBA_TRY(upload(ctx, &pose_d, pb->cam_pose, 6 * (size_t)M));
+  RPBA_TRY(alloc_n(ctx, &ctx->R, 9 * (size_t)M));
+  RPBA_TRY(alloc_n(ctx, &ctx->t, 3 * (size_t)M));
+  RPBA_TRY(alloc_n(ctx, &ctx->Rt, 9 * (size_t)M));
+  RPBA_TRY(alloc_n(ctx, &ctx->tt, 3 * (size_t)M));
+  RPBA_TRY(upload(ctx, &ctx->intr, pb->cam_intr, 3 * (size_t)M));
+  RPBA_TRY(upload(ctx, &ctx->cam_sub, pb->cam_subblock, (size_t)M));
+  RPBA_TRY(upload(ctx, &ctx->cam_local, cam_local.data(), (size_t)M));
+  RPBA_TRY(upload(ctx, &ctx->sub_cam_ptr, scp.data(), (size_t)L + 1));
+  RPBA_TRY(upload(ctx, &ctx->sub_cam, sc.data(), (size_t)M));
+  RPBA_TRY(upload(ctx, &ctx->cam_obs_ptr, cop.data(), (size_t)M + 1));
+  RPBA_TRY(upload(ctx, &ctx->cam_obs, cob.data(), (size_t)K));
+  RPBA_TRY(alloc_n(ctx, &ctx->cam_sigma, (size_t)M));
+  RPBA_TRY(upload(ctx, &ctx->X, pb->points, 3 * (size_t)N));
+  RPBA_TRY(upload(ctx, &ctx->active, active.data(), (size_t)N));
+  RPBA_TRY(upload(ctx, &ctx->pt_inst_ptr, pip.data(), (size_t)N + 1));
+  RPBA_TRY(upload(ctx, &ctx->pt_inst, pin.data(), (size_t)P));
+  RPBA_TRY(upload(ctx, &ctx->inst_pt, inst_pt.data(), (size_t)P));
+  RPBA_TRY(upload(ctx, &ctx->inst_sub, inst_sub.data(), (size_t)P));
+  RPBA_TRY(upload(ctx, &ctx->inst_obs_ptr, inst_obs_ptr.data(), (size_t)P + 1));
+  RPBA_TRY(upload(ctx, &ctx->sub_inst_ptr, sip.data(), (size_t)L + 1));
+  RPBA_TRY(alloc_n(ctx, &ctx->Xl, 3 * (size_t)P));
+  RPBA_TRY(alloc_n(ctx, &ctx->Xlt, 3 * (size_t)P));
+  RPBA_TRY(alloc_n(ctx, &ctx->Wl, 6 * (size_t)P));
+  RPBA_TRY(alloc_n(ctx, &ctx->inst_cost, (size_t)P));
+  size_t rs = ctx->opt.precision == 1 ? sizeof(float) : sizeof(double);
+  RPBA_TRY(dev_alloc(ctx, &ctx->Ninv, 6 * (size_t)P * rs));
+  RPBA_TRY(dev_alloc(ctx, &ctx->gX, 3 * (size_t)P * rs));
+  RPBA_TRY(alloc_n(ctx, &ctx->isect_N, 10 * (size_t)P));
+  RPBA_TRY(alloc_n(ctx, &ctx->isect_state, (size_t)N));
+  RPBA_TRY(alloc_n(ctx, &ctx->isect_iter, (size_t)N));
+  RPBA_TRY(upload(ctx, &ctx->obs_cam, ocam.data(), (size_t)K));
+  RPBA_TRY(upload(ctx, &ctx->obs_inst, obs_inst.data(), (size_t)K));
+  RPBA_TRY(upload(ctx, &ctx->obs_user, order.data(), (size_t)K));
+  RPBA_TRY(upload(ctx, &ctx->obs_pt, opt.data(), (size_t)K));
+  RPBA_TRY(upload(ctx, &ctx->obs_xy, oxy.data(), 2 * (size_t)K));
+  if (ctx->has_winv) RPBA_TRY(upload(ctx, &ctx->obs_winv, ow.data(), 3 * (size_t)K));
+  RPBA_TRY(alloc_n(ctx, &ctx->obs_w, (size_t)K));
+  RPBA_TRY(dev_alloc(ctx, &ctx->NXC, 18 * (size_t)K * rs));
+  RPBA_TRY(dev_alloc(ctx, &ctx->Z, 18 * (size_t)K * rs));
+  RPBA_TRY(upload(ctx, &ctx->pair_a, pa.data(), pa.size()));
+  RPBA_TRY(upload(ctx, &ctx->pair_b, pb_.data(), pb_.size()));
+  RPBA_TRY(alloc_n(ctx, &ctx->S, (size_t)std::max(stot, 1LL)));
+  RPBA_TRY(alloc_n(ctx, &ctx->y, (size_t)std::max(yt, 1)));
+  RPBA_TRY(alloc_n(ctx, &ctx->dC, (size_t)std::max(yt, 1)));
+  RPBA_TRY(upload(ctx, &ctx->S_off, soff.data(), (size_t)L));
+  RPBA_TRY(upload(ctx, &ctx->npad, npad.data(), (size_t)L));
+  RPBA_TRY(upload(ctx, &ctx->ycam_off, yoff.data(), (size_t)L));
+  RPBA_TRY(upload(ctx, &ctx->sub_ntiles, ntiles.data(), (size_t)L));
+  RPBA_TRY(alloc_n(ctx, &ctx->lm_lambda, (size_t)L));
+  RPBA_TRY(alloc_n(ctx, &ctx->lm_F, (size_t)L));
+  RPBA_TRY(alloc_n(ctx, &ctx->lm_Ft, (size_t)L));
+  RPBA_TRY(alloc_n(ctx, &ctx->lm_best, (size_t)L));
+  RPBA_TRY(alloc_n(ctx, &ctx->lm_grace, (size_t)L));
+  RPBA_TRY(alloc_n(ctx, &ctx->lm_rej, (size_t)L));
+  RPBA_TRY(alloc_n(ctx, &ctx->lm_it, (size_t)L));
+  RPBA_TRY(alloc_n(ctx, &ctx->lm_run, (size_t)L));
+  RPBA_TRY(alloc_n(ctx, &ctx->lm_acc, (size_t)L));
+  RPBA_TRY(alloc_n(ctx, &ctx->lm_cholfail, (size_t)L));
+  ctx->red_blocks = 304;
+  RPBA_TRY(alloc_n(ctx, &ctx->red, (size_t)ctx->red_blocks * 6 + 16));
+  RPBA_TRY(alloc_n(ctx, &ctx->counters, 16));
+  RPBA_CUDA(cudaMallocHost((void **)&ctx->h_pinned_counter, 16 * sizeof(int)));
+  RPBA_CUDA(cudaMallocHost((void **)&ctx->h_pinned_d, 16 * sizeof(double)));
+  // state: rotations from the poses, unit weights, instance copies at X
+  if (M) RPBA_KERNEL(ctx, "k_pose_to_R", k_pose_to_R<<<nblk(M, 128), 128, 0, ctx->stream>>>(M, pose_d, ctx->R, ctx->t));
+  RPBA_TRY(launch_fill_double(ctx, ctx->obs_w, K, 1.0));
+  RPBA_TRY(launch_fill_double(ctx, ctx->Wl, 6LL * P, 0.0));
+  RPBA_TRY(launch_tp_copies(ctx, 0));
+  RPBA_TRY(sync(ctx));
+  ctx->n_active_start = nact;
+  return RPBA_OK;
+}
+
+extern "C" rpba_status rpba_create(const rpba_problem *prob, const rpba_options *opt, void *stream,
+                                   rpba_ctx **out) {
+  if (!out) return RPBA_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!prob) return RPBA_ERR_INVALID_ARG;
+  rpba_ctx *h = new (std::nothrow) rpba_ctx();
+  if (!h) return RPBA_ERR_OOM;
+  Ctx *ctx = &h->c;
+  if (opt) ctx->opt = *opt;
+  else rpba_default_options(&ctx->opt);
+  if (ctx->opt.precision != 0 && ctx->opt.precision != 1) {
+    ctx->err = "precision must be 0 or 1";
+    *out = h;
+    return RPBA_ERR_INVALID_ARG;
+  }
+  ctx->stream = (cudaStream_t)stream;
+  *out = h;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    ctx->err = std::string("no CUDA device: ") + cudaGetErrorString(e);
+    return RPBA_ERR_CUDA;
+  }
+  RPBA_CUDA(cudaGetDevice(&ctx->dev));
+  return build(ctx, prob);
+}
+
+// ---------------------------------------------------------------------------
+// state access
+// ---------------------------------------------------------------------------
+#define CTX_OR_FAIL                          \
+  if (!h) return RPBA_ERR_INVALID_ARG;       \
+  Ctx *ctx = &h->c;
+
+// temporary device buffer for host transfers (freed at return)
+struct Tmp {
+  Ctx *ctx;
+  void *p = nullptr;
+  Tmp(Ctx *c) : ctx(c) {}
+  ~Tmp() {
+    if (p) {
+      cudaStreamSynchronize(ctx->stream);
+      if (ctx->opt.dev_free) ctx->opt.dev_free(p, ctx->opt.alloc_user);
+      else cudaFree(p);
+    }
+  }
+  rpba_status alloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (ctx->opt.dev_alloc) {
+      p = ctx->opt.dev_alloc(bytes, ctx->opt.alloc_user);
+      if (!p) { ctx->err = "allocator hook returned NULL"; return RPBA_ERR_OOM; }
+      return RPBA_OK;
+    }
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) { p = nullptr; ctx->err = cudaGetErrorString(e); return RPBA_ERR_OOM; }
+    return RPBA_OK;
+  }
+};
+
+extern "C" rpba_status rpba_info(rpba_ctx *h, int32_t *L, int32_t *P) {
+  CTX_OR_FAIL;
+  if (L) *L = ctx->L;
+  if (P) *P = ctx->P;
+  return RPBA_OK;
+}
+
+extern "C" rpba_status rpba_sub_cameras(rpba_ctx *h, int32_t l, int32_t *cams, int32_t *n) {
+  CTX_OR_FAIL;
+  if (l < 0 || l >= ctx->L) { ctx->err = "sub-block index out of range"; return RPBA_ERR_STATE; }
+  int a = ctx->h_sub_cam_ptr[l], b = ctx->h_sub_cam_ptr[l + 1];
+  if (cams) for (int p = a; p < b; p++) cams[p - a] = ctx->h_sub_cam[p];
+  if (n) *n = b - a;
+  return RPBA_OK;
+}
+
+extern "C" rpba_status rpba_set_cameras(rpba_ctx *h, const double *pose) {
+  CTX_OR_FAIL;
+  if (!pose) return RPBA_ERR_INVALID_ARG;
+  Tmp d(ctx);
+  RPBA_TRY(d.alloc(6 * (size_t)ctx->M * sizeof(double)));
+  RPBA_CUDA(cudaMemcpyAsync(d.p, pose, 6 * (size_t)ctx->M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  if (ctx->M) RPBA_KERNEL(ctx, "k_pose_to_R", k_pose_to_R<<<nblk(ctx->M, 128), 128, 0, ctx->stream>>>(ctx->M, (double *)d.p, ctx->R, ctx->t));
+  return sync(ctx);
+}
+
+extern "C" rpba_status rpba_get_cameras(rpba_ctx *h, double *pose) {
+  CTX_OR_FAIL;
+  if (!pose) return RPBA_ERR_INVALID_ARG;
+  Tmp d(ctx);
+  RPBA_TRY(d.alloc(6 * (size_t)ctx->M * sizeof(double)));
+  if (ctx->M) RPBA_KERNEL(ctx, "k_R_to_pose", k_R_to_pose<<<nblk(ctx->M, 128), 128, 0, ctx->stream>>>(ctx->M, ctx->R, ctx->t, (double *)d.p));
+  RPBA_CUDA(cudaMemcpyAsync(pose, d.p, 6 * (size_t)ctx->M * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return sync(ctx);
+}
+
+extern "C" rpba_status rpba_set_points(rpba_ctx *h, const double *X, const uint8_t *active) {
+  CTX_OR_FAIL;
+  if (X) RPBA_CUDA(cudaMemcpyAsync(ctx->X, X, 3 * (size_t)ctx->N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  if (active) RPBA_CUDA(cudaMemcpyAsync(ctx->active, active, (size_t)ctx->N, cudaMemcpyHostToDevice, ctx->stream));
+  return sync(ctx);
+}
+
+extern "C" rpba_status rpba_get_points(rpba_ctx *h, double *X, uint8_t *active) {
+  CTX_OR_FAIL;
+  if (X) RPBA_CUDA(cudaMemcpyAsync(X, ctx->X, 3 * (size_t)ctx->N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  if (active) RPBA_CUDA(cudaMemcpyAsync(active, ctx->active, (size_t)ctx->N, cudaMemcpyDeviceToHost, ctx->stream));
+  return sync(ctx);
+}
+
+extern "C" rpba_status rpba_get_instances(rpba_ctx *h, int32_t *ip, int32_t *is, double *Xl, double *Wl) {
+  CTX_OR_FAIL;
+  if (ip) std::copy(ctx->h_inst_pt.begin(), ctx->h_inst_pt.end(), ip);
+  if (is) std::copy(ctx->h_inst_sub.begin(), ctx->h_inst_sub.end(), is);
+  if (Xl) RPBA_CUDA(cudaMemcpyAsync(Xl, ctx->Xl, 3 * (size_t)ctx->P * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  if (Wl) RPBA_CUDA(cudaMemcpyAsync(Wl, ctx->Wl, 6 * (size_t)ctx->P * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return sync(ctx);
+}
+
+extern "C" rpba_status rpba_set_instances(rpba_ctx *h, const double *Xl, const double *Wl) {
+  CTX_OR_FAIL;
+  if (Xl) RPBA_CUDA(cudaMemcpyAsync(ctx->Xl, Xl, 3 * (size_t)ctx->P * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  if (Wl) RPBA_CUDA(cudaMemcpyAsync(ctx->Wl, Wl, 6 * (size_t)ctx->P * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  return sync(ctx);
+}
+
+extern "C" rpba_status rpba_get_weights(rpba_ctx *h, double *w) {
+  CTX_OR_FAIL;
+  if (!w) return RPBA_ERR_INVALID_ARG;
+  std::vector<double> g(ctx->K);
+  if (ctx->K) RPBA_CUDA(cudaMemcpyAsync(g.data(), ctx->obs_w, ctx->K * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  RPBA_TRY(sync(ctx));
+  for (int p = 0; p < ctx->K; p++) w[ctx->h_obs_user[p]] = g[p];
+  return RPBA_OK;
+}
+
+extern "C" rpba_status rpba_set_weights(rpba_ctx *h, const double *w) {
+  CTX_OR_FAIL;
+  if (!w) return RPBA_ERR_INVALID_ARG;
+  std::vector<double> g(ctx->K);
+  for (int p = 0; p < ctx->K; p++) g[p] = w[ctx->h_obs_user[p]];
+  if (ctx->K) RPBA_CUDA(cudaMemcpyAsync(ctx->obs_w, g.data(), ctx->K * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  return sync(ctx);
+}
+
+extern "C" rpba_status rpba_residuals(rpba_ctx *h, double *v) {
+  CTX_OR_FAIL;
+  if (!v) return RPBA_ERR_INVALID_ARG;
+  Tmp d(ctx);
+  RPBA_TRY(d.alloc(2 * (size_t)ctx->K * sizeof(double)));
+  RPBA_TRY(launch_residuals(ctx, (double *)d.p));
+  RPBA_CUDA(cudaMemcpyAsync(v, d.p, 2 * (size_t)ctx->K * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return sync(ctx);
+}
+
+extern "C" rpba_status rpba_jacobians(rpba_ctx *h, double *Jc, double *Jx) {
+  CTX_OR_FAIL;
+  if (!Jc || !Jx) return RPBA_ERR_INVALID_ARG;
+  Tmp a(ctx), b(ctx);
+  RPBA_TRY(a.alloc(12 * (size_t)ctx->K * sizeof(double)));
+  RPBA_TRY(b.alloc(6 * (size_t)ctx->K * sizeof(double)));
+  RPBA_TRY(launch_jacobians(ctx, (double *)a.p, (double *)b.p));
+  RPBA_CUDA(cudaMemcpyAsync(Jc, a.p, 12 * (size_t)ctx->K * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  RPBA_CUDA(cudaMemcpyAsync(Jx, b.p, 6 * (size_t)ctx->K * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return sync(ctx);
+}
+
+extern "C" rpba_status rpba_sigma0(rpba_ctx *h, double *s0, double *rms) {
+  CTX_OR_FAIL;
+  return launch_sigma0(ctx, s0, rms);
+}
+
+extern "C" rpba_status rpba_camera_scale(rpba_ctx *h, double *sigma) {
+  CTX_OR_FAIL;
+  RPBA_TRY(launch_camera_scale(ctx));
+  if (sigma && ctx->M)
+    RPBA_CUDA(cudaMemcpyAsync(sigma, ctx->cam_sigma, ctx->M * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return sync(ctx);
+}
+
+extern "C" rpba_status rpba_robust_weights(rpba_ctx *h, int32_t *n_down) {
+  CTX_OR_FAIL;
+  int nd = 0;
+  RPBA_TRY(launch_robust_weights(ctx, &nd));
+  if (n_down) *n_down = nd;
+  return RPBA_OK;
+}
+
+extern "C" rpba_status rpba_intersect_points(rpba_ctx *h, int32_t tp_only, int32_t *n_dropped) {
+  CTX_OR_FAIL;
+  int nd = 0;
+  RPBA_TRY(launch_intersect(ctx, tp_only ? 1 : 0, &nd));
+  if (n_dropped) *n_dropped = nd;
+  return RPBA_OK;
+}
+
+extern "C" rpba_status rpba_intersect(rpba_ctx *h) {
+  CTX_OR_FAIL;
+  RPBA_TRY(launch_intersect(ctx, 0, nullptr));
+  RPBA_TRY(launch_tp_copies(ctx, 0));
+  ctx->intersected = true;
+  return sync(ctx);
+}
+
+extern "C" rpba_status rpba_covariance(rpba_ctx *h, const int32_t *ids, int32_t n, double *out9) {
+  CTX_OR_FAIL;
+  if (n < 0 || (n && (!ids || !out9))) return RPBA_ERR_INVALID_ARG;
+  if (n == 0) return RPBA_OK;
+  Tmp di(ctx), dout(ctx);
+  RPBA_TRY(di.alloc((size_t)n * sizeof(int)));
+  RPBA_TRY(dout.alloc(9 * (size_t)n * sizeof(double)));
+  RPBA_CUDA(cudaMemcpyAsync(di.p, ids, n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  RPBA_KERNEL(ctx, "k_covariance", k_covariance<<<nblk(n, 128), 128, 0, ctx->stream>>>(n, (const int *)di.p, ctx->R, ctx->t, ctx->intr, ctx->X,
+                                                     ctx->active, ctx->pt_inst_ptr, ctx->pt_inst, ctx->inst_obs_ptr,
+                                                     ctx->obs_cam, ctx->obs_winv, ctx->has_winv, ctx->obs_w, ctx->N,
+                                                     (double *)dout.p));
+  RPBA_CUDA(cudaMemcpyAsync(out9, dout.p, 9 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return sync(ctx);
+}
+
+extern "C" rpba_status rpba_sub_costs(rpba_ctx *h, double *F) {
+  CTX_OR_FAIL;
+  RPBA_TRY(launch_sub_costs(ctx, 0, ctx->lm_F));
+  if (F && ctx->L) RPBA_CUDA(cudaMemcpyAsync(F, ctx->lm_F, ctx->L * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return sync(ctx);
+}
+
+extern "C" rpba_status rpba_rcs(rpba_ctx *h, int32_t l, double lambda, double *S, double *y) {
+  CTX_OR_FAIL;
+  if (l < 0 || l >= ctx->L) { ctx->err = "sub-block index out of range"; return RPBA_ERR_STATE; }
+  RPBA_TRY(launch_fill_double(ctx, ctx->lm_lambda, ctx->L, lambda));
+  RPBA_TRY(launch_fill_int(ctx, ctx->lm_run, ctx->L, 0));
+  RPBA_TRY(launch_fill_int(ctx, ctx->lm_run + l, 1, 1));
+  RPBA_TRY(launch_build_rcs(ctx, ctx->lm_lambda, ctx->lm_run));
+  int n = 6 * (ctx->h_sub_cam_ptr[l + 1] - ctx->h_sub_cam_ptr[l]);
+  int np = ctx->h_npad[l];
+  std::vector<double> full((size_t)np * np), yf(np);
+  if (np) {
+    RPBA_CUDA(cudaMemcpyAsync(full.data(), ctx->S + ctx->h_S_off[l], (size_t)np * np * sizeof(double),
+                              cudaMemcpyDeviceToHost, ctx->stream));
+    int yoff = 0;
+    for (int a = 0; a < l; a++) yoff += ctx->h_npad[a];
+    RPBA_CUDA(cudaMemcpyAsync(yf.data(), ctx->y + yoff, np * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  RPBA_TRY(sync(ctx));
+  for (int r = 0; r < n; r++) {
+    if (S) for (int c = 0; c < n; c++) S[(size_t)r * n + c] = full[(size_t)r * np + c];
+    if (y) y[r] = yf[r];
+  }
+  return RPBA_OK;
+}
+
+// one lock-step LM iteration of the running sub-blocks
+static rpba_status lm_iteration(Ctx *ctx) {
+  RPBA_TRY(launch_build_rcs(ctx, ctx->lm_lambda, ctx->lm_run));
+  RPBA_TRY(launch_solve_rcs(ctx, ctx->lm_run, ctx->lm_cholfail));
+  RPBA_TRY(launch_backsub_trial(ctx, ctx->lm_run));
+  return RPBA_OK;
+}
+
+extern "C" rpba_status rpba_lm_step(rpba_ctx *h, double lambda, int32_t *accepted, double *Fb, double *Ft,
+                                    double *dc, double *dx) {
+  CTX_OR_FAIL;
+  int L = ctx->L;
+  RPBA_TRY(launch_lm_init(ctx));
+  RPBA_TRY(launch_fill_double(ctx, ctx->lm_lambda, L, lambda));
+  RPBA_TRY(lm_iteration(ctx));
+  std::vector<double> F(L), Fn(L);
+  std::vector<int> fail(L), run(L);
+  RPBA_CUDA(cudaMemcpyAsync(F.data(), ctx->lm_F, L * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  RPBA_CUDA(cudaMemcpyAsync(Fn.data(), ctx->lm_Ft, L * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  RPBA_CUDA(cudaMemcpyAsync(fail.data(), ctx->lm_cholfail, L * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RPBA_CUDA(cudaMemcpyAsync(run.data(), ctx->lm_run, L * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  std::vector<double> Xl(3 * (size_t)ctx->P), Xlt(3 * (size_t)ctx->P);
+  if (dx && ctx->P) {
+    RPBA_CUDA(cudaMemcpyAsync(Xl.data(), ctx->Xl, Xl.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    RPBA_CUDA(cudaMemcpyAsync(Xlt.data(), ctx->Xlt, Xlt.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  int ytot = 0;
+  for (int l = 0; l < L; l++) ytot += ctx->h_npad[l];
+  std::vector<double> dCh(ytot);
+  if (dc && ytot)
+    RPBA_CUDA(cudaMemcpyAsync(dCh.data(), ctx->dC, ytot * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  RPBA_TRY(sync(ctx));
+  std::vector<int> acc(L);
+  for (int l = 0; l < L; l++) {
+    if (!run[l]) acc[l] = 0;
+    else if (fail[l]) acc[l] = -1;
+    else acc[l] = (isfinite(Fn[l]) && Fn[l] < F[l]) ? 1 : 0;
+    if (accepted) accepted[l] = acc[l];
+    if (Fb) Fb[l] = F[l];
+    if (Ft) Ft[l] = (run[l] && !fail[l]) ? Fn[l] : F[l];
+  }
+  if (dc) {
+    int o = 0, yo = 0;
+    for (int l = 0; l < L; l++) {
+      int n = 6 * (ctx->h_sub_cam_ptr[l + 1] - ctx->h_sub_cam_ptr[l]);
+      for (int r = 0; r < n; r++) dc[o + r] = dCh[yo + r];
+      o += n;
+      yo += ctx->h_npad[l];
+    }
+  }
+  if (dx)
+    for (size_t e = 0; e < Xl.size(); e++) dx[e] = Xlt[e] - Xl[e];
+  std::vector<int> accp(L);
+  for (int l = 0; l < L; l++) accp[l] = acc[l] == 1;
+  RPBA_CUDA(cudaMemcpyAsync(ctx->lm_acc, accp.data(), L * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  RPBA_TRY(launch_lm_apply(ctx, ctx->lm_acc));
+  return sync(ctx);
+}
+
+// ---------------------------------------------------------------------------
+// the iteration (Sec. 5)
+// ---------------------------------------------------------------------------
+// bact of all sub-blocks in lock step; returns LM iterations summed over
+// sub-blocks and the lock-step count
+static rpba_status run_bact(Ctx *ctx, int *inner_total, int *launches) {
+  RPBA_TRY(launch_lm_init(ctx));
+  int n = 0;
+  for (;;) {
+    RPBA_TRY(lm_iteration(ctx));
+    RPBA_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(int), ctx->stream));
+    RPBA_TRY(launch_lm_decide(ctx));
+    RPBA_TRY(launch_lm_apply(ctx, ctx->lm_acc));
+    RPBA_CUDA(cudaMemcpyAsync(ctx->h_pinned_counter, ctx->counters, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    RPBA_TRY(sync(ctx));
+    n++;
+    if (ctx->h_pinned_counter[0] == 0) break;
+    if (n > 100000) { ctx->err = "LM loop did not terminate"; return RPBA_ERR_NOT_CONVERGED; }
+  }
+  std::vector<int> it(ctx->L);
+  if (ctx->L) RPBA_CUDA(cudaMemcpyAsync(it.data(), ctx->lm_it, ctx->L * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RPBA_TRY(sync(ctx));
+  *inner_total += std::accumulate(it.begin(), it.end(), 0);
+  *launches += n;
+  return RPBA_OK;
+}
+
+extern "C" rpba_status rpba_iterate(rpba_ctx *h, int32_t max_outer, rpba_report *rep) {
+  CTX_OR_FAIL;
+  const rpba_options &o = ctx->opt;
+  if (max_outer <= 0) max_outer = o.max_outer;
+  rpba_report r;
+  memset(&r, 0, sizeof(r));
+  r.robust_started_at = -1;
+  if (!ctx->intersected) RPBA_TRY(rpba_intersect(h));
+  double s = 0.0;
+  RPBA_TRY(launch_sigma0(ctx, &s, nullptr));
+  r.sigma0_initial = s;
+  double best = s;
+  int grace = o.grace;
+  bool robust_on = false;
+  for (int outer = 0; outer < max_outer; outer++) {
+    RPBA_TRY(run_bact(ctx, &r.inner_total, &r.lm_launches));
+    RPBA_TRY(launch_exchange(ctx));
+    if (o.robust && o.robust_from_start && !robust_on) {
+      robust_on = true;
+      r.robust_started_at = r.outer;
+    }
+    if (robust_on) RPBA_TRY(launch_robust_weights(ctx, nullptr));
+    RPBA_TRY(launch_intersect(ctx, 1, nullptr));
+    RPBA_TRY(launch_tp_copies(ctx, 1));
+    RPBA_TRY(launch_sigma0(ctx, &s, nullptr));
+    if (r.outer < 128) r.sigma0_hist[r.outer] = s;
+    r.outer++;
+    double ratio = best / (s > 1e-300 ? s : 1e-300);
+    if (s < best) best = s;
+    if (ratio < o.stop_ratio) {
+      if (grace > 0) { grace--; continue; }
+      if (o.robust && !robust_on) {
+        robust_on = true;
+        r.robust_started_at = r.outer;
+        RPBA_TRY(launch_robust_weights(ctx, nullptr));
+        RPBA_TRY(launch_intersect(ctx, 1, nullptr));
+        RPBA_TRY(launch_tp_copies(ctx, 1));
+        RPBA_TRY(launch_sigma0(ctx, &best, nullptr));
+        grace = o.grace;
+        continue;
+      }
+      break;
+    }
+  }
+  if (robust_on) RPBA_TRY(launch_eliminate(ctx));
+  RPBA_TRY(launch_sigma0(ctx, &r.sigma0, &r.rms));
+  // counts
+  std::vector<uint8_t> a(ctx->N);
+  if (ctx->N) RPBA_CUDA(cudaMemcpyAsync(a.data(), ctx->active, ctx->N, cudaMemcpyDeviceToHost, ctx->stream));
+  RPBA_TRY(sync(ctx));
+  int na = 0;
+  long long ka = 0;
+  for (int j = 0; j < ctx->N; j++)
+    if (a[j]) { na++; ka += ctx->h_pt_nobs[j]; }
+  r.active_points = na;
+  r.deleted_points = ctx->n_active_start - na;
+  r.active_obs = (int)ka;
+  if (rep) *rep = r;
+  return RPBA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// profiling
+// ---------------------------------------------------------------------------
+extern "C" rpba_status rpba_profile_enable(rpba_ctx *h, int32_t enable) {
+  CTX_OR_FAIL;
+  RPBA_TRY(sync(ctx));
+  for (auto &r : ctx->prof_recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  ctx->prof_recs.clear();
+  ctx->prof_ms.clear();
+  ctx->launch_by_name.clear();
+  ctx->launches = 0;
+  ctx->prof_enabled = enable != 0;
+  return RPBA_OK;
+}
+
+extern "C" rpba_status rpba_profile_read(rpba_ctx *h, int32_t max_kernels, char *names, double *ms,
+                                         int64_t *launches, int32_t *n_kernels, int64_t *total_launches) {
+  CTX_OR_FAIL;
+  RPBA_TRY(sync(ctx));
+  for (auto &r : ctx->prof_recs) {
+    float t = 0.f;
+    RPBA_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+    ctx->prof_ms[r.name] += t;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  ctx->prof_recs.clear();
+  int n = 0;
+  for (auto &kv : ctx->launch_by_name) {
+    if (n < max_kernels) {
+      if (names) {
+        strncpy(names + 48 * n, kv.first.c_str(), 47);
+        names[48 * n + 47] = 0;
+      }
+      if (ms) ms[n] = ctx->prof_ms.count(kv.first) ? ctx->prof_ms[kv.first] : 0.0;
+      if (launches) launches[n] = kv.second;
+    }
+    n++;
+  }
+  if (n_kernels) *n_kernels = n;
+  if (total_launches) *total_launches = ctx->launches;
+  return RPBA_OK;
+}

@@ -1,0 +1,286 @@
+// rpba_internal.cuh -- device data layout and shared device helpers of the
+// GB300 RPBA library. Everything here is GPU-side code of the library; the
+// CPU oracle used by the tests is separate and shares nothing with it.
+//
+// Data layout in HBM (all arrays device-resident for the life of a context):
+//   cameras (M):   R (9 f64), t (3 f64), intrinsics (3 f64), trial R/t,
+//                  sub-block id, position inside the sub-block (RCS row / 6)
+//   points (N):    X (3 f64), active flag (u8), CSR point -> instances
+//   instances (P): sorted by (sub-block l, point j); X^l (3 f64), trial X^l,
+//                  W^l (sym3 f64), damped inverse point block Ninv (sym3),
+//                  point gradient gX (3), TP flag = point has >= 2 instances
+//   observations (K): sorted by instance (so every instance and every
+//                  sub-block is a contiguous segment), structure of arrays:
+//                  cam (i32), inst (i32), xy (2 f64), C^-1 (3 f64), robust
+//                  weight w (f64), user index (i32); per-LM-step N_XC (3x6)
+//                  and Z = Ninv N_XC (3x6) in the compute precision
+//   camera order:  CSR camera -> observation positions (gather list)
+//   Schur pairs:   (a, b) observation positions of one instance whose cameras
+//                  differ, local(cam a) > local(cam b): lower-triangle blocks
+//   RCS:           per sub-block a dense n_pad x n_pad f64 matrix (row-major,
+//                  n_pad = 64 * ceil(6 M_l / 64), padding = identity), rhs
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/rpba.h"
+
+#define RPBA_TILE 64
+
+namespace rpba {
+
+// ---------------------------------------------------------------------------
+// small device math (sym3 = a00 a01 a02 a11 a12 a22)
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int s3idx(int r, int c) {
+  return (r == c) ? (r == 0 ? 0 : (r == 1 ? 3 : 5)) : (r + c == 1 ? 1 : (r + c == 2 ? 2 : 4));
+}
+
+template <typename T>
+__device__ inline T sym3_inv(const T a[6], T inv[6]) {
+  T c00 = a[3] * a[5] - a[4] * a[4];
+  T c01 = a[2] * a[4] - a[1] * a[5];
+  T c02 = a[1] * a[4] - a[2] * a[3];
+  T c11 = a[0] * a[5] - a[2] * a[2];
+  T c12 = a[1] * a[2] - a[0] * a[4];
+  T c22 = a[0] * a[3] - a[1] * a[1];
+  T det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+  T id = T(1) / det;
+  inv[0] = c00 * id; inv[1] = c01 * id; inv[2] = c02 * id;
+  inv[3] = c11 * id; inv[4] = c12 * id; inv[5] = c22 * id;
+  return det;
+}
+
+template <typename T>
+__device__ inline T sym3_frob(const T a[6]) {
+  return sqrt(a[0] * a[0] + a[3] * a[3] + a[5] * a[5] + T(2) * (a[1] * a[1] + a[2] * a[2] + a[4] * a[4]));
+}
+
+// R = exp([w]x), Rodrigues formula with a series for small angles
+__device__ inline void rodrigues(const double w[3], double R[9]) {
+  double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  double a, b;
+  if (th2 < 1e-8) {
+    a = 1.0 - th2 * (1.0 / 6.0) + th2 * th2 * (1.0 / 120.0);
+    b = 0.5 - th2 * (1.0 / 24.0) + th2 * th2 * (1.0 / 720.0);
+  } else {
+    double th = sqrt(th2);
+    double s, c;
+    sincos(th, &s, &c);
+    a = s / th;
+    b = (1.0 - c) / th2;
+  }
+  // R = I + a K + b K^2, K = [w]x, K^2 = w w^T - th2 I
+  R[0] = 1.0 + b * (w[0] * w[0] - th2);
+  R[4] = 1.0 + b * (w[1] * w[1] - th2);
+  R[8] = 1.0 + b * (w[2] * w[2] - th2);
+  R[1] = -a * w[2] + b * w[0] * w[1];
+  R[3] = a * w[2] + b * w[0] * w[1];
+  R[2] = a * w[1] + b * w[0] * w[2];
+  R[6] = -a * w[1] + b * w[0] * w[2];
+  R[5] = -a * w[0] + b * w[1] * w[2];
+  R[7] = a * w[0] + b * w[1] * w[2];
+}
+
+// Projection g_k (Sec. 2) of a camera-frame point Xc and its Jacobians.
+// RX = R X (camera frame before the translation) enters the rotation part:
+// d Xc / d dw = -[R X]x for R' = exp([dw]x) R; d Xc / dt = I; d Xc / dX = R.
+template <typename T>
+struct ProjJac {
+  T u, v;     // projection
+  T Jc[12];   // 2x6
+  T Jx[6];    // 2x3
+};
+
+template <typename T>
+__device__ inline void project_jac(const T R[9], const T Xc[3], const T RX[3], T f, T cx, T cy,
+                                   ProjJac<T> &o) {
+  T iz = T(1) / Xc[2];
+  T fx = f * iz;
+  T px = Xc[0] * iz, py = Xc[1] * iz;
+  o.u = fx * Xc[0] + cx;
+  o.v = fx * Xc[1] + cy;
+  // P = d(u,v)/dXc = fx [[1, 0, -px], [0, 1, -py]]
+  // Jx = P R
+  for (int c = 0; c < 3; c++) {
+    o.Jx[c] = fx * (R[c] - px * R[6 + c]);
+    o.Jx[3 + c] = fx * (R[3 + c] - py * R[6 + c]);
+  }
+  // rotation part: P * (-[RX]x); -[a]x = [[0, a2, -a1], [-a2, 0, a0], [a1, -a0, 0]]
+  T a0 = RX[0], a1 = RX[1], a2 = RX[2];
+  o.Jc[0] = fx * (0 - px * a1);
+  o.Jc[1] = fx * (a2 + px * a0);
+  o.Jc[2] = fx * (-a1);
+  o.Jc[6] = fx * (-a2 - py * a1);
+  o.Jc[7] = fx * (py * a0);
+  o.Jc[8] = fx * (a0);
+  // translation part: P
+  o.Jc[3] = fx; o.Jc[4] = 0; o.Jc[5] = -fx * px;
+  o.Jc[9] = 0; o.Jc[10] = fx; o.Jc[11] = -fx * py;
+}
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Ctx {
+  rpba_options opt;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int dev = 0;
+
+  int M = 0, N = 0, K = 0, L = 0, P = 0;
+  long long n_pairs = 0;
+  bool has_winv = false;
+  bool intersected = false;
+  int max_cam_obs = 0;  // largest observation count of one camera
+  int max_tiles = 0;    // largest RCS tile count of a sub-block
+
+  // host copies of the topology
+  std::vector<int> h_sub_cam_ptr;   // L+1 (cameras sorted by (sub, id))
+  std::vector<int> h_sub_cam;       // M
+  std::vector<int> h_sub_inst_ptr;  // L+1
+  std::vector<int> h_inst_pt, h_inst_sub;
+  std::vector<int> h_obs_user;      // K: GPU position -> user index
+  std::vector<int> h_pt_nobs;       // N: observations per point
+  int n_active_start = 0;
+  std::vector<long long> h_S_off;   // L: offset (doubles) of the RCS of l
+  std::vector<int> h_npad;          // L: padded RCS size
+  long long S_total = 0;
+
+  // every device allocation, freed at destroy
+  std::vector<void *> allocs;
+
+  // cameras
+  double *R = nullptr, *t = nullptr, *intr = nullptr, *Rt = nullptr, *tt = nullptr;
+  int *cam_sub = nullptr, *cam_local = nullptr, *sub_cam_ptr = nullptr, *sub_cam = nullptr;
+  int *cam_obs_ptr = nullptr, *cam_obs = nullptr;
+  double *cam_sigma = nullptr;
+  // points
+  double *X = nullptr;
+  uint8_t *active = nullptr;
+  int *pt_inst_ptr = nullptr, *pt_inst = nullptr;
+  // instances
+  int *inst_pt = nullptr, *inst_sub = nullptr, *inst_obs_ptr = nullptr, *sub_inst_ptr = nullptr;
+  double *Xl = nullptr, *Xlt = nullptr, *Wl = nullptr, *inst_cost = nullptr;
+  void *Ninv = nullptr, *gX = nullptr;  // compute precision
+  // intersection scratch
+  double *isect_N = nullptr;  // P x 9 (sym3 + gradient)
+  int *isect_state = nullptr; // N: 0 idle, 1 running, 2 converged, 3 failed
+  int *isect_iter = nullptr;
+  // observations
+  int *obs_cam = nullptr, *obs_inst = nullptr, *obs_user = nullptr, *obs_pt = nullptr;
+  double *obs_xy = nullptr, *obs_winv = nullptr, *obs_w = nullptr;
+  void *NXC = nullptr, *Z = nullptr;  // compute precision, K x 18 each
+  // Schur pairs
+  int *pair_a = nullptr, *pair_b = nullptr;
+  // RCS
+  double *S = nullptr, *y = nullptr, *dC = nullptr;  // y, dC: sum of n_pad over l
+  long long *S_off = nullptr;
+  int *npad = nullptr, *ycam_off = nullptr, *sub_ntiles = nullptr;
+  // LM control per sub-block
+  double *lm_lambda = nullptr, *lm_F = nullptr, *lm_Ft = nullptr, *lm_best = nullptr;
+  int *lm_grace = nullptr, *lm_rej = nullptr, *lm_it = nullptr, *lm_run = nullptr;
+  int *lm_acc = nullptr, *lm_cholfail = nullptr;
+  // reductions
+  double *red = nullptr;   // scratch for block partials
+  int red_blocks = 0;
+  int *counters = nullptr; // small device counters
+  // profiling: kernel launch counts (always) and event-timed phases (when enabled)
+  long long launches = 0;
+  std::map<std::string, long long> launch_by_name;
+  bool prof_enabled = false;
+  struct ProfRec {
+    const char *name;
+    cudaEvent_t a, b;
+  };
+  std::vector<ProfRec> prof_recs;
+  std::map<std::string, double> prof_ms;
+  int *h_pinned_counter = nullptr;
+  double *h_pinned_d = nullptr;
+};
+
+// error helpers
+#define RPBA_CUDA(call)                                                              \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                 \
+      return RPBA_ERR_CUDA;                                                          \
+    }                                                                                \
+  } while (0)
+
+#define RPBA_TRY(call)                \
+  do {                                \
+    rpba_status s_ = (call);          \
+    if (s_ != RPBA_OK) return s_;     \
+  } while (0)
+
+rpba_status check_launch(Ctx *ctx, const char *what);
+
+// times the kernel launched in its scope with CUDA events on the context stream
+struct PhaseTimer {
+  Ctx *ctx;
+  const char *name;
+  cudaEvent_t a = nullptr, b = nullptr;
+  PhaseTimer(Ctx *c, const char *n) : ctx(c), name(n) {
+    if (ctx->prof_enabled) {
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, ctx->stream);
+    }
+  }
+  ~PhaseTimer() {
+    if (a) {
+      cudaEventRecord(b, ctx->stream);
+      ctx->prof_recs.push_back({name, a, b});
+    }
+  }
+};
+
+// after every kernel launch: count it and check the launch status
+inline rpba_status post_launch(Ctx *ctx, const char *name) {
+  ctx->launches++;
+  ctx->launch_by_name[name]++;
+  return check_launch(ctx, name);
+}
+
+#define RPBA_KERNEL(ctx, name, ...)      \
+  do {                                   \
+    {                                    \
+      PhaseTimer pt_(ctx, name);         \
+      __VA_ARGS__;                       \
+    }                                    \
+    RPBA_TRY(post_launch(ctx, name));    \
+  } while (0)
+
+// kernels (host launchers), see kernels_*.cu
+rpba_status launch_residuals(Ctx *ctx, double *v_dev /* K x 2, GPU order */);
+rpba_status launch_jacobians(Ctx *ctx, double *Jc_dev, double *Jx_dev);
+rpba_status launch_sigma0(Ctx *ctx, double *sigma0, double *rms);
+rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped);
+rpba_status launch_exchange(Ctx *ctx);
+rpba_status launch_tp_copies(Ctx *ctx, int tp_only);
+rpba_status launch_camera_scale(Ctx *ctx);
+rpba_status launch_robust_weights(Ctx *ctx, int *n_down);
+rpba_status launch_eliminate(Ctx *ctx);
+rpba_status launch_sub_costs(Ctx *ctx, int trial, double *F_dev);
+rpba_status launch_build_rcs(Ctx *ctx, const double *lambda_dev, const int *run_dev);
+rpba_status launch_solve_rcs(Ctx *ctx, const int *run_dev, int *fail_dev);
+rpba_status launch_backsub_trial(Ctx *ctx, const int *run_dev);
+rpba_status launch_lm_decide(Ctx *ctx);
+rpba_status launch_lm_apply(Ctx *ctx, const int *acc_dev);
+rpba_status launch_lm_init(Ctx *ctx);
+rpba_status launch_fill_int(Ctx *ctx, int *p, int n, int v);
+rpba_status launch_fill_double(Ctx *ctx, double *p, long long n, double v);
+
+}  // namespace rpba

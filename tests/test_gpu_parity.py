@@ -1,0 +1,231 @@
+"""GPU path (through the C ABI) against the FP64 CPU oracle.
+
+Every comparison starts both sides from the same state (cameras, points,
+sub-block copies X^l, weights W^l, robust weights), so that LM trajectories
+never enter kernel parity. Tolerances: FP64 form ("plain") to rounding level;
+FP32 form Jacobian relative error <= 1e-5, per-point covariance relative
+Frobenius error <= 1e-4, final RMS within 1e-3 px of the oracle.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1910_08138_gb300 import rpba, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def sync_state(o, g):
+    g.set_cameras(o.cameras())
+    X, a = o.points()
+    g.set_points(X, a)
+    Xl, Wl = o.instance_state()
+    g.set_instance_state(Xl, Wl)
+    g.set_weights(o.weights())
+
+
+def rel_frob(a, b, axis):
+    return np.linalg.norm(a - b, axis=axis) / np.maximum(np.linalg.norm(b, axis=axis), 1e-300)
+
+
+def prepared(prob, precision, seed=0, weights=False, **opts):
+    if weights:
+        rng = np.random.default_rng(seed)
+        K = prob["obs_cam"].size
+        a, c = rng.uniform(0.5, 2, K), rng.uniform(0.5, 2, K)
+        prob = dict(prob)
+        prob["obs_winv"] = np.stack([a, rng.uniform(-0.4, 0.4, K) * np.sqrt(a * c), c], 1)
+    o = oracle.Oracle(prob)
+    g = rpba.Rpba(prob, precision=precision, **opts)
+    return prob, o, g
+
+
+PROBS = {
+    "tiny2": lambda: synth.tiny(seed=1, runs=[3, 3]),
+    "tiny3w": lambda: synth.tiny(seed=2, nx=4, ny=3, n_points=80, runs=[5, 4, 3], oblique_deg=30, nadir_every=3),
+    "cfg1": lambda: synth.config(1),
+}
+
+
+def test_topology_matches_oracle():
+    prob, o, g = prepared(PROBS["tiny3w"](), 0)
+    ip_o, is_o = o.instances()
+    ip_g, is_g = g.instances()
+    np.testing.assert_array_equal(ip_o, ip_g)
+    np.testing.assert_array_equal(is_o, is_g)
+    for l in range(o.L):
+        np.testing.assert_array_equal(o.sub_cameras(l), g.sub_cameras(l))
+
+
+@pytest.mark.parametrize("name", list(PROBS))
+@pytest.mark.parametrize("precision", [0, 1])
+def test_residuals_and_jacobians(name, precision):
+    prob, o, g = prepared(PROBS[name](), precision, weights=(name == "tiny3w"))
+    sync_state(o, g)
+    np.testing.assert_allclose(g.residuals(), o.residuals(), rtol=0, atol=1e-9)
+    Jc_o, Jx_o = o.jacobians()
+    Jc_g, Jx_g = g.jacobians()
+    tol = 1e-12 if precision == 0 else 1e-5
+    assert rel_frob(Jc_g, Jc_o, (1, 2)).max() <= tol
+    assert rel_frob(Jx_g, Jx_o, (1, 2)).max() <= tol
+
+
+@pytest.mark.parametrize("name", list(PROBS))
+@pytest.mark.parametrize("precision", [0, 1])
+def test_intersection_covariance_and_refined_weights(name, precision):
+    prob, o, g = prepared(PROBS[name](), precision, weights=(name == "tiny3w"))
+    sync_state(o, g)
+    o.intersect()
+    g.intersect_points(False)
+    Xo, ao = o.points()
+    Xg, ag = g.points()
+    np.testing.assert_array_equal(ao, ag)
+    act = ao == 1
+    tolX = 1e-9 if precision == 0 else 2e-5
+    assert np.abs(Xg[act] - Xo[act]).max() <= tolX
+    # covariance at the same (oracle) state, per point relative Frobenius error
+    sync_state(o, g)
+    ids = np.nonzero(act)[0]
+    Co, Cg = o.covariance(ids), g.covariance(ids)
+    assert rel_frob(Cg, Co, (1, 2)).max() <= (1e-10 if precision == 0 else 1e-4)
+    # refined weights W^l (intersection output of each side from the same start)
+    _, Wo = o.instance_state()
+    prob2, o2, g2 = prepared(PROBS[name](), precision, weights=(name == "tiny3w"))
+    sync_state(o2, g2)
+    o2.intersect(); g2.intersect_points(False)
+    _, W_o = o2.instance_state()
+    _, W_g = g2.instance_state()
+    ip, _ = o2.instances()
+    keep = (o2.points()[1][ip] == 1) & (np.abs(W_o).max(1) > 0)
+    full = lambda s: np.stack([s[:, [0, 1, 2]], s[:, [1, 3, 4]], s[:, [2, 4, 5]]], 1)
+    err = rel_frob(full(W_g[keep]), full(W_o[keep]), (1, 2))
+    assert err.max() <= (1e-8 if precision == 0 else 2e-3)
+    assert np.median(err) <= (1e-10 if precision == 0 else 1e-4)
+    assert np.all(W_g[~keep] == 0)
+
+
+def _state_after_intersection(name, precision, weights=False):
+    prob, o, g = prepared(PROBS[name](), precision, weights=weights)
+    o.intersect()
+    rng = np.random.default_rng(5)
+    Xl, Wl = o.instance_state()
+    o.set_instance_state(Xl + rng.normal(0, 0.02, Xl.shape), Wl)
+    w = np.where(rng.random(o.K) < 0.05, 1e-4, 1.0)
+    o.set_weights(w)
+    sync_state(o, g)
+    return prob, o, g
+
+
+@pytest.mark.parametrize("name", list(PROBS))
+@pytest.mark.parametrize("precision", [0, 1])
+def test_reduced_camera_system(name, precision):
+    prob, o, g = _state_after_intersection(name, precision, weights=(name == "tiny3w"))
+    Fo = np.array([o.sub_cost(l) for l in range(o.L)])
+    np.testing.assert_allclose(g.sub_costs(), Fo, rtol=1e-10 if precision == 0 else 1e-5)
+    for l in range(o.L):
+        for lam in (1e-4, 1e-2):
+            So, yo = o.rcs(l, lam)
+            Sg, yg = g.rcs(l, lam)
+            low = np.tril(np.ones_like(So, dtype=bool))
+            scale = np.abs(So).max()
+            tol = 1e-10 if precision == 0 else 2e-5
+            assert np.abs(Sg[low] - So[low]).max() <= tol * scale
+            assert np.abs(yg - yo).max() <= tol * 10 * np.abs(yo).max()
+
+
+@pytest.mark.parametrize("name", list(PROBS))
+@pytest.mark.parametrize("precision", [0, 1])
+def test_lm_step(name, precision):
+    prob, o, g = _state_after_intersection(name, precision, weights=(name == "tiny3w"))
+    acc, Fb, Ft, dc, dx = g.lm_step(1e-4)
+    off = 0
+    _, isub = o.instances()
+    for l in range(o.L):
+        r, fb, ft, dco, dxo = o.lm_step(l, 1e-4)
+        n = dco.size
+        np.testing.assert_allclose(Fb[l], fb, rtol=1e-10 if precision == 0 else 1e-5)
+        tol = 1e-7 if precision == 0 else 5e-3
+        sc = max(np.abs(dco).max(), 1e-12)
+        assert np.abs(dc[off:off + n] - dco).max() <= tol * sc
+        sx = max(np.abs(dxo).max(), 1e-12)
+        assert np.abs(dx[isub == l] - dxo).max() <= tol * sx
+        np.testing.assert_allclose(Ft[l], ft, rtol=1e-8 if precision == 0 else 1e-4)
+        assert acc[l] == r
+        off += n
+    # both applied the same accepted steps
+    np.testing.assert_allclose(g.cameras(), o.cameras(), atol=1e-8 if precision == 0 else 1e-5)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_camera_scale_and_robust_weights(precision):
+    prob, o, g = prepared(synth.config(1), precision)
+    o.intersect()
+    sync_state(o, g)
+    np.testing.assert_allclose(g.camera_scale(), o.camera_scale(), rtol=1e-12, atol=1e-12)
+    nd_o = o.robust_weights()
+    nd_g = g.robust_weights()
+    assert nd_o == nd_g
+    np.testing.assert_array_equal(g.weights(), o.weights())
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("robust", [0, 1])
+def test_whole_iteration_final_rms(precision, robust):
+    prob = synth.config(1)
+    o = oracle.Oracle(prob)
+    ro = o.run(robust=robust, robust_from_start=robust)
+    g = rpba.Rpba(prob, precision=precision, robust=robust, robust_from_start=robust)
+    rg = g.iterate()
+    assert abs(rg["rms"] - ro["rms"]) <= 1e-3
+    if precision == 0:
+        assert rg["outer"] == ro["outer"]
+        assert rg["inner_total"] == ro["inner_total"]
+        assert rg["deleted_points"] == ro["deleted_points"]
+        np.testing.assert_allclose(rg["sigma0_hist"], ro["sigma0_hist"], rtol=1e-6)
+    else:
+        assert abs(rg["deleted_points"] - ro["deleted_points"]) <= max(3, 0.02 * ro["deleted_points"])
+
+
+def test_empty_subblock_single_observation_point_and_errors():
+    prob = synth.tiny(seed=9, runs=[3, 3])
+    prob["cam_subblock"] = np.where(prob["cam_subblock"] == 1, 2, 0).astype(np.int32)  # id 1 unused
+    # a point with a single observation stays inactive
+    prob["obs_cam"] = prob["obs_cam"].copy(); prob["obs_point"] = prob["obs_point"].copy()
+    j0 = prob["obs_point"][0]
+    keep = (prob["obs_point"] != j0) | (np.arange(prob["obs_point"].size) == 0)
+    for k in ("obs_cam", "obs_point", "obs_xy"):
+        prob[k] = prob[k][keep]
+    o = oracle.Oracle(prob)
+    ro = o.run()
+    g = rpba.Rpba(prob)
+    rg = g.iterate()
+    assert g.L == 3 and len(g.sub_cameras(1)) == 0
+    assert g.points()[1][j0] == 0
+    assert abs(rg["rms"] - ro["rms"]) <= 1e-9
+    # invalid inputs are rejected with a status, not a crash
+    bad = dict(prob); bad["obs_cam"] = prob["obs_cam"].copy(); bad["obs_cam"][0] = 999
+    with pytest.raises(rpba.RpbaError) as e:
+        rpba.Rpba(bad)
+    assert e.value.status == 1
+    dup = dict(prob)
+    for k in ("obs_cam", "obs_point", "obs_xy"):
+        dup[k] = np.concatenate([prob[k], prob[k][:1]])
+    with pytest.raises(rpba.RpbaError):
+        rpba.Rpba(dup)
+    nan = dict(prob); nan["obs_xy"] = prob["obs_xy"].copy(); nan["obs_xy"][3, 0] = np.nan
+    with pytest.raises(rpba.RpbaError) as e:
+        rpba.Rpba(nan)
+    assert e.value.status == 6
+
+
+def test_torch_allocator_and_stream():
+    import torch
+    prob = synth.config(1)
+    s = torch.cuda.Stream()
+    g = rpba.Rpba(prob, stream=s, torch_alloc=True)
+    rg = g.iterate()
+    g2 = rpba.Rpba(prob)
+    rg2 = g2.iterate()
+    assert rg["rms"] == pytest.approx(rg2["rms"], abs=1e-9)
+    g.close()
