@@ -87,9 +87,11 @@ typedef struct {
   double isect_tol;      /* ||dX|| <= tol (1 + ||X||) ends it, 1e-10 (FP64) */
   double cond_max;       /* Frobenius condition number that drops a point, 1e12 */
   int32_t precision;     /* 0: all FP64 ("plain"); 1: FP32 bulk, FP64 solve/reductions */
-  int32_t solver;        /* 0: dense Cholesky of the RCS; 1: block-Jacobi PCG */
+  int32_t solver;        /* RCS solve: 0 FP64 Cholesky; 2 FP32 Cholesky of the Jacobi-scaled
+                            RCS with FP64 iterative refinement */
   double pcg_tol;        /* relative residual of the PCG solve, 1e-8 */
   int32_t pcg_max_iter;  /* PCG iteration cap, 500 */
+  int32_t ir_steps;      /* refinement passes of solver 2 after the first solve, 2 */
   /* optional device allocator (NULL: cudaMalloc / cudaFree) */
   void *(*dev_alloc)(size_t bytes, void *user);
   void (*dev_free)(void *ptr, void *user);

@@ -177,24 +177,23 @@ void orc_rodrigues(const double w[3], double R[9]) {
     }
 }
 
-/* angle-axis vector of a rotation matrix */
+/* angle-axis vector of a rotation matrix: theta = atan2(sin, cos) with
+ * sin(theta) = |v| / 2, v = (R32 - R23, R13 - R31, R21 - R12) = 2 sin(theta) axis;
+ * near theta = pi the axis comes from the symmetric part
+ * cos(theta) I + (1 - cos(theta)) a a^T instead of v */
 void orc_rotation_log(const double R[9], double w[3]) {
-  double tr = R[0] + R[4] + R[8];
-  double c = 0.5 * (tr - 1.0);
-  if (c > 1.0) c = 1.0;
-  if (c < -1.0) c = -1.0;
-  double th = acos(c);
-  double v[3] = {R[7] - R[5], R[2] - R[6], R[3] - R[1]}; /* 2 sin(th) * axis */
+  double c = 0.5 * (R[0] + R[4] + R[8] - 1.0);
+  double v[3] = {R[7] - R[5], R[2] - R[6], R[3] - R[1]};
+  double s = 0.5 * sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  double th = atan2(s, c);
   if (th < 1e-6) {
-    for (int i = 0; i < 3; i++) w[i] = 0.5 * v[i];
+    for (int i = 0; i < 3; i++) w[i] = 0.5 * v[i] * (1.0 + th * th / 6.0);
     return;
   }
-  if (th < 3.14159265358979323846 - 1e-4) {
-    double s = th / (2.0 * sin(th));
-    for (int i = 0; i < 3; i++) w[i] = s * v[i];
+  if (th < 3.14159265358979323846 - 1e-3) {
+    for (int i = 0; i < 3; i++) w[i] = th / (2.0 * s) * v[i];
     return;
   }
-  /* near pi: axis from the symmetric part cos(th) I + (1 - cos(th)) a a^T */
   double B[3] = {(R[0] - c) / (1.0 - c), (R[4] - c) / (1.0 - c), (R[8] - c) / (1.0 - c)};
   int k = 0;
   if (B[1] > B[k]) k = 1;

@@ -1,14 +1,26 @@
 // kernels_chol.cu -- solve of the reduced camera systems S_l dC_l = y_l of all
-// running sub-blocks at once (Sec. 2: direct Cholesky factorisation of the RCS).
+// running sub-blocks at once (Sec. 2: Cholesky factorisation of the RCS).
 //
-// Each S_l is dense, row-major, padded to n_pad = 64 * tiles (identity on the
-// padding). Right-looking blocked Cholesky with 64 x 64 tiles, lower factor
-// in place, batched over sub-blocks of different sizes:
-//   step k: k_potrf_panel  one CTA per tile row i >= k: factor A_kk in shared
-//                          memory (every CTA redundantly), then L_ik = A_ik L_kk^-T
-//           k_syrk_update  one CTA per trailing tile (i, j), k < j <= i:
-//                          A_ij -= L_ik L_jk^T
-// then k_trsv: one CTA per sub-block, forward and backward substitution.
+// Layout: each S_l is dense, row-major, padded to n_pad = 32 * tiles with the
+// identity on the padding; only the lower triangle is read.
+//
+// Blocked right-looking Cholesky with 32 x 32 tiles, batched over sub-blocks
+// of different sizes, templated on the arithmetic type T:
+//   k_chol_first   tile (0,0): factor and invert (one warp)
+//   step k:
+//   k_chol_panel   one CTA per tile row i > k:  L_ik = A_ik Linv_kk^T
+//   k_chol_update  one CTA per trailing tile (i, j), k < j <= i:
+//                  A_ij -= L_ik L_jk^T; the CTA of tile (k+1, k+1) then
+//                  factors and inverts it, so the next panel can start
+// The inverted diagonal tiles Linv_kk turn the panel solve into a GEMM and
+// the diagonal steps of the triangular solves into 32 x 32 matrix-vector
+// products. k_trsv: forward and backward substitution, one CTA per sub-block.
+//
+// Two solvers use these kernels:
+//   FP64 direct: factor S in place (the all-FP64 form).
+//   mixed: Jacobi-scaled S' = D S D (D = diag(S)^-1/2) is rounded to FP32 and
+//   factored in FP32; the FP64 solution comes from iterative refinement
+//   x += L^-T L^-1 (D y - D S D x) with the residual in FP64 (k_symv).
 // A non-positive pivot marks the sub-block as failed (its LM step is rejected).
 #include <cuda_runtime.h>
 #include <math.h>
@@ -17,85 +29,152 @@
 
 namespace rpba {
 
-#define NB RPBA_TILE
-#define LDS (NB + 1)
+#define CT 32  // tile size
+#define CLD (CT + 1)
 
-__global__ void __launch_bounds__(256) k_potrf_panel(double *S, const long long *S_off, const int *npad,
-                                                     const int *run, int *fail, int k) {
-  int l = blockIdx.y;
-  if (!run[l] || fail[l]) return;
-  int np = npad[l];
-  int T = np / NB;
-  int ti = k + blockIdx.x;
-  if (ti >= T) return;
-  extern __shared__ double sm[];
-  double *D = sm, *B = sm + NB * LDS;
-  __shared__ int bad;
-  double *A = S + S_off[l];
-  int tid = threadIdx.x;
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    int r = e / NB, c = e - r * NB;
-    D[r * LDS + c] = A[(size_t)(k * NB + r) * np + k * NB + c];
-  }
-  if (tid == 0) bad = 0;
-  __syncthreads();
-  for (int j = 0; j < NB; j++) {
-    if (tid == 0) {
-      double d = D[j * LDS + j];
-      if (!(d > 0.0)) bad = 1;
-      else D[j * LDS + j] = sqrt(d);
-    }
-    __syncthreads();
-    if (bad) break;
-    double dj = D[j * LDS + j];
-    for (int r = j + 1 + tid; r < NB; r += blockDim.x) D[r * LDS + j] /= dj;
-    __syncthreads();
-    int w = NB - 1 - j;
-    for (int e = tid; e < w * w; e += blockDim.x) {
-      int rr = j + 1 + e / w, cc = j + 1 + e % w;
-      if (cc <= rr) D[rr * LDS + cc] -= D[rr * LDS + j] * D[cc * LDS + j];
-    }
-    __syncthreads();
-  }
-  if (bad) {
-    if (tid == 0) fail[l] = 1;
-    return;
-  }
-  if (ti == k) {
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-      int r = e / NB, c = e - r * NB;
-      if (c <= r) A[(size_t)(k * NB + r) * np + k * NB + c] = D[r * LDS + c];
-    }
-    return;
-  }
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    int r = e / NB, c = e - r * NB;
-    B[r * LDS + c] = A[(size_t)(ti * NB + r) * np + k * NB + c];
-  }
-  __syncthreads();
-  // X L_kk^T = B, row by row (each row independent)
-  if (tid < NB) {
-    double *x = B + tid * LDS;
-    for (int c = 0; c < NB; c++) {
-      double s = x[c];
-      for (int cp = 0; cp < c; cp++) s -= x[cp] * D[c * LDS + cp];
-      x[c] = s / D[c * LDS + c];
+struct CholView {
+  const long long *off;  // per sub-block offset of its matrix (elements)
+  const int *npad;       // padded size
+  const int *linv_off;   // per sub-block offset of its inverted diagonal tiles (elements)
+  const int *run;
+  int *fail;
+};
+
+// ---------------------------------------------------------------------------
+// one warp: factor the 32 x 32 tile held as rows in registers (lane = row),
+// then invert the factor into smem Xs (row-major, CLD stride). Returns false on
+// a non-positive pivot (uniform across the warp).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ bool warp_potrf_inv(T (&x)[CT], T *Ls, T *Xs) {
+  int lane = threadIdx.x & 31;
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < CT; j++) {
+    T piv = __shfl_sync(0xffffffffu, x[j], j);
+    if (!(piv > T(0))) ok = false;
+    T d = sqrt(piv);
+    T lj = (lane == j) ? d : x[j] / d;  // L[lane][j] for lane >= j
+    if (lane >= j) x[j] = lj;
+#pragma unroll
+    for (int c = j + 1; c < CT; c++) {
+      T lcj = __shfl_sync(0xffffffffu, lj, c);  // L[c][j]
+      if (lane >= c) x[c] -= lj * lcj;
     }
   }
-  __syncthreads();
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    int r = e / NB, c = e - r * NB;
-    A[(size_t)(ti * NB + r) * np + k * NB + c] = B[r * LDS + c];
+  ok = __all_sync(0xffffffffu, ok);
+  if (!ok) return false;
+  // L to smem (row lane), zeros above the diagonal
+#pragma unroll
+  for (int c = 0; c < CT; c++) Ls[lane * CLD + c] = (c <= lane) ? x[c] : T(0);
+  __syncwarp();
+  // inverse, column `lane`: forward substitution L xcol = e_lane
+  T xc[CT];
+#pragma unroll
+  for (int r = 0; r < CT; r++) {
+    T s = (r == lane) ? T(1) : T(0);
+#pragma unroll
+    for (int m = 0; m < r; m++) s -= Ls[r * CLD + m] * xc[m];
+    xc[r] = (r >= lane) ? s / Ls[r * CLD + r] : T(0);
+  }
+#pragma unroll
+  for (int r = 0; r < CT; r++) Xs[r * CLD + lane] = xc[r];
+  __syncwarp();
+  return true;
+}
+
+// store the factored tile (lower part) and its inverse
+template <typename T>
+__device__ void store_diag(T *A, int np, int k, const T *Ls, const T *Xs, T *Linv) {
+  for (int e = threadIdx.x; e < CT * CT; e += blockDim.x) {
+    int r = e / CT, c = e - r * CT;
+    if (c <= r) A[(size_t)(k * CT + r) * np + k * CT + c] = Ls[r * CLD + c];
+    Linv[e] = Xs[r * CLD + c];
   }
 }
 
-__global__ void __launch_bounds__(256) k_syrk_update(double *S, const long long *S_off, const int *npad,
-                                                     const int *run, const int *fail, int k) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_chol_first(T *S, T *Linv, CholView cv) {
+  int l = blockIdx.x;
+  if (!cv.run[l] || cv.fail[l] || cv.npad[l] == 0) return;
+  int np = cv.npad[l];
+  T *A = S + cv.off[l];
+  __shared__ T Ls[CT * CLD], Xs[CT * CLD];
+  __shared__ int bad;
+  if (threadIdx.x < 32) {
+    T x[CT];
+    int lane = threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < CT; c++) x[c] = A[(size_t)lane * np + c];
+    bool ok = warp_potrf_inv<T>(x, Ls, Xs);
+    if (lane == 0) bad = !ok;
+  }
+  __syncthreads();
+  if (bad) {
+    if (threadIdx.x == 0) cv.fail[l] = 1;
+    return;
+  }
+  store_diag<T>(A, np, 0, Ls, Xs, Linv + cv.linv_off[l]);
+}
+
+// 32 x 32 x 32 product on 256 threads, 2 x 2 outputs per thread:
+// out[r][c] = sum_m P[r][m] Q[c][m]  (P, Q in smem, CLD stride)
+template <typename T>
+__device__ inline void tile_nt(const T *P, const T *Q, T (&acc)[2][2]) {
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int r = 0; r < 2; r++)
+#pragma unroll
+    for (int c = 0; c < 2; c++) acc[r][c] = T(0);
+#pragma unroll 8
+  for (int m = 0; m < CT; m++) {
+    T a0 = P[ty * CLD + m], a1 = P[(ty + 16) * CLD + m];
+    T b0 = Q[tx * CLD + m], b1 = Q[(tx + 16) * CLD + m];
+    acc[0][0] = fma(a0, b0, acc[0][0]);
+    acc[0][1] = fma(a0, b1, acc[0][1]);
+    acc[1][0] = fma(a1, b0, acc[1][0]);
+    acc[1][1] = fma(a1, b1, acc[1][1]);
+  }
+}
+
+template <typename T>
+__device__ inline void load_tile(T *dst, const T *A, int np, int ti, int tj) {
+  for (int e = threadIdx.x; e < CT * CT; e += blockDim.x) {
+    int r = e / CT, c = e - r * CT;
+    dst[r * CLD + c] = A[(size_t)(ti * CT + r) * np + tj * CT + c];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_chol_panel(T *S, const T *Linv, CholView cv, int k) {
   int l = blockIdx.y;
-  if (!run[l] || fail[l]) return;
-  int np = npad[l];
-  int T = np / NB;
-  int rem = T - k - 1;
+  if (!cv.run[l] || cv.fail[l]) return;
+  int np = cv.npad[l];
+  int nt = np / CT;
+  int ti = k + 1 + blockIdx.x;
+  if (ti >= nt) return;
+  T *A = S + cv.off[l];
+  __shared__ T P[CT * CLD], Q[CT * CLD];
+  load_tile<T>(P, A, np, ti, k);
+  const T *Li = Linv + cv.linv_off[l] + (size_t)k * CT * CT;
+  for (int e = threadIdx.x; e < CT * CT; e += blockDim.x) Q[(e / CT) * CLD + e % CT] = Li[e];
+  __syncthreads();
+  T acc[2][2];
+  tile_nt<T>(P, Q, acc);  // A_ik Linv_kk^T
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int r = 0; r < 2; r++)
+#pragma unroll
+    for (int c = 0; c < 2; c++) A[(size_t)(ti * CT + ty + 16 * r) * np + k * CT + tx + 16 * c] = acc[r][c];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_chol_update(T *S, T *Linv, CholView cv, int k) {
+  int l = blockIdx.y;
+  if (!cv.run[l] || cv.fail[l]) return;
+  int np = cv.npad[l];
+  int nt = np / CT;
+  int rem = nt - k - 1;
   if (rem <= 0) return;
   long long p = blockIdx.x;
   int a = (int)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
@@ -104,123 +183,274 @@ __global__ void __launch_bounds__(256) k_syrk_update(double *S, const long long 
   int b = (int)(p - (long long)a * (a + 1) / 2);
   if (a >= rem) return;
   int ti = k + 1 + a, tj = k + 1 + b;
-  extern __shared__ double sm[];
-  double *Li = sm, *Lj = sm + NB * LDS;
-  double *A = S + S_off[l];
-  int tid = threadIdx.x;
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    int r = e / NB, c = e - r * NB;
-    Li[r * LDS + c] = A[(size_t)(ti * NB + r) * np + k * NB + c];
-    Lj[r * LDS + c] = A[(size_t)(tj * NB + r) * np + k * NB + c];
+  T *A = S + cv.off[l];
+  __shared__ T P[CT * CLD], Q[CT * CLD], C[CT * CLD];
+  __shared__ int bad;
+  load_tile<T>(P, A, np, ti, k);
+  load_tile<T>(Q, A, np, tj, k);
+  __syncthreads();
+  T acc[2][2];
+  tile_nt<T>(P, Q, acc);
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  bool diag_next = (ti == k + 1) && (tj == k + 1);
+  if (!diag_next) {
+#pragma unroll
+    for (int r = 0; r < 2; r++)
+#pragma unroll
+      for (int c = 0; c < 2; c++) A[(size_t)(ti * CT + ty + 16 * r) * np + tj * CT + tx + 16 * c] -= acc[r][c];
+    return;
+  }
+  // tile (k+1, k+1) is complete: update, factor and invert it here
+#pragma unroll
+  for (int r = 0; r < 2; r++)
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+      int rr = ty + 16 * r, cc = tx + 16 * c;
+      C[rr * CLD + cc] = A[(size_t)(ti * CT + rr) * np + tj * CT + cc] - acc[r][c];
+    }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    T x[CT];
+    int lane = threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < CT; c++) x[c] = C[lane * CLD + c];
+    bool ok = warp_potrf_inv<T>(x, P, Q);  // P <- L, Q <- L^-1
+    if (lane == 0) bad = !ok;
   }
   __syncthreads();
-  int tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
-#pragma unroll
-  for (int r = 0; r < 4; r++)
-#pragma unroll
-    for (int c = 0; c < 4; c++) acc[r][c] = 0.0;
-#pragma unroll 4
-  for (int kk = 0; kk < NB; kk++) {
-    double av[4], bv[4];
-#pragma unroll
-    for (int r = 0; r < 4; r++) av[r] = Li[(ty + 16 * r) * LDS + kk];
-#pragma unroll
-    for (int c = 0; c < 4; c++) bv[c] = Lj[(tx + 16 * c) * LDS + kk];
-#pragma unroll
-    for (int r = 0; r < 4; r++)
-#pragma unroll
-      for (int c = 0; c < 4; c++) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+  if (bad) {
+    if (threadIdx.x == 0) cv.fail[l] = 1;
+    return;
   }
-#pragma unroll
-  for (int r = 0; r < 4; r++)
-#pragma unroll
-    for (int c = 0; c < 4; c++) {
-      size_t off = (size_t)(ti * NB + ty + 16 * r) * np + tj * NB + tx + 16 * c;
-      A[off] -= acc[r][c];
-    }
+  store_diag<T>(A, np, k + 1, P, Q, Linv + cv.linv_off[l] + (size_t)(k + 1) * CT * CT);
 }
 
-// forward L z = y (z stored in y) and backward L^T x = z (x stored in dC)
-__global__ void __launch_bounds__(256) k_trsv(const double *S, const long long *S_off, const int *npad,
-                                              const int *ycam_off, const int *run, const int *fail, double *y,
-                                              double *dC) {
+// forward L z = r and backward L^T x = z; r (in) and x (out) in T, one CTA per
+// sub-block; diagonal tiles through their inverses
+template <typename T>
+__global__ void __launch_bounds__(256) k_trsv(const T *S, const T *Linv, CholView cv, const int *voff, T *r,
+                                              T *x) {
   int l = blockIdx.x;
-  if (!run[l] || fail[l]) return;
-  int np = npad[l];
-  int T = np / NB;
-  const double *A = S + S_off[l];
-  double *z = y + ycam_off[l];
-  double *x = dC + ycam_off[l];
-  __shared__ double xs[NB];
-  int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  for (int kt = 0; kt < T; kt++) {
-    int base = kt * NB;
-    if (warp == 0) {
-      for (int r = 0; r < NB; r++) {
-        const double *row = A + (size_t)(base + r) * np + base;
-        double s = 0.0;
-        for (int c = lane; c < r; c += 32) s += row[c] * xs[c];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) xs[r] = (z[base + r] - s) / row[r];
-        __syncwarp();
-      }
-    }
+  if (!cv.run[l] || cv.fail[l]) return;
+  int np = cv.npad[l];
+  int nt = np / CT;
+  const T *A = S + cv.off[l];
+  const T *LI = Linv + cv.linv_off[l];
+  T *z = r + voff[l];
+  T *xo = x + voff[l];
+  __shared__ T zs[CT];
+  int tid = threadIdx.x;
+  int row = tid >> 3, part = tid & 7;  // 32 rows x 8 parts for the 32 x 32 products
+  for (int kt = 0; kt < nt; kt++) {
+    int base = kt * CT;
+    const T *Li = LI + (size_t)kt * CT * CT;
+    T s = 0;
+#pragma unroll
+    for (int c = 0; c < 4; c++) s += Li[row * CT + part * 4 + c] * z[base + part * 4 + c];
+    for (int o = 4; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, 8);
     __syncthreads();
-    for (int r = tid; r < NB; r += blockDim.x) z[base + r] = xs[r];
-    for (int i = base + NB + warp; i < np; i += nw) {
-      const double *row = A + (size_t)i * np + base;
-      double s = row[lane] * xs[lane] + row[lane + 32] * xs[lane + 32];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      if (lane == 0) z[i] -= s;
+    if (part == 0) zs[row] = s;
+    __syncthreads();
+    if (tid < CT) z[base + tid] = zs[tid];
+    for (int i = base + CT + tid; i < np; i += blockDim.x) {
+      const T *rowp = A + (size_t)i * np + base;
+      T acc = 0;
+#pragma unroll
+      for (int c = 0; c < CT; c++) acc += rowp[c] * zs[c];
+      z[i] -= acc;
     }
     __syncthreads();
   }
-  for (int e = tid; e < np; e += blockDim.x) x[e] = z[e];
-  __syncthreads();
-  for (int kt = T - 1; kt >= 0; kt--) {
-    int base = kt * NB;
-    if (warp == 0) {
-      for (int r = NB - 1; r >= 0; r--) {
-        double s = 0.0;
-        for (int c = r + 1 + lane; c < NB; c += 32) s += A[(size_t)(base + c) * np + base + r] * xs[c];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) xs[r] = (x[base + r] - s) / A[(size_t)(base + r) * np + base + r];
-        __syncwarp();
-      }
-    }
+  for (int kt = nt - 1; kt >= 0; kt--) {
+    int base = kt * CT;
+    const T *Li = LI + (size_t)kt * CT * CT;
+    // x_k = Linv_kk^T z_k
+    T s = 0;
+#pragma unroll
+    for (int c = 0; c < 4; c++) s += Li[(part * 4 + c) * CT + row] * z[base + part * 4 + c];
+    for (int o = 4; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, 8);
     __syncthreads();
-    for (int r = tid; r < NB; r += blockDim.x) x[base + r] = xs[r];
+    if (part == 0) zs[row] = s;
+    __syncthreads();
+    if (tid < CT) xo[base + tid] = zs[tid];
     for (int c = tid; c < base; c += blockDim.x) {
-      double s = 0.0;
-      for (int r = 0; r < NB; r++) s += A[(size_t)(base + r) * np + c] * xs[r];
-      x[c] -= s;
+      T acc = 0;
+#pragma unroll 8
+      for (int rr = 0; rr < CT; rr++) acc += A[(size_t)(base + rr) * np + c] * zs[rr];
+      z[c] -= acc;
     }
     __syncthreads();
+  }
+}
+
+template <typename T>
+static rpba_status factor(Ctx *ctx, T *S, T *Linv, CholView cv, int T_max) {
+  const char *n_first = sizeof(T) == 8 ? "k_chol_first_f64" : "k_chol_first_f32";
+  const char *n_panel = sizeof(T) == 8 ? "k_chol_panel_f64" : "k_chol_panel_f32";
+  const char *n_upd = sizeof(T) == 8 ? "k_chol_update_f64" : "k_chol_update_f32";
+  RPBA_KERNEL(ctx, n_first, k_chol_first<T><<<ctx->L, 256, 0, ctx->stream>>>(S, Linv, cv));
+  for (int k = 0; k + 1 < T_max; k++) {
+    dim3 gp(T_max - k - 1, ctx->L);
+    RPBA_KERNEL(ctx, n_panel, k_chol_panel<T><<<gp, 256, 0, ctx->stream>>>(S, Linv, cv, k));
+    int rem = T_max - k - 1;
+    dim3 gu((unsigned)((long long)rem * (rem + 1) / 2), ctx->L);
+    RPBA_KERNEL(ctx, n_upd, k_chol_update<T><<<gu, 256, 0, ctx->stream>>>(S, Linv, cv, k));
+  }
+  return RPBA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// mixed-precision solve: scaling, FP64 residual, refinement updates
+// ---------------------------------------------------------------------------
+// d = diag(S)^-1/2 (1 on the padding), rs = D y, x = 0
+__global__ void k_mixed_scale(const double *S, const long long *off, const int *npad, const int *voff,
+                              const int *run, const double *y, double *d, double *rs, double *x) {
+  int l = blockIdx.y;
+  if (!run[l]) return;
+  int np = npad[l];
+  const double *A = S + off[l];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < np; e += gridDim.x * blockDim.x) {
+    double s = A[(size_t)e * np + e];
+    double de = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
+    int g = voff[l] + e;
+    d[g] = de;
+    rs[g] = de * y[g];
+    x[g] = 0.0;
+  }
+}
+
+// S32 = D S D rounded to FP32 (lower triangle); the products are formed in
+// FP32 (the refinement corrects the factor's rounding)
+__global__ void k_mixed_convert(const double *S, float *S32, const long long *off, const long long *off32,
+                                const int *npad, const int *voff, const int *run, const double *d) {
+  int l = blockIdx.y;
+  if (!run[l]) return;
+  int np = npad[l];
+  const double *A = S + off[l];
+  float *B = S32 + off32[l];
+  const double *dl = d + voff[l];
+  size_t tot = (size_t)np * np;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    size_t r = e / np, c = e - r * np;
+    if (c > r) continue;
+    B[e] = (float)A[e] * (float)dl[r] * (float)dl[c];
+  }
+}
+
+// u = D x (FP64); t = S u with S symmetric from its lower triangle, one CTA per
+// 32 x 32 lower tile: t_I += S_IJ u_J and, off the diagonal, t_J += S_IJ^T u_I
+__global__ void __launch_bounds__(256) k_symv(const double *S, const long long *off, const int *npad,
+                                              const int *voff, const int *run, const int *fail, const double *d,
+                                              const double *x, double *t, int T_max) {
+  int l = blockIdx.y;
+  if (!run[l] || fail[l]) return;
+  int np = npad[l];
+  int nt = np / CT;
+  long long p = blockIdx.x;
+  int a = (int)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
+  while ((long long)(a + 1) * (a + 2) / 2 <= p) a++;
+  while ((long long)a * (a + 1) / 2 > p) a--;
+  int b = (int)(p - (long long)a * (a + 1) / 2);
+  if (a >= nt) return;
+  const double *A = S + off[l];
+  const double *dl = d + voff[l], *xl = x + voff[l];
+  double *tl = t + voff[l];
+  __shared__ double uI[CT], uJ[CT];
+  __shared__ double blk[CT][CLD];
+  int tid = threadIdx.x;
+  if (tid < CT) {
+    uI[tid] = dl[a * CT + tid] * xl[a * CT + tid];
+    uJ[tid] = dl[b * CT + tid] * xl[b * CT + tid];
+  }
+  for (int e = tid; e < CT * CT; e += blockDim.x) {
+    int r = e / CT, c = e - r * CT;
+    double v = A[(size_t)(a * CT + r) * np + b * CT + c];
+    if (a == b && c > r) v = A[(size_t)(a * CT + c) * np + b * CT + r];  // mirror the diagonal tile
+    blk[r][c] = v;
+  }
+  __syncthreads();
+  if (tid < CT) {
+    double s = 0.0;
+    for (int c = 0; c < CT; c++) s += blk[tid][c] * uJ[c];
+    atomicAdd(tl + a * CT + tid, s);
+  } else if (tid < 2 * CT && a != b) {
+    int c = tid - CT;
+    double s = 0.0;
+    for (int r = 0; r < CT; r++) s += blk[r][c] * uI[r];
+    atomicAdd(tl + b * CT + c, s);
+  }
+}
+
+// r32 = (float)(rs - D t)   (residual of the scaled system), or rs on the first pass
+__global__ void k_mixed_residual(const int *run, const int *fail, const int *voff, const int *npad, int L,
+                                 const double *rs, const double *d, const double *t, float *r32, int first) {
+  int l = blockIdx.y;
+  if (l >= L || !run[l] || fail[l]) return;
+  int np = npad[l];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < np; e += gridDim.x * blockDim.x) {
+    int g = voff[l] + e;
+    r32[g] = (float)(first ? rs[g] : rs[g] - d[g] * t[g]);
+  }
+}
+
+// x += z; on the last pass dC = D x
+__global__ void k_mixed_update(const int *run, const int *fail, const int *voff, const int *npad, int L,
+                               const float *z, double *x, const double *d, double *dC, int last) {
+  int l = blockIdx.y;
+  if (l >= L || !run[l] || fail[l]) return;
+  int np = npad[l];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < np; e += gridDim.x * blockDim.x) {
+    int g = voff[l] + e;
+    double v = x[g] + (double)z[g];
+    x[g] = v;
+    if (last) dC[g] = d[g] * v;
   }
 }
 
 rpba_status launch_solve_rcs(Ctx *ctx, const int *run_dev, int *fail_dev) {
   RPBA_CUDA(cudaMemsetAsync(fail_dev, 0, ctx->L * sizeof(int), ctx->stream));
-  size_t smem = 2 * NB * LDS * sizeof(double);
-  static bool attr_done = false;
-  if (!attr_done) {
-    RPBA_CUDA(cudaFuncSetAttribute(k_potrf_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    RPBA_CUDA(cudaFuncSetAttribute(k_syrk_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_done = true;
+  int T_max = ctx->max_tiles;
+  if (T_max == 0) return RPBA_OK;
+  if (ctx->opt.solver != 2) {
+    // FP64 direct: factor S in place, one forward/backward solve
+    CholView cv{ctx->S_off, ctx->npad, ctx->linv_off, run_dev, fail_dev};
+    RPBA_TRY(factor<double>(ctx, ctx->S, ctx->Linv64, cv, T_max));
+    RPBA_CUDA(cudaMemcpyAsync(ctx->dC, ctx->y, ctx->ytot * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    RPBA_KERNEL(ctx, "k_trsv_f64", k_trsv<double><<<ctx->L, 256, 0, ctx->stream>>>(ctx->S, ctx->Linv64, cv,
+                                                                               ctx->ycam_off, ctx->dC, ctx->dC));
+    return RPBA_OK;
   }
-  int T = ctx->max_tiles;
-  for (int k = 0; k < T; k++) {
-    dim3 gp(T - k, ctx->L);
-    RPBA_KERNEL(ctx, "k_potrf_panel", k_potrf_panel<<<gp, 256, smem, ctx->stream>>>(ctx->S, ctx->S_off, ctx->npad, run_dev, fail_dev, k));
-    int rem = T - k - 1;
-    if (rem > 0) {
-      dim3 gu((unsigned)((long long)rem * (rem + 1) / 2), ctx->L);
-      RPBA_KERNEL(ctx, "k_syrk_update", k_syrk_update<<<gu, 256, smem, ctx->stream>>>(ctx->S, ctx->S_off, ctx->npad, run_dev, fail_dev, k));
+  // mixed: FP32 factor of the scaled system, FP64 iterative refinement
+  dim3 g(16, ctx->L);
+  RPBA_KERNEL(ctx, "k_mixed_scale",
+              k_mixed_scale<<<g, 256, 0, ctx->stream>>>(ctx->S, ctx->S_off, ctx->npad, ctx->ycam_off, run_dev, ctx->y,
+                                                        ctx->ir_d, ctx->ir_rs, ctx->ir_x));
+  RPBA_KERNEL(ctx, "k_mixed_convert",
+              k_mixed_convert<<<dim3(64, ctx->L), 256, 0, ctx->stream>>>(ctx->S, ctx->S32, ctx->S_off, ctx->S32_off,
+                                                                         ctx->npad, ctx->ycam_off, run_dev,
+                                                                         ctx->ir_d));
+  CholView cv{ctx->S32_off, ctx->npad, ctx->linv_off, run_dev, fail_dev};
+  RPBA_TRY(factor<float>(ctx, ctx->S32, ctx->Linv32, cv, T_max));
+  int passes = 1 + ctx->opt.ir_steps;
+  for (int it = 0; it < passes; it++) {
+    if (it > 0) {
+      RPBA_CUDA(cudaMemsetAsync(ctx->ir_t, 0, ctx->ytot * sizeof(double), ctx->stream));
+      dim3 gs((unsigned)((long long)T_max * (T_max + 1) / 2), ctx->L);
+      RPBA_KERNEL(ctx, "k_symv", k_symv<<<gs, 256, 0, ctx->stream>>>(ctx->S, ctx->S_off, ctx->npad, ctx->ycam_off,
+                                                                     run_dev, fail_dev, ctx->ir_d, ctx->ir_x,
+                                                                     ctx->ir_t, T_max));
     }
+    RPBA_KERNEL(ctx, "k_mixed_residual",
+                k_mixed_residual<<<g, 256, 0, ctx->stream>>>(run_dev, fail_dev, ctx->ycam_off, ctx->npad, ctx->L,
+                                                             ctx->ir_rs, ctx->ir_d, ctx->ir_t, ctx->ir_r32, it == 0));
+    RPBA_KERNEL(ctx, "k_trsv_f32", k_trsv<float><<<ctx->L, 256, 0, ctx->stream>>>(ctx->S32, ctx->Linv32, cv,
+                                                                               ctx->ycam_off, ctx->ir_r32,
+                                                                               ctx->ir_r32));
+    RPBA_KERNEL(ctx, "k_mixed_update",
+                k_mixed_update<<<g, 256, 0, ctx->stream>>>(run_dev, fail_dev, ctx->ycam_off, ctx->npad, ctx->L,
+                                                           ctx->ir_r32, ctx->ir_x, ctx->ir_d, ctx->dC,
+                                                           it == passes - 1));
   }
-  RPBA_KERNEL(ctx, "k_trsv", k_trsv<<<ctx->L, 256, 0, ctx->stream>>>(ctx->S, ctx->S_off, ctx->npad, ctx->ycam_off, run_dev, fail_dev, ctx->y,
-                                          ctx->dC));
   return RPBA_OK;
 }
 

@@ -506,14 +506,13 @@ __global__ void k_sub_sum(View v, const int *run, double *F) {
   if (threadIdx.x == 0) F[l] = out[0];
 }
 
+// The cost that decides acceptance is evaluated in FP64 in both forms: FP32
+// residuals of ~1000 px coordinates carry ~1e-4 px rounding, which hides the
+// last LM improvements.
 static rpba_status sub_costs_impl(Ctx *ctx, int trial, const int *run, double *F_dev) {
   View v = make_view(ctx);
-  if (ctx->P) {
-    if (ctx->opt.precision == 1)
-      RPBA_KERNEL(ctx, "k_inst_cost", k_inst_cost<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, trial, run));
-    else
-      RPBA_KERNEL(ctx, "k_inst_cost", k_inst_cost<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, trial, run));
-  }
+  if (ctx->P)
+    RPBA_KERNEL(ctx, "k_inst_cost", k_inst_cost<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, trial, run));
   RPBA_KERNEL(ctx, "k_sub_sum", k_sub_sum<<<ctx->L, 256, 0, ctx->stream>>>(v, run, F_dev));
   return RPBA_OK;
 }

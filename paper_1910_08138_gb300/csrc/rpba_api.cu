@@ -31,21 +31,24 @@ __global__ void k_pose_to_R(int M, const double *pose, double *R, double *t) {
   for (int e = 0; e < 3; e++) t[3 * i + e] = pose[6 * i + 3 + e];
 }
 
-// angle-axis vector of R (log map; axis from the symmetric part near pi)
+// angle-axis vector of R: theta = atan2(|v| / 2, (tr R - 1) / 2) with v the
+// skew part (2 sin(theta) axis); close to theta = pi the axis is taken from
+// the symmetric part, whose conditioning does not degrade there
 __global__ void k_R_to_pose(int M, const double *R, const double *t, double *pose) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
   const double *Q = R + 9 * i;
   double c = 0.5 * (Q[0] + Q[4] + Q[8] - 1.0);
-  c = fmin(1.0, fmax(-1.0, c));
-  double th = acos(c);
   double v[3] = {Q[7] - Q[5], Q[2] - Q[6], Q[3] - Q[1]};
+  double sn = 0.5 * sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  double th = atan2(sn, c);
   double w[3];
   if (th < 1e-6) {
-    for (int e = 0; e < 3; e++) w[e] = 0.5 * v[e];
-  } else if (th < 3.14159265358979323846 - 1e-4) {
-    double s = th / (2.0 * sin(th));
-    for (int e = 0; e < 3; e++) w[e] = s * v[e];
+    double f = 0.5 * (1.0 + th * th / 6.0);
+    for (int e = 0; e < 3; e++) w[e] = f * v[e];
+  } else if (th < 3.14159265358979323846 - 1e-3) {
+    double f = th / (2.0 * sn);
+    for (int e = 0; e < 3; e++) w[e] = f * v[e];
   } else {
     double B[3] = {(Q[0] - c) / (1.0 - c), (Q[4] - c) / (1.0 - c), (Q[8] - c) / (1.0 - c)};
     int k = 0;
@@ -172,6 +175,7 @@ extern "C" void rpba_default_options(rpba_options *o) {
   o->solver = 0;
   o->pcg_tol = 1e-8;
   o->pcg_max_iter = 500;
+  o->ir_steps = 2;
 }
 
 extern "C" const char *rpba_last_error(const rpba_ctx *ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
@@ -338,6 +342,13 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   ctx->h_npad = npad;
   ctx->S_total = stot;
   ctx->max_tiles = maxT;
+  ctx->ytot = yt;
+  std::vector<int> loff(L);
+  int ltot = 0;
+  for (int l = 0; l < L; l++) {
+    loff[l] = ltot;
+    ltot += ntiles[l] * RPBA_TILE * RPBA_TILE;
+  }
   // per-observation arrays in GPU order
   std::vector<int> ocam(K), opt(K);
   std::vector<double> oxy(2 * (size_t)K), ow(3 * (size_t)(ctx->has_winv ? K : 0));
@@ -410,6 +421,18 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   RPBA_TRY(upload(ctx, &ctx->npad, npad.data(), (size_t)L));
   RPBA_TRY(upload(ctx, &ctx->ycam_off, yoff.data(), (size_t)L));
   RPBA_TRY(upload(ctx, &ctx->sub_ntiles, ntiles.data(), (size_t)L));
+  RPBA_TRY(upload(ctx, &ctx->linv_off, loff.data(), (size_t)L));
+  RPBA_TRY(alloc_n(ctx, &ctx->Linv64, (size_t)std::max(ltot, 1)));
+  if (ctx->opt.solver == 2) {
+    RPBA_TRY(alloc_n(ctx, &ctx->S32, (size_t)std::max(stot, 1LL)));
+    RPBA_TRY(upload(ctx, &ctx->S32_off, soff.data(), (size_t)L));
+    RPBA_TRY(alloc_n(ctx, &ctx->Linv32, (size_t)std::max(ltot, 1)));
+    RPBA_TRY(alloc_n(ctx, &ctx->ir_r32, (size_t)std::max(yt, 1)));
+    RPBA_TRY(alloc_n(ctx, &ctx->ir_d, (size_t)std::max(yt, 1)));
+    RPBA_TRY(alloc_n(ctx, &ctx->ir_rs, (size_t)std::max(yt, 1)));
+    RPBA_TRY(alloc_n(ctx, &ctx->ir_x, (size_t)std::max(yt, 1)));
+    RPBA_TRY(alloc_n(ctx, &ctx->ir_t, (size_t)std::max(yt, 1)));
+  }
   RPBA_TRY(alloc_n(ctx, &ctx->lm_lambda, (size_t)L));
   RPBA_TRY(alloc_n(ctx, &ctx->lm_F, (size_t)L));
   RPBA_TRY(alloc_n(ctx, &ctx->lm_Ft, (size_t)L));
@@ -445,8 +468,9 @@ extern "C" rpba_status rpba_create(const rpba_problem *prob, const rpba_options 
   Ctx *ctx = &h->c;
   if (opt) ctx->opt = *opt;
   else rpba_default_options(&ctx->opt);
-  if (ctx->opt.precision != 0 && ctx->opt.precision != 1) {
-    ctx->err = "precision must be 0 or 1";
+  if ((ctx->opt.precision != 0 && ctx->opt.precision != 1) || ctx->opt.solver < 0 || ctx->opt.solver > 2 ||
+      ctx->opt.solver == 1 || ctx->opt.ir_steps < 0 || ctx->opt.ir_steps > 20) {
+    ctx->err = "invalid precision / solver / ir_steps option";
     *out = h;
     return RPBA_ERR_INVALID_ARG;
   }

@@ -18,7 +18,10 @@
 //   Schur pairs:   (a, b) observation positions of one instance whose cameras
 //                  differ, local(cam a) > local(cam b): lower-triangle blocks
 //   RCS:           per sub-block a dense n_pad x n_pad f64 matrix (row-major,
-//                  n_pad = 64 * ceil(6 M_l / 64), padding = identity), rhs
+//                  n_pad = 32 * ceil(6 M_l / 32), padding = identity), rhs;
+//                  inverted 32 x 32 diagonal tiles of the factor; for the
+//                  mixed solver an FP32 copy of the scaled RCS and FP64
+//                  refinement vectors
 #pragma once
 
 #include <cuda_runtime.h>
@@ -30,7 +33,7 @@
 
 #include "../../include/rpba.h"
 
-#define RPBA_TILE 64
+#define RPBA_TILE 32
 
 namespace rpba {
 
@@ -186,7 +189,12 @@ struct Ctx {
   // RCS
   double *S = nullptr, *y = nullptr, *dC = nullptr;  // y, dC: sum of n_pad over l
   long long *S_off = nullptr;
-  int *npad = nullptr, *ycam_off = nullptr, *sub_ntiles = nullptr;
+  int *npad = nullptr, *ycam_off = nullptr, *sub_ntiles = nullptr, *linv_off = nullptr;
+  int ytot = 0;
+  double *Linv64 = nullptr;
+  float *S32 = nullptr, *Linv32 = nullptr, *ir_r32 = nullptr;
+  long long *S32_off = nullptr;
+  double *ir_d = nullptr, *ir_rs = nullptr, *ir_x = nullptr, *ir_t = nullptr;
   // LM control per sub-block
   double *lm_lambda = nullptr, *lm_F = nullptr, *lm_Ft = nullptr, *lm_best = nullptr;
   int *lm_grace = nullptr, *lm_rej = nullptr, *lm_it = nullptr, *lm_run = nullptr;
