@@ -84,14 +84,15 @@ typedef struct {
   int32_t robust;        /* 1: robust stage (Sec. 5.3, parallel variant) */
   int32_t robust_from_start; /* 1: robust weights from the first intersection on */
   int32_t isect_max_iter;/* Gauss-Newton iterations of the intersection, 10 */
-  double isect_tol;      /* ||dX|| <= tol (1 + ||X||) ends it, 1e-10 (FP64) */
+  double isect_tol;      /* ||dX|| <= tol (1 + ||X||) ends it, 1e-10; the FP32 form also
+                            stops once dX moves the image residuals by < 1e-3 px */
   double cond_max;       /* Frobenius condition number that drops a point, 1e12 */
   int32_t precision;     /* 0: all FP64 ("plain"); 1: FP32 bulk, FP64 solve/reductions */
   int32_t solver;        /* RCS solve: 0 FP64 Cholesky; 2 FP32 Cholesky of the Jacobi-scaled
                             RCS with FP64 iterative refinement */
   double pcg_tol;        /* relative residual of the PCG solve, 1e-8 */
   int32_t pcg_max_iter;  /* PCG iteration cap, 500 */
-  int32_t ir_steps;      /* refinement passes of solver 2 after the first solve, 2 */
+  int32_t ir_steps;      /* refinement passes of solver 2 after the first solve, 1 */
   /* optional device allocator (NULL: cudaMalloc / cudaFree) */
   void *(*dev_alloc)(size_t bytes, void *user);
   void (*dev_free)(void *ptr, void *user);

@@ -14,7 +14,8 @@
 //                  factors and inverts it, so the next panel can start
 // The inverted diagonal tiles Linv_kk turn the panel solve into a GEMM and
 // the diagonal steps of the triangular solves into 32 x 32 matrix-vector
-// products. k_trsv: forward and backward substitution, one CTA per sub-block.
+// products. k_trsv_cluster: forward and backward substitution, one thread
+// block cluster per sub-block.
 //
 // Two solvers use these kernels:
 //   FP64 direct: factor S in place (the all-FP64 form).
@@ -22,6 +23,7 @@
 //   factored in FP32; the FP64 solution comes from iterative refinement
 //   x += L^-T L^-1 (D y - D S D x) with the residual in FP64 (k_symv).
 // A non-positive pivot marks the sub-block as failed (its LM step is rejected).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -38,7 +40,20 @@ struct CholView {
   const int *linv_off;   // per sub-block offset of its inverted diagonal tiles (elements)
   const int *run;
   int *fail;
+  const int *sched;      // per step k: L+1 prefix sums of panel tiles, then L+1 of update tiles
+  int L;
 };
+
+// CTA -> (sub-block, local index) through the prefix sums of step k
+__device__ inline int sched_find(const int *base, int L, int idx, int *local) {
+  int lo = 0, hi = L - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (base[mid] <= idx) lo = mid; else hi = mid - 1;
+  }
+  *local = idx - base[lo];
+  return lo;
+}
 
 // ---------------------------------------------------------------------------
 // one warp: factor the 32 x 32 tile held as rows in registers (lane = row),
@@ -147,11 +162,12 @@ __device__ inline void load_tile(T *dst, const T *A, int np, int ti, int tj) {
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_chol_panel(T *S, const T *Linv, CholView cv, int k) {
-  int l = blockIdx.y;
+  int loc;
+  int l = sched_find(cv.sched + (size_t)k * 2 * (cv.L + 1), cv.L, blockIdx.x, &loc);
   if (!cv.run[l] || cv.fail[l]) return;
   int np = cv.npad[l];
   int nt = np / CT;
-  int ti = k + 1 + blockIdx.x;
+  int ti = k + 1 + loc;
   if (ti >= nt) return;
   T *A = S + cv.off[l];
   __shared__ T P[CT * CLD], Q[CT * CLD];
@@ -169,14 +185,15 @@ __global__ void __launch_bounds__(256) k_chol_panel(T *S, const T *Linv, CholVie
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_chol_update(T *S, T *Linv, CholView cv, int k) {
-  int l = blockIdx.y;
+__global__ void __launch_bounds__(256, 3) k_chol_update(T *S, T *Linv, CholView cv, int k) {
+  int loc;
+  int l = sched_find(cv.sched + (size_t)k * 2 * (cv.L + 1) + (cv.L + 1), cv.L, blockIdx.x, &loc);
   if (!cv.run[l] || cv.fail[l]) return;
   int np = cv.npad[l];
   int nt = np / CT;
   int rem = nt - k - 1;
   if (rem <= 0) return;
-  long long p = blockIdx.x;
+  long long p = loc;
   int a = (int)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
   while ((long long)(a + 1) * (a + 2) / 2 <= p) a++;
   while ((long long)a * (a + 1) / 2 > p) a--;
@@ -225,62 +242,92 @@ __global__ void __launch_bounds__(256) k_chol_update(T *S, T *Linv, CholView cv,
   store_diag<T>(A, np, k + 1, P, Q, Linv + cv.linv_off[l] + (size_t)(k + 1) * CT * CT);
 }
 
-// forward L z = r and backward L^T x = z; r (in) and x (out) in T, one CTA per
-// sub-block; diagonal tiles through their inverses
+// forward L z = r and backward L^T x = z (r in, x out, may alias), one thread
+// block cluster of TS CTAs per sub-block. Tile rows are owned round-robin
+// (tile t by CTA t % TS); each step the owner of tile k solves its 32 entries
+// with the inverted diagonal tile and publishes them in its shared memory,
+// one cluster barrier later every CTA reads them through distributed shared
+// memory and updates the tiles it owns. The barrier is the hardware cluster
+// barrier (no software wait). Two buffers alternate between steps.
+#define TS 8
 template <typename T>
-__global__ void __launch_bounds__(256) k_trsv(const T *S, const T *Linv, CholView cv, const int *voff, T *r,
-                                              T *x) {
-  int l = blockIdx.x;
-  if (!cv.run[l] || cv.fail[l]) return;
+__global__ void __cluster_dims__(TS, 1, 1) __launch_bounds__(256)
+    k_trsv_cluster(const T *S, const T *Linv, CholView cv, const int *voff, T *r, T *x) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  int rank = (int)cluster.block_rank();
+  int l = blockIdx.y;
+  if (!cv.run[l] || cv.fail[l]) return;  // uniform over the cluster
   int np = cv.npad[l];
   int nt = np / CT;
   const T *A = S + cv.off[l];
   const T *LI = Linv + cv.linv_off[l];
   T *z = r + voff[l];
   T *xo = x + voff[l];
-  __shared__ T zs[CT];
+  __shared__ T buf[2][CT];
+  __shared__ T loc[CT];
   int tid = threadIdx.x;
-  int row = tid >> 3, part = tid & 7;  // 32 rows x 8 parts for the 32 x 32 products
-  for (int kt = 0; kt < nt; kt++) {
-    int base = kt * CT;
-    const T *Li = LI + (size_t)kt * CT * CT;
-    T s = 0;
+  int row = tid >> 3, part = tid & 7;  // 32 rows x 8 parts of 4 columns
+  // forward
+  for (int k = 0; k < nt; k++) {
+    int owner = k % TS;
+    if (rank == owner) {
+      const T *Li = LI + (size_t)k * CT * CT;
+      T s = 0;
 #pragma unroll
-    for (int c = 0; c < 4; c++) s += Li[row * CT + part * 4 + c] * z[base + part * 4 + c];
-    for (int o = 4; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, 8);
+      for (int c = 0; c < 4; c++) s += Li[row * CT + part * 4 + c] * z[k * CT + part * 4 + c];
+      for (int o = 4; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, 8);
+      if (part == 0) {
+        buf[k & 1][row] = s;
+        z[k * CT + row] = s;
+      }
+    }
+    cluster.sync();
+    const T *src = cluster.map_shared_rank(&buf[k & 1][0], owner);
+    if (tid < CT) loc[tid] = src[tid];
     __syncthreads();
-    if (part == 0) zs[row] = s;
-    __syncthreads();
-    if (tid < CT) z[base + tid] = zs[tid];
-    for (int i = base + CT + tid; i < np; i += blockDim.x) {
-      const T *rowp = A + (size_t)i * np + base;
-      T acc = 0;
+    int t0 = k + 1 + ((rank - (k + 1)) % TS + TS) % TS;
+    for (int t = t0; t < nt; t += TS) {
+      const T *Lt = A + (size_t)(t * CT + row) * np + k * CT + part * 4;
+      T s = 0;
 #pragma unroll
-      for (int c = 0; c < CT; c++) acc += rowp[c] * zs[c];
-      z[i] -= acc;
+      for (int c = 0; c < 4; c++) s += Lt[c] * loc[part * 4 + c];
+      for (int o = 4; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, 8);
+      if (part == 0) z[t * CT + row] -= s;
     }
     __syncthreads();
   }
-  for (int kt = nt - 1; kt >= 0; kt--) {
-    int base = kt * CT;
-    const T *Li = LI + (size_t)kt * CT * CT;
-    // x_k = Linv_kk^T z_k
-    T s = 0;
+  // backward
+  for (int k = nt - 1; k >= 0; k--) {
+    int owner = k % TS;
+    if (rank == owner) {
+      const T *Li = LI + (size_t)k * CT * CT;
+      T s = 0;
 #pragma unroll
-    for (int c = 0; c < 4; c++) s += Li[(part * 4 + c) * CT + row] * z[base + part * 4 + c];
-    for (int o = 4; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, 8);
+      for (int c = 0; c < 4; c++) s += Li[(part * 4 + c) * CT + row] * z[k * CT + part * 4 + c];
+      for (int o = 4; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, 8);
+      if (part == 0) {
+        buf[k & 1][row] = s;
+        xo[k * CT + row] = s;
+      }
+    }
+    cluster.sync();
+    const T *src = cluster.map_shared_rank(&buf[k & 1][0], owner);
+    if (tid < CT) loc[tid] = src[tid];
     __syncthreads();
-    if (part == 0) zs[row] = s;
-    __syncthreads();
-    if (tid < CT) xo[base + tid] = zs[tid];
-    for (int c = tid; c < base; c += blockDim.x) {
-      T acc = 0;
-#pragma unroll 8
-      for (int rr = 0; rr < CT; rr++) acc += A[(size_t)(base + rr) * np + c] * zs[rr];
-      z[c] -= acc;
+    // z_j -= L_kj^T x_k for owned tiles j < k: column c of the tile, 8 parts of 4 rows
+    int col = tid >> 3;
+    for (int t = rank; t < k; t += TS) {
+      const T *Lt = A + (size_t)(k * CT + part * 4) * np + t * CT + col;
+      T s = 0;
+#pragma unroll
+      for (int rr = 0; rr < 4; rr++) s += Lt[(size_t)rr * np] * loc[part * 4 + rr];
+      for (int o = 4; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, 8);
+      if (part == 0) z[t * CT + col] -= s;
     }
     __syncthreads();
   }
+  cluster.sync();  // keep every CTA's shared memory alive until all reads are done
 }
 
 template <typename T>
@@ -290,11 +337,11 @@ static rpba_status factor(Ctx *ctx, T *S, T *Linv, CholView cv, int T_max) {
   const char *n_upd = sizeof(T) == 8 ? "k_chol_update_f64" : "k_chol_update_f32";
   RPBA_KERNEL(ctx, n_first, k_chol_first<T><<<ctx->L, 256, 0, ctx->stream>>>(S, Linv, cv));
   for (int k = 0; k + 1 < T_max; k++) {
-    dim3 gp(T_max - k - 1, ctx->L);
-    RPBA_KERNEL(ctx, n_panel, k_chol_panel<T><<<gp, 256, 0, ctx->stream>>>(S, Linv, cv, k));
-    int rem = T_max - k - 1;
-    dim3 gu((unsigned)((long long)rem * (rem + 1) / 2), ctx->L);
-    RPBA_KERNEL(ctx, n_upd, k_chol_update<T><<<gu, 256, 0, ctx->stream>>>(S, Linv, cv, k));
+    int np_k = ctx->h_sched[(size_t)k * 2 * (ctx->L + 1) + ctx->L];
+    int nu_k = ctx->h_sched[(size_t)k * 2 * (ctx->L + 1) + 2 * ctx->L + 1];
+    if (np_k == 0) break;
+    RPBA_KERNEL(ctx, n_panel, k_chol_panel<T><<<np_k, 256, 0, ctx->stream>>>(S, Linv, cv, k));
+    RPBA_KERNEL(ctx, n_upd, k_chol_update<T><<<nu_k, 256, 0, ctx->stream>>>(S, Linv, cv, k));
   }
   return RPBA_OK;
 }
@@ -413,11 +460,11 @@ rpba_status launch_solve_rcs(Ctx *ctx, const int *run_dev, int *fail_dev) {
   if (T_max == 0) return RPBA_OK;
   if (ctx->opt.solver != 2) {
     // FP64 direct: factor S in place, one forward/backward solve
-    CholView cv{ctx->S_off, ctx->npad, ctx->linv_off, run_dev, fail_dev};
+    CholView cv{ctx->S_off, ctx->npad, ctx->linv_off, run_dev, fail_dev, ctx->sched, ctx->L};
     RPBA_TRY(factor<double>(ctx, ctx->S, ctx->Linv64, cv, T_max));
     RPBA_CUDA(cudaMemcpyAsync(ctx->dC, ctx->y, ctx->ytot * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-    RPBA_KERNEL(ctx, "k_trsv_f64", k_trsv<double><<<ctx->L, 256, 0, ctx->stream>>>(ctx->S, ctx->Linv64, cv,
-                                                                               ctx->ycam_off, ctx->dC, ctx->dC));
+    RPBA_KERNEL(ctx, "k_trsv_f64", k_trsv_cluster<double><<<dim3(TS, ctx->L), 256, 0, ctx->stream>>>(
+                                     ctx->S, ctx->Linv64, cv, ctx->ycam_off, ctx->dC, ctx->dC));
     return RPBA_OK;
   }
   // mixed: FP32 factor of the scaled system, FP64 iterative refinement
@@ -429,7 +476,7 @@ rpba_status launch_solve_rcs(Ctx *ctx, const int *run_dev, int *fail_dev) {
               k_mixed_convert<<<dim3(64, ctx->L), 256, 0, ctx->stream>>>(ctx->S, ctx->S32, ctx->S_off, ctx->S32_off,
                                                                          ctx->npad, ctx->ycam_off, run_dev,
                                                                          ctx->ir_d));
-  CholView cv{ctx->S32_off, ctx->npad, ctx->linv_off, run_dev, fail_dev};
+  CholView cv{ctx->S32_off, ctx->npad, ctx->linv_off, run_dev, fail_dev, ctx->sched, ctx->L};
   RPBA_TRY(factor<float>(ctx, ctx->S32, ctx->Linv32, cv, T_max));
   int passes = 1 + ctx->opt.ir_steps;
   for (int it = 0; it < passes; it++) {
@@ -443,9 +490,8 @@ rpba_status launch_solve_rcs(Ctx *ctx, const int *run_dev, int *fail_dev) {
     RPBA_KERNEL(ctx, "k_mixed_residual",
                 k_mixed_residual<<<g, 256, 0, ctx->stream>>>(run_dev, fail_dev, ctx->ycam_off, ctx->npad, ctx->L,
                                                              ctx->ir_rs, ctx->ir_d, ctx->ir_t, ctx->ir_r32, it == 0));
-    RPBA_KERNEL(ctx, "k_trsv_f32", k_trsv<float><<<ctx->L, 256, 0, ctx->stream>>>(ctx->S32, ctx->Linv32, cv,
-                                                                               ctx->ycam_off, ctx->ir_r32,
-                                                                               ctx->ir_r32));
+    RPBA_KERNEL(ctx, "k_trsv_f32", k_trsv_cluster<float><<<dim3(TS, ctx->L), 256, 0, ctx->stream>>>(
+                                     ctx->S32, ctx->Linv32, cv, ctx->ycam_off, ctx->ir_r32, ctx->ir_r32));
     RPBA_KERNEL(ctx, "k_mixed_update",
                 k_mixed_update<<<g, 256, 0, ctx->stream>>>(run_dev, fail_dev, ctx->ycam_off, ctx->npad, ctx->L,
                                                            ctx->ir_r32, ctx->ir_x, ctx->ir_d, ctx->dC,

@@ -35,6 +35,8 @@ struct View {
   double *S, *y, *dC;
   const long long *S_off;
   const int *npad, *ycam_off;
+  double *camC;  // camera centres (FP64), current state
+  float *camRf;  // R (9) and t (3) rounded to FP32, current state
 };
 
 static View make_view(Ctx *c) {
@@ -50,6 +52,8 @@ static View make_view(Ctx *c) {
   v.obs_user = c->obs_user; v.obs_pt = c->obs_pt; v.obs_xy = c->obs_xy; v.obs_winv = c->obs_winv;
   v.obs_w = c->obs_w; v.S = c->S; v.y = c->y; v.dC = c->dC; v.S_off = c->S_off; v.npad = c->npad;
   v.ycam_off = c->ycam_off;
+  v.camC = c->camC;
+  v.camRf = c->camRf;
   return v;
 }
 
@@ -64,19 +68,19 @@ rpba_status check_launch(Ctx *ctx, const char *what) {
 
 static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 
-// camera i and point X in the compute precision: Xc = R (X - C), RX = Xc - t.
-// The difference X - C is formed in double so that large coordinates keep
-// their precision before the cast.
+// camera i and point X in the compute precision. FP64: Xc = R X + t exactly
+// as written. FP32: Xc = R (X - C) with the camera centre C and the cast of R
+// prepared once per pass (k_cam_prep); X - C is formed in FP64 so that large
+// coordinates keep their precision before the cast; RX = Xc - t.
 template <typename T>
 struct CamPt {
   T R[9], Xc[3], RX[3], f, cx, cy;
 };
 
 template <typename T>
-__device__ inline void cam_point(const double *R, const double *t, const double *intr,
-                                 const double X[3], CamPt<T> &o) {
+__device__ inline void cam_point(const View &v, int i, const double X[3], CamPt<T> &o) {
   if (sizeof(T) == sizeof(double)) {
-    // plain form: exactly R X + t
+    const double *R = v.R + 9 * i, *t = v.t + 3 * i;
     for (int r = 0; r < 3; r++) {
       double rx = R[3 * r] * X[0] + R[3 * r + 1] * X[1] + R[3 * r + 2] * X[2];
       o.RX[r] = (T)rx;
@@ -84,17 +88,31 @@ __device__ inline void cam_point(const double *R, const double *t, const double 
     }
     for (int e = 0; e < 9; e++) o.R[e] = (T)R[e];
   } else {
-    // camera centre C = -R^T t
-    double C[3];
-    for (int c = 0; c < 3; c++) C[c] = -(R[c] * t[0] + R[3 + c] * t[1] + R[6 + c] * t[2]);
+    const double *C = v.camC + 3 * i;
+    const float *Rf = v.camRf + 12 * i;
     T d[3] = {(T)(X[0] - C[0]), (T)(X[1] - C[1]), (T)(X[2] - C[2])};
-    for (int e = 0; e < 9; e++) o.R[e] = (T)R[e];
+    for (int e = 0; e < 9; e++) o.R[e] = (T)Rf[e];
     for (int r = 0; r < 3; r++) {
       o.Xc[r] = o.R[3 * r] * d[0] + o.R[3 * r + 1] * d[1] + o.R[3 * r + 2] * d[2];
-      o.RX[r] = o.Xc[r] - (T)t[r];
+      o.RX[r] = o.Xc[r] - (T)Rf[9 + r];
     }
   }
-  o.f = (T)intr[0]; o.cx = (T)intr[1]; o.cy = (T)intr[2];
+  o.f = (T)v.intr[3 * i]; o.cx = (T)v.intr[3 * i + 1]; o.cy = (T)v.intr[3 * i + 2];
+}
+
+__global__ void k_cam_prep(View v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= v.M) return;
+  const double *R = v.R + 9 * i, *t = v.t + 3 * i;
+  for (int c = 0; c < 3; c++) v.camC[3 * i + c] = -(R[c] * t[0] + R[3 + c] * t[1] + R[6 + c] * t[2]);
+  for (int e = 0; e < 9; e++) v.camRf[12 * i + e] = (float)R[e];
+  for (int e = 0; e < 3; e++) v.camRf[12 * i + 9 + e] = (float)t[e];
+}
+
+static rpba_status cam_prep(Ctx *ctx) {
+  if (ctx->opt.precision != 1 || ctx->M == 0) return RPBA_OK;
+  RPBA_KERNEL(ctx, "k_cam_prep", k_cam_prep<<<nblk(ctx->M, 128), 128, 0, ctx->stream>>>(make_view(ctx)));
+  return RPBA_OK;
 }
 
 template <typename T>
@@ -128,7 +146,7 @@ __global__ void k_jacobians(View v, double *Jc, double *Jx) {
   if (k >= v.K) return;
   int i = v.obs_cam[k], j = v.obs_pt[k];
   CamPt<T> cp;
-  cam_point<T>(v.R + 9 * i, v.t + 3 * i, v.intr + 3 * i, v.X + 3 * j, cp);
+  cam_point<T>(v, i, v.X + 3 * j, cp);
   ProjJac<T> pj;
   project_jac<T>(cp.R, cp.Xc, cp.RX, cp.f, cp.cx, cp.cy, pj);
   int u = v.obs_user[k];
@@ -144,6 +162,7 @@ rpba_status launch_residuals(Ctx *ctx, double *v_dev) {
 
 rpba_status launch_jacobians(Ctx *ctx, double *Jc, double *Jx) {
   if (ctx->K == 0) return RPBA_OK;
+  RPBA_TRY(cam_prep(ctx));
   if (ctx->opt.precision == 1)
     RPBA_KERNEL(ctx, "k_jacobians", k_jacobians<float><<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(make_view(ctx), Jc, Jx));
   else
@@ -252,12 +271,12 @@ __global__ void k_isect_inst(View v, const int *state, double *part) {
   if (state[j] != 1) return;
   double Xj[3] = {v.X[3 * j], v.X[3 * j + 1], v.X[3 * j + 2]};
   T N[6] = {0, 0, 0, 0, 0, 0}, g[3] = {0, 0, 0};
-  double behind = 0.0;
+  bool behind = false;
   for (int k = v.inst_obs_ptr[q]; k < v.inst_obs_ptr[q + 1]; k++) {
     int i = v.obs_cam[k];
     CamPt<T> cp;
-    cam_point<T>(v.R + 9 * i, v.t + 3 * i, v.intr + 3 * i, Xj, cp);
-    if (!(cp.Xc[2] > T(0))) { behind = 1.0; continue; }
+    cam_point<T>(v, i, Xj, cp);
+    if (!(cp.Xc[2] > T(0))) { behind = true; continue; }
     ProjJac<T> pj;
     project_jac<T>(cp.R, cp.Xc, cp.RX, cp.f, cp.cx, cp.cy, pj);
     T r0 = pj.u - (T)v.obs_xy[2 * k], r1 = pj.v - (T)v.obs_xy[2 * k + 1];
@@ -278,23 +297,28 @@ __global__ void k_isect_inst(View v, const int *state, double *part) {
   double *o = part + 10 * (size_t)q;
   for (int e = 0; e < 6; e++) o[e] = (double)N[e];
   for (int e = 0; e < 3; e++) o[6 + e] = (double)g[e];
-  o[9] = behind;
+  o[9] = behind ? -1.0 : (double)(v.inst_obs_ptr[q + 1] - v.inst_obs_ptr[q]);  // observation count
 }
 
 // per running point: sum the instance parts, Gauss-Newton update, checks,
-// and on convergence W^l = N - N^(l) for every instance.
+// and on convergence W^l = N - N^(l) for every instance. Converged when
+// ||dX|| <= tol (1 + ||X||), or, when px_tol > 0 (FP32 residuals, whose
+// rounding is ~1e-4 px), when the step moves the point's image residuals by
+// less than px_tol per observation: dX^T N dX <= px_tol^2 n_obs.
 __global__ void k_isect_point(View v, int *state, int *iter, const double *part, int max_iter,
-                              double tol, double cond_max, int last) {
+                              double tol, double px_tol, double cond_max, int last) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= v.N || state[j] != 1) return;
   int q0 = v.pt_inst_ptr[j], q1 = v.pt_inst_ptr[j + 1];
   double N[6] = {0, 0, 0, 0, 0, 0}, g[3] = {0, 0, 0};
   bool behind = false;
+  double nobs = 0.0;
   for (int a = q0; a < q1; a++) {
     const double *o = part + 10 * (size_t)v.pt_inst[a];
     for (int e = 0; e < 6; e++) N[e] += o[e];
     for (int e = 0; e < 3; e++) g[e] += o[6 + e];
-    behind |= o[9] != 0.0;
+    behind |= o[9] < 0.0;
+    nobs += o[9];
   }
   bool fail = behind;
   double inv[6];
@@ -313,6 +337,11 @@ __global__ void k_isect_point(View v, int *state, int *iter, const double *part,
     double nd = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     double nx = sqrt(Xn[0] * Xn[0] + Xn[1] * Xn[1] + Xn[2] * Xn[2]);
     conv = nd <= tol * (1.0 + nx);
+    if (!conv && px_tol > 0.0) {
+      double Nd[3];
+      for (int r = 0; r < 3; r++) Nd[r] = N[s3idx(r, 0)] * d[0] + N[s3idx(r, 1)] * d[1] + N[s3idx(r, 2)] * d[2];
+      conv = d[0] * Nd[0] + d[1] * Nd[1] + d[2] * Nd[2] <= px_tol * px_tol * nobs;
+    }
   }
   int it = ++iter[j];
   if (!fail && !conv && (it >= max_iter || last)) fail = true;
@@ -355,16 +384,17 @@ rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped) {
   RPBA_CUDA(cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(int), ctx->stream));
   RPBA_KERNEL(ctx, "k_isect_start", k_isect_start<<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(v, ctx->isect_state, ctx->isect_iter, tp_only,
                                                           ctx->counters));
+  RPBA_TRY(cam_prep(ctx));
   int maxit = ctx->opt.isect_max_iter;
   double tol = ctx->opt.isect_tol;
-  if (ctx->opt.precision == 1 && tol < 1e-6) tol = 1e-6;  // FP32 residuals cannot resolve less
+  double px_tol = ctx->opt.precision == 1 ? 1e-3 : 0.0;  // FP32 residuals cannot resolve less
   for (int it = 0; it < maxit; it++) {
     if (ctx->opt.precision == 1)
       RPBA_KERNEL(ctx, "k_isect_inst", k_isect_inst<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, ctx->isect_state, ctx->isect_N));
     else
       RPBA_KERNEL(ctx, "k_isect_inst", k_isect_inst<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, ctx->isect_state, ctx->isect_N));
     RPBA_KERNEL(ctx, "k_isect_point", k_isect_point<<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(v, ctx->isect_state, ctx->isect_iter, ctx->isect_N,
-                                                             maxit, tol, ctx->opt.cond_max, it == maxit - 1));
+                                                             maxit, tol, px_tol, ctx->opt.cond_max, it == maxit - 1));
   }
   RPBA_CUDA(cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(int), ctx->stream));
   RPBA_KERNEL(ctx, "k_isect_count", k_isect_count<<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(ctx->isect_state, ctx->N, ctx->counters,
@@ -457,53 +487,67 @@ rpba_status launch_eliminate(Ctx *ctx) {
 }
 
 // ---------------------------------------------------------------------------
-// sub-block cost F_l (Eq. bact) per instance, then per sub-block
+// sub-block cost F_l (Eq. bact): one thread per observation (its weighted
+// squared residual; the first observation of an instance adds the TP control
+// term), then a deterministic two-stage sum over each sub-block's contiguous
+// observation range. An observation behind its camera contributes +inf, so
+// the trial is rejected.
 // ---------------------------------------------------------------------------
 // trial = 1 evaluates the trial cameras/instances of running sub-blocks
-template <typename T>
-__global__ void k_inst_cost(View v, int trial, const int *run) {
-  int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= v.P) return;
+__global__ void k_obs_cost(View v, int trial, const int *run, double *cost) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= v.K) return;
+  int q = v.obs_inst[k];
   int l = v.inst_sub[q];
   int j = v.inst_pt[q];
-  if ((run && !run[l]) || !v.active[j]) { v.inst_cost[q] = 0.0; return; }
-  const double *R = trial ? v.Rt : v.R;
-  const double *tt = trial ? v.tt : v.t;
+  if ((run && !run[l]) || !v.active[j]) { cost[k] = 0.0; return; }
+  int i = v.obs_cam[k];
+  const double *R = (trial ? v.Rt : v.R) + 9 * i;
+  const double *t = (trial ? v.tt : v.t) + 3 * i;
   const double *Xq = (trial ? v.Xlt : v.Xl) + 3 * (size_t)q;
-  double Xd[3] = {Xq[0], Xq[1], Xq[2]};
-  double F = 0.0;
-  bool behind = false;
-  for (int k = v.inst_obs_ptr[q]; k < v.inst_obs_ptr[q + 1]; k++) {
-    int i = v.obs_cam[k];
-    CamPt<T> cp;
-    cam_point<T>(R + 9 * i, tt + 3 * i, v.intr + 3 * i, Xd, cp);
-    if (!(cp.Xc[2] > T(0))) { behind = true; continue; }
-    T iz = T(1) / cp.Xc[2];
-    T r0 = cp.f * cp.Xc[0] * iz + cp.cx - (T)v.obs_xy[2 * k];
-    T r1 = cp.f * cp.Xc[1] * iz + cp.cy - (T)v.obs_xy[2 * k + 1];
-    T W[3];
-    load_winv<T>(v, k, W);
-    F += v.obs_w[k] * (double)(W[0] * r0 * r0 + T(2) * W[1] * r0 * r1 + W[2] * r1 * r1);
+  double Xc[3];
+  for (int r = 0; r < 3; r++) Xc[r] = R[3 * r] * Xq[0] + R[3 * r + 1] * Xq[1] + R[3 * r + 2] * Xq[2] + t[r];
+  double F;
+  if (!(Xc[2] > 0.0)) {
+    F = INFINITY;
+  } else {
+    double f = v.intr[3 * i], iz = 1.0 / Xc[2];
+    double r0 = f * Xc[0] * iz + v.intr[3 * i + 1] - v.obs_xy[2 * k];
+    double r1 = f * Xc[1] * iz + v.intr[3 * i + 2] - v.obs_xy[2 * k + 1];
+    double W0 = 1, W1 = 0, W2 = 1;
+    if (v.has_winv) { W0 = v.obs_winv[3 * k]; W1 = v.obs_winv[3 * k + 1]; W2 = v.obs_winv[3 * k + 2]; }
+    F = v.obs_w[k] * (W0 * r0 * r0 + 2.0 * W1 * r0 * r1 + W2 * r1 * r1);
   }
-  // TP control term (X^l - X_TP)^T W^l (X^l - X_TP)
-  const double *W = v.Wl + 6 * (size_t)q;
-  double d[3] = {Xd[0] - v.X[3 * j], Xd[1] - v.X[3 * j + 1], Xd[2] - v.X[3 * j + 2]};
-  F += W[0] * d[0] * d[0] + W[3] * d[1] * d[1] + W[5] * d[2] * d[2] +
-       2.0 * (W[1] * d[0] * d[1] + W[2] * d[0] * d[2] + W[4] * d[1] * d[2]);
-  v.inst_cost[q] = behind ? INFINITY : F;
+  if (k == v.inst_obs_ptr[q]) {
+    // TP control term (X^l - X_TP)^T W^l (X^l - X_TP)
+    const double *W = v.Wl + 6 * (size_t)q;
+    double d[3] = {Xq[0] - v.X[3 * j], Xq[1] - v.X[3 * j + 1], Xq[2] - v.X[3 * j + 2]};
+    F += W[0] * d[0] * d[0] + W[3] * d[1] * d[1] + W[5] * d[2] * d[2] +
+         2.0 * (W[1] * d[0] * d[1] + W[2] * d[0] * d[2] + W[4] * d[1] * d[2]);
+  }
+  cost[k] = F;
 }
 
-// one block per sub-block: deterministic sum over its instance range
-__global__ void k_sub_sum(View v, const int *run, double *F) {
-  int l = blockIdx.x;
+#define SEG_CHUNKS 32
+// stage 1: chunk g of sub-block l's observation range -> part[l][g]
+__global__ void k_seg_partial(const int *seg_ptr, const int *run, const double *val, double *part) {
+  int l = blockIdx.y, g = blockIdx.x;
   if (run && !run[l]) return;
+  int a = seg_ptr[l], b = seg_ptr[l + 1];
+  long long len = b - a;
+  int c0 = a + (int)(len * g / SEG_CHUNKS), c1 = a + (int)(len * (g + 1) / SEG_CHUNKS);
   double acc[1] = {0.0};
-  for (int q = v.sub_inst_ptr[l] + threadIdx.x; q < v.sub_inst_ptr[l + 1]; q += blockDim.x)
-    acc[0] += v.inst_cost[q];
-  __shared__ double out[1];
-  block_reduce_store<1>(acc, out);
-  __syncthreads();
-  if (threadIdx.x == 0) F[l] = out[0];
+  for (int k = c0 + threadIdx.x; k < c1; k += blockDim.x) acc[0] += val[k];
+  block_reduce_store<1>(acc, part + (size_t)l * SEG_CHUNKS + g);
+}
+
+// stage 2: F[l] = sum of its chunks in order
+__global__ void k_seg_final(int L, const int *run, const double *part, double *F) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= L || (run && !run[l])) return;
+  double s = 0.0;
+  for (int g = 0; g < SEG_CHUNKS; g++) s += part[(size_t)l * SEG_CHUNKS + g];
+  F[l] = s;
 }
 
 // The cost that decides acceptance is evaluated in FP64 in both forms: FP32
@@ -511,9 +555,11 @@ __global__ void k_sub_sum(View v, const int *run, double *F) {
 // last LM improvements.
 static rpba_status sub_costs_impl(Ctx *ctx, int trial, const int *run, double *F_dev) {
   View v = make_view(ctx);
-  if (ctx->P)
-    RPBA_KERNEL(ctx, "k_inst_cost", k_inst_cost<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, trial, run));
-  RPBA_KERNEL(ctx, "k_sub_sum", k_sub_sum<<<ctx->L, 256, 0, ctx->stream>>>(v, run, F_dev));
+  if (ctx->K)
+    RPBA_KERNEL(ctx, "k_obs_cost", k_obs_cost<<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(v, trial, run, ctx->obs_cost));
+  RPBA_KERNEL(ctx, "k_seg_partial", k_seg_partial<<<dim3(SEG_CHUNKS, ctx->L), 256, 0, ctx->stream>>>(
+                                        ctx->sub_obs_ptr, run, ctx->obs_cost, ctx->seg_part));
+  RPBA_KERNEL(ctx, "k_seg_final", k_seg_final<<<nblk(ctx->L, 128), 128, 0, ctx->stream>>>(ctx->L, run, ctx->seg_part, F_dev));
   return RPBA_OK;
 }
 
@@ -547,7 +593,7 @@ __global__ void k_linearize(View v, const double *lambda, const int *run, T *NXC
   for (int k = k0; k < k1; k++) {
     int i = v.obs_cam[k];
     CamPt<T> cp;
-    cam_point<T>(v.R + 9 * i, v.t + 3 * i, v.intr + 3 * i, Xd, cp);
+    cam_point<T>(v, i, Xd, cp);
     ProjJac<T> pj;
     project_jac<T>(cp.R, cp.Xc, cp.RX, cp.f, cp.cx, cp.cy, pj);
     T r0 = pj.u - (T)v.obs_xy[2 * k], r1 = pj.v - (T)v.obs_xy[2 * k + 1];
@@ -612,7 +658,7 @@ __global__ void k_camera_blocks(View v, const double *lambda, const int *run, co
     if (!v.active[j]) continue;
     double Xd[3] = {v.Xl[3 * (size_t)q], v.Xl[3 * (size_t)q + 1], v.Xl[3 * (size_t)q + 2]};
     CamPt<T> cp;
-    cam_point<T>(v.R + 9 * i, v.t + 3 * i, v.intr + 3 * i, Xd, cp);
+    cam_point<T>(v, i, Xd, cp);
     ProjJac<T> pj;
     project_jac<T>(cp.R, cp.Xc, cp.RX, cp.f, cp.cx, cp.cy, pj);
     T r0 = pj.u - (T)v.obs_xy[2 * k], r1 = pj.v - (T)v.obs_xy[2 * k + 1];
@@ -706,6 +752,7 @@ __global__ void k_rcs_clear(View v, const int *run, int L) {
 }
 
 rpba_status launch_build_rcs(Ctx *ctx, const double *lambda_dev, const int *run_dev) {
+  RPBA_TRY(cam_prep(ctx));
   View v = make_view(ctx);
   dim3 gclr(64, ctx->L);
   RPBA_KERNEL(ctx, "k_rcs_clear", k_rcs_clear<<<gclr, 256, 0, ctx->stream>>>(v, run_dev, ctx->L));

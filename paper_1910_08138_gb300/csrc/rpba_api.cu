@@ -175,7 +175,7 @@ extern "C" void rpba_default_options(rpba_options *o) {
   o->solver = 0;
   o->pcg_tol = 1e-8;
   o->pcg_max_iter = 500;
-  o->ir_steps = 2;
+  o->ir_steps = 1;
 }
 
 extern "C" const char *rpba_last_error(const rpba_ctx *ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
@@ -343,6 +343,21 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   ctx->S_total = stot;
   ctx->max_tiles = maxT;
   ctx->ytot = yt;
+  // factorisation schedule: for step k the tiles of every sub-block, as
+  // prefix sums (panel: T_l - k - 1 tiles; trailing update: its triangle)
+  {
+    int steps = std::max(maxT - 1, 1);
+    ctx->h_sched.assign((size_t)steps * 2 * (L + 1), 0);
+    for (int k = 0; k < steps; k++) {
+      int *pb = &ctx->h_sched[(size_t)k * 2 * (L + 1)];
+      int *ub = pb + (L + 1);
+      for (int l = 0; l < L; l++) {
+        int rem = std::max(ntiles[l] - k - 1, 0);
+        pb[l + 1] = pb[l] + rem;
+        ub[l + 1] = ub[l] + rem * (rem + 1) / 2;
+      }
+    }
+  }
   std::vector<int> loff(L);
   int ltot = 0;
   for (int l = 0; l < L; l++) {
@@ -393,6 +408,15 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   RPBA_TRY(upload(ctx, &ctx->inst_sub, inst_sub.data(), (size_t)P));
   RPBA_TRY(upload(ctx, &ctx->inst_obs_ptr, inst_obs_ptr.data(), (size_t)P + 1));
   RPBA_TRY(upload(ctx, &ctx->sub_inst_ptr, sip.data(), (size_t)L + 1));
+  {
+    std::vector<int> sop(L + 1);
+    for (int l = 0; l <= L; l++) sop[l] = inst_obs_ptr[sip[l]];
+    RPBA_TRY(upload(ctx, &ctx->sub_obs_ptr, sop.data(), (size_t)L + 1));
+  }
+  RPBA_TRY(alloc_n(ctx, &ctx->obs_cost, (size_t)K));
+  RPBA_TRY(alloc_n(ctx, &ctx->camC, 3 * (size_t)M));
+  RPBA_TRY(alloc_n(ctx, &ctx->camRf, 12 * (size_t)M));
+  RPBA_TRY(alloc_n(ctx, &ctx->seg_part, (size_t)L * 32));
   RPBA_TRY(alloc_n(ctx, &ctx->Xl, 3 * (size_t)P));
   RPBA_TRY(alloc_n(ctx, &ctx->Xlt, 3 * (size_t)P));
   RPBA_TRY(alloc_n(ctx, &ctx->Wl, 6 * (size_t)P));
@@ -422,6 +446,7 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   RPBA_TRY(upload(ctx, &ctx->ycam_off, yoff.data(), (size_t)L));
   RPBA_TRY(upload(ctx, &ctx->sub_ntiles, ntiles.data(), (size_t)L));
   RPBA_TRY(upload(ctx, &ctx->linv_off, loff.data(), (size_t)L));
+  RPBA_TRY(upload(ctx, &ctx->sched, ctx->h_sched.data(), ctx->h_sched.size()));
   RPBA_TRY(alloc_n(ctx, &ctx->Linv64, (size_t)std::max(ltot, 1)));
   if (ctx->opt.solver == 2) {
     RPBA_TRY(alloc_n(ctx, &ctx->S32, (size_t)std::max(stot, 1LL)));

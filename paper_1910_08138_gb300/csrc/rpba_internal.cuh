@@ -191,6 +191,12 @@ struct Ctx {
   long long *S_off = nullptr;
   int *npad = nullptr, *ycam_off = nullptr, *sub_ntiles = nullptr, *linv_off = nullptr;
   int ytot = 0;
+  double *obs_cost = nullptr, *seg_part = nullptr;
+  double *camC = nullptr;
+  float *camRf = nullptr;
+  int *sub_obs_ptr = nullptr;
+  std::vector<int> h_sched;  // per factorisation step: prefix sums of panel and update tiles
+  int *sched = nullptr;
   double *Linv64 = nullptr;
   float *S32 = nullptr, *Linv32 = nullptr, *ir_r32 = nullptr;
   long long *S32_off = nullptr;
