@@ -1,8 +1,10 @@
 // kernels_mad.cu -- per-camera robust scale (Sec. 5.3): 1.4826 times the
 // median absolute deviation of the whitened residual components of every
 // observation of the camera. One CTA per camera; the 2 K_i components are
-// sorted in shared memory (bitonic network, padded to a power of two with
-// +inf), the median is read off, the absolute deviations are sorted again.
+// sorted in shared memory (bitonic network, padded to a power of two), the
+// median is read off, the absolute deviations are sorted again.
+// The FP64 values are sorted as order-preserving 64-bit integer keys: on this
+// GPU FP64 compares run on the slow FP64 pipe, integer compares do not.
 #include <cuda_runtime.h>
 #include <float.h>
 
@@ -10,14 +12,24 @@
 
 namespace rpba {
 
-__device__ static void bitonic_sort(double *a, int n2) {
+// IEEE-754 double -> unsigned key with the same order (and back)
+__device__ inline unsigned long long dkey(double x) {
+  unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ inline double dval(unsigned long long k) {
+  unsigned long long u = (k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k;
+  return __longlong_as_double((long long)u);
+}
+
+__device__ static void bitonic_sort(unsigned long long *a, int n2) {
   for (int size = 2; size <= n2; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
       for (int idx = threadIdx.x; idx < (n2 >> 1); idx += blockDim.x) {
         int i = 2 * stride * (idx / stride) + (idx % stride);
         int j = i + stride;
         bool up = (i & size) == 0;
-        double x = a[i], y = a[j];
+        unsigned long long x = a[i], y = a[j];
         if ((x > y) == up) {
           a[i] = y;
           a[j] = x;
@@ -28,14 +40,14 @@ __device__ static void bitonic_sort(double *a, int n2) {
   }
 }
 
-__device__ static double sorted_median(const double *a, int n) {
-  return (n & 1) ? a[n / 2] : 0.5 * (a[n / 2 - 1] + a[n / 2]);
+__device__ static double sorted_median(const unsigned long long *a, int n) {
+  return (n & 1) ? dval(a[n / 2]) : 0.5 * (dval(a[n / 2 - 1]) + dval(a[n / 2]));
 }
 
 __global__ void k_camera_mad(int M, const double *R, const double *t, const double *intr, const double *X,
                              const uint8_t *active, const int *cam_obs_ptr, const int *cam_obs, const int *obs_pt,
                              const double *obs_xy, const double *obs_winv, int has_winv, double *sigma) {
-  extern __shared__ double sh[];
+  extern __shared__ unsigned long long sh[];
   __shared__ int count;
   int i = blockIdx.x;
   if (i >= M) return;
@@ -60,8 +72,8 @@ __global__ void k_camera_mad(int M, const double *R, const double *t, const doub
     double e0 = a * r0 + (W1 / a) * r1;
     double e1 = sqrt(W2 - W1 * W1 / W0) * r1;
     int slot = atomicAdd(&count, 2);
-    sh[slot] = e0;
-    sh[slot + 1] = e1;
+    sh[slot] = dkey(e0);
+    sh[slot + 1] = dkey(e1);
   }
   __syncthreads();
   int n = count;
@@ -71,12 +83,12 @@ __global__ void k_camera_mad(int M, const double *R, const double *t, const doub
   }
   int n2 = 1;
   while (n2 < n) n2 <<= 1;
-  for (int e = n + threadIdx.x; e < n2; e += blockDim.x) sh[e] = DBL_MAX;
+  for (int e = n + threadIdx.x; e < n2; e += blockDim.x) sh[e] = ~0ull;  // sorts last
   __syncthreads();
   bitonic_sort(sh, n2);
   double med = sorted_median(sh, n);
   __syncthreads();
-  for (int e = threadIdx.x; e < n; e += blockDim.x) sh[e] = fabs(sh[e] - med);
+  for (int e = threadIdx.x; e < n; e += blockDim.x) sh[e] = dkey(fabs(dval(sh[e]) - med));
   __syncthreads();
   bitonic_sort(sh, n2);
   if (threadIdx.x == 0) sigma[i] = 1.4826 * sorted_median(sh, n);
@@ -86,7 +98,7 @@ rpba_status launch_camera_scale(Ctx *ctx) {
   if (ctx->M == 0) return RPBA_OK;
   int n2 = 1;
   while (n2 < 2 * ctx->max_cam_obs) n2 <<= 1;
-  size_t smem = (size_t)n2 * sizeof(double);
+  size_t smem = (size_t)n2 * sizeof(unsigned long long);
   if (smem > 200 * 1024) {
     ctx->err = "camera with too many observations for the shared-memory median";
     return RPBA_ERR_INVALID_ARG;

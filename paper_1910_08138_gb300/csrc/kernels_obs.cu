@@ -37,6 +37,14 @@ struct View {
   const int *npad, *ycam_off;
   double *camC;  // camera centres (FP64), current state
   float *camRf;  // R (9) and t (3) rounded to FP32, current state
+  // FP32 form: inputs rounded once, positions as float hi + lo pairs
+  const float *obs_xy32;   // (x - cx, y - cy)
+  const float *obs_winv32;
+  float *obs_w32;
+  float *camChi, *camClo;  // camera centres
+  float *Xl_hi, *Xl_lo;    // sub-block copies X^l
+  float *X_hi, *X_lo;      // points X
+  float *dC32;             // camera updates
 };
 
 static View make_view(Ctx *c) {
@@ -54,6 +62,10 @@ static View make_view(Ctx *c) {
   v.ycam_off = c->ycam_off;
   v.camC = c->camC;
   v.camRf = c->camRf;
+  v.obs_xy32 = c->obs_xy32; v.obs_winv32 = c->obs_winv32; v.obs_w32 = c->obs_w32;
+  v.camChi = c->camChi; v.camClo = c->camClo;
+  v.Xl_hi = c->Xl_hi; v.Xl_lo = c->Xl_lo; v.X_hi = c->X_hi; v.X_lo = c->X_lo;
+  v.dC32 = c->dC32;
   return v;
 }
 
@@ -68,45 +80,73 @@ rpba_status check_launch(Ctx *ctx, const char *what) {
 
 static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 
-// camera i and point X in the compute precision. FP64: Xc = R X + t exactly
-// as written. FP32: Xc = R (X - C) with the camera centre C and the cast of R
-// prepared once per pass (k_cam_prep); X - C is formed in FP64 so that large
-// coordinates keep their precision before the cast; RX = Xc - t.
+// camera i and a point in the compute precision.
+// FP64: Xc = R X + t exactly as written (cam_point_d).
+// FP32 (cam_point_f): Xc = R (X - C) with the camera centre C and the point X
+// both held as float pairs hi + lo (hi = fl(x), lo = fl(x - hi)), so that
+// d = (X_hi - C_hi) + (X_lo - C_lo) keeps large coordinates exact to FP32
+// precision without any FP64 instruction per observation; RX = Xc - t. On
+// this GPU FP64 instructions, conversions included, issue at 1/64 of the
+// FP32 rate, so the FP32 form rounds every input once per pass instead.
 template <typename T>
 struct CamPt {
   T R[9], Xc[3], RX[3], f, cx, cy;
 };
 
-template <typename T>
-__device__ inline void cam_point(const View &v, int i, const double X[3], CamPt<T> &o) {
-  if (sizeof(T) == sizeof(double)) {
-    const double *R = v.R + 9 * i, *t = v.t + 3 * i;
-    for (int r = 0; r < 3; r++) {
-      double rx = R[3 * r] * X[0] + R[3 * r + 1] * X[1] + R[3 * r + 2] * X[2];
-      o.RX[r] = (T)rx;
-      o.Xc[r] = (T)(rx + t[r]);
-    }
-    for (int e = 0; e < 9; e++) o.R[e] = (T)R[e];
-  } else {
-    const double *C = v.camC + 3 * i;
-    const float *Rf = v.camRf + 12 * i;
-    T d[3] = {(T)(X[0] - C[0]), (T)(X[1] - C[1]), (T)(X[2] - C[2])};
-    for (int e = 0; e < 9; e++) o.R[e] = (T)Rf[e];
-    for (int r = 0; r < 3; r++) {
-      o.Xc[r] = o.R[3 * r] * d[0] + o.R[3 * r + 1] * d[1] + o.R[3 * r + 2] * d[2];
-      o.RX[r] = o.Xc[r] - (T)Rf[9 + r];
-    }
+__device__ inline void cam_point_d(const View &v, int i, const double X[3], CamPt<double> &o) {
+  const double *R = v.R + 9 * i, *t = v.t + 3 * i;
+  for (int r = 0; r < 3; r++) {
+    double rx = R[3 * r] * X[0] + R[3 * r + 1] * X[1] + R[3 * r + 2] * X[2];
+    o.RX[r] = rx;
+    o.Xc[r] = rx + t[r];
   }
-  o.f = (T)v.intr[3 * i]; o.cx = (T)v.intr[3 * i + 1]; o.cy = (T)v.intr[3 * i + 2];
+  for (int e = 0; e < 9; e++) o.R[e] = R[e];
+  o.f = v.intr[3 * i]; o.cx = v.intr[3 * i + 1]; o.cy = v.intr[3 * i + 2];
+}
+
+__device__ inline void cam_point_f(const View &v, int i, const float *Xh, const float *Xlw, CamPt<float> &o) {
+  const float *Rf = v.camRf + 16 * i;
+  const float *Ch = v.camChi + 3 * i, *Cl = v.camClo + 3 * i;
+  float d[3];
+  for (int r = 0; r < 3; r++) d[r] = (Xh[r] - Ch[r]) + (Xlw[r] - Cl[r]);
+  for (int e = 0; e < 9; e++) o.R[e] = Rf[e];
+  for (int r = 0; r < 3; r++) {
+    o.Xc[r] = o.R[3 * r] * d[0] + o.R[3 * r + 1] * d[1] + o.R[3 * r + 2] * d[2];
+    o.RX[r] = o.Xc[r] - Rf[9 + r];
+  }
+  o.f = Rf[12]; o.cx = Rf[13]; o.cy = Rf[14];
+}
+
+__device__ inline void split(double x, float &hi, float &lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
 }
 
 __global__ void k_cam_prep(View v) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= v.M) return;
   const double *R = v.R + 9 * i, *t = v.t + 3 * i;
-  for (int c = 0; c < 3; c++) v.camC[3 * i + c] = -(R[c] * t[0] + R[3 + c] * t[1] + R[6 + c] * t[2]);
-  for (int e = 0; e < 9; e++) v.camRf[12 * i + e] = (float)R[e];
-  for (int e = 0; e < 3; e++) v.camRf[12 * i + 9 + e] = (float)t[e];
+  for (int c = 0; c < 3; c++) {
+    double C = -(R[c] * t[0] + R[3 + c] * t[1] + R[6 + c] * t[2]);
+    v.camC[3 * i + c] = C;
+    split(C, v.camChi[3 * i + c], v.camClo[3 * i + c]);
+  }
+  float *o = v.camRf + 16 * i;
+  for (int e = 0; e < 9; e++) o[e] = (float)R[e];
+  for (int e = 0; e < 3; e++) o[9 + e] = (float)t[e];
+  for (int e = 0; e < 3; e++) o[12 + e] = (float)v.intr[3 * i + e];
+  o[15] = 0.f;
+}
+
+// hi/lo pairs of the sub-block copies (which = 0) or of the points (which = 1)
+__global__ void k_split_points(View v, int which) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  int n = which ? v.N : v.P;
+  if (q >= n) return;
+  const double *X = (which ? v.X : v.Xl) + 3 * (size_t)q;
+  float *hi = (which ? v.X_hi : v.Xl_hi) + 3 * (size_t)q;
+  float *lo = (which ? v.X_lo : v.Xl_lo) + 3 * (size_t)q;
+  for (int e = 0; e < 3; e++) split(X[e], hi[e], lo[e]);
 }
 
 static rpba_status cam_prep(Ctx *ctx) {
@@ -115,13 +155,48 @@ static rpba_status cam_prep(Ctx *ctx) {
   return RPBA_OK;
 }
 
+static rpba_status split_points(Ctx *ctx, int which) {
+  int n = which ? ctx->N : ctx->P;
+  if (ctx->opt.precision != 1 || n == 0) return RPBA_OK;
+  RPBA_KERNEL(ctx, "k_split_points", k_split_points<<<nblk(n, 256), 256, 0, ctx->stream>>>(make_view(ctx), which));
+  return RPBA_OK;
+}
+
+// observation k in the compute precision: residual-relevant data
 template <typename T>
-__device__ inline void load_winv(const View &v, int k, T W[3]) {
-  if (v.has_winv) {
-    W[0] = (T)v.obs_winv[3 * k]; W[1] = (T)v.obs_winv[3 * k + 1]; W[2] = (T)v.obs_winv[3 * k + 2];
+struct ObsT {
+  T x, y;    // observation minus principal point
+  T W[3];    // C^-1
+  T w;       // robust weight
+};
+
+template <typename T>
+__device__ inline void load_obs(const View &v, int k, ObsT<T> &o) {
+  if constexpr (sizeof(T) == sizeof(float)) {
+    o.x = v.obs_xy32[2 * k]; o.y = v.obs_xy32[2 * k + 1];
+    if (v.has_winv) { o.W[0] = v.obs_winv32[3 * k]; o.W[1] = v.obs_winv32[3 * k + 1]; o.W[2] = v.obs_winv32[3 * k + 2]; }
+    else { o.W[0] = 1; o.W[1] = 0; o.W[2] = 1; }
+    o.w = v.obs_w32[k];
   } else {
-    W[0] = 1; W[1] = 0; W[2] = 1;
+    int i = v.obs_cam[k];
+    o.x = v.obs_xy[2 * k] - v.intr[3 * i + 1];
+    o.y = v.obs_xy[2 * k + 1] - v.intr[3 * i + 2];
+    if (v.has_winv) { o.W[0] = v.obs_winv[3 * k]; o.W[1] = v.obs_winv[3 * k + 1]; o.W[2] = v.obs_winv[3 * k + 2]; }
+    else { o.W[0] = 1; o.W[1] = 0; o.W[2] = 1; }
+    o.w = v.obs_w[k];
   }
+}
+
+// projection (relative to the principal point) and Jacobians of camera i at
+// a point given in FP64 (Xd) or as FP32 hi/lo pairs (Xh, Xlw)
+template <typename T>
+__device__ inline void obs_proj(const View &v, int i, const double *Xd, const float *Xh, const float *Xlw,
+                                ProjJac<T> &pj, T &z) {
+  CamPt<T> cp;
+  if constexpr (sizeof(T) == sizeof(float)) cam_point_f(v, i, Xh, Xlw, cp);
+  else cam_point_d(v, i, Xd, cp);
+  z = cp.Xc[2];
+  project_jac<T>(cp.R, cp.Xc, cp.RX, cp.f, T(0), T(0), pj);
 }
 
 // ---------------------------------------------------------------------------
@@ -145,10 +220,9 @@ __global__ void k_jacobians(View v, double *Jc, double *Jx) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= v.K) return;
   int i = v.obs_cam[k], j = v.obs_pt[k];
-  CamPt<T> cp;
-  cam_point<T>(v, i, v.X + 3 * j, cp);
   ProjJac<T> pj;
-  project_jac<T>(cp.R, cp.Xc, cp.RX, cp.f, cp.cx, cp.cy, pj);
+  T z;
+  obs_proj<T>(v, i, v.X + 3 * j, v.X_hi + 3 * j, v.X_lo + 3 * j, pj, z);
   int u = v.obs_user[k];
   for (int e = 0; e < 12; e++) Jc[12 * u + e] = (double)pj.Jc[e];
   for (int e = 0; e < 6; e++) Jx[6 * u + e] = (double)pj.Jx[e];
@@ -163,6 +237,7 @@ rpba_status launch_residuals(Ctx *ctx, double *v_dev) {
 rpba_status launch_jacobians(Ctx *ctx, double *Jc, double *Jx) {
   if (ctx->K == 0) return RPBA_OK;
   RPBA_TRY(cam_prep(ctx));
+  RPBA_TRY(split_points(ctx, 1));
   if (ctx->opt.precision == 1)
     RPBA_KERNEL(ctx, "k_jacobians", k_jacobians<float><<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(make_view(ctx), Jc, Jx));
   else
@@ -264,40 +339,37 @@ rpba_status launch_sigma0(Ctx *ctx, double *sigma0, double *rms) {
 // per instance of a running point: partial normal matrix N^(l) (sym3) and
 // gradient g^(l) at the current X_j, cameras fixed. flag bit: behind camera.
 template <typename T>
-__global__ void k_isect_inst(View v, const int *state, double *part) {
+__global__ void k_isect_inst(View v, const int *state, T *part) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= v.P) return;
   int j = v.inst_pt[q];
   if (state[j] != 1) return;
-  double Xj[3] = {v.X[3 * j], v.X[3 * j + 1], v.X[3 * j + 2]};
   T N[6] = {0, 0, 0, 0, 0, 0}, g[3] = {0, 0, 0};
   bool behind = false;
   for (int k = v.inst_obs_ptr[q]; k < v.inst_obs_ptr[q + 1]; k++) {
     int i = v.obs_cam[k];
-    CamPt<T> cp;
-    cam_point<T>(v, i, Xj, cp);
-    if (!(cp.Xc[2] > T(0))) { behind = true; continue; }
     ProjJac<T> pj;
-    project_jac<T>(cp.R, cp.Xc, cp.RX, cp.f, cp.cx, cp.cy, pj);
-    T r0 = pj.u - (T)v.obs_xy[2 * k], r1 = pj.v - (T)v.obs_xy[2 * k + 1];
-    T W[3];
-    load_winv<T>(v, k, W);
-    T w = (T)v.obs_w[k];
-    // WA = w W Jx (2x3)
+    T z;
+    obs_proj<T>(v, i, v.X + 3 * j, v.X_hi + 3 * j, v.X_lo + 3 * j, pj, z);
+    if (!(z > T(0))) { behind = true; continue; }
+    ObsT<T> ob;
+    load_obs<T>(v, k, ob);
+    T r0 = pj.u - ob.x, r1 = pj.v - ob.y;
+    // w W Jx (2x3)
     T a0[3], a1[3];
     for (int c = 0; c < 3; c++) {
-      a0[c] = w * (W[0] * pj.Jx[c] + W[1] * pj.Jx[3 + c]);
-      a1[c] = w * (W[1] * pj.Jx[c] + W[2] * pj.Jx[3 + c]);
+      a0[c] = ob.w * (ob.W[0] * pj.Jx[c] + ob.W[1] * pj.Jx[3 + c]);
+      a1[c] = ob.w * (ob.W[1] * pj.Jx[c] + ob.W[2] * pj.Jx[3 + c]);
     }
     for (int r = 0; r < 3; r++) {
       for (int c = r; c < 3; c++) N[s3idx(r, c)] += pj.Jx[r] * a0[c] + pj.Jx[3 + r] * a1[c];
       g[r] += a0[r] * r0 + a1[r] * r1;
     }
   }
-  double *o = part + 10 * (size_t)q;
-  for (int e = 0; e < 6; e++) o[e] = (double)N[e];
-  for (int e = 0; e < 3; e++) o[6 + e] = (double)g[e];
-  o[9] = behind ? -1.0 : (double)(v.inst_obs_ptr[q + 1] - v.inst_obs_ptr[q]);  // observation count
+  T *o = part + 10 * (size_t)q;
+  for (int e = 0; e < 6; e++) o[e] = N[e];
+  for (int e = 0; e < 3; e++) o[6 + e] = g[e];
+  o[9] = behind ? T(-1) : T(v.inst_obs_ptr[q + 1] - v.inst_obs_ptr[q]);  // observation count
 }
 
 // per running point: sum the instance parts, Gauss-Newton update, checks,
@@ -305,43 +377,60 @@ __global__ void k_isect_inst(View v, const int *state, double *part) {
 // ||dX|| <= tol (1 + ||X||), or, when px_tol > 0 (FP32 residuals, whose
 // rounding is ~1e-4 px), when the step moves the point's image residuals by
 // less than px_tol per observation: dX^T N dX <= px_tol^2 n_obs.
-__global__ void k_isect_point(View v, int *state, int *iter, const double *part, int max_iter,
-                              double tol, double px_tol, double cond_max, int last) {
+// FP32 form: the 3x3 system is solved in FP32, and again in FP64 when its
+// Frobenius condition number exceeds 1e6.
+template <typename T>
+__global__ void k_isect_point(View v, int *state, int *iter, const T *part, int max_iter, double tol,
+                              double px_tol, double cond_max, int last) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= v.N || state[j] != 1) return;
   int q0 = v.pt_inst_ptr[j], q1 = v.pt_inst_ptr[j + 1];
-  double N[6] = {0, 0, 0, 0, 0, 0}, g[3] = {0, 0, 0};
+  T N[6] = {0, 0, 0, 0, 0, 0}, g[3] = {0, 0, 0};
   bool behind = false;
-  double nobs = 0.0;
+  T nobs = 0;
   for (int a = q0; a < q1; a++) {
-    const double *o = part + 10 * (size_t)v.pt_inst[a];
+    const T *o = part + 10 * (size_t)v.pt_inst[a];
     for (int e = 0; e < 6; e++) N[e] += o[e];
     for (int e = 0; e < 3; e++) g[e] += o[6 + e];
-    behind |= o[9] < 0.0;
+    behind |= o[9] < T(0);
     nobs += o[9];
   }
   bool fail = behind;
-  double inv[6];
+  double d[3] = {0, 0, 0};
+  double nd2_img = 0.0;
   if (!fail) {
-    double det = sym3_inv<double>(N, inv);
-    fail = !(det > 0.0) || !(sym3_frob<double>(N) * sym3_frob<double>(inv) <= cond_max);
+    T inv[6];
+    T det = sym3_inv<T>(N, inv);
+    T cond = sym3_frob<T>(N) * sym3_frob<T>(inv);
+    if (sizeof(T) == sizeof(float) && !(cond <= T(1e6))) {
+      double Nd[6], invd[6];
+      for (int e = 0; e < 6; e++) Nd[e] = (double)N[e];
+      double detd = sym3_inv<double>(Nd, invd);
+      fail = !(detd > 0.0) || !(sym3_frob<double>(Nd) * sym3_frob<double>(invd) <= cond_max);
+      for (int r = 0; r < 3; r++)
+        d[r] = invd[s3idx(r, 0)] * (double)g[0] + invd[s3idx(r, 1)] * (double)g[1] + invd[s3idx(r, 2)] * (double)g[2];
+    } else {
+      fail = !(det > T(0)) || !((double)cond <= cond_max);
+      for (int r = 0; r < 3; r++)
+        d[r] = (double)(inv[s3idx(r, 0)] * g[0] + inv[s3idx(r, 1)] * g[1] + inv[s3idx(r, 2)] * g[2]);
+    }
+    if (px_tol > 0.0) {
+      T dt[3] = {(T)d[0], (T)d[1], (T)d[2]}, Nd3[3];
+      for (int r = 0; r < 3; r++) Nd3[r] = N[s3idx(r, 0)] * dt[0] + N[s3idx(r, 1)] * dt[1] + N[s3idx(r, 2)] * dt[2];
+      nd2_img = (double)(dt[0] * Nd3[0] + dt[1] * Nd3[1] + dt[2] * Nd3[2]);
+    }
   }
   bool conv = false;
   if (!fail) {
-    double d[3];
-    for (int r = 0; r < 3; r++)
-      d[r] = inv[s3idx(r, 0)] * g[0] + inv[s3idx(r, 1)] * g[1] + inv[s3idx(r, 2)] * g[2];
     double Xn[3];
     for (int r = 0; r < 3; r++) Xn[r] = v.X[3 * j + r] - d[r];
     for (int r = 0; r < 3; r++) v.X[3 * j + r] = Xn[r];
+    if (sizeof(T) == sizeof(float))
+      for (int r = 0; r < 3; r++) split(Xn[r], v.X_hi[3 * j + r], v.X_lo[3 * j + r]);
     double nd = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     double nx = sqrt(Xn[0] * Xn[0] + Xn[1] * Xn[1] + Xn[2] * Xn[2]);
     conv = nd <= tol * (1.0 + nx);
-    if (!conv && px_tol > 0.0) {
-      double Nd[3];
-      for (int r = 0; r < 3; r++) Nd[r] = N[s3idx(r, 0)] * d[0] + N[s3idx(r, 1)] * d[1] + N[s3idx(r, 2)] * d[2];
-      conv = d[0] * Nd[0] + d[1] * Nd[1] + d[2] * Nd[2] <= px_tol * px_tol * nobs;
-    }
+    if (!conv && px_tol > 0.0) conv = nd2_img <= px_tol * px_tol * (double)nobs;
   }
   int it = ++iter[j];
   if (!fail && !conv && (it >= max_iter || last)) fail = true;
@@ -355,8 +444,8 @@ __global__ void k_isect_point(View v, int *state, int *iter, const double *part,
     bool tp = (q1 - q0) >= 2;
     for (int a = q0; a < q1; a++) {
       int q = v.pt_inst[a];
-      const double *o = part + 10 * (size_t)q;
-      for (int e = 0; e < 6; e++) v.Wl[6 * (size_t)q + e] = tp ? N[e] - o[e] : 0.0;
+      const T *o = part + 10 * (size_t)q;
+      for (int e = 0; e < 6; e++) v.Wl[6 * (size_t)q + e] = tp ? (double)(N[e] - o[e]) : 0.0;
     }
   }
 }
@@ -381,24 +470,33 @@ __global__ void k_isect_count(const int *state, int n, int *running, int *failed
 rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped) {
   View v = make_view(ctx);
   if (ctx->N == 0) { if (n_dropped) *n_dropped = 0; return RPBA_OK; }
-  RPBA_CUDA(cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(int), ctx->stream));
-  RPBA_KERNEL(ctx, "k_isect_start", k_isect_start<<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(v, ctx->isect_state, ctx->isect_iter, tp_only,
-                                                          ctx->counters));
   RPBA_TRY(cam_prep(ctx));
+  RPBA_TRY(split_points(ctx, 1));
+  RPBA_CUDA(cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(int), ctx->stream));
+  RPBA_KERNEL(ctx, "k_isect_start", k_isect_start<<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(
+                                        v, ctx->isect_state, ctx->isect_iter, tp_only, ctx->counters));
   int maxit = ctx->opt.isect_max_iter;
   double tol = ctx->opt.isect_tol;
   double px_tol = ctx->opt.precision == 1 ? 1e-3 : 0.0;  // FP32 residuals cannot resolve less
   for (int it = 0; it < maxit; it++) {
-    if (ctx->opt.precision == 1)
-      RPBA_KERNEL(ctx, "k_isect_inst", k_isect_inst<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, ctx->isect_state, ctx->isect_N));
-    else
-      RPBA_KERNEL(ctx, "k_isect_inst", k_isect_inst<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, ctx->isect_state, ctx->isect_N));
-    RPBA_KERNEL(ctx, "k_isect_point", k_isect_point<<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(v, ctx->isect_state, ctx->isect_iter, ctx->isect_N,
-                                                             maxit, tol, px_tol, ctx->opt.cond_max, it == maxit - 1));
+    if (ctx->opt.precision == 1) {
+      float *part = (float *)ctx->isect_N;
+      RPBA_KERNEL(ctx, "k_isect_inst", k_isect_inst<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(
+                                           v, ctx->isect_state, part));
+      RPBA_KERNEL(ctx, "k_isect_point", k_isect_point<float><<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(
+                                            v, ctx->isect_state, ctx->isect_iter, part, maxit, tol, px_tol,
+                                            ctx->opt.cond_max, it == maxit - 1));
+    } else {
+      RPBA_KERNEL(ctx, "k_isect_inst", k_isect_inst<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(
+                                           v, ctx->isect_state, ctx->isect_N));
+      RPBA_KERNEL(ctx, "k_isect_point", k_isect_point<double><<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(
+                                            v, ctx->isect_state, ctx->isect_iter, ctx->isect_N, maxit, tol, px_tol,
+                                            ctx->opt.cond_max, it == maxit - 1));
+    }
   }
   RPBA_CUDA(cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(int), ctx->stream));
-  RPBA_KERNEL(ctx, "k_isect_count", k_isect_count<<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(ctx->isect_state, ctx->N, ctx->counters,
-                                                          ctx->counters + 1));
+  RPBA_KERNEL(ctx, "k_isect_count", k_isect_count<<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(
+                                        ctx->isect_state, ctx->N, ctx->counters, ctx->counters + 1));
   int h[2];
   RPBA_CUDA(cudaMemcpyAsync(h, ctx->counters, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   RPBA_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -456,6 +554,7 @@ __global__ void k_robust_weights(View v, const double *sigma, double t_v, double
   double s = sigma[i];
   bool out = (s > 0.0) && (nr / s > t_v);
   v.obs_w[k] = out ? dw : 1.0;
+  if (v.obs_w32) v.obs_w32[k] = out ? (float)dw : 1.0f;
   if (out) atomicAdd(count, 1);
 }
 
@@ -588,22 +687,21 @@ __global__ void k_linearize(View v, const double *lambda, const int *run, T *NXC
       for (int e = 0; e < 18; e++) { NXC[18 * (size_t)k + e] = 0; Z[18 * (size_t)k + e] = 0; }
     return;
   }
-  double Xd[3] = {v.Xl[3 * (size_t)q], v.Xl[3 * (size_t)q + 1], v.Xl[3 * (size_t)q + 2]};
+  const double *Xd = v.Xl + 3 * (size_t)q;
+  const float *Xh = v.Xl_hi + 3 * (size_t)q, *Xw = v.Xl_lo + 3 * (size_t)q;
   T N[6] = {0, 0, 0, 0, 0, 0}, g[3] = {0, 0, 0};
   for (int k = k0; k < k1; k++) {
     int i = v.obs_cam[k];
-    CamPt<T> cp;
-    cam_point<T>(v, i, Xd, cp);
     ProjJac<T> pj;
-    project_jac<T>(cp.R, cp.Xc, cp.RX, cp.f, cp.cx, cp.cy, pj);
-    T r0 = pj.u - (T)v.obs_xy[2 * k], r1 = pj.v - (T)v.obs_xy[2 * k + 1];
-    T W[3];
-    load_winv<T>(v, k, W);
-    T w = (T)v.obs_w[k];
+    T z;
+    obs_proj<T>(v, i, Xd, Xh, Xw, pj, z);
+    ObsT<T> ob;
+    load_obs<T>(v, k, ob);
+    T r0 = pj.u - ob.x, r1 = pj.v - ob.y;
     T a0[3], a1[3];  // rows of w W A_X, transposed use
     for (int c = 0; c < 3; c++) {
-      a0[c] = w * (W[0] * pj.Jx[c] + W[1] * pj.Jx[3 + c]);
-      a1[c] = w * (W[1] * pj.Jx[c] + W[2] * pj.Jx[3 + c]);
+      a0[c] = ob.w * (ob.W[0] * pj.Jx[c] + ob.W[1] * pj.Jx[3 + c]);
+      a1[c] = ob.w * (ob.W[1] * pj.Jx[c] + ob.W[2] * pj.Jx[3 + c]);
     }
     for (int r = 0; r < 3; r++) {
       for (int c = r; c < 3; c++) N[s3idx(r, c)] += pj.Jx[r] * a0[c] + pj.Jx[3 + r] * a1[c];
@@ -656,19 +754,16 @@ __global__ void k_camera_blocks(View v, const double *lambda, const int *run, co
     int q = v.obs_inst[k];
     int j = v.inst_pt[q];
     if (!v.active[j]) continue;
-    double Xd[3] = {v.Xl[3 * (size_t)q], v.Xl[3 * (size_t)q + 1], v.Xl[3 * (size_t)q + 2]};
-    CamPt<T> cp;
-    cam_point<T>(v, i, Xd, cp);
     ProjJac<T> pj;
-    project_jac<T>(cp.R, cp.Xc, cp.RX, cp.f, cp.cx, cp.cy, pj);
-    T r0 = pj.u - (T)v.obs_xy[2 * k], r1 = pj.v - (T)v.obs_xy[2 * k + 1];
-    T W[3];
-    load_winv<T>(v, k, W);
-    T w = (T)v.obs_w[k];
+    T z;
+    obs_proj<T>(v, i, v.Xl + 3 * (size_t)q, v.Xl_hi + 3 * (size_t)q, v.Xl_lo + 3 * (size_t)q, pj, z);
+    ObsT<T> ob;
+    load_obs<T>(v, k, ob);
+    T r0 = pj.u - ob.x, r1 = pj.v - ob.y;
     T b0[6], b1[6];  // w W A_C
     for (int c = 0; c < 6; c++) {
-      b0[c] = w * (W[0] * pj.Jc[c] + W[1] * pj.Jc[6 + c]);
-      b1[c] = w * (W[1] * pj.Jc[c] + W[2] * pj.Jc[6 + c]);
+      b0[c] = ob.w * (ob.W[0] * pj.Jc[c] + ob.W[1] * pj.Jc[6 + c]);
+      b1[c] = ob.w * (ob.W[1] * pj.Jc[c] + ob.W[2] * pj.Jc[6 + c]);
     }
     const T *B = NXC + 18 * (size_t)k, *Zk = Z + 18 * (size_t)k, *gq = gX + 3 * (size_t)q;
     int e = 0;
@@ -753,6 +848,7 @@ __global__ void k_rcs_clear(View v, const int *run, int L) {
 
 rpba_status launch_build_rcs(Ctx *ctx, const double *lambda_dev, const int *run_dev) {
   RPBA_TRY(cam_prep(ctx));
+  RPBA_TRY(split_points(ctx, 0));
   View v = make_view(ctx);
   dim3 gclr(64, ctx->L);
   RPBA_KERNEL(ctx, "k_rcs_clear", k_rcs_clear<<<gclr, 256, 0, ctx->stream>>>(v, run_dev, ctx->L));
@@ -795,14 +891,19 @@ __global__ void k_backsub(View v, const int *run, const T *NXC, const T *Ninv, c
     for (int e = 0; e < 3; e++) Xt[e] = Xq[e];
     return;
   }
-  const double *dC = v.dC + v.ycam_off[l];
   T rhs[3] = {-gX[3 * (size_t)q], -gX[3 * (size_t)q + 1], -gX[3 * (size_t)q + 2]};
   for (int k = v.inst_obs_ptr[q]; k < v.inst_obs_ptr[q + 1]; k++) {
-    const double *dc = dC + 6 * v.cam_local[v.obs_cam[k]];
+    int off = v.ycam_off[l] + 6 * v.cam_local[v.obs_cam[k]];
+    T dc[6];
+    if constexpr (sizeof(T) == sizeof(float)) {
+      for (int c = 0; c < 6; c++) dc[c] = v.dC32[off + c];
+    } else {
+      for (int c = 0; c < 6; c++) dc[c] = v.dC[off + c];
+    }
     const T *B = NXC + 18 * (size_t)k;
     for (int r = 0; r < 3; r++) {
       T s = 0;
-      for (int c = 0; c < 6; c++) s += B[6 * r + c] * (T)dc[c];
+      for (int c = 0; c < 6; c++) s += B[6 * r + c] * dc[c];
       rhs[r] -= s;
     }
   }
@@ -832,8 +933,15 @@ __global__ void k_cam_trial(View v, const int *run) {
   for (int e = 0; e < 3; e++) v.tt[3 * i + e] = v.t[3 * i + e] + dc[3 + e];
 }
 
+__global__ void k_to_float(const double *a, float *b, int n) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) b[e] = (float)a[e];
+}
+
 rpba_status launch_backsub_trial(Ctx *ctx, const int *run_dev) {
   View v = make_view(ctx);
+  if (ctx->opt.precision == 1 && ctx->ytot)
+    RPBA_KERNEL(ctx, "k_to_float", k_to_float<<<nblk(ctx->ytot, 256), 256, 0, ctx->stream>>>(ctx->dC, ctx->dC32, ctx->ytot));
   if (ctx->P) {
     if (ctx->opt.precision == 1)
       RPBA_KERNEL(ctx, "k_backsub", k_backsub<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, run_dev, (const float *)ctx->NXC,

@@ -415,7 +415,28 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   }
   RPBA_TRY(alloc_n(ctx, &ctx->obs_cost, (size_t)K));
   RPBA_TRY(alloc_n(ctx, &ctx->camC, 3 * (size_t)M));
-  RPBA_TRY(alloc_n(ctx, &ctx->camRf, 12 * (size_t)M));
+  RPBA_TRY(alloc_n(ctx, &ctx->camRf, 16 * (size_t)M));
+  if (ctx->opt.precision == 1) {
+    // FP32 form: inputs rounded once (observations relative to the principal point)
+    std::vector<float> xy32(2 * (size_t)K), w32((size_t)K, 1.0f), wi32(ctx->has_winv ? 3 * (size_t)K : 0);
+    for (int p = 0; p < K; p++) {
+      int i = ocam[p];
+      xy32[2 * (size_t)p] = (float)(oxy[2 * (size_t)p] - pb->cam_intr[3 * (size_t)i + 1]);
+      xy32[2 * (size_t)p + 1] = (float)(oxy[2 * (size_t)p + 1] - pb->cam_intr[3 * (size_t)i + 2]);
+      if (ctx->has_winv)
+        for (int e = 0; e < 3; e++) wi32[3 * (size_t)p + e] = (float)ow[3 * (size_t)p + e];
+    }
+    RPBA_TRY(upload(ctx, &ctx->obs_xy32, xy32.data(), xy32.size()));
+    RPBA_TRY(upload(ctx, &ctx->obs_w32, w32.data(), w32.size()));
+    if (ctx->has_winv) RPBA_TRY(upload(ctx, &ctx->obs_winv32, wi32.data(), wi32.size()));
+    RPBA_TRY(alloc_n(ctx, &ctx->camChi, 3 * (size_t)M));
+    RPBA_TRY(alloc_n(ctx, &ctx->camClo, 3 * (size_t)M));
+    RPBA_TRY(alloc_n(ctx, &ctx->Xl_hi, 3 * (size_t)P));
+    RPBA_TRY(alloc_n(ctx, &ctx->Xl_lo, 3 * (size_t)P));
+    RPBA_TRY(alloc_n(ctx, &ctx->X_hi, 3 * (size_t)N));
+    RPBA_TRY(alloc_n(ctx, &ctx->X_lo, 3 * (size_t)N));
+    RPBA_TRY(alloc_n(ctx, &ctx->dC32, (size_t)std::max(yt, 1)));
+  }
   RPBA_TRY(alloc_n(ctx, &ctx->seg_part, (size_t)L * 32));
   RPBA_TRY(alloc_n(ctx, &ctx->Xl, 3 * (size_t)P));
   RPBA_TRY(alloc_n(ctx, &ctx->Xlt, 3 * (size_t)P));
@@ -625,6 +646,11 @@ extern "C" rpba_status rpba_set_weights(rpba_ctx *h, const double *w) {
   std::vector<double> g(ctx->K);
   for (int p = 0; p < ctx->K; p++) g[p] = w[ctx->h_obs_user[p]];
   if (ctx->K) RPBA_CUDA(cudaMemcpyAsync(ctx->obs_w, g.data(), ctx->K * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  if (ctx->obs_w32 && ctx->K) {
+    std::vector<float> g32(g.begin(), g.end());
+    RPBA_CUDA(cudaMemcpyAsync(ctx->obs_w32, g32.data(), ctx->K * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    return sync(ctx);
+  }
   return sync(ctx);
 }
 

@@ -194,6 +194,9 @@ struct Ctx {
   double *obs_cost = nullptr, *seg_part = nullptr;
   double *camC = nullptr;
   float *camRf = nullptr;
+  float *obs_xy32 = nullptr, *obs_winv32 = nullptr, *obs_w32 = nullptr;
+  float *camChi = nullptr, *camClo = nullptr, *Xl_hi = nullptr, *Xl_lo = nullptr, *X_hi = nullptr,
+        *X_lo = nullptr, *dC32 = nullptr;
   int *sub_obs_ptr = nullptr;
   std::vector<int> h_sched;  // per factorisation step: prefix sums of panel and update tiles
   int *sched = nullptr;
