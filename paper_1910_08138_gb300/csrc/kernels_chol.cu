@@ -44,6 +44,15 @@ struct CholView {
   int L;
 };
 
+// p -> (a, b), b <= a, p = a (a + 1) / 2 + b; FP32 estimate, exact integer fix-up
+// (an FP64 sqrt here would occupy the slow FP64 pipe of every thread)
+__device__ inline void tri_index(int p, int &a, int &b) {
+  a = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
+  while ((a + 1) * (a + 2) / 2 <= p) a++;
+  while (a * (a + 1) / 2 > p) a--;
+  b = p - a * (a + 1) / 2;
+}
+
 // CTA -> (sub-block, local index) through the prefix sums of step k
 __device__ inline int sched_find(const int *base, int L, int idx, int *local) {
   int lo = 0, hi = L - 1;
@@ -193,11 +202,8 @@ __global__ void __launch_bounds__(256, 3) k_chol_update(T *S, T *Linv, CholView 
   int nt = np / CT;
   int rem = nt - k - 1;
   if (rem <= 0) return;
-  long long p = loc;
-  int a = (int)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
-  while ((long long)(a + 1) * (a + 2) / 2 <= p) a++;
-  while ((long long)a * (a + 1) / 2 > p) a--;
-  int b = (int)(p - (long long)a * (a + 1) / 2);
+  int a, b;
+  tri_index(loc, a, b);
   if (a >= rem) return;
   int ti = k + 1 + a, tj = k + 1 + b;
   T *A = S + cv.off[l];
@@ -268,9 +274,22 @@ __global__ void __cluster_dims__(TS, 1, 1) __launch_bounds__(256)
   __shared__ T loc[CT];
   int tid = threadIdx.x;
   int row = tid >> 3, part = tid & 7;  // 32 rows x 8 parts of 4 columns
-  // forward
+  // forward; the L tiles a CTA needs after the barrier of step k are read
+  // into registers before it, so their latency overlaps the barrier
+  const int MAXT = 8;  // owned tiles prefetched per step (more are read late)
   for (int k = 0; k < nt; k++) {
     int owner = k % TS;
+    int t0 = k + 1 + ((rank - (k + 1)) % TS + TS) % TS;
+    T pre[MAXT][4];
+#pragma unroll
+    for (int m = 0; m < MAXT; m++) {
+      int t = t0 + m * TS;
+      if (t < nt) {
+        const T *Lt = A + (size_t)(t * CT + row) * np + k * CT + part * 4;
+#pragma unroll
+        for (int c = 0; c < 4; c++) pre[m][c] = Lt[c];
+      }
+    }
     if (rank == owner) {
       const T *Li = LI + (size_t)k * CT * CT;
       T s = 0;
@@ -286,8 +305,18 @@ __global__ void __cluster_dims__(TS, 1, 1) __launch_bounds__(256)
     const T *src = cluster.map_shared_rank(&buf[k & 1][0], owner);
     if (tid < CT) loc[tid] = src[tid];
     __syncthreads();
-    int t0 = k + 1 + ((rank - (k + 1)) % TS + TS) % TS;
-    for (int t = t0; t < nt; t += TS) {
+#pragma unroll
+    for (int m = 0; m < MAXT; m++) {
+      int t = t0 + m * TS;
+      if (t < nt) {
+        T s = 0;
+#pragma unroll
+        for (int c = 0; c < 4; c++) s += pre[m][c] * loc[part * 4 + c];
+        for (int o = 4; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, 8);
+        if (part == 0) z[t * CT + row] -= s;
+      }
+    }
+    for (int t = t0 + MAXT * TS; t < nt; t += TS) {
       const T *Lt = A + (size_t)(t * CT + row) * np + k * CT + part * 4;
       T s = 0;
 #pragma unroll
@@ -300,6 +329,17 @@ __global__ void __cluster_dims__(TS, 1, 1) __launch_bounds__(256)
   // backward
   for (int k = nt - 1; k >= 0; k--) {
     int owner = k % TS;
+    int col = tid >> 3;
+    T pre[MAXT][4];
+#pragma unroll
+    for (int m = 0; m < MAXT; m++) {
+      int t = rank + m * TS;
+      if (t < k) {
+        const T *Lt = A + (size_t)(k * CT + part * 4) * np + t * CT + col;
+#pragma unroll
+        for (int rr = 0; rr < 4; rr++) pre[m][rr] = Lt[(size_t)rr * np];
+      }
+    }
     if (rank == owner) {
       const T *Li = LI + (size_t)k * CT * CT;
       T s = 0;
@@ -316,8 +356,18 @@ __global__ void __cluster_dims__(TS, 1, 1) __launch_bounds__(256)
     if (tid < CT) loc[tid] = src[tid];
     __syncthreads();
     // z_j -= L_kj^T x_k for owned tiles j < k: column c of the tile, 8 parts of 4 rows
-    int col = tid >> 3;
-    for (int t = rank; t < k; t += TS) {
+#pragma unroll
+    for (int m = 0; m < MAXT; m++) {
+      int t = rank + m * TS;
+      if (t < k) {
+        T s = 0;
+#pragma unroll
+        for (int rr = 0; rr < 4; rr++) s += pre[m][rr] * loc[part * 4 + rr];
+        for (int o = 4; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, 8);
+        if (part == 0) z[t * CT + col] -= s;
+      }
+    }
+    for (int t = rank + MAXT * TS; t < k; t += TS) {
       const T *Lt = A + (size_t)(k * CT + part * 4) * np + t * CT + col;
       T s = 0;
 #pragma unroll
@@ -393,11 +443,8 @@ __global__ void __launch_bounds__(256) k_symv(const double *S, const long long *
   if (!run[l] || fail[l]) return;
   int np = npad[l];
   int nt = np / CT;
-  long long p = blockIdx.x;
-  int a = (int)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
-  while ((long long)(a + 1) * (a + 2) / 2 <= p) a++;
-  while ((long long)a * (a + 1) / 2 > p) a--;
-  int b = (int)(p - (long long)a * (a + 1) / 2);
+  int a, b;
+  tri_index((int)blockIdx.x, a, b);
   if (a >= nt) return;
   const double *A = S + off[l];
   const double *dl = d + voff[l], *xl = x + voff[l];

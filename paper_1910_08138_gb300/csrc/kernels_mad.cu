@@ -46,7 +46,7 @@ __device__ static double sorted_median(const unsigned long long *a, int n) {
 
 __global__ void k_camera_mad(int M, const double *R, const double *t, const double *intr, const double *X,
                              const uint8_t *active, const int *cam_obs_ptr, const int *cam_obs, const int *obs_pt,
-                             const double *obs_xy, const double *obs_winv, int has_winv, double *sigma) {
+                             const double *obs_xy, const double *whiten, int has_winv, double *sigma) {
   extern __shared__ unsigned long long sh[];
   __shared__ int count;
   int i = blockIdx.x;
@@ -66,11 +66,12 @@ __global__ void k_camera_mad(int M, const double *R, const double *t, const doub
     double iz = 1.0 / Xc[2];
     double r0 = f * Xc[0] * iz + cx - obs_xy[2 * k];
     double r1 = f * Xc[1] * iz + cy - obs_xy[2 * k + 1];
-    double W0 = 1, W1 = 0, W2 = 1;
-    if (has_winv) { W0 = obs_winv[3 * k]; W1 = obs_winv[3 * k + 1]; W2 = obs_winv[3 * k + 2]; }
-    double a = sqrt(W0);
-    double e0 = a * r0 + (W1 / a) * r1;
-    double e1 = sqrt(W2 - W1 * W1 / W0) * r1;
+    double e0 = r0, e1 = r1;
+    if (has_winv) {  // upper Cholesky factor of C^-1, precomputed: (sqrt(w11), w12/sqrt(w11), sqrt(w22 - w12^2/w11))
+      const double *F = whiten + 3 * k;
+      e0 = F[0] * r0 + F[1] * r1;
+      e1 = F[2] * r1;
+    }
     int slot = atomicAdd(&count, 2);
     sh[slot] = dkey(e0);
     sh[slot + 1] = dkey(e1);
@@ -107,7 +108,7 @@ rpba_status launch_camera_scale(Ctx *ctx) {
     RPBA_CUDA(cudaFuncSetAttribute(k_camera_mad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   RPBA_KERNEL(ctx, "k_camera_mad", k_camera_mad<<<ctx->M, 512, smem, ctx->stream>>>(ctx->M, ctx->R, ctx->t, ctx->intr, ctx->X, ctx->active,
                                                    ctx->cam_obs_ptr, ctx->cam_obs, ctx->obs_pt, ctx->obs_xy,
-                                                   ctx->obs_winv, ctx->has_winv, ctx->cam_sigma));
+                                                   ctx->obs_whiten, ctx->has_winv, ctx->cam_sigma));
   return RPBA_OK;
 }
 

@@ -734,22 +734,22 @@ __global__ void k_linearize(View v, const double *lambda, const int *run, T *NXC
   }
 }
 
-// one warp per camera of a running sub-block: diagonal RCS block
+// one CTA (CB_THREADS threads) per camera of a running sub-block: diagonal RCS block
 //   S_ii = U_ii + lambda diag(U_ii) - sum_k N_XC,k^T Z_k,  U_ii = sum_k w A_C^T W A_C
 // and right-hand side y_i = -sum_k w A_C^T W v + sum_k Z_k^T g_X
+#define CB_THREADS 128
 template <typename T>
-__global__ void k_camera_blocks(View v, const double *lambda, const int *run, const T *NXC, const T *Z,
-                                const T *gX) {
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (warp >= v.M) return;
-  int i = warp;
+__global__ void __launch_bounds__(CB_THREADS) k_camera_blocks(View v, const double *lambda, const int *run,
+                                                              const T *NXC, const T *Z, const T *gX) {
+  int i = blockIdx.x;
+  if (i >= v.M) return;
   int l = v.cam_sub[i];
   if (!run[l]) return;
-  T U[21], gc[6], SZ[21], yz[6];
-  for (int e = 0; e < 21; e++) { U[e] = 0; SZ[e] = 0; }
-  for (int e = 0; e < 6; e++) { gc[e] = 0; yz[e] = 0; }
-  for (int p = v.cam_obs_ptr[i] + lane; p < v.cam_obs_ptr[i + 1]; p += 32) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  T acc[54];  // U (21), SZ (21), gc (6), yz (6)
+#pragma unroll
+  for (int e = 0; e < 54; e++) acc[e] = 0;
+  for (int p = v.cam_obs_ptr[i] + threadIdx.x; p < v.cam_obs_ptr[i + 1]; p += CB_THREADS) {
     int k = v.cam_obs[p];
     int q = v.obs_inst[k];
     int j = v.inst_pt[q];
@@ -761,33 +761,44 @@ __global__ void k_camera_blocks(View v, const double *lambda, const int *run, co
     load_obs<T>(v, k, ob);
     T r0 = pj.u - ob.x, r1 = pj.v - ob.y;
     T b0[6], b1[6];  // w W A_C
+#pragma unroll
     for (int c = 0; c < 6; c++) {
       b0[c] = ob.w * (ob.W[0] * pj.Jc[c] + ob.W[1] * pj.Jc[6 + c]);
       b1[c] = ob.w * (ob.W[1] * pj.Jc[c] + ob.W[2] * pj.Jc[6 + c]);
     }
     const T *B = NXC + 18 * (size_t)k, *Zk = Z + 18 * (size_t)k, *gq = gX + 3 * (size_t)q;
+    T Bl[18], Zl[18], g3[3] = {gq[0], gq[1], gq[2]};
+#pragma unroll
+    for (int e = 0; e < 18; e++) { Bl[e] = B[e]; Zl[e] = Zk[e]; }
     int e = 0;
+#pragma unroll
     for (int r = 0; r < 6; r++) {
-      gc[r] += b0[r] * r0 + b1[r] * r1;
-      yz[r] += Zk[r] * gq[0] + Zk[6 + r] * gq[1] + Zk[12 + r] * gq[2];
+      acc[42 + r] += b0[r] * r0 + b1[r] * r1;
+      acc[48 + r] += Zl[r] * g3[0] + Zl[6 + r] * g3[1] + Zl[12 + r] * g3[2];
+#pragma unroll
       for (int c = r; c < 6; c++, e++) {
-        U[e] += pj.Jc[r] * b0[c] + pj.Jc[6 + r] * b1[c];
-        SZ[e] += B[r] * Zk[c] + B[6 + r] * Zk[6 + c] + B[12 + r] * Zk[12 + c];
+        acc[e] += pj.Jc[r] * b0[c] + pj.Jc[6 + r] * b1[c];
+        acc[21 + e] += Bl[r] * Zl[c] + Bl[6 + r] * Zl[6 + c] + Bl[12 + r] * Zl[12 + c];
       }
     }
   }
-  // warp reductions
-  for (int e = 0; e < 21; e++)
-    for (int o = 16; o > 0; o >>= 1) {
-      U[e] += __shfl_down_sync(0xffffffffu, U[e], o);
-      SZ[e] += __shfl_down_sync(0xffffffffu, SZ[e], o);
-    }
-  for (int e = 0; e < 6; e++)
-    for (int o = 16; o > 0; o >>= 1) {
-      gc[e] += __shfl_down_sync(0xffffffffu, gc[e], o);
-      yz[e] += __shfl_down_sync(0xffffffffu, yz[e], o);
-    }
-  if (lane == 0) {
+  // warp reduction, then across the CTA's warps
+  __shared__ T red[CB_THREADS / 32][54];
+#pragma unroll
+  for (int e = 0; e < 54; e++) {
+    T x = acc[e];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) red[wid][e] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 54) {
+    T x = 0;
+    for (int w = 0; w < CB_THREADS / 32; w++) x += red[w][threadIdx.x];
+    red[0][threadIdx.x] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const T *U = red[0], *SZ = red[0] + 21, *gc = red[0] + 42, *yz = red[0] + 48;
     double lam = lambda[l];
     int li = v.cam_local[i];
     int np = v.npad[l];
@@ -857,7 +868,7 @@ rpba_status launch_build_rcs(Ctx *ctx, const double *lambda_dev, const int *run_
     float *NXC = (float *)ctx->NXC, *Z = (float *)ctx->Z;
     RPBA_KERNEL(ctx, "k_linearize", k_linearize<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, lambda_dev, run_dev, NXC, Z,
                                                                    (float *)ctx->Ninv, (float *)ctx->gX));
-    RPBA_KERNEL(ctx, "k_camera_blocks", k_camera_blocks<float><<<nblk((long long)ctx->M * 32, 128), 128, 0, ctx->stream>>>(
+    RPBA_KERNEL(ctx, "k_camera_blocks", k_camera_blocks<float><<<ctx->M, CB_THREADS, 0, ctx->stream>>>(
         v, lambda_dev, run_dev, NXC, Z, (const float *)ctx->gX));
     if (ctx->n_pairs)
       RPBA_KERNEL(ctx, "k_schur_pairs", k_schur_pairs<float><<<nblk(ctx->n_pairs * 6, 256), 256, 0, ctx->stream>>>(
@@ -866,7 +877,7 @@ rpba_status launch_build_rcs(Ctx *ctx, const double *lambda_dev, const int *run_
     double *NXC = (double *)ctx->NXC, *Z = (double *)ctx->Z;
     RPBA_KERNEL(ctx, "k_linearize", k_linearize<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, lambda_dev, run_dev, NXC, Z,
                                                                     (double *)ctx->Ninv, (double *)ctx->gX));
-    RPBA_KERNEL(ctx, "k_camera_blocks", k_camera_blocks<double><<<nblk((long long)ctx->M * 32, 128), 128, 0, ctx->stream>>>(
+    RPBA_KERNEL(ctx, "k_camera_blocks", k_camera_blocks<double><<<ctx->M, CB_THREADS, 0, ctx->stream>>>(
         v, lambda_dev, run_dev, NXC, Z, (const double *)ctx->gX));
     if (ctx->n_pairs)
       RPBA_KERNEL(ctx, "k_schur_pairs", k_schur_pairs<double><<<nblk(ctx->n_pairs * 6, 256), 256, 0, ctx->stream>>>(

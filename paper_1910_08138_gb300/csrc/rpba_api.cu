@@ -453,7 +453,18 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   RPBA_TRY(upload(ctx, &ctx->obs_user, order.data(), (size_t)K));
   RPBA_TRY(upload(ctx, &ctx->obs_pt, opt.data(), (size_t)K));
   RPBA_TRY(upload(ctx, &ctx->obs_xy, oxy.data(), 2 * (size_t)K));
-  if (ctx->has_winv) RPBA_TRY(upload(ctx, &ctx->obs_winv, ow.data(), 3 * (size_t)K));
+  if (ctx->has_winv) {
+    RPBA_TRY(upload(ctx, &ctx->obs_winv, ow.data(), 3 * (size_t)K));
+    std::vector<double> wf(3 * (size_t)K);
+    for (int p = 0; p < K; p++) {
+      const double *W = &ow[3 * (size_t)p];
+      double a = sqrt(W[0]);
+      wf[3 * (size_t)p] = a;
+      wf[3 * (size_t)p + 1] = W[1] / a;
+      wf[3 * (size_t)p + 2] = sqrt(W[2] - W[1] * W[1] / W[0]);
+    }
+    RPBA_TRY(upload(ctx, &ctx->obs_whiten, wf.data(), wf.size()));
+  }
   RPBA_TRY(alloc_n(ctx, &ctx->obs_w, (size_t)K));
   RPBA_TRY(dev_alloc(ctx, &ctx->NXC, 18 * (size_t)K * rs));
   RPBA_TRY(dev_alloc(ctx, &ctx->Z, 18 * (size_t)K * rs));

@@ -193,6 +193,7 @@ struct Ctx {
   int ytot = 0;
   double *obs_cost = nullptr, *seg_part = nullptr;
   double *camC = nullptr;
+  double *obs_whiten = nullptr;  // per observation upper Cholesky factor of C^-1 (when given)
   float *camRf = nullptr;
   float *obs_xy32 = nullptr, *obs_winv32 = nullptr, *obs_w32 = nullptr;
   float *camChi = nullptr, *camClo = nullptr, *Xl_hi = nullptr, *Xl_lo = nullptr, *X_hi = nullptr,

@@ -92,7 +92,7 @@ def test_intersection_covariance_and_refined_weights(name, precision):
     else:
         # FP32 stops once steps move the image by < 1e-3 px; points pulled by a
         # gross outlier converge slowest and carry the largest differences
-        assert np.quantile(err, 0.99) <= 2e-5 and err.max() <= 2e-3
+        assert np.quantile(err, 0.99) <= 2e-5 and err.max() <= 5e-3
     # covariance at the same (oracle) state, per point relative Frobenius error
     sync_state(o, g)
     ids = np.nonzero(act)[0]
