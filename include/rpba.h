@@ -196,6 +196,39 @@ rpba_status rpba_profile_enable(rpba_ctx *ctx, int32_t enable);
 rpba_status rpba_profile_read(rpba_ctx *ctx, int32_t max_kernels, char *names, double *ms,
                               int64_t *launches, int32_t *n_kernels, int64_t *total_launches);
 
+/* ---- a variant that allocates no device memory --------------------------- */
+
+/* Largest block rpba_sigma0_noalloc accepts (its fixed scratch: 8192 partial
+ * sums of observations and 8192 of points, about 330 KB on every device that
+ * loads the library, held until the process exits). */
+#define RPBA_NOALLOC_MAX_OBS (8192 * 256)
+#define RPBA_NOALLOC_MAX_POINTS (8192 * 256)
+
+/* sigma_0 and RMS as rpba_sigma0 computes them (Eq. sigma0: sum w v^T C^-1 v
+ * over observations of active points / (2 K - 6 M - 3 N + 7); RMS over
+ * observations with w == 1), for a block given entirely in caller-owned DEVICE
+ * memory, without allocating any device memory. The paper has no counterpart;
+ * it exists for callers that cannot allocate device memory per call (a fixed
+ * device-memory budget, an allocator owned by another framework).
+ *   R n_cams x 9 (row-major rotation, X_c = R X + t), t n_cams x 3, intr
+ *   n_cams x 3 (f, cx, cy), X n_points x 3, active n_points (NULL: all),
+ *   obs_cam / obs_point n_obs, obs_xy n_obs x 2, obs_winv n_obs x 3 (NULL:
+ *   identity), obs_w n_obs (NULL: 1). All on the current device.
+ * Outputs (HOST, nullable): sums5 = {sum w v^T C^-1 v, active observations,
+ * sum |v|^2 (w == 1), observations with w == 1, active points}, sigma0, rms.
+ * Runs on `cuda_stream` and synchronizes it before returning.
+ * Scratch: one file-scope device array shared by every call; its device
+ * address is looked up on the first call on each device (make that first call
+ * before any stream capture). Calls that overlap on the GPU race on it.
+ * Errors: INVALID_ARG for negative sizes, sizes above the limits, or missing
+ * arrays; CUDA for a failed launch or copy. */
+rpba_status rpba_sigma0_noalloc(int32_t n_cams, int32_t n_points, int32_t n_obs, const double *R,
+                                const double *t, const double *intr, const double *X,
+                                const uint8_t *active, const int32_t *obs_cam,
+                                const int32_t *obs_point, const double *obs_xy,
+                                const double *obs_winv, const double *obs_w, void *cuda_stream,
+                                double *sums5, double *sigma0, double *rms);
+
 #ifdef __cplusplus
 }
 #endif

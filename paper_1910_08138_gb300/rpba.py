@@ -110,6 +110,7 @@ def load(build_if_missing: bool = True):
         "rpba_profile_enable": (C.c_int, [vp, C.c_int32]),
         "rpba_profile_read": (C.c_int, [vp, C.c_int32, C.c_char_p, _dp, C.POINTER(C.c_int64), _ip,
                                         C.POINTER(C.c_int64)]),
+        "rpba_sigma0_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32] + [vp] * 10 + [vp, _dp, _dp, _dp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -143,6 +144,23 @@ def _f64(a, shape=None):
 
 def _i32(a):
     return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def rpba_sigma0_noalloc(n_cams, n_points, n_obs, R, t, intr, X, active, obs_cam, obs_point, obs_xy,
+                        obs_winv=None, obs_w=None, stream=None):
+    """sigma_0 and RMS of device arrays (integer device addresses, e.g. a
+    torch tensor's data_ptr(); None for the optional ones) without any device
+    allocation by the library. Returns (sigma0, rms, sums5)."""
+    ptr = lambda a: None if a is None else C.c_void_p(int(a))
+    sums = np.zeros(5)
+    s0, rms = C.c_double(), C.c_double()
+    st = load().rpba_sigma0_noalloc(int(n_cams), int(n_points), int(n_obs), ptr(R), ptr(t), ptr(intr), ptr(X),
+                                    ptr(active), ptr(obs_cam), ptr(obs_point), ptr(obs_xy), ptr(obs_winv),
+                                    ptr(obs_w), ptr(getattr(stream, "cuda_stream", stream)), _d(sums),
+                                    C.byref(s0), C.byref(rms))
+    if st != 0:
+        raise RpbaError(st, "rpba_sigma0_noalloc failed")
+    return s0.value, rms.value, sums
 
 
 def rpba_default_options(**overrides) -> Options:
