@@ -115,6 +115,7 @@ __global__ void k_covariance(int n, const int *ids, const double *R, const doubl
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
+static void free_graph(GraphRec *g);
 static rpba_status dev_alloc(Ctx *ctx, void **p, size_t bytes) {
   if (bytes == 0) bytes = 16;
   bytes = (bytes + 255) & ~(size_t)255;
@@ -190,6 +191,12 @@ extern "C" void rpba_destroy(rpba_ctx *h) {
   }
   if (ctx->h_pinned_counter) cudaFreeHost(ctx->h_pinned_counter);
   if (ctx->h_pinned_d) cudaFreeHost(ctx->h_pinned_d);
+  free_graph(ctx->lm_graph);
+  for (auto &r : ctx->prof_recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
   delete h;
 }
 
@@ -533,6 +540,12 @@ extern "C" rpba_status rpba_create(const rpba_problem *prob, const rpba_options 
   }
   ctx->stream = (cudaStream_t)stream;
   *out = h;
+  if (ctx->stream == nullptr || ctx->stream == cudaStreamLegacy) {
+    // the legacy default stream cannot be captured into a graph: use a blocking
+    // stream of our own, which stays ordered with the legacy stream
+    cudaError_t es = cudaStreamCreate(&ctx->own_stream);
+    if (es == cudaSuccess) ctx->stream = ctx->own_stream;
+  }
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || ndev == 0) {
@@ -836,16 +849,98 @@ extern "C" rpba_status rpba_lm_step(rpba_ctx *h, double lambda, int32_t *accepte
 // ---------------------------------------------------------------------------
 // bact of all sub-blocks in lock step; returns LM iterations summed over
 // sub-blocks and the lock-step count
+// the work of one lock-step LM iteration after the RCS solve inputs are set:
+// build, solve, trial, decide, apply, and the running count to pinned memory
+static rpba_status lm_step_body(Ctx *ctx) {
+  RPBA_TRY(lm_iteration(ctx));
+  RPBA_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(int), ctx->stream));
+  RPBA_TRY(launch_lm_decide(ctx));
+  RPBA_TRY(launch_lm_apply(ctx, ctx->lm_acc));
+  RPBA_CUDA(cudaMemcpyAsync(ctx->h_pinned_counter, ctx->counters, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  return RPBA_OK;
+}
+
+static void free_graph(GraphRec *g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  for (auto &e : g->events) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  delete g;
+}
+
+// capture lm_step_body into a graph (all launch parameters are fixed per context)
+static rpba_status capture_lm_graph(Ctx *ctx) {
+  GraphRec *g = new GraphRec();
+  g->with_events = ctx->prof_enabled;
+  cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    delete g;
+    ctx->use_graphs = false;  // e.g. the legacy default stream: run eagerly
+    cudaGetLastError();
+    return RPBA_OK;
+  }
+  ctx->capture = g;
+  rpba_status st = lm_step_body(ctx);
+  ctx->capture = nullptr;
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(ctx->stream, &graph);
+  if (st != RPBA_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    free_graph(g);
+    if (st == RPBA_OK) {
+      ctx->err = std::string("graph capture: ") + cudaGetErrorString(e);
+      st = RPBA_ERR_CUDA;
+    }
+    return st;
+  }
+  e = cudaGraphInstantiate(&g->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    free_graph(g);
+    ctx->err = std::string("graph instantiate: ") + cudaGetErrorString(e);
+    return RPBA_ERR_CUDA;
+  }
+  ctx->lm_graph = g;
+  return RPBA_OK;
+}
+
+// one lock-step LM iteration through the graph (or eagerly), then the host
+// reads the running count
+static rpba_status lm_step_run(Ctx *ctx) {
+  if (ctx->lm_graph && ctx->lm_graph->with_events != ctx->prof_enabled) {
+    free_graph(ctx->lm_graph);  // timing nodes only while profiling
+    ctx->lm_graph = nullptr;
+  }
+  if (ctx->use_graphs && !ctx->lm_graph) RPBA_TRY(capture_lm_graph(ctx));
+  if (ctx->use_graphs && ctx->lm_graph) {
+    GraphRec *g = ctx->lm_graph;
+    RPBA_CUDA(cudaGraphLaunch(g->exec, ctx->stream));
+    RPBA_TRY(sync(ctx));
+    for (const char *k : g->kernels) {
+      ctx->launches++;
+      ctx->launch_by_name[k]++;
+    }
+    if (ctx->prof_enabled)
+      for (auto &ev : g->events) {
+        float t = 0.f;
+        RPBA_CUDA(cudaEventElapsedTime(&t, ev.a, ev.b));
+        ctx->prof_ms[ev.name] += t;
+      }
+    return RPBA_OK;
+  }
+  RPBA_TRY(lm_step_body(ctx));
+  return sync(ctx);
+}
+
+// bact of all sub-blocks in lock step; returns LM iterations summed over
+// sub-blocks and the lock-step count
 static rpba_status run_bact(Ctx *ctx, int *inner_total, int *launches) {
   RPBA_TRY(launch_lm_init(ctx));
   int n = 0;
   for (;;) {
-    RPBA_TRY(lm_iteration(ctx));
-    RPBA_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(int), ctx->stream));
-    RPBA_TRY(launch_lm_decide(ctx));
-    RPBA_TRY(launch_lm_apply(ctx, ctx->lm_acc));
-    RPBA_CUDA(cudaMemcpyAsync(ctx->h_pinned_counter, ctx->counters, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    RPBA_TRY(sync(ctx));
+    RPBA_TRY(lm_step_run(ctx));
     n++;
     if (ctx->h_pinned_counter[0] == 0) break;
     if (n > 100000) { ctx->err = "LM loop did not terminate"; return RPBA_ERR_NOT_CONVERGED; }

@@ -135,6 +135,8 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
+struct GraphRec;
+
 struct Ctx {
   rpba_options opt;
   cudaStream_t stream = nullptr;
@@ -223,6 +225,11 @@ struct Ctx {
   };
   std::vector<ProfRec> prof_recs;
   std::map<std::string, double> prof_ms;
+  // CUDA graph of one lock-step LM iteration (captured on first use)
+  GraphRec *capture = nullptr;  // non-null while capturing
+  GraphRec *lm_graph = nullptr;
+  bool use_graphs = true;
+  cudaStream_t own_stream = nullptr;  // created when the caller passes the legacy default stream
   int *h_pinned_counter = nullptr;
   double *h_pinned_d = nullptr;
 };
@@ -245,20 +252,44 @@ struct Ctx {
 
 rpba_status check_launch(Ctx *ctx, const char *what);
 
-// times the kernel launched in its scope with CUDA events on the context stream
+// A captured CUDA graph with the names of its kernels and, per kernel, a pair
+// of event-record nodes, so that replays can be counted and timed per kernel.
+struct GraphRec {
+  cudaGraphExec_t exec = nullptr;
+  bool with_events = false;  // captured with per-kernel event-record nodes
+  std::vector<const char *> kernels;
+  struct Ev {
+    const char *name;
+    cudaEvent_t a, b;
+  };
+  std::vector<Ev> events;
+};
+
+// times the kernel launched in its scope with CUDA events on the context
+// stream; while a graph is being captured the events become record nodes of
+// the graph (timed on every replay)
 struct PhaseTimer {
   Ctx *ctx;
   const char *name;
   cudaEvent_t a = nullptr, b = nullptr;
   PhaseTimer(Ctx *c, const char *n) : ctx(c), name(n) {
-    if (ctx->prof_enabled) {
+    if (ctx->capture && !ctx->capture->with_events) return;
+    if (ctx->capture) {
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecordWithFlags(a, ctx->stream, cudaEventRecordExternal);
+    } else if (ctx->prof_enabled) {
       cudaEventCreate(&a);
       cudaEventCreate(&b);
       cudaEventRecord(a, ctx->stream);
     }
   }
   ~PhaseTimer() {
-    if (a) {
+    if (!a) return;
+    if (ctx->capture) {
+      cudaEventRecordWithFlags(b, ctx->stream, cudaEventRecordExternal);
+      ctx->capture->events.push_back({name, a, b});
+    } else {
       cudaEventRecord(b, ctx->stream);
       ctx->prof_recs.push_back({name, a, b});
     }
@@ -267,8 +298,12 @@ struct PhaseTimer {
 
 // after every kernel launch: count it and check the launch status
 inline rpba_status post_launch(Ctx *ctx, const char *name) {
-  ctx->launches++;
-  ctx->launch_by_name[name]++;
+  if (ctx->capture) {
+    ctx->capture->kernels.push_back(name);
+  } else {
+    ctx->launches++;
+    ctx->launch_by_name[name]++;
+  }
   return check_launch(ctx, name);
 }
 
