@@ -124,6 +124,25 @@ def cholesky_update_flops(sub_sizes, tile=32):
     return tot
 
 
+# DRAM bytes per unit of work from the ncu captures summarised under profiles/
+# (dram__bytes_read.sum + dram__bytes_write.sum); None once a kernel has changed
+NCU_TRAFFIC_PER_TILE = {
+    # profiles/k_chol_update_f32_cfg2_1000cam.md: 8.55 MB over 1,910 tiles
+    "k_chol_update_f32": 8.547840e6 / 1910,
+}
+
+
+def update_tiles(sub_sizes, tile=32):
+    """Trailing-update tiles (CTAs) of one factorisation of every sub-block RCS."""
+    tot = 0
+    for n in sub_sizes:
+        T = (n + tile - 1) // tile
+        for k in range(T - 1):
+            rem = T - k - 1
+            tot += rem * (rem + 1) // 2
+    return tot
+
+
 def roofline(prof, steps, n_sub_sizes, K, peaks, mem_bound_bytes):
     # dominant kernel = largest summed event time over the timed region
     name, (launches, ms) = max(prof.items(), key=lambda kv: kv[1][1])
@@ -133,8 +152,12 @@ def roofline(prof, steps, n_sub_sizes, K, peaks, mem_bound_bytes):
         achieved = work / per_launch_s / 1e12
         f64 = name.endswith("f64")
         peak = fp64_peak_gflops() / 1e3 if f64 else 74.6
+        traffic = None
+        if name in NCU_TRAFFIC_PER_TILE:
+            traffic = NCU_TRAFFIC_PER_TILE[name] * update_tiles(n_sub_sizes) * steps / max(launches, 1)
         return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_note": "ncu DRAM bytes per tile scaled to the average launch" if traffic else None,
                 "peak_source": "FP64 1.2 / FP32 74.6 TFLOP/s measured by an FMA-chain probe on this GB300",
                 "launches": launches, "avg_launch_ms": per_launch_s * 1e3}
     bytes_per_launch = mem_bound_bytes.get(name)
