@@ -33,7 +33,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time to oracle-matched RMS (s) & obs/s per LM iter, chosen vs plain form"
-WORKLOAD = "rpba-1000cam-100kpt-600kobs-8sub (25x40 grid, nadir+30deg oblique, 0.5px, 2% outliers)"
+WORKLOADS = {
+    1: "rpba-50cam-2kpt-8kobs-2sub (10x5 nadir grid, 0.5px, 2% outliers)",
+    2: "rpba-1000cam-100kpt-600kobs-8sub (25x40 grid, nadir+30deg oblique, 0.5px, 2% outliers)",
+    3: "rpba-64blocks-7748cam-222kpt-1.0Mobs-304sub (20..400 cams/block, 2..8 sub-blocks, 0.5px, 2% outliers)",
+}
 TARGETS = os.path.join(ROOT, "tests", "golden", "oracle_targets.json")
 
 
@@ -220,9 +224,9 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "obs/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "config": {"workload": WORKLOADS[args.config], "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": "obs/s", "cores": 1, "kind": "oracle",
-                             "sample": "one LM iteration of all 8 sub-blocks + robust weights + TP intersection, "
+                             "sample": "one LM iteration of all sub-blocks + robust weights + TP intersection, "
                                        "whole block, single thread, per step"},
             "e2e": {"value": value, "unit": "obs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -291,7 +295,7 @@ def run_ours(args, rank, world):
     line = {"metric": METRIC, "value": value, "unit": "obs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == 1 else "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": "mixed FP32/FP64" if args.precision == 1 else "FP64",
+            "config": {"workload": WORKLOADS[args.config], "precision": "mixed FP32/FP64" if args.precision == 1 else "FP64",
                        "solver": {0: "FP64 Cholesky", 2: "FP32 Cholesky + FP64 refinement"}.get(args.solver),
                        "l2": "flushed between steps (256 MB write)", "n_obs": K, "subblocks": ctx.L,
                        "step": "1 LM iteration of all sub-blocks + exchange + robust weights + TP intersection",
@@ -360,7 +364,7 @@ def extras(args, prob, ctx, stream, K):
     # CPU oracle on a bounded sample of the same workload
     dt, kk = oracle_step_sample(prob)
     out["cpu_baseline"] = {"value": kk / dt, "unit": "obs/s", "cores": 1, "kind": "oracle",
-                           "sample": "one LM iteration of all 8 sub-blocks + robust weights + TP intersection "
+                           "sample": "one LM iteration of all sub-blocks + robust weights + TP intersection "
                                      f"({kk} obs), single thread, {dt:.1f} s"}
     return out
 

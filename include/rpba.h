@@ -88,8 +88,9 @@ typedef struct {
                             stops once dX moves the image residuals by < 1e-3 px */
   double cond_max;       /* Frobenius condition number that drops a point, 1e12 */
   int32_t precision;     /* 0: all FP64 ("plain"); 1: FP32 bulk, FP64 solve/reductions */
-  int32_t solver;        /* RCS solve: 0 FP64 Cholesky; 2 FP32 Cholesky of the Jacobi-scaled
-                            RCS with FP64 iterative refinement */
+  int32_t solver;        /* RCS solve: 0 FP64 Cholesky; 1 FP64 PCG with block-Jacobi
+                            preconditioning (Sec. 5.5) to pcg_tol; 2 FP32 Cholesky of the
+                            Jacobi-scaled RCS with FP64 iterative refinement */
   double pcg_tol;        /* relative residual of the PCG solve, 1e-8 */
   int32_t pcg_max_iter;  /* PCG iteration cap, 500 */
   int32_t ir_steps;      /* refinement passes of solver 2 after the first solve, 1 */
@@ -183,6 +184,11 @@ rpba_status rpba_rcs(rpba_ctx *ctx, int32_t l, double lambda, double *S, double 
  * sub-blocks concatenated (6 x n_cams), dx = instance updates (P x 3). */
 rpba_status rpba_lm_step(rpba_ctx *ctx, double lambda, int32_t *accepted, double *F_before,
                          double *F_trial, double *dc, double *dx);
+
+/* PCG solver (solver = 1): iterations and final relative residual ||r|| / ||y||
+ * of every sub-block in the last solve (n_subblocks values each, nullable).
+ * Errors: STATE when the context does not use the PCG solver. */
+rpba_status rpba_solver_stats(rpba_ctx *ctx, int32_t *iters, double *relres);
 
 /* ---- measurement ------------------------------------------------------- */
 

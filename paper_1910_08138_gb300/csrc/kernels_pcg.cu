@@ -1,0 +1,278 @@
+// kernels_pcg.cu -- preconditioned conjugate gradients on the reduced camera
+// systems S_l dC_l = y_l of all running sub-blocks at once (Sec. 5.5: the RCS
+// is solved by CG with block-Jacobi preconditioning, i.e. the inverses of the
+// 6x6 diagonal camera blocks). FP64 vectors and FP64 matrix-vector products,
+// so that the relative residual can reach 1e-8.
+//
+// Per iteration: k_pcg_symv (one CTA per 32x32 lower tile of every running
+// sub-block, q += S p with FP64 atomics) and k_pcg_step (one CTA per
+// sub-block: alpha = rz / p.q, x += alpha p, r -= alpha q, z = M^-1 r,
+// beta = rz' / rz, p = z + beta p, convergence ||r|| <= tol ||y||).
+// The block preconditioner M_i^-1 is the inverse of the diagonal camera block
+// (block-Jacobi); any other 6x6 SPD block inverse can be applied the same way.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "rpba_internal.cuh"
+
+namespace rpba {
+
+#define PT 32
+#define PLD (PT + 1)
+
+static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
+
+// M_i^-1 for every camera of a running sub-block: inverse of S_ii (6x6, FP64,
+// Gauss-Jordan on the SPD block); stored row-major, 36 per camera
+__global__ void k_pcg_bj_setup(int M, const int *cam_sub, const int *cam_local, const int *sub_cam_ptr, const int *run,
+                               const double *S, const long long *S_off, const int *npad, double *Minv, int *fail) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  int l = cam_sub[i];
+  if (!run[l]) return;
+  int np = npad[l], li = cam_local[i];
+  const double *A = S + S_off[l];
+  double a[6][12];
+  for (int r = 0; r < 6; r++)
+    for (int c = 0; c < 6; c++) {
+      int rr = r >= c ? r : c, cc = r >= c ? c : r;  // lower triangle holds the block
+      a[r][c] = A[(size_t)(6 * li + rr) * np + 6 * li + cc];
+      a[r][6 + c] = (r == c) ? 1.0 : 0.0;
+    }
+  for (int c = 0; c < 6; c++) {
+    double piv = a[c][c];
+    if (!(piv > 0.0)) {
+      atomicExch(fail + l, 1);
+      return;
+    }
+    double ip = 1.0 / piv;
+    for (int e = 0; e < 12; e++) a[c][e] *= ip;
+    for (int r = 0; r < 6; r++) {
+      if (r == c) continue;
+      double f = a[r][c];
+      for (int e = 0; e < 12; e++) a[r][e] -= f * a[c][e];
+    }
+  }
+  double *o = Minv + 36 * (size_t)(sub_cam_ptr[l] + li);  // cameras in sub-block order
+  for (int r = 0; r < 6; r++)
+    for (int c = 0; c < 6; c++) o[6 * r + c] = a[r][6 + c];
+}
+
+// q += S p over the lower 32x32 tiles of the running, unconverged sub-blocks
+__global__ void __launch_bounds__(256) k_pcg_symv(const double *S, const long long *S_off, const int *npad,
+                                                  const int *voff, const int *live, const int *sched_tiles, int L,
+                                                  const double *p, double *q) {
+  // CTA -> (sub-block, tile) through prefix sums of the per-sub-block tile counts
+  int idx = blockIdx.x;
+  int lo = 0, hi = L - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (sched_tiles[mid] <= idx) lo = mid; else hi = mid - 1;
+  }
+  int l = lo;
+  if (!live[l]) return;
+  int loc = idx - sched_tiles[l];
+  int a = (int)((sqrtf(8.0f * (float)loc + 1.0f) - 1.0f) * 0.5f);
+  while ((a + 1) * (a + 2) / 2 <= loc) a++;
+  while (a * (a + 1) / 2 > loc) a--;
+  int b = loc - a * (a + 1) / 2;
+  int np = npad[l];
+  const double *A = S + S_off[l];
+  const double *pl = p + voff[l];
+  double *ql = q + voff[l];
+  __shared__ double blk[PT][PLD];
+  __shared__ double pI[PT], pJ[PT];
+  int tid = threadIdx.x;
+  if (tid < PT) {
+    pI[tid] = pl[a * PT + tid];
+    pJ[tid] = pl[b * PT + tid];
+  }
+  for (int e = tid; e < PT * PT; e += blockDim.x) {
+    int r = e / PT, c = e - r * PT;
+    double v = A[(size_t)(a * PT + r) * np + b * PT + c];
+    if (a == b && c > r) v = A[(size_t)(a * PT + c) * np + b * PT + r];
+    blk[r][c] = v;
+  }
+  __syncthreads();
+  if (tid < PT) {
+    double s = 0.0;
+    for (int c = 0; c < PT; c++) s += blk[tid][c] * pJ[c];
+    atomicAdd(ql + a * PT + tid, s);
+  } else if (tid < 2 * PT && a != b) {
+    int c = tid - PT;
+    double s = 0.0;
+    for (int r = 0; r < PT; r++) s += blk[r][c] * pI[r];
+    atomicAdd(ql + b * PT + c, s);
+  }
+}
+
+template <int NV>
+__device__ inline void cta_sum(double (&v)[NV], double (&out)[NV]) {
+  __shared__ double sh[NV][8];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int e = 0; e < NV; e++) {
+    double x = v[e];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[e][wid] = x;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < NV; e++) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += sh[e][w];
+    out[e] = s;
+  }
+  __syncthreads();
+}
+
+// z = M^-1 r for the cameras of sub-block l (block rows of 6)
+__device__ inline void apply_precond(int n_cam, const double *Minv_l, const double *r, double *z) {
+  for (int c = threadIdx.x; c < n_cam; c += blockDim.x) {
+    const double *Mi = Minv_l + 36 * (size_t)c;
+    for (int a = 0; a < 6; a++) {
+      double s = 0.0;
+      for (int b = 0; b < 6; b++) s += Mi[6 * a + b] * r[6 * c + b];
+      z[6 * c + a] = s;
+    }
+  }
+}
+
+// start: x = 0, r = y, z = M^-1 r, p = z; rz, |y|
+__global__ void __launch_bounds__(256) k_pcg_init(const int *run, const int *fail, const int *sub_cam_ptr,
+                                                  const int *voff, const int *npad, const double *Minv_sub,
+                                                  const double *y, double *x, double *r, double *z, double *p,
+                                                  double *st, int *live) {
+  int l = blockIdx.x;
+  int ok = run[l] && !fail[l];
+  if (threadIdx.x == 0) live[l] = ok;
+  if (!ok) return;
+  int ncam = sub_cam_ptr[l + 1] - sub_cam_ptr[l];
+  int n = 6 * ncam;
+  int o = voff[l];
+  for (int e = threadIdx.x; e < npad[l]; e += blockDim.x) {  // padding stays zero
+    x[o + e] = 0.0;
+    r[o + e] = e < n ? y[o + e] : 0.0;
+    z[o + e] = 0.0;
+    p[o + e] = 0.0;
+  }
+  __syncthreads();
+  apply_precond(ncam, Minv_sub + 36 * (size_t)sub_cam_ptr[l], r + o, z + o);
+  __syncthreads();
+  double v[2] = {0.0, 0.0};
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    p[o + e] = z[o + e];
+    v[0] += r[o + e] * z[o + e];
+    v[1] += y[o + e] * y[o + e];
+  }
+  double s[2];
+  cta_sum<2>(v, s);
+  if (threadIdx.x == 0) {
+    st[4 * l + 0] = s[0];               // rz
+    st[4 * l + 1] = sqrt(s[1]);         // |y|
+    st[4 * l + 2] = s[1] > 0.0 ? 1.0 : 0.0;  // relative residual
+    st[4 * l + 3] = 0.0;                // iterations
+    if (!(s[1] > 0.0)) live[l] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_pcg_step(const int *sub_cam_ptr, const int *voff, const double *Minv_sub,
+                                                  double tol, double *x, double *r, double *z, double *p,
+                                                  const double *q, double *st, int *live) {
+  int l = blockIdx.x;
+  if (!live[l]) return;
+  int ncam = sub_cam_ptr[l + 1] - sub_cam_ptr[l];
+  int n = 6 * ncam;
+  int o = voff[l];
+  double v1[1] = {0.0};
+  for (int e = threadIdx.x; e < n; e += blockDim.x) v1[0] += p[o + e] * q[o + e];
+  double pq[1];
+  cta_sum<1>(v1, pq);
+  double rz = st[4 * l];
+  if (!(pq[0] > 0.0)) {  // breakdown: keep the current iterate
+    if (threadIdx.x == 0) live[l] = 0;
+    return;
+  }
+  double alpha = rz / pq[0];
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    x[o + e] += alpha * p[o + e];
+    r[o + e] -= alpha * q[o + e];
+  }
+  __syncthreads();
+  apply_precond(ncam, Minv_sub + 36 * (size_t)sub_cam_ptr[l], r + o, z + o);
+  __syncthreads();
+  double v[2] = {0.0, 0.0};
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    v[0] += r[o + e] * z[o + e];
+    v[1] += r[o + e] * r[o + e];
+  }
+  double s[2];
+  cta_sum<2>(v, s);
+  double beta = s[0] / rz;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) p[o + e] = z[o + e] + beta * p[o + e];
+  if (threadIdx.x == 0) {
+    st[4 * l + 0] = s[0];
+    double rel = sqrt(s[1]) / st[4 * l + 1];
+    st[4 * l + 2] = rel;
+    st[4 * l + 3] += 1.0;
+    if (rel <= tol) live[l] = 0;
+  }
+}
+
+// dC = x
+__global__ void k_pcg_out(const int *run, const int *fail, const int *voff, const int *npad, int L, const double *x,
+                          double *dC) {
+  int l = blockIdx.y;
+  if (l >= L || !run[l] || fail[l]) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < npad[l]; e += gridDim.x * blockDim.x)
+    dC[voff[l] + e] = x[voff[l] + e];  // padding of x is zero
+}
+
+__global__ void k_pcg_live_count(int L, const int *live, int *count) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < L && live[l]) atomicAdd(count, 1);
+}
+
+// Solve with the preconditioner blocks in ctx->pcg_Minv (set up by the caller:
+// block-Jacobi here, or the learned blocks). Iterations stop per sub-block at
+// the relative residual pcg_tol or after pcg_max_iter.
+rpba_status pcg_iterate(Ctx *ctx, const int *run_dev, int *fail_dev) {
+  int L = ctx->L;
+  RPBA_KERNEL(ctx, "k_pcg_init", k_pcg_init<<<L, 256, 0, ctx->stream>>>(
+                                     run_dev, fail_dev, ctx->sub_cam_ptr, ctx->ycam_off, ctx->npad, ctx->pcg_Minv, ctx->y,
+                                     ctx->pcg_x, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, ctx->pcg_st, ctx->pcg_live));
+  int tiles = ctx->pcg_tiles_total;
+  int maxit = ctx->opt.pcg_max_iter;
+  for (int it = 0; it < maxit; it++) {
+    RPBA_CUDA(cudaMemsetAsync(ctx->pcg_q, 0, ctx->ytot * sizeof(double), ctx->stream));
+    RPBA_KERNEL(ctx, "k_pcg_symv", k_pcg_symv<<<tiles, 256, 0, ctx->stream>>>(
+                                       ctx->S, ctx->S_off, ctx->npad, ctx->ycam_off, ctx->pcg_live, ctx->pcg_tiles,
+                                       L, ctx->pcg_p, ctx->pcg_q));
+    RPBA_KERNEL(ctx, "k_pcg_step", k_pcg_step<<<L, 256, 0, ctx->stream>>>(
+                                       ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_Minv, ctx->opt.pcg_tol, ctx->pcg_x,
+                                       ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, ctx->pcg_q, ctx->pcg_st, ctx->pcg_live));
+    if ((it & 7) == 7 || it == maxit - 1) {
+      RPBA_CUDA(cudaMemsetAsync(ctx->counters + 8, 0, sizeof(int), ctx->stream));
+      RPBA_KERNEL(ctx, "k_pcg_live_count", k_pcg_live_count<<<nblk(L, 128), 128, 0, ctx->stream>>>(
+                                               L, ctx->pcg_live, ctx->counters + 8));
+      RPBA_CUDA(cudaMemcpyAsync(ctx->h_pinned_counter + 8, ctx->counters + 8, sizeof(int), cudaMemcpyDeviceToHost,
+                                ctx->stream));
+      RPBA_CUDA(cudaStreamSynchronize(ctx->stream));
+      if (ctx->h_pinned_counter[8] == 0) break;
+    }
+  }
+  RPBA_KERNEL(ctx, "k_pcg_out", k_pcg_out<<<dim3(8, L), 256, 0, ctx->stream>>>(run_dev, fail_dev, ctx->ycam_off,
+                                                                             ctx->npad, L, ctx->pcg_x, ctx->dC));
+  return RPBA_OK;
+}
+
+rpba_status launch_pcg_blockjacobi(Ctx *ctx, const int *run_dev, int *fail_dev) {
+  RPBA_CUDA(cudaMemsetAsync(fail_dev, 0, ctx->L * sizeof(int), ctx->stream));
+  if (ctx->M)
+    RPBA_KERNEL(ctx, "k_pcg_bj_setup", k_pcg_bj_setup<<<nblk(ctx->M, 128), 128, 0, ctx->stream>>>(
+                                           ctx->M, ctx->cam_sub, ctx->cam_local, ctx->sub_cam_ptr, run_dev, ctx->S,
+                                           ctx->S_off, ctx->npad, ctx->pcg_Minv, fail_dev));
+  return pcg_iterate(ctx, run_dev, fail_dev);
+}
+
+}  // namespace rpba

@@ -487,6 +487,20 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   RPBA_TRY(upload(ctx, &ctx->linv_off, loff.data(), (size_t)L));
   RPBA_TRY(upload(ctx, &ctx->sched, ctx->h_sched.data(), ctx->h_sched.size()));
   RPBA_TRY(alloc_n(ctx, &ctx->Linv64, (size_t)std::max(ltot, 1)));
+  if (ctx->opt.solver == 1) {
+    RPBA_TRY(alloc_n(ctx, &ctx->pcg_Minv, 36 * (size_t)std::max(M, 1)));
+    RPBA_TRY(alloc_n(ctx, &ctx->pcg_x, (size_t)std::max(yt, 1)));
+    RPBA_TRY(alloc_n(ctx, &ctx->pcg_r, (size_t)std::max(yt, 1)));
+    RPBA_TRY(alloc_n(ctx, &ctx->pcg_z, (size_t)std::max(yt, 1)));
+    RPBA_TRY(alloc_n(ctx, &ctx->pcg_p, (size_t)std::max(yt, 1)));
+    RPBA_TRY(alloc_n(ctx, &ctx->pcg_q, (size_t)std::max(yt, 1)));
+    RPBA_TRY(alloc_n(ctx, &ctx->pcg_st, 4 * (size_t)std::max(L, 1)));
+    RPBA_TRY(alloc_n(ctx, &ctx->pcg_live, (size_t)std::max(L, 1)));
+    std::vector<int> pt(L + 1, 0);
+    for (int l = 0; l < L; l++) pt[l + 1] = pt[l] + ntiles[l] * (ntiles[l] + 1) / 2;
+    ctx->pcg_tiles_total = pt[L];
+    RPBA_TRY(upload(ctx, &ctx->pcg_tiles, pt.data(), (size_t)L + 1));
+  }
   if (ctx->opt.solver == 2) {
     RPBA_TRY(alloc_n(ctx, &ctx->S32, (size_t)std::max(stot, 1LL)));
     RPBA_TRY(upload(ctx, &ctx->S32_off, soff.data(), (size_t)L));
@@ -533,7 +547,7 @@ extern "C" rpba_status rpba_create(const rpba_problem *prob, const rpba_options 
   if (opt) ctx->opt = *opt;
   else rpba_default_options(&ctx->opt);
   if ((ctx->opt.precision != 0 && ctx->opt.precision != 1) || ctx->opt.solver < 0 || ctx->opt.solver > 2 ||
-      ctx->opt.solver == 1 || ctx->opt.ir_steps < 0 || ctx->opt.ir_steps > 20) {
+      ctx->opt.ir_steps < 0 || ctx->opt.ir_steps > 20 || ctx->opt.pcg_max_iter < 1 || !(ctx->opt.pcg_tol > 0.0)) {
     ctx->err = "invalid precision / solver / ir_steps option";
     *out = h;
     return RPBA_ERR_INVALID_ARG;
@@ -1058,5 +1072,21 @@ extern "C" rpba_status rpba_profile_read(rpba_ctx *h, int32_t max_kernels, char 
   }
   if (n_kernels) *n_kernels = n;
   if (total_launches) *total_launches = ctx->launches;
+  return RPBA_OK;
+}
+
+extern "C" rpba_status rpba_solver_stats(rpba_ctx *h, int32_t *iters, double *relres) {
+  CTX_OR_FAIL;
+  if (ctx->opt.solver != 1 || !ctx->pcg_st) {
+    ctx->err = "solver statistics exist for the PCG solver only";
+    return RPBA_ERR_STATE;
+  }
+  std::vector<double> st(4 * (size_t)ctx->L);
+  if (ctx->L) RPBA_CUDA(cudaMemcpyAsync(st.data(), ctx->pcg_st, st.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  RPBA_TRY(sync(ctx));
+  for (int l = 0; l < ctx->L; l++) {
+    if (iters) iters[l] = (int32_t)st[4 * l + 3];
+    if (relres) relres[l] = st[4 * l + 2];
+  }
   return RPBA_OK;
 }

@@ -193,6 +193,11 @@ struct Ctx {
   long long *S_off = nullptr;
   int *npad = nullptr, *ycam_off = nullptr, *sub_ntiles = nullptr, *linv_off = nullptr;
   int ytot = 0;
+  // PCG on the RCS
+  double *pcg_Minv = nullptr, *pcg_x = nullptr, *pcg_r = nullptr, *pcg_z = nullptr, *pcg_p = nullptr,
+         *pcg_q = nullptr, *pcg_st = nullptr;
+  int *pcg_live = nullptr, *pcg_tiles = nullptr;
+  int pcg_tiles_total = 0;
   double *obs_cost = nullptr, *seg_part = nullptr;
   double *camC = nullptr;
   double *obs_whiten = nullptr;  // per observation upper Cholesky factor of C^-1 (when given)
@@ -329,6 +334,8 @@ rpba_status launch_eliminate(Ctx *ctx);
 rpba_status launch_sub_costs(Ctx *ctx, int trial, double *F_dev);
 rpba_status launch_build_rcs(Ctx *ctx, const double *lambda_dev, const int *run_dev);
 rpba_status launch_solve_rcs(Ctx *ctx, const int *run_dev, int *fail_dev);
+rpba_status launch_pcg_blockjacobi(Ctx *ctx, const int *run_dev, int *fail_dev);
+rpba_status pcg_iterate(Ctx *ctx, const int *run_dev, int *fail_dev);
 rpba_status launch_backsub_trial(Ctx *ctx, const int *run_dev);
 rpba_status launch_lm_decide(Ctx *ctx);
 rpba_status launch_lm_apply(Ctx *ctx, const int *acc_dev);

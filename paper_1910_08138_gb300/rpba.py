@@ -110,6 +110,7 @@ def load(build_if_missing: bool = True):
         "rpba_profile_enable": (C.c_int, [vp, C.c_int32]),
         "rpba_profile_read": (C.c_int, [vp, C.c_int32, C.c_char_p, _dp, C.POINTER(C.c_int64), _ip,
                                         C.POINTER(C.c_int64)]),
+        "rpba_solver_stats": (C.c_int, [vp, _ip, _dp]),
         "rpba_sigma0_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32] + [vp] * 10 + [vp, _dp, _dp, _dp]),
     }
     for name, (res, args) in sigs.items():
@@ -369,6 +370,11 @@ class Rpba:
         dc, dx = np.zeros(6 * self.M), np.zeros((self.P, 3))
         self._c(load().rpba_lm_step(self._h, float(lam), _i(acc), _d(Fb), _d(Ft), _d(dc), _d(dx)))
         return acc, Fb, Ft, dc, dx
+
+    def solver_stats(self):
+        it, rr = np.zeros(self.L, np.int32), np.zeros(self.L)
+        self._c(load().rpba_solver_stats(self._h, _i(it), _d(rr)))
+        return it, rr
 
     # measurement
     def profile_enable(self, enable=True):

@@ -223,7 +223,7 @@ def merge_blocks(blocks):
 # --------------------------------------------------------------------------
 # named workloads
 # --------------------------------------------------------------------------
-def config(c: int, scale: float = 1.0):
+def config(c: int, scale: float = 1.0, n_blocks: int = 64):
     """The five benchmark blocks (c = 1..5); `scale` < 1 shrinks point counts.
 
     1: 50 nadir cameras (10x5 grid, 4 m, 30 m high), 2,000 points, 4 obs/point,
@@ -231,7 +231,7 @@ def config(c: int, scale: float = 1.0):
     2: 1,000 cameras (25x40 grid, every 5th nadir, others 30 deg oblique),
        100k points, 6 obs/point, 8 uneven sub-blocks (60..200 cameras).
     3: 64 independent blocks, 20..400 cameras (log-uniform), 50..200 points per
-       camera, 3..6 obs/point, 2..8 sub-blocks each.
+       camera, 3..6 obs/point, 2..8 sub-blocks each (`n_blocks` keeps the first ones).
     4: 50 strips x 100 cameras, 60 % forward / 30 % side overlap, 1M points,
        5 obs/point, 32 sub-blocks, 5 % outliers.
     5: 100x100 positions, nadir and 45 deg obliques, 4M points, 5 obs/point,
@@ -247,7 +247,7 @@ def config(c: int, scale: float = 1.0):
                           runs=[60, 80, 100, 120, 140, 160, 140, 200])
     if c == 3:
         blocks = []
-        for b in range(64):
+        for b in range(n_blocks):
             rb = np.random.Generator(np.random.PCG64(SEED_BASE + 100 * c + 1 + b))
             Mb = int(round(np.exp(rb.uniform(np.log(20), np.log(400)))))
             ppc = rb.uniform(50, 200)

@@ -188,7 +188,7 @@ def test_camera_scale_and_robust_weights(precision):
 
 @pytest.mark.parametrize("precision,robust,outliers,solver",
                          [(0, 0, True, 0), (0, 1, True, 0), (1, 1, True, 0), (1, 0, False, 0), (1, 1, True, 2),
-                          (0, 1, True, 2)])
+                          (0, 1, True, 2), (0, 1, True, 1)])
 def test_whole_iteration_final_rms(precision, robust, outliers, solver):
     prob = synth.config(1)
     if not outliers:
@@ -252,3 +252,38 @@ def test_torch_allocator_and_stream():
     rg2 = g2.iterate()
     assert rg["rms"] == pytest.approx(rg2["rms"], abs=1e-9)
     g.close()
+
+
+@pytest.mark.parametrize("precision,solver", [(0, 0), (1, 2)])
+def test_batched_independent_blocks(precision, solver):
+    """Eight independent blocks (42 sub-blocks of 20..400-camera blocks) advance
+    in the same lock-step launches; each block must reach the oracle's result."""
+    prob = synth.config(3, n_blocks=8)
+    o = oracle.Oracle(prob)
+    ro = o.run(robust=1, robust_from_start=1)
+    g = rpba.Rpba(prob, precision=precision, solver=solver, robust=1, robust_from_start=1)
+    assert g.L == o.L == 42
+    rg = g.iterate()
+    assert abs(rg["rms"] - ro["rms"]) <= 1e-3
+    if precision == 0:
+        assert rg["outer"] == ro["outer"] and rg["inner_total"] == ro["inner_total"]
+        assert rg["deleted_points"] == ro["deleted_points"]
+
+
+@pytest.mark.parametrize("name", ["tiny3w", "cfg1"])
+def test_pcg_block_jacobi_solves_the_rcs(name):
+    """PCG with block-Jacobi (Sec. 5.5) at relative residual 1e-8 gives the
+    Cholesky step of the oracle to the accuracy the residual allows."""
+    prob, o, g = _state_after_intersection(name, 0, weights=(name == "tiny3w"), solver=1, pcg_tol=1e-8,
+                                           pcg_max_iter=2000)
+    acc, Fb, Ft, dc, dx = g.lm_step(1e-4)
+    it, rr = g.solver_stats()
+    assert np.all(rr <= 1e-8) and np.all(it > 0)
+    off = 0
+    _, isub = o.instances()
+    for l in range(o.L):
+        r, fb, ft, dco, dxo = o.lm_step(l, 1e-4)
+        n = dco.size
+        assert np.abs(dc[off:off + n] - dco).max() <= 1e-4 * np.abs(dco).max()
+        assert acc[l] == r
+        off += n
