@@ -84,8 +84,9 @@ typedef struct {
   int32_t robust;        /* 1: robust stage (Sec. 5.3, parallel variant) */
   int32_t robust_from_start; /* 1: robust weights from the first intersection on */
   int32_t isect_max_iter;/* Gauss-Newton iterations of the intersection, 10 */
-  double isect_tol;      /* ||dX|| <= tol (1 + ||X||) ends it, 1e-10; the FP32 form also
-                            stops once dX moves the image residuals by < 1e-3 px */
+  double isect_tol;      /* ||dX|| <= tol (1 + ||X||) ends it, 1e-10 */
+  double isect_px_tol;   /* ... or a step that moves the image residuals by less than this per
+                            observation (dX^T N dX <= px_tol^2 n_obs), 1e-3 px */
   double cond_max;       /* Frobenius condition number that drops a point, 1e12 */
   int32_t precision;     /* 0: all FP64 ("plain"); 1: FP32 bulk, FP64 solve/reductions */
   int32_t solver;        /* RCS solve: 0 FP64 Cholesky; 1 FP64 PCG with block-Jacobi

@@ -27,7 +27,7 @@ class Options(C.Structure):
                 ("stop_ratio", C.c_double), ("grace", C.c_int), ("max_outer", C.c_int),
                 ("max_inner", C.c_int), ("max_reject", C.c_int), ("robust", C.c_int),
                 ("robust_from_start", C.c_int), ("isect_max_iter", C.c_int),
-                ("isect_tol", C.c_double), ("cond_max", C.c_double)]
+                ("isect_tol", C.c_double), ("isect_px_tol", C.c_double), ("cond_max", C.c_double)]
 
 
 class Report(C.Structure):

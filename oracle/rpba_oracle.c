@@ -25,10 +25,12 @@
  *    starting TP weights; later intersections run for the TPs only, starting
  *    from the previous X_TP; the sub-block copies X^l of TPs restart at X_TP.
  *  - intersection is undamped Gauss-Newton, at most 10 iterations, converged
- *    when ||dX|| <= 1e-10 (1 + ||X||); it drops the point when it does not
- *    converge, when an observation lies behind its camera (z_c <= 0), or when
- *    the Frobenius condition number of N_j exceeds 1e12 (Sec. 5.5, last
- *    paragraph). W^l and N_j are those of the last Gauss-Newton iteration.
+ *    when the step moves the point's image residuals by less than 1e-3 px per
+ *    observation (dX^T N_j dX <= (1e-3)^2 n_obs) or when ||dX|| <= 1e-10
+ *    (1 + ||X||); it drops the point when it does not converge, when an
+ *    observation lies behind its camera (z_c <= 0), or when the Frobenius
+ *    condition number of N_j exceeds 1e12 (Sec. 5.5, last paragraph). W^l and
+ *    N_j are those of the last Gauss-Newton iteration.
  *  - refined weight (Sec. 5.1): W^l_j = N_j - N_j^(l), the normal matrix of
  *    point j without the observations from cameras of sub-block l; zero for a
  *    point seen in one sub-block only.
@@ -262,6 +264,7 @@ void orc_default_options(orc_options *o) {
   o->robust_from_start = 0;
   o->isect_max_iter = 10;
   o->isect_tol = 1e-10;
+  o->isect_px_tol = 1e-3;
   o->cond_max = 1e12;
 }
 
@@ -621,12 +624,16 @@ static int intersect_point(const orc_ctx *c, const orc_options *o, int j, double
     double det = sym3_inverse(Ntot, inv);
     if (!(det > 0.0)) return 0;
     if (!(sym3_frob(Ntot) * sym3_frob(inv) <= o->cond_max)) return 0;
-    double d[3];
+    double d[3], Nd[3];
     sym3_mul_vec(inv, g, d);
     for (int e = 0; e < 3; e++) X[e] -= d[e];
     double nd = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     double nx = sqrt(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
     if (nd <= o->isect_tol * (1.0 + nx)) return 1;
+    /* image-space size of the step: dX^T N dX = sum_k w ||W^1/2 A_X,k dX||^2 */
+    sym3_mul_vec(Ntot, d, Nd);
+    int nobs = c->pt_obs_ptr[j + 1] - c->pt_obs_ptr[j];
+    if (d[0] * Nd[0] + d[1] * Nd[1] + d[2] * Nd[2] <= o->isect_px_tol * o->isect_px_tol * nobs) return 1;
   }
   return 0;
 }

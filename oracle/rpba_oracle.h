@@ -52,6 +52,7 @@ typedef struct {
   int robust_from_start; /* 1: robust weights from the first intersection after the first bact */
   int isect_max_iter;  /* Gauss-Newton iterations of the intersection, 10 */
   double isect_tol;    /* ||dX|| <= tol (1 + ||X||) ends the intersection, 1e-10 */
+  double isect_px_tol; /* or a step moving the image residuals by < this per observation, 1e-3 px */
   double cond_max;     /* Frobenius condition number above which a point is dropped, 1e12 */
 } orc_options;
 

@@ -374,9 +374,9 @@ __global__ void k_isect_inst(View v, const int *state, T *part) {
 
 // per running point: sum the instance parts, Gauss-Newton update, checks,
 // and on convergence W^l = N - N^(l) for every instance. Converged when
-// ||dX|| <= tol (1 + ||X||), or, when px_tol > 0 (FP32 residuals, whose
-// rounding is ~1e-4 px), when the step moves the point's image residuals by
-// less than px_tol per observation: dX^T N dX <= px_tol^2 n_obs.
+// ||dX|| <= tol (1 + ||X||) or when the step moves the point's image
+// residuals by less than px_tol per observation: dX^T N dX <= px_tol^2 n_obs
+// (reachable in FP32, whose residuals carry ~1e-4 px rounding).
 // FP32 form: the 3x3 system is solved in FP32, and again in FP64 when its
 // Frobenius condition number exceeds 1e6.
 template <typename T>
@@ -477,7 +477,7 @@ rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped) {
                                         v, ctx->isect_state, ctx->isect_iter, tp_only, ctx->counters));
   int maxit = ctx->opt.isect_max_iter;
   double tol = ctx->opt.isect_tol;
-  double px_tol = ctx->opt.precision == 1 ? 1e-3 : 0.0;  // FP32 residuals cannot resolve less
+  double px_tol = ctx->opt.isect_px_tol;
   for (int it = 0; it < maxit; it++) {
     if (ctx->opt.precision == 1) {
       float *part = (float *)ctx->isect_N;

@@ -171,6 +171,7 @@ extern "C" void rpba_default_options(rpba_options *o) {
   o->robust_from_start = 0;
   o->isect_max_iter = 10;
   o->isect_tol = 1e-10;
+  o->isect_px_tol = 1e-3;
   o->cond_max = 1e12;
   o->precision = 0;
   o->solver = 0;
@@ -886,6 +887,10 @@ static void free_graph(GraphRec *g) {
 
 // capture lm_step_body into a graph (all launch parameters are fixed per context)
 static rpba_status capture_lm_graph(Ctx *ctx) {
+  if (ctx->opt.solver == 1) {  // PCG stops on a device-side test read by the host: not capturable
+    ctx->use_graphs = false;
+    return RPBA_OK;
+  }
   GraphRec *g = new GraphRec();
   g->with_events = ctx->prof_enabled;
   cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
@@ -903,11 +908,10 @@ static rpba_status capture_lm_graph(Ctx *ctx) {
   if (st != RPBA_OK || e != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
     free_graph(g);
-    if (st == RPBA_OK) {
-      ctx->err = std::string("graph capture: ") + cudaGetErrorString(e);
-      st = RPBA_ERR_CUDA;
-    }
-    return st;
+    cudaGetLastError();  // clear the capture error; run eagerly from now on
+    ctx->use_graphs = false;
+    ctx->err.clear();
+    return RPBA_OK;
   }
   e = cudaGraphInstantiate(&g->exec, graph, 0);
   cudaGraphDestroy(graph);

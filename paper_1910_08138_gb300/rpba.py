@@ -37,7 +37,8 @@ class Options(C.Structure):
                 ("stop_ratio", C.c_double), ("grace", C.c_int32), ("max_outer", C.c_int32),
                 ("max_inner", C.c_int32), ("max_reject", C.c_int32), ("robust", C.c_int32),
                 ("robust_from_start", C.c_int32), ("isect_max_iter", C.c_int32),
-                ("isect_tol", C.c_double), ("cond_max", C.c_double), ("precision", C.c_int32),
+                ("isect_tol", C.c_double), ("isect_px_tol", C.c_double), ("cond_max", C.c_double),
+                ("precision", C.c_int32),
                 ("solver", C.c_int32), ("pcg_tol", C.c_double), ("pcg_max_iter", C.c_int32),
                 ("ir_steps", C.c_int32),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", C.c_void_p)]

@@ -264,7 +264,8 @@ def test_batched_independent_blocks(precision, solver):
     g = rpba.Rpba(prob, precision=precision, solver=solver, robust=1, robust_from_start=1)
     assert g.L == o.L == 42
     rg = g.iterate()
-    assert abs(rg["rms"] - ro["rms"]) <= 1e-3
+    info = (rg["rms"], ro["rms"], rg["outer"], ro["outer"], rg["sigma0_hist"], ro["sigma0_hist"])
+    assert abs(rg["rms"] - ro["rms"]) <= 1e-3, info
     if precision == 0:
         assert rg["outer"] == ro["outer"] and rg["inner_total"] == ro["inner_total"]
         assert rg["deleted_points"] == ro["deleted_points"]
@@ -287,3 +288,13 @@ def test_pcg_block_jacobi_solves_the_rcs(name):
         assert np.abs(dc[off:off + n] - dco).max() <= 1e-4 * np.abs(dco).max()
         assert acc[l] == r
         off += n
+
+
+@pytest.mark.parametrize("precision,solver", [(1, 0), (0, 2)])
+def test_batched_independent_blocks_isolated(precision, solver):
+    """FP32 assembly with the FP64 solve, and FP64 assembly with the mixed solve."""
+    prob = synth.config(3, n_blocks=8)
+    ro = oracle.Oracle(prob).run(robust=1, robust_from_start=1)
+    rg = rpba.Rpba(prob, precision=precision, solver=solver, robust=1, robust_from_start=1).iterate()
+    info = (rg["rms"], ro["rms"], rg["outer"], ro["outer"], rg["sigma0_hist"][:4], ro["sigma0_hist"][:4])
+    assert abs(rg["rms"] - ro["rms"]) <= 1e-3, info

@@ -407,14 +407,16 @@ def test_covariance_is_inverse_normal_matrix_and_refined_weights():
         np.testing.assert_allclose(Cov[a] @ N, np.eye(3), atol=1e-6)
         # the adjusted point is stationary: J^T W v = 0
         assert np.abs(grad).max() < 1e-6 * np.abs(N).max()
-        # W^l = N_j - N_j^(l) for every instance, zero for a single-instance point
+        # W^l = N_j - N_j^(l) for every instance, zero for a single-instance point;
+        # W^l comes from the last Gauss-Newton iteration, before its final step
+        # (< 1e-3 px in the image), so it matches N at the final X to ~1e-5
         for q in np.nonzero(ip == j)[0]:
             Wexp = N - Nsub[isub[q]] if len(Nsub) >= 2 else np.zeros((3, 3))
-            np.testing.assert_allclose(sym6_full(Wl[q]), Wexp, atol=1e-6 * np.abs(N).max())
+            np.testing.assert_allclose(sym6_full(Wl[q]), Wexp, atol=2e-5 * np.abs(N).max())
             # invariant W^l + N^(l) = N
             if len(Nsub) >= 2:
                 np.testing.assert_allclose(sym6_full(Wl[q]) + Nsub[isub[q]], N,
-                                           atol=1e-6 * np.abs(N).max())
+                                           atol=2e-5 * np.abs(N).max())
 
 
 def test_intersection_drops_point_behind_camera():
