@@ -345,15 +345,18 @@ def extras(args, prob, ctx, stream, K):
         t0 = time.perf_counter()
         g.intersect()
         rep = g.iterate()
+        own_rms, outer, lm = rep["rms"], rep["outer"], rep["lm_launches"]
         extra = 0
         # keep iterating the same process until the oracle's final RMS is met
         while target is not None and rep["rms"] > target + 1e-3 and extra < 10:
             rep = g.iterate(1)
             extra += 1
+            outer += rep["outer"]
+            lm += rep["lm_launches"]
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        ttr[form] = {"seconds": dt, "final_rms": rep["rms"], "outer": rep["outer"] + extra,
-                     "lm_iterations": rep["lm_launches"], "deleted_points": rep["deleted_points"],
+        ttr[form] = {"seconds": dt, "final_rms": rep["rms"], "own_convergence_rms": own_rms, "outer": outer,
+                     "lm_iterations": lm, "deleted_points": rep["deleted_points"],
                      "extra_outer_after_own_convergence": extra,
                      "matches_oracle": (target is not None and rep["rms"] <= target + 1e-3)}
         g.close()

@@ -94,7 +94,7 @@ typedef struct {
                             Jacobi-scaled RCS with FP64 iterative refinement */
   double pcg_tol;        /* relative residual of the PCG solve, 1e-8 */
   int32_t pcg_max_iter;  /* PCG iteration cap, 500 */
-  int32_t ir_steps;      /* refinement passes of solver 2 after the first solve, 1 */
+  int32_t ir_steps;      /* refinement passes of solver 2 after the first solve, 2 */
   /* optional device allocator (NULL: cudaMalloc / cudaFree) */
   void *(*dev_alloc)(size_t bytes, void *user);
   void (*dev_free)(void *ptr, void *user);
@@ -130,7 +130,8 @@ const char *rpba_last_error(const rpba_ctx *ctx);
 /* Intersection of every active point with all cameras fixed (Eq. bars, the
  * start values for the first bact): Gauss-Newton on X_j, then W^l_j = N_j -
  * N_j^(l) for every instance (Sec. 5.1). Points that do not converge are
- * dropped (Sec. 5.5). */
+ * dropped (Sec. 5.5). Runs in FP64 whatever options.precision says: it runs
+ * once, from the raw input, and both forms start from the same point set. */
 rpba_status rpba_intersect(rpba_ctx *ctx);
 
 /* The RPBA iteration (Sec. 5): up to max_outer (<= 0: options.max_outer)

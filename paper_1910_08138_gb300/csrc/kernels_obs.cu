@@ -467,7 +467,7 @@ __global__ void k_isect_count(const int *state, int n, int *running, int *failed
   if (state[j] == 3) atomicAdd(failed, 1);
 }
 
-rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped) {
+rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped, bool fp64) {
   View v = make_view(ctx);
   if (ctx->N == 0) { if (n_dropped) *n_dropped = 0; return RPBA_OK; }
   RPBA_TRY(cam_prep(ctx));
@@ -479,7 +479,7 @@ rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped) {
   double tol = ctx->opt.isect_tol;
   double px_tol = ctx->opt.isect_px_tol;
   for (int it = 0; it < maxit; it++) {
-    if (ctx->opt.precision == 1) {
+    if (ctx->opt.precision == 1 && !fp64) {
       float *part = (float *)ctx->isect_N;
       RPBA_KERNEL(ctx, "k_isect_inst", k_isect_inst<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(
                                            v, ctx->isect_state, part));

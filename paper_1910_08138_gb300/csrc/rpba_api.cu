@@ -177,7 +177,7 @@ extern "C" void rpba_default_options(rpba_options *o) {
   o->solver = 0;
   o->pcg_tol = 1e-8;
   o->pcg_max_iter = 500;
-  o->ir_steps = 1;
+  o->ir_steps = 2;
 }
 
 extern "C" const char *rpba_last_error(const rpba_ctx *ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
@@ -746,7 +746,11 @@ extern "C" rpba_status rpba_intersect_points(rpba_ctx *h, int32_t tp_only, int32
 
 extern "C" rpba_status rpba_intersect(rpba_ctx *h) {
   CTX_OR_FAIL;
-  RPBA_TRY(launch_intersect(ctx, 0, nullptr));
+  // The first intersection starts from the raw input, far from the solution,
+  // where a point's fate (kept or dropped) decides which local minimum the
+  // blocks descend to. It runs once per run, in FP64 in every form, so that
+  // both forms start from the same point set.
+  RPBA_TRY(launch_intersect(ctx, 0, nullptr, true));
   RPBA_TRY(launch_tp_copies(ctx, 0));
   ctx->intersected = true;
   return sync(ctx);

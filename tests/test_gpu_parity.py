@@ -86,17 +86,24 @@ def test_intersection_covariance_and_refined_weights(name, precision):
         # FP32 Gauss-Newton stops at a looser tolerance: borderline points may differ
         assert (ao != ag).mean() <= 0.01
     act = (ao == 1) & (ag == 1)
+    ids = np.nonzero(act)[0]
+    Co = o.covariance(ids)
     err = np.abs(Xg[act] - Xo[act]).max(1)
     if precision == 0:
         assert err.max() <= 1e-9
     else:
-        # FP32 stops once steps move the image by < 1e-3 px; points pulled by a
-        # gross outlier converge slowest and carry the largest differences
-        assert np.quantile(err, 0.99) <= 2e-5 and err.max() <= 5e-3
+        assert np.quantile(err, 0.99) <= 2e-5
+        # both sides stop once a step moves the image by < 1e-3 px per observation,
+        # possibly at different iterations: a slowly converging point may then still
+        # differ along a weakly determined direction. In image space, with
+        # N_j = C_j^-1, the difference stays a few times the stopping step.
+        d = Xg[act] - Xo[act]
+        nobs = np.bincount(np.asarray(prob["obs_point"]), minlength=o.N)[ids]
+        img = np.einsum("ni,nij,nj->n", d, np.linalg.inv(Co), d) / nobs
+        assert np.sqrt(img.max()) <= 1e-2
     # covariance at the same (oracle) state, per point relative Frobenius error
     sync_state(o, g)
-    ids = np.nonzero(act)[0]
-    Co, Cg = o.covariance(ids), g.covariance(ids)
+    Cg = g.covariance(ids)
     assert rel_frob(Cg, Co, (1, 2)).max() <= (1e-10 if precision == 0 else 1e-4)
     # refined weights W^l (intersection output of each side from the same start)
     _, Wo = o.instance_state()
