@@ -186,6 +186,14 @@ rpba_status rpba_rcs(rpba_ctx *ctx, int32_t l, double lambda, double *S, double 
  * sub-blocks concatenated (6 x n_cams), dx = instance updates (P x 3). */
 rpba_status rpba_lm_step(rpba_ctx *ctx, double lambda, int32_t *accepted, double *F_before,
                          double *F_trial, double *dc, double *dx);
+/* the LM adjustment of every sub-block to its own stop (Eq. bact, with the
+ * damping and stop rules of Sec. 5.5) from the current state, the tie points
+ * held by their current X_TP and W^l: all sub-blocks advance in lock step,
+ * each with its own lambda. iters (nullable, n_subblocks) receives each
+ * sub-block's LM iterations. This is the first stage of every outer
+ * iteration of rpba_iterate. Errors: NOT_CONVERGED if the loop does not end,
+ * CUDA. */
+rpba_status rpba_bact(rpba_ctx *ctx, int32_t *iters);
 
 /* PCG solver (solver = 1): iterations and final relative residual ||r|| / ||y||
  * of every sub-block in the last solve (n_subblocks values each, nullable).

@@ -336,6 +336,35 @@ rpba_status launch_sigma0(Ctx *ctx, double *sigma0, double *rms) {
 // ---------------------------------------------------------------------------
 // intersection (Eq. bars) and refined weights (Sec. 5.1)
 // ---------------------------------------------------------------------------
+// N_j and g_j of point j over all its observations in FP64 at the FP64 X_j
+// (Eq. bars); false when an observation lies behind its camera
+__device__ __noinline__ bool point_normal_fp64(const View &v, int j, double *N, double *g) {
+  for (int e = 0; e < 6; e++) N[e] = 0.0;
+  for (int e = 0; e < 3; e++) g[e] = 0.0;
+  bool ok = true;
+  for (int a = v.pt_inst_ptr[j]; a < v.pt_inst_ptr[j + 1]; a++) {
+    int q = v.pt_inst[a];
+    for (int k = v.inst_obs_ptr[q]; k < v.inst_obs_ptr[q + 1]; k++) {
+      ProjJac<double> pj;
+      double z;
+      obs_proj<double>(v, v.obs_cam[k], v.X + 3 * (size_t)j, nullptr, nullptr, pj, z);
+      if (!(z > 0.0)) { ok = false; continue; }
+      ObsT<double> ob;
+      load_obs<double>(v, k, ob);
+      double r0 = pj.u - ob.x, r1 = pj.v - ob.y, a0[3], a1[3];
+      for (int c = 0; c < 3; c++) {
+        a0[c] = ob.w * (ob.W[0] * pj.Jx[c] + ob.W[1] * pj.Jx[3 + c]);
+        a1[c] = ob.w * (ob.W[1] * pj.Jx[c] + ob.W[2] * pj.Jx[3 + c]);
+      }
+      for (int r = 0; r < 3; r++) {
+        for (int c = r; c < 3; c++) N[s3idx(r, c)] += pj.Jx[r] * a0[c] + pj.Jx[3 + r] * a1[c];
+        g[r] += a0[r] * r0 + a1[r] * r1;
+      }
+    }
+  }
+  return ok;
+}
+
 // per instance of a running point: partial normal matrix N^(l) (sym3) and
 // gradient g^(l) at the current X_j, cameras fixed. flag bit: behind camera.
 template <typename T>
@@ -377,8 +406,9 @@ __global__ void k_isect_inst(View v, const int *state, T *part) {
 // ||dX|| <= tol (1 + ||X||) or when the step moves the point's image
 // residuals by less than px_tol per observation: dX^T N dX <= px_tol^2 n_obs
 // (reachable in FP32, whose residuals carry ~1e-4 px rounding).
-// FP32 form: the 3x3 system is solved in FP32, and again in FP64 when its
-// Frobenius condition number exceeds 1e6.
+// FP32 form: the 3x3 system is solved in FP32; when its Frobenius condition
+// number exceeds 1e6, N_j and g_j are formed again in FP64 from the
+// observations, and the cond_max test and the solve use those.
 template <typename T>
 __global__ void k_isect_point(View v, int *state, int *iter, const T *part, int max_iter, double tol,
                               double px_tol, double cond_max, int last) {
@@ -402,22 +432,26 @@ __global__ void k_isect_point(View v, int *state, int *iter, const T *part, int 
     T inv[6];
     T det = sym3_inv<T>(N, inv);
     T cond = sym3_frob<T>(N) * sym3_frob<T>(inv);
+    double Nimg[6];
     if (sizeof(T) == sizeof(float) && !(cond <= T(1e6))) {
-      double Nd[6], invd[6];
-      for (int e = 0; e < 6; e++) Nd[e] = (double)N[e];
-      double detd = sym3_inv<double>(Nd, invd);
-      fail = !(detd > 0.0) || !(sym3_frob<double>(Nd) * sym3_frob<double>(invd) <= cond_max);
+      // FP32 sums round a nearly singular N_j into a better conditioned one,
+      // so the cond_max test cannot be taken on them: N_j and g_j again in FP64
+      double gd[3], invd[6];
+      fail = !point_normal_fp64(v, j, Nimg, gd);
+      double detd = sym3_inv<double>(Nimg, invd);
+      fail = fail || !(detd > 0.0) || !(sym3_frob<double>(Nimg) * sym3_frob<double>(invd) <= cond_max);
       for (int r = 0; r < 3; r++)
-        d[r] = invd[s3idx(r, 0)] * (double)g[0] + invd[s3idx(r, 1)] * (double)g[1] + invd[s3idx(r, 2)] * (double)g[2];
+        d[r] = invd[s3idx(r, 0)] * gd[0] + invd[s3idx(r, 1)] * gd[1] + invd[s3idx(r, 2)] * gd[2];
     } else {
       fail = !(det > T(0)) || !((double)cond <= cond_max);
       for (int r = 0; r < 3; r++)
         d[r] = (double)(inv[s3idx(r, 0)] * g[0] + inv[s3idx(r, 1)] * g[1] + inv[s3idx(r, 2)] * g[2]);
+      for (int e = 0; e < 6; e++) Nimg[e] = (double)N[e];
     }
     if (px_tol > 0.0) {
-      T dt[3] = {(T)d[0], (T)d[1], (T)d[2]}, Nd3[3];
-      for (int r = 0; r < 3; r++) Nd3[r] = N[s3idx(r, 0)] * dt[0] + N[s3idx(r, 1)] * dt[1] + N[s3idx(r, 2)] * dt[2];
-      nd2_img = (double)(dt[0] * Nd3[0] + dt[1] * Nd3[1] + dt[2] * Nd3[2]);
+      double Nd3[3];
+      for (int r = 0; r < 3; r++) Nd3[r] = Nimg[s3idx(r, 0)] * d[0] + Nimg[s3idx(r, 1)] * d[1] + Nimg[s3idx(r, 2)] * d[2];
+      nd2_img = d[0] * Nd3[0] + d[1] * Nd3[1] + d[2] * Nd3[2];
     }
   }
   bool conv = false;
@@ -445,7 +479,20 @@ __global__ void k_isect_point(View v, int *state, int *iter, const T *part, int 
     for (int a = q0; a < q1; a++) {
       int q = v.pt_inst[a];
       const T *o = part + 10 * (size_t)q;
-      for (int e = 0; e < 6; e++) v.Wl[6 * (size_t)q + e] = tp ? (double)(N[e] - o[e]) : 0.0;
+      if constexpr (sizeof(T) == sizeof(float)) {
+        // FP32 form: W^l as the FP64 sum of the other instances' parts. N - N^(l)
+        // in FP32 cancels when the other sub-blocks' observations are
+        // down-weighted (w = 1e-4), and can lose positive semi-definiteness.
+        double W[6] = {0, 0, 0, 0, 0, 0};
+        for (int b = q0; b < q1; b++) {
+          if (b == a) continue;
+          const T *ob = part + 10 * (size_t)v.pt_inst[b];
+          for (int e = 0; e < 6; e++) W[e] += (double)ob[e];
+        }
+        for (int e = 0; e < 6; e++) v.Wl[6 * (size_t)q + e] = tp ? W[e] : 0.0;
+      } else {
+        for (int e = 0; e < 6; e++) v.Wl[6 * (size_t)q + e] = tp ? (double)(N[e] - o[e]) : 0.0;
+      }
     }
   }
 }
@@ -669,8 +716,40 @@ rpba_status launch_sub_costs(Ctx *ctx, int trial, double *F_dev) {
 // ---------------------------------------------------------------------------
 // normal equations of the sub-blocks and the Schur complement (Sec. 2, 5.5)
 // ---------------------------------------------------------------------------
+// N_XX (+ W^l, damped) and g_X of instance q in FP64 at its FP64 position
+__device__ __noinline__ void instance_normal_fp64(const View &v, int q, double lam, double *N, double *g) {
+  int j = v.inst_pt[q];
+  const double *Xd = v.Xl + 3 * (size_t)q;
+  for (int e = 0; e < 6; e++) N[e] = 0.0;
+  for (int e = 0; e < 3; e++) g[e] = 0.0;
+  for (int k = v.inst_obs_ptr[q]; k < v.inst_obs_ptr[q + 1]; k++) {
+    ProjJac<double> pj;
+    double z;
+    obs_proj<double>(v, v.obs_cam[k], Xd, nullptr, nullptr, pj, z);
+    ObsT<double> ob;
+    load_obs<double>(v, k, ob);
+    double r0 = pj.u - ob.x, r1 = pj.v - ob.y, a0[3], a1[3];
+    for (int c = 0; c < 3; c++) {
+      a0[c] = ob.w * (ob.W[0] * pj.Jx[c] + ob.W[1] * pj.Jx[3 + c]);
+      a1[c] = ob.w * (ob.W[1] * pj.Jx[c] + ob.W[2] * pj.Jx[3 + c]);
+    }
+    for (int r = 0; r < 3; r++) {
+      for (int c = r; c < 3; c++) N[s3idx(r, c)] += pj.Jx[r] * a0[c] + pj.Jx[3 + r] * a1[c];
+      g[r] += a0[r] * r0 + a1[r] * r1;
+    }
+  }
+  const double *Wq = v.Wl + 6 * (size_t)q;
+  double d[3] = {Xd[0] - v.X[3 * j], Xd[1] - v.X[3 * j + 1], Xd[2] - v.X[3 * j + 2]};
+  for (int e = 0; e < 6; e++) N[e] += Wq[e];
+  for (int r = 0; r < 3; r++) g[r] += Wq[s3idx(r, 0)] * d[0] + Wq[s3idx(r, 1)] * d[1] + Wq[s3idx(r, 2)] * d[2];
+  N[0] += lam * N[0]; N[3] += lam * N[3]; N[5] += lam * N[5];
+}
+
 // per instance: N_XX (+ W^l, damped), g_X, Ninv; per observation N_XC = w A_X^T W A_C
-// and Z = Ninv N_XC (both 3x6 row-major)
+// and Z = Ninv N_XC (both 3x6 row-major). FP32 form: when the FP32 N_XX has a
+// Frobenius condition number above 1e5, N_XX and g_X are formed again in FP64
+// and the FP64 inverse is rounded to FP32 (an FP32 inverse would be wrong in
+// the weak direction).
 template <typename T>
 __global__ void k_linearize(View v, const double *lambda, const int *run, T *NXC, T *Z, T *Ninv_out,
                             T *gX_out) {
@@ -722,7 +801,16 @@ __global__ void k_linearize(View v, const double *lambda, const int *run, T *NXC
   T lam = (T)lambda[l];
   N[0] += lam * N[0]; N[3] += lam * N[3]; N[5] += lam * N[5];
   T inv[6];
-  sym3_inv<T>(N, inv);
+  T det = sym3_inv<T>(N, inv);
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (!(det > T(0)) || !(sym3_frob<T>(N) * sym3_frob<T>(inv) <= T(1e5))) {
+      double Nd[6], gd[3], invd[6];
+      instance_normal_fp64(v, q, lambda[l], Nd, gd);
+      sym3_inv<double>(Nd, invd);
+      for (int e = 0; e < 6; e++) inv[e] = (T)invd[e];
+      for (int e = 0; e < 3; e++) g[e] = (T)gd[e];
+    }
+  }
   for (int e = 0; e < 6; e++) Ninv_out[6 * (size_t)q + e] = inv[e];
   for (int e = 0; e < 3; e++) gX_out[3 * (size_t)q + e] = g[e];
   for (int k = k0; k < k1; k++) {

@@ -975,6 +975,17 @@ static rpba_status run_bact(Ctx *ctx, int *inner_total, int *launches) {
   return RPBA_OK;
 }
 
+extern "C" rpba_status rpba_bact(rpba_ctx *h, int32_t *iters) {
+  CTX_OR_FAIL;
+  int tot = 0, launches = 0;
+  RPBA_TRY(run_bact(ctx, &tot, &launches));
+  if (iters && ctx->L) {
+    RPBA_CUDA(cudaMemcpyAsync(iters, ctx->lm_it, ctx->L * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    RPBA_TRY(sync(ctx));
+  }
+  return RPBA_OK;
+}
+
 extern "C" rpba_status rpba_iterate(rpba_ctx *h, int32_t max_outer, rpba_report *rep) {
   CTX_OR_FAIL;
   const rpba_options &o = ctx->opt;

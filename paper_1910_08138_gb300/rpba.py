@@ -108,6 +108,7 @@ def load(build_if_missing: bool = True):
         "rpba_sub_costs": (C.c_int, [vp, _dp]),
         "rpba_rcs": (C.c_int, [vp, C.c_int32, C.c_double, _dp, _dp]),
         "rpba_lm_step": (C.c_int, [vp, C.c_double, _ip, _dp, _dp, _dp, _dp]),
+        "rpba_bact": (C.c_int, [vp, _ip]),
         "rpba_profile_enable": (C.c_int, [vp, C.c_int32]),
         "rpba_profile_read": (C.c_int, [vp, C.c_int32, C.c_char_p, _dp, C.POINTER(C.c_int64), _ip,
                                         C.POINTER(C.c_int64)]),
@@ -371,6 +372,11 @@ class Rpba:
         dc, dx = np.zeros(6 * self.M), np.zeros((self.P, 3))
         self._c(load().rpba_lm_step(self._h, float(lam), _i(acc), _d(Fb), _d(Ft), _d(dc), _d(dx)))
         return acc, Fb, Ft, dc, dx
+
+    def bact(self):
+        it = np.zeros(self.L, np.int32)
+        self._c(load().rpba_bact(self._h, _i(it)))
+        return it
 
     def solver_stats(self):
         it, rr = np.zeros(self.L, np.int32), np.zeros(self.L)

@@ -223,6 +223,20 @@ def merge_blocks(blocks):
 # --------------------------------------------------------------------------
 # named workloads
 # --------------------------------------------------------------------------
+def multi_block_member(b: int, scale: float = 1.0):
+    """Block b of the 64-block workload (config 3), on its own: 20..400 cameras
+    (log-uniform), 50..200 points per camera, 3..6 obs/point, 2..8 sub-blocks."""
+    rb = np.random.Generator(np.random.PCG64(SEED_BASE + 100 * 3 + 1 + b))
+    Mb = int(round(np.exp(rb.uniform(np.log(20), np.log(400)))))
+    ppc = rb.uniform(50, 200)
+    Lb = int(rb.integers(2, 9))
+    ny = int(np.ceil(np.sqrt(Mb)))
+    nx = int(np.ceil(Mb / ny))
+    Nb = max(8, int(round(Mb * ppc / 4.5 * scale)))
+    return grid_block(rb, nx, ny, 4.0, 30.0, Nb, lambda r, n: r.integers(3, 7, size=n), 0.5, 0.02,
+                      oblique_deg=30.0, nadir_every=5, n_cams=Mb, runs=_even_runs(Mb, Lb))
+
+
 def config(c: int, scale: float = 1.0, n_blocks: int = 64):
     """The five benchmark blocks (c = 1..5); `scale` < 1 shrinks point counts.
 
@@ -246,20 +260,7 @@ def config(c: int, scale: float = 1.0, n_blocks: int = 64):
                           oblique_deg=30.0, nadir_every=5,
                           runs=[60, 80, 100, 120, 140, 160, 140, 200])
     if c == 3:
-        blocks = []
-        for b in range(n_blocks):
-            rb = np.random.Generator(np.random.PCG64(SEED_BASE + 100 * c + 1 + b))
-            Mb = int(round(np.exp(rb.uniform(np.log(20), np.log(400)))))
-            ppc = rb.uniform(50, 200)
-            Lb = int(rb.integers(2, 9))
-            ny = int(np.ceil(np.sqrt(Mb)))
-            nx = int(np.ceil(Mb / ny))
-            Nb = max(8, int(round(Mb * ppc / 4.5 * scale)))
-            blocks.append(grid_block(rb, nx, ny, 4.0, 30.0, Nb,
-                                     lambda r, n: r.integers(3, 7, size=n), 0.5, 0.02,
-                                     oblique_deg=30.0, nadir_every=5, n_cams=Mb,
-                                     runs=_even_runs(Mb, Lb)))
-        return merge_blocks(blocks)
+        return merge_blocks([multi_block_member(b, scale) for b in range(n_blocks)])
     if c == 4:
         # strips run along y; 60 % forward overlap of the 45 m along-track footprint
         # (18 m base), 30 % side overlap of the 60 m across-track footprint (42 m).
