@@ -319,3 +319,30 @@ def tiny(seed=0, nx=3, ny=2, n_points=30, opp=4, runs=None, sigma_px=0.5, outlie
 
 PROBLEM_KEYS = ("cam_pose", "cam_intr", "points", "obs_cam", "obs_point", "obs_xy",
                 "obs_winv", "cam_subblock", "cam_block")
+
+
+# --------------------------------------------------------------------------
+# RCS-shaped matrices for the learned preconditioner
+# --------------------------------------------------------------------------
+def rcs_like_systems(seed: int, sizes=(12, 20, 7), points_per_cam: int = 6, n_probes: int = 4):
+    """Random symmetric positive definite 6n x 6n matrices with the block
+    structure of a reduced camera system: cameras on a strip, each "point"
+    couples 2..4 neighbouring cameras through a rank-3 term, camera scales
+    spread over two decades. Returns a list of (S, z) with z the Gaussian
+    probe vectors (n_probes x 6n)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for n in sizes:
+        scale = np.repeat(np.exp(rng.uniform(0.0, np.log(100.0), n)), 6) * rng.uniform(0.5, 2.0, 6 * n)
+        S = np.zeros((6 * n, 6 * n))
+        for _ in range(points_per_cam * n):
+            c0 = int(rng.integers(0, n))
+            k = int(rng.integers(2, 5))
+            cams = sorted({min(n - 1, max(0, c0 + int(d))) for d in rng.integers(-2, 3, size=k)} | {c0})
+            idx = np.concatenate([np.arange(6 * c, 6 * c + 6) for c in cams])
+            G = rng.normal(size=(3, idx.size)) * np.sqrt(scale[idx])
+            S[np.ix_(idx, idx)] += G.T @ G
+        S += np.diag(1e-3 * np.diag(S).mean() + 1e-2 * np.diag(S))
+        z = rng.normal(size=(n_probes, 6 * n))
+        out.append((S, z))
+    return out
