@@ -1,14 +1,14 @@
-"""FP64 oracle of the learned block preconditioner for PCG on the reduced
-camera system (RCS) of a sub-block.
+"""FP64 oracle of the learned preconditioner for PCG on the reduced camera
+system (RCS) of a sub-block.
 
 TEST INFRASTRUCTURE ONLY: the tests load this module to check the CUDA
 network kernels; nothing in the library package imports it.
 
 The paper solves the RCS with conjugate gradients and block-Jacobi
-preconditioning (Sec. 5.5: the 6x6 camera blocks on the diagonal). This
-network predicts a correction of each camera's block so that the
-preconditioned system is closer to the identity. Definitions, in the order
-they are applied:
+preconditioning (Sec. 5.5: the inverses of the 6x6 camera blocks S_ii). This
+network predicts a correction of each camera's block and a coupling gain for
+every pair of cameras that share points, forming a factorised sparse
+approximate inverse P^-1 = G^T G. Definitions, in the order they are applied:
 
 Graph. One node per camera of the system (S of size 6n x 6n, block (i, j) the
 6x6 block of cameras i and j). An edge joins i != j when S_ij has a non-zero
@@ -24,19 +24,30 @@ Network (hidden width 64, three message-passing layers):
   h0   = relu(W0 x + b0)
   m_t  = sum_{j ~ i} e_ij h_{t-1, j}
   h_t  = relu(A_t h_{t-1} + B_t m_t + c_t),    t = 1, 2, 3
-  C    = Wo h3 + bo           (21 values: a lower-triangular 6x6, row by row)
+  C_i  = Wo h3_i + bo                  (21 values: a lower-triangular 6x6, row by row)
+  q_ij = ws . (h3_i + h3_j) + wp . (h3_i * h3_j) + we e_ij + bq   (every edge i > j)
 
-Preconditioner block: E = 0.5 tanh(C) (lower triangular, diagonal included),
-L = chol(B_i), P_i = L (I + E)(I + E)^T L^T, so P_i is SPD whenever
-|E_kk| < 1, and P_i = B_i (block-Jacobi) when the output layer is zero.
-P_i^-1 = G^T G with G = (I + E)^-1 L^-1.
+Preconditioner. L_i = chol(B_i), M_i = I + 0.5 tanh(C_i) (lower triangular),
+gamma_ij = tanh(q_ij), N_ij = gamma_ij L_i^-1 S_ij L_j^-T for i > j (the
+normalised coupling), and
+  G = M^-1 (I - N) L^-1      (block lower triangular, M, L block diagonal)
+  P^-1 = G^T G.
+P^-1 is SPD for every parameter value; with a zero output layer and zero
+edge head it is block-Jacobi, blockdiag(B_i)^-1.
 
-Loss over a set of systems with probe vectors z^p (u^p = S z^p):
-  loss = sum_sys sum_p sum_i ||P_i^-1 u_i^p - z_i^p||^2 / sum ||z^p||^2
-(for a block-diagonal P, (P^-1 S z)_i = P_i^-1 (S z)_i).
+Loss (Kaporin's condition number of A = G S G^T, per unit of dimension d=6n,
+less its constant log det S):
+  l = log(tr(A) / d) - (1/d) log det A
+    = log(tr(A) / d) + (2/d) sum_i (log det M_i + log det L_i) - (1/d) log det S
+with tr(A) estimated from the probe vectors z^p (Hutchinson):
+  tr(A) ~ (1/n_p) sum_p v_p^T S v_p,   v_p = G^T z_p.
+The reported loss is l + (1/d) log det S averaged over the systems (the
+constant dropped), so it equals log(T/d) + (2/d) sum_i log det(M_i L_i).
+K >= 1 always; block-Jacobi minimises it among block-diagonal
+preconditioners, so what the network gains comes from the coupling N.
 
 Parameters are one flat vector in the order W0, b0, (A_t, B_t, c_t) for
-t = 1..3, Wo, bo; matrices row-major (out x in).
+t = 1..3, Wo, bo, ws, wp, we, bq; matrices row-major (out x in).
 """
 
 from __future__ import annotations
@@ -55,8 +66,12 @@ def param_shapes():
     sh = [("W0", (HID, NF)), ("b0", (HID,))]
     for t in range(1, LAYERS + 1):
         sh += [(f"A{t}", (HID, HID)), (f"B{t}", (HID, HID)), (f"c{t}", (HID,))]
-    sh += [("Wo", (NF, HID)), ("bo", (NF,))]
+    sh += [("Wo", (NF, HID)), ("bo", (NF,)), ("ws", (HID,)), ("wp", (HID,)), ("we", (1,)), ("bq", (1,))]
     return sh
+
+
+# parameters applied as matrices (BF16 in the CUDA kernels); the rest are biases
+MATRICES = {"W0", "A1", "B1", "A2", "B2", "A3", "B3", "Wo"}
 
 
 def param_count():
@@ -89,13 +104,13 @@ def to_bf16(w):
 # ---------------------------------------------------------------------------
 def _sym(S):
     """The symmetric matrix held by the lower triangle of S."""
-    Lw = np.tril(S)
-    return Lw + np.tril(S, -1).T
+    return np.tril(S) + np.tril(S, -1).T
 
 
 def graph(S, n):
-    """Features, CSR adjacency (sorted neighbours), edge weights and the
-    Cholesky factors of the diagonal blocks of one system."""
+    """Features, CSR adjacency (sorted neighbours), edge weights, the
+    Cholesky factors of the diagonal blocks and the normalised couplings of
+    one system."""
     A = _sym(np.asarray(S, dtype=np.float64)[:6 * n, :6 * n])
     B = [A[6 * i:6 * i + 6, 6 * i:6 * i + 6] for i in range(n)]
     logd = np.array([np.log(np.diag(b)) for b in B]).reshape(n, 6)
@@ -106,7 +121,11 @@ def graph(S, n):
         d = np.sqrt(np.diag(b))
         x[i, 6:] = [b[r, c] / (d[r] * d[c]) for r, c in STRICT]
     nb = np.array([np.linalg.norm(b) for b in B])
+    L = np.array([np.linalg.cholesky(b) for b in B]).reshape(n, 6, 6)
+    Li = np.array([np.linalg.inv(l) for l in L]).reshape(n, 6, 6)
     ptr, adj, e = [0], [], []
+    lower = []                          # (i, j) with i > j, in CSR order of i
+    Shat = []
     for i in range(n):
         for j in range(n):
             if j == i:
@@ -115,13 +134,16 @@ def graph(S, n):
             if np.any(blk != 0.0):
                 adj.append(j)
                 e.append(np.linalg.norm(blk) / np.sqrt(nb[i] * nb[j]))
+                if j < i:
+                    lower.append((i, j, len(adj) - 1))
+                    Shat.append(Li[i] @ blk @ Li[j].T)
         ptr.append(len(adj))
-    L = np.array([np.linalg.cholesky(b) for b in B]).reshape(n, 6, 6)
-    return dict(x=x, ptr=np.array(ptr), adj=np.array(adj, dtype=np.int64), e=np.array(e), L=L, A=A)
+    return dict(x=x, ptr=np.array(ptr), adj=np.array(adj, dtype=np.int64), e=np.array(e), L=L, Li=Li, A=A,
+                lower=lower, Shat=np.array(Shat).reshape(-1, 6, 6), n=n)
 
 
 # ---------------------------------------------------------------------------
-# forward, head, loss and backward
+# forward
 # ---------------------------------------------------------------------------
 def _aggregate(ptr, adj, e, h):
     m = np.zeros_like(h)
@@ -141,7 +163,10 @@ def forward(w, g):
         m.append(mt)
         h.append(np.maximum(h[-1] @ p[f"A{t}"].T + mt @ p[f"B{t}"].T + p[f"c{t}"], 0.0))
     C = h[-1] @ p["Wo"].T + p["bo"]
-    return dict(h=h, m=m, C=C)
+    hl = h[-1]
+    q = np.array([p["ws"] @ (hl[i] + hl[j]) + p["wp"] @ (hl[i] * hl[j]) + p["we"][0] * g["e"][a] + p["bq"][0]
+                  for i, j, a in g["lower"]])
+    return dict(h=h, m=m, C=C, q=q)
 
 
 def lower(c):
@@ -152,58 +177,107 @@ def lower(c):
     return M
 
 
-def block_inverse(C_i, L_i):
-    """P_i^-1 = G^T G, G = (I + E)^-1 L^-1, E = 0.5 tanh(C)."""
-    M = np.eye(6) + lower(EPS * np.tanh(C_i))
-    G = np.linalg.solve(M, np.linalg.inv(L_i))
-    return G.T @ G
+def factor(w, g, f=None):
+    """Dense G = M^-1 (I - N) L^-1 of one system."""
+    f = forward(w, g) if f is None else f
+    n = g["n"]
+    Mi = np.zeros((6 * n, 6 * n))
+    Lb = np.zeros((6 * n, 6 * n))
+    N = np.zeros((6 * n, 6 * n))
+    for i in range(n):
+        Mi[6 * i:6 * i + 6, 6 * i:6 * i + 6] = np.linalg.inv(np.eye(6) + lower(EPS * np.tanh(f["C"][i])))
+        Lb[6 * i:6 * i + 6, 6 * i:6 * i + 6] = g["Li"][i]
+    for k, (i, j, _) in enumerate(g["lower"]):
+        N[6 * i:6 * i + 6, 6 * j:6 * j + 6] = np.tanh(f["q"][k]) * g["Shat"][k]
+    return Mi @ (np.eye(6 * n) - N) @ Lb
 
 
-def preconditioner(w, g):
-    f = forward(w, g)
-    return np.array([block_inverse(f["C"][i], g["L"][i]) for i in range(g["x"].shape[0])])
+def precondition(w, g, r):
+    """P^-1 r = G^T G r for one system."""
+    G = factor(w, g)
+    return G.T @ (G @ r)
+
+
+# ---------------------------------------------------------------------------
+# loss and backward
+# ---------------------------------------------------------------------------
+def system_loss(w, g, z, f=None):
+    f = forward(w, g) if f is None else f
+    G = factor(w, g, f)
+    d = 6 * g["n"]
+    V = z @ G                                 # rows v_p^T = (G^T z_p)^T
+    T = np.mean(np.einsum("pi,ij,pj->p", V, g["A"], V))
+    ld = 0.0
+    for i in range(g["n"]):
+        M = np.eye(6) + lower(EPS * np.tanh(f["C"][i]))
+        ld += np.sum(np.log(np.diag(M))) + np.sum(np.log(np.diag(g["L"][i])))
+    return np.log(T / d) + 2.0 * ld / d
+
+
+def loss(w, systems):
+    return float(np.mean([system_loss(w, g, z) for g, z in systems]))
 
 
 def loss_and_grad(w, systems):
-    """systems: list of (graph, z) with z of shape (n_probes, 6 n).
-    Returns the loss and its gradient with respect to the flat parameters."""
+    """systems: list of (graph, z), z of shape (n_probes, 6 n). Mean over the
+    systems of the Kaporin loss, and its gradient with respect to the flat
+    parameters."""
     p = unpack(w)
     grads = {k: np.zeros_like(v) for k, v in p.items()}
-    num, den = 0.0, 0.0
-    cache = []
+    total = 0.0
+    ns = len(systems)
     for g, z in systems:
         f = forward(w, g)
-        n = g["x"].shape[0]
-        U = z @ g["A"]                     # rows u^p = S z^p (S symmetric)
+        n, d, npr = g["n"], 6 * g["n"], z.shape[0]
+        Mb = [np.eye(6) + lower(EPS * np.tanh(f["C"][i])) for i in range(n)]
+        gam = np.tanh(f["q"])
+        Nk = [gam[k] * g["Shat"][k] for k in range(len(g["lower"]))]
+        # forward per probe: t = M^-T z, s = (I - N)^T t, v = L^-T s, u = S v
+        T = 0.0
+        cache = []
+        for zp in z:
+            t = np.concatenate([np.linalg.solve(Mb[i].T, zp[6 * i:6 * i + 6]) for i in range(n)])
+            s = t.copy()
+            for k, (i, j, _) in enumerate(g["lower"]):
+                s[6 * j:6 * j + 6] -= Nk[k].T @ t[6 * i:6 * i + 6]
+            v = np.concatenate([np.linalg.solve(g["L"][i].T, s[6 * i:6 * i + 6]) for i in range(n)])
+            u = g["A"] @ v
+            T += v @ u / npr
+            cache.append((t, s, v, u))
+        ld = sum(np.sum(np.log(np.diag(Mb[i]))) + np.sum(np.log(np.diag(g["L"][i]))) for i in range(n))
+        total += (np.log(T / d) + 2.0 * ld / d) / ns
+        # backward
+        Mbar = [np.zeros((6, 6)) for _ in range(n)]
+        gbar = np.zeros(len(g["lower"]))
+        for t, s, v, u in cache:
+            vb = (2.0 / (npr * T)) * u / ns
+            sb = np.concatenate([np.linalg.solve(g["L"][i], vb[6 * i:6 * i + 6]) for i in range(n)])
+            tb = sb.copy()
+            for k, (i, j, _) in enumerate(g["lower"]):
+                tb[6 * i:6 * i + 6] -= Nk[k] @ sb[6 * j:6 * j + 6]
+                gbar[k] -= t[6 * i:6 * i + 6] @ g["Shat"][k] @ sb[6 * j:6 * j + 6]
+            for i in range(n):
+                ti, tbi = t[6 * i:6 * i + 6], tb[6 * i:6 * i + 6]
+                Mbar[i] -= np.outer(ti, np.linalg.solve(Mb[i], tbi))
         dC = np.zeros((n, NF))
         for i in range(n):
-            L = g["L"][i]
+            Mbar[i] += np.diag(2.0 / (d * ns) / np.diag(Mb[i]))
             th = np.tanh(f["C"][i])
-            M = np.eye(6) + lower(EPS * th)
-            Mbar = np.zeros((6, 6))
-            for pz, pu in zip(z, U):
-                zi, ui = pz[6 * i:6 * i + 6], pu[6 * i:6 * i + 6]
-                a = np.linalg.solve(L, ui)
-                y1 = np.linalg.solve(M, a)
-                y2 = np.linalg.solve(M.T, y1)
-                r = np.linalg.solve(L.T, y2) - zi
-                num += r @ r
-                # backward of r = L^-T M^-T M^-1 a - z (the 1/den scale is applied below)
-                rb = 2.0 * r
-                y2b = np.linalg.solve(L, rb)
-                y1b = np.linalg.solve(M, y2b)
-                Mbar -= np.outer(y2, y1b)
-                ab = np.linalg.solve(M.T, y1b)
-                Mbar -= np.outer(ab, y1)
-            Ebar = np.array([Mbar[r, c] for r, c in TRIL])
-            dC[i] = Ebar * EPS * (1.0 - th * th)
-        den += float(np.sum(z * z))
-        cache.append((g, f, dC))
-    for g, f, dC in cache:
+            dC[i] = np.array([Mbar[i][r, c] for r, c in TRIL]) * EPS * (1.0 - th * th)
+        qb = gbar * (1.0 - gam * gam)
+        # edge head
         h, m = f["h"], f["m"]
-        grads["Wo"] += dC.T @ h[-1]
-        grads["bo"] += dC.sum(0)
+        hl = h[-1]
         dh = dC @ p["Wo"]
+        grads["Wo"] += dC.T @ hl
+        grads["bo"] += dC.sum(0)
+        for k, (i, j, a) in enumerate(g["lower"]):
+            grads["ws"] += qb[k] * (hl[i] + hl[j])
+            grads["wp"] += qb[k] * hl[i] * hl[j]
+            grads["we"][0] += qb[k] * g["e"][a]
+            grads["bq"][0] += qb[k]
+            dh[i] += qb[k] * (p["ws"] + p["wp"] * hl[j])
+            dh[j] += qb[k] * (p["ws"] + p["wp"] * hl[i])
         for t in range(LAYERS, 0, -1):
             dz = dh * (h[t] > 0.0)
             grads[f"A{t}"] += dz.T @ h[t - 1]
@@ -214,9 +288,4 @@ def loss_and_grad(w, systems):
         dz0 = dh * (h[0] > 0.0)
         grads["W0"] += dz0.T @ g["x"]
         grads["b0"] += dz0.sum(0)
-    grad = pack(grads) / den
-    return num / den, grad
-
-
-def loss(w, systems):
-    return loss_and_grad(w, systems)[0]
+    return total, pack(grads)
