@@ -91,7 +91,9 @@ typedef struct {
   int32_t precision;     /* 0: all FP64 ("plain"); 1: FP32 bulk, FP64 solve/reductions */
   int32_t solver;        /* RCS solve: 0 FP64 Cholesky; 1 FP64 PCG with block-Jacobi
                             preconditioning (Sec. 5.5) to pcg_tol; 2 FP32 Cholesky of the
-                            Jacobi-scaled RCS with FP64 iterative refinement */
+                            Jacobi-scaled RCS with FP64 iterative refinement; 3 FP64 PCG
+                            with the learned block preconditioner (rpba_set_gnn_weights),
+                            block-Jacobi PCG again for a sub-block it leaves above pcg_tol */
   double pcg_tol;        /* relative residual of the PCG solve, 1e-8 */
   int32_t pcg_max_iter;  /* PCG iteration cap, 500 */
   int32_t ir_steps;      /* refinement passes of solver 2 after the first solve, 2 */
@@ -195,10 +197,82 @@ rpba_status rpba_lm_step(rpba_ctx *ctx, double lambda, int32_t *accepted, double
  * CUDA. */
 rpba_status rpba_bact(rpba_ctx *ctx, int32_t *iters);
 
-/* PCG solver (solver = 1): iterations and final relative residual ||r|| / ||y||
- * of every sub-block in the last solve (n_subblocks values each, nullable).
- * Errors: STATE when the context does not use the PCG solver. */
+/* PCG solvers (solver = 1 or 3): iterations and final relative residual
+ * ||r|| / ||y|| of every sub-block in the last PCG pass (n_subblocks values
+ * each, nullable). Errors: STATE when the context does not use PCG. */
 rpba_status rpba_solver_stats(rpba_ctx *ctx, int32_t *iters, double *relres);
+/* solver 3: number of sub-block solves, since create, that the learned
+ * preconditioner left above pcg_tol and block-Jacobi PCG solved again */
+rpba_status rpba_solver_fallbacks(rpba_ctx *ctx, int64_t *n);
+
+/* ---- learned preconditioner (solver 3) ------------------------------------
+ * The paper preconditions CG on the RCS with the inverses of the 6x6 camera
+ * blocks S_ii (block-Jacobi, Sec. 5.5). A graph network over the cameras of a
+ * sub-block (edge i-j where S_ij != 0, i.e. the cameras share a point)
+ * predicts a correction of every camera block and a gain for every camera
+ * pair; the paper has no such network.
+ *   features x_i (21): log S_ii[k,k] minus its mean over the sub-block (6),
+ *     S_ii[k,l] / sqrt(S_ii[k,k] S_ii[l,l]) for k > l, row by row (15)
+ *   edge weight e_ij = ||S_ij||_F / sqrt(||S_ii||_F ||S_jj||_F)
+ *   h0 = relu(W0 x + b0); h_t = relu(A_t h_{t-1} + B_t sum_j e_ij h_{t-1,j} + c_t),
+ *   t = 1..3 (width 64); C_i = Wo h3_i + bo (21 entries of a lower-triangular
+ *   6x6, row by row); q_ij = ws.(h3_i + h3_j) + wp.(h3_i * h3_j) + we e_ij + bq
+ *   M_i = I + 0.5 tanh(C_i), L_i = chol(S_ii), N_ij = tanh(q_ij) L_i^-1 S_ij L_j^-T
+ *   (i > j in the sub-block's camera order), G = M^-1 (I - N) L^-1,
+ *   P^-1 = G^T G: SPD, and block-Jacobi when both output heads are zero.
+ * Parameters: one FP32 vector of rpba_gnn_param_count() values in the order
+ * W0 (64x21), b0, then for t = 1..3 A_t (64x64), B_t (64x64), c_t, then Wo
+ * (21x64), bo, ws (64), wp (64), we, bq; matrices row-major. The matrices
+ * W0, A_t, B_t, Wo are applied in BF16, activations accumulate in FP32; the
+ * factor G is formed in FP64 and applied in FP32; PCG vectors are FP64. */
+#define RPBA_GNN_FEATURES 21
+#define RPBA_GNN_HIDDEN 64
+#define RPBA_GNN_LAYERS 3
+int32_t rpba_gnn_param_count(void);
+/* copies the parameters (host, rpba_gnn_param_count() floats) into a context
+ * created with solver = 3. Errors: INVALID_ARG (count), STATE (other solver). */
+rpba_status rpba_set_gnn_weights(rpba_ctx *ctx, const float *w, int32_t n);
+
+/* Trainer: a network, a dataset of systems and Adam, on the current device.
+ * Loss: the mean over the systems of Kaporin's condition number of
+ * A = G S G^T per unit of dimension d, less its constant log det S / d:
+ *   log(T / d) + (2 / d) sum_i log det(M_i L_i),  T = (1/n_p) sum_p v_p^T S v_p,
+ *   v_p = G^T z_p, with the system's Gaussian probe vectors z_p (T estimates
+ *   tr A). Block-Jacobi minimises it among block-diagonal preconditioners. */
+typedef struct rpba_gnn rpba_gnn;
+/* He-normal hidden layers from `seed` (splitmix64, Box-Muller), zero output
+ * layer: the new network is block-Jacobi. */
+rpba_status rpba_gnn_create(uint64_t seed, rpba_gnn **out);
+void rpba_gnn_destroy(rpba_gnn *g);
+const char *rpba_gnn_last_error(const rpba_gnn *g);
+rpba_status rpba_gnn_get_weights(rpba_gnn *g, float *w);
+/* also resets the Adam moments */
+rpba_status rpba_gnn_set_weights(rpba_gnn *g, const float *w);
+/* adds one system: S (HOST, n_cams*6 rows of leading dimension ld >= 6 n_cams,
+ * row-major; only the lower triangle is read), z (HOST, n_probes x 6 n_cams).
+ * Every system of a dataset has the same n_probes. Errors: INVALID_ARG,
+ * NUMERIC when a diagonal camera block is not positive definite. */
+rpba_status rpba_gnn_add_system(rpba_gnn *g, int32_t n_cams, const double *S, int32_t ld, int32_t n_probes,
+                                const double *z);
+/* adds the damped RCS (damping lambda) of every sub-block of a context at its
+ * current state, with n_probes probes drawn from `seed`. The context must be
+ * on the trainer's device. */
+rpba_status rpba_gnn_add_rcs(rpba_gnn *g, rpba_ctx *ctx, double lambda, int32_t n_probes, uint64_t seed);
+rpba_status rpba_gnn_dataset_size(rpba_gnn *g, int32_t *n_nodes, int32_t *n_edges, int32_t *n_systems);
+/* the dataset's graph: x n_nodes x 21, ptr n_nodes + 1, adj and e n_edges
+ * (nodes of all systems numbered consecutively); HOST, nullable */
+rpba_status rpba_gnn_graph(rpba_gnn *g, float *x, int32_t *ptr, int32_t *adj, float *e);
+/* z = P^-1 r for every dataset system at the current weights (HOST, r and z
+ * n_nodes x 6: the systems' vectors one after another) */
+rpba_status rpba_gnn_precondition(rpba_gnn *g, const double *r, double *z);
+/* loss and its gradient (HOST, rpba_gnn_param_count() floats, nullable) */
+rpba_status rpba_gnn_loss_grad(rpba_gnn *g, double *loss, float *grad);
+/* `steps` Adam steps (beta 0.9, 0.999, eps 1e-8) with learning rate lr over
+ * the whole dataset; loss_hist (nullable, steps values) the loss before each.
+ * probe_seed != 0 draws new probe vectors before every step (splitmix64 of
+ * (probe_seed, Adam step, element), Box-Muller), so that the network cannot
+ * fit a fixed set of probes; 0 keeps the dataset's probes. */
+rpba_status rpba_gnn_train(rpba_gnn *g, int32_t steps, float lr, uint64_t probe_seed, double *loss_hist);
 
 /* ---- measurement ------------------------------------------------------- */
 

@@ -503,6 +503,7 @@ __global__ void k_mixed_update(const int *run, const int *fail, const int *voff,
 
 rpba_status launch_solve_rcs(Ctx *ctx, const int *run_dev, int *fail_dev) {
   if (ctx->opt.solver == 1) return launch_pcg_blockjacobi(ctx, run_dev, fail_dev);
+  if (ctx->opt.solver == 3) return launch_pcg_learned(ctx, run_dev, fail_dev);
   RPBA_CUDA(cudaMemsetAsync(fail_dev, 0, ctx->L * sizeof(int), ctx->stream));
   int T_max = ctx->max_tiles;
   if (T_max == 0) return RPBA_OK;

@@ -8,8 +8,8 @@
 // sub-block, q += S p with FP64 atomics) and k_pcg_step (one CTA per
 // sub-block: alpha = rz / p.q, x += alpha p, r -= alpha q, z = M^-1 r,
 // beta = rz' / rz, p = z + beta p, convergence ||r|| <= tol ||y||).
-// The block preconditioner M_i^-1 is the inverse of the diagonal camera block
-// (block-Jacobi); any other 6x6 SPD block inverse can be applied the same way.
+// The preconditioner is the inverse of the diagonal camera blocks
+// (block-Jacobi), or the learned factorised inverse G^T G (solver 3).
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -219,6 +219,205 @@ __global__ void __launch_bounds__(256) k_pcg_step(const int *sub_cam_ptr, const 
   }
 }
 
+// ---- learned preconditioner: the PCG step split around a grid-wide apply ----
+// start without the preconditioner: x = 0, r = y, z = p = 0, |y|
+__global__ void __launch_bounds__(256) k_pcg_init_a(const int *run, const int *fail, const int *sub_cam_ptr,
+                                                    const int *voff, const int *npad, const double *y, double *x,
+                                                    double *r, double *z, double *p, double *st, int *live) {
+  int l = blockIdx.x;
+  int ok = run[l] && !fail[l];
+  if (threadIdx.x == 0) live[l] = ok;
+  if (!ok) return;
+  int n = 6 * (sub_cam_ptr[l + 1] - sub_cam_ptr[l]);
+  int o = voff[l];
+  double v1[1] = {0.0};
+  for (int e = threadIdx.x; e < npad[l]; e += blockDim.x) {
+    x[o + e] = 0.0;
+    r[o + e] = e < n ? y[o + e] : 0.0;
+    z[o + e] = 0.0;
+    p[o + e] = 0.0;
+    if (e < n) v1[0] += y[o + e] * y[o + e];
+  }
+  double s[1];
+  cta_sum<1>(v1, s);
+  if (threadIdx.x == 0) {
+    st[4 * l + 1] = sqrt(s[0]);
+    st[4 * l + 2] = s[0] > 0.0 ? 1.0 : 0.0;
+    st[4 * l + 3] = 0.0;
+    if (!(s[0] > 0.0)) live[l] = 0;
+  }
+}
+
+// after z = M^-1 r: p = z, rz
+__global__ void __launch_bounds__(256) k_pcg_init_b(const int *sub_cam_ptr, const int *voff, const double *r,
+                                                    const double *z, double *p, double *st, const int *live) {
+  int l = blockIdx.x;
+  if (!live[l]) return;
+  int n = 6 * (sub_cam_ptr[l + 1] - sub_cam_ptr[l]);
+  int o = voff[l];
+  double v1[1] = {0.0};
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    p[o + e] = z[o + e];
+    v1[0] += r[o + e] * z[o + e];
+  }
+  double s[1];
+  cta_sum<1>(v1, s);
+  if (threadIdx.x == 0) st[4 * l] = s[0];
+}
+
+// alpha = rz / p.q, x += alpha p, r -= alpha q, convergence on ||r||
+__global__ void __launch_bounds__(256) k_pcg_alpha(const int *sub_cam_ptr, const int *voff, double tol, double *x,
+                                                   double *r, const double *p, const double *q, double *st,
+                                                   int *live) {
+  int l = blockIdx.x;
+  if (!live[l]) return;
+  int n = 6 * (sub_cam_ptr[l + 1] - sub_cam_ptr[l]);
+  int o = voff[l];
+  double v1[1] = {0.0};
+  for (int e = threadIdx.x; e < n; e += blockDim.x) v1[0] += p[o + e] * q[o + e];
+  double pq[1];
+  cta_sum<1>(v1, pq);
+  if (!(pq[0] > 0.0)) {  // breakdown: keep the current iterate
+    if (threadIdx.x == 0) live[l] = 0;
+    return;
+  }
+  double alpha = st[4 * l] / pq[0];
+  double v2[1] = {0.0};
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    x[o + e] += alpha * p[o + e];
+    double re = r[o + e] - alpha * q[o + e];
+    r[o + e] = re;
+    v2[0] += re * re;
+  }
+  double rr[1];
+  cta_sum<1>(v2, rr);
+  if (threadIdx.x == 0) {
+    double rel = sqrt(rr[0]) / st[4 * l + 1];
+    st[4 * l + 2] = rel;
+    st[4 * l + 3] += 1.0;
+    if (rel <= tol) live[l] = 0;
+  }
+}
+
+// after z = M^-1 r: beta = rz' / rz, p = z + beta p
+__global__ void __launch_bounds__(256) k_pcg_beta(const int *sub_cam_ptr, const int *voff, const double *r,
+                                                  const double *z, double *p, double *st, const int *live) {
+  int l = blockIdx.x;
+  if (!live[l]) return;
+  int n = 6 * (sub_cam_ptr[l + 1] - sub_cam_ptr[l]);
+  int o = voff[l];
+  double v1[1] = {0.0};
+  for (int e = threadIdx.x; e < n; e += blockDim.x) v1[0] += r[o + e] * z[o + e];
+  double s[1];
+  cta_sum<1>(v1, s);
+  double beta = s[0] / st[4 * l];
+  for (int e = threadIdx.x; e < n; e += blockDim.x) p[o + e] = z[o + e] + beta * p[o + e];
+  if (threadIdx.x == 0) st[4 * l] = s[0];
+}
+
+// z = G^T G r over the cameras of the live sub-blocks, in FP32: three passes,
+// the neighbour sums with one warp per camera (lanes split its graph entries).
+// Per camera g: vector offset nvo[g]; rh and y hold 6 floats per camera.
+__global__ void k_fsai_p1(int M, const int *node_sys, const int *live, const int *nvo, FsaiView P, const double *r,
+                          float *rh) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= M || (live && !live[node_sys[g]])) return;
+  const float *A = P.Li + 36 * (size_t)g;
+  const double *rg = r + nvo[g];
+  float rc[6];
+  for (int b = 0; b < 6; b++) rc[b] = (float)rg[b];
+  for (int a = 0; a < 6; a++) {
+    float t = 0.f;
+    for (int b = 0; b <= a; b++) t += A[6 * a + b] * rc[b];
+    rh[6 * (size_t)g + a] = t;
+  }
+}
+
+__global__ void k_fsai_p2(int M, const int *node_sys, const int *live, const int *nvo, FsaiView P, const double *r,
+                          const float *rh, float *y) {
+  int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (v >= M || (live && !live[node_sys[v]])) return;
+  float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int e = P.ptr[v] + lane; e < P.ptr[v + 1]; e += 32) {
+    int u = P.adj[e];
+    if (u >= v) continue;
+    const float *Fe = P.F + 36 * (size_t)e;
+    float x[6];
+    for (int b = 0; b < 6; b++) x[b] = rh[6 * (size_t)u + b];
+    for (int a = 0; a < 6; a++) {
+      float t = 0.f;
+      for (int b = 0; b < 6; b++) t += Fe[6 * a + b] * x[b];
+      acc[a] += t;
+    }
+  }
+  for (int a = 0; a < 6; a++)
+    for (int o = 16; o > 0; o >>= 1) acc[a] += __shfl_down_sync(0xffffffffu, acc[a], o);
+  if (lane == 0) {
+    const float *A = P.D + 36 * (size_t)v;
+    const double *rv = r + nvo[v];
+    for (int a = 0; a < 6; a++) {
+      float t = 0.f;
+      for (int b = 0; b <= a; b++) t += A[6 * a + b] * (float)rv[b];
+      y[6 * (size_t)v + a] = t - acc[a];
+    }
+  }
+}
+
+__global__ void k_fsai_p3(int M, const int *node_sys, const int *live, const int *nvo, FsaiView P, const float *y,
+                          double *z) {
+  int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (v >= M || (live && !live[node_sys[v]])) return;
+  float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int e = P.ptr[v] + lane; e < P.ptr[v + 1]; e += 32) {
+    int u = P.adj[e];
+    if (u <= v) continue;
+    const float *Fe = P.F + 36 * (size_t)P.mir[e];
+    float x[6];
+    for (int a = 0; a < 6; a++) x[a] = y[6 * (size_t)u + a];
+    for (int b = 0; b < 6; b++) {
+      float t = 0.f;
+      for (int a = 0; a < 6; a++) t += Fe[6 * a + b] * x[a];
+      w[b] += t;
+    }
+  }
+  for (int b = 0; b < 6; b++)
+    for (int o = 16; o > 0; o >>= 1) w[b] += __shfl_down_sync(0xffffffffu, w[b], o);
+  if (lane == 0) {
+    const float *A = P.D + 36 * (size_t)v, *B = P.Li + 36 * (size_t)v;
+    const float *yv = y + 6 * (size_t)v;
+    double *zv = z + nvo[v];
+    for (int b = 0; b < 6; b++) {
+      float t = 0.f;
+      for (int a = b; a < 6; a++) t += A[6 * a + b] * yv[a] - B[6 * a + b] * w[a];
+      zv[b] = (double)t;
+    }
+  }
+}
+
+rpba_status fsai_apply(Ctx *ctx, const FsaiApply &F, const int *live, const double *r, double *z) {
+  int M = F.M;
+  if (M == 0) return RPBA_OK;
+  cudaStream_t st = ctx ? ctx->stream : F.stream;
+  auto launch = [&](const char *name, auto fn) -> rpba_status {
+    if (ctx) {
+      RPBA_KERNEL(ctx, name, fn());
+      return RPBA_OK;
+    }
+    fn();
+    return cudaGetLastError() == cudaSuccess ? RPBA_OK : RPBA_ERR_CUDA;
+  };
+  RPBA_TRY(launch("k_fsai_p1", [&] {
+    k_fsai_p1<<<nblk(M, 128), 128, 0, st>>>(M, F.node_sys, live, F.nvo, F.P, r, F.rh);
+  }));
+  RPBA_TRY(launch("k_fsai_p2", [&] {
+    k_fsai_p2<<<nblk(32LL * M, 256), 256, 0, st>>>(M, F.node_sys, live, F.nvo, F.P, r, F.rh, F.y);
+  }));
+  RPBA_TRY(launch("k_fsai_p3", [&] {
+    k_fsai_p3<<<nblk(32LL * M, 256), 256, 0, st>>>(M, F.node_sys, live, F.nvo, F.P, F.y, z);
+  }));
+  return RPBA_OK;
+}
+
 // dC = x
 __global__ void k_pcg_out(const int *run, const int *fail, const int *voff, const int *npad, int L, const double *x,
                           double *dC) {
@@ -233,36 +432,62 @@ __global__ void k_pcg_live_count(int L, const int *live, int *count) {
   if (l < L && live[l]) atomicAdd(count, 1);
 }
 
-// Solve with the preconditioner blocks in ctx->pcg_Minv (set up by the caller:
-// block-Jacobi here, or the learned blocks). Iterations stop per sub-block at
-// the relative residual pcg_tol or after pcg_max_iter.
-rpba_status pcg_iterate(Ctx *ctx, const int *run_dev, int *fail_dev) {
+// Solve with the preconditioner set up by the caller: the inverse blocks in
+// ctx->pcg_Minv (block-Jacobi, one fused step kernel per iteration), or the
+// learned factor when fsai is given (the step split around the grid-wide
+// apply). Iterations stop per sub-block at the relative residual pcg_tol or
+// after pcg_max_iter.
+rpba_status pcg_iterate(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiApply *fsai) {
   int L = ctx->L;
-  RPBA_KERNEL(ctx, "k_pcg_init", k_pcg_init<<<L, 256, 0, ctx->stream>>>(
-                                     run_dev, fail_dev, ctx->sub_cam_ptr, ctx->ycam_off, ctx->npad, ctx->pcg_Minv, ctx->y,
-                                     ctx->pcg_x, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, ctx->pcg_st, ctx->pcg_live));
+  cudaStream_t st = ctx->stream;
+  if (fsai) {
+    RPBA_KERNEL(ctx, "k_pcg_init_a", k_pcg_init_a<<<L, 256, 0, st>>>(run_dev, fail_dev, ctx->sub_cam_ptr, ctx->ycam_off,
+                                                                    ctx->npad, ctx->y, ctx->pcg_x, ctx->pcg_r,
+                                                                    ctx->pcg_z, ctx->pcg_p, ctx->pcg_st,
+                                                                    ctx->pcg_live));
+    RPBA_TRY(fsai_apply(ctx, *fsai, ctx->pcg_live, ctx->pcg_r, ctx->pcg_z));
+    RPBA_KERNEL(ctx, "k_pcg_init_b", k_pcg_init_b<<<L, 256, 0, st>>>(ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_r,
+                                                                    ctx->pcg_z, ctx->pcg_p, ctx->pcg_st,
+                                                                    ctx->pcg_live));
+  } else {
+    RPBA_KERNEL(ctx, "k_pcg_init", k_pcg_init<<<L, 256, 0, st>>>(
+                                       run_dev, fail_dev, ctx->sub_cam_ptr, ctx->ycam_off, ctx->npad, ctx->pcg_Minv,
+                                       ctx->y, ctx->pcg_x, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, ctx->pcg_st,
+                                       ctx->pcg_live));
+  }
   int tiles = ctx->pcg_tiles_total;
   int maxit = ctx->opt.pcg_max_iter;
   for (int it = 0; it < maxit; it++) {
-    RPBA_CUDA(cudaMemsetAsync(ctx->pcg_q, 0, ctx->ytot * sizeof(double), ctx->stream));
-    RPBA_KERNEL(ctx, "k_pcg_symv", k_pcg_symv<<<tiles, 256, 0, ctx->stream>>>(
+    RPBA_CUDA(cudaMemsetAsync(ctx->pcg_q, 0, ctx->ytot * sizeof(double), st));
+    RPBA_KERNEL(ctx, "k_pcg_symv", k_pcg_symv<<<tiles, 256, 0, st>>>(
                                        ctx->S, ctx->S_off, ctx->npad, ctx->ycam_off, ctx->pcg_live, ctx->pcg_tiles,
                                        L, ctx->pcg_p, ctx->pcg_q));
-    RPBA_KERNEL(ctx, "k_pcg_step", k_pcg_step<<<L, 256, 0, ctx->stream>>>(
-                                       ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_Minv, ctx->opt.pcg_tol, ctx->pcg_x,
-                                       ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, ctx->pcg_q, ctx->pcg_st, ctx->pcg_live));
+    if (fsai) {
+      RPBA_KERNEL(ctx, "k_pcg_alpha", k_pcg_alpha<<<L, 256, 0, st>>>(ctx->sub_cam_ptr, ctx->ycam_off,
+                                                                    ctx->opt.pcg_tol, ctx->pcg_x, ctx->pcg_r,
+                                                                    ctx->pcg_p, ctx->pcg_q, ctx->pcg_st,
+                                                                    ctx->pcg_live));
+      RPBA_TRY(fsai_apply(ctx, *fsai, ctx->pcg_live, ctx->pcg_r, ctx->pcg_z));
+      RPBA_KERNEL(ctx, "k_pcg_beta", k_pcg_beta<<<L, 256, 0, st>>>(ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_r,
+                                                                  ctx->pcg_z, ctx->pcg_p, ctx->pcg_st,
+                                                                  ctx->pcg_live));
+    } else {
+      RPBA_KERNEL(ctx, "k_pcg_step", k_pcg_step<<<L, 256, 0, st>>>(
+                                         ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_Minv, ctx->opt.pcg_tol, ctx->pcg_x,
+                                         ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, ctx->pcg_q, ctx->pcg_st, ctx->pcg_live));
+    }
     if ((it & 7) == 7 || it == maxit - 1) {
-      RPBA_CUDA(cudaMemsetAsync(ctx->counters + 8, 0, sizeof(int), ctx->stream));
-      RPBA_KERNEL(ctx, "k_pcg_live_count", k_pcg_live_count<<<nblk(L, 128), 128, 0, ctx->stream>>>(
+      RPBA_CUDA(cudaMemsetAsync(ctx->counters + 8, 0, sizeof(int), st));
+      RPBA_KERNEL(ctx, "k_pcg_live_count", k_pcg_live_count<<<nblk(L, 128), 128, 0, st>>>(
                                                L, ctx->pcg_live, ctx->counters + 8));
       RPBA_CUDA(cudaMemcpyAsync(ctx->h_pinned_counter + 8, ctx->counters + 8, sizeof(int), cudaMemcpyDeviceToHost,
-                                ctx->stream));
-      RPBA_CUDA(cudaStreamSynchronize(ctx->stream));
+                                st));
+      RPBA_CUDA(cudaStreamSynchronize(st));
       if (ctx->h_pinned_counter[8] == 0) break;
     }
   }
-  RPBA_KERNEL(ctx, "k_pcg_out", k_pcg_out<<<dim3(8, L), 256, 0, ctx->stream>>>(run_dev, fail_dev, ctx->ycam_off,
-                                                                             ctx->npad, L, ctx->pcg_x, ctx->dC));
+  RPBA_KERNEL(ctx, "k_pcg_out", k_pcg_out<<<dim3(8, L), 256, 0, st>>>(run_dev, fail_dev, ctx->ycam_off,
+                                                                     ctx->npad, L, ctx->pcg_x, ctx->dC));
   return RPBA_OK;
 }
 
@@ -272,7 +497,7 @@ rpba_status launch_pcg_blockjacobi(Ctx *ctx, const int *run_dev, int *fail_dev) 
     RPBA_KERNEL(ctx, "k_pcg_bj_setup", k_pcg_bj_setup<<<nblk(ctx->M, 128), 128, 0, ctx->stream>>>(
                                            ctx->M, ctx->cam_sub, ctx->cam_local, ctx->sub_cam_ptr, run_dev, ctx->S,
                                            ctx->S_off, ctx->npad, ctx->pcg_Minv, fail_dev));
-  return pcg_iterate(ctx, run_dev, fail_dev);
+  return pcg_iterate(ctx, run_dev, fail_dev, nullptr);
 }
 
 }  // namespace rpba

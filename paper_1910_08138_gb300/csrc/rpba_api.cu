@@ -14,9 +14,6 @@
 
 using namespace rpba;
 
-struct rpba_ctx {
-  Ctx c;
-};
 
 namespace rpba {
 
@@ -137,6 +134,8 @@ static rpba_status dev_alloc(Ctx *ctx, void **p, size_t bytes) {
   *p = q;
   return RPBA_OK;
 }
+
+rpba_status rpba::ctx_alloc(Ctx *ctx, void **p, size_t bytes) { return dev_alloc(ctx, p, bytes); }
 
 template <typename T>
 static rpba_status alloc_n(Ctx *ctx, T **p, size_t n) {
@@ -330,6 +329,11 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
         if (la > lb) { pa.push_back(a); pb_.push_back(b); }
       }
   ctx->n_pairs = (long long)pa.size();
+  if (ctx->opt.solver == 3) {
+    std::vector<int> oc(K);
+    for (int p = 0; p < K; p++) oc[p] = pb->obs_cam[order[p]];
+    build_camera_graph(ctx, inst_obs_ptr, oc, inst_sub, cam_local);
+  }
   // RCS layout
   std::vector<long long> soff(L);
   std::vector<int> npad(L), yoff(L), ntiles(L);
@@ -488,7 +492,7 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   RPBA_TRY(upload(ctx, &ctx->linv_off, loff.data(), (size_t)L));
   RPBA_TRY(upload(ctx, &ctx->sched, ctx->h_sched.data(), ctx->h_sched.size()));
   RPBA_TRY(alloc_n(ctx, &ctx->Linv64, (size_t)std::max(ltot, 1)));
-  if (ctx->opt.solver == 1) {
+  if (ctx->opt.solver == 1 || ctx->opt.solver == 3) {
     RPBA_TRY(alloc_n(ctx, &ctx->pcg_Minv, 36 * (size_t)std::max(M, 1)));
     RPBA_TRY(alloc_n(ctx, &ctx->pcg_x, (size_t)std::max(yt, 1)));
     RPBA_TRY(alloc_n(ctx, &ctx->pcg_r, (size_t)std::max(yt, 1)));
@@ -547,7 +551,7 @@ extern "C" rpba_status rpba_create(const rpba_problem *prob, const rpba_options 
   Ctx *ctx = &h->c;
   if (opt) ctx->opt = *opt;
   else rpba_default_options(&ctx->opt);
-  if ((ctx->opt.precision != 0 && ctx->opt.precision != 1) || ctx->opt.solver < 0 || ctx->opt.solver > 2 ||
+  if ((ctx->opt.precision != 0 && ctx->opt.precision != 1) || ctx->opt.solver < 0 || ctx->opt.solver > 3 ||
       ctx->opt.ir_steps < 0 || ctx->opt.ir_steps > 20 || ctx->opt.pcg_max_iter < 1 || !(ctx->opt.pcg_tol > 0.0)) {
     ctx->err = "invalid precision / solver / ir_steps option";
     *out = h;
@@ -891,7 +895,7 @@ static void free_graph(GraphRec *g) {
 
 // capture lm_step_body into a graph (all launch parameters are fixed per context)
 static rpba_status capture_lm_graph(Ctx *ctx) {
-  if (ctx->opt.solver == 1) {  // PCG stops on a device-side test read by the host: not capturable
+  if (ctx->opt.solver == 1 || ctx->opt.solver == 3) {  // PCG stops on a device-side test read by the host
     ctx->use_graphs = false;
     return RPBA_OK;
   }
@@ -1096,8 +1100,8 @@ extern "C" rpba_status rpba_profile_read(rpba_ctx *h, int32_t max_kernels, char 
 
 extern "C" rpba_status rpba_solver_stats(rpba_ctx *h, int32_t *iters, double *relres) {
   CTX_OR_FAIL;
-  if (ctx->opt.solver != 1 || !ctx->pcg_st) {
-    ctx->err = "solver statistics exist for the PCG solver only";
+  if ((ctx->opt.solver != 1 && ctx->opt.solver != 3) || !ctx->pcg_st) {
+    ctx->err = "solver statistics exist for the PCG solvers only";
     return RPBA_ERR_STATE;
   }
   std::vector<double> st(4 * (size_t)ctx->L);
@@ -1107,5 +1111,12 @@ extern "C" rpba_status rpba_solver_stats(rpba_ctx *h, int32_t *iters, double *re
     if (iters) iters[l] = (int32_t)st[4 * l + 3];
     if (relres) relres[l] = st[4 * l + 2];
   }
+  return RPBA_OK;
+}
+
+extern "C" rpba_status rpba_solver_fallbacks(rpba_ctx *h, int64_t *n) {
+  CTX_OR_FAIL;
+  if (!n) return RPBA_ERR_INVALID_ARG;
+  *n = ctx->gnn_fallbacks;
   return RPBA_OK;
 }

@@ -128,6 +128,30 @@ __device__ inline void project_jac(const T R[9], const T Xc[3], const T RX[3], T
 }
 
 // ---------------------------------------------------------------------------
+// learned preconditioner: z = G^T G r, G = M^-1 (I - N) L^-1 block lower
+// triangular over the camera graph, applied in FP32 (a preconditioner needs no
+// FP64; the PCG vectors stay FP64). Per camera g: D = M^-1 L^-1 and Li = L^-1
+// (36 floats each, row-major); per CSR entry a = (row v, column u < v):
+// F = M_v^-1 N_vu (36 floats); mir[a] = position of the reverse entry.
+//   pass 1  rh_c = Li_c r_c
+//   pass 2  y_i = D_i r_i - sum_{j<i} F_ij rh_j                     (y = G r)
+//   pass 3  z_j = D_j^T y_j - Li_j^T sum_{i>j} F_ij^T y_i           (z = G^T y)
+// ---------------------------------------------------------------------------
+struct FsaiView {
+  const int *ptr, *adj, *mir;
+  const float *D, *Li, *F;
+};
+
+struct FsaiApply {
+  int M = 0;                       // cameras
+  const int *node_sys = nullptr;   // camera -> system (sub-block), for the live mask
+  const int *nvo = nullptr;        // camera -> offset of its 6 entries in r and z
+  FsaiView P{};
+  float *rh = nullptr, *y = nullptr;  // 6 floats per camera each
+  cudaStream_t stream = nullptr;      // used when no context is given
+};
+
+// ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------
 struct DevBuf {
@@ -237,7 +261,24 @@ struct Ctx {
   cudaStream_t own_stream = nullptr;  // created when the caller passes the legacy default stream
   int *h_pinned_counter = nullptr;
   double *h_pinned_d = nullptr;
+  // learned block preconditioner (solver 3): camera graph in sub-block order,
+  // network parameters (FP32 and BF16) and per-camera work arrays
+  std::vector<int> h_nadj_ptr, h_nadj, h_nadj_mir, h_nadj_row;
+  int *node_sys = nullptr, *nadj_ptr = nullptr, *nadj = nullptr, *nadj_mir = nullptr, *nadj_row = nullptr;
+  float *gnn_w = nullptr;
+  void *gnn_wb = nullptr;
+  float *gnn_x = nullptr, *gnn_e = nullptr, *gnn_h = nullptr, *gnn_C = nullptr;
+  double *gnn_L = nullptr, *gnn_nrm = nullptr, *gnn_shat = nullptr, *gnn_gam = nullptr;
+  float *pcg_D32 = nullptr, *pcg_Li32 = nullptr, *pcg_F32 = nullptr;  // factor of the learned P^-1
+  float *gnn_rh = nullptr, *gnn_y = nullptr;                            // apply scratch, 6 per camera
+  int *node_voff = nullptr;                                             // camera -> RCS vector offset
+  int *gnn_ok = nullptr, *pcg_run2 = nullptr, *pcg_fail2 = nullptr;
+  bool gnn_ready = false;
+  long long gnn_fallbacks = 0;  // sub-block solves re-done by block-Jacobi PCG
 };
+
+// device allocation through the context's allocator (freed at destroy)
+rpba_status ctx_alloc(Ctx *ctx, void **p, size_t bytes);
 
 // error helpers
 #define RPBA_CUDA(call)                                                              \
@@ -337,7 +378,13 @@ rpba_status launch_sub_costs(Ctx *ctx, int trial, double *F_dev);
 rpba_status launch_build_rcs(Ctx *ctx, const double *lambda_dev, const int *run_dev);
 rpba_status launch_solve_rcs(Ctx *ctx, const int *run_dev, int *fail_dev);
 rpba_status launch_pcg_blockjacobi(Ctx *ctx, const int *run_dev, int *fail_dev);
-rpba_status pcg_iterate(Ctx *ctx, const int *run_dev, int *fail_dev);
+rpba_status launch_pcg_learned(Ctx *ctx, const int *run_dev, int *fail_dev);
+void build_camera_graph(Ctx *ctx, const std::vector<int> &inst_obs_ptr, const std::vector<int> &obs_cam_sorted,
+                        const std::vector<int> &inst_sub, const std::vector<int> &cam_local);
+rpba_status pcg_iterate(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiApply *fsai);
+// z = P^-1 r with the learned factor over the cameras of the live systems
+// (live NULL: all); counted on ctx when given, else launched on F.stream
+rpba_status fsai_apply(Ctx *ctx, const FsaiApply &F, const int *live, const double *r, double *z);
 rpba_status launch_backsub_trial(Ctx *ctx, const int *run_dev);
 rpba_status launch_lm_decide(Ctx *ctx);
 rpba_status launch_lm_apply(Ctx *ctx, const int *acc_dev);
@@ -346,3 +393,9 @@ rpba_status launch_fill_int(Ctx *ctx, int *p, int n, int v);
 rpba_status launch_fill_double(Ctx *ctx, double *p, long long n, double v);
 
 }  // namespace rpba
+
+// the opaque handle of the C ABI
+struct rpba_ctx {
+  rpba::Ctx c;
+};
+

@@ -20,6 +20,7 @@ from . import build as _build
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
 _u8 = C.POINTER(C.c_uint8)
+_fp = C.POINTER(C.c_float)
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -113,6 +114,21 @@ def load(build_if_missing: bool = True):
         "rpba_profile_read": (C.c_int, [vp, C.c_int32, C.c_char_p, _dp, C.POINTER(C.c_int64), _ip,
                                         C.POINTER(C.c_int64)]),
         "rpba_solver_stats": (C.c_int, [vp, _ip, _dp]),
+        "rpba_solver_fallbacks": (C.c_int, [vp, C.POINTER(C.c_int64)]),
+        "rpba_gnn_param_count": (C.c_int32, []),
+        "rpba_set_gnn_weights": (C.c_int, [vp, _fp, C.c_int32]),
+        "rpba_gnn_create": (C.c_int, [C.c_uint64, C.POINTER(vp)]),
+        "rpba_gnn_destroy": (None, [vp]),
+        "rpba_gnn_last_error": (C.c_char_p, [vp]),
+        "rpba_gnn_get_weights": (C.c_int, [vp, _fp]),
+        "rpba_gnn_set_weights": (C.c_int, [vp, _fp]),
+        "rpba_gnn_add_system": (C.c_int, [vp, C.c_int32, _dp, C.c_int32, C.c_int32, _dp]),
+        "rpba_gnn_add_rcs": (C.c_int, [vp, vp, C.c_double, C.c_int32, C.c_uint64]),
+        "rpba_gnn_dataset_size": (C.c_int, [vp, _ip, _ip, _ip]),
+        "rpba_gnn_graph": (C.c_int, [vp, _fp, _ip, _ip, _fp]),
+        "rpba_gnn_precondition": (C.c_int, [vp, _dp, _dp]),
+        "rpba_gnn_loss_grad": (C.c_int, [vp, _dp, _fp]),
+        "rpba_gnn_train": (C.c_int, [vp, C.c_int32, C.c_float, C.c_uint64, _dp]),
         "rpba_sigma0_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32] + [vp] * 10 + [vp, _dp, _dp, _dp]),
     }
     for name, (res, args) in sigs.items():
@@ -127,7 +143,7 @@ def exported_symbols():
     """Names declared in include/rpba.h that the library must export."""
     hdr = os.path.join(os.path.dirname(_build.HERE), "include", "rpba.h")
     import re
-    names = re.findall(r"^\s*(?:rpba_status|void|const char\s*\*)\s*\*?\s*(rpba_\w+)\s*\(",
+    names = re.findall(r"^\s*(?:rpba_status|void|int32_t|const char\s*\*)\s*\*?\s*(rpba_\w+)\s*\(",
                        open(hdr).read(), flags=re.M)
     return sorted(set(names))
 
@@ -138,6 +154,10 @@ def _d(a):
 
 def _i(a):
     return a.ctypes.data_as(_ip) if a is not None else None
+
+
+def _f(a):
+    return a.ctypes.data_as(_fp) if a is not None else None
 
 
 def _f64(a, shape=None):
@@ -383,6 +403,15 @@ class Rpba:
         self._c(load().rpba_solver_stats(self._h, _i(it), _d(rr)))
         return it, rr
 
+    def solver_fallbacks(self):
+        n = C.c_int64()
+        self._c(load().rpba_solver_fallbacks(self._h, C.byref(n)))
+        return int(n.value)
+
+    def set_gnn_weights(self, w):
+        w = np.ascontiguousarray(np.asarray(w, dtype=np.float32))
+        self._c(load().rpba_set_gnn_weights(self._h, _f(w), int(w.size)))
+
     # measurement
     def profile_enable(self, enable=True):
         self._c(load().rpba_profile_enable(self._h, int(bool(enable))))
@@ -403,3 +432,87 @@ class Rpba:
             nm = raw[48 * a:48 * a + 48].split(b"\0", 1)[0].decode()
             out[nm] = (int(la[a]), float(ms[a]))
         return out, int(tot.value)
+
+
+def gnn_param_count() -> int:
+    return int(load().rpba_gnn_param_count())
+
+
+class Gnn:
+    """The learned block preconditioner's trainer (rpba_gnn_*): network,
+    dataset of systems and Adam, on the current CUDA device."""
+
+    def __init__(self, seed=0):
+        L = load()
+        self._h = C.c_void_p()
+        st = L.rpba_gnn_create(int(seed), C.byref(self._h))
+        self._c(st)
+        self.n_params = gnn_param_count()
+
+    def _c(self, st):
+        if st != 0:
+            msg = load().rpba_gnn_last_error(self._h) if self._h.value else b""
+            raise RpbaError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().rpba_gnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def weights(self):
+        w = np.zeros(self.n_params, np.float32)
+        self._c(load().rpba_gnn_get_weights(self._h, _f(w)))
+        return w
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(np.asarray(w, dtype=np.float32))
+        assert w.size == self.n_params
+        self._c(load().rpba_gnn_set_weights(self._h, _f(w)))
+
+    def add_system(self, S, z):
+        S = _f64(S)
+        z = _f64(z)
+        n = S.shape[0] // 6
+        self._c(load().rpba_gnn_add_system(self._h, n, _d(S), S.shape[1], z.shape[0], _d(z)))
+
+    def add_rcs(self, ctx, lam=1e-4, n_probes=4, seed=0):
+        self._c(load().rpba_gnn_add_rcs(self._h, ctx._h, float(lam), int(n_probes), int(seed)))
+
+    def size(self):
+        n, e, s = C.c_int32(), C.c_int32(), C.c_int32()
+        self._c(load().rpba_gnn_dataset_size(self._h, C.byref(n), C.byref(e), C.byref(s)))
+        return n.value, e.value, s.value
+
+    def graph(self):
+        n, ne, _ = self.size()
+        x = np.zeros((n, 21), np.float32)
+        ptr = np.zeros(n + 1, np.int32)
+        adj = np.zeros(max(ne, 1), np.int32)
+        e = np.zeros(max(ne, 1), np.float32)
+        self._c(load().rpba_gnn_graph(self._h, _f(x), _i(ptr), _i(adj), _f(e)))
+        return x, ptr, adj[:ne], e[:ne]
+
+    def precondition(self, r):
+        """z = P^-1 r for every dataset system (r: n_nodes x 6 values)."""
+        r = _f64(r).reshape(-1)
+        z = np.zeros_like(r)
+        self._c(load().rpba_gnn_precondition(self._h, _d(r), _d(z)))
+        return z
+
+    def loss_grad(self):
+        loss = C.c_double()
+        g = np.zeros(self.n_params, np.float32)
+        self._c(load().rpba_gnn_loss_grad(self._h, C.byref(loss), _f(g)))
+        return loss.value, g
+
+    def train(self, steps, lr=1e-3, probe_seed=0):
+        """Adam steps; probe_seed != 0 draws new probes before every step."""
+        hist = np.zeros(max(int(steps), 1))
+        self._c(load().rpba_gnn_train(self._h, int(steps), float(lr), int(probe_seed), _d(hist)))
+        return hist[:int(steps)]
