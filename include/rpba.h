@@ -280,6 +280,10 @@ rpba_status rpba_gnn_train(rpba_gnn *g, int32_t steps, float lr, uint64_t probe_
  * with a pair of CUDA events on the context stream (adds two event records
  * per launch; leave it off outside measurements). */
 rpba_status rpba_profile_enable(rpba_ctx *ctx, int32_t enable);
+/* While profiling is enabled, time only the launches of the kernel named
+ * `kernel` (NULL or "": all kernels); every launch is still counted. Timing
+ * one kernel keeps the event records out of the rest of the step. */
+rpba_status rpba_profile_select(rpba_ctx *ctx, const char *kernel);
 /* Kernel launches since the last rpba_profile_enable, per kernel name (names:
  * max_kernels slots of 48 chars), their summed event time in ms (0 when
  * timing was off), the number of distinct kernels and of launches. */

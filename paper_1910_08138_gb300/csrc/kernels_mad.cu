@@ -1,12 +1,17 @@
 // kernels_mad.cu -- per-camera robust scale (Sec. 5.3): 1.4826 times the
 // median absolute deviation of the whitened residual components of every
 // observation of the camera. One CTA per camera; the 2 K_i components are
-// sorted in shared memory (bitonic network, padded to a power of two), the
-// median is read off, the absolute deviations are sorted again.
+// sorted in shared memory (bitonic network, padded to a power of two) and the
+// median is read off. The absolute deviations need no second sort: those of
+// the components below the median, read backwards, and those of the
+// components from the median up are two ascending lists, and their median
+// is found by a binary search over the two.
 // The FP64 values are sorted as order-preserving 64-bit integer keys: on this
 // GPU FP64 compares run on the slow FP64 pipe, integer compares do not.
 #include <cuda_runtime.h>
 #include <float.h>
+
+#include <algorithm>
 
 #include "rpba_internal.cuh"
 
@@ -42,6 +47,33 @@ __device__ static void bitonic_sort(unsigned long long *a, int n2) {
 
 __device__ static double sorted_median(const unsigned long long *a, int n) {
   return (n & 1) ? dval(a[n / 2]) : 0.5 * (dval(a[n / 2 - 1]) + dval(a[n / 2]));
+}
+
+// the deviation lists of the sorted values a[0..n) around med, split at s
+// (a[s-1] < med <= a[s]): lower list j -> med - a[s-1-j] (j < s), upper list
+// j -> a[s+j] - med (j < n - s); both ascending
+struct DevLists {
+  const unsigned long long *a;
+  int n, s;
+  double med;
+  __device__ double lo(int j) const { return med - dval(a[s - 1 - j]); }
+  __device__ double hi(int j) const { return dval(a[s + j]) - med; }
+};
+
+// k-th smallest (0-based) of the union of the two deviation lists
+__device__ static double dev_select(const DevLists &D, int k) {
+  int na = D.s, nb = D.n - D.s;
+  int lo = max(0, k + 1 - nb), hi = min(k + 1, na);  // i values taken from the lower list
+  while (lo < hi) {
+    int i = (lo + hi) >> 1;  // candidate: i from the lower list, k + 1 - i from the upper
+    int j = k + 1 - i;
+    // too few from the lower list when its next element is below the upper list's last taken one
+    if (i < na && j > 0 && D.lo(i) < D.hi(j - 1)) lo = i + 1;
+    else hi = i;
+  }
+  int i = lo, j = k + 1 - lo;
+  double x = i > 0 ? D.lo(i - 1) : -1.0, y = j > 0 ? D.hi(j - 1) : -1.0;
+  return x > y ? x : y;
 }
 
 __global__ void k_camera_mad(int M, const double *R, const double *t, const double *intr, const double *X,
@@ -87,12 +119,18 @@ __global__ void k_camera_mad(int M, const double *R, const double *t, const doub
   for (int e = n + threadIdx.x; e < n2; e += blockDim.x) sh[e] = ~0ull;  // sorts last
   __syncthreads();
   bitonic_sort(sh, n2);
-  double med = sorted_median(sh, n);
-  __syncthreads();
-  for (int e = threadIdx.x; e < n; e += blockDim.x) sh[e] = dkey(fabs(dval(sh[e]) - med));
-  __syncthreads();
-  bitonic_sort(sh, n2);
-  if (threadIdx.x == 0) sigma[i] = 1.4826 * sorted_median(sh, n);
+  if (threadIdx.x == 0) {
+    double med = sorted_median(sh, n);
+    unsigned long long km = dkey(med);
+    int a = 0, b = n;  // s = first index with a[s] >= med
+    while (a < b) {
+      int c = (a + b) >> 1;
+      if (sh[c] < km) a = c + 1; else b = c;
+    }
+    DevLists D{sh, n, a, med};
+    double mad = (n & 1) ? dev_select(D, n / 2) : 0.5 * (dev_select(D, n / 2 - 1) + dev_select(D, n / 2));
+    sigma[i] = 1.4826 * mad;
+  }
 }
 
 rpba_status launch_camera_scale(Ctx *ctx) {
@@ -106,7 +144,8 @@ rpba_status launch_camera_scale(Ctx *ctx) {
   }
   if (smem > 48 * 1024)
     RPBA_CUDA(cudaFuncSetAttribute(k_camera_mad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  RPBA_KERNEL(ctx, "k_camera_mad", k_camera_mad<<<ctx->M, 512, smem, ctx->stream>>>(ctx->M, ctx->R, ctx->t, ctx->intr, ctx->X, ctx->active,
+  int threads = std::min(1024, std::max(64, n2 / 2));  // one thread per compare-exchange of a pass
+  RPBA_KERNEL(ctx, "k_camera_mad", k_camera_mad<<<ctx->M, threads, smem, ctx->stream>>>(ctx->M, ctx->R, ctx->t, ctx->intr, ctx->X, ctx->active,
                                                    ctx->cam_obs_ptr, ctx->cam_obs, ctx->obs_pt, ctx->obs_xy,
                                                    ctx->obs_whiten, ctx->has_winv, ctx->cam_sigma));
   return RPBA_OK;

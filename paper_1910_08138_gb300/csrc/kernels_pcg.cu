@@ -5,9 +5,11 @@
 // so that the relative residual can reach 1e-8.
 //
 // Per iteration: k_pcg_symv (one CTA per 32x32 lower tile of every running
-// sub-block, q += S p with FP64 atomics) and k_pcg_step (one CTA per
-// sub-block: alpha = rz / p.q, x += alpha p, r -= alpha q, z = M^-1 r,
-// beta = rz' / rz, p = z + beta p, convergence ||r|| <= tol ||y||).
+// sub-block, q += S p and p^T S p with FP64 atomics) and k_pcg_step (one CTA
+// per sub-block: alpha = rz / p.Sp, x += alpha p, r -= alpha q, z = M^-1 r,
+// beta = rz' / rz, p = z + beta p, convergence ||r|| <= tol ||y||). An 8-CTA
+// cluster per sub-block, tried for the step, was slower: the 64-block
+// workload's 304 small sub-blocks then need 2432 cluster CTAs.
 // The preconditioner is the inverse of the diagonal camera blocks
 // (block-Jacobi), or the learned factorised inverse G^T G (solver 3).
 #include <cuda_runtime.h>
@@ -19,6 +21,7 @@ namespace rpba {
 
 #define PT 32
 #define PLD (PT + 1)
+#define PCG_THREADS 256  // per-sub-block kernels: one CTA
 
 static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 
@@ -61,7 +64,7 @@ __global__ void k_pcg_bj_setup(int M, const int *cam_sub, const int *cam_local, 
 // q += S p over the lower 32x32 tiles of the running, unconverged sub-blocks
 __global__ void __launch_bounds__(256) k_pcg_symv(const double *S, const long long *S_off, const int *npad,
                                                   const int *voff, const int *live, const int *sched_tiles, int L,
-                                                  const double *p, double *q) {
+                                                  const double *p, double *q, double *pq) {
   // CTA -> (sub-block, tile) through prefix sums of the per-sub-block tile counts
   int idx = blockIdx.x;
   int lo = 0, hi = L - 1;
@@ -98,6 +101,10 @@ __global__ void __launch_bounds__(256) k_pcg_symv(const double *S, const long lo
     double s = 0.0;
     for (int c = 0; c < PT; c++) s += blk[tid][c] * pJ[c];
     atomicAdd(ql + a * PT + tid, s);
+    // p^T S p: p_I^T S_IJ p_J, twice for an off-diagonal tile
+    double t = pI[tid] * s * (a == b ? 1.0 : 2.0);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (tid == 0) atomicAdd(pq + l, t);
   } else if (tid < 2 * PT && a != b) {
     int c = tid - PT;
     double s = 0.0;
@@ -108,7 +115,7 @@ __global__ void __launch_bounds__(256) k_pcg_symv(const double *S, const long lo
 
 template <int NV>
 __device__ inline void cta_sum(double (&v)[NV], double (&out)[NV]) {
-  __shared__ double sh[NV][8];
+  __shared__ double sh[NV][32];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int e = 0; e < NV; e++) {
@@ -139,7 +146,7 @@ __device__ inline void apply_precond(int n_cam, const double *Minv_l, const doub
 }
 
 // start: x = 0, r = y, z = M^-1 r, p = z; rz, |y|
-__global__ void __launch_bounds__(256) k_pcg_init(const int *run, const int *fail, const int *sub_cam_ptr,
+__global__ void __launch_bounds__(PCG_THREADS) k_pcg_init(const int *run, const int *fail, const int *sub_cam_ptr,
                                                   const int *voff, const int *npad, const double *Minv_sub,
                                                   const double *y, double *x, double *r, double *z, double *p,
                                                   double *st, int *live) {
@@ -176,52 +183,9 @@ __global__ void __launch_bounds__(256) k_pcg_init(const int *run, const int *fai
   }
 }
 
-__global__ void __launch_bounds__(256) k_pcg_step(const int *sub_cam_ptr, const int *voff, const double *Minv_sub,
-                                                  double tol, double *x, double *r, double *z, double *p,
-                                                  const double *q, double *st, int *live) {
-  int l = blockIdx.x;
-  if (!live[l]) return;
-  int ncam = sub_cam_ptr[l + 1] - sub_cam_ptr[l];
-  int n = 6 * ncam;
-  int o = voff[l];
-  double v1[1] = {0.0};
-  for (int e = threadIdx.x; e < n; e += blockDim.x) v1[0] += p[o + e] * q[o + e];
-  double pq[1];
-  cta_sum<1>(v1, pq);
-  double rz = st[4 * l];
-  if (!(pq[0] > 0.0)) {  // breakdown: keep the current iterate
-    if (threadIdx.x == 0) live[l] = 0;
-    return;
-  }
-  double alpha = rz / pq[0];
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    x[o + e] += alpha * p[o + e];
-    r[o + e] -= alpha * q[o + e];
-  }
-  __syncthreads();
-  apply_precond(ncam, Minv_sub + 36 * (size_t)sub_cam_ptr[l], r + o, z + o);
-  __syncthreads();
-  double v[2] = {0.0, 0.0};
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    v[0] += r[o + e] * z[o + e];
-    v[1] += r[o + e] * r[o + e];
-  }
-  double s[2];
-  cta_sum<2>(v, s);
-  double beta = s[0] / rz;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) p[o + e] = z[o + e] + beta * p[o + e];
-  if (threadIdx.x == 0) {
-    st[4 * l + 0] = s[0];
-    double rel = sqrt(s[1]) / st[4 * l + 1];
-    st[4 * l + 2] = rel;
-    st[4 * l + 3] += 1.0;
-    if (rel <= tol) live[l] = 0;
-  }
-}
-
 // ---- learned preconditioner: the PCG step split around a grid-wide apply ----
 // start without the preconditioner: x = 0, r = y, z = p = 0, |y|
-__global__ void __launch_bounds__(256) k_pcg_init_a(const int *run, const int *fail, const int *sub_cam_ptr,
+__global__ void __launch_bounds__(PCG_THREADS) k_pcg_init_a(const int *run, const int *fail, const int *sub_cam_ptr,
                                                     const int *voff, const int *npad, const double *y, double *x,
                                                     double *r, double *z, double *p, double *st, int *live) {
   int l = blockIdx.x;
@@ -249,7 +213,7 @@ __global__ void __launch_bounds__(256) k_pcg_init_a(const int *run, const int *f
 }
 
 // after z = M^-1 r: p = z, rz
-__global__ void __launch_bounds__(256) k_pcg_init_b(const int *sub_cam_ptr, const int *voff, const double *r,
+__global__ void __launch_bounds__(PCG_THREADS) k_pcg_init_b(const int *sub_cam_ptr, const int *voff, const double *r,
                                                     const double *z, double *p, double *st, const int *live) {
   int l = blockIdx.x;
   if (!live[l]) return;
@@ -262,56 +226,6 @@ __global__ void __launch_bounds__(256) k_pcg_init_b(const int *sub_cam_ptr, cons
   }
   double s[1];
   cta_sum<1>(v1, s);
-  if (threadIdx.x == 0) st[4 * l] = s[0];
-}
-
-// alpha = rz / p.q, x += alpha p, r -= alpha q, convergence on ||r||
-__global__ void __launch_bounds__(256) k_pcg_alpha(const int *sub_cam_ptr, const int *voff, double tol, double *x,
-                                                   double *r, const double *p, const double *q, double *st,
-                                                   int *live) {
-  int l = blockIdx.x;
-  if (!live[l]) return;
-  int n = 6 * (sub_cam_ptr[l + 1] - sub_cam_ptr[l]);
-  int o = voff[l];
-  double v1[1] = {0.0};
-  for (int e = threadIdx.x; e < n; e += blockDim.x) v1[0] += p[o + e] * q[o + e];
-  double pq[1];
-  cta_sum<1>(v1, pq);
-  if (!(pq[0] > 0.0)) {  // breakdown: keep the current iterate
-    if (threadIdx.x == 0) live[l] = 0;
-    return;
-  }
-  double alpha = st[4 * l] / pq[0];
-  double v2[1] = {0.0};
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    x[o + e] += alpha * p[o + e];
-    double re = r[o + e] - alpha * q[o + e];
-    r[o + e] = re;
-    v2[0] += re * re;
-  }
-  double rr[1];
-  cta_sum<1>(v2, rr);
-  if (threadIdx.x == 0) {
-    double rel = sqrt(rr[0]) / st[4 * l + 1];
-    st[4 * l + 2] = rel;
-    st[4 * l + 3] += 1.0;
-    if (rel <= tol) live[l] = 0;
-  }
-}
-
-// after z = M^-1 r: beta = rz' / rz, p = z + beta p
-__global__ void __launch_bounds__(256) k_pcg_beta(const int *sub_cam_ptr, const int *voff, const double *r,
-                                                  const double *z, double *p, double *st, const int *live) {
-  int l = blockIdx.x;
-  if (!live[l]) return;
-  int n = 6 * (sub_cam_ptr[l + 1] - sub_cam_ptr[l]);
-  int o = voff[l];
-  double v1[1] = {0.0};
-  for (int e = threadIdx.x; e < n; e += blockDim.x) v1[0] += r[o + e] * z[o + e];
-  double s[1];
-  cta_sum<1>(v1, s);
-  double beta = s[0] / st[4 * l];
-  for (int e = threadIdx.x; e < n; e += blockDim.x) p[o + e] = z[o + e] + beta * p[o + e];
   if (threadIdx.x == 0) st[4 * l] = s[0];
 }
 
@@ -394,7 +308,7 @@ __global__ void k_fsai_p3(int M, const int *node_sys, const int *live, const int
   }
 }
 
-rpba_status fsai_apply(Ctx *ctx, const FsaiApply &F, const int *live, const double *r, double *z) {
+rpba_status fsai_apply(Ctx *ctx, const FsaiApply &F, const int *live, const double *r, double *z, bool skip_first) {
   int M = F.M;
   if (M == 0) return RPBA_OK;
   cudaStream_t st = ctx ? ctx->stream : F.stream;
@@ -406,9 +320,10 @@ rpba_status fsai_apply(Ctx *ctx, const FsaiApply &F, const int *live, const doub
     fn();
     return cudaGetLastError() == cudaSuccess ? RPBA_OK : RPBA_ERR_CUDA;
   };
-  RPBA_TRY(launch("k_fsai_p1", [&] {
-    k_fsai_p1<<<nblk(M, 128), 128, 0, st>>>(M, F.node_sys, live, F.nvo, F.P, r, F.rh);
-  }));
+  if (!skip_first)
+    RPBA_TRY(launch("k_fsai_p1", [&] {
+      k_fsai_p1<<<nblk(M, 128), 128, 0, st>>>(M, F.node_sys, live, F.nvo, F.P, r, F.rh);
+    }));
   RPBA_TRY(launch("k_fsai_p2", [&] {
     k_fsai_p2<<<nblk(32LL * M, 256), 256, 0, st>>>(M, F.node_sys, live, F.nvo, F.P, r, F.rh, F.y);
   }));
@@ -416,6 +331,116 @@ rpba_status fsai_apply(Ctx *ctx, const FsaiApply &F, const int *live, const doub
     k_fsai_p3<<<nblk(32LL * M, 256), 256, 0, st>>>(M, F.node_sys, live, F.nvo, F.P, F.y, z);
   }));
   return RPBA_OK;
+}
+
+// ---- the CG step, one CTA per sub-block ----
+// block-Jacobi step: alpha = rz / p.Sp, x += alpha p, r -= alpha q, z = M^-1 r,
+// beta = rz' / rz, p = z + beta p, convergence ||r|| <= tol ||y||
+__global__ void __launch_bounds__(PCG_THREADS) k_pcg_step(const int *sub_cam_ptr, const int *voff,
+                                                          const double *Minv_sub, double tol, double *x, double *r,
+                                                          double *z, double *p, const double *q, const double *pq,
+                                                          double *st, int *live) {
+  int l = blockIdx.x;
+  if (!live[l]) return;
+  double rz_old = st[4 * l], pql = pq[l];
+  if (!(pql > 0.0)) {  // breakdown: keep the current iterate
+    if (threadIdx.x == 0) live[l] = 0;
+    return;
+  }
+  int g0 = sub_cam_ptr[l], ncam = sub_cam_ptr[l + 1] - g0;
+  int n = 6 * ncam, o = voff[l];
+  double alpha = rz_old / pql;
+  double v[2] = {0.0, 0.0};
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    x[o + e] += alpha * p[o + e];
+    double re = r[o + e] - alpha * q[o + e];
+    r[o + e] = re;
+    v[0] += re * re;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncam; c += blockDim.x) {
+    const double *Mi = Minv_sub + 36 * (size_t)(g0 + c);
+    const double *rc = r + o + 6 * c;
+    double *zc = z + o + 6 * c;
+    for (int a = 0; a < 6; a++) {
+      double t = 0.0;
+      for (int b = 0; b < 6; b++) t += Mi[6 * a + b] * rc[b];
+      zc[a] = t;
+      v[1] += rc[a] * t;
+    }
+  }
+  double tot[2];
+  cta_sum<2>(v, tot);
+  double beta = tot[1] / rz_old;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) p[o + e] = z[o + e] + beta * p[o + e];
+  if (threadIdx.x == 0) {
+    st[4 * l] = tot[1];
+    double rel = sqrt(tot[0]) / st[4 * l + 1];
+    st[4 * l + 2] = rel;
+    st[4 * l + 3] += 1.0;
+    if (rel <= tol) live[l] = 0;
+  }
+}
+
+// learned form, first half: alpha, x, r, ||r||, then rh = L^-1 r for the
+// sub-block's cameras (the first pass of the factor's application)
+__global__ void __launch_bounds__(PCG_THREADS) k_pcg_alpha(const int *sub_cam_ptr, const int *voff, double tol,
+                                                           double *x, double *r, const double *p, const double *q,
+                                                           const double *pq, double *st, int *live, const float *Li,
+                                                           float *rh) {
+  int l = blockIdx.x;
+  if (!live[l]) return;
+  double rz_old = st[4 * l], pql = pq[l];
+  if (!(pql > 0.0)) {
+    if (threadIdx.x == 0) live[l] = 0;
+    return;
+  }
+  int g0 = sub_cam_ptr[l], ncam = sub_cam_ptr[l + 1] - g0;
+  int n = 6 * ncam, o = voff[l];
+  double alpha = rz_old / pql;
+  double v[1] = {0.0};
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    x[o + e] += alpha * p[o + e];
+    double re = r[o + e] - alpha * q[o + e];
+    r[o + e] = re;
+    v[0] += re * re;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncam; c += blockDim.x) {
+    const float *A = Li + 36 * (size_t)(g0 + c);
+    const double *rc = r + o + 6 * c;
+    float rf[6];
+    for (int b = 0; b < 6; b++) rf[b] = (float)rc[b];
+    for (int a = 0; a < 6; a++) {
+      float t = 0.f;
+      for (int b = 0; b <= a; b++) t += A[6 * a + b] * rf[b];
+      rh[6 * (size_t)(g0 + c) + a] = t;
+    }
+  }
+  double tot[1];
+  cta_sum<1>(v, tot);
+  if (threadIdx.x == 0) {
+    double rel = sqrt(tot[0]) / st[4 * l + 1];
+    st[4 * l + 2] = rel;
+    st[4 * l + 3] += 1.0;
+    if (rel <= tol) live[l] = 0;
+  }
+}
+
+// learned form, second half (after z = M^-1 r): beta = rz' / rz, p = z + beta p
+__global__ void __launch_bounds__(PCG_THREADS) k_pcg_beta(const int *sub_cam_ptr, const int *voff, const double *r,
+                                                          const double *z, double *p, double *st, const int *live) {
+  int l = blockIdx.x;
+  if (!live[l]) return;
+  int n = 6 * (sub_cam_ptr[l + 1] - sub_cam_ptr[l]);
+  int o = voff[l];
+  double v[1] = {0.0};
+  for (int e = threadIdx.x; e < n; e += blockDim.x) v[0] += r[o + e] * z[o + e];
+  double tot[1];
+  cta_sum<1>(v, tot);
+  double beta = tot[0] / st[4 * l];
+  for (int e = threadIdx.x; e < n; e += blockDim.x) p[o + e] = z[o + e] + beta * p[o + e];
+  if (threadIdx.x == 0) st[4 * l] = tot[0];
 }
 
 // dC = x
@@ -441,16 +466,16 @@ rpba_status pcg_iterate(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiA
   int L = ctx->L;
   cudaStream_t st = ctx->stream;
   if (fsai) {
-    RPBA_KERNEL(ctx, "k_pcg_init_a", k_pcg_init_a<<<L, 256, 0, st>>>(run_dev, fail_dev, ctx->sub_cam_ptr, ctx->ycam_off,
+    RPBA_KERNEL(ctx, "k_pcg_init_a", k_pcg_init_a<<<L, PCG_THREADS, 0, st>>>(run_dev, fail_dev, ctx->sub_cam_ptr, ctx->ycam_off,
                                                                     ctx->npad, ctx->y, ctx->pcg_x, ctx->pcg_r,
                                                                     ctx->pcg_z, ctx->pcg_p, ctx->pcg_st,
                                                                     ctx->pcg_live));
     RPBA_TRY(fsai_apply(ctx, *fsai, ctx->pcg_live, ctx->pcg_r, ctx->pcg_z));
-    RPBA_KERNEL(ctx, "k_pcg_init_b", k_pcg_init_b<<<L, 256, 0, st>>>(ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_r,
+    RPBA_KERNEL(ctx, "k_pcg_init_b", k_pcg_init_b<<<L, PCG_THREADS, 0, st>>>(ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_r,
                                                                     ctx->pcg_z, ctx->pcg_p, ctx->pcg_st,
                                                                     ctx->pcg_live));
   } else {
-    RPBA_KERNEL(ctx, "k_pcg_init", k_pcg_init<<<L, 256, 0, st>>>(
+    RPBA_KERNEL(ctx, "k_pcg_init", k_pcg_init<<<L, PCG_THREADS, 0, st>>>(
                                        run_dev, fail_dev, ctx->sub_cam_ptr, ctx->ycam_off, ctx->npad, ctx->pcg_Minv,
                                        ctx->y, ctx->pcg_x, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, ctx->pcg_st,
                                        ctx->pcg_live));
@@ -459,22 +484,24 @@ rpba_status pcg_iterate(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiA
   int maxit = ctx->opt.pcg_max_iter;
   for (int it = 0; it < maxit; it++) {
     RPBA_CUDA(cudaMemsetAsync(ctx->pcg_q, 0, ctx->ytot * sizeof(double), st));
+    RPBA_CUDA(cudaMemsetAsync(ctx->pcg_pq, 0, L * sizeof(double), st));
     RPBA_KERNEL(ctx, "k_pcg_symv", k_pcg_symv<<<tiles, 256, 0, st>>>(
                                        ctx->S, ctx->S_off, ctx->npad, ctx->ycam_off, ctx->pcg_live, ctx->pcg_tiles,
-                                       L, ctx->pcg_p, ctx->pcg_q));
+                                       L, ctx->pcg_p, ctx->pcg_q, ctx->pcg_pq));
     if (fsai) {
-      RPBA_KERNEL(ctx, "k_pcg_alpha", k_pcg_alpha<<<L, 256, 0, st>>>(ctx->sub_cam_ptr, ctx->ycam_off,
-                                                                    ctx->opt.pcg_tol, ctx->pcg_x, ctx->pcg_r,
-                                                                    ctx->pcg_p, ctx->pcg_q, ctx->pcg_st,
-                                                                    ctx->pcg_live));
-      RPBA_TRY(fsai_apply(ctx, *fsai, ctx->pcg_live, ctx->pcg_r, ctx->pcg_z));
-      RPBA_KERNEL(ctx, "k_pcg_beta", k_pcg_beta<<<L, 256, 0, st>>>(ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_r,
-                                                                  ctx->pcg_z, ctx->pcg_p, ctx->pcg_st,
-                                                                  ctx->pcg_live));
+      RPBA_KERNEL(ctx, "k_pcg_alpha", k_pcg_alpha<<<L, PCG_THREADS, 0, st>>>(
+                                          ctx->sub_cam_ptr, ctx->ycam_off, ctx->opt.pcg_tol, ctx->pcg_x, ctx->pcg_r,
+                                          ctx->pcg_p, ctx->pcg_q, ctx->pcg_pq, ctx->pcg_st, ctx->pcg_live,
+                                          fsai->P.Li, fsai->rh));
+      RPBA_TRY(fsai_apply(ctx, *fsai, ctx->pcg_live, ctx->pcg_r, ctx->pcg_z, /*skip_first=*/true));
+      RPBA_KERNEL(ctx, "k_pcg_beta", k_pcg_beta<<<L, PCG_THREADS, 0, st>>>(
+                                         ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p,
+                                         ctx->pcg_st, ctx->pcg_live));
     } else {
-      RPBA_KERNEL(ctx, "k_pcg_step", k_pcg_step<<<L, 256, 0, st>>>(
+      RPBA_KERNEL(ctx, "k_pcg_step", k_pcg_step<<<L, PCG_THREADS, 0, st>>>(
                                          ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_Minv, ctx->opt.pcg_tol, ctx->pcg_x,
-                                         ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, ctx->pcg_q, ctx->pcg_st, ctx->pcg_live));
+                                         ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, ctx->pcg_q, ctx->pcg_pq, ctx->pcg_st,
+                                         ctx->pcg_live));
     }
     if ((it & 7) == 7 || it == maxit - 1) {
       RPBA_CUDA(cudaMemsetAsync(ctx->counters + 8, 0, sizeof(int), st));

@@ -500,6 +500,7 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
     RPBA_TRY(alloc_n(ctx, &ctx->pcg_p, (size_t)std::max(yt, 1)));
     RPBA_TRY(alloc_n(ctx, &ctx->pcg_q, (size_t)std::max(yt, 1)));
     RPBA_TRY(alloc_n(ctx, &ctx->pcg_st, 4 * (size_t)std::max(L, 1)));
+    RPBA_TRY(alloc_n(ctx, &ctx->pcg_pq, (size_t)std::max(L, 1)));
     RPBA_TRY(alloc_n(ctx, &ctx->pcg_live, (size_t)std::max(L, 1)));
     std::vector<int> pt(L + 1, 0);
     for (int l = 0; l < L; l++) pt[l + 1] = pt[l] + ntiles[l] * (ntiles[l] + 1) / 2;
@@ -901,6 +902,7 @@ static rpba_status capture_lm_graph(Ctx *ctx) {
   }
   GraphRec *g = new GraphRec();
   g->with_events = ctx->prof_enabled;
+  g->prof_only = ctx->prof_only;
   cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) {
     delete g;
@@ -935,7 +937,8 @@ static rpba_status capture_lm_graph(Ctx *ctx) {
 // one lock-step LM iteration through the graph (or eagerly), then the host
 // reads the running count
 static rpba_status lm_step_run(Ctx *ctx) {
-  if (ctx->lm_graph && ctx->lm_graph->with_events != ctx->prof_enabled) {
+  if (ctx->lm_graph &&
+      (ctx->lm_graph->with_events != ctx->prof_enabled || ctx->lm_graph->prof_only != ctx->prof_only)) {
     free_graph(ctx->lm_graph);  // timing nodes only while profiling
     ctx->lm_graph = nullptr;
   }
@@ -1118,5 +1121,11 @@ extern "C" rpba_status rpba_solver_fallbacks(rpba_ctx *h, int64_t *n) {
   CTX_OR_FAIL;
   if (!n) return RPBA_ERR_INVALID_ARG;
   *n = ctx->gnn_fallbacks;
+  return RPBA_OK;
+}
+
+extern "C" rpba_status rpba_profile_select(rpba_ctx *h, const char *kernel) {
+  CTX_OR_FAIL;
+  ctx->prof_only = kernel ? std::string(kernel) : std::string();
   return RPBA_OK;
 }

@@ -219,7 +219,7 @@ struct Ctx {
   int ytot = 0;
   // PCG on the RCS
   double *pcg_Minv = nullptr, *pcg_x = nullptr, *pcg_r = nullptr, *pcg_z = nullptr, *pcg_p = nullptr,
-         *pcg_q = nullptr, *pcg_st = nullptr;
+         *pcg_q = nullptr, *pcg_st = nullptr, *pcg_pq = nullptr;
   int *pcg_live = nullptr, *pcg_tiles = nullptr;
   int pcg_tiles_total = 0;
   double *obs_cost = nullptr, *seg_part = nullptr;
@@ -248,6 +248,7 @@ struct Ctx {
   long long launches = 0;
   std::map<std::string, long long> launch_by_name;
   bool prof_enabled = false;
+  std::string prof_only;  // when set, only launches of this kernel are timed
   struct ProfRec {
     const char *name;
     cudaEvent_t a, b;
@@ -303,6 +304,7 @@ rpba_status check_launch(Ctx *ctx, const char *what);
 struct GraphRec {
   cudaGraphExec_t exec = nullptr;
   bool with_events = false;  // captured with per-kernel event-record nodes
+  std::string prof_only;     // ... for this kernel only (empty: all)
   std::vector<const char *> kernels;
   struct Ev {
     const char *name;
@@ -320,6 +322,7 @@ struct PhaseTimer {
   cudaEvent_t a = nullptr, b = nullptr;
   PhaseTimer(Ctx *c, const char *n) : ctx(c), name(n) {
     if (ctx->capture && !ctx->capture->with_events) return;
+    if (!ctx->prof_only.empty() && ctx->prof_only != name) return;
     if (ctx->capture) {
       cudaEventCreate(&a);
       cudaEventCreate(&b);
@@ -384,7 +387,8 @@ void build_camera_graph(Ctx *ctx, const std::vector<int> &inst_obs_ptr, const st
 rpba_status pcg_iterate(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiApply *fsai);
 // z = P^-1 r with the learned factor over the cameras of the live systems
 // (live NULL: all); counted on ctx when given, else launched on F.stream
-rpba_status fsai_apply(Ctx *ctx, const FsaiApply &F, const int *live, const double *r, double *z);
+rpba_status fsai_apply(Ctx *ctx, const FsaiApply &F, const int *live, const double *r, double *z,
+                       bool skip_first = false);
 rpba_status launch_backsub_trial(Ctx *ctx, const int *run_dev);
 rpba_status launch_lm_decide(Ctx *ctx);
 rpba_status launch_lm_apply(Ctx *ctx, const int *acc_dev);

@@ -111,6 +111,7 @@ def load(build_if_missing: bool = True):
         "rpba_lm_step": (C.c_int, [vp, C.c_double, _ip, _dp, _dp, _dp, _dp]),
         "rpba_bact": (C.c_int, [vp, _ip]),
         "rpba_profile_enable": (C.c_int, [vp, C.c_int32]),
+        "rpba_profile_select": (C.c_int, [vp, C.c_char_p]),
         "rpba_profile_read": (C.c_int, [vp, C.c_int32, C.c_char_p, _dp, C.POINTER(C.c_int64), _ip,
                                         C.POINTER(C.c_int64)]),
         "rpba_solver_stats": (C.c_int, [vp, _ip, _dp]),
@@ -415,6 +416,10 @@ class Rpba:
     # measurement
     def profile_enable(self, enable=True):
         self._c(load().rpba_profile_enable(self._h, int(bool(enable))))
+
+    def profile_select(self, kernel=None):
+        """Time only this kernel's launches while profiling (None: all)."""
+        self._c(load().rpba_profile_select(self._h, kernel.encode() if kernel else None))
 
     def profile_read(self):
         """{kernel: (launches, ms)}, total launches since profile_enable."""
