@@ -1,8 +1,9 @@
 // kernels_mad.cu -- per-camera robust scale (Sec. 5.3): 1.4826 times the
 // median absolute deviation of the whitened residual components of every
 // observation of the camera. One CTA per camera; the 2 K_i components are
-// sorted in shared memory (bitonic network, padded to a power of two) and the
-// median is read off. The absolute deviations need no second sort: those of
+// sorted in shared memory (bitonic network, padded to a power of two >= 64;
+// the stages with stride < 64 run in registers, one warp per 64-key chunk,
+// with shuffles) and the median is read off. The absolute deviations need no second sort: those of
 // the components below the median, read backwards, and those of the
 // components from the median up are two ascending lists, and their median
 // is found by a binary search over the two.
@@ -27,9 +28,48 @@ __device__ inline double dval(unsigned long long k) {
   return __longlong_as_double((long long)u);
 }
 
+// compare-exchange of the bitonic network for the key held at position pos,
+// partner at pos ^ stride (value y): keep the min at the lower position of an
+// ascending pair, the max at its upper position (reversed when descending)
+__device__ inline unsigned long long bitonic_keep(unsigned long long x, unsigned long long y, int pos, int stride,
+                                                  int size) {
+  bool asc = (pos & size) == 0;
+  bool lower = (pos & stride) == 0;
+  bool take_min = (lower == asc);
+  return take_min ? (x < y ? x : y) : (x < y ? y : x);
+}
+
+// the stages of one merge size with stride <= 32 on 64-key chunks, one warp
+// per chunk, keys in registers (lane and lane + 32 of the chunk)
+__device__ inline void bitonic_chunk_stages(unsigned long long *a, int n2, int size, int first_stride) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = 64 * warp; c < n2; c += 64 * nw) {
+    unsigned long long x0 = a[c + lane], x1 = a[c + 32 + lane];
+    for (int stride = first_stride; stride > 0; stride >>= 1) {
+      if (stride == 32) {  // the pair is (lane, lane + 32) of this thread
+        bool asc = ((c + lane) & size) == 0;
+        unsigned long long lo = x0 < x1 ? x0 : x1, hi = x0 < x1 ? x1 : x0;
+        x0 = asc ? lo : hi;
+        x1 = asc ? hi : lo;
+      } else {
+        unsigned long long y0 = __shfl_xor_sync(0xffffffffu, x0, stride);
+        unsigned long long y1 = __shfl_xor_sync(0xffffffffu, x1, stride);
+        x0 = bitonic_keep(x0, y0, c + lane, stride, size);
+        x1 = bitonic_keep(x1, y1, c + 32 + lane, stride, size);
+      }
+    }
+    a[c + lane] = x0;
+    a[c + 32 + lane] = x1;
+  }
+}
+
+// ascending bitonic sort of a[0..n2), n2 a power of two >= 64: the stages with
+// stride >= 64 as shared-memory passes, the others in registers per 64-key chunk
 __device__ static void bitonic_sort(unsigned long long *a, int n2) {
-  for (int size = 2; size <= n2; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+  for (int size = 2; size <= 64; size <<= 1) bitonic_chunk_stages(a, n2, size, size >> 1);
+  __syncthreads();
+  for (int size = 128; size <= n2; size <<= 1) {
+    for (int stride = size >> 1; stride >= 64; stride >>= 1) {
       for (int idx = threadIdx.x; idx < (n2 >> 1); idx += blockDim.x) {
         int i = 2 * stride * (idx / stride) + (idx % stride);
         int j = i + stride;
@@ -42,6 +82,8 @@ __device__ static void bitonic_sort(unsigned long long *a, int n2) {
       }
       __syncthreads();
     }
+    bitonic_chunk_stages(a, n2, size, 32);
+    __syncthreads();
   }
 }
 
@@ -114,7 +156,7 @@ __global__ void k_camera_mad(int M, const double *R, const double *t, const doub
     if (threadIdx.x == 0) sigma[i] = 0.0;
     return;
   }
-  int n2 = 1;
+  int n2 = 64;
   while (n2 < n) n2 <<= 1;
   for (int e = n + threadIdx.x; e < n2; e += blockDim.x) sh[e] = ~0ull;  // sorts last
   __syncthreads();
@@ -135,7 +177,7 @@ __global__ void k_camera_mad(int M, const double *R, const double *t, const doub
 
 rpba_status launch_camera_scale(Ctx *ctx) {
   if (ctx->M == 0) return RPBA_OK;
-  int n2 = 1;
+  int n2 = 64;
   while (n2 < 2 * ctx->max_cam_obs) n2 <<= 1;
   size_t smem = (size_t)n2 * sizeof(unsigned long long);
   if (smem > 200 * 1024) {
@@ -144,7 +186,7 @@ rpba_status launch_camera_scale(Ctx *ctx) {
   }
   if (smem > 48 * 1024)
     RPBA_CUDA(cudaFuncSetAttribute(k_camera_mad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int threads = std::min(1024, std::max(64, n2 / 2));  // one thread per compare-exchange of a pass
+  int threads = std::min(1024, std::max(32, n2 / 2));  // one thread per compare-exchange of a pass
   RPBA_KERNEL(ctx, "k_camera_mad", k_camera_mad<<<ctx->M, threads, smem, ctx->stream>>>(ctx->M, ctx->R, ctx->t, ctx->intr, ctx->X, ctx->active,
                                                    ctx->cam_obs_ptr, ctx->cam_obs, ctx->obs_pt, ctx->obs_xy,
                                                    ctx->obs_whiten, ctx->has_winv, ctx->cam_sigma));

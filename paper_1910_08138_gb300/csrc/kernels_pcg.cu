@@ -7,9 +7,11 @@
 // Per iteration: k_pcg_symv (one CTA per 32x32 lower tile of every running
 // sub-block, q += S p and p^T S p with FP64 atomics) and k_pcg_step (one CTA
 // per sub-block: alpha = rz / p.Sp, x += alpha p, r -= alpha q, z = M^-1 r,
-// beta = rz' / rz, p = z + beta p, convergence ||r|| <= tol ||y||). An 8-CTA
-// cluster per sub-block, tried for the step, was slower: the 64-block
-// workload's 304 small sub-blocks then need 2432 cluster CTAs.
+// beta = rz' / rz, p = z + beta p, convergence ||r|| <= tol ||y||). Two other
+// step designs were slower: an 8-CTA cluster per sub-block (the 64-block
+// workload's 304 small sub-blocks then need 2432 cluster CTAs) and three
+// grid-wide kernels with one thread per camera (three launch latencies for
+// ~1000 threads of work).
 // The preconditioner is the inverse of the diagonal camera blocks
 // (block-Jacobi), or the learned factorised inverse G^T G (solver 3).
 #include <cuda_runtime.h>
