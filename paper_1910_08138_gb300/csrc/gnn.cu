@@ -899,7 +899,9 @@ __global__ void k_pcg_unconverged(int L, const int *run, const int *fail, const 
   if (r) atomicAdd(count, 1);
 }
 
-rpba_status launch_pcg_learned(Ctx *ctx, const int *run_dev, int *fail_dev) {
+// learned preconditioner for this LM iteration: network inference on the
+// current RCS and the factor G; fills F (failure flags reset first)
+rpba_status learned_setup(Ctx *ctx, const int *run_dev, int *fail_dev, FsaiApply *F) {
   if (!ctx->gnn_ready) {
     ctx->err = "solver 3 needs the network weights (rpba_set_gnn_weights)";
     return RPBA_ERR_STATE;
@@ -954,16 +956,21 @@ rpba_status launch_pcg_learned(Ctx *ctx, const int *run_dev, int *fail_dev) {
                                                      ctx->gnn_gam, ctx->pcg_F32);
       }));
   }
-  FsaiApply F;
-  F.M = M;
-  F.node_sys = ctx->node_sys;
-  F.nvo = ctx->node_voff;
-  F.P = P;
-  F.rh = ctx->gnn_rh;
-  F.y = ctx->gnn_y;
-  RPBA_TRY(pcg_iterate(ctx, run_dev, fail_dev, &F));
-  // judge: a sub-block the learned preconditioner did not bring to pcg_tol is
-  // solved again with block-Jacobi PCG
+  F->M = M;
+  F->node_sys = ctx->node_sys;
+  F->nvo = ctx->node_voff;
+  F->P = P;
+  F->rh = ctx->gnn_rh;
+  F->y = ctx->gnn_y;
+  return RPBA_OK;
+}
+
+// judge: a sub-block the learned preconditioner did not bring to pcg_tol is
+// solved again with block-Jacobi PCG (reads a count on the host)
+rpba_status learned_fallback(Ctx *ctx, const int *run_dev, int *fail_dev) {
+  cudaStream_t st = ctx->stream;
+  int L = ctx->L;
+  KL kl{ctx, &ctx->err};
   RPBA_CUDA(cudaMemsetAsync(ctx->counters + 9, 0, sizeof(int), st));
   RPBA_TRY(kl("k_pcg_unconverged", [&] {
     k_pcg_unconverged<<<nblk(L, 128), 128, 0, st>>>(L, run_dev, fail_dev, ctx->pcg_st, ctx->opt.pcg_tol,
@@ -980,6 +987,13 @@ rpba_status launch_pcg_learned(Ctx *ctx, const int *run_dev, int *fail_dev) {
     RPBA_TRY(kl("k_or_flags", [&] { k_or_flags<<<nblk(L, 128), 128, 0, st>>>(L, ctx->pcg_fail2, fail_dev); }));
   }
   return RPBA_OK;
+}
+
+rpba_status launch_pcg_learned(Ctx *ctx, const int *run_dev, int *fail_dev) {
+  FsaiApply F;
+  RPBA_TRY(learned_setup(ctx, run_dev, fail_dev, &F));
+  RPBA_TRY(pcg_iterate(ctx, run_dev, fail_dev, &F));
+  return learned_fallback(ctx, run_dev, fail_dev);
 }
 
 }  // namespace rpba

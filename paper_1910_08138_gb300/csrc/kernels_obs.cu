@@ -541,13 +541,14 @@ rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped, bool fp64) {
                                             ctx->opt.cond_max, it == maxit - 1));
     }
   }
+  if (!n_dropped) return RPBA_OK;  // no count wanted: no host synchronisation
   RPBA_CUDA(cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(int), ctx->stream));
   RPBA_KERNEL(ctx, "k_isect_count", k_isect_count<<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(
                                         ctx->isect_state, ctx->N, ctx->counters, ctx->counters + 1));
   int h[2];
   RPBA_CUDA(cudaMemcpyAsync(h, ctx->counters, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   RPBA_CUDA(cudaStreamSynchronize(ctx->stream));
-  if (n_dropped) *n_dropped = h[1];
+  *n_dropped = h[1];
   return RPBA_OK;
 }
 

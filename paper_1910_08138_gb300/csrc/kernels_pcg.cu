@@ -459,12 +459,13 @@ __global__ void k_pcg_live_count(int L, const int *live, int *count) {
   if (l < L && live[l]) atomicAdd(count, 1);
 }
 
-// Solve with the preconditioner set up by the caller: the inverse blocks in
-// ctx->pcg_Minv (block-Jacobi, one fused step kernel per iteration), or the
-// learned factor when fsai is given (the step split around the grid-wide
-// apply). Iterations stop per sub-block at the relative residual pcg_tol or
-// after pcg_max_iter.
-rpba_status pcg_iterate(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiApply *fsai) {
+// The phases of a PCG solve, with the preconditioner set up by the caller:
+// the inverse blocks in ctx->pcg_Minv (block-Jacobi, one fused step kernel
+// per iteration), or the learned factor when fsai is given (the step split
+// around the grid-wide apply). The loop stops per sub-block at the relative
+// residual pcg_tol or after pcg_max_iter; it reads the count of unconverged
+// sub-blocks every 8 iterations, so it runs outside any captured graph.
+rpba_status pcg_init(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiApply *fsai) {
   int L = ctx->L;
   cudaStream_t st = ctx->stream;
   if (fsai) {
@@ -482,6 +483,12 @@ rpba_status pcg_iterate(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiA
                                        ctx->y, ctx->pcg_x, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, ctx->pcg_st,
                                        ctx->pcg_live));
   }
+  return RPBA_OK;
+}
+
+rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai) {
+  int L = ctx->L;
+  cudaStream_t st = ctx->stream;
   int tiles = ctx->pcg_tiles_total;
   int maxit = ctx->opt.pcg_max_iter;
   for (int it = 0; it < maxit; it++) {
@@ -515,17 +522,34 @@ rpba_status pcg_iterate(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiA
       if (ctx->h_pinned_counter[8] == 0) break;
     }
   }
-  RPBA_KERNEL(ctx, "k_pcg_out", k_pcg_out<<<dim3(8, L), 256, 0, st>>>(run_dev, fail_dev, ctx->ycam_off,
-                                                                     ctx->npad, L, ctx->pcg_x, ctx->dC));
   return RPBA_OK;
 }
 
-rpba_status launch_pcg_blockjacobi(Ctx *ctx, const int *run_dev, int *fail_dev) {
+rpba_status pcg_out(Ctx *ctx, const int *run_dev, const int *fail_dev) {
+  int L = ctx->L;
+  RPBA_KERNEL(ctx, "k_pcg_out", k_pcg_out<<<dim3(8, L), 256, 0, ctx->stream>>>(run_dev, fail_dev, ctx->ycam_off,
+                                                                              ctx->npad, L, ctx->pcg_x, ctx->dC));
+  return RPBA_OK;
+}
+
+rpba_status pcg_iterate(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiApply *fsai) {
+  RPBA_TRY(pcg_init(ctx, run_dev, fail_dev, fsai));
+  RPBA_TRY(pcg_loop(ctx, fsai));
+  return pcg_out(ctx, run_dev, fail_dev);
+}
+
+// block-Jacobi: the inverse 6x6 camera blocks (failure flags reset first)
+rpba_status pcg_bj_setup(Ctx *ctx, const int *run_dev, int *fail_dev) {
   RPBA_CUDA(cudaMemsetAsync(fail_dev, 0, ctx->L * sizeof(int), ctx->stream));
   if (ctx->M)
     RPBA_KERNEL(ctx, "k_pcg_bj_setup", k_pcg_bj_setup<<<nblk(ctx->M, 128), 128, 0, ctx->stream>>>(
                                            ctx->M, ctx->cam_sub, ctx->cam_local, ctx->sub_cam_ptr, run_dev, ctx->S,
                                            ctx->S_off, ctx->npad, ctx->pcg_Minv, fail_dev));
+  return RPBA_OK;
+}
+
+rpba_status launch_pcg_blockjacobi(Ctx *ctx, const int *run_dev, int *fail_dev) {
+  RPBA_TRY(pcg_bj_setup(ctx, run_dev, fail_dev));
   return pcg_iterate(ctx, run_dev, fail_dev, nullptr);
 }
 

@@ -192,6 +192,8 @@ extern "C" void rpba_destroy(rpba_ctx *h) {
   if (ctx->h_pinned_counter) cudaFreeHost(ctx->h_pinned_counter);
   if (ctx->h_pinned_d) cudaFreeHost(ctx->h_pinned_d);
   free_graph(ctx->lm_graph);
+  free_graph(ctx->lm_graph_pre);
+  free_graph(ctx->lm_graph_post);
   for (auto &r : ctx->prof_recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -871,17 +873,51 @@ extern "C" rpba_status rpba_lm_step(rpba_ctx *h, double lambda, int32_t *accepte
 // ---------------------------------------------------------------------------
 // the iteration (Sec. 5)
 // ---------------------------------------------------------------------------
-// bact of all sub-blocks in lock step; returns LM iterations summed over
-// sub-blocks and the lock-step count
-// the work of one lock-step LM iteration after the RCS solve inputs are set:
-// build, solve, trial, decide, apply, and the running count to pinned memory
-static rpba_status lm_step_body(Ctx *ctx) {
-  RPBA_TRY(lm_iteration(ctx));
+// after the RCS solve: back-substitution, trial cost, LM decision and update,
+// and the running count for the host
+static rpba_status lm_post(Ctx *ctx) {
+  RPBA_TRY(launch_backsub_trial(ctx, ctx->lm_run));
   RPBA_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(int), ctx->stream));
   RPBA_TRY(launch_lm_decide(ctx));
   RPBA_TRY(launch_lm_apply(ctx, ctx->lm_acc));
   RPBA_CUDA(cudaMemcpyAsync(ctx->h_pinned_counter, ctx->counters, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   return RPBA_OK;
+}
+
+static bool pcg_solver(const Ctx *ctx) { return ctx->opt.solver == 1 || ctx->opt.solver == 3; }
+
+// PCG solvers: RCS assembly, preconditioner set-up and CG start (the part
+// before the host-driven CG loop)
+static rpba_status lm_pre_pcg(Ctx *ctx) {
+  RPBA_TRY(launch_build_rcs(ctx, ctx->lm_lambda, ctx->lm_run));
+  if (ctx->opt.solver == 3) {
+    RPBA_TRY(learned_setup(ctx, ctx->lm_run, ctx->lm_cholfail, &ctx->fsai));
+    return pcg_init(ctx, ctx->lm_run, ctx->lm_cholfail, &ctx->fsai);
+  }
+  RPBA_TRY(pcg_bj_setup(ctx, ctx->lm_run, ctx->lm_cholfail));
+  return pcg_init(ctx, ctx->lm_run, ctx->lm_cholfail, nullptr);
+}
+
+// PCG solvers: the CG loop and the solution (and solver 3's block-Jacobi judge)
+static rpba_status lm_cg(Ctx *ctx) {
+  const FsaiApply *f = ctx->opt.solver == 3 ? &ctx->fsai : nullptr;
+  RPBA_TRY(pcg_loop(ctx, f));
+  RPBA_TRY(pcg_out(ctx, ctx->lm_run, ctx->lm_cholfail));
+  if (ctx->opt.solver == 3) RPBA_TRY(learned_fallback(ctx, ctx->lm_run, ctx->lm_cholfail));
+  return RPBA_OK;
+}
+
+// the work of one lock-step LM iteration after the LM inputs are set: build,
+// solve, trial, decide, apply, and the running count to pinned memory
+static rpba_status lm_step_body(Ctx *ctx) {
+  if (pcg_solver(ctx)) {
+    RPBA_TRY(lm_pre_pcg(ctx));
+    RPBA_TRY(lm_cg(ctx));
+    return lm_post(ctx);
+  }
+  RPBA_TRY(launch_build_rcs(ctx, ctx->lm_lambda, ctx->lm_run));
+  RPBA_TRY(launch_solve_rcs(ctx, ctx->lm_run, ctx->lm_cholfail));
+  return lm_post(ctx);
 }
 
 static void free_graph(GraphRec *g) {
@@ -894,24 +930,30 @@ static void free_graph(GraphRec *g) {
   delete g;
 }
 
-// capture lm_step_body into a graph (all launch parameters are fixed per context)
-static rpba_status capture_lm_graph(Ctx *ctx) {
-  if (ctx->opt.solver == 1 || ctx->opt.solver == 3) {  // PCG stops on a device-side test read by the host
-    ctx->use_graphs = false;
-    return RPBA_OK;
-  }
+static void free_lm_graphs(Ctx *ctx) {
+  free_graph(ctx->lm_graph);
+  free_graph(ctx->lm_graph_pre);
+  free_graph(ctx->lm_graph_post);
+  ctx->lm_graph = ctx->lm_graph_pre = ctx->lm_graph_post = nullptr;
+}
+
+// capture fn's launches into a graph (all launch parameters are fixed per
+// context). *out stays NULL when the stream cannot be captured (e.g. the
+// legacy default stream) or the capture fails: the caller then runs eagerly.
+template <class F>
+static rpba_status capture_graph(Ctx *ctx, GraphRec **out, F fn) {
+  *out = nullptr;
   GraphRec *g = new GraphRec();
   g->with_events = ctx->prof_enabled;
   g->prof_only = ctx->prof_only;
   cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) {
     delete g;
-    ctx->use_graphs = false;  // e.g. the legacy default stream: run eagerly
     cudaGetLastError();
     return RPBA_OK;
   }
   ctx->capture = g;
-  rpba_status st = lm_step_body(ctx);
+  rpba_status st = fn();
   ctx->capture = nullptr;
   cudaGraph_t graph = nullptr;
   e = cudaStreamEndCapture(ctx->stream, &graph);
@@ -919,7 +961,6 @@ static rpba_status capture_lm_graph(Ctx *ctx) {
     if (graph) cudaGraphDestroy(graph);
     free_graph(g);
     cudaGetLastError();  // clear the capture error; run eagerly from now on
-    ctx->use_graphs = false;
     ctx->err.clear();
     return RPBA_OK;
   }
@@ -930,34 +971,62 @@ static rpba_status capture_lm_graph(Ctx *ctx) {
     ctx->err = std::string("graph instantiate: ") + cudaGetErrorString(e);
     return RPBA_ERR_CUDA;
   }
-  ctx->lm_graph = g;
+  *out = g;
   return RPBA_OK;
 }
 
-// one lock-step LM iteration through the graph (or eagerly), then the host
-// reads the running count
-static rpba_status lm_step_run(Ctx *ctx) {
-  if (ctx->lm_graph &&
-      (ctx->lm_graph->with_events != ctx->prof_enabled || ctx->lm_graph->prof_only != ctx->prof_only)) {
-    free_graph(ctx->lm_graph);  // timing nodes only while profiling
-    ctx->lm_graph = nullptr;
+// count a replayed graph's kernels (and add their event times while
+// profiling); the stream has been synchronised
+static rpba_status account(Ctx *ctx, GraphRec *g) {
+  for (const char *k : g->kernels) {
+    ctx->launches++;
+    ctx->launch_by_name[k]++;
   }
-  if (ctx->use_graphs && !ctx->lm_graph) RPBA_TRY(capture_lm_graph(ctx));
-  if (ctx->use_graphs && ctx->lm_graph) {
-    GraphRec *g = ctx->lm_graph;
-    RPBA_CUDA(cudaGraphLaunch(g->exec, ctx->stream));
-    RPBA_TRY(sync(ctx));
-    for (const char *k : g->kernels) {
-      ctx->launches++;
-      ctx->launch_by_name[k]++;
+  if (ctx->prof_enabled)
+    for (auto &ev : g->events) {
+      float t = 0.f;
+      RPBA_CUDA(cudaEventElapsedTime(&t, ev.a, ev.b));
+      ctx->prof_ms[ev.name] += t;
     }
-    if (ctx->prof_enabled)
-      for (auto &ev : g->events) {
-        float t = 0.f;
-        RPBA_CUDA(cudaEventElapsedTime(&t, ev.a, ev.b));
-        ctx->prof_ms[ev.name] += t;
+  return RPBA_OK;
+}
+
+// one lock-step LM iteration, then the host reads the running count. Direct
+// solvers: one captured graph. PCG solvers: a graph up to the CG start, the
+// CG loop run from the host (it stops on a count read every 8 iterations),
+// and a graph from the back-substitution on.
+static rpba_status lm_step_run(Ctx *ctx) {
+  GraphRec *any = ctx->lm_graph ? ctx->lm_graph : ctx->lm_graph_pre;
+  if (any && (any->with_events != ctx->prof_enabled || any->prof_only != ctx->prof_only))
+    free_lm_graphs(ctx);  // timing nodes only while profiling
+  if (pcg_solver(ctx)) {
+    if (ctx->use_graphs && !ctx->lm_graph_pre) {
+      RPBA_TRY(capture_graph(ctx, &ctx->lm_graph_pre, [&] { return lm_pre_pcg(ctx); }));
+      if (ctx->lm_graph_pre) RPBA_TRY(capture_graph(ctx, &ctx->lm_graph_post, [&] { return lm_post(ctx); }));
+      if (!ctx->lm_graph_pre || !ctx->lm_graph_post) {
+        free_lm_graphs(ctx);
+        ctx->use_graphs = false;
       }
-    return RPBA_OK;
+    }
+    if (ctx->use_graphs) {
+      RPBA_CUDA(cudaGraphLaunch(ctx->lm_graph_pre->exec, ctx->stream));
+      RPBA_TRY(lm_cg(ctx));
+      RPBA_CUDA(cudaGraphLaunch(ctx->lm_graph_post->exec, ctx->stream));
+      RPBA_TRY(sync(ctx));
+      RPBA_TRY(account(ctx, ctx->lm_graph_pre));
+      return account(ctx, ctx->lm_graph_post);
+    }
+    RPBA_TRY(lm_step_body(ctx));
+    return sync(ctx);
+  }
+  if (ctx->use_graphs && !ctx->lm_graph) {
+    RPBA_TRY(capture_graph(ctx, &ctx->lm_graph, [&] { return lm_step_body(ctx); }));
+    if (!ctx->lm_graph) ctx->use_graphs = false;
+  }
+  if (ctx->use_graphs && ctx->lm_graph) {
+    RPBA_CUDA(cudaGraphLaunch(ctx->lm_graph->exec, ctx->stream));
+    RPBA_TRY(sync(ctx));
+    return account(ctx, ctx->lm_graph);
   }
   RPBA_TRY(lm_step_body(ctx));
   return sync(ctx);

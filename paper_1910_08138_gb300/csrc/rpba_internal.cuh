@@ -258,6 +258,7 @@ struct Ctx {
   // CUDA graph of one lock-step LM iteration (captured on first use)
   GraphRec *capture = nullptr;  // non-null while capturing
   GraphRec *lm_graph = nullptr;
+  GraphRec *lm_graph_pre = nullptr, *lm_graph_post = nullptr;  // PCG solvers: around the CG loop
   bool use_graphs = true;
   cudaStream_t own_stream = nullptr;  // created when the caller passes the legacy default stream
   int *h_pinned_counter = nullptr;
@@ -276,6 +277,7 @@ struct Ctx {
   int *gnn_ok = nullptr, *pcg_run2 = nullptr, *pcg_fail2 = nullptr;
   bool gnn_ready = false;
   long long gnn_fallbacks = 0;  // sub-block solves re-done by block-Jacobi PCG
+  FsaiApply fsai;               // the learned factor of the current LM iteration
 };
 
 // device allocation through the context's allocator (freed at destroy)
@@ -385,6 +387,13 @@ rpba_status launch_pcg_learned(Ctx *ctx, const int *run_dev, int *fail_dev);
 void build_camera_graph(Ctx *ctx, const std::vector<int> &inst_obs_ptr, const std::vector<int> &obs_cam_sorted,
                         const std::vector<int> &inst_sub, const std::vector<int> &cam_local);
 rpba_status pcg_iterate(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiApply *fsai);
+// the phases of pcg_iterate, and the preconditioner set-ups
+rpba_status pcg_init(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiApply *fsai);
+rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai);
+rpba_status pcg_out(Ctx *ctx, const int *run_dev, const int *fail_dev);
+rpba_status pcg_bj_setup(Ctx *ctx, const int *run_dev, int *fail_dev);
+rpba_status learned_setup(Ctx *ctx, const int *run_dev, int *fail_dev, FsaiApply *F);
+rpba_status learned_fallback(Ctx *ctx, const int *run_dev, int *fail_dev);
 // z = P^-1 r with the learned factor over the cameras of the live systems
 // (live NULL: all); counted on ctx when given, else launched on F.stream
 rpba_status fsai_apply(Ctx *ctx, const FsaiApply &F, const int *live, const double *r, double *z,
