@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--config", type=int, default=2)
     p.add_argument("--precision", type=int, default=1)
-    p.add_argument("--solver", type=int, default=1)
+    p.add_argument("--solver", type=int, default=4)
     p.add_argument("--no-extras", action="store_true", help="skip e2e / time-to-RMS / cpu legs")
     return p.parse_args()
 
@@ -217,7 +217,7 @@ def train_preconditioner(stream):
     return w, time.perf_counter() - t0
 
 
-FORMS = {"chosen": (1, 1), "plain": (0, 0)}  # (precision, solver)
+FORMS = {"chosen": (1, 4), "plain": (0, 0)}  # (precision, solver); solver 4 = auto
 
 
 # ---------------------------------------------------------------------------
@@ -282,6 +282,7 @@ def run_ours(args, rank, world):
     if gnn_w is not None:
         ctx.set_gnn_weights(gnn_w)
     ctx.intersect()
+    solver = ctx.resolved_options().solver  # auto (4) resolved by the library
     n_sub = [6 * len(ctx.sub_cameras(l)) for l in range(ctx.L)]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
     # the last warm-up step times every kernel (the breakdown and the dominant
@@ -315,7 +316,7 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
         k_act = rep["active_obs"]
-        if args.solver in (1, 3):
+        if solver in (1, 3):
             pcg_iters.append(ctx.solver_stats()[0])
     clk = clocks.stop()
     prof, launches = ctx.profile_read()
@@ -364,7 +365,8 @@ def run_ours(args, rank, world):
             "vs_baseline": None, "dtype": "f32" if args.precision == 1 else "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.config], "precision": "mixed FP32/FP64" if args.precision == 1 else "FP64",
                        "solver": {0: "FP64 Cholesky", 1: "FP64 PCG, block-Jacobi", 2: "FP32 Cholesky + FP64 refinement",
-                                  3: "FP64 PCG, learned preconditioner"}.get(args.solver),
+                                  3: "FP64 PCG, learned preconditioner"}.get(solver)
+                       + (" (auto: PCG up to 64 sub-blocks, else the direct solve)" if args.solver == 4 else ""),
                        "l2": "flushed between steps (256 MB write)", "n_obs": K, "subblocks": ctx.L,
                        "step": "1 LM iteration of all sub-blocks + exchange + robust weights + TP intersection",
                        "parallelism": f"replicas x{world}"},

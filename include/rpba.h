@@ -71,6 +71,9 @@ typedef struct {
   const int32_t *cam_block;
 } rpba_problem;
 
+/* solver 4 (auto) picks block-Jacobi PCG for at most this many sub-blocks */
+#define RPBA_AUTO_PCG_MAX_SUBBLOCKS 64
+
 /* Options; rpba_default_options fills the paper's values (Sec. 5.3, 5.5). */
 typedef struct {
   double lambda0;        /* LM damping N + lambda diag(N), 1e-4 (Sec. 5.5) */
@@ -92,8 +95,10 @@ typedef struct {
   int32_t solver;        /* RCS solve: 0 FP64 Cholesky; 1 FP64 PCG with block-Jacobi
                             preconditioning (Sec. 5.5) to pcg_tol; 2 FP32 Cholesky of the
                             Jacobi-scaled RCS with FP64 iterative refinement; 3 FP64 PCG
-                            with the learned block preconditioner (rpba_set_gnn_weights),
-                            block-Jacobi PCG again for a sub-block it leaves above pcg_tol */
+                            with the learned preconditioner (rpba_set_gnn_weights),
+                            block-Jacobi PCG again for a sub-block it leaves above pcg_tol;
+                            4 auto: 1 for at most RPBA_AUTO_PCG_MAX_SUBBLOCKS sub-blocks,
+                            else 2 (resolved at create, see rpba_get_options) */
   double pcg_tol;        /* relative residual of the PCG solve, 1e-8 */
   int32_t pcg_max_iter;  /* PCG iteration cap, 500 */
   int32_t ir_steps;      /* refinement passes of solver 2 after the first solve, 2 */
@@ -153,6 +158,8 @@ rpba_status rpba_get_points(rpba_ctx *ctx, double *X /* n_points x 3 */, uint8_t
 /* ---- state access and single steps (used by the parity tests) ---------- */
 
 rpba_status rpba_info(rpba_ctx *ctx, int32_t *n_subblocks, int32_t *n_instances);
+/* the context's options, with solver 4 (auto) resolved */
+rpba_status rpba_get_options(rpba_ctx *ctx, rpba_options *out);
 /* cameras of sub-block l in RCS row order (ascending global id); n_out = count */
 rpba_status rpba_sub_cameras(rpba_ctx *ctx, int32_t l, int32_t *cams, int32_t *n_out);
 rpba_status rpba_set_cameras(rpba_ctx *ctx, const double *pose);

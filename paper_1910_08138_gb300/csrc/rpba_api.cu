@@ -220,6 +220,10 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
     L = std::max(L, s + 1);
   }
   ctx->L = L;
+  // solver 4 (auto): lock-step PCG runs as many iterations as its slowest
+  // sub-block needs, a maximum that grows with the number of sub-blocks; the
+  // direct solve's critical path is set by the largest sub-block alone
+  if (ctx->opt.solver == 4) ctx->opt.solver = L <= RPBA_AUTO_PCG_MAX_SUBBLOCKS ? 1 : 2;
   for (int k = 0; k < K; k++) {
     if (pb->obs_cam[k] < 0 || pb->obs_cam[k] >= M || pb->obs_point[k] < 0 || pb->obs_point[k] >= N) {
       ctx->err = "observation index out of range";
@@ -554,7 +558,7 @@ extern "C" rpba_status rpba_create(const rpba_problem *prob, const rpba_options 
   Ctx *ctx = &h->c;
   if (opt) ctx->opt = *opt;
   else rpba_default_options(&ctx->opt);
-  if ((ctx->opt.precision != 0 && ctx->opt.precision != 1) || ctx->opt.solver < 0 || ctx->opt.solver > 3 ||
+  if ((ctx->opt.precision != 0 && ctx->opt.precision != 1) || ctx->opt.solver < 0 || ctx->opt.solver > 4 ||
       ctx->opt.ir_steps < 0 || ctx->opt.ir_steps > 20 || ctx->opt.pcg_max_iter < 1 || !(ctx->opt.pcg_tol > 0.0)) {
     ctx->err = "invalid precision / solver / ir_steps option";
     *out = h;
@@ -1196,5 +1200,12 @@ extern "C" rpba_status rpba_solver_fallbacks(rpba_ctx *h, int64_t *n) {
 extern "C" rpba_status rpba_profile_select(rpba_ctx *h, const char *kernel) {
   CTX_OR_FAIL;
   ctx->prof_only = kernel ? std::string(kernel) : std::string();
+  return RPBA_OK;
+}
+
+extern "C" rpba_status rpba_get_options(rpba_ctx *h, rpba_options *out) {
+  CTX_OR_FAIL;
+  if (!out) return RPBA_ERR_INVALID_ARG;
+  *out = ctx->opt;
   return RPBA_OK;
 }

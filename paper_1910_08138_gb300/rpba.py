@@ -93,6 +93,7 @@ def load(build_if_missing: bool = True):
         "rpba_get_cameras": (C.c_int, [vp, _dp]),
         "rpba_get_points": (C.c_int, [vp, _dp, _u8]),
         "rpba_info": (C.c_int, [vp, _ip, _ip]),
+        "rpba_get_options": (C.c_int, [vp, C.POINTER(Options)]),
         "rpba_sub_cameras": (C.c_int, [vp, C.c_int32, _ip, _ip]),
         "rpba_set_cameras": (C.c_int, [vp, _dp]),
         "rpba_set_points": (C.c_int, [vp, _dp, _u8]),
@@ -398,6 +399,12 @@ class Rpba:
         it = np.zeros(self.L, np.int32)
         self._c(load().rpba_bact(self._h, _i(it)))
         return it
+
+    def resolved_options(self):
+        """The context's options, with solver 4 (auto) resolved."""
+        o = Options()
+        self._c(load().rpba_get_options(self._h, C.byref(o)))
+        return o
 
     def solver_stats(self):
         it, rr = np.zeros(self.L, np.int32), np.zeros(self.L)

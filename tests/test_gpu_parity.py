@@ -321,3 +321,16 @@ def test_first_intersection_decides_the_minimum():
         assert abs(rg["rms"] - ro["rms"]) <= (1e-9 if precision == 0 else 1e-3), info
         if precision == 0:
             assert rg["deleted_points"] == ro["deleted_points"]
+
+
+def test_auto_solver_choice():
+    """solver 4 resolves at create: block-Jacobi PCG for at most 64 sub-blocks,
+    else the FP32 Cholesky with FP64 refinement."""
+    few = rpba.Rpba(synth.config(1), precision=1, solver=4)
+    assert few.L == 2 and few.resolved_options().solver == 1
+    prob = synth.config(3, n_blocks=24)
+    many = rpba.Rpba(prob, precision=1, solver=4)
+    assert many.L > 64 and many.resolved_options().solver == 2
+    ro = oracle.Oracle(synth.config(1)).run(robust=1, robust_from_start=1)
+    rg = rpba.Rpba(synth.config(1), precision=1, solver=4, robust=1, robust_from_start=1).iterate()
+    assert abs(rg["rms"] - ro["rms"]) <= 1e-3
