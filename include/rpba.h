@@ -71,8 +71,12 @@ typedef struct {
   const int32_t *cam_block;
 } rpba_problem;
 
-/* solver 4 (auto) picks block-Jacobi PCG for at most this many sub-blocks */
+/* solver 4 (auto) starts with block-Jacobi PCG for at most this many
+ * sub-blocks (else the direct FP32 Cholesky with FP64 refinement), and moves
+ * to the direct solver for good once a PCG solve needs more than this many
+ * lock-step iterations (one iteration costs ~1/50 of a direct solve) */
 #define RPBA_AUTO_PCG_MAX_SUBBLOCKS 64
+#define RPBA_AUTO_PCG_MAX_ITER 48
 
 /* Options; rpba_default_options fills the paper's values (Sec. 5.3, 5.5). */
 typedef struct {
@@ -98,7 +102,8 @@ typedef struct {
                             with the learned preconditioner (rpba_set_gnn_weights),
                             block-Jacobi PCG again for a sub-block it leaves above pcg_tol;
                             4 auto: 1 for at most RPBA_AUTO_PCG_MAX_SUBBLOCKS sub-blocks,
-                            else 2 (resolved at create, see rpba_get_options) */
+                            else 2; 1 becomes 2 after a solve of more than
+                            RPBA_AUTO_PCG_MAX_ITER iterations (rpba_get_options) */
   double pcg_tol;        /* relative residual of the PCG solve, 1e-8 */
   int32_t pcg_max_iter;  /* PCG iteration cap, 500 */
   int32_t ir_steps;      /* refinement passes of solver 2 after the first solve, 2 */
@@ -158,7 +163,8 @@ rpba_status rpba_get_points(rpba_ctx *ctx, double *X /* n_points x 3 */, uint8_t
 /* ---- state access and single steps (used by the parity tests) ---------- */
 
 rpba_status rpba_info(rpba_ctx *ctx, int32_t *n_subblocks, int32_t *n_instances);
-/* the context's options, with solver 4 (auto) resolved */
+/* the context's options, with solver 4 (auto) resolved to the solver the next
+ * LM step uses */
 rpba_status rpba_get_options(rpba_ctx *ctx, rpba_options *out);
 /* cameras of sub-block l in RCS row order (ascending global id); n_out = count */
 rpba_status rpba_sub_cameras(rpba_ctx *ctx, int32_t l, int32_t *cams, int32_t *n_out);
@@ -204,9 +210,10 @@ rpba_status rpba_lm_step(rpba_ctx *ctx, double lambda, int32_t *accepted, double
  * CUDA. */
 rpba_status rpba_bact(rpba_ctx *ctx, int32_t *iters);
 
-/* PCG solvers (solver = 1 or 3): iterations and final relative residual
- * ||r|| / ||y|| of every sub-block in the last PCG pass (n_subblocks values
- * each, nullable). Errors: STATE when the context does not use PCG. */
+/* PCG solvers (solver = 1, 3, or 4 while or after it used PCG): iterations
+ * and final relative residual ||r|| / ||y|| of every sub-block in the last PCG
+ * pass (n_subblocks values each, nullable). Errors: STATE when the context
+ * has no PCG state. */
 rpba_status rpba_solver_stats(rpba_ctx *ctx, int32_t *iters, double *relres);
 /* solver 3: number of sub-block solves, since create, that the learned
  * preconditioner left above pcg_tol and block-Jacobi PCG solved again */

@@ -486,8 +486,9 @@ rpba_status pcg_init(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiAppl
   return RPBA_OK;
 }
 
-rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai) {
+rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai, int *iters) {
   int L = ctx->L;
+  if (iters) *iters = 0;
   cudaStream_t st = ctx->stream;
   int tiles = ctx->pcg_tiles_total;
   int maxit = ctx->opt.pcg_max_iter;
@@ -519,6 +520,7 @@ rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai) {
       RPBA_CUDA(cudaMemcpyAsync(ctx->h_pinned_counter + 8, ctx->counters + 8, sizeof(int), cudaMemcpyDeviceToHost,
                                 st));
       RPBA_CUDA(cudaStreamSynchronize(st));
+      if (iters) *iters = it + 1;
       if (ctx->h_pinned_counter[8] == 0) break;
     }
   }
@@ -534,7 +536,7 @@ rpba_status pcg_out(Ctx *ctx, const int *run_dev, const int *fail_dev) {
 
 rpba_status pcg_iterate(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiApply *fsai) {
   RPBA_TRY(pcg_init(ctx, run_dev, fail_dev, fsai));
-  RPBA_TRY(pcg_loop(ctx, fsai));
+  RPBA_TRY(pcg_loop(ctx, fsai, nullptr));
   return pcg_out(ctx, run_dev, fail_dev);
 }
 

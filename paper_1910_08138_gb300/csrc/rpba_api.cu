@@ -223,7 +223,10 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   // solver 4 (auto): lock-step PCG runs as many iterations as its slowest
   // sub-block needs, a maximum that grows with the number of sub-blocks; the
   // direct solve's critical path is set by the largest sub-block alone
-  if (ctx->opt.solver == 4) ctx->opt.solver = L <= RPBA_AUTO_PCG_MAX_SUBBLOCKS ? 1 : 2;
+  if (ctx->opt.solver == 4) {
+    ctx->auto_solver = true;
+    ctx->opt.solver = L <= RPBA_AUTO_PCG_MAX_SUBBLOCKS ? 1 : 2;
+  }
   for (int k = 0; k < K; k++) {
     if (pb->obs_cam[k] < 0 || pb->obs_cam[k] >= M || pb->obs_point[k] < 0 || pb->obs_point[k] >= N) {
       ctx->err = "observation index out of range";
@@ -498,7 +501,7 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   RPBA_TRY(upload(ctx, &ctx->linv_off, loff.data(), (size_t)L));
   RPBA_TRY(upload(ctx, &ctx->sched, ctx->h_sched.data(), ctx->h_sched.size()));
   RPBA_TRY(alloc_n(ctx, &ctx->Linv64, (size_t)std::max(ltot, 1)));
-  if (ctx->opt.solver == 1 || ctx->opt.solver == 3) {
+  if (ctx->opt.solver == 1 || ctx->opt.solver == 3 || ctx->auto_solver) {
     RPBA_TRY(alloc_n(ctx, &ctx->pcg_Minv, 36 * (size_t)std::max(M, 1)));
     RPBA_TRY(alloc_n(ctx, &ctx->pcg_x, (size_t)std::max(yt, 1)));
     RPBA_TRY(alloc_n(ctx, &ctx->pcg_r, (size_t)std::max(yt, 1)));
@@ -513,7 +516,7 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
     ctx->pcg_tiles_total = pt[L];
     RPBA_TRY(upload(ctx, &ctx->pcg_tiles, pt.data(), (size_t)L + 1));
   }
-  if (ctx->opt.solver == 2) {
+  if (ctx->opt.solver == 2 || ctx->auto_solver) {
     RPBA_TRY(alloc_n(ctx, &ctx->S32, (size_t)std::max(stot, 1LL)));
     RPBA_TRY(upload(ctx, &ctx->S32_off, soff.data(), (size_t)L));
     RPBA_TRY(alloc_n(ctx, &ctx->Linv32, (size_t)std::max(ltot, 1)));
@@ -905,7 +908,12 @@ static rpba_status lm_pre_pcg(Ctx *ctx) {
 // PCG solvers: the CG loop and the solution (and solver 3's block-Jacobi judge)
 static rpba_status lm_cg(Ctx *ctx) {
   const FsaiApply *f = ctx->opt.solver == 3 ? &ctx->fsai : nullptr;
-  RPBA_TRY(pcg_loop(ctx, f));
+  int iters = 0;
+  RPBA_TRY(pcg_loop(ctx, f, &iters));
+  // solver 4 (auto): a solve that needed more lock-step iterations than the
+  // direct solve is worth moves the context to the direct solver, from the
+  // next LM step on
+  if (ctx->auto_solver && iters > RPBA_AUTO_PCG_MAX_ITER) ctx->auto_switch = true;
   RPBA_TRY(pcg_out(ctx, ctx->lm_run, ctx->lm_cholfail));
   if (ctx->opt.solver == 3) RPBA_TRY(learned_fallback(ctx, ctx->lm_run, ctx->lm_cholfail));
   return RPBA_OK;
@@ -999,7 +1007,7 @@ static rpba_status account(Ctx *ctx, GraphRec *g) {
 // solvers: one captured graph. PCG solvers: a graph up to the CG start, the
 // CG loop run from the host (it stops on a count read every 8 iterations),
 // and a graph from the back-substitution on.
-static rpba_status lm_step_run(Ctx *ctx) {
+static rpba_status lm_step_exec(Ctx *ctx) {
   GraphRec *any = ctx->lm_graph ? ctx->lm_graph : ctx->lm_graph_pre;
   if (any && (any->with_events != ctx->prof_enabled || any->prof_only != ctx->prof_only))
     free_lm_graphs(ctx);  // timing nodes only while profiling
@@ -1034,6 +1042,16 @@ static rpba_status lm_step_run(Ctx *ctx) {
   }
   RPBA_TRY(lm_step_body(ctx));
   return sync(ctx);
+}
+
+static rpba_status lm_step_run(Ctx *ctx) {
+  RPBA_TRY(lm_step_exec(ctx));
+  if (ctx->auto_switch) {  // the step is complete: its graphs can go
+    ctx->auto_switch = false;
+    ctx->opt.solver = 2;
+    free_lm_graphs(ctx);
+  }
+  return RPBA_OK;
 }
 
 // bact of all sub-blocks in lock step; returns LM iterations summed over
@@ -1176,7 +1194,7 @@ extern "C" rpba_status rpba_profile_read(rpba_ctx *h, int32_t max_kernels, char 
 
 extern "C" rpba_status rpba_solver_stats(rpba_ctx *h, int32_t *iters, double *relres) {
   CTX_OR_FAIL;
-  if ((ctx->opt.solver != 1 && ctx->opt.solver != 3) || !ctx->pcg_st) {
+  if (!ctx->pcg_st) {
     ctx->err = "solver statistics exist for the PCG solvers only";
     return RPBA_ERR_STATE;
   }

@@ -278,6 +278,8 @@ struct Ctx {
   bool gnn_ready = false;
   long long gnn_fallbacks = 0;  // sub-block solves re-done by block-Jacobi PCG
   FsaiApply fsai;               // the learned factor of the current LM iteration
+  bool auto_solver = false;     // solver 4: PCG until a solve needs too many iterations
+  bool auto_switch = false;     // ... then the direct solver from the next LM step
 };
 
 // device allocation through the context's allocator (freed at destroy)
@@ -389,7 +391,7 @@ void build_camera_graph(Ctx *ctx, const std::vector<int> &inst_obs_ptr, const st
 rpba_status pcg_iterate(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiApply *fsai);
 // the phases of pcg_iterate, and the preconditioner set-ups
 rpba_status pcg_init(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiApply *fsai);
-rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai);
+rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai, int *iters /* lock-step iterations run, nullable */);
 rpba_status pcg_out(Ctx *ctx, const int *run_dev, const int *fail_dev);
 rpba_status pcg_bj_setup(Ctx *ctx, const int *run_dev, int *fail_dev);
 rpba_status learned_setup(Ctx *ctx, const int *run_dev, int *fail_dev, FsaiApply *F);

@@ -334,3 +334,23 @@ def test_auto_solver_choice():
     ro = oracle.Oracle(synth.config(1)).run(robust=1, robust_from_start=1)
     rg = rpba.Rpba(synth.config(1), precision=1, solver=4, robust=1, robust_from_start=1).iterate()
     assert abs(rg["rms"] - ro["rms"]) <= 1e-3
+
+
+def test_auto_solver_switches_after_a_slow_pcg_solve():
+    """solver 4 keeps PCG while its solves take few lock-step iterations and
+    moves to the direct solver after the first LM step whose solve needs more
+    than RPBA_AUTO_PCG_MAX_ITER; the run ends at the direct solver's RMS."""
+    prob = synth.config(4, scale=0.1)
+    ctx = rpba.Rpba(prob, precision=1, solver=4, robust=1, robust_from_start=1)
+    assert ctx.L <= 64 and ctx.resolved_options().solver == 1
+    rg = ctx.iterate()
+    it, _ = ctx.solver_stats()  # the last PCG pass, the one that switched
+    assert it.max() > 48 and ctx.resolved_options().solver == 2
+    r2 = rpba.Rpba(prob, precision=1, solver=2, robust=1, robust_from_start=1).iterate()
+    assert abs(rg["rms"] - r2["rms"]) <= 1e-3, (rg["rms"], r2["rms"])
+    few = rpba.Rpba(synth.config(2), precision=1, solver=4, robust=1, robust_from_start=1)
+    few.iterate()
+    it, _ = few.solver_stats()
+    assert it.max() <= 48 and few.resolved_options().solver == 1
+    for c in (ctx, few):
+        c.close()
