@@ -21,19 +21,19 @@ OPTIONS = dict(robust=1, robust_from_start=1)
 
 
 def main(configs):
-    data = json.load(open(OUT)) if os.path.exists(OUT) else {}
     for c in configs:
         prob = synth.config(c)
         t0 = time.perf_counter()
         rep = oracle.Oracle(prob).run(**OPTIONS)
         dt = time.perf_counter() - t0
+        data = json.load(open(OUT)) if os.path.exists(OUT) else {}  # written after every block
         data[f"config{c}"] = {"rms": rep["rms"], "sigma0": rep["sigma0"], "outer": rep["outer"],
                               "inner_total": rep["inner_total"], "deleted_points": rep["deleted_points"],
                               "active_obs": rep["active_obs"], "options": OPTIONS,
                               "oracle_seconds_single_thread": round(dt, 1),
                               "source": "oracle/make_targets.py (FP64 CPU oracle)"}
+        json.dump(data, open(OUT, "w"), indent=1, sort_keys=True)
         print(c, data[f"config{c}"], flush=True)
-    json.dump(data, open(OUT, "w"), indent=1, sort_keys=True)
 
 
 if __name__ == "__main__":

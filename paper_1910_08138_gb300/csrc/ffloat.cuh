@@ -1,0 +1,123 @@
+// ffloat.cuh -- float-float arithmetic for the FP32 form's residuals.
+//
+// A value is carried as an unevaluated sum hi + lo of two floats (about 48
+// significant bits). The building blocks are the classical error-free
+// transformations: Knuth's TwoSum (a + b = s + e exactly, any a, b), Dekker's
+// Fast2Sum (the same when |a| >= |b|) and the FMA form of Dekker's
+// TwoProduct (a b = p + e exactly). A dot product of float-float operands
+// follows the compensated scheme of Ogita, Rump and Oishi ("Accurate sum and
+// dot product", SIAM J. Sci. Comput. 26, 2005, Algorithm Dot2), with the
+// cross terms hi*lo folded into the compensation.
+//
+// The rounded intrinsics (__fadd_rn, __fmul_rn, __fmaf_rn) are used
+// throughout: the compiler never contracts or reassociates them, which the
+// transformations rely on.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace rpba {
+
+__device__ __forceinline__ float ff_two_sum(float a, float b, float &e) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return s;
+}
+
+// |a| >= |b| (or a == 0)
+__device__ __forceinline__ float ff_fast_two_sum(float a, float b, float &e) {
+  float s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+  return s;
+}
+
+__device__ __forceinline__ float ff_two_prod(float a, float b, float &e) {
+  float p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+  return p;
+}
+
+// sum_c (ah[c] + al[c]) (bh[c] + bl[c]) over three terms, as hi + lo
+__device__ __forceinline__ float ff_dot3(const float *ah, const float *al, const float *bh, const float *bl,
+                                         float &lo) {
+  float pe;
+  float s = ff_two_prod(ah[0], bh[0], pe);
+  float c = __fmaf_rn(al[0], bh[0], __fmaf_rn(ah[0], bl[0], pe));
+#pragma unroll
+  for (int k = 1; k < 3; k++) {
+    float p = ff_two_prod(ah[k], bh[k], pe);
+    float se;
+    s = ff_two_sum(s, p, se);
+    c = __fadd_rn(c, __fadd_rn(se, __fmaf_rn(al[k], bh[k], __fmaf_rn(ah[k], bl[k], pe))));
+  }
+  return ff_fast_two_sum(s, c, lo);
+}
+
+// (ah + al) / (bh + bl) as hi + lo, bh != 0: the quotient of the leading
+// parts, then one correction from the remainder (computed with an FMA)
+__device__ __forceinline__ float ff_div(float ah, float al, float bh, float bl, float rb, float &lo) {
+  float q = __fmul_rn(ah, rb);
+  float rho = __fmaf_rn(-q, bh, ah);
+  rho = __fmaf_rn(-q, bl, __fadd_rn(rho, al));
+  lo = __fmul_rn(rho, rb);
+  return q;
+}
+
+// host-side or device-side split of a double into hi + lo
+__host__ __device__ __forceinline__ void ff_split(double x, float &hi, float &lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+
+// Camera record of the FP32 form's residuals, FF_CAM floats per camera:
+// rotation R (row-major) hi [0, 9) and lo [9, 18), centre C = -R^T t hi
+// [18, 21) and lo [21, 24), focal length hi [24] and lo [25], zero padding.
+#define FF_CAM 32
+
+__host__ __device__ inline void ff_camera_record(const double *R, const double *t, double f, float *o) {
+  for (int e = 0; e < 9; e++) ff_split(R[e], o[e], o[9 + e]);
+  for (int c = 0; c < 3; c++) {
+    double C = -(R[c] * t[0] + R[3 + c] * t[1] + R[6 + c] * t[2]);
+    ff_split(C, o[18 + c], o[21 + c]);
+  }
+  ff_split(f, o[24], o[25]);
+  for (int e = 26; e < FF_CAM; e++) o[e] = 0.f;
+}
+
+// Reprojection residual (Eq. ta) of a point X = Xh + Xl in the camera of
+// record cf against an observation given relative to the principal point as
+// (oxh + oxl, oyh + oyl): X_c = R (X - C) as float-float, the perspective
+// division with one remainder correction, f times the quotient, and the
+// subtraction of the observation, whose leading parts cancel exactly. The
+// residual is returned in FP32 (it is small: its leading bits are exact).
+// Returns z_c > 0; the residual is computed either way, as in FP64.
+__device__ __forceinline__ bool ff_residual(const float *cf, const float *Xh, const float *Xl, float oxh, float oxl,
+                                            float oyh, float oyl, float &r0, float &r1) {
+  float dh[3], dl[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    float e;
+    dh[c] = ff_two_sum(Xh[c], -cf[18 + c], e);
+    dl[c] = __fadd_rn(e, __fsub_rn(Xl[c], cf[21 + c]));
+  }
+  float xl, yl, zl;
+  float xh = ff_dot3(cf + 0, cf + 9, dh, dl, xl);
+  float yh = ff_dot3(cf + 3, cf + 12, dh, dl, yl);
+  float zh = ff_dot3(cf + 6, cf + 15, dh, dl, zl);
+  float rz = __frcp_rn(zh);
+  float qxl, qyl;
+  float qx = ff_div(xh, xl, zh, zl, rz, qxl);
+  float qy = ff_div(yh, yl, zh, zl, rz, qyl);
+  float fh = cf[24], fl = cf[25];
+  float ue, ve;
+  float uh = ff_two_prod(fh, qx, ue);
+  ue = __fmaf_rn(fl, qx, __fmaf_rn(fh, qxl, ue));
+  float vh = ff_two_prod(fh, qy, ve);
+  ve = __fmaf_rn(fl, qy, __fmaf_rn(fh, qyl, ve));
+  r0 = __fadd_rn(__fsub_rn(uh, oxh), __fsub_rn(ue, oxl));
+  r1 = __fadd_rn(__fsub_rn(vh, oyh), __fsub_rn(ve, oyl));
+  return zh > 0.f;
+}
+
+}  // namespace rpba

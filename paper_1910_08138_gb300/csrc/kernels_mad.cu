@@ -7,8 +7,10 @@
 // the components below the median, read backwards, and those of the
 // components from the median up are two ascending lists, and their median
 // is found by a binary search over the two.
-// The FP64 values are sorted as order-preserving 64-bit integer keys: on this
-// GPU FP64 compares run on the slow FP64 pipe, integer compares do not.
+// The values are sorted as order-preserving integer keys: 64-bit for the
+// FP64 form, 32-bit for the FP32 form, whose residuals are float-float
+// evaluations rounded to FP32. On this GPU FP64 compares run on the slow FP64
+// pipe, integer compares do not.
 #include <cuda_runtime.h>
 #include <float.h>
 
@@ -27,12 +29,22 @@ __device__ inline double dval(unsigned long long k) {
   unsigned long long u = (k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k;
   return __longlong_as_double((long long)u);
 }
+__device__ inline unsigned fkey(float x) {
+  unsigned u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ inline double dval(unsigned k) {
+  unsigned u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+  return (double)__uint_as_float(u);
+}
+__device__ inline unsigned long long key_of(double x, unsigned long long) { return dkey(x); }
+__device__ inline unsigned key_of(double x, unsigned) { return fkey((float)x); }
 
 // compare-exchange of the bitonic network for the key held at position pos,
 // partner at pos ^ stride (value y): keep the min at the lower position of an
 // ascending pair, the max at its upper position (reversed when descending)
-__device__ inline unsigned long long bitonic_keep(unsigned long long x, unsigned long long y, int pos, int stride,
-                                                  int size) {
+template <typename Key>
+__device__ inline Key bitonic_keep(Key x, Key y, int pos, int stride, int size) {
   bool asc = (pos & size) == 0;
   bool lower = (pos & stride) == 0;
   bool take_min = (lower == asc);
@@ -41,19 +53,20 @@ __device__ inline unsigned long long bitonic_keep(unsigned long long x, unsigned
 
 // the stages of one merge size with stride <= 32 on 64-key chunks, one warp
 // per chunk, keys in registers (lane and lane + 32 of the chunk)
-__device__ inline void bitonic_chunk_stages(unsigned long long *a, int n2, int size, int first_stride) {
+template <typename Key>
+__device__ inline void bitonic_chunk_stages(Key *a, int n2, int size, int first_stride) {
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int c = 64 * warp; c < n2; c += 64 * nw) {
-    unsigned long long x0 = a[c + lane], x1 = a[c + 32 + lane];
+    Key x0 = a[c + lane], x1 = a[c + 32 + lane];
     for (int stride = first_stride; stride > 0; stride >>= 1) {
       if (stride == 32) {  // the pair is (lane, lane + 32) of this thread
         bool asc = ((c + lane) & size) == 0;
-        unsigned long long lo = x0 < x1 ? x0 : x1, hi = x0 < x1 ? x1 : x0;
+        Key lo = x0 < x1 ? x0 : x1, hi = x0 < x1 ? x1 : x0;
         x0 = asc ? lo : hi;
         x1 = asc ? hi : lo;
       } else {
-        unsigned long long y0 = __shfl_xor_sync(0xffffffffu, x0, stride);
-        unsigned long long y1 = __shfl_xor_sync(0xffffffffu, x1, stride);
+        Key y0 = __shfl_xor_sync(0xffffffffu, x0, stride);
+        Key y1 = __shfl_xor_sync(0xffffffffu, x1, stride);
         x0 = bitonic_keep(x0, y0, c + lane, stride, size);
         x1 = bitonic_keep(x1, y1, c + 32 + lane, stride, size);
       }
@@ -65,7 +78,8 @@ __device__ inline void bitonic_chunk_stages(unsigned long long *a, int n2, int s
 
 // ascending bitonic sort of a[0..n2), n2 a power of two >= 64: the stages with
 // stride >= 64 as shared-memory passes, the others in registers per 64-key chunk
-__device__ static void bitonic_sort(unsigned long long *a, int n2) {
+template <typename Key>
+__device__ static void bitonic_sort(Key *a, int n2) {
   for (int size = 2; size <= 64; size <<= 1) bitonic_chunk_stages(a, n2, size, size >> 1);
   __syncthreads();
   for (int size = 128; size <= n2; size <<= 1) {
@@ -74,7 +88,7 @@ __device__ static void bitonic_sort(unsigned long long *a, int n2) {
         int i = 2 * stride * (idx / stride) + (idx % stride);
         int j = i + stride;
         bool up = (i & size) == 0;
-        unsigned long long x = a[i], y = a[j];
+        Key x = a[i], y = a[j];
         if ((x > y) == up) {
           a[i] = y;
           a[j] = x;
@@ -87,15 +101,17 @@ __device__ static void bitonic_sort(unsigned long long *a, int n2) {
   }
 }
 
-__device__ static double sorted_median(const unsigned long long *a, int n) {
+template <typename Key>
+__device__ static double sorted_median(const Key *a, int n) {
   return (n & 1) ? dval(a[n / 2]) : 0.5 * (dval(a[n / 2 - 1]) + dval(a[n / 2]));
 }
 
 // the deviation lists of the sorted values a[0..n) around med, split at s
 // (a[s-1] < med <= a[s]): lower list j -> med - a[s-1-j] (j < s), upper list
 // j -> a[s+j] - med (j < n - s); both ascending
+template <typename Key>
 struct DevLists {
-  const unsigned long long *a;
+  const Key *a;
   int n, s;
   double med;
   __device__ double lo(int j) const { return med - dval(a[s - 1 - j]); }
@@ -103,7 +119,8 @@ struct DevLists {
 };
 
 // k-th smallest (0-based) of the union of the two deviation lists
-__device__ static double dev_select(const DevLists &D, int k) {
+template <typename Key>
+__device__ static double dev_select(const DevLists<Key> &D, int k) {
   int na = D.s, nb = D.n - D.s;
   int lo = max(0, k + 1 - nb), hi = min(k + 1, na);  // i values taken from the lower list
   while (lo < hi) {
@@ -118,78 +135,118 @@ __device__ static double dev_select(const DevLists &D, int k) {
   return x > y ? x : y;
 }
 
-__global__ void k_camera_mad(int M, const double *R, const double *t, const double *intr, const double *X,
-                             const uint8_t *active, const int *cam_obs_ptr, const int *cam_obs, const int *obs_pt,
-                             const double *obs_xy, const double *whiten, int has_winv, double *sigma) {
-  extern __shared__ unsigned long long sh[];
+// inputs of the residuals: FP64 state (FP64 form) or the FP32 form's
+// camera records, points as hi + lo and observations as hi + lo
+struct MadIn {
+  const double *R, *t, *intr, *X, *obs_xy, *whiten;
+  const float *camff, *Xh, *Xl, *oxy, *oxylo, *whiten32;
+};
+
+template <typename Key>
+__global__ void k_camera_mad(int M, MadIn in, const uint8_t *active, const int *cam_obs_ptr, const int *cam_obs,
+                             const int *obs_pt, int has_winv, double *sigma, float *sigma32) {
+  extern __shared__ __align__(16) unsigned char sh_raw[];
+  Key *sh = reinterpret_cast<Key *>(sh_raw);
   __shared__ int count;
   int i = blockIdx.x;
   if (i >= M) return;
   if (threadIdx.x == 0) count = 0;
   __syncthreads();
   int p0 = cam_obs_ptr[i], p1 = cam_obs_ptr[i + 1];
-  const double *Ri = R + 9 * i, *ti = t + 3 * i;
-  double f = intr[3 * i], cx = intr[3 * i + 1], cy = intr[3 * i + 2];
   for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
     int k = cam_obs[p];
     int j = obs_pt[k];
     if (!active[j]) continue;
-    const double *Xj = X + 3 * j;
-    double Xc[3];
-    for (int r = 0; r < 3; r++) Xc[r] = Ri[3 * r] * Xj[0] + Ri[3 * r + 1] * Xj[1] + Ri[3 * r + 2] * Xj[2] + ti[r];
-    double iz = 1.0 / Xc[2];
-    double r0 = f * Xc[0] * iz + cx - obs_xy[2 * k];
-    double r1 = f * Xc[1] * iz + cy - obs_xy[2 * k + 1];
-    double e0 = r0, e1 = r1;
-    if (has_winv) {  // upper Cholesky factor of C^-1, precomputed: (sqrt(w11), w12/sqrt(w11), sqrt(w22 - w12^2/w11))
-      const double *F = whiten + 3 * k;
-      e0 = F[0] * r0 + F[1] * r1;
-      e1 = F[2] * r1;
+    double e0, e1;
+    if constexpr (sizeof(Key) == 4) {
+      float r0, r1;
+      ff_residual(in.camff + FF_CAM * (size_t)i, in.Xh + 3 * (size_t)j, in.Xl + 3 * (size_t)j, in.oxy[2 * k],
+                  in.oxylo[2 * k], in.oxy[2 * k + 1], in.oxylo[2 * k + 1], r0, r1);
+      if (has_winv) {
+        const float *F = in.whiten32 + 3 * (size_t)k;
+        float a = F[0] * r0 + F[1] * r1, b = F[2] * r1;
+        r0 = a;
+        r1 = b;
+      }
+      e0 = r0;
+      e1 = r1;
+    } else {
+      const double *Ri = in.R + 9 * i, *ti = in.t + 3 * i, *Xj = in.X + 3 * j;
+      double f = in.intr[3 * i], cx = in.intr[3 * i + 1], cy = in.intr[3 * i + 2];
+      double Xc[3];
+      for (int r = 0; r < 3; r++) Xc[r] = Ri[3 * r] * Xj[0] + Ri[3 * r + 1] * Xj[1] + Ri[3 * r + 2] * Xj[2] + ti[r];
+      double iz = 1.0 / Xc[2];
+      double r0 = f * Xc[0] * iz + cx - in.obs_xy[2 * k];
+      double r1 = f * Xc[1] * iz + cy - in.obs_xy[2 * k + 1];
+      e0 = r0;
+      e1 = r1;
+      if (has_winv) {  // upper Cholesky factor of C^-1, precomputed: (sqrt(w11), w12/sqrt(w11), sqrt(w22 - w12^2/w11))
+        const double *F = in.whiten + 3 * k;
+        e0 = F[0] * r0 + F[1] * r1;
+        e1 = F[2] * r1;
+      }
     }
     int slot = atomicAdd(&count, 2);
-    sh[slot] = dkey(e0);
-    sh[slot + 1] = dkey(e1);
+    sh[slot] = key_of(e0, Key());
+    sh[slot + 1] = key_of(e1, Key());
   }
   __syncthreads();
   int n = count;
   if (n == 0) {
-    if (threadIdx.x == 0) sigma[i] = 0.0;
+    if (threadIdx.x == 0) {
+      sigma[i] = 0.0;
+      if (sigma32) sigma32[i] = 0.f;
+    }
     return;
   }
   int n2 = 64;
   while (n2 < n) n2 <<= 1;
-  for (int e = n + threadIdx.x; e < n2; e += blockDim.x) sh[e] = ~0ull;  // sorts last
+  for (int e = n + threadIdx.x; e < n2; e += blockDim.x) sh[e] = ~Key(0);  // sorts last
   __syncthreads();
   bitonic_sort(sh, n2);
   if (threadIdx.x == 0) {
     double med = sorted_median(sh, n);
-    unsigned long long km = dkey(med);
-    int a = 0, b = n;  // s = first index with a[s] >= med
+    int a = 0, b = n;  // s = first index with a[s] >= med (compared as values: med need not be a key)
     while (a < b) {
       int c = (a + b) >> 1;
-      if (sh[c] < km) a = c + 1; else b = c;
+      if (dval(sh[c]) < med) a = c + 1; else b = c;
     }
-    DevLists D{sh, n, a, med};
+    DevLists<Key> D{sh, n, a, med};
     double mad = (n & 1) ? dev_select(D, n / 2) : 0.5 * (dev_select(D, n / 2 - 1) + dev_select(D, n / 2));
     sigma[i] = 1.4826 * mad;
+    if (sigma32) sigma32[i] = (float)(1.4826 * mad);
   }
 }
 
 rpba_status launch_camera_scale(Ctx *ctx) {
   if (ctx->M == 0) return RPBA_OK;
+  bool f32 = ctx->opt.precision == 1;
+  size_t ks = f32 ? sizeof(unsigned) : sizeof(unsigned long long);
   int n2 = 64;
   while (n2 < 2 * ctx->max_cam_obs) n2 <<= 1;
-  size_t smem = (size_t)n2 * sizeof(unsigned long long);
+  size_t smem = (size_t)n2 * ks;
   if (smem > 200 * 1024) {
     ctx->err = "camera with too many observations for the shared-memory median";
     return RPBA_ERR_INVALID_ARG;
   }
-  if (smem > 48 * 1024)
-    RPBA_CUDA(cudaFuncSetAttribute(k_camera_mad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  MadIn in{ctx->R, ctx->t, ctx->intr, ctx->X, ctx->obs_xy, ctx->obs_whiten,
+           ctx->camff, ctx->X_hi, ctx->X_lo, ctx->obs_xy32, ctx->obs_xylo, ctx->obs_whiten32};
   int threads = std::min(1024, std::max(32, n2 / 2));  // one thread per compare-exchange of a pass
-  RPBA_KERNEL(ctx, "k_camera_mad", k_camera_mad<<<ctx->M, threads, smem, ctx->stream>>>(ctx->M, ctx->R, ctx->t, ctx->intr, ctx->X, ctx->active,
-                                                   ctx->cam_obs_ptr, ctx->cam_obs, ctx->obs_pt, ctx->obs_xy,
-                                                   ctx->obs_whiten, ctx->has_winv, ctx->cam_sigma));
+  if (f32) {
+    RPBA_TRY(prep_ff_state(ctx));
+    if (smem > 48 * 1024)
+      RPBA_CUDA(cudaFuncSetAttribute(k_camera_mad<unsigned>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RPBA_KERNEL(ctx, "k_camera_mad", k_camera_mad<unsigned><<<ctx->M, threads, smem, ctx->stream>>>(
+                                         ctx->M, in, ctx->active, ctx->cam_obs_ptr, ctx->cam_obs, ctx->obs_pt,
+                                         ctx->has_winv, ctx->cam_sigma, ctx->cam_sigma32));
+  } else {
+    if (smem > 48 * 1024)
+      RPBA_CUDA(cudaFuncSetAttribute(k_camera_mad<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    RPBA_KERNEL(ctx, "k_camera_mad", k_camera_mad<unsigned long long><<<ctx->M, threads, smem, ctx->stream>>>(
+                                         ctx->M, in, ctx->active, ctx->cam_obs_ptr, ctx->cam_obs, ctx->obs_pt,
+                                         ctx->has_winv, ctx->cam_sigma, nullptr));
+  }
   return RPBA_OK;
 }
 

@@ -45,6 +45,11 @@ struct View {
   float *Xl_hi, *Xl_lo;    // sub-block copies X^l
   float *X_hi, *X_lo;      // points X
   float *dC32;             // camera updates
+  // float-float residuals: camera records, observation low words, trial X^l
+  float *camff, *camff_t;
+  const float *obs_xylo;
+  float *Xlt_hi, *Xlt_lo;
+  float *Wl32;
 };
 
 static View make_view(Ctx *c) {
@@ -66,6 +71,8 @@ static View make_view(Ctx *c) {
   v.camChi = c->camChi; v.camClo = c->camClo;
   v.Xl_hi = c->Xl_hi; v.Xl_lo = c->Xl_lo; v.X_hi = c->X_hi; v.X_lo = c->X_lo;
   v.dC32 = c->dC32;
+  v.camff = c->camff; v.camff_t = c->camff_t; v.obs_xylo = c->obs_xylo;
+  v.Xlt_hi = c->Xlt_hi; v.Xlt_lo = c->Xlt_lo; v.Wl32 = c->Wl32;
   return v;
 }
 
@@ -136,6 +143,7 @@ __global__ void k_cam_prep(View v) {
   for (int e = 0; e < 3; e++) o[9 + e] = (float)t[e];
   for (int e = 0; e < 3; e++) o[12 + e] = (float)v.intr[3 * i + e];
   o[15] = 0.f;
+  ff_camera_record(R, t, v.intr[3 * i], v.camff + FF_CAM * (size_t)i);
 }
 
 // hi/lo pairs of the sub-block copies (which = 0) or of the points (which = 1)
@@ -160,6 +168,12 @@ static rpba_status split_points(Ctx *ctx, int which) {
   if (ctx->opt.precision != 1 || n == 0) return RPBA_OK;
   RPBA_KERNEL(ctx, "k_split_points", k_split_points<<<nblk(n, 256), 256, 0, ctx->stream>>>(make_view(ctx), which));
   return RPBA_OK;
+}
+
+// FP32 form: camera records and points as hi + lo at the current state
+rpba_status prep_ff_state(Ctx *ctx) {
+  RPBA_TRY(cam_prep(ctx));
+  return split_points(ctx, 1);
 }
 
 // observation k in the compute precision: residual-relevant data
@@ -308,6 +322,34 @@ __global__ void k_obs_sigma(View v, double *part) {
   block_reduce_store<4>(acc, part + 4 * blockIdx.x);
 }
 
+// FP32 form: the same sums from float-float residuals (Eq. ta) formed in
+// FP32, each thread accumulating float-float (TwoSum), the blocks in FP64
+__global__ void k_obs_sigma_f(View v, double *part) {
+  float sh = 0.f, sl = 0.f, rh = 0.f, rl = 0.f;
+  int n1 = 0, n3 = 0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < v.K; k += gridDim.x * blockDim.x) {
+    int j = v.obs_pt[k];
+    if (!v.active[j]) continue;
+    int i = v.obs_cam[k];
+    float r0, r1;
+    ff_residual(v.camff + FF_CAM * (size_t)i, v.X_hi + 3 * (size_t)j, v.X_lo + 3 * (size_t)j, v.obs_xy32[2 * k],
+                v.obs_xylo[2 * k], v.obs_xy32[2 * k + 1], v.obs_xylo[2 * k + 1], r0, r1);
+    float W0 = 1.f, W1 = 0.f, W2 = 1.f;
+    if (v.has_winv) { W0 = v.obs_winv32[3 * k]; W1 = v.obs_winv32[3 * k + 1]; W2 = v.obs_winv32[3 * k + 2]; }
+    float w = v.obs_w32[k], e;
+    sh = ff_two_sum(sh, w * (W0 * r0 * r0 + 2.f * W1 * r0 * r1 + W2 * r1 * r1), e);
+    sl += e;
+    n1++;
+    if (w == 1.f) {
+      rh = ff_two_sum(rh, r0 * r0 + r1 * r1, e);
+      rl += e;
+      n3++;
+    }
+  }
+  double acc[4] = {(double)sh + (double)sl, (double)n1, (double)rh + (double)rl, (double)n3};
+  block_reduce_store<4>(acc, part + 4 * blockIdx.x);
+}
+
 __global__ void k_count_active(View v, double *part) {
   double acc[1] = {0};
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < v.N; j += gridDim.x * blockDim.x)
@@ -318,7 +360,13 @@ __global__ void k_count_active(View v, double *part) {
 rpba_status launch_sigma0(Ctx *ctx, double *sigma0, double *rms) {
   View v = make_view(ctx);
   int nb = ctx->red_blocks;
-  RPBA_KERNEL(ctx, "k_obs_sigma", k_obs_sigma<<<nb, 256, 0, ctx->stream>>>(v, ctx->red));
+  if (ctx->opt.precision == 1) {
+    RPBA_TRY(cam_prep(ctx));
+    RPBA_TRY(split_points(ctx, 1));
+    RPBA_KERNEL(ctx, "k_obs_sigma", k_obs_sigma_f<<<nb, 256, 0, ctx->stream>>>(v, ctx->red));
+  } else {
+    RPBA_KERNEL(ctx, "k_obs_sigma", k_obs_sigma<<<nb, 256, 0, ctx->stream>>>(v, ctx->red));
+  }
   RPBA_KERNEL(ctx, "k_sum_partials", k_sum_partials<4><<<1, 256, 0, ctx->stream>>>(ctx->red, nb, ctx->red + 4 * nb));
   RPBA_KERNEL(ctx, "k_count_active", k_count_active<<<nb, 256, 0, ctx->stream>>>(v, ctx->red + 4 * nb + 4));
   RPBA_KERNEL(ctx, "k_sum_partials", k_sum_partials<1><<<1, 256, 0, ctx->stream>>>(ctx->red + 4 * nb + 4, nb, ctx->red + 5 * nb + 4));
@@ -472,7 +520,10 @@ __global__ void k_isect_point(View v, int *state, int *iter, const T *part, int 
     state[j] = 3;
     v.active[j] = 0;
     for (int a = q0; a < q1; a++)
-      for (int e = 0; e < 6; e++) v.Wl[6 * (size_t)v.pt_inst[a] + e] = 0.0;
+      for (int e = 0; e < 6; e++) {
+        v.Wl[6 * (size_t)v.pt_inst[a] + e] = 0.0;
+        if (v.Wl32) v.Wl32[6 * (size_t)v.pt_inst[a] + e] = 0.f;
+      }
   } else if (conv) {
     state[j] = 2;
     bool tp = (q1 - q0) >= 2;
@@ -490,8 +541,11 @@ __global__ void k_isect_point(View v, int *state, int *iter, const T *part, int 
           for (int e = 0; e < 6; e++) W[e] += (double)ob[e];
         }
         for (int e = 0; e < 6; e++) v.Wl[6 * (size_t)q + e] = tp ? W[e] : 0.0;
+        for (int e = 0; e < 6; e++) v.Wl32[6 * (size_t)q + e] = tp ? (float)W[e] : 0.f;
       } else {
         for (int e = 0; e < 6; e++) v.Wl[6 * (size_t)q + e] = tp ? (double)(N[e] - o[e]) : 0.0;
+        if (v.Wl32)
+          for (int e = 0; e < 6; e++) v.Wl32[6 * (size_t)q + e] = tp ? (float)(N[e] - o[e]) : 0.f;
       }
     }
   }
@@ -606,10 +660,34 @@ __global__ void k_robust_weights(View v, const double *sigma, double t_v, double
   if (out) atomicAdd(count, 1);
 }
 
+// FP32 form: float-float residual, the test |v|_W > t_v sigma_i in FP32
+__global__ void k_robust_weights_f(View v, const float *sigma, float t_v, double dw, int *count) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= v.K) return;
+  int j = v.obs_pt[k];
+  if (!v.active[j]) return;
+  int i = v.obs_cam[k];
+  float r0, r1;
+  ff_residual(v.camff + FF_CAM * (size_t)i, v.X_hi + 3 * (size_t)j, v.X_lo + 3 * (size_t)j, v.obs_xy32[2 * k],
+              v.obs_xylo[2 * k], v.obs_xy32[2 * k + 1], v.obs_xylo[2 * k + 1], r0, r1);
+  float W0 = 1.f, W1 = 0.f, W2 = 1.f;
+  if (v.has_winv) { W0 = v.obs_winv32[3 * k]; W1 = v.obs_winv32[3 * k + 1]; W2 = v.obs_winv32[3 * k + 2]; }
+  float nr = sqrtf(W0 * r0 * r0 + 2.f * W1 * r0 * r1 + W2 * r1 * r1);
+  float s = sigma[i];
+  bool out = (s > 0.f) && (nr > t_v * s);
+  v.obs_w[k] = out ? dw : 1.0;
+  v.obs_w32[k] = out ? (float)dw : 1.0f;
+  if (out) atomicAdd(count, 1);
+}
+
 rpba_status launch_robust_weights(Ctx *ctx, int *n_down) {
   RPBA_TRY(launch_camera_scale(ctx));
   RPBA_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(int), ctx->stream));
-  if (ctx->K)
+  if (ctx->K && ctx->opt.precision == 1)
+    RPBA_KERNEL(ctx, "k_robust_weights", k_robust_weights_f<<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(
+                                             make_view(ctx), ctx->cam_sigma32, (float)ctx->opt.t_v, ctx->opt.downweight,
+                                             ctx->counters));
+  else if (ctx->K)
     RPBA_KERNEL(ctx, "k_robust_weights", k_robust_weights<<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(make_view(ctx), ctx->cam_sigma, ctx->opt.t_v,
                                                                 ctx->opt.downweight, ctx->counters));
   if (n_down) {
@@ -675,6 +753,41 @@ __global__ void k_obs_cost(View v, int trial, const int *run, double *cost) {
   cost[k] = F;
 }
 
+// FP32 form: the observation's term from its float-float residual, formed
+// in FP32 and stored in FP64 for the FP64 sum; the TP control term from the
+// float-float difference X^l - X_TP and W^l in FP32
+__global__ void k_obs_cost_f(View v, int trial, const int *run, double *cost) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= v.K) return;
+  int q = v.obs_inst[k];
+  int l = v.inst_sub[q];
+  int j = v.inst_pt[q];
+  if ((run && !run[l]) || !v.active[j]) { cost[k] = 0.0; return; }
+  int i = v.obs_cam[k];
+  const float *cf = (trial ? v.camff_t : v.camff) + FF_CAM * (size_t)i;
+  const float *Xh = (trial ? v.Xlt_hi : v.Xl_hi) + 3 * (size_t)q;
+  const float *Xw = (trial ? v.Xlt_lo : v.Xl_lo) + 3 * (size_t)q;
+  float r0, r1;
+  float F;
+  if (!ff_residual(cf, Xh, Xw, v.obs_xy32[2 * k], v.obs_xylo[2 * k], v.obs_xy32[2 * k + 1], v.obs_xylo[2 * k + 1],
+                   r0, r1)) {
+    F = INFINITY;
+  } else {
+    float W0 = 1.f, W1 = 0.f, W2 = 1.f;
+    if (v.has_winv) { W0 = v.obs_winv32[3 * k]; W1 = v.obs_winv32[3 * k + 1]; W2 = v.obs_winv32[3 * k + 2]; }
+    F = v.obs_w32[k] * (W0 * r0 * r0 + 2.f * W1 * r0 * r1 + W2 * r1 * r1);
+  }
+  if (k == v.inst_obs_ptr[q]) {
+    const float *W = v.Wl32 + 6 * (size_t)q;
+    float d[3];
+    for (int e = 0; e < 3; e++)
+      d[e] = __fadd_rn(__fsub_rn(Xh[e], v.X_hi[3 * (size_t)j + e]), __fsub_rn(Xw[e], v.X_lo[3 * (size_t)j + e]));
+    F += W[0] * d[0] * d[0] + W[3] * d[1] * d[1] + W[5] * d[2] * d[2] +
+         2.f * (W[1] * d[0] * d[1] + W[2] * d[0] * d[2] + W[4] * d[1] * d[2]);
+  }
+  cost[k] = (double)F;
+}
+
 #define SEG_CHUNKS 32
 // stage 1: chunk g of sub-block l's observation range -> part[l][g]
 __global__ void k_seg_partial(const int *seg_ptr, const int *run, const double *val, double *part) {
@@ -697,13 +810,23 @@ __global__ void k_seg_final(int L, const int *run, const double *part, double *F
   F[l] = s;
 }
 
-// The cost that decides acceptance is evaluated in FP64 in both forms: FP32
-// residuals of ~1000 px coordinates carry ~1e-4 px rounding, which hides the
-// last LM improvements.
+// The cost that decides acceptance needs residuals far more accurate than
+// FP32 image coordinates give: FP32 residuals of ~1000 px coordinates carry
+// ~1e-4 px rounding, which hides the last LM improvements. The FP64 form
+// evaluates them in FP64; the FP32 form in float-float on the FP32 pipes
+// (~1e-10 px), with each term then formed in FP32 and all sums in FP64.
 static rpba_status sub_costs_impl(Ctx *ctx, int trial, const int *run, double *F_dev) {
   View v = make_view(ctx);
-  if (ctx->K)
+  if (ctx->K && ctx->opt.precision == 1) {
+    if (!trial) {  // the trial state's records come from the trial kernels
+      RPBA_TRY(cam_prep(ctx));
+      RPBA_TRY(split_points(ctx, 0));
+      RPBA_TRY(split_points(ctx, 1));
+    }
+    RPBA_KERNEL(ctx, "k_obs_cost", k_obs_cost_f<<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(v, trial, run, ctx->obs_cost));
+  } else if (ctx->K) {
     RPBA_KERNEL(ctx, "k_obs_cost", k_obs_cost<<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(v, trial, run, ctx->obs_cost));
+  }
   RPBA_KERNEL(ctx, "k_seg_partial", k_seg_partial<<<dim3(SEG_CHUNKS, ctx->L), 256, 0, ctx->stream>>>(
                                         ctx->sub_obs_ptr, run, ctx->obs_cost, ctx->seg_part));
   RPBA_KERNEL(ctx, "k_seg_final", k_seg_final<<<nblk(ctx->L, 128), 128, 0, ctx->stream>>>(ctx->L, run, ctx->seg_part, F_dev));
@@ -989,6 +1112,8 @@ __global__ void k_backsub(View v, const int *run, const T *NXC, const T *Ninv, c
   double *Xt = v.Xlt + 3 * (size_t)q;
   if (!v.active[v.inst_pt[q]]) {
     for (int e = 0; e < 3; e++) Xt[e] = Xq[e];
+    if constexpr (sizeof(T) == sizeof(float))
+      for (int e = 0; e < 3; e++) split(Xq[e], v.Xlt_hi[3 * (size_t)q + e], v.Xlt_lo[3 * (size_t)q + e]);
     return;
   }
   T rhs[3] = {-gX[3 * (size_t)q], -gX[3 * (size_t)q + 1], -gX[3 * (size_t)q + 2]};
@@ -1008,8 +1133,11 @@ __global__ void k_backsub(View v, const int *run, const T *NXC, const T *Ninv, c
     }
   }
   const T *iv = Ninv + 6 * (size_t)q;
-  for (int r = 0; r < 3; r++)
-    Xt[r] = Xq[r] + (double)(iv[s3idx(r, 0)] * rhs[0] + iv[s3idx(r, 1)] * rhs[1] + iv[s3idx(r, 2)] * rhs[2]);
+  for (int r = 0; r < 3; r++) {
+    double x = Xq[r] + (double)(iv[s3idx(r, 0)] * rhs[0] + iv[s3idx(r, 1)] * rhs[1] + iv[s3idx(r, 2)] * rhs[2]);
+    Xt[r] = x;
+    if constexpr (sizeof(T) == sizeof(float)) split(x, v.Xlt_hi[3 * (size_t)q + r], v.Xlt_lo[3 * (size_t)q + r]);
+  }
 }
 
 // trial cameras: R' = exp([dw]x) R, t' = t + dt
@@ -1022,6 +1150,7 @@ __global__ void k_cam_trial(View v, const int *run) {
   if (!run[l]) {
     for (int e = 0; e < 9; e++) Rt[e] = R[e];
     for (int e = 0; e < 3; e++) v.tt[3 * i + e] = v.t[3 * i + e];
+    if (v.camff_t) ff_camera_record(Rt, v.tt + 3 * i, v.intr[3 * i], v.camff_t + FF_CAM * (size_t)i);
     return;
   }
   const double *dc = v.dC + v.ycam_off[l] + 6 * v.cam_local[i];
@@ -1031,6 +1160,7 @@ __global__ void k_cam_trial(View v, const int *run) {
     for (int c = 0; c < 3; c++)
       Rt[3 * r + c] = dR[3 * r] * R[c] + dR[3 * r + 1] * R[3 + c] + dR[3 * r + 2] * R[6 + c];
   for (int e = 0; e < 3; e++) v.tt[3 * i + e] = v.t[3 * i + e] + dc[3 + e];
+  if (v.camff_t) ff_camera_record(Rt, v.tt + 3 * i, v.intr[3 * i], v.camff_t + FF_CAM * (size_t)i);
 }
 
 __global__ void k_to_float(const double *a, float *b, int n) {

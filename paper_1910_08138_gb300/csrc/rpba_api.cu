@@ -447,7 +447,14 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
       if (ctx->has_winv)
         for (int e = 0; e < 3; e++) wi32[3 * (size_t)p + e] = (float)ow[3 * (size_t)p + e];
     }
+    std::vector<float> xylo(2 * (size_t)K);
+    for (size_t e = 0; e < xy32.size(); e++) {
+      int i = ocam[e / 2];
+      double rel = oxy[e] - pb->cam_intr[3 * (size_t)i + 1 + (e & 1)];
+      xylo[e] = (float)(rel - (double)xy32[e]);
+    }
     RPBA_TRY(upload(ctx, &ctx->obs_xy32, xy32.data(), xy32.size()));
+    RPBA_TRY(upload(ctx, &ctx->obs_xylo, xylo.data(), xylo.size()));
     RPBA_TRY(upload(ctx, &ctx->obs_w32, w32.data(), w32.size()));
     if (ctx->has_winv) RPBA_TRY(upload(ctx, &ctx->obs_winv32, wi32.data(), wi32.size()));
     RPBA_TRY(alloc_n(ctx, &ctx->camChi, 3 * (size_t)M));
@@ -457,6 +464,13 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
     RPBA_TRY(alloc_n(ctx, &ctx->X_hi, 3 * (size_t)N));
     RPBA_TRY(alloc_n(ctx, &ctx->X_lo, 3 * (size_t)N));
     RPBA_TRY(alloc_n(ctx, &ctx->dC32, (size_t)std::max(yt, 1)));
+    RPBA_TRY(alloc_n(ctx, &ctx->camff, FF_CAM * (size_t)M));
+    RPBA_TRY(alloc_n(ctx, &ctx->camff_t, FF_CAM * (size_t)M));
+    RPBA_TRY(alloc_n(ctx, &ctx->Xlt_hi, 3 * (size_t)P));
+    RPBA_TRY(alloc_n(ctx, &ctx->Xlt_lo, 3 * (size_t)P));
+    RPBA_TRY(alloc_n(ctx, &ctx->Wl32, 6 * (size_t)P));
+    RPBA_TRY(alloc_n(ctx, &ctx->cam_sigma32, (size_t)M));
+    if (P) RPBA_CUDA(cudaMemsetAsync(ctx->Wl32, 0, 6 * (size_t)P * sizeof(float), ctx->stream));
   }
   RPBA_TRY(alloc_n(ctx, &ctx->seg_part, (size_t)L * 32));
   RPBA_TRY(alloc_n(ctx, &ctx->Xl, 3 * (size_t)P));
@@ -485,6 +499,10 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
       wf[3 * (size_t)p + 2] = sqrt(W[2] - W[1] * W[1] / W[0]);
     }
     RPBA_TRY(upload(ctx, &ctx->obs_whiten, wf.data(), wf.size()));
+    if (ctx->opt.precision == 1) {
+      std::vector<float> wf32(wf.begin(), wf.end());
+      RPBA_TRY(upload(ctx, &ctx->obs_whiten32, wf32.data(), wf32.size()));
+    }
   }
   RPBA_TRY(alloc_n(ctx, &ctx->obs_w, (size_t)K));
   RPBA_TRY(dev_alloc(ctx, &ctx->NXC, 18 * (size_t)K * rs));
@@ -680,6 +698,11 @@ extern "C" rpba_status rpba_set_instances(rpba_ctx *h, const double *Xl, const d
   CTX_OR_FAIL;
   if (Xl) RPBA_CUDA(cudaMemcpyAsync(ctx->Xl, Xl, 3 * (size_t)ctx->P * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   if (Wl) RPBA_CUDA(cudaMemcpyAsync(ctx->Wl, Wl, 6 * (size_t)ctx->P * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  if (Wl && ctx->Wl32 && ctx->P) {
+    std::vector<float> w32(Wl, Wl + 6 * (size_t)ctx->P);
+    RPBA_CUDA(cudaMemcpyAsync(ctx->Wl32, w32.data(), w32.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    return sync(ctx);  // before w32 goes
+  }
   return sync(ctx);
 }
 

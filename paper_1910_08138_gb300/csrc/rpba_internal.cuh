@@ -32,6 +32,7 @@
 #include <vector>
 
 #include "../../include/rpba.h"
+#include "ffloat.cuh"
 
 #define RPBA_TILE 32
 
@@ -229,6 +230,12 @@ struct Ctx {
   float *obs_xy32 = nullptr, *obs_winv32 = nullptr, *obs_w32 = nullptr;
   float *camChi = nullptr, *camClo = nullptr, *Xl_hi = nullptr, *Xl_lo = nullptr, *X_hi = nullptr,
         *X_lo = nullptr, *dC32 = nullptr;
+  // FP32 form, float-float residuals: camera records (FF_CAM floats) of the
+  // current and the trial state, the low words of the observations relative
+  // to the principal point, trial copies X^l as hi + lo, W^l and the
+  // whitening factors in FP32, and the per-camera robust scale in FP32
+  float *camff = nullptr, *camff_t = nullptr, *obs_xylo = nullptr, *Xlt_hi = nullptr, *Xlt_lo = nullptr,
+        *Wl32 = nullptr, *obs_whiten32 = nullptr, *cam_sigma32 = nullptr;
   int *sub_obs_ptr = nullptr;
   std::vector<int> h_sched;  // per factorisation step: prefix sums of panel and update tiles
   int *sched = nullptr;
@@ -379,6 +386,8 @@ rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped, bool fp64 = 
 rpba_status launch_exchange(Ctx *ctx);
 rpba_status launch_tp_copies(Ctx *ctx, int tp_only);
 rpba_status launch_camera_scale(Ctx *ctx);
+// FP32 form: camera records and the points' hi + lo words at the current state
+rpba_status prep_ff_state(Ctx *ctx);
 rpba_status launch_robust_weights(Ctx *ctx, int *n_down);
 rpba_status launch_eliminate(Ctx *ctx);
 rpba_status launch_sub_costs(Ctx *ctx, int trial, double *F_dev);
