@@ -70,19 +70,34 @@ __host__ __device__ __forceinline__ void ff_split(double x, float &hi, float &lo
   lo = (float)(x - (double)hi);
 }
 
-// Camera record of the FP32 form's residuals, FF_CAM floats per camera:
-// rotation R (row-major) hi [0, 9) and lo [9, 18), centre C = -R^T t hi
-// [18, 21) and lo [21, 24), focal length hi [24] and lo [25], zero padding.
+// Camera record of the FP32 form, FF_CAM floats (128 bytes, read as float4):
+//   [0, 9) R hi (row-major)   [9, 12) centre C = -R^T t hi   [12, 15) C lo
+//   [15] f hi                 [16, 25) R lo                   [25] f lo
+//   [26, 29) zero             [29, 32) t rounded to FP32
+// The FP32 projection and Jacobians read floats [0, 16) and [28, 32); the
+// float-float residual reads [0, 28).
 #define FF_CAM 32
 
 __host__ __device__ inline void ff_camera_record(const double *R, const double *t, double f, float *o) {
-  for (int e = 0; e < 9; e++) ff_split(R[e], o[e], o[9 + e]);
+  for (int e = 0; e < 9; e++) ff_split(R[e], o[e], o[16 + e]);
   for (int c = 0; c < 3; c++) {
     double C = -(R[c] * t[0] + R[3 + c] * t[1] + R[6 + c] * t[2]);
-    ff_split(C, o[18 + c], o[21 + c]);
+    ff_split(C, o[9 + c], o[12 + c]);
   }
-  ff_split(f, o[24], o[25]);
-  for (int e = 26; e < FF_CAM; e++) o[e] = 0.f;
+  ff_split(f, o[15], o[25]);
+  for (int e = 26; e < 29; e++) o[e] = 0.f;
+  for (int e = 0; e < 3; e++) o[29 + e] = (float)t[e];
+}
+
+// floats [0, 4 n4) of a record into registers
+template <int N4>
+__device__ __forceinline__ void ff_load_record(const float *cf, float (&c)[4 * N4]) {
+  const float4 *p = reinterpret_cast<const float4 *>(cf);
+#pragma unroll
+  for (int e = 0; e < N4; e++) {
+    float4 a = __ldg(p + e);
+    c[4 * e] = a.x; c[4 * e + 1] = a.y; c[4 * e + 2] = a.z; c[4 * e + 3] = a.w;
+  }
 }
 
 // Reprojection residual (Eq. ta) of a point X = Xh + Xl in the camera of
@@ -94,22 +109,24 @@ __host__ __device__ inline void ff_camera_record(const double *R, const double *
 // Returns z_c > 0; the residual is computed either way, as in FP64.
 __device__ __forceinline__ bool ff_residual(const float *cf, const float *Xh, const float *Xl, float oxh, float oxl,
                                             float oyh, float oyl, float &r0, float &r1) {
+  float c[28];
+  ff_load_record<7>(cf, c);
   float dh[3], dl[3];
 #pragma unroll
-  for (int c = 0; c < 3; c++) {
+  for (int k = 0; k < 3; k++) {
     float e;
-    dh[c] = ff_two_sum(Xh[c], -cf[18 + c], e);
-    dl[c] = __fadd_rn(e, __fsub_rn(Xl[c], cf[21 + c]));
+    dh[k] = ff_two_sum(Xh[k], -c[9 + k], e);
+    dl[k] = __fadd_rn(e, __fsub_rn(Xl[k], c[12 + k]));
   }
   float xl, yl, zl;
-  float xh = ff_dot3(cf + 0, cf + 9, dh, dl, xl);
-  float yh = ff_dot3(cf + 3, cf + 12, dh, dl, yl);
-  float zh = ff_dot3(cf + 6, cf + 15, dh, dl, zl);
+  float xh = ff_dot3(c + 0, c + 16, dh, dl, xl);
+  float yh = ff_dot3(c + 3, c + 19, dh, dl, yl);
+  float zh = ff_dot3(c + 6, c + 22, dh, dl, zl);
   float rz = __frcp_rn(zh);
   float qxl, qyl;
   float qx = ff_div(xh, xl, zh, zl, rz, qxl);
   float qy = ff_div(yh, yl, zh, zl, rz, qyl);
-  float fh = cf[24], fl = cf[25];
+  float fh = c[15], fl = c[25];
   float ue, ve;
   float uh = ff_two_prod(fh, qx, ue);
   ue = __fmaf_rn(fl, qx, __fmaf_rn(fh, qxl, ue));

@@ -233,7 +233,6 @@ rpba_status launch_camera_scale(Ctx *ctx) {
            ctx->camff, ctx->X_hi, ctx->X_lo, ctx->obs_xy32, ctx->obs_xylo, ctx->obs_whiten32};
   int threads = std::min(1024, std::max(32, n2 / 2));  // one thread per compare-exchange of a pass
   if (f32) {
-    RPBA_TRY(prep_ff_state(ctx));
     if (smem > 48 * 1024)
       RPBA_CUDA(cudaFuncSetAttribute(k_camera_mad<unsigned>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     RPBA_KERNEL(ctx, "k_camera_mad", k_camera_mad<unsigned><<<ctx->M, threads, smem, ctx->stream>>>(

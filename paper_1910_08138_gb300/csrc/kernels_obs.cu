@@ -35,13 +35,10 @@ struct View {
   double *S, *y, *dC;
   const long long *S_off;
   const int *npad, *ycam_off;
-  double *camC;  // camera centres (FP64), current state
-  float *camRf;  // R (9) and t (3) rounded to FP32, current state
   // FP32 form: inputs rounded once, positions as float hi + lo pairs
   const float *obs_xy32;   // (x - cx, y - cy)
   const float *obs_winv32;
   float *obs_w32;
-  float *camChi, *camClo;  // camera centres
   float *Xl_hi, *Xl_lo;    // sub-block copies X^l
   float *X_hi, *X_lo;      // points X
   float *dC32;             // camera updates
@@ -65,10 +62,7 @@ static View make_view(Ctx *c) {
   v.obs_user = c->obs_user; v.obs_pt = c->obs_pt; v.obs_xy = c->obs_xy; v.obs_winv = c->obs_winv;
   v.obs_w = c->obs_w; v.S = c->S; v.y = c->y; v.dC = c->dC; v.S_off = c->S_off; v.npad = c->npad;
   v.ycam_off = c->ycam_off;
-  v.camC = c->camC;
-  v.camRf = c->camRf;
   v.obs_xy32 = c->obs_xy32; v.obs_winv32 = c->obs_winv32; v.obs_w32 = c->obs_w32;
-  v.camChi = c->camChi; v.camClo = c->camClo;
   v.Xl_hi = c->Xl_hi; v.Xl_lo = c->Xl_lo; v.X_hi = c->X_hi; v.X_lo = c->X_lo;
   v.dC32 = c->dC32;
   v.camff = c->camff; v.camff_t = c->camff_t; v.obs_xylo = c->obs_xylo;
@@ -112,16 +106,23 @@ __device__ inline void cam_point_d(const View &v, int i, const double X[3], CamP
 }
 
 __device__ inline void cam_point_f(const View &v, int i, const float *Xh, const float *Xlw, CamPt<float> &o) {
-  const float *Rf = v.camRf + 16 * i;
-  const float *Ch = v.camChi + 3 * i, *Cl = v.camClo + 3 * i;
+  const float4 *p = reinterpret_cast<const float4 *>(v.camff + FF_CAM * (size_t)i);
+  float c[16];
+#pragma unroll
+  for (int e = 0; e < 4; e++) {
+    float4 a = __ldg(p + e);
+    c[4 * e] = a.x; c[4 * e + 1] = a.y; c[4 * e + 2] = a.z; c[4 * e + 3] = a.w;
+  }
+  float4 tt = __ldg(p + 7);
   float d[3];
-  for (int r = 0; r < 3; r++) d[r] = (Xh[r] - Ch[r]) + (Xlw[r] - Cl[r]);
-  for (int e = 0; e < 9; e++) o.R[e] = Rf[e];
+  for (int r = 0; r < 3; r++) d[r] = (Xh[r] - c[9 + r]) + (Xlw[r] - c[12 + r]);
+  for (int e = 0; e < 9; e++) o.R[e] = c[e];
+  float t[3] = {tt.y, tt.z, tt.w};
   for (int r = 0; r < 3; r++) {
     o.Xc[r] = o.R[3 * r] * d[0] + o.R[3 * r + 1] * d[1] + o.R[3 * r + 2] * d[2];
-    o.RX[r] = o.Xc[r] - Rf[9 + r];
+    o.RX[r] = o.Xc[r] - t[r];
   }
-  o.f = Rf[12]; o.cx = Rf[13]; o.cy = Rf[14];
+  o.f = c[15]; o.cx = 0.f; o.cy = 0.f;
 }
 
 __device__ inline void split(double x, float &hi, float &lo) {
@@ -129,21 +130,11 @@ __device__ inline void split(double x, float &hi, float &lo) {
   lo = (float)(x - (double)hi);
 }
 
+// FP32 form: camera records of the current state
 __global__ void k_cam_prep(View v) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= v.M) return;
-  const double *R = v.R + 9 * i, *t = v.t + 3 * i;
-  for (int c = 0; c < 3; c++) {
-    double C = -(R[c] * t[0] + R[3 + c] * t[1] + R[6 + c] * t[2]);
-    v.camC[3 * i + c] = C;
-    split(C, v.camChi[3 * i + c], v.camClo[3 * i + c]);
-  }
-  float *o = v.camRf + 16 * i;
-  for (int e = 0; e < 9; e++) o[e] = (float)R[e];
-  for (int e = 0; e < 3; e++) o[9 + e] = (float)t[e];
-  for (int e = 0; e < 3; e++) o[12 + e] = (float)v.intr[3 * i + e];
-  o[15] = 0.f;
-  ff_camera_record(R, t, v.intr[3 * i], v.camff + FF_CAM * (size_t)i);
+  ff_camera_record(v.R + 9 * i, v.t + 3 * i, v.intr[3 * i], v.camff + FF_CAM * (size_t)i);
 }
 
 // hi/lo pairs of the sub-block copies (which = 0) or of the points (which = 1)
@@ -170,9 +161,13 @@ static rpba_status split_points(Ctx *ctx, int which) {
   return RPBA_OK;
 }
 
-// FP32 form: camera records and points as hi + lo at the current state
-rpba_status prep_ff_state(Ctx *ctx) {
+// FP32 form: the camera records and the hi + lo words of X and X^l follow
+// the FP64 state. Kernels that change that state keep them current
+// (intersection, exchange, TP copies, LM apply); this rebuilds all of them
+// after the host sets the state.
+rpba_status sync_mirrors(Ctx *ctx) {
   RPBA_TRY(cam_prep(ctx));
+  RPBA_TRY(split_points(ctx, 0));
   return split_points(ctx, 1);
 }
 
@@ -250,8 +245,6 @@ rpba_status launch_residuals(Ctx *ctx, double *v_dev) {
 
 rpba_status launch_jacobians(Ctx *ctx, double *Jc, double *Jx) {
   if (ctx->K == 0) return RPBA_OK;
-  RPBA_TRY(cam_prep(ctx));
-  RPBA_TRY(split_points(ctx, 1));
   if (ctx->opt.precision == 1)
     RPBA_KERNEL(ctx, "k_jacobians", k_jacobians<float><<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(make_view(ctx), Jc, Jx));
   else
@@ -361,8 +354,6 @@ rpba_status launch_sigma0(Ctx *ctx, double *sigma0, double *rms) {
   View v = make_view(ctx);
   int nb = ctx->red_blocks;
   if (ctx->opt.precision == 1) {
-    RPBA_TRY(cam_prep(ctx));
-    RPBA_TRY(split_points(ctx, 1));
     RPBA_KERNEL(ctx, "k_obs_sigma", k_obs_sigma_f<<<nb, 256, 0, ctx->stream>>>(v, ctx->red));
   } else {
     RPBA_KERNEL(ctx, "k_obs_sigma", k_obs_sigma<<<nb, 256, 0, ctx->stream>>>(v, ctx->red));
@@ -490,16 +481,23 @@ __global__ void k_isect_point(View v, int *state, int *iter, const T *part, int 
       fail = fail || !(detd > 0.0) || !(sym3_frob<double>(Nimg) * sym3_frob<double>(invd) <= cond_max);
       for (int r = 0; r < 3; r++)
         d[r] = invd[s3idx(r, 0)] * gd[0] + invd[s3idx(r, 1)] * gd[1] + invd[s3idx(r, 2)] * gd[2];
+      if (px_tol > 0.0) {
+        double Nd3[3];
+        for (int r = 0; r < 3; r++) Nd3[r] = Nimg[s3idx(r, 0)] * d[0] + Nimg[s3idx(r, 1)] * d[1] + Nimg[s3idx(r, 2)] * d[2];
+        nd2_img = d[0] * Nd3[0] + d[1] * Nd3[1] + d[2] * Nd3[2];
+      }
     } else {
+      // the step and its image-space size in the compute precision; only the
+      // position update below is FP64
       fail = !(det > T(0)) || !((double)cond <= cond_max);
-      for (int r = 0; r < 3; r++)
-        d[r] = (double)(inv[s3idx(r, 0)] * g[0] + inv[s3idx(r, 1)] * g[1] + inv[s3idx(r, 2)] * g[2]);
-      for (int e = 0; e < 6; e++) Nimg[e] = (double)N[e];
-    }
-    if (px_tol > 0.0) {
-      double Nd3[3];
-      for (int r = 0; r < 3; r++) Nd3[r] = Nimg[s3idx(r, 0)] * d[0] + Nimg[s3idx(r, 1)] * d[1] + Nimg[s3idx(r, 2)] * d[2];
-      nd2_img = d[0] * Nd3[0] + d[1] * Nd3[1] + d[2] * Nd3[2];
+      T dT[3];
+      for (int r = 0; r < 3; r++) dT[r] = inv[s3idx(r, 0)] * g[0] + inv[s3idx(r, 1)] * g[1] + inv[s3idx(r, 2)] * g[2];
+      if (px_tol > 0.0) {
+        T Nd3[3];
+        for (int r = 0; r < 3; r++) Nd3[r] = N[s3idx(r, 0)] * dT[0] + N[s3idx(r, 1)] * dT[1] + N[s3idx(r, 2)] * dT[2];
+        nd2_img = (double)(dT[0] * Nd3[0] + dT[1] * Nd3[1] + dT[2] * Nd3[2]);
+      }
+      for (int r = 0; r < 3; r++) d[r] = (double)dT[r];
     }
   }
   bool conv = false;
@@ -507,11 +505,19 @@ __global__ void k_isect_point(View v, int *state, int *iter, const T *part, int 
     double Xn[3];
     for (int r = 0; r < 3; r++) Xn[r] = v.X[3 * j + r] - d[r];
     for (int r = 0; r < 3; r++) v.X[3 * j + r] = Xn[r];
-    if (sizeof(T) == sizeof(float))
+    if (v.X_hi)  // FP32 form (also under its FP64 first intersection): the hi + lo mirror
       for (int r = 0; r < 3; r++) split(Xn[r], v.X_hi[3 * j + r], v.X_lo[3 * j + r]);
-    double nd = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    double nx = sqrt(Xn[0] * Xn[0] + Xn[1] * Xn[1] + Xn[2] * Xn[2]);
-    conv = nd <= tol * (1.0 + nx);
+    if constexpr (sizeof(T) == sizeof(float)) {
+      float df[3] = {(float)d[0], (float)d[1], (float)d[2]};
+      const float *xh = v.X_hi + 3 * j;
+      float nd = sqrtf(df[0] * df[0] + df[1] * df[1] + df[2] * df[2]);
+      float nx = sqrtf(xh[0] * xh[0] + xh[1] * xh[1] + xh[2] * xh[2]);
+      conv = nd <= (float)tol * (1.f + nx);
+    } else {
+      double nd = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      double nx = sqrt(Xn[0] * Xn[0] + Xn[1] * Xn[1] + Xn[2] * Xn[2]);
+      conv = nd <= tol * (1.0 + nx);
+    }
     if (!conv && px_tol > 0.0) conv = nd2_img <= px_tol * px_tol * (double)nobs;
   }
   int it = ++iter[j];
@@ -571,8 +577,6 @@ __global__ void k_isect_count(const int *state, int n, int *running, int *failed
 rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped, bool fp64) {
   View v = make_view(ctx);
   if (ctx->N == 0) { if (n_dropped) *n_dropped = 0; return RPBA_OK; }
-  RPBA_TRY(cam_prep(ctx));
-  RPBA_TRY(split_points(ctx, 1));
   RPBA_CUDA(cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(int), ctx->stream));
   RPBA_KERNEL(ctx, "k_isect_start", k_isect_start<<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(
                                         v, ctx->isect_state, ctx->isect_iter, tp_only, ctx->counters));
@@ -614,6 +618,11 @@ __global__ void k_exchange(View v) {
   if (v.pt_inst_ptr[j + 1] - q0 != 1) return;
   int q = v.pt_inst[q0];
   for (int e = 0; e < 3; e++) v.X[3 * j + e] = v.Xl[3 * (size_t)q + e];
+  if (v.X_hi)
+    for (int e = 0; e < 3; e++) {
+      v.X_hi[3 * j + e] = v.Xl_hi[3 * (size_t)q + e];
+      v.X_lo[3 * j + e] = v.Xl_lo[3 * (size_t)q + e];
+    }
 }
 
 // sub-block copies restart at the intersected position
@@ -623,6 +632,11 @@ __global__ void k_tp_copies(View v, int tp_only) {
   int j = v.inst_pt[q];
   if (tp_only && v.pt_inst_ptr[j + 1] - v.pt_inst_ptr[j] < 2) return;
   for (int e = 0; e < 3; e++) v.Xl[3 * (size_t)q + e] = v.X[3 * j + e];
+  if (v.Xl_hi)
+    for (int e = 0; e < 3; e++) {
+      v.Xl_hi[3 * (size_t)q + e] = v.X_hi[3 * j + e];
+      v.Xl_lo[3 * (size_t)q + e] = v.X_lo[3 * j + e];
+    }
 }
 
 rpba_status launch_exchange(Ctx *ctx) {
@@ -818,11 +832,6 @@ __global__ void k_seg_final(int L, const int *run, const double *part, double *F
 static rpba_status sub_costs_impl(Ctx *ctx, int trial, const int *run, double *F_dev) {
   View v = make_view(ctx);
   if (ctx->K && ctx->opt.precision == 1) {
-    if (!trial) {  // the trial state's records come from the trial kernels
-      RPBA_TRY(cam_prep(ctx));
-      RPBA_TRY(split_points(ctx, 0));
-      RPBA_TRY(split_points(ctx, 1));
-    }
     RPBA_KERNEL(ctx, "k_obs_cost", k_obs_cost_f<<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(v, trial, run, ctx->obs_cost));
   } else if (ctx->K) {
     RPBA_KERNEL(ctx, "k_obs_cost", k_obs_cost<<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(v, trial, run, ctx->obs_cost));
@@ -916,11 +925,20 @@ __global__ void k_linearize(View v, const double *lambda, const int *run, T *NXC
       for (int c = 0; c < 6; c++) o[6 * r + c] = a0[r] * pj.Jc[c] + a1[r] * pj.Jc[6 + c];
   }
   // TP control term
-  const double *Wq = v.Wl + 6 * (size_t)q;
-  double d[3] = {Xd[0] - v.X[3 * j], Xd[1] - v.X[3 * j + 1], Xd[2] - v.X[3 * j + 2]};
-  for (int e = 0; e < 6; e++) N[e] += (T)Wq[e];
-  for (int r = 0; r < 3; r++)
-    g[r] += (T)(Wq[s3idx(r, 0)] * d[0] + Wq[s3idx(r, 1)] * d[1] + Wq[s3idx(r, 2)] * d[2]);
+  if constexpr (sizeof(T) == sizeof(float)) {
+    // X^l - X_TP from the hi + lo words (the leading parts cancel exactly), W^l in FP32
+    const float *Wq = v.Wl32 + 6 * (size_t)q;
+    float d[3];
+    for (int e = 0; e < 3; e++)
+      d[e] = __fadd_rn(__fsub_rn(Xh[e], v.X_hi[3 * (size_t)j + e]), __fsub_rn(Xw[e], v.X_lo[3 * (size_t)j + e]));
+    for (int e = 0; e < 6; e++) N[e] += Wq[e];
+    for (int r = 0; r < 3; r++) g[r] += Wq[s3idx(r, 0)] * d[0] + Wq[s3idx(r, 1)] * d[1] + Wq[s3idx(r, 2)] * d[2];
+  } else {
+    const double *Wq = v.Wl + 6 * (size_t)q;
+    double d[3] = {Xd[0] - v.X[3 * j], Xd[1] - v.X[3 * j + 1], Xd[2] - v.X[3 * j + 2]};
+    for (int e = 0; e < 6; e++) N[e] += Wq[e];
+    for (int r = 0; r < 3; r++) g[r] += Wq[s3idx(r, 0)] * d[0] + Wq[s3idx(r, 1)] * d[1] + Wq[s3idx(r, 2)] * d[2];
+  }
   // damping of the point block
   T lam = (T)lambda[l];
   N[0] += lam * N[0]; N[3] += lam * N[3]; N[5] += lam * N[5];
@@ -1070,8 +1088,6 @@ __global__ void k_rcs_clear(View v, const int *run, int L) {
 }
 
 rpba_status launch_build_rcs(Ctx *ctx, const double *lambda_dev, const int *run_dev) {
-  RPBA_TRY(cam_prep(ctx));
-  RPBA_TRY(split_points(ctx, 0));
   View v = make_view(ctx);
   dim3 gclr(64, ctx->L);
   RPBA_KERNEL(ctx, "k_rcs_clear", k_rcs_clear<<<gclr, 256, 0, ctx->stream>>>(v, run_dev, ctx->L));
@@ -1240,12 +1256,19 @@ __global__ void k_lm_apply_cams(View v, const int *acc) {
   double *t = const_cast<double *>(v.t) + 3 * i;
   for (int e = 0; e < 9; e++) R[e] = v.Rt[9 * i + e];
   for (int e = 0; e < 3; e++) t[e] = v.tt[3 * i + e];
+  if (v.camff)
+    for (int e = 0; e < FF_CAM; e++) v.camff[FF_CAM * (size_t)i + e] = v.camff_t[FF_CAM * (size_t)i + e];
 }
 
 __global__ void k_lm_apply_inst(View v, const int *acc) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= v.P || !acc[v.inst_sub[q]]) return;
   for (int e = 0; e < 3; e++) v.Xl[3 * (size_t)q + e] = v.Xlt[3 * (size_t)q + e];
+  if (v.Xl_hi)
+    for (int e = 0; e < 3; e++) {
+      v.Xl_hi[3 * (size_t)q + e] = v.Xlt_hi[3 * (size_t)q + e];
+      v.Xl_lo[3 * (size_t)q + e] = v.Xlt_lo[3 * (size_t)q + e];
+    }
 }
 
 rpba_status launch_lm_apply(Ctx *ctx, const int *acc_dev) {

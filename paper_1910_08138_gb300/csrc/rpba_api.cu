@@ -435,8 +435,6 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
     RPBA_TRY(upload(ctx, &ctx->sub_obs_ptr, sop.data(), (size_t)L + 1));
   }
   RPBA_TRY(alloc_n(ctx, &ctx->obs_cost, (size_t)K));
-  RPBA_TRY(alloc_n(ctx, &ctx->camC, 3 * (size_t)M));
-  RPBA_TRY(alloc_n(ctx, &ctx->camRf, 16 * (size_t)M));
   if (ctx->opt.precision == 1) {
     // FP32 form: inputs rounded once (observations relative to the principal point)
     std::vector<float> xy32(2 * (size_t)K), w32((size_t)K, 1.0f), wi32(ctx->has_winv ? 3 * (size_t)K : 0);
@@ -457,8 +455,6 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
     RPBA_TRY(upload(ctx, &ctx->obs_xylo, xylo.data(), xylo.size()));
     RPBA_TRY(upload(ctx, &ctx->obs_w32, w32.data(), w32.size()));
     if (ctx->has_winv) RPBA_TRY(upload(ctx, &ctx->obs_winv32, wi32.data(), wi32.size()));
-    RPBA_TRY(alloc_n(ctx, &ctx->camChi, 3 * (size_t)M));
-    RPBA_TRY(alloc_n(ctx, &ctx->camClo, 3 * (size_t)M));
     RPBA_TRY(alloc_n(ctx, &ctx->Xl_hi, 3 * (size_t)P));
     RPBA_TRY(alloc_n(ctx, &ctx->Xl_lo, 3 * (size_t)P));
     RPBA_TRY(alloc_n(ctx, &ctx->X_hi, 3 * (size_t)N));
@@ -563,6 +559,7 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   if (M) RPBA_KERNEL(ctx, "k_pose_to_R", k_pose_to_R<<<nblk(M, 128), 128, 0, ctx->stream>>>(M, pose_d, ctx->R, ctx->t));
   RPBA_TRY(launch_fill_double(ctx, ctx->obs_w, K, 1.0));
   RPBA_TRY(launch_fill_double(ctx, ctx->Wl, 6LL * P, 0.0));
+  RPBA_TRY(sync_mirrors(ctx));
   RPBA_TRY(launch_tp_copies(ctx, 0));
   RPBA_TRY(sync(ctx));
   ctx->n_active_start = nact;
@@ -658,6 +655,7 @@ extern "C" rpba_status rpba_set_cameras(rpba_ctx *h, const double *pose) {
   RPBA_TRY(d.alloc(6 * (size_t)ctx->M * sizeof(double)));
   RPBA_CUDA(cudaMemcpyAsync(d.p, pose, 6 * (size_t)ctx->M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   if (ctx->M) RPBA_KERNEL(ctx, "k_pose_to_R", k_pose_to_R<<<nblk(ctx->M, 128), 128, 0, ctx->stream>>>(ctx->M, (double *)d.p, ctx->R, ctx->t));
+  RPBA_TRY(sync_mirrors(ctx));
   return sync(ctx);
 }
 
@@ -675,6 +673,7 @@ extern "C" rpba_status rpba_set_points(rpba_ctx *h, const double *X, const uint8
   CTX_OR_FAIL;
   if (X) RPBA_CUDA(cudaMemcpyAsync(ctx->X, X, 3 * (size_t)ctx->N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   if (active) RPBA_CUDA(cudaMemcpyAsync(ctx->active, active, (size_t)ctx->N, cudaMemcpyHostToDevice, ctx->stream));
+  RPBA_TRY(sync_mirrors(ctx));
   return sync(ctx);
 }
 
@@ -698,6 +697,7 @@ extern "C" rpba_status rpba_set_instances(rpba_ctx *h, const double *Xl, const d
   CTX_OR_FAIL;
   if (Xl) RPBA_CUDA(cudaMemcpyAsync(ctx->Xl, Xl, 3 * (size_t)ctx->P * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   if (Wl) RPBA_CUDA(cudaMemcpyAsync(ctx->Wl, Wl, 6 * (size_t)ctx->P * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  RPBA_TRY(sync_mirrors(ctx));
   if (Wl && ctx->Wl32 && ctx->P) {
     std::vector<float> w32(Wl, Wl + 6 * (size_t)ctx->P);
     RPBA_CUDA(cudaMemcpyAsync(ctx->Wl32, w32.data(), w32.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));

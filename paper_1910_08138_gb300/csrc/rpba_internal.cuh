@@ -224,11 +224,9 @@ struct Ctx {
   int *pcg_live = nullptr, *pcg_tiles = nullptr;
   int pcg_tiles_total = 0;
   double *obs_cost = nullptr, *seg_part = nullptr;
-  double *camC = nullptr;
   double *obs_whiten = nullptr;  // per observation upper Cholesky factor of C^-1 (when given)
-  float *camRf = nullptr;
   float *obs_xy32 = nullptr, *obs_winv32 = nullptr, *obs_w32 = nullptr;
-  float *camChi = nullptr, *camClo = nullptr, *Xl_hi = nullptr, *Xl_lo = nullptr, *X_hi = nullptr,
+  float *Xl_hi = nullptr, *Xl_lo = nullptr, *X_hi = nullptr,
         *X_lo = nullptr, *dC32 = nullptr;
   // FP32 form, float-float residuals: camera records (FF_CAM floats) of the
   // current and the trial state, the low words of the observations relative
@@ -386,8 +384,9 @@ rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped, bool fp64 = 
 rpba_status launch_exchange(Ctx *ctx);
 rpba_status launch_tp_copies(Ctx *ctx, int tp_only);
 rpba_status launch_camera_scale(Ctx *ctx);
-// FP32 form: camera records and the points' hi + lo words at the current state
-rpba_status prep_ff_state(Ctx *ctx);
+// FP32 form: rebuild the camera records and the hi + lo words of X and X^l
+// from the FP64 state (after the host sets it)
+rpba_status sync_mirrors(Ctx *ctx);
 rpba_status launch_robust_weights(Ctx *ctx, int *n_down);
 rpba_status launch_eliminate(Ctx *ctx);
 rpba_status launch_sub_costs(Ctx *ctx, int trial, double *F_dev);
