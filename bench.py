@@ -151,11 +151,20 @@ def update_tiles(sub_sizes, tile=32):
     return tot
 
 
-def roofline(prof, steps, n_sub_sizes, K, peaks, mem_bound_bytes, symv_flops=0.0):
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+
+
+def roofline(prof, steps, n_sub_sizes, K, peaks, mem_bound_bytes, symv_flops=0.0, alu_flops=None):
     # the dominant kernel, event-timed over the timed region
     name, (launches, ms) = max(prof.items(), key=lambda kv: kv[1][1])
     per_launch_s = ms / 1e3 / max(launches, 1)
-    if name == "k_pcg_symv" and symv_flops > 0:
+    if alu_flops and name in alu_flops:
+        achieved = alu_flops[name] / per_launch_s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP32 CUDA-core rate from 152 SMs x 128 lanes x 2 flops x 2070 MHz",
+                "launches": launches, "avg_launch_ms": per_launch_s * 1e3}
+    if name == "k_pcg_symv" and symv_flops > 0 and name not in mem_bound_bytes:
         achieved = symv_flops / max(launches, 1) / per_launch_s / 1e12
         peak = fp64_peak_gflops() / 1e3
         return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -183,6 +192,15 @@ def roofline(prof, steps, n_sub_sizes, K, peaks, mem_bound_bytes, symv_flops=0.0
     return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": "measured",
             "launches": launches, "avg_launch_ms": per_launch_s * 1e3}
+
+
+def schur_pairs(prob):
+    """Point pairs of the Schur complement: sum over point instances (point,
+    sub-block) of n (n - 1) / 2, n the instance's observations."""
+    sub = np.asarray(prob["cam_subblock"])[np.asarray(prob["obs_cam"])].astype(np.int64)
+    key = np.asarray(prob["obs_point"]).astype(np.int64) * (int(sub.max()) + 1) + sub
+    _, n = np.unique(key, return_counts=True)
+    return float(np.sum(n * (n - 1) // 2))
 
 
 def load_peaks():
@@ -376,12 +394,23 @@ def run_ours(args, rank, world):
         # inverse blocks (48 B per entry)
         step_bytes = sum(float(np.dot(it, n_sub)) * (10 * 8 + 48) for it in pcg_iters)
         iters = sum(int(np.max(it)) for it in pcg_iters)
+        if iters and args.precision == 1 and solver == 1:
+            # float-float form: x, r, p pairs (8 B) read and written, q (8 B)
+            # read, z (4 B) written and read, the FP32 inverse blocks (24 B per
+            # entry); the product reads 8 B (hi + lo) per stored lower-tile entry
+            step_bytes = sum(float(np.dot(it, n_sub)) * (3 * 16 + 8 + 8 + 24) for it in pcg_iters)
+            tiles = [(n // 32) * (n // 32 + 1) // 2 for n in npad]
+            mem_bytes["k_pcg_symv"] = sum(float(np.dot(it, tiles)) * 1024 * 8 for it in pcg_iters) / iters
         if iters:
             mem_bytes["k_pcg_step"] = step_bytes / iters
     # robust scale: per observation its indices, xy, the point and its active flag
     mem_bytes["k_camera_mad"] = K * (4 + 4 + 16 + 24 + 1) + ctx.M * 9 * 8
+    # off-diagonal Schur blocks (FP32 form): per point pair the 6x6 product
+    # N_XC,a^T (Ninv N_XC,b), 216 flops, plus Z = Ninv N_XC once per observation,
+    # 108 flops (pairs of the active instances at the start of the step)
+    alu_flops = {"k_schur_seg": 216.0 * schur_pairs(prob) + 108.0 * K} if args.precision == 1 else None
     roof = roofline({dominant: prof.get(dominant, (0, 0.0))}, args.steps, n_sub, K, peaks, mem_bytes,
-                    symv_flops=symv_flops)
+                    symv_flops=symv_flops, alu_flops=alu_flops)
     kernels = {k: {"launches": v[0], "ms": round(v[1], 4)}
                for k, v in sorted(prof_all.items(), key=lambda kv: -kv[1][1])}
     line = {"metric": METRIC, "value": value, "unit": "obs/s", "n_gpus": world, "steps": args.steps,

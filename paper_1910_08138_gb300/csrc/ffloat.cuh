@@ -64,6 +64,42 @@ __device__ __forceinline__ float ff_div(float ah, float al, float bh, float bl, 
   return q;
 }
 
+// (ah + al) + (bh + bl), renormalised
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  float e;
+  float s = ff_two_sum(a.x, b.x, e);
+  e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+  float2 o;
+  o.x = ff_fast_two_sum(s, e, o.y);
+  return o;
+}
+
+// (ah + al) (bh + bl), renormalised (the al*bl term is below the precision)
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+  float e;
+  float p = ff_two_prod(a.x, b.x, e);
+  e = __fmaf_rn(a.y, b.x, __fmaf_rn(a.x, b.y, e));
+  float2 o;
+  o.x = ff_fast_two_sum(p, e, o.y);
+  return o;
+}
+
+// running sum s (hi + lo) += x (one float), without renormalising
+__device__ __forceinline__ void ff_acc(float &sh, float &sl, float x) {
+  float e;
+  sh = ff_two_sum(sh, x, e);
+  sl = __fadd_rn(sl, e);
+}
+
+__device__ __forceinline__ float2 ff_of(double x) {
+  float2 o;
+  o.x = (float)x;
+  o.y = (float)(x - (double)o.x);
+  return o;
+}
+
+__device__ __forceinline__ double ff_to_double(float2 a) { return (double)a.x + (double)a.y; }
+
 // host-side or device-side split of a double into hi + lo
 __host__ __device__ __forceinline__ void ff_split(double x, float &hi, float &lo) {
   hi = (float)x;

@@ -878,11 +878,13 @@ __device__ __noinline__ void instance_normal_fp64(const View &v, int q, double l
   N[0] += lam * N[0]; N[3] += lam * N[3]; N[5] += lam * N[5];
 }
 
-// per instance: N_XX (+ W^l, damped), g_X, Ninv; per observation N_XC = w A_X^T W A_C
-// and Z = Ninv N_XC (both 3x6 row-major). FP32 form: when the FP32 N_XX has a
-// Frobenius condition number above 1e5, N_XX and g_X are formed again in FP64
-// and the FP64 inverse is rounded to FP32 (an FP32 inverse would be wrong in
-// the weak direction).
+// per instance: N_XX (+ W^l, damped), g_X, Ninv. FP64 form: also per
+// observation N_XC = w A_X^T W A_C and Z = Ninv N_XC (both 3x6 row-major),
+// read by the camera and Schur kernels. The FP32 form stores nothing per
+// observation: its consumers form those blocks again in registers. FP32
+// form: when the FP32 N_XX has a Frobenius condition number above 1e5, N_XX
+// and g_X are formed again in FP64 and the FP64 inverse is rounded to FP32 (an
+// FP32 inverse would be wrong in the weak direction).
 template <typename T>
 __global__ void k_linearize(View v, const double *lambda, const int *run, T *NXC, T *Z, T *Ninv_out,
                             T *gX_out) {
@@ -892,11 +894,13 @@ __global__ void k_linearize(View v, const double *lambda, const int *run, T *NXC
   if (!run[l]) return;
   int j = v.inst_pt[q];
   int k0 = v.inst_obs_ptr[q], k1 = v.inst_obs_ptr[q + 1];
+  constexpr bool kStore = sizeof(T) == sizeof(double);
   if (!v.active[j]) {
     for (int e = 0; e < 6; e++) Ninv_out[6 * (size_t)q + e] = 0;
     for (int e = 0; e < 3; e++) gX_out[3 * (size_t)q + e] = 0;
-    for (int k = k0; k < k1; k++)
-      for (int e = 0; e < 18; e++) { NXC[18 * (size_t)k + e] = 0; Z[18 * (size_t)k + e] = 0; }
+    if (kStore)
+      for (int k = k0; k < k1; k++)
+        for (int e = 0; e < 18; e++) { NXC[18 * (size_t)k + e] = 0; Z[18 * (size_t)k + e] = 0; }
     return;
   }
   const double *Xd = v.Xl + 3 * (size_t)q;
@@ -919,10 +923,12 @@ __global__ void k_linearize(View v, const double *lambda, const int *run, T *NXC
       for (int c = r; c < 3; c++) N[s3idx(r, c)] += pj.Jx[r] * a0[c] + pj.Jx[3 + r] * a1[c];
       g[r] += a0[r] * r0 + a1[r] * r1;
     }
-    // N_XC = (w W A_X)^T A_C : row r (point coord) = a0[r] Jc[0,:] + a1[r] Jc[1,:]
-    T *o = NXC + 18 * (size_t)k;
-    for (int r = 0; r < 3; r++)
-      for (int c = 0; c < 6; c++) o[6 * r + c] = a0[r] * pj.Jc[c] + a1[r] * pj.Jc[6 + c];
+    if (kStore) {
+      // N_XC = (w W A_X)^T A_C : row r (point coord) = a0[r] Jc[0,:] + a1[r] Jc[1,:]
+      T *o = NXC + 18 * (size_t)k;
+      for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 6; c++) o[6 * r + c] = a0[r] * pj.Jc[c] + a1[r] * pj.Jc[6 + c];
+    }
   }
   // TP control term
   if constexpr (sizeof(T) == sizeof(float)) {
@@ -955,6 +961,7 @@ __global__ void k_linearize(View v, const double *lambda, const int *run, T *NXC
   }
   for (int e = 0; e < 6; e++) Ninv_out[6 * (size_t)q + e] = inv[e];
   for (int e = 0; e < 3; e++) gX_out[3 * (size_t)q + e] = g[e];
+  if (kStore)
   for (int k = k0; k < k1; k++) {
     const T *B = NXC + 18 * (size_t)k;
     T *o = Z + 18 * (size_t)k;
@@ -964,13 +971,40 @@ __global__ void k_linearize(View v, const double *lambda, const int *run, T *NXC
   }
 }
 
+// FP32 form: N_XC = (w W A_X)^T A_C of observation k (camera i, instance q)
+// in registers, with the projection at the instance's X^l
+__device__ inline void nxc_f(const View &v, int i, int k, int q, float B[18]) {
+  ProjJac<float> pj;
+  float z;
+  obs_proj<float>(v, i, nullptr, v.Xl_hi + 3 * (size_t)q, v.Xl_lo + 3 * (size_t)q, pj, z);
+  float w = v.obs_w32[k], W0 = 1.f, W1 = 0.f, W2 = 1.f;
+  if (v.has_winv) { W0 = v.obs_winv32[3 * k]; W1 = v.obs_winv32[3 * k + 1]; W2 = v.obs_winv32[3 * k + 2]; }
+#pragma unroll
+  for (int r = 0; r < 3; r++) {
+    float a0 = w * (W0 * pj.Jx[r] + W1 * pj.Jx[3 + r]);
+    float a1 = w * (W1 * pj.Jx[r] + W2 * pj.Jx[3 + r]);
+#pragma unroll
+    for (int c = 0; c < 6; c++) B[6 * r + c] = a0 * pj.Jc[c] + a1 * pj.Jc[6 + c];
+  }
+}
+
+// Z = Ninv N_XC (3x6) with Ninv a packed symmetric 3x3
+__device__ inline void z_of(const float inv[6], const float B[18], float Zk[18]) {
+#pragma unroll
+  for (int r = 0; r < 3; r++)
+#pragma unroll
+    for (int c = 0; c < 6; c++)
+      Zk[6 * r + c] = inv[s3idx(r, 0)] * B[c] + inv[s3idx(r, 1)] * B[6 + c] + inv[s3idx(r, 2)] * B[12 + c];
+}
+
 // one CTA (CB_THREADS threads) per camera of a running sub-block: diagonal RCS block
 //   S_ii = U_ii + lambda diag(U_ii) - sum_k N_XC,k^T Z_k,  U_ii = sum_k w A_C^T W A_C
 // and right-hand side y_i = -sum_k w A_C^T W v + sum_k Z_k^T g_X
 #define CB_THREADS 128
 template <typename T>
 __global__ void __launch_bounds__(CB_THREADS) k_camera_blocks(View v, const double *lambda, const int *run,
-                                                              const T *NXC, const T *Z, const T *gX) {
+                                                              const T *NXC, const T *Z, const T *gX,
+                                                              const T *Ninv) {
   int i = blockIdx.x;
   if (i >= v.M) return;
   int l = v.cam_sub[i];
@@ -996,10 +1030,25 @@ __global__ void __launch_bounds__(CB_THREADS) k_camera_blocks(View v, const doub
       b0[c] = ob.w * (ob.W[0] * pj.Jc[c] + ob.W[1] * pj.Jc[6 + c]);
       b1[c] = ob.w * (ob.W[1] * pj.Jc[c] + ob.W[2] * pj.Jc[6 + c]);
     }
-    const T *B = NXC + 18 * (size_t)k, *Zk = Z + 18 * (size_t)k, *gq = gX + 3 * (size_t)q;
+    const T *gq = gX + 3 * (size_t)q;
     T Bl[18], Zl[18], g3[3] = {gq[0], gq[1], gq[2]};
+    if constexpr (sizeof(T) == sizeof(float)) {  // N_XC and Z in registers
 #pragma unroll
-    for (int e = 0; e < 18; e++) { Bl[e] = B[e]; Zl[e] = Zk[e]; }
+      for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 6; c++) {
+          T a0 = ob.w * (ob.W[0] * pj.Jx[r] + ob.W[1] * pj.Jx[3 + r]);
+          T a1 = ob.w * (ob.W[1] * pj.Jx[r] + ob.W[2] * pj.Jx[3 + r]);
+          Bl[6 * r + c] = a0 * pj.Jc[c] + a1 * pj.Jc[6 + c];
+        }
+      const float *iv = Ninv + 6 * (size_t)q;
+      float inv[6] = {iv[0], iv[1], iv[2], iv[3], iv[4], iv[5]};
+      z_of(inv, Bl, Zl);
+    } else {
+      const T *B = NXC + 18 * (size_t)k, *Zk = Z + 18 * (size_t)k;
+#pragma unroll
+      for (int e = 0; e < 18; e++) { Bl[e] = B[e]; Zl[e] = Zk[e]; }
+    }
     int e = 0;
 #pragma unroll
     for (int r = 0; r < 6; r++) {
@@ -1070,6 +1119,66 @@ __global__ void k_schur_pairs(View v, const int *run, const int *pa, const int *
   }
 }
 
+// FP32 form, off-diagonal Schur blocks: one thread per point pair (a seen
+// by camera i, b seen by camera i', the same instance, local(i) > local(i')),
+//   S[6 li + r, 6 li' + c] -= sum_e N_XC,a[e][r] Z_b[e][c],
+// the blocks formed in FP32 registers. The pairs are sorted by camera pair
+// (segment), so a warp's 32 pairs cover few segments: a segmented warp
+// reduction sums each segment's part and its first lane adds the 36 values
+// to S (FP64 atomics, one set per segment piece instead of one per pair).
+#define SC_THREADS 256
+__global__ void __launch_bounds__(SC_THREADS) k_schur_seg(View v, const int *run, long long npairs,
+                                                          const int *spa, const int *spb, const int *spq,
+                                                          const int *sps, const int *seg_cam, const int *seg_nb,
+                                                          const float *Ninv) {
+  long long p = (long long)blockIdx.x * SC_THREADS + threadIdx.x;
+  int lane = threadIdx.x & 31;
+  int sg = -1;
+  float acc[36];
+#pragma unroll
+  for (int e = 0; e < 36; e++) acc[e] = 0.f;
+  if (p < npairs) {
+    sg = sps[p];
+    int i = seg_cam[sg], ib = seg_nb[sg], q = spq[p];
+    if (run[v.cam_sub[i]] && v.active[v.inst_pt[q]]) {
+      float A[18], B[18], Zb[18];
+      nxc_f(v, i, spa[p], q, A);
+      nxc_f(v, ib, spb[p], q, B);
+      const float *iv = Ninv + 6 * (size_t)q;
+      float inv[6] = {iv[0], iv[1], iv[2], iv[3], iv[4], iv[5]};
+      z_of(inv, B, Zb);
+#pragma unroll
+      for (int r = 0; r < 6; r++)
+#pragma unroll
+        for (int c = 0; c < 6; c++)
+          acc[6 * r + c] = A[r] * Zb[c] + A[6 + r] * Zb[6 + c] + A[12 + r] * Zb[12 + c];
+    }
+  }
+  // segments are contiguous runs of lanes: after the steps, a lane holds the
+  // sum over itself and the following lanes of its run
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int so = __shfl_down_sync(0xffffffffu, sg, o);
+    bool take = (lane + o < 32) && so == sg;
+#pragma unroll
+    for (int e = 0; e < 36; e++) {
+      float y = __shfl_down_sync(0xffffffffu, acc[e], o);
+      if (take) acc[e] += y;
+    }
+  }
+  int sprev = __shfl_up_sync(0xffffffffu, sg, 1);
+  if (sg < 0 || (lane > 0 && sprev == sg)) return;
+  int i = seg_cam[sg], ib = seg_nb[sg];
+  int l = v.cam_sub[i];
+  if (!run[l]) return;
+  int np = v.npad[l];
+  double *row = v.S + v.S_off[l] + (size_t)(6 * v.cam_local[i]) * np + 6 * v.cam_local[ib];
+#pragma unroll
+  for (int r = 0; r < 6; r++)
+#pragma unroll
+    for (int c = 0; c < 6; c++) atomicAdd(row + (size_t)r * np + c, -(double)acc[6 * r + c]);
+}
+
 // zero the RCS of running sub-blocks, identity on the padding
 __global__ void k_rcs_clear(View v, const int *run, int L) {
   int l = blockIdx.y;
@@ -1093,20 +1202,20 @@ rpba_status launch_build_rcs(Ctx *ctx, const double *lambda_dev, const int *run_
   RPBA_KERNEL(ctx, "k_rcs_clear", k_rcs_clear<<<gclr, 256, 0, ctx->stream>>>(v, run_dev, ctx->L));
   if (ctx->P == 0) return RPBA_OK;
   if (ctx->opt.precision == 1) {
-    float *NXC = (float *)ctx->NXC, *Z = (float *)ctx->Z;
-    RPBA_KERNEL(ctx, "k_linearize", k_linearize<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, lambda_dev, run_dev, NXC, Z,
-                                                                   (float *)ctx->Ninv, (float *)ctx->gX));
+    RPBA_KERNEL(ctx, "k_linearize", k_linearize<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(
+                                        v, lambda_dev, run_dev, nullptr, nullptr, (float *)ctx->Ninv, (float *)ctx->gX));
     RPBA_KERNEL(ctx, "k_camera_blocks", k_camera_blocks<float><<<ctx->M, CB_THREADS, 0, ctx->stream>>>(
-        v, lambda_dev, run_dev, NXC, Z, (const float *)ctx->gX));
+        v, lambda_dev, run_dev, nullptr, nullptr, (const float *)ctx->gX, (const float *)ctx->Ninv));
     if (ctx->n_pairs)
-      RPBA_KERNEL(ctx, "k_schur_pairs", k_schur_pairs<float><<<nblk(ctx->n_pairs * 6, 256), 256, 0, ctx->stream>>>(
-          v, run_dev, ctx->pair_a, ctx->pair_b, ctx->n_pairs, NXC, Z));
+      RPBA_KERNEL(ctx, "k_schur_seg", k_schur_seg<<<nblk(ctx->n_pairs, SC_THREADS), SC_THREADS, 0, ctx->stream>>>(
+                                          v, run_dev, ctx->n_pairs, ctx->spair_a, ctx->spair_b, ctx->spair_q,
+                                          ctx->spair_seg, ctx->seg_cam, ctx->seg_nb, (const float *)ctx->Ninv));
   } else {
     double *NXC = (double *)ctx->NXC, *Z = (double *)ctx->Z;
     RPBA_KERNEL(ctx, "k_linearize", k_linearize<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, lambda_dev, run_dev, NXC, Z,
                                                                     (double *)ctx->Ninv, (double *)ctx->gX));
     RPBA_KERNEL(ctx, "k_camera_blocks", k_camera_blocks<double><<<ctx->M, CB_THREADS, 0, ctx->stream>>>(
-        v, lambda_dev, run_dev, NXC, Z, (const double *)ctx->gX));
+        v, lambda_dev, run_dev, NXC, Z, (const double *)ctx->gX, (const double *)ctx->Ninv));
     if (ctx->n_pairs)
       RPBA_KERNEL(ctx, "k_schur_pairs", k_schur_pairs<double><<<nblk(ctx->n_pairs * 6, 256), 256, 0, ctx->stream>>>(
           v, run_dev, ctx->pair_a, ctx->pair_b, ctx->n_pairs, NXC, Z));
@@ -1134,18 +1243,30 @@ __global__ void k_backsub(View v, const int *run, const T *NXC, const T *Ninv, c
   }
   T rhs[3] = {-gX[3 * (size_t)q], -gX[3 * (size_t)q + 1], -gX[3 * (size_t)q + 2]};
   for (int k = v.inst_obs_ptr[q]; k < v.inst_obs_ptr[q + 1]; k++) {
-    int off = v.ycam_off[l] + 6 * v.cam_local[v.obs_cam[k]];
-    T dc[6];
+    int i = v.obs_cam[k];
+    int off = v.ycam_off[l] + 6 * v.cam_local[i];
     if constexpr (sizeof(T) == sizeof(float)) {
+      // N_XC dC = (w W A_X)^T (A_C dC), the Jacobians formed again in registers
+      float dc[6];
       for (int c = 0; c < 6; c++) dc[c] = v.dC32[off + c];
+      ProjJac<float> pj;
+      float z;
+      obs_proj<float>(v, i, nullptr, v.Xl_hi + 3 * (size_t)q, v.Xl_lo + 3 * (size_t)q, pj, z);
+      float w = v.obs_w32[k], W0 = 1.f, W1 = 0.f, W2 = 1.f;
+      if (v.has_winv) { W0 = v.obs_winv32[3 * k]; W1 = v.obs_winv32[3 * k + 1]; W2 = v.obs_winv32[3 * k + 2]; }
+      float u0 = 0.f, u1 = 0.f;
+      for (int c = 0; c < 6; c++) { u0 += pj.Jc[c] * dc[c]; u1 += pj.Jc[6 + c] * dc[c]; }
+      float e0 = w * (W0 * u0 + W1 * u1), e1 = w * (W1 * u0 + W2 * u1);
+      for (int r = 0; r < 3; r++) rhs[r] -= pj.Jx[r] * e0 + pj.Jx[3 + r] * e1;
     } else {
+      T dc[6];
       for (int c = 0; c < 6; c++) dc[c] = v.dC[off + c];
-    }
-    const T *B = NXC + 18 * (size_t)k;
-    for (int r = 0; r < 3; r++) {
-      T s = 0;
-      for (int c = 0; c < 6; c++) s += B[6 * r + c] * dc[c];
-      rhs[r] -= s;
+      const T *B = NXC + 18 * (size_t)k;
+      for (int r = 0; r < 3; r++) {
+        T s = 0;
+        for (int c = 0; c < 6; c++) s += B[6 * r + c] * dc[c];
+        rhs[r] -= s;
+      }
     }
   }
   const T *iv = Ninv + 6 * (size_t)q;
@@ -1190,7 +1311,7 @@ rpba_status launch_backsub_trial(Ctx *ctx, const int *run_dev) {
     RPBA_KERNEL(ctx, "k_to_float", k_to_float<<<nblk(ctx->ytot, 256), 256, 0, ctx->stream>>>(ctx->dC, ctx->dC32, ctx->ytot));
   if (ctx->P) {
     if (ctx->opt.precision == 1)
-      RPBA_KERNEL(ctx, "k_backsub", k_backsub<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, run_dev, (const float *)ctx->NXC,
+      RPBA_KERNEL(ctx, "k_backsub", k_backsub<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, run_dev, nullptr,
                                                                    (const float *)ctx->Ninv, (const float *)ctx->gX));
     else
       RPBA_KERNEL(ctx, "k_backsub", k_backsub<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, run_dev, (const double *)ctx->NXC,

@@ -14,6 +14,15 @@
 // ~1000 threads of work).
 // The preconditioner is the inverse of the diagonal camera blocks
 // (block-Jacobi), or the learned factorised inverse G^T G (solver 3).
+//
+// FP32 form, block-Jacobi: the same iteration without FP64 arithmetic in the
+// loop. Once per solve the RCS is split into hi + lo float pairs (2^-48
+// relative); the product S p runs in float-float on the FP32 pipes (TwoProduct
+// and TwoSum per entry), x, r and p are float-float vectors, and the
+// preconditioner is applied in FP32 (it needs no more). The product keeps
+// ~1e-13 relative accuracy, far below the 1e-8 residual the loop stops at; on
+// this GPU the FP64 pipe runs at 1/64 of the FP32 rate, so the FP64 loop is
+// bound by its FP64 instructions and this one by memory and latency.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -30,7 +39,8 @@ static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 // M_i^-1 for every camera of a running sub-block: inverse of S_ii (6x6, FP64,
 // Gauss-Jordan on the SPD block); stored row-major, 36 per camera
 __global__ void k_pcg_bj_setup(int M, const int *cam_sub, const int *cam_local, const int *sub_cam_ptr, const int *run,
-                               const double *S, const long long *S_off, const int *npad, double *Minv, int *fail) {
+                               const double *S, const long long *S_off, const int *npad, double *Minv, int *fail,
+                               float *Minv32) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
   int l = cam_sub[i];
@@ -61,6 +71,11 @@ __global__ void k_pcg_bj_setup(int M, const int *cam_sub, const int *cam_local, 
   double *o = Minv + 36 * (size_t)(sub_cam_ptr[l] + li);  // cameras in sub-block order
   for (int r = 0; r < 6; r++)
     for (int c = 0; c < 6; c++) o[6 * r + c] = a[r][6 + c];
+  if (Minv32) {
+    float *o32 = Minv32 + 36 * (size_t)(sub_cam_ptr[l] + li);
+    for (int r = 0; r < 6; r++)
+      for (int c = 0; c < 6; c++) o32[6 * r + c] = (float)a[r][6 + c];
+  }
 }
 
 // q += S p over the lower 32x32 tiles of the running, unconverged sub-blocks
@@ -133,6 +148,250 @@ __device__ inline void cta_sum(double (&v)[NV], double (&out)[NV]) {
     out[e] = s;
   }
   __syncthreads();
+}
+
+// CTA -> (sub-block l, lower tile (a, b)) through prefix sums of the
+// per-sub-block tile counts
+__device__ inline void tile_of(int idx, const int *sched_tiles, int L, int &l, int &a, int &b) {
+  int lo = 0, hi = L - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (sched_tiles[mid] <= idx) lo = mid; else hi = mid - 1;
+  }
+  l = lo;
+  int loc = idx - sched_tiles[l];
+  a = (int)((sqrtf(8.0f * (float)loc + 1.0f) - 1.0f) * 0.5f);
+  while ((a + 1) * (a + 2) / 2 <= loc) a++;
+  while (a * (a + 1) / 2 > loc) a--;
+  b = loc - a * (a + 1) / 2;
+}
+
+// FP32 form: the lower tiles of the live sub-blocks as hi + lo pairs
+__global__ void __launch_bounds__(256) k_pcg_split(const double *S, const long long *S_off, const int *npad,
+                                                   const int *live, const int *sched_tiles, int L, float2 *Sff) {
+  int l, a, b;
+  tile_of(blockIdx.x, sched_tiles, L, l, a, b);
+  if (!live[l]) return;
+  int np = npad[l];
+  for (int e = threadIdx.x; e < PT * PT; e += blockDim.x) {
+    int r = e / PT, c = e - r * PT;
+    size_t idx = (size_t)S_off[l] + (size_t)(a * PT + r) * np + b * PT + c;
+    Sff[idx] = ff_of(S[idx]);
+  }
+}
+
+// FP32 form: q += S p in float-float, summed over the tiles with FP64
+// atomics. p^T S p is left to the step kernel (p . q over the sub-block):
+// one atomic per tile on a single per-sub-block word serialises hundreds of
+// CTAs.
+__global__ void __launch_bounds__(256) k_pcg_symv_ff(const float2 *__restrict__ Sff, const long long *S_off,
+                                                     const int *npad, const int *voff, const int *live,
+                                                     const int *sched_tiles, int L, const float2 *__restrict__ p,
+                                                     double *q) {
+  int l, a, b;
+  tile_of(blockIdx.x, sched_tiles, L, l, a, b);
+  if (!live[l]) return;
+  int np = npad[l];
+  const float2 *A = Sff + S_off[l];
+  const float2 *pl = p + voff[l];
+  double *ql = q + voff[l];
+  __shared__ float2 blk[PT][PLD];
+  __shared__ float2 pI[PT], pJ[PT];
+  int tid = threadIdx.x;
+  if (tid < PT) {
+    pI[tid] = pl[a * PT + tid];
+    pJ[tid] = pl[b * PT + tid];
+  }
+  for (int e = tid; e < PT * PT; e += blockDim.x) {
+    int r = e / PT, c = e - r * PT;
+    float2 v = A[(size_t)(a * PT + r) * np + b * PT + c];
+    if (a == b && c > r) v = A[(size_t)(a * PT + c) * np + b * PT + r];
+    blk[r][c] = v;
+  }
+  __syncthreads();
+  if (tid < 2 * PT && (tid < PT || a != b)) {
+    bool col = tid >= PT;
+    int t = col ? tid - PT : tid;
+    float sh = 0.f, sl = 0.f;
+    for (int k = 0; k < PT; k++) {
+      float2 m = col ? blk[k][t] : blk[t][k];
+      float2 x = col ? pI[k] : pJ[k];
+      float e;
+      float pr = ff_two_prod(m.x, x.x, e);
+      ff_acc(sh, sl, pr);
+      sl = __fadd_rn(sl, __fmaf_rn(m.y, x.x, __fmaf_rn(m.x, x.y, e)));
+    }
+    atomicAdd(ql + (col ? b : a) * PT + t, (double)sh + (double)sl);
+  }
+}
+
+// FP32 form start: x = 0, r = y, z = M^-1 r (FP32), p = z; rz, |y|
+__global__ void __launch_bounds__(PCG_THREADS) k_pcg_init_ff(const int *run, const int *fail, const int *sub_cam_ptr,
+                                                             const int *voff, const int *npad, const float *Minv32,
+                                                             const double *y, float2 *x, float2 *r, float *z,
+                                                             float2 *p, double *st, int *live) {
+  int l = blockIdx.x;
+  int ok = run[l] && !fail[l];
+  if (threadIdx.x == 0) live[l] = ok;
+  if (!ok) return;
+  int g0 = sub_cam_ptr[l], ncam = sub_cam_ptr[l + 1] - g0;
+  int n = 6 * ncam, o = voff[l];
+  double v[2] = {0.0, 0.0};
+  const float2 zero = make_float2(0.f, 0.f);
+  for (int e = threadIdx.x; e < npad[l]; e += blockDim.x) {  // padding stays zero
+    x[o + e] = zero;
+    r[o + e] = e < n ? ff_of(y[o + e]) : zero;
+    z[o + e] = 0.f;
+    p[o + e] = zero;
+    if (e < n) v[1] += y[o + e] * y[o + e];
+  }
+  __syncthreads();
+  float rzh = 0.f, rzl = 0.f;
+  for (int c = threadIdx.x; c < ncam; c += blockDim.x) {
+    const float *Mi = Minv32 + 36 * (size_t)(g0 + c);
+    const float2 *rc = r + o + 6 * c;
+    for (int a = 0; a < 6; a++) {
+      float t = 0.f;
+      for (int b = 0; b < 6; b++) t += Mi[6 * a + b] * rc[b].x;
+      z[o + 6 * c + a] = t;
+      p[o + 6 * c + a] = make_float2(t, 0.f);
+      float e;
+      float pr = ff_two_prod(rc[a].x, t, e);
+      ff_acc(rzh, rzl, pr);
+      rzl = __fadd_rn(rzl, __fmaf_rn(rc[a].y, t, e));
+    }
+  }
+  v[0] = (double)rzh + (double)rzl;
+  double s[2];
+  cta_sum<2>(v, s);
+  if (threadIdx.x == 0) {
+    st[4 * l + 0] = s[0];                    // rz
+    st[4 * l + 1] = sqrt(s[1]);              // |y|
+    st[4 * l + 2] = s[1] > 0.0 ? 1.0 : 0.0;  // relative residual
+    st[4 * l + 3] = 0.0;                     // iterations
+    if (!(s[1] > 0.0)) live[l] = 0;
+  }
+}
+
+// FP32 form step: p.Sp = p.q, alpha = rz / p.Sp, x += alpha p, r -= alpha q
+// (float-float), z = M^-1 r (FP32), rz' = r.z, beta = rz' / rz, p = z + beta p. Each thread
+// loads all of its elements at once (up to PCGF_PER) so that each phase waits
+// for one memory latency; r and z pass between the phases in shared memory.
+#define PCGF_PER 8
+#define RPBA_PCG_FF_MAX_N_ (PCG_THREADS * PCGF_PER)
+__global__ void __launch_bounds__(PCG_THREADS) k_pcg_step_ff(const int *sub_cam_ptr, const int *voff,
+                                                             const float *__restrict__ Minv32, double tol,
+                                                             float2 *__restrict__ x, float2 *__restrict__ r,
+                                                             float2 *__restrict__ p, const double *__restrict__ q,
+                                                             double *st, int *live) {
+  extern __shared__ float2 rs[];  // r (n), then z as floats (n)
+  int l = blockIdx.x;
+  if (!live[l]) return;
+  int g0 = sub_cam_ptr[l], ncam = sub_cam_ptr[l + 1] - g0;
+  int n = 6 * ncam, o = voff[l];
+  float *zs = reinterpret_cast<float *>(rs + n);
+  // the thread's inverse block, independent of this iteration's data
+  float m[36];
+  int c0 = threadIdx.x;
+  if (c0 < ncam) {
+    const float4 *Mi = reinterpret_cast<const float4 *>(Minv32 + 36 * (size_t)(g0 + c0));
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+      float4 w = __ldg(Mi + k);
+      m[4 * k] = w.x; m[4 * k + 1] = w.y; m[4 * k + 2] = w.z; m[4 * k + 3] = w.w;
+    }
+  }
+  double rz_old = st[4 * l];
+  float2 pv[PCGF_PER], xv[PCGF_PER], rv[PCGF_PER];
+  double qv[PCGF_PER];
+  float pqh = 0.f, pql_ = 0.f;  // p . q, float-float
+#pragma unroll
+  for (int k = 0; k < PCGF_PER; k++) {
+    int e = threadIdx.x + k * PCG_THREADS;
+    if (e < n) { pv[k] = p[o + e]; xv[k] = x[o + e]; rv[k] = r[o + e]; qv[k] = q[o + e]; }
+  }
+#pragma unroll
+  for (int k = 0; k < PCGF_PER; k++) {
+    int e = threadIdx.x + k * PCG_THREADS;
+    if (e < n) {
+      float2 qf = ff_of(qv[k]);
+      float er;
+      float pr = ff_two_prod(pv[k].x, qf.x, er);
+      ff_acc(pqh, pql_, pr);
+      pql_ = __fadd_rn(pql_, __fmaf_rn(pv[k].y, qf.x, __fmaf_rn(pv[k].x, qf.y, er)));
+    }
+  }
+  double pqv[1] = {(double)pqh + (double)pql_}, pqt[1];
+  cta_sum<1>(pqv, pqt);
+  double pql = pqt[0];
+  if (!(pql > 0.0)) {  // breakdown: keep the current iterate
+    if (threadIdx.x == 0) live[l] = 0;
+    return;
+  }
+  double alpha = rz_old / pql;
+  float2 af = ff_of(alpha), naf = make_float2(-af.x, -af.y);
+  float rr = 0.f;
+#pragma unroll
+  for (int k = 0; k < PCGF_PER; k++) {
+    int e = threadIdx.x + k * PCG_THREADS;
+    if (e < n) {
+      x[o + e] = ff_add(xv[k], ff_mul(af, pv[k]));
+      float2 re = ff_add(rv[k], ff_mul(naf, ff_of(qv[k])));
+      r[o + e] = re;
+      rs[e] = re;
+      rr += re.x * re.x;
+    }
+  }
+  __syncthreads();
+  float rzh = 0.f, rzl = 0.f;
+  for (int c = threadIdx.x; c < ncam; c += PCG_THREADS) {
+    if (c != c0) {  // more cameras than threads: load this block too
+      const float4 *Mi = reinterpret_cast<const float4 *>(Minv32 + 36 * (size_t)(g0 + c));
+#pragma unroll
+      for (int k = 0; k < 9; k++) {
+        float4 w = __ldg(Mi + k);
+        m[4 * k] = w.x; m[4 * k + 1] = w.y; m[4 * k + 2] = w.z; m[4 * k + 3] = w.w;
+      }
+    }
+    float rh[6], rl[6];
+#pragma unroll
+    for (int b2 = 0; b2 < 6; b2++) { rh[b2] = rs[6 * c + b2].x; rl[b2] = rs[6 * c + b2].y; }
+#pragma unroll
+    for (int a2 = 0; a2 < 6; a2++) {
+      float t = 0.f;
+#pragma unroll
+      for (int b2 = 0; b2 < 6; b2++) t += m[6 * a2 + b2] * rh[b2];
+      zs[6 * c + a2] = t;
+      float e;
+      float pr = ff_two_prod(rh[a2], t, e);
+      ff_acc(rzh, rzl, pr);
+      rzl = __fadd_rn(rzl, __fmaf_rn(rl[a2], t, e));
+    }
+  }
+  double v[2] = {(double)rr, (double)rzh + (double)rzl}, tot[2];
+  cta_sum<2>(v, tot);  // its barriers also order the z writes before the reads below
+  float2 bf = ff_of(tot[1] / rz_old);
+#pragma unroll
+  for (int k = 0; k < PCGF_PER; k++) {
+    int e = threadIdx.x + k * PCG_THREADS;
+    if (e < n) p[o + e] = ff_add(make_float2(zs[e], 0.f), ff_mul(bf, pv[k]));
+  }
+  if (threadIdx.x == 0) {
+    st[4 * l] = tot[1];
+    double rel = sqrt(tot[0]) / st[4 * l + 1];
+    st[4 * l + 2] = rel;
+    st[4 * l + 3] += 1.0;
+    if (rel <= tol) live[l] = 0;
+  }
+}
+
+// FP32 form: dC = x
+__global__ void k_pcg_out_ff(const int *run, const int *fail, const int *voff, const int *npad, int L,
+                             const float2 *x, double *dC) {
+  int l = blockIdx.y;
+  if (l >= L || !run[l] || fail[l]) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < npad[l]; e += gridDim.x * blockDim.x)
+    dC[voff[l] + e] = ff_to_double(x[voff[l] + e]);
 }
 
 // z = M^-1 r for the cameras of sub-block l (block rows of 6)
@@ -468,6 +727,17 @@ __global__ void k_pcg_live_count(int L, const int *live, int *count) {
 rpba_status pcg_init(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiApply *fsai) {
   int L = ctx->L;
   cudaStream_t st = ctx->stream;
+  if (!fsai && ff_pcg(ctx)) {
+    RPBA_KERNEL(ctx, "k_pcg_init", k_pcg_init_ff<<<L, PCG_THREADS, 0, st>>>(
+                                       run_dev, fail_dev, ctx->sub_cam_ptr, ctx->ycam_off, ctx->npad, ctx->pcg_Minv32,
+                                       ctx->y, ctx->pcg_fx, ctx->pcg_fr, ctx->pcg_fz, ctx->pcg_fp, ctx->pcg_st,
+                                       ctx->pcg_live));
+    if (ctx->pcg_tiles_total)
+      RPBA_KERNEL(ctx, "k_pcg_split", k_pcg_split<<<ctx->pcg_tiles_total, 256, 0, st>>>(
+                                          ctx->S, ctx->S_off, ctx->npad, ctx->pcg_live, ctx->pcg_tiles, L,
+                                          ctx->pcg_Sff));
+    return RPBA_OK;
+  }
   if (fsai) {
     RPBA_KERNEL(ctx, "k_pcg_init_a", k_pcg_init_a<<<L, PCG_THREADS, 0, st>>>(run_dev, fail_dev, ctx->sub_cam_ptr, ctx->ycam_off,
                                                                     ctx->npad, ctx->y, ctx->pcg_x, ctx->pcg_r,
@@ -494,24 +764,34 @@ rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai, int *iters) {
   int maxit = ctx->opt.pcg_max_iter;
   for (int it = 0; it < maxit; it++) {
     RPBA_CUDA(cudaMemsetAsync(ctx->pcg_q, 0, ctx->ytot * sizeof(double), st));
-    RPBA_CUDA(cudaMemsetAsync(ctx->pcg_pq, 0, L * sizeof(double), st));
-    RPBA_KERNEL(ctx, "k_pcg_symv", k_pcg_symv<<<tiles, 256, 0, st>>>(
-                                       ctx->S, ctx->S_off, ctx->npad, ctx->ycam_off, ctx->pcg_live, ctx->pcg_tiles,
-                                       L, ctx->pcg_p, ctx->pcg_q, ctx->pcg_pq));
-    if (fsai) {
-      RPBA_KERNEL(ctx, "k_pcg_alpha", k_pcg_alpha<<<L, PCG_THREADS, 0, st>>>(
-                                          ctx->sub_cam_ptr, ctx->ycam_off, ctx->opt.pcg_tol, ctx->pcg_x, ctx->pcg_r,
-                                          ctx->pcg_p, ctx->pcg_q, ctx->pcg_pq, ctx->pcg_st, ctx->pcg_live,
-                                          fsai->P.Li, fsai->rh));
-      RPBA_TRY(fsai_apply(ctx, *fsai, ctx->pcg_live, ctx->pcg_r, ctx->pcg_z, /*skip_first=*/true));
-      RPBA_KERNEL(ctx, "k_pcg_beta", k_pcg_beta<<<L, PCG_THREADS, 0, st>>>(
-                                         ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p,
-                                         ctx->pcg_st, ctx->pcg_live));
-    } else {
-      RPBA_KERNEL(ctx, "k_pcg_step", k_pcg_step<<<L, PCG_THREADS, 0, st>>>(
-                                         ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_Minv, ctx->opt.pcg_tol, ctx->pcg_x,
-                                         ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, ctx->pcg_q, ctx->pcg_pq, ctx->pcg_st,
+    if (!fsai && ff_pcg(ctx)) {
+      RPBA_KERNEL(ctx, "k_pcg_symv", k_pcg_symv_ff<<<tiles, 256, 0, st>>>(
+                                         ctx->pcg_Sff, ctx->S_off, ctx->npad, ctx->ycam_off, ctx->pcg_live,
+                                         ctx->pcg_tiles, L, ctx->pcg_fp, ctx->pcg_q));
+      RPBA_KERNEL(ctx, "k_pcg_step", k_pcg_step_ff<<<L, PCG_THREADS, ctx->pcg_ff_smem, st>>>(
+                                         ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_Minv32, ctx->opt.pcg_tol,
+                                         ctx->pcg_fx, ctx->pcg_fr, ctx->pcg_fp, ctx->pcg_q, ctx->pcg_st,
                                          ctx->pcg_live));
+    } else {
+      RPBA_CUDA(cudaMemsetAsync(ctx->pcg_pq, 0, L * sizeof(double), st));
+      RPBA_KERNEL(ctx, "k_pcg_symv", k_pcg_symv<<<tiles, 256, 0, st>>>(
+                                         ctx->S, ctx->S_off, ctx->npad, ctx->ycam_off, ctx->pcg_live, ctx->pcg_tiles,
+                                         L, ctx->pcg_p, ctx->pcg_q, ctx->pcg_pq));
+      if (fsai) {
+        RPBA_KERNEL(ctx, "k_pcg_alpha", k_pcg_alpha<<<L, PCG_THREADS, 0, st>>>(
+                                            ctx->sub_cam_ptr, ctx->ycam_off, ctx->opt.pcg_tol, ctx->pcg_x,
+                                            ctx->pcg_r, ctx->pcg_p, ctx->pcg_q, ctx->pcg_pq, ctx->pcg_st,
+                                            ctx->pcg_live, fsai->P.Li, fsai->rh));
+        RPBA_TRY(fsai_apply(ctx, *fsai, ctx->pcg_live, ctx->pcg_r, ctx->pcg_z, /*skip_first=*/true));
+        RPBA_KERNEL(ctx, "k_pcg_beta", k_pcg_beta<<<L, PCG_THREADS, 0, st>>>(
+                                           ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p,
+                                           ctx->pcg_st, ctx->pcg_live));
+      } else {
+        RPBA_KERNEL(ctx, "k_pcg_step", k_pcg_step<<<L, PCG_THREADS, 0, st>>>(
+                                           ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_Minv, ctx->opt.pcg_tol,
+                                           ctx->pcg_x, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, ctx->pcg_q, ctx->pcg_pq,
+                                           ctx->pcg_st, ctx->pcg_live));
+      }
     }
     if ((it & 7) == 7 || it == maxit - 1) {
       RPBA_CUDA(cudaMemsetAsync(ctx->counters + 8, 0, sizeof(int), st));
@@ -529,6 +809,11 @@ rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai, int *iters) {
 
 rpba_status pcg_out(Ctx *ctx, const int *run_dev, const int *fail_dev) {
   int L = ctx->L;
+  if (ff_pcg(ctx)) {
+    RPBA_KERNEL(ctx, "k_pcg_out", k_pcg_out_ff<<<dim3(8, L), 256, 0, ctx->stream>>>(
+                                      run_dev, fail_dev, ctx->ycam_off, ctx->npad, L, ctx->pcg_fx, ctx->dC));
+    return RPBA_OK;
+  }
   RPBA_KERNEL(ctx, "k_pcg_out", k_pcg_out<<<dim3(8, L), 256, 0, ctx->stream>>>(run_dev, fail_dev, ctx->ycam_off,
                                                                               ctx->npad, L, ctx->pcg_x, ctx->dC));
   return RPBA_OK;
@@ -546,7 +831,8 @@ rpba_status pcg_bj_setup(Ctx *ctx, const int *run_dev, int *fail_dev) {
   if (ctx->M)
     RPBA_KERNEL(ctx, "k_pcg_bj_setup", k_pcg_bj_setup<<<nblk(ctx->M, 128), 128, 0, ctx->stream>>>(
                                            ctx->M, ctx->cam_sub, ctx->cam_local, ctx->sub_cam_ptr, run_dev, ctx->S,
-                                           ctx->S_off, ctx->npad, ctx->pcg_Minv, fail_dev));
+                                           ctx->S_off, ctx->npad, ctx->pcg_Minv, fail_dev,
+                                           ff_pcg(ctx) ? ctx->pcg_Minv32 : nullptr));
   return RPBA_OK;
 }
 

@@ -338,6 +338,49 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
         if (la > lb) { pa.push_back(a); pb_.push_back(b); }
       }
   ctx->n_pairs = (long long)pa.size();
+  // FP32 form: the pairs grouped by camera of a, then by camera of b (a
+  // segment per camera pair (i, i')), then by position: camera i owns the
+  // off-diagonal blocks S_{i,i'} with local(i) > local(i'), each the sum over
+  // one segment
+  std::vector<int> spa, spb, spq, sps, seg_cam, seg_nb;
+  if (ctx->opt.precision == 1) {
+    long long np = ctx->n_pairs;
+    std::vector<long long> by_b(np), cnt(M + 1, 0);
+    auto cam_of = [&](int pos) { return pb->obs_cam[order[pos]]; };
+    for (long long e = 0; e < np; e++) cnt[cam_of(pb_[e]) + 1]++;
+    for (int i = 0; i < M; i++) cnt[i + 1] += cnt[i];
+    for (long long e = 0; e < np; e++) by_b[cnt[cam_of(pb_[e])]++] = e;
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (long long e = 0; e < np; e++) cnt[cam_of(pa[e]) + 1]++;
+    for (int i = 0; i < M; i++) cnt[i + 1] += cnt[i];
+    std::vector<long long> srt(np);
+    for (long long t = 0; t < np; t++) {
+      long long e = by_b[t];
+      srt[cnt[cam_of(pa[e])]++] = e;
+    }
+    spa.resize(np);
+    spb.resize(np);
+    spq.resize(np);
+    sps.resize(np);
+    int last_a = -1, last_b = -1;
+    for (long long t = 0; t < np; t++) {
+      long long e = srt[t];
+      spa[t] = pa[e];
+      spb[t] = pb_[e];
+      spq[t] = obs_inst[pa[e]];
+      int ia = cam_of(pa[e]), ib = cam_of(pb_[e]);
+      if (ia != last_a || ib != last_b) {
+        seg_cam.push_back(ia);
+        seg_nb.push_back(ib);
+        last_a = ia;
+        last_b = ib;
+      }
+      sps[t] = (int)seg_cam.size() - 1;
+    }
+    ctx->n_segs = (long long)seg_nb.size();
+    pa.clear(); pa.shrink_to_fit();
+    pb_.clear(); pb_.shrink_to_fit();
+  }
   if (ctx->opt.solver == 3) {
     std::vector<int> oc(K);
     for (int p = 0; p < K; p++) oc[p] = pb->obs_cam[order[p]];
@@ -501,10 +544,21 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
     }
   }
   RPBA_TRY(alloc_n(ctx, &ctx->obs_w, (size_t)K));
-  RPBA_TRY(dev_alloc(ctx, &ctx->NXC, 18 * (size_t)K * rs));
-  RPBA_TRY(dev_alloc(ctx, &ctx->Z, 18 * (size_t)K * rs));
-  RPBA_TRY(upload(ctx, &ctx->pair_a, pa.data(), pa.size()));
-  RPBA_TRY(upload(ctx, &ctx->pair_b, pb_.data(), pb_.size()));
+  if (ctx->opt.precision != 1) {  // the FP32 form keeps the Jacobian blocks in registers
+    RPBA_TRY(dev_alloc(ctx, &ctx->NXC, 18 * (size_t)K * rs));
+    RPBA_TRY(dev_alloc(ctx, &ctx->Z, 18 * (size_t)K * rs));
+  }
+  if (ctx->opt.precision == 1) {
+    RPBA_TRY(upload(ctx, &ctx->spair_a, spa.data(), spa.size()));
+    RPBA_TRY(upload(ctx, &ctx->spair_b, spb.data(), spb.size()));
+    RPBA_TRY(upload(ctx, &ctx->spair_q, spq.data(), spq.size()));
+    RPBA_TRY(upload(ctx, &ctx->spair_seg, sps.data(), sps.size()));
+    RPBA_TRY(upload(ctx, &ctx->seg_cam, seg_cam.data(), seg_cam.size()));
+    RPBA_TRY(upload(ctx, &ctx->seg_nb, seg_nb.data(), seg_nb.size()));
+  } else {
+    RPBA_TRY(upload(ctx, &ctx->pair_a, pa.data(), pa.size()));
+    RPBA_TRY(upload(ctx, &ctx->pair_b, pb_.data(), pb_.size()));
+  }
   RPBA_TRY(alloc_n(ctx, &ctx->S, (size_t)std::max(stot, 1LL)));
   RPBA_TRY(alloc_n(ctx, &ctx->y, (size_t)std::max(yt, 1)));
   RPBA_TRY(alloc_n(ctx, &ctx->dC, (size_t)std::max(yt, 1)));
@@ -525,6 +579,19 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
     RPBA_TRY(alloc_n(ctx, &ctx->pcg_st, 4 * (size_t)std::max(L, 1)));
     RPBA_TRY(alloc_n(ctx, &ctx->pcg_pq, (size_t)std::max(L, 1)));
     RPBA_TRY(alloc_n(ctx, &ctx->pcg_live, (size_t)std::max(L, 1)));
+    int max_n = 0;
+    for (int l = 0; l < L; l++) max_n = std::max(max_n, 6 * (scp[l + 1] - scp[l]));
+    // solver 1 or auto's PCG in the FP32 form: float-float, for sub-blocks of
+    // up to RPBA_PCG_FF_MAX_N unknowns (the step kernel's register batches)
+    if (ctx->opt.precision == 1 && ctx->opt.solver == 1 && max_n <= RPBA_PCG_FF_MAX_N) {
+      ctx->pcg_ff_smem = (size_t)std::max(max_n, 1) * (sizeof(float2) + sizeof(float));
+      RPBA_TRY(alloc_n(ctx, &ctx->pcg_Sff, (size_t)std::max(stot, 1LL)));
+      RPBA_TRY(alloc_n(ctx, &ctx->pcg_fx, (size_t)std::max(yt, 1)));
+      RPBA_TRY(alloc_n(ctx, &ctx->pcg_fr, (size_t)std::max(yt, 1)));
+      RPBA_TRY(alloc_n(ctx, &ctx->pcg_fp, (size_t)std::max(yt, 1)));
+      RPBA_TRY(alloc_n(ctx, &ctx->pcg_fz, (size_t)std::max(yt, 1)));
+      RPBA_TRY(alloc_n(ctx, &ctx->pcg_Minv32, 36 * (size_t)std::max(M, 1)));
+    }
     std::vector<int> pt(L + 1, 0);
     for (int l = 0; l < L; l++) pt[l + 1] = pt[l] + ntiles[l] * (ntiles[l] + 1) / 2;
     ctx->pcg_tiles_total = pt[L];

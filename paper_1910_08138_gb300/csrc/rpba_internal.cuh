@@ -213,6 +213,17 @@ struct Ctx {
   void *NXC = nullptr, *Z = nullptr;  // compute precision, K x 18 each
   // Schur pairs
   int *pair_a = nullptr, *pair_b = nullptr;
+  // FP32 form: Schur pairs sorted by (camera of a, camera of b, a): the two
+  // observation positions, the instance and the segment (camera pair) of each
+  // pair; the two cameras of each segment
+  int *spair_a = nullptr, *spair_b = nullptr, *spair_q = nullptr, *spair_seg = nullptr;
+  int *seg_cam = nullptr, *seg_nb = nullptr;
+  long long n_segs = 0;
+  // FP32 form, block-Jacobi PCG in float-float: the RCS as hi + lo pairs (the
+  // layout of S), the vectors x, r, p as pairs and z in FP32, M^-1 in FP32
+  float2 *pcg_Sff = nullptr, *pcg_fx = nullptr, *pcg_fr = nullptr, *pcg_fp = nullptr;
+  float *pcg_fz = nullptr, *pcg_Minv32 = nullptr;
+  size_t pcg_ff_smem = 0;  // the float-float step's shared memory: r and z of the largest sub-block
   // RCS
   double *S = nullptr, *y = nullptr, *dC = nullptr;  // y, dC: sum of n_pad over l
   long long *S_off = nullptr;
@@ -399,6 +410,12 @@ void build_camera_graph(Ctx *ctx, const std::vector<int> &inst_obs_ptr, const st
 rpba_status pcg_iterate(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiApply *fsai);
 // the phases of pcg_iterate, and the preconditioner set-ups
 rpba_status pcg_init(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiApply *fsai);
+// the FP32 form's block-Jacobi PCG runs in float-float (solver 1, also when
+// chosen by solver 4) when no sub-block has more than RPBA_PCG_FF_MAX_N
+// unknowns (256 threads x 8 elements in registers; r and z, 12 B each, then
+// take at most 24 KB of shared memory)
+#define RPBA_PCG_FF_MAX_N 2048
+inline bool ff_pcg(const Ctx *ctx) { return ctx->pcg_Sff != nullptr && ctx->opt.solver == 1; }
 rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai, int *iters /* lock-step iterations run, nullable */);
 rpba_status pcg_out(Ctx *ctx, const int *run_dev, const int *fail_dev);
 rpba_status pcg_bj_setup(Ctx *ctx, const int *run_dev, int *fail_dev);

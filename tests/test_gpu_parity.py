@@ -366,15 +366,23 @@ def test_auto_solver_choice():
 def test_auto_solver_switches_after_a_slow_pcg_solve():
     """solver 4 keeps PCG while its solves take few lock-step iterations and
     moves to the direct solver after the first LM step whose solve needs more
-    than RPBA_AUTO_PCG_MAX_ITER; the run ends at the direct solver's RMS."""
+    than RPBA_AUTO_PCG_MAX_ITER; after 4 outer iterations the run, like the
+    direct solver's, is within 1e-3 px of the oracle's RMS after 4 (stored by
+    oracle/make_targets.py). A fixed count: on this slowly converging block
+    sigma_0 falls ~1% per outer iteration, so where the 1.01 ratio stops a run
+    turns on last-bit differences and moves its final RMS by more than 1e-3."""
+    import json, os
+    targets = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_targets.json")))
+    target = targets["config4@0.1/outer4"]
     prob = synth.config(4, scale=0.1)
     ctx = rpba.Rpba(prob, precision=1, solver=4, robust=1, robust_from_start=1)
     assert ctx.L <= 64 and ctx.resolved_options().solver == 1
-    rg = ctx.iterate()
+    rg = ctx.iterate(4)
     it, _ = ctx.solver_stats()  # the last PCG pass, the one that switched
     assert it.max() > 48 and ctx.resolved_options().solver == 2
-    r2 = rpba.Rpba(prob, precision=1, solver=2, robust=1, robust_from_start=1).iterate()
-    assert abs(rg["rms"] - r2["rms"]) <= 1e-3, (rg["rms"], r2["rms"])
+    r2 = rpba.Rpba(prob, precision=1, solver=2, robust=1, robust_from_start=1).iterate(4)
+    for r in (rg, r2):
+        assert abs(r["rms"] - target["rms"]) <= 1e-3, (r["rms"], target["rms"])
     few = rpba.Rpba(synth.config(2), precision=1, solver=4, robust=1, robust_from_start=1)
     few.iterate()
     it, _ = few.solver_stats()
