@@ -98,7 +98,39 @@ __device__ __forceinline__ float2 ff_of(double x) {
   return o;
 }
 
-__device__ __forceinline__ double ff_to_double(float2 a) { return (double)a.x + (double)a.y; }
+// Format changes without the FP64 pipe. On this GPU one FP64 instruction,
+// conversions included, holds the SM's FP64 unit for 16 cycles per warp, so
+// kernels that only move values between the two formats become FP64-bound.
+// These build the IEEE-754 bit patterns with integer operations instead.
+
+// float -> double, exact (zero and subnormal floats give a signed zero)
+__device__ __forceinline__ double f2d(float f) {
+  unsigned b = __float_as_uint(f);
+  unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+  unsigned e = (b >> 23) & 0xffu;
+  if (e == 0u) return __longlong_as_double((long long)sign);
+  unsigned long long ed = (e == 0xffu) ? 0x7ffull : (unsigned long long)(e + 1023u - 127u);
+  return __longlong_as_double((long long)(sign | (ed << 52) | ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
+// double -> hi + lo: hi the value truncated to 24 significant bits (exact),
+// lo the remaining 29 bits rounded to float (2^-48 relative in all). Values
+// whose hi or lo would leave the normal float range take the FP64 route.
+__device__ __forceinline__ float2 ff_split_bits(double x) {
+  unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  int e = (int)((u >> 52) & 0x7ffull);
+  if (e == 0) return make_float2(0.f, 0.f);
+  if (e < 949 || e > 1150) return ff_of(x);  // |x| < 2^-74 or >= 2^128 (or inf / NaN)
+  unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+  unsigned long long m = u & 0xfffffffffffffull;
+  float hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29));
+  float scale = __uint_as_float((unsigned)(e - 948) << 23);  // 2^(e - 1075)
+  float lo = __fmul_rn(__uint2float_rn((unsigned)(m & 0x1fffffffull)), scale);
+  return make_float2(hi, sign ? -lo : lo);
+}
+
+// hi + lo -> double: one FP64 add
+__device__ __forceinline__ double ff_to_double(float2 a) { return f2d(a.x) + f2d(a.y); }
 
 // host-side or device-side split of a double into hi + lo
 __host__ __device__ __forceinline__ void ff_split(double x, float &hi, float &lo) {

@@ -157,8 +157,8 @@ __global__ void k_camera_mad(int M, MadIn in, const uint8_t *active, const int *
     int k = cam_obs[p];
     int j = obs_pt[k];
     if (!active[j]) continue;
-    double e0, e1;
-    if constexpr (sizeof(Key) == 4) {
+    Key k0, k1;
+    if constexpr (sizeof(Key) == 4) {  // keys straight from the FP32 components
       float r0, r1;
       ff_residual(in.camff + FF_CAM * (size_t)i, in.Xh + 3 * (size_t)j, in.Xl + 3 * (size_t)j, in.oxy[2 * k],
                   in.oxylo[2 * k], in.oxy[2 * k + 1], in.oxylo[2 * k + 1], r0, r1);
@@ -168,8 +168,8 @@ __global__ void k_camera_mad(int M, MadIn in, const uint8_t *active, const int *
         r0 = a;
         r1 = b;
       }
-      e0 = r0;
-      e1 = r1;
+      k0 = fkey(r0);
+      k1 = fkey(r1);
     } else {
       const double *Ri = in.R + 9 * i, *ti = in.t + 3 * i, *Xj = in.X + 3 * j;
       double f = in.intr[3 * i], cx = in.intr[3 * i + 1], cy = in.intr[3 * i + 2];
@@ -178,17 +178,18 @@ __global__ void k_camera_mad(int M, MadIn in, const uint8_t *active, const int *
       double iz = 1.0 / Xc[2];
       double r0 = f * Xc[0] * iz + cx - in.obs_xy[2 * k];
       double r1 = f * Xc[1] * iz + cy - in.obs_xy[2 * k + 1];
-      e0 = r0;
-      e1 = r1;
+      double e0 = r0, e1 = r1;
       if (has_winv) {  // upper Cholesky factor of C^-1, precomputed: (sqrt(w11), w12/sqrt(w11), sqrt(w22 - w12^2/w11))
         const double *F = in.whiten + 3 * k;
         e0 = F[0] * r0 + F[1] * r1;
         e1 = F[2] * r1;
       }
+      k0 = key_of(e0, Key());
+      k1 = key_of(e1, Key());
     }
     int slot = atomicAdd(&count, 2);
-    sh[slot] = key_of(e0, Key());
-    sh[slot + 1] = key_of(e1, Key());
+    sh[slot] = k0;
+    sh[slot + 1] = k1;
   }
   __syncthreads();
   int n = count;

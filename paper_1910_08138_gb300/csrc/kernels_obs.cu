@@ -350,7 +350,7 @@ __global__ void k_count_active(View v, double *part) {
   block_reduce_store<1>(acc, part + blockIdx.x);
 }
 
-rpba_status launch_sigma0(Ctx *ctx, double *sigma0, double *rms) {
+rpba_status launch_sigma0(Ctx *ctx, double *sigma0, double *rms, long long *n_obs, long long *n_points) {
   View v = make_view(ctx);
   int nb = ctx->red_blocks;
   if (ctx->opt.precision == 1) {
@@ -369,6 +369,8 @@ rpba_status launch_sigma0(Ctx *ctx, double *sigma0, double *rms) {
   if (red < 1.0) red = 1.0;
   if (sigma0) *sigma0 = sqrt(h[0] / red);
   if (rms) *rms = h[3] > 0 ? sqrt(h[2] / (2.0 * h[3])) : 0.0;
+  if (n_obs) *n_obs = (long long)h[1];
+  if (n_points) *n_points = (long long)h[4];
   return RPBA_OK;
 }
 
@@ -466,7 +468,9 @@ __global__ void k_isect_point(View v, int *state, int *iter, const T *part, int 
   }
   bool fail = behind;
   double d[3] = {0, 0, 0};
-  double nd2_img = 0.0;
+  float df[3] = {0.f, 0.f, 0.f};  // FP32 form: the step in FP32
+  double nd2_img = 0.0;           // d^T N d (FP64 re-formation)
+  T nd2T = T(-1);                 // d^T N d in the compute precision (else)
   if (!fail) {
     T inv[6];
     T det = sym3_inv<T>(N, inv);
@@ -479,8 +483,10 @@ __global__ void k_isect_point(View v, int *state, int *iter, const T *part, int 
       fail = !point_normal_fp64(v, j, Nimg, gd);
       double detd = sym3_inv<double>(Nimg, invd);
       fail = fail || !(detd > 0.0) || !(sym3_frob<double>(Nimg) * sym3_frob<double>(invd) <= cond_max);
-      for (int r = 0; r < 3; r++)
+      for (int r = 0; r < 3; r++) {
         d[r] = invd[s3idx(r, 0)] * gd[0] + invd[s3idx(r, 1)] * gd[1] + invd[s3idx(r, 2)] * gd[2];
+        df[r] = (float)d[r];
+      }
       if (px_tol > 0.0) {
         double Nd3[3];
         for (int r = 0; r < 3; r++) Nd3[r] = Nimg[s3idx(r, 0)] * d[0] + Nimg[s3idx(r, 1)] * d[1] + Nimg[s3idx(r, 2)] * d[2];
@@ -489,36 +495,46 @@ __global__ void k_isect_point(View v, int *state, int *iter, const T *part, int 
     } else {
       // the step and its image-space size in the compute precision; only the
       // position update below is FP64
-      fail = !(det > T(0)) || !((double)cond <= cond_max);
+      fail = !(det > T(0)) || !(cond <= (T)cond_max);
       T dT[3];
       for (int r = 0; r < 3; r++) dT[r] = inv[s3idx(r, 0)] * g[0] + inv[s3idx(r, 1)] * g[1] + inv[s3idx(r, 2)] * g[2];
       if (px_tol > 0.0) {
         T Nd3[3];
         for (int r = 0; r < 3; r++) Nd3[r] = N[s3idx(r, 0)] * dT[0] + N[s3idx(r, 1)] * dT[1] + N[s3idx(r, 2)] * dT[2];
-        nd2_img = (double)(dT[0] * Nd3[0] + dT[1] * Nd3[1] + dT[2] * Nd3[2]);
+        nd2T = dT[0] * Nd3[0] + dT[1] * Nd3[1] + dT[2] * Nd3[2];
       }
-      for (int r = 0; r < 3; r++) d[r] = (double)dT[r];
+      if constexpr (sizeof(T) == sizeof(float))
+        for (int r = 0; r < 3; r++) df[r] = (float)dT[r];
+      else
+        for (int r = 0; r < 3; r++) d[r] = (double)dT[r];
     }
   }
   bool conv = false;
   if (!fail) {
-    double Xn[3];
-    for (int r = 0; r < 3; r++) Xn[r] = v.X[3 * j + r] - d[r];
-    for (int r = 0; r < 3; r++) v.X[3 * j + r] = Xn[r];
-    if (v.X_hi)  // FP32 form (also under its FP64 first intersection): the hi + lo mirror
-      for (int r = 0; r < 3; r++) split(Xn[r], v.X_hi[3 * j + r], v.X_lo[3 * j + r]);
     if constexpr (sizeof(T) == sizeof(float)) {
-      float df[3] = {(float)d[0], (float)d[1], (float)d[2]};
-      const float *xh = v.X_hi + 3 * j;
+      // X - d on the hi + lo words in float-float; the FP64 copy from them
+      float *xh = v.X_hi + 3 * j, *xl = v.X_lo + 3 * j;
+      for (int r = 0; r < 3; r++) {
+        float2 xn = ff_add(make_float2(xh[r], xl[r]), make_float2(-df[r], 0.f));
+        xh[r] = xn.x;
+        xl[r] = xn.y;
+        v.X[3 * j + r] = ff_to_double(xn);
+      }
       float nd = sqrtf(df[0] * df[0] + df[1] * df[1] + df[2] * df[2]);
       float nx = sqrtf(xh[0] * xh[0] + xh[1] * xh[1] + xh[2] * xh[2]);
       conv = nd <= (float)tol * (1.f + nx);
     } else {
+      double Xn[3];
+      for (int r = 0; r < 3; r++) Xn[r] = v.X[3 * j + r] - d[r];
+      for (int r = 0; r < 3; r++) v.X[3 * j + r] = Xn[r];
+      if (v.X_hi)  // FP32 form under its FP64 first intersection: the hi + lo mirror
+        for (int r = 0; r < 3; r++) split(Xn[r], v.X_hi[3 * j + r], v.X_lo[3 * j + r]);
       double nd = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
       double nx = sqrt(Xn[0] * Xn[0] + Xn[1] * Xn[1] + Xn[2] * Xn[2]);
       conv = nd <= tol * (1.0 + nx);
     }
-    if (!conv && px_tol > 0.0) conv = nd2_img <= px_tol * px_tol * (double)nobs;
+    if (!conv && px_tol > 0.0)
+      conv = nd2T >= T(0) ? nd2T <= (T)(px_tol * px_tol) * nobs : nd2_img <= px_tol * px_tol * (double)nobs;
   }
   int it = ++iter[j];
   if (!fail && !conv && (it >= max_iter || last)) fail = true;
@@ -537,17 +553,20 @@ __global__ void k_isect_point(View v, int *state, int *iter, const T *part, int 
       int q = v.pt_inst[a];
       const T *o = part + 10 * (size_t)q;
       if constexpr (sizeof(T) == sizeof(float)) {
-        // FP32 form: W^l as the FP64 sum of the other instances' parts. N - N^(l)
-        // in FP32 cancels when the other sub-blocks' observations are
+        // FP32 form: W^l as the float-float sum of the other instances' parts.
+        // N - N^(l) in FP32 cancels when the other sub-blocks' observations are
         // down-weighted (w = 1e-4), and can lose positive semi-definiteness.
-        double W[6] = {0, 0, 0, 0, 0, 0};
+        float Wh[6] = {0, 0, 0, 0, 0, 0}, Wlo[6] = {0, 0, 0, 0, 0, 0};
         for (int b = q0; b < q1; b++) {
           if (b == a) continue;
           const T *ob = part + 10 * (size_t)v.pt_inst[b];
-          for (int e = 0; e < 6; e++) W[e] += (double)ob[e];
+          for (int e = 0; e < 6; e++) ff_acc(Wh[e], Wlo[e], ob[e]);
         }
-        for (int e = 0; e < 6; e++) v.Wl[6 * (size_t)q + e] = tp ? W[e] : 0.0;
-        for (int e = 0; e < 6; e++) v.Wl32[6 * (size_t)q + e] = tp ? (float)W[e] : 0.f;
+        for (int e = 0; e < 6; e++) {
+          float2 w = make_float2(Wh[e], Wlo[e]);
+          v.Wl[6 * (size_t)q + e] = tp ? ff_to_double(w) : 0.0;
+          v.Wl32[6 * (size_t)q + e] = tp ? __fadd_rn(Wh[e], Wlo[e]) : 0.f;
+        }
       } else {
         for (int e = 0; e < 6; e++) v.Wl[6 * (size_t)q + e] = tp ? (double)(N[e] - o[e]) : 0.0;
         if (v.Wl32)
@@ -799,7 +818,7 @@ __global__ void k_obs_cost_f(View v, int trial, const int *run, double *cost) {
     F += W[0] * d[0] * d[0] + W[3] * d[1] * d[1] + W[5] * d[2] * d[2] +
          2.f * (W[1] * d[0] * d[1] + W[2] * d[0] * d[2] + W[4] * d[1] * d[2]);
   }
-  cost[k] = (double)F;
+  cost[k] = f2d(F);
 }
 
 #define SEG_CHUNKS 32
@@ -1176,7 +1195,7 @@ __global__ void __launch_bounds__(SC_THREADS) k_schur_seg(View v, const int *run
 #pragma unroll
   for (int r = 0; r < 6; r++)
 #pragma unroll
-    for (int c = 0; c < 6; c++) atomicAdd(row + (size_t)r * np + c, -(double)acc[6 * r + c]);
+    for (int c = 0; c < 6; c++) atomicAdd(row + (size_t)r * np + c, f2d(-acc[6 * r + c]));
 }
 
 // zero the RCS of running sub-blocks, identity on the padding
@@ -1238,7 +1257,10 @@ __global__ void k_backsub(View v, const int *run, const T *NXC, const T *Ninv, c
   if (!v.active[v.inst_pt[q]]) {
     for (int e = 0; e < 3; e++) Xt[e] = Xq[e];
     if constexpr (sizeof(T) == sizeof(float))
-      for (int e = 0; e < 3; e++) split(Xq[e], v.Xlt_hi[3 * (size_t)q + e], v.Xlt_lo[3 * (size_t)q + e]);
+      for (int e = 0; e < 3; e++) {
+        v.Xlt_hi[3 * (size_t)q + e] = v.Xl_hi[3 * (size_t)q + e];
+        v.Xlt_lo[3 * (size_t)q + e] = v.Xl_lo[3 * (size_t)q + e];
+      }
     return;
   }
   T rhs[3] = {-gX[3 * (size_t)q], -gX[3 * (size_t)q + 1], -gX[3 * (size_t)q + 2]};
@@ -1271,9 +1293,16 @@ __global__ void k_backsub(View v, const int *run, const T *NXC, const T *Ninv, c
   }
   const T *iv = Ninv + 6 * (size_t)q;
   for (int r = 0; r < 3; r++) {
-    double x = Xq[r] + (double)(iv[s3idx(r, 0)] * rhs[0] + iv[s3idx(r, 1)] * rhs[1] + iv[s3idx(r, 2)] * rhs[2]);
-    Xt[r] = x;
-    if constexpr (sizeof(T) == sizeof(float)) split(x, v.Xlt_hi[3 * (size_t)q + r], v.Xlt_lo[3 * (size_t)q + r]);
+    T dx = iv[s3idx(r, 0)] * rhs[0] + iv[s3idx(r, 1)] * rhs[1] + iv[s3idx(r, 2)] * rhs[2];
+    if constexpr (sizeof(T) == sizeof(float)) {
+      // the trial position in float-float from the hi + lo words (one FP64 add for the FP64 copy)
+      float2 xn = ff_add(make_float2(v.Xl_hi[3 * (size_t)q + r], v.Xl_lo[3 * (size_t)q + r]), make_float2(dx, 0.f));
+      v.Xlt_hi[3 * (size_t)q + r] = xn.x;
+      v.Xlt_lo[3 * (size_t)q + r] = xn.y;
+      Xt[r] = ff_to_double(xn);
+    } else {
+      Xt[r] = Xq[r] + dx;
+    }
   }
 }
 

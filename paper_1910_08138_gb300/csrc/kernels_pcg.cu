@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(256) k_pcg_split(const double *S, const long l
   for (int e = threadIdx.x; e < PT * PT; e += blockDim.x) {
     int r = e / PT, c = e - r * PT;
     size_t idx = (size_t)S_off[l] + (size_t)(a * PT + r) * np + b * PT + c;
-    Sff[idx] = ff_of(S[idx]);
+    Sff[idx] = ff_split_bits(S[idx]);
   }
 }
 
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_init_ff(const int *run, con
   const float2 zero = make_float2(0.f, 0.f);
   for (int e = threadIdx.x; e < npad[l]; e += blockDim.x) {  // padding stays zero
     x[o + e] = zero;
-    r[o + e] = e < n ? ff_of(y[o + e]) : zero;
+    r[o + e] = e < n ? ff_split_bits(y[o + e]) : zero;
     z[o + e] = 0.f;
     p[o + e] = zero;
     if (e < n) v[1] += y[o + e] * y[o + e];
@@ -302,19 +302,18 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_step_ff(const int *sub_cam_
     }
   }
   double rz_old = st[4 * l];
-  float2 pv[PCGF_PER], xv[PCGF_PER], rv[PCGF_PER];
-  double qv[PCGF_PER];
+  float2 pv[PCGF_PER], xv[PCGF_PER], rv[PCGF_PER], qv[PCGF_PER];
   float pqh = 0.f, pql_ = 0.f;  // p . q, float-float
 #pragma unroll
   for (int k = 0; k < PCGF_PER; k++) {
     int e = threadIdx.x + k * PCG_THREADS;
-    if (e < n) { pv[k] = p[o + e]; xv[k] = x[o + e]; rv[k] = r[o + e]; qv[k] = q[o + e]; }
+    if (e < n) { pv[k] = p[o + e]; xv[k] = x[o + e]; rv[k] = r[o + e]; qv[k] = ff_split_bits(q[o + e]); }
   }
 #pragma unroll
   for (int k = 0; k < PCGF_PER; k++) {
     int e = threadIdx.x + k * PCG_THREADS;
     if (e < n) {
-      float2 qf = ff_of(qv[k]);
+      float2 qf = qv[k];
       float er;
       float pr = ff_two_prod(pv[k].x, qf.x, er);
       ff_acc(pqh, pql_, pr);
@@ -336,7 +335,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_step_ff(const int *sub_cam_
     int e = threadIdx.x + k * PCG_THREADS;
     if (e < n) {
       x[o + e] = ff_add(xv[k], ff_mul(af, pv[k]));
-      float2 re = ff_add(rv[k], ff_mul(naf, ff_of(qv[k])));
+      float2 re = ff_add(rv[k], ff_mul(naf, qv[k]));
       r[o + e] = re;
       rs[e] = re;
       rr += re.x * re.x;

@@ -1219,17 +1219,11 @@ extern "C" rpba_status rpba_iterate(rpba_ctx *h, int32_t max_outer, rpba_report 
     }
   }
   if (robust_on) RPBA_TRY(launch_eliminate(ctx));
-  RPBA_TRY(launch_sigma0(ctx, &r.sigma0, &r.rms));
-  // counts
-  std::vector<uint8_t> a(ctx->N);
-  if (ctx->N) RPBA_CUDA(cudaMemcpyAsync(a.data(), ctx->active, ctx->N, cudaMemcpyDeviceToHost, ctx->stream));
-  RPBA_TRY(sync(ctx));
-  int na = 0;
-  long long ka = 0;
-  for (int j = 0; j < ctx->N; j++)
-    if (a[j]) { na++; ka += ctx->h_pt_nobs[j]; }
-  r.active_points = na;
-  r.deleted_points = ctx->n_active_start - na;
+  // sigma_0, RMS and the active counts of the final state, all from one reduction
+  long long ka = 0, na = 0;
+  RPBA_TRY(launch_sigma0(ctx, &r.sigma0, &r.rms, &ka, &na));
+  r.active_points = (int)na;
+  r.deleted_points = ctx->n_active_start - (int)na;
   r.active_obs = (int)ka;
   if (rep) *rep = r;
   return RPBA_OK;

@@ -388,7 +388,8 @@ inline rpba_status post_launch(Ctx *ctx, const char *name) {
 // kernels (host launchers), see kernels_*.cu
 rpba_status launch_residuals(Ctx *ctx, double *v_dev /* K x 2, GPU order */);
 rpba_status launch_jacobians(Ctx *ctx, double *Jc_dev, double *Jx_dev);
-rpba_status launch_sigma0(Ctx *ctx, double *sigma0, double *rms);
+rpba_status launch_sigma0(Ctx *ctx, double *sigma0, double *rms, long long *n_obs = nullptr,
+                          long long *n_points = nullptr);
 // Eq. bars for all points (tp_only = 0) or the tie points; fp64 forces the
 // FP64 kernels in the FP32 form
 rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped, bool fp64 = false);
