@@ -304,6 +304,20 @@ rpba_status rpba_profile_select(rpba_ctx *ctx, const char *kernel);
 rpba_status rpba_profile_read(rpba_ctx *ctx, int32_t max_kernels, char *names, double *ms,
                               int64_t *launches, int32_t *n_kernels, int64_t *total_launches);
 
+/* ---- format checks (tests) ----------------------------------------------- */
+
+/* Runs the FP32 form's format changes on the device (default stream) over n
+ * host values: x[e] split into hi[e] + lo[e] (hi: x truncated to 24
+ * significant bits, lo: the remaining bits rounded to float; values below
+ * 2^-74 or at or above 2^128 in magnitude take the FP64 conversion, zeros
+ * give 0 + 0), back[e] = hi[e] + lo[e] summed in FP64, and f[e] widened to
+ * double (fd[e]; subnormal floats give a signed zero). x and f are read
+ * when their outputs are asked for; every output may be NULL. Allocates and
+ * frees its own device buffers. Errors: INVALID_ARG (n < 0, or an output
+ * without its input), OOM, CUDA. */
+rpba_status rpba_check_formats(const double *x, const float *f, int32_t n, float *hi, float *lo, double *back,
+                               double *fd);
+
 /* ---- a variant that allocates no device memory --------------------------- */
 
 /* Largest block rpba_sigma0_noalloc accepts (its fixed scratch: 8192 partial

@@ -1305,6 +1305,49 @@ extern "C" rpba_status rpba_profile_select(rpba_ctx *h, const char *kernel) {
   return RPBA_OK;
 }
 
+__global__ void k_check_formats(const double *x, const float *f, int n, float *hi, float *lo, double *back,
+                                double *fd) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  if (x) {
+    float2 s = ff_split_bits(x[e]);
+    hi[e] = s.x;
+    lo[e] = s.y;
+    back[e] = ff_to_double(s);
+  }
+  if (f) fd[e] = f2d(f[e]);
+}
+
+extern "C" rpba_status rpba_check_formats(const double *x, const float *f, int32_t n, float *hi, float *lo,
+                                          double *back, double *fd) {
+  if (n < 0 || ((hi || lo || back) && !x) || (fd && !f)) return RPBA_ERR_INVALID_ARG;
+  if (n == 0) return RPBA_OK;
+  bool wx = hi || lo || back, wf = fd != nullptr;
+  char *buf = nullptr;
+  size_t nb = (size_t)n * (wx ? 8 + 4 + 4 + 8 : 0) + (size_t)n * (wf ? 4 + 8 : 0);
+  if (cudaMalloc((void **)&buf, nb) != cudaSuccess) return RPBA_ERR_OOM;
+  char *c = buf;
+  auto take = [&](size_t bytes) { char *p = c; c += bytes; return p; };
+  double *dx = wx ? (double *)take(8 * (size_t)n) : nullptr, *dback = wx ? (double *)take(8 * (size_t)n) : nullptr;
+  double *dfd = wf ? (double *)take(8 * (size_t)n) : nullptr;
+  float *dhi = wx ? (float *)take(4 * (size_t)n) : nullptr, *dlo = wx ? (float *)take(4 * (size_t)n) : nullptr;
+  float *df = wf ? (float *)take(4 * (size_t)n) : nullptr;
+  cudaError_t e = cudaSuccess;
+  if (wx && e == cudaSuccess) e = cudaMemcpy(dx, x, 8 * (size_t)n, cudaMemcpyHostToDevice);
+  if (wf && e == cudaSuccess) e = cudaMemcpy(df, f, 4 * (size_t)n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_check_formats<<<nblk(n, 256), 256>>>(dx, df, n, dhi, dlo, dback, dfd);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && hi) e = cudaMemcpy(hi, dhi, 4 * (size_t)n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && lo) e = cudaMemcpy(lo, dlo, 4 * (size_t)n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && back) e = cudaMemcpy(back, dback, 8 * (size_t)n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && fd) e = cudaMemcpy(fd, dfd, 8 * (size_t)n, cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  return e == cudaSuccess ? RPBA_OK : RPBA_ERR_CUDA;
+}
+
 extern "C" rpba_status rpba_get_options(rpba_ctx *h, rpba_options *out) {
   CTX_OR_FAIL;
   if (!out) return RPBA_ERR_INVALID_ARG;

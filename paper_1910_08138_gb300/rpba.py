@@ -132,6 +132,7 @@ def load(build_if_missing: bool = True):
         "rpba_gnn_loss_grad": (C.c_int, [vp, _dp, _fp]),
         "rpba_gnn_train": (C.c_int, [vp, C.c_int32, C.c_float, C.c_uint64, _dp]),
         "rpba_sigma0_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32] + [vp] * 10 + [vp, _dp, _dp, _dp]),
+        "rpba_check_formats": (C.c_int, [_dp, _fp, C.c_int32, _fp, _fp, _dp, _dp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -186,6 +187,21 @@ def rpba_sigma0_noalloc(n_cams, n_points, n_obs, R, t, intr, X, active, obs_cam,
     if st != 0:
         raise RpbaError(st, "rpba_sigma0_noalloc failed")
     return s0.value, rms.value, sums
+
+
+def rpba_check_formats(x, f):
+    """The FP32 form's device format changes: x (float64) -> (hi, lo, hi + lo)
+    and f (float32) -> float64 (rpba_check_formats)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    assert x.size == f.size
+    n = x.size
+    hi, lo = np.zeros(n, np.float32), np.zeros(n, np.float32)
+    back, fd = np.zeros(n), np.zeros(n)
+    st = load().rpba_check_formats(_d(x), _f(f), n, _f(hi), _f(lo), _d(back), _d(fd))
+    if st != 0:
+        raise RpbaError(st, "rpba_check_formats failed")
+    return hi, lo, back, fd
 
 
 def rpba_default_options(**overrides) -> Options:
