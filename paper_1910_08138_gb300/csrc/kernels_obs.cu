@@ -289,9 +289,12 @@ __global__ void k_sum_partials(const double *part, int nb, double *out) {
   block_reduce_store<NV>(acc, out);
 }
 
-// sigma_0 / RMS sums: [sum w v^T W v, n_active_obs, sum |v|^2 (w == 1), n (w == 1)]
+// sigma_0 / RMS sums: [sum w v^T W v, n_active_obs, sum |v|^2 (w == 1), n (w == 1),
+// n_active_points]
 __global__ void k_obs_sigma(View v, double *part) {
-  double acc[4] = {0, 0, 0, 0};
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < v.N; j += gridDim.x * blockDim.x)
+    acc[4] += v.active[j] ? 1.0 : 0.0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < v.K; k += gridDim.x * blockDim.x) {
     int j = v.obs_pt[k];
     if (!v.active[j]) continue;
@@ -312,14 +315,15 @@ __global__ void k_obs_sigma(View v, double *part) {
       acc[3] += 1.0;
     }
   }
-  block_reduce_store<4>(acc, part + 4 * blockIdx.x);
+  block_reduce_store<5>(acc, part + 5 * blockIdx.x);
 }
 
 // FP32 form: the same sums from float-float residuals (Eq. ta) formed in
 // FP32, each thread accumulating float-float (TwoSum), the blocks in FP64
 __global__ void k_obs_sigma_f(View v, double *part) {
   float sh = 0.f, sl = 0.f, rh = 0.f, rl = 0.f;
-  int n1 = 0, n3 = 0;
+  int n1 = 0, n3 = 0, np = 0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < v.N; j += gridDim.x * blockDim.x) np += v.active[j] ? 1 : 0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < v.K; k += gridDim.x * blockDim.x) {
     int j = v.obs_pt[k];
     if (!v.active[j]) continue;
@@ -339,18 +343,13 @@ __global__ void k_obs_sigma_f(View v, double *part) {
       n3++;
     }
   }
-  double acc[4] = {(double)sh + (double)sl, (double)n1, (double)rh + (double)rl, (double)n3};
-  block_reduce_store<4>(acc, part + 4 * blockIdx.x);
+  double acc[5] = {(double)sh + (double)sl, (double)n1, (double)rh + (double)rl, (double)n3, (double)np};
+  block_reduce_store<5>(acc, part + 5 * blockIdx.x);
 }
 
-__global__ void k_count_active(View v, double *part) {
-  double acc[1] = {0};
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < v.N; j += gridDim.x * blockDim.x)
-    acc[0] += v.active[j] ? 1.0 : 0.0;
-  block_reduce_store<1>(acc, part + blockIdx.x);
-}
-
-rpba_status launch_sigma0(Ctx *ctx, double *sigma0, double *rms, long long *n_obs, long long *n_points) {
+// the sigma_0 sums of the current state into pinned host memory (no
+// synchronisation; capturable): 5 doubles at ctx->h_pinned_d
+rpba_status sigma0_launch(Ctx *ctx) {
   View v = make_view(ctx);
   int nb = ctx->red_blocks;
   if (ctx->opt.precision == 1) {
@@ -358,19 +357,28 @@ rpba_status launch_sigma0(Ctx *ctx, double *sigma0, double *rms, long long *n_ob
   } else {
     RPBA_KERNEL(ctx, "k_obs_sigma", k_obs_sigma<<<nb, 256, 0, ctx->stream>>>(v, ctx->red));
   }
-  RPBA_KERNEL(ctx, "k_sum_partials", k_sum_partials<4><<<1, 256, 0, ctx->stream>>>(ctx->red, nb, ctx->red + 4 * nb));
-  RPBA_KERNEL(ctx, "k_count_active", k_count_active<<<nb, 256, 0, ctx->stream>>>(v, ctx->red + 4 * nb + 4));
-  RPBA_KERNEL(ctx, "k_sum_partials", k_sum_partials<1><<<1, 256, 0, ctx->stream>>>(ctx->red + 4 * nb + 4, nb, ctx->red + 5 * nb + 4));
-  double h[6];
-  RPBA_CUDA(cudaMemcpyAsync(h, ctx->red + 4 * nb, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  RPBA_CUDA(cudaMemcpyAsync(h + 4, ctx->red + 5 * nb + 4, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  RPBA_CUDA(cudaStreamSynchronize(ctx->stream));
+  RPBA_KERNEL(ctx, "k_sum_partials", k_sum_partials<5><<<1, 256, 0, ctx->stream>>>(ctx->red, nb, ctx->red + 5 * nb));
+  RPBA_CUDA(cudaMemcpyAsync(ctx->h_pinned_d, ctx->red + 5 * nb, 5 * sizeof(double), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+  return RPBA_OK;
+}
+
+// sigma_0 (Eq. sigma0), RMS and the active counts from the sums of
+// sigma0_launch, after the stream has been synchronised
+void sigma0_finish(const Ctx *ctx, double *sigma0, double *rms, long long *n_obs, long long *n_points) {
+  const double *h = ctx->h_pinned_d;
   double red = 2.0 * h[1] - 6.0 * ctx->M - 3.0 * h[4] + 7.0;
   if (red < 1.0) red = 1.0;
   if (sigma0) *sigma0 = sqrt(h[0] / red);
   if (rms) *rms = h[3] > 0 ? sqrt(h[2] / (2.0 * h[3])) : 0.0;
   if (n_obs) *n_obs = (long long)h[1];
   if (n_points) *n_points = (long long)h[4];
+}
+
+rpba_status launch_sigma0(Ctx *ctx, double *sigma0, double *rms, long long *n_obs, long long *n_points) {
+  RPBA_TRY(sigma0_launch(ctx));
+  RPBA_CUDA(cudaStreamSynchronize(ctx->stream));
+  sigma0_finish(ctx, sigma0, rms, n_obs, n_points);
   return RPBA_OK;
 }
 

@@ -26,6 +26,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "rpba_internal.cuh"
 
 namespace rpba {
@@ -232,7 +234,10 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_init_ff(const int *run, con
                                                              float2 *p, double *st, int *live) {
   int l = blockIdx.x;
   int ok = run[l] && !fail[l];
-  if (threadIdx.x == 0) live[l] = ok;
+  if (threadIdx.x == 0) {
+    live[l] = ok;
+    if (!ok) st[4 * l + 3] = 0.0;  // no iterations in this solve
+  }
   if (!ok) return;
   int g0 = sub_cam_ptr[l], ncam = sub_cam_ptr[l + 1] - g0;
   int n = 6 * ncam, o = voff[l];
@@ -412,7 +417,10 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_init(const int *run, const 
                                                   double *st, int *live) {
   int l = blockIdx.x;
   int ok = run[l] && !fail[l];
-  if (threadIdx.x == 0) live[l] = ok;
+  if (threadIdx.x == 0) {
+    live[l] = ok;
+    if (!ok) st[4 * l + 3] = 0.0;  // no iterations in this solve
+  }
   if (!ok) return;
   int ncam = sub_cam_ptr[l + 1] - sub_cam_ptr[l];
   int n = 6 * ncam;
@@ -450,7 +458,10 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_init_a(const int *run, cons
                                                     double *r, double *z, double *p, double *st, int *live) {
   int l = blockIdx.x;
   int ok = run[l] && !fail[l];
-  if (threadIdx.x == 0) live[l] = ok;
+  if (threadIdx.x == 0) {
+    live[l] = ok;
+    if (!ok) st[4 * l + 3] = 0.0;  // no iterations in this solve
+  }
   if (!ok) return;
   int n = 6 * (sub_cam_ptr[l + 1] - sub_cam_ptr[l]);
   int o = voff[l];
@@ -712,9 +723,12 @@ __global__ void k_pcg_out(const int *run, const int *fail, const int *voff, cons
     dC[voff[l] + e] = x[voff[l] + e];  // padding of x is zero
 }
 
-__global__ void k_pcg_live_count(int L, const int *live, int *count) {
+// count[0] = unconverged sub-blocks, count[1] = the most CG iterations any ran
+__global__ void k_pcg_live_count(int L, const int *live, const double *st, int *count) {
   int l = blockIdx.x * blockDim.x + threadIdx.x;
-  if (l < L && live[l]) atomicAdd(count, 1);
+  if (l >= L) return;
+  if (live[l]) atomicAdd(count, 1);
+  atomicMax(count + 1, (int)st[4 * l + 3]);
 }
 
 // The phases of a PCG solve, with the preconditioner set up by the caller:
@@ -761,6 +775,9 @@ rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai, int *iters) {
   cudaStream_t st = ctx->stream;
   int tiles = ctx->pcg_tiles_total;
   int maxit = ctx->opt.pcg_max_iter;
+  // the first convergence read after as many iterations as the previous solve
+  // took (launches for converged sub-blocks return at once), then every 8
+  int next_check = std::min(maxit, std::max(8, ctx->pcg_pred));
   for (int it = 0; it < maxit; it++) {
     RPBA_CUDA(cudaMemsetAsync(ctx->pcg_q, 0, ctx->ytot * sizeof(double), st));
     if (!fsai && ff_pcg(ctx)) {
@@ -792,15 +809,20 @@ rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai, int *iters) {
                                            ctx->pcg_st, ctx->pcg_live));
       }
     }
-    if ((it & 7) == 7 || it == maxit - 1) {
-      RPBA_CUDA(cudaMemsetAsync(ctx->counters + 8, 0, sizeof(int), st));
+    if (it + 1 == next_check || it == maxit - 1) {
+      RPBA_CUDA(cudaMemsetAsync(ctx->counters + 8, 0, 2 * sizeof(int), st));
       RPBA_KERNEL(ctx, "k_pcg_live_count", k_pcg_live_count<<<nblk(L, 128), 128, 0, st>>>(
-                                               L, ctx->pcg_live, ctx->counters + 8));
-      RPBA_CUDA(cudaMemcpyAsync(ctx->h_pinned_counter + 8, ctx->counters + 8, sizeof(int), cudaMemcpyDeviceToHost,
-                                st));
+                                               L, ctx->pcg_live, ctx->pcg_st, ctx->counters + 8));
+      RPBA_CUDA(cudaMemcpyAsync(ctx->h_pinned_counter + 8, ctx->counters + 8, 2 * sizeof(int),
+                                cudaMemcpyDeviceToHost, st));
       RPBA_CUDA(cudaStreamSynchronize(st));
-      if (iters) *iters = it + 1;
-      if (ctx->h_pinned_counter[8] == 0) break;
+      int ran = ctx->h_pinned_counter[9];  // iterations of the slowest sub-block so far
+      if (iters) *iters = ran;
+      if (ctx->h_pinned_counter[8] == 0) {
+        ctx->pcg_pred = ran;
+        break;
+      }
+      next_check = it + 1 + 8;
     }
   }
   return RPBA_OK;

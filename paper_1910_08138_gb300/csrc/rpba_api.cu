@@ -1037,6 +1037,10 @@ static void free_lm_graphs(Ctx *ctx) {
   free_graph(ctx->lm_graph_pre);
   free_graph(ctx->lm_graph_post);
   ctx->lm_graph = ctx->lm_graph_pre = ctx->lm_graph_post = nullptr;
+  for (GraphRec *&g : ctx->outer_graph) {
+    free_graph(g);
+    g = nullptr;
+  }
 }
 
 // capture fn's launches into a graph (all launch parameters are fixed per
@@ -1144,6 +1148,36 @@ static rpba_status lm_step_run(Ctx *ctx) {
   return RPBA_OK;
 }
 
+// the tail of one outer iteration: exchange, robust weights (when on), TP
+// intersection, TP copies and the sigma_0 sums. Nothing in it needs a host
+// read, so it runs as one captured graph; then the host reads sigma_0.
+static rpba_status outer_tail_body(Ctx *ctx, bool robust) {
+  RPBA_TRY(launch_exchange(ctx));
+  if (robust) RPBA_TRY(launch_robust_weights(ctx, nullptr));
+  RPBA_TRY(launch_intersect(ctx, 1, nullptr));
+  RPBA_TRY(launch_tp_copies(ctx, 1));
+  return sigma0_launch(ctx);
+}
+
+static rpba_status outer_tail(Ctx *ctx, bool robust, double *sigma0) {
+  GraphRec *&g = ctx->outer_graph[robust ? 1 : 0];
+  if (g && (g->with_events != ctx->prof_enabled || g->prof_only != ctx->prof_only)) {
+    free_graph(g);  // timing nodes only while profiling
+    g = nullptr;
+  }
+  if (ctx->use_graphs && !g) RPBA_TRY(capture_graph(ctx, &g, [&] { return outer_tail_body(ctx, robust); }));
+  if (g) {
+    RPBA_CUDA(cudaGraphLaunch(g->exec, ctx->stream));
+    RPBA_TRY(sync(ctx));
+    RPBA_TRY(account(ctx, g));
+  } else {
+    RPBA_TRY(outer_tail_body(ctx, robust));
+    RPBA_TRY(sync(ctx));
+  }
+  sigma0_finish(ctx, sigma0, nullptr, nullptr, nullptr);
+  return RPBA_OK;
+}
+
 // bact of all sub-blocks in lock step; returns LM iterations summed over
 // sub-blocks and the lock-step count
 static rpba_status run_bact(Ctx *ctx, int *inner_total, int *launches) {
@@ -1190,15 +1224,11 @@ extern "C" rpba_status rpba_iterate(rpba_ctx *h, int32_t max_outer, rpba_report 
   bool robust_on = false;
   for (int outer = 0; outer < max_outer; outer++) {
     RPBA_TRY(run_bact(ctx, &r.inner_total, &r.lm_launches));
-    RPBA_TRY(launch_exchange(ctx));
     if (o.robust && o.robust_from_start && !robust_on) {
       robust_on = true;
       r.robust_started_at = r.outer;
     }
-    if (robust_on) RPBA_TRY(launch_robust_weights(ctx, nullptr));
-    RPBA_TRY(launch_intersect(ctx, 1, nullptr));
-    RPBA_TRY(launch_tp_copies(ctx, 1));
-    RPBA_TRY(launch_sigma0(ctx, &s, nullptr));
+    RPBA_TRY(outer_tail(ctx, robust_on, &s));
     if (r.outer < 128) r.sigma0_hist[r.outer] = s;
     r.outer++;
     double ratio = best / (s > 1e-300 ? s : 1e-300);

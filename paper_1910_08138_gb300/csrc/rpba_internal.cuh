@@ -223,7 +223,8 @@ struct Ctx {
   // layout of S), the vectors x, r, p as pairs and z in FP32, M^-1 in FP32
   float2 *pcg_Sff = nullptr, *pcg_fx = nullptr, *pcg_fr = nullptr, *pcg_fp = nullptr;
   float *pcg_fz = nullptr, *pcg_Minv32 = nullptr;
-  size_t pcg_ff_smem = 0;  // the float-float step's shared memory: r and z of the largest sub-block
+  size_t pcg_ff_smem = 0;
+  int pcg_pred = 8;        // CG iterations of the previous solve: the first convergence read  // the float-float step's shared memory: r and z of the largest sub-block
   // RCS
   double *S = nullptr, *y = nullptr, *dC = nullptr;  // y, dC: sum of n_pad over l
   long long *S_off = nullptr;
@@ -275,6 +276,7 @@ struct Ctx {
   GraphRec *capture = nullptr;  // non-null while capturing
   GraphRec *lm_graph = nullptr;
   GraphRec *lm_graph_pre = nullptr, *lm_graph_post = nullptr;  // PCG solvers: around the CG loop
+  GraphRec *outer_graph[2] = {nullptr, nullptr};  // one outer iteration's tail (without / with robust weights)
   bool use_graphs = true;
   cudaStream_t own_stream = nullptr;  // created when the caller passes the legacy default stream
   int *h_pinned_counter = nullptr;
@@ -388,6 +390,10 @@ inline rpba_status post_launch(Ctx *ctx, const char *name) {
 // kernels (host launchers), see kernels_*.cu
 rpba_status launch_residuals(Ctx *ctx, double *v_dev /* K x 2, GPU order */);
 rpba_status launch_jacobians(Ctx *ctx, double *Jc_dev, double *Jx_dev);
+// sigma_0 in two halves: the sums into pinned memory (capturable), and the
+// values from them after a synchronisation
+rpba_status sigma0_launch(Ctx *ctx);
+void sigma0_finish(const Ctx *ctx, double *sigma0, double *rms, long long *n_obs, long long *n_points);
 rpba_status launch_sigma0(Ctx *ctx, double *sigma0, double *rms, long long *n_obs = nullptr,
                           long long *n_points = nullptr);
 // Eq. bars for all points (tp_only = 0) or the tie points; fp64 forces the
