@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(256) k_pcg_symv_ff(const float2 *__restrict__ 
       ff_acc(sh, sl, pr);
       sl = __fadd_rn(sl, __fmaf_rn(m.y, x.x, __fmaf_rn(m.x, x.y, e)));
     }
-    atomicAdd(ql + (col ? b : a) * PT + t, (double)sh + (double)sl);
+    atomicAdd(ql + (col ? b : a) * PT + t, ff_to_double(make_float2(sh, sl)));
   }
 }
 
@@ -278,18 +278,53 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_init_ff(const int *run, con
   }
 }
 
+// float-float sum over a warp (lane 0 holds the result)
+__device__ inline void ff_warp_sum(float &h, float &l) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float oh = __shfl_down_sync(0xffffffffu, h, o), ol = __shfl_down_sync(0xffffffffu, l, o);
+    float e;
+    h = ff_two_sum(h, oh, e);
+    l = __fadd_rn(l, __fadd_rn(e, ol));
+  }
+}
+
+// float-float sums of NV values over the CTA; thread 0 gets the totals (as
+// doubles). sh: [NV][32] float2 scratch
+template <int NV>
+__device__ inline void ff_cta_sum(float (&h)[NV], float (&l)[NV], float2 (*sh)[32], double (&tot)[NV]) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    ff_warp_sum(h[k], l[k]);
+    if (lane == 0) sh[k][wid] = make_float2(h[k], l[k]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int k = 0; k < NV; k++) {
+      float2 t = sh[k][0];
+      for (int w = 1; w < nw; w++) t = ff_add(t, sh[k][w]);
+      tot[k] = ff_to_double(t);
+    }
+}
+
 // FP32 form step: p.Sp = p.q, alpha = rz / p.Sp, x += alpha p, r -= alpha q
-// (float-float), z = M^-1 r (FP32), rz' = r.z, beta = rz' / rz, p = z + beta p. Each thread
-// loads all of its elements at once (up to PCGF_PER) so that each phase waits
-// for one memory latency; r and z pass between the phases in shared memory.
+// (float-float), z = M^-1 r (FP32), rz' = r.z, beta = rz' / rz, p = z + beta p.
+// Each thread loads all of its elements at once (up to PCGF_PER) so that each
+// phase waits for one memory latency; r and z pass between the phases in
+// shared memory. The block sums are float-float and the scalar FP64
+// arithmetic (alpha, beta, the statistics) runs in thread 0 alone: on this GPU
+// one SM's FP64 unit would serialise it across the block.
 #define PCGF_PER 8
-#define RPBA_PCG_FF_MAX_N_ (PCG_THREADS * PCGF_PER)
 __global__ void __launch_bounds__(PCG_THREADS) k_pcg_step_ff(const int *sub_cam_ptr, const int *voff,
                                                              const float *__restrict__ Minv32, double tol,
                                                              float2 *__restrict__ x, float2 *__restrict__ r,
                                                              float2 *__restrict__ p, const double *__restrict__ q,
                                                              double *st, int *live) {
   extern __shared__ float2 rs[];  // r (n), then z as floats (n)
+  __shared__ float2 red[2][32];
+  __shared__ float2 bc;           // broadcast scalar (alpha, then beta) as a pair
+  __shared__ int stop;
   int l = blockIdx.x;
   if (!live[l]) return;
   int g0 = sub_cam_ptr[l], ncam = sub_cam_ptr[l + 1] - g0;
@@ -306,34 +341,33 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_step_ff(const int *sub_cam_
       m[4 * k] = w.x; m[4 * k + 1] = w.y; m[4 * k + 2] = w.z; m[4 * k + 3] = w.w;
     }
   }
-  double rz_old = st[4 * l];
   float2 pv[PCGF_PER], xv[PCGF_PER], rv[PCGF_PER], qv[PCGF_PER];
-  float pqh = 0.f, pql_ = 0.f;  // p . q, float-float
 #pragma unroll
   for (int k = 0; k < PCGF_PER; k++) {
     int e = threadIdx.x + k * PCG_THREADS;
     if (e < n) { pv[k] = p[o + e]; xv[k] = x[o + e]; rv[k] = r[o + e]; qv[k] = ff_split_bits(q[o + e]); }
   }
+  float ph[1] = {0.f}, pl[1] = {0.f};  // p . q
 #pragma unroll
   for (int k = 0; k < PCGF_PER; k++) {
     int e = threadIdx.x + k * PCG_THREADS;
     if (e < n) {
-      float2 qf = qv[k];
       float er;
-      float pr = ff_two_prod(pv[k].x, qf.x, er);
-      ff_acc(pqh, pql_, pr);
-      pql_ = __fadd_rn(pql_, __fmaf_rn(pv[k].y, qf.x, __fmaf_rn(pv[k].x, qf.y, er)));
+      float pr = ff_two_prod(pv[k].x, qv[k].x, er);
+      ff_acc(ph[0], pl[0], pr);
+      pl[0] = __fadd_rn(pl[0], __fmaf_rn(pv[k].y, qv[k].x, __fmaf_rn(pv[k].x, qv[k].y, er)));
     }
   }
-  double pqv[1] = {(double)pqh + (double)pql_}, pqt[1];
-  cta_sum<1>(pqv, pqt);
-  double pql = pqt[0];
-  if (!(pql > 0.0)) {  // breakdown: keep the current iterate
-    if (threadIdx.x == 0) live[l] = 0;
-    return;
+  double pqt[1];
+  ff_cta_sum<1>(ph, pl, red, pqt);
+  if (threadIdx.x == 0) {
+    stop = !(pqt[0] > 0.0);  // breakdown: keep the current iterate
+    if (stop) live[l] = 0;
+    else bc = ff_of(st[4 * l] / pqt[0]);
   }
-  double alpha = rz_old / pql;
-  float2 af = ff_of(alpha), naf = make_float2(-af.x, -af.y);
+  __syncthreads();
+  if (stop) return;
+  float2 af = bc, naf = make_float2(-af.x, -af.y);
   float rr = 0.f;
 #pragma unroll
   for (int k = 0; k < PCGF_PER; k++) {
@@ -347,7 +381,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_step_ff(const int *sub_cam_
     }
   }
   __syncthreads();
-  float rzh = 0.f, rzl = 0.f;
+  float vh[2] = {rr, 0.f}, vl[2] = {0.f, 0.f};  // r.r (FP32 is enough for the test), r.z
   for (int c = threadIdx.x; c < ncam; c += PCG_THREADS) {
     if (c != c0) {  // more cameras than threads: load this block too
       const float4 *Mi = reinterpret_cast<const float4 *>(Minv32 + 36 * (size_t)(g0 + c));
@@ -368,24 +402,26 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_step_ff(const int *sub_cam_
       zs[6 * c + a2] = t;
       float e;
       float pr = ff_two_prod(rh[a2], t, e);
-      ff_acc(rzh, rzl, pr);
-      rzl = __fadd_rn(rzl, __fmaf_rn(rl[a2], t, e));
+      ff_acc(vh[1], vl[1], pr);
+      vl[1] = __fadd_rn(vl[1], __fmaf_rn(rl[a2], t, e));
     }
   }
-  double v[2] = {(double)rr, (double)rzh + (double)rzl}, tot[2];
-  cta_sum<2>(v, tot);  // its barriers also order the z writes before the reads below
-  float2 bf = ff_of(tot[1] / rz_old);
-#pragma unroll
-  for (int k = 0; k < PCGF_PER; k++) {
-    int e = threadIdx.x + k * PCG_THREADS;
-    if (e < n) p[o + e] = ff_add(make_float2(zs[e], 0.f), ff_mul(bf, pv[k]));
-  }
+  double tot[2];
+  ff_cta_sum<2>(vh, vl, red, tot);  // its barrier also orders the z writes before the reads below
   if (threadIdx.x == 0) {
+    bc = ff_of(tot[1] / st[4 * l]);
     st[4 * l] = tot[1];
     double rel = sqrt(tot[0]) / st[4 * l + 1];
     st[4 * l + 2] = rel;
     st[4 * l + 3] += 1.0;
     if (rel <= tol) live[l] = 0;
+  }
+  __syncthreads();
+  float2 bf = bc;
+#pragma unroll
+  for (int k = 0; k < PCGF_PER; k++) {
+    int e = threadIdx.x + k * PCG_THREADS;
+    if (e < n) p[o + e] = ff_add(make_float2(zs[e], 0.f), ff_mul(bf, pv[k]));
   }
 }
 
