@@ -1,9 +1,10 @@
 // kernels_mad.cu -- per-camera robust scale (Sec. 5.3): 1.4826 times the
 // median absolute deviation of the whitened residual components of every
-// observation of the camera. One CTA per camera; the 2 K_i components are
-// sorted in shared memory (bitonic network, padded to a power of two >= 64;
-// the stages with stride < 64 run in registers, one warp per 64-key chunk,
-// with shuffles) and the median is read off. The absolute deviations need no second sort: those of
+// observation of the camera. One CTA per camera, the 2 K_i components in
+// shared memory. FP32 form: the two medians by radix select (below). FP64
+// form: the components are sorted (bitonic network, padded to a power of two
+// >= 64; the stages with stride < 64 run in registers, one warp per 64-key
+// chunk, with shuffles) and the median is read off. The absolute deviations need no second sort: those of
 // the components below the median, read backwards, and those of the
 // components from the median up are two ascending lists, and their median
 // is found by a binary search over the two.
@@ -135,6 +136,93 @@ __device__ static double dev_select(const DevLists<Key> &D, int k) {
   return x > y ? x : y;
 }
 
+// ---- FP32 form: order statistics by radix select instead of a sort ----
+// k-th smallest (0-based) of the 32-bit keys a[0..n): most significant digit
+// first, 8 bits per pass. Each pass histograms the keys that share the digits
+// found so far (lanes with the same bin add once, __match_any_sync), and warp 0
+// finds the bin that holds rank k by a prefix sum over the 256 bins.
+struct SelScratch {
+  unsigned hist[256];
+  int bin, rank;
+  unsigned cnt, minv;
+};
+
+__device__ static unsigned radix_select(const unsigned *a, int n, int k, SelScratch &S) {
+  unsigned prefix = 0, mask = 0;
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) S.hist[b] = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += blockDim.x) {
+      int e = base + threadIdx.x;
+      unsigned x = e < n ? a[e] : 0u;
+      bool in = e < n && (x & mask) == prefix;
+      unsigned bin = in ? (x >> shift) & 255u : 256u;
+      unsigned peers = __match_any_sync(__activemask(), bin);
+      if (in && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicAdd(&S.hist[bin], (unsigned)__popc(peers));
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      int lane = threadIdx.x;
+      unsigned c[8], sum = 0;
+#pragma unroll
+      for (int q = 0; q < 8; q++) { c[q] = S.hist[8 * lane + q]; sum += c[q]; }
+      unsigned incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      unsigned excl = incl - sum;
+      if (excl <= (unsigned)k && (unsigned)k < incl) {
+        unsigned acc = excl;
+        int q = 0;
+        while (acc + c[q] <= (unsigned)k) acc += c[q++];
+        S.bin = 8 * lane + q;
+        S.rank = k - (int)acc;
+      }
+    }
+    __syncthreads();
+    prefix |= (unsigned)S.bin << shift;
+    mask |= 255u << shift;
+    k = S.rank;
+    __syncthreads();  // every thread has read S before the next pass clears it
+  }
+  return prefix;
+}
+
+// the k-th and (k+1)-th smallest keys (k + 1 < n)
+__device__ static void radix_select_pair(const unsigned *a, int n, int k, SelScratch &S, unsigned &v0, unsigned &v1) {
+  v0 = radix_select(a, n, k, S);
+  if (threadIdx.x == 0) { S.cnt = 0; S.minv = 0xffffffffu; }
+  __syncthreads();
+  unsigned le = 0, mn = 0xffffffffu;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    unsigned x = a[e];
+    if (x <= v0) le++;
+    else mn = x < mn ? x : mn;
+  }
+  atomicAdd(&S.cnt, le);
+  atomicMin(&S.minv, mn);
+  __syncthreads();
+  v1 = S.cnt >= (unsigned)(k + 2) ? v0 : S.minv;  // a tie with the k-th, or the next larger key
+  __syncthreads();
+}
+
+__device__ inline float fval(unsigned k) {
+  unsigned u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+  return __uint_as_float(u);
+}
+
+// median of the n keys as hi + lo (the mean of the middle pair for even n, exact)
+__device__ static float2 radix_median(const unsigned *a, int n, SelScratch &S) {
+  if (n & 1) return make_float2(fval(radix_select(a, n, n / 2, S)), 0.f);
+  unsigned v0, v1;
+  radix_select_pair(a, n, n / 2 - 1, S, v0, v1);
+  float e;
+  float h = ff_two_sum(fval(v0), fval(v1), e);
+  return make_float2(0.5f * h, 0.5f * e);  // halving is exact
+}
+
 // inputs of the residuals: FP64 state (FP64 form) or the FP32 form's
 // camera records, points as hi + lo and observations as hi + lo
 struct MadIn {
@@ -200,6 +288,31 @@ __global__ void k_camera_mad(int M, MadIn in, const uint8_t *active, const int *
     }
     return;
   }
+  if constexpr (sizeof(Key) == 4) {
+    // FP32 form: median by radix select; the absolute deviations from it (in
+    // float-float, then FP32) overwrite the keys, and their median is the MAD
+    __shared__ SelScratch S;
+    unsigned *ka = reinterpret_cast<unsigned *>(sh);
+    float2 med = radix_median(ka, n, S);
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      float d = fabsf(__fsub_rn(__fsub_rn(fval(ka[e]), med.x), med.y));
+      ka[e] = __float_as_uint(d);  // non-negative floats order as their bit patterns
+    }
+    __syncthreads();
+    double mad;
+    if (n & 1) {
+      mad = (double)__uint_as_float(radix_select(ka, n, n / 2, S));
+    } else {
+      unsigned v0, v1;
+      radix_select_pair(ka, n, n / 2 - 1, S, v0, v1);
+      mad = 0.5 * ((double)__uint_as_float(v0) + (double)__uint_as_float(v1));
+    }
+    if (threadIdx.x == 0) {
+      sigma[i] = 1.4826 * mad;
+      if (sigma32) sigma32[i] = (float)(1.4826 * mad);
+    }
+    return;
+  }
   int n2 = 64;
   while (n2 < n) n2 <<= 1;
   for (int e = n + threadIdx.x; e < n2; e += blockDim.x) sh[e] = ~Key(0);  // sorts last
@@ -234,6 +347,10 @@ rpba_status launch_camera_scale(Ctx *ctx) {
            ctx->camff, ctx->X_hi, ctx->X_lo, ctx->obs_xy32, ctx->obs_xylo, ctx->obs_whiten32};
   int threads = std::min(1024, std::max(32, n2 / 2));  // one thread per compare-exchange of a pass
   if (f32) {
+    smem = (size_t)std::max(2 * ctx->max_cam_obs, 1) * sizeof(unsigned);  // radix select: no padding
+    // two observations per thread (up to 1024 threads): the residual phase is
+    // a chain of dependent gathers, so it wants many threads in flight
+    threads = std::min(1024, std::max(64, 32 * ((ctx->max_cam_obs + 63) / 64)));  // two observations per thread
     if (smem > 48 * 1024)
       RPBA_CUDA(cudaFuncSetAttribute(k_camera_mad<unsigned>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     RPBA_KERNEL(ctx, "k_camera_mad", k_camera_mad<unsigned><<<ctx->M, threads, smem, ctx->stream>>>(

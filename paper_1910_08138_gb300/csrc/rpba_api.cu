@@ -248,6 +248,38 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
         return RPBA_ERR_INVALID_ARG;
       }
     }
+  // Internal point numbering: points sorted by (sub-block of their first
+  // camera, first camera, id). The observations and point instances follow
+  // the point order inside each sub-block, so neighbouring threads then see
+  // the same cameras and nearby points; with the caller's numbering (often
+  // unrelated to geometry) every observation gathers its camera record and
+  // point words from a random line. Every entry point translates: points and
+  // covariance ids use the caller's numbering, instances the canonical order
+  // (sub-block, caller's point id).
+  std::vector<int> &pperm = ctx->h_pt_perm, &pinv = ctx->h_pt_inv;
+  std::vector<double> Xperm(3 * (size_t)N);
+  std::vector<int32_t> operm(K);
+  rpba_problem pbi = *pb;
+  {
+    std::vector<int> first(N, M);
+    for (int k = 0; k < K; k++) first[pb->obs_point[k]] = std::min(first[pb->obs_point[k]], pb->obs_cam[k]);
+    std::vector<long long> key(N);
+    for (int j = 0; j < N; j++) {
+      long long sub = first[j] < M ? pb->cam_subblock[first[j]] : (1 << 20);
+      key[j] = (sub << 32) | (long long)first[j];
+    }
+    pinv.resize(N);
+    std::iota(pinv.begin(), pinv.end(), 0);
+    std::stable_sort(pinv.begin(), pinv.end(), [&](int a, int b) { return key[a] < key[b]; });
+    pperm.resize(N);
+    for (int n = 0; n < N; n++) pperm[pinv[n]] = n;
+    for (int n = 0; n < N; n++)
+      for (int e = 0; e < 3; e++) Xperm[3 * (size_t)n + e] = pb->points[3 * (size_t)pinv[n] + e];
+    for (int k = 0; k < K; k++) operm[k] = pperm[pb->obs_point[k]];
+    pbi.points = Xperm.data();
+    pbi.obs_point = operm.data();
+    pb = &pbi;
+  }
   // cameras by (sub-block, id)
   std::vector<int> &scp = ctx->h_sub_cam_ptr, &sc = ctx->h_sub_cam;
   scp.assign(L + 1, 0);
@@ -305,6 +337,15 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   ctx->P = P;
   ctx->h_inst_pt = inst_pt;
   ctx->h_inst_sub = inst_sub;
+  {  // canonical instance order: (sub-block, caller's point id)
+    std::vector<int> &canon = ctx->h_inst_canon;
+    canon.resize(P);
+    std::iota(canon.begin(), canon.end(), 0);
+    std::sort(canon.begin(), canon.end(), [&](int a, int b) {
+      if (inst_sub[a] != inst_sub[b]) return inst_sub[a] < inst_sub[b];
+      return pinv[inst_pt[a]] < pinv[inst_pt[b]];
+    });
+  }
   ctx->h_obs_user = order;
   std::vector<int> sip(L + 1, 0);
   for (int q = 0; q < P; q++) sip[inst_sub[q] + 1]++;
@@ -467,6 +508,11 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   RPBA_TRY(upload(ctx, &ctx->X, pb->points, 3 * (size_t)N));
   RPBA_TRY(upload(ctx, &ctx->active, active.data(), (size_t)N));
   RPBA_TRY(upload(ctx, &ctx->pt_inst_ptr, pip.data(), (size_t)N + 1));
+  // index maps of the boundary translation and their scratch (one per-point
+  // or per-instance array at a time)
+  RPBA_TRY(upload(ctx, &ctx->d_pt_inv, ctx->h_pt_inv.data(), (size_t)N));
+  RPBA_TRY(upload(ctx, &ctx->d_inst_canon, ctx->h_inst_canon.data(), (size_t)P));
+  RPBA_TRY(alloc_n(ctx, &ctx->perm_scratch, std::max<size_t>(std::max(3 * (size_t)N, 6 * (size_t)P), 1)));
   RPBA_TRY(upload(ctx, &ctx->pt_inst, pin.data(), (size_t)P));
   RPBA_TRY(upload(ctx, &ctx->inst_pt, inst_pt.data(), (size_t)P));
   RPBA_TRY(upload(ctx, &ctx->inst_sub, inst_sub.data(), (size_t)P));
@@ -736,40 +782,105 @@ extern "C" rpba_status rpba_get_cameras(rpba_ctx *h, double *pose) {
   return sync(ctx);
 }
 
+// rows of width w permuted by an index map: dst[r] = src[map[r]] (gather)
+// or dst[map[r]] = src[r] (scatter)
+template <typename T>
+__global__ void k_permute_rows(long long n, int w, const int *map, const T *src, T *dst, int gather) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * w) return;
+  long long r = e / w;
+  int c = (int)(e - r * w);
+  long long m = map[r];
+  if (gather) dst[r * w + c] = src[m * w + c];
+  else dst[m * w + c] = src[r * w + c];
+}
+
+// host rows (caller's order) -> device array (internal order), through the scratch
+template <typename T>
+static rpba_status rows_in(Ctx *ctx, const T *host, T *dev, long long n, int w, const int *map) {
+  if (n == 0) return RPBA_OK;
+  T *tmp = reinterpret_cast<T *>(ctx->perm_scratch);
+  RPBA_CUDA(cudaMemcpyAsync(tmp, host, (size_t)n * w * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+  RPBA_KERNEL(ctx, "k_permute_rows", (k_permute_rows<T><<<nblk(n * w, 256), 256, 0, ctx->stream>>>(n, w, map, tmp, dev, 1)));
+  return RPBA_OK;
+}
+
+// device array (internal order) -> host rows (caller's order)
+template <typename T>
+static rpba_status rows_out(Ctx *ctx, const T *dev, T *host, long long n, int w, const int *map) {
+  if (n == 0) return RPBA_OK;
+  T *tmp = reinterpret_cast<T *>(ctx->perm_scratch);
+  RPBA_KERNEL(ctx, "k_permute_rows", (k_permute_rows<T><<<nblk(n * w, 256), 256, 0, ctx->stream>>>(n, w, map, dev, tmp, 0)));
+  RPBA_CUDA(cudaMemcpyAsync(host, tmp, (size_t)n * w * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
+  return sync(ctx);
+}
+
+// instance rows: map[c] = internal row of canonical row c.
+// host (canonical) -> device (internal): internal[map[c]] = host[c]
+template <typename T>
+static rpba_status rows_in_scatter(Ctx *ctx, const T *host, T *dev, long long n, int w, const int *map) {
+  if (n == 0) return RPBA_OK;
+  T *tmp = reinterpret_cast<T *>(ctx->perm_scratch);
+  RPBA_CUDA(cudaMemcpyAsync(tmp, host, (size_t)n * w * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+  RPBA_KERNEL(ctx, "k_permute_rows", (k_permute_rows<T><<<nblk(n * w, 256), 256, 0, ctx->stream>>>(n, w, map, tmp, dev, 0)));
+  return RPBA_OK;
+}
+
+// device (internal) -> host (canonical): host[c] = internal[map[c]]
+template <typename T>
+static rpba_status rows_out_gather(Ctx *ctx, const T *dev, T *host, long long n, int w, const int *map) {
+  if (n == 0) return RPBA_OK;
+  T *tmp = reinterpret_cast<T *>(ctx->perm_scratch);
+  RPBA_KERNEL(ctx, "k_permute_rows", (k_permute_rows<T><<<nblk(n * w, 256), 256, 0, ctx->stream>>>(n, w, map, dev, tmp, 1)));
+  RPBA_CUDA(cudaMemcpyAsync(host, tmp, (size_t)n * w * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
+  return sync(ctx);
+}
+
+__global__ void k_to_float32(long long n, const double *a, float *b) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) b[e] = (float)a[e];
+}
+
 extern "C" rpba_status rpba_set_points(rpba_ctx *h, const double *X, const uint8_t *active) {
   CTX_OR_FAIL;
-  if (X) RPBA_CUDA(cudaMemcpyAsync(ctx->X, X, 3 * (size_t)ctx->N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-  if (active) RPBA_CUDA(cudaMemcpyAsync(ctx->active, active, (size_t)ctx->N, cudaMemcpyHostToDevice, ctx->stream));
+  if (X) RPBA_TRY(rows_in(ctx, X, ctx->X, ctx->N, 3, ctx->d_pt_inv));
+  if (active) RPBA_TRY(rows_in(ctx, active, ctx->active, ctx->N, 1, ctx->d_pt_inv));
   RPBA_TRY(sync_mirrors(ctx));
   return sync(ctx);
 }
 
 extern "C" rpba_status rpba_get_points(rpba_ctx *h, double *X, uint8_t *active) {
   CTX_OR_FAIL;
-  if (X) RPBA_CUDA(cudaMemcpyAsync(X, ctx->X, 3 * (size_t)ctx->N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  if (active) RPBA_CUDA(cudaMemcpyAsync(active, ctx->active, (size_t)ctx->N, cudaMemcpyDeviceToHost, ctx->stream));
+  if (X) RPBA_TRY(rows_out(ctx, ctx->X, X, ctx->N, 3, ctx->d_pt_inv));
+  if (active) RPBA_TRY(rows_out(ctx, ctx->active, active, ctx->N, 1, ctx->d_pt_inv));
   return sync(ctx);
 }
 
+// instances leave and enter in the canonical order (sub-block, caller's point id)
 extern "C" rpba_status rpba_get_instances(rpba_ctx *h, int32_t *ip, int32_t *is, double *Xl, double *Wl) {
   CTX_OR_FAIL;
-  if (ip) std::copy(ctx->h_inst_pt.begin(), ctx->h_inst_pt.end(), ip);
-  if (is) std::copy(ctx->h_inst_sub.begin(), ctx->h_inst_sub.end(), is);
-  if (Xl) RPBA_CUDA(cudaMemcpyAsync(Xl, ctx->Xl, 3 * (size_t)ctx->P * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  if (Wl) RPBA_CUDA(cudaMemcpyAsync(Wl, ctx->Wl, 6 * (size_t)ctx->P * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  const std::vector<int> &canon = ctx->h_inst_canon;
+  for (size_t c = 0; c < (size_t)ctx->P; c++) {
+    int q = canon[c];
+    if (ip) ip[c] = ctx->h_pt_inv[ctx->h_inst_pt[q]];
+    if (is) is[c] = ctx->h_inst_sub[q];
+  }
+  // canonical c <- internal canon[c]: the caller's order is the canonical one
+  if (Xl) RPBA_TRY(rows_out_gather(ctx, ctx->Xl, Xl, ctx->P, 3, ctx->d_inst_canon));
+  if (Wl) RPBA_TRY(rows_out_gather(ctx, ctx->Wl, Wl, ctx->P, 6, ctx->d_inst_canon));
   return sync(ctx);
 }
 
 extern "C" rpba_status rpba_set_instances(rpba_ctx *h, const double *Xl, const double *Wl) {
   CTX_OR_FAIL;
-  if (Xl) RPBA_CUDA(cudaMemcpyAsync(ctx->Xl, Xl, 3 * (size_t)ctx->P * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-  if (Wl) RPBA_CUDA(cudaMemcpyAsync(ctx->Wl, Wl, 6 * (size_t)ctx->P * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-  RPBA_TRY(sync_mirrors(ctx));
-  if (Wl && ctx->Wl32 && ctx->P) {
-    std::vector<float> w32(Wl, Wl + 6 * (size_t)ctx->P);
-    RPBA_CUDA(cudaMemcpyAsync(ctx->Wl32, w32.data(), w32.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-    return sync(ctx);  // before w32 goes
+  if (Xl) RPBA_TRY(rows_in_scatter(ctx, Xl, ctx->Xl, ctx->P, 3, ctx->d_inst_canon));
+  if (Wl) {
+    RPBA_TRY(rows_in_scatter(ctx, Wl, ctx->Wl, ctx->P, 6, ctx->d_inst_canon));
+    if (ctx->Wl32 && ctx->P)
+      RPBA_KERNEL(ctx, "k_to_float32", k_to_float32<<<nblk(6LL * ctx->P, 256), 256, 0, ctx->stream>>>(
+                                           6LL * ctx->P, ctx->Wl, ctx->Wl32));
   }
+  RPBA_TRY(sync_mirrors(ctx));
   return sync(ctx);
 }
 
@@ -867,13 +978,18 @@ extern "C" rpba_status rpba_covariance(rpba_ctx *h, const int32_t *ids, int32_t 
   Tmp di(ctx), dout(ctx);
   RPBA_TRY(di.alloc((size_t)n * sizeof(int)));
   RPBA_TRY(dout.alloc(9 * (size_t)n * sizeof(double)));
-  RPBA_CUDA(cudaMemcpyAsync(di.p, ids, n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  std::vector<int> idi(n);  // the internal numbering of the points asked for
+  for (int e = 0; e < n; e++) {
+    if (ids[e] < 0 || ids[e] >= ctx->N) { ctx->err = "point id out of range"; return RPBA_ERR_INVALID_ARG; }
+    idi[e] = ctx->h_pt_perm[ids[e]];
+  }
+  RPBA_CUDA(cudaMemcpyAsync(di.p, idi.data(), n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
   RPBA_KERNEL(ctx, "k_covariance", k_covariance<<<nblk(n, 128), 128, 0, ctx->stream>>>(n, (const int *)di.p, ctx->R, ctx->t, ctx->intr, ctx->X,
                                                      ctx->active, ctx->pt_inst_ptr, ctx->pt_inst, ctx->inst_obs_ptr,
                                                      ctx->obs_cam, ctx->obs_winv, ctx->has_winv, ctx->obs_w, ctx->N,
                                                      (double *)dout.p));
   RPBA_CUDA(cudaMemcpyAsync(out9, dout.p, 9 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  return sync(ctx);
+  return sync(ctx);  // before idi goes
 }
 
 extern "C" rpba_status rpba_sub_costs(rpba_ctx *h, double *F) {
@@ -958,8 +1074,11 @@ extern "C" rpba_status rpba_lm_step(rpba_ctx *h, double lambda, int32_t *accepte
       yo += ctx->h_npad[l];
     }
   }
-  if (dx)
-    for (size_t e = 0; e < Xl.size(); e++) dx[e] = Xlt[e] - Xl[e];
+  if (dx)  // instances in the canonical order
+    for (size_t c = 0; c < (size_t)ctx->P; c++) {
+      size_t q = ctx->h_inst_canon[c];
+      for (int e = 0; e < 3; e++) dx[3 * c + e] = Xlt[3 * q + e] - Xl[3 * q + e];
+    }
   std::vector<int> accp(L);
   for (int l = 0; l < L; l++) accp[l] = acc[l] == 1;
   RPBA_CUDA(cudaMemcpyAsync(ctx->lm_acc, accp.data(), L * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));

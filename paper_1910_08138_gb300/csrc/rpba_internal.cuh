@@ -182,6 +182,11 @@ struct Ctx {
   std::vector<int> h_inst_pt, h_inst_sub;
   std::vector<int> h_obs_user;      // K: GPU position -> user index
   std::vector<int> h_pt_nobs;       // N: observations per point
+  // internal point numbering (see build): caller's id -> internal, and back;
+  // canonical instance order (sub-block, caller's id) -> internal instance
+  std::vector<int> h_pt_perm, h_pt_inv, h_inst_canon;
+  int *d_pt_inv = nullptr, *d_inst_canon = nullptr;  // the same maps on the device
+  double *perm_scratch = nullptr;                      // one per-point or per-instance array
   int n_active_start = 0;
   std::vector<long long> h_S_off;   // L: offset (doubles) of the RCS of l
   std::vector<int> h_npad;          // L: padded RCS size
