@@ -797,13 +797,10 @@ __global__ void k_obs_cost(View v, int trial, const int *run, double *cost) {
 // FP32 form: the observation's term from its float-float residual, formed
 // in FP32 and stored in FP64 for the FP64 sum; the TP control term from the
 // float-float difference X^l - X_TP and W^l in FP32
-__global__ void k_obs_cost_f(View v, int trial, const int *run, double *cost) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= v.K) return;
+__device__ inline float obs_cost_term_f(const View &v, int trial, int k) {
   int q = v.obs_inst[k];
-  int l = v.inst_sub[q];
   int j = v.inst_pt[q];
-  if ((run && !run[l]) || !v.active[j]) { cost[k] = 0.0; return; }
+  if (!v.active[j]) return 0.f;
   int i = v.obs_cam[k];
   const float *cf = (trial ? v.camff_t : v.camff) + FF_CAM * (size_t)i;
   const float *Xh = (trial ? v.Xlt_hi : v.Xl_hi) + 3 * (size_t)q;
@@ -826,7 +823,44 @@ __global__ void k_obs_cost_f(View v, int trial, const int *run, double *cost) {
     F += W[0] * d[0] * d[0] + W[3] * d[1] * d[1] + W[5] * d[2] * d[2] +
          2.f * (W[1] * d[0] * d[1] + W[2] * d[0] * d[2] + W[4] * d[1] * d[2]);
   }
-  cost[k] = f2d(F);
+  return F;
+}
+
+// FP32 form, F_l in two deterministic stages without a per-observation array:
+// one CTA per chunk (<= 256 observations of one sub-block, one per thread)
+// writes its sum, then one CTA per sub-block adds its chunks' sums in order
+__global__ void __launch_bounds__(256) k_cost_chunks_f(View v, int trial, const int *run, const int *chunk_sub,
+                                                       const int *chunk_start, const int *sub_obs_ptr, double *part) {
+  __shared__ float2 ws[8];
+  int c = blockIdx.x, l = chunk_sub[c];
+  if (run && !run[l]) return;
+  int k = chunk_start[c] + threadIdx.x;
+  float F = k < sub_obs_ptr[l + 1] ? obs_cost_term_f(v, trial, k) : 0.f;
+  // a point behind its camera makes the sum +inf (TwoSum would turn it into NaN)
+  int any_inf = __syncthreads_or(isinf(F));
+  float h = any_inf ? 0.f : F, lo = 0.f;  // float-float sum: off the FP64 pipe
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float oh = __shfl_down_sync(0xffffffffu, h, o), ol = __shfl_down_sync(0xffffffffu, lo, o);
+    float e;
+    h = ff_two_sum(h, oh, e);
+    lo = __fadd_rn(lo, __fadd_rn(e, ol));
+  }
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = make_float2(h, lo);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float2 t = ws[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) t = ff_add(t, ws[w]);
+    part[c] = any_inf ? (double)INFINITY : ff_to_double(t);
+  }
+}
+
+__global__ void k_cost_sub_f(int L, const int *run, const int *sub_chunk_ptr, const double *part, double *F) {
+  int l = blockIdx.x;
+  if (l >= L || (run && !run[l])) return;
+  double acc[1] = {0.0};
+  for (int c = sub_chunk_ptr[l] + threadIdx.x; c < sub_chunk_ptr[l + 1]; c += blockDim.x) acc[0] += part[c];
+  block_reduce_store<1>(acc, F + l);
 }
 
 #define SEG_CHUNKS 32
@@ -858,9 +892,17 @@ __global__ void k_seg_final(int L, const int *run, const double *part, double *F
 // (~1e-10 px), with each term then formed in FP32 and all sums in FP64.
 static rpba_status sub_costs_impl(Ctx *ctx, int trial, const int *run, double *F_dev) {
   View v = make_view(ctx);
-  if (ctx->K && ctx->opt.precision == 1) {
-    RPBA_KERNEL(ctx, "k_obs_cost", k_obs_cost_f<<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(v, trial, run, ctx->obs_cost));
-  } else if (ctx->K) {
+  if (ctx->opt.precision == 1) {
+    if (ctx->n_chunks)
+      RPBA_KERNEL(ctx, "k_obs_cost", k_cost_chunks_f<<<ctx->n_chunks, 256, 0, ctx->stream>>>(
+                                         v, trial, run, ctx->chunk_sub, ctx->chunk_start, ctx->sub_obs_ptr,
+                                         ctx->chunk_part));
+    if (ctx->L)
+      RPBA_KERNEL(ctx, "k_cost_sub", k_cost_sub_f<<<ctx->L, 256, 0, ctx->stream>>>(ctx->L, run, ctx->sub_chunk_ptr,
+                                                                                   ctx->chunk_part, F_dev));
+    return RPBA_OK;
+  }
+  if (ctx->K) {
     RPBA_KERNEL(ctx, "k_obs_cost", k_obs_cost<<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(v, trial, run, ctx->obs_cost));
   }
   RPBA_KERNEL(ctx, "k_seg_partial", k_seg_partial<<<dim3(SEG_CHUNKS, ctx->L), 256, 0, ctx->stream>>>(

@@ -522,6 +522,18 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
     std::vector<int> sop(L + 1);
     for (int l = 0; l <= L; l++) sop[l] = inst_obs_ptr[sip[l]];
     RPBA_TRY(upload(ctx, &ctx->sub_obs_ptr, sop.data(), (size_t)L + 1));
+    // chunks of at most 256 observations that never straddle two sub-blocks
+    // (the sub-block cost: one CTA per chunk, one thread per observation)
+    std::vector<int> cs, cst, cp(L + 1, 0);
+    for (int l = 0; l < L; l++) {
+      for (int k = sop[l]; k < sop[l + 1]; k += 256) { cs.push_back(l); cst.push_back(k); }
+      cp[l + 1] = (int)cs.size();
+    }
+    ctx->n_chunks = (int)cs.size();
+    RPBA_TRY(upload(ctx, &ctx->chunk_sub, cs.data(), cs.size()));
+    RPBA_TRY(upload(ctx, &ctx->chunk_start, cst.data(), cst.size()));
+    RPBA_TRY(upload(ctx, &ctx->sub_chunk_ptr, cp.data(), cp.size()));
+    RPBA_TRY(alloc_n(ctx, &ctx->chunk_part, (size_t)std::max(ctx->n_chunks, 1)));
   }
   RPBA_TRY(alloc_n(ctx, &ctx->obs_cost, (size_t)K));
   if (ctx->opt.precision == 1) {
@@ -663,7 +675,14 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   RPBA_TRY(alloc_n(ctx, &ctx->lm_run, (size_t)L));
   RPBA_TRY(alloc_n(ctx, &ctx->lm_acc, (size_t)L));
   RPBA_TRY(alloc_n(ctx, &ctx->lm_cholfail, (size_t)L));
-  ctx->red_blocks = 304;
+  {  // grid-stride reductions (sigma_0): ~8 observations per thread, at most
+     // 8 CTAs of 256 threads per SM
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0)
+      sms = 152;
+    ctx->red_blocks = (int)std::max(1LL, std::min<long long>(8LL * sms, ((long long)K + 2047) / 2048));
+  }
   RPBA_TRY(alloc_n(ctx, &ctx->red, (size_t)ctx->red_blocks * 6 + 16));
   RPBA_TRY(alloc_n(ctx, &ctx->counters, 16));
   RPBA_CUDA(cudaMallocHost((void **)&ctx->h_pinned_counter, 16 * sizeof(int)));

@@ -252,6 +252,11 @@ struct Ctx {
   float *camff = nullptr, *camff_t = nullptr, *obs_xylo = nullptr, *Xlt_hi = nullptr, *Xlt_lo = nullptr,
         *Wl32 = nullptr, *obs_whiten32 = nullptr, *cam_sigma32 = nullptr;
   int *sub_obs_ptr = nullptr;
+  // chunks of <= 256 observations inside one sub-block: sub-block, first
+  // observation, chunks per sub-block (CSR), one partial cost per chunk
+  int *chunk_sub = nullptr, *chunk_start = nullptr, *sub_chunk_ptr = nullptr;
+  int n_chunks = 0;
+  double *chunk_part = nullptr;
   std::vector<int> h_sched;  // per factorisation step: prefix sums of panel and update tiles
   int *sched = nullptr;
   double *Linv64 = nullptr;
