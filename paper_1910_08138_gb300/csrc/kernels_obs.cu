@@ -584,6 +584,138 @@ __global__ void k_isect_point(View v, int *state, int *iter, const T *part, int 
   }
 }
 
+// FP32 form, one Gauss-Newton iteration of Eq. bars in one kernel, one thread
+// per running point: N_j and g_j over all the point's observations at the
+// current X_j (hi + lo), the FP32 solve with the same checks, FP64
+// re-formation and convergence tests as k_isect_point, the position update
+// in float-float. On convergence the refined weights W^l = N_j - N_j^(l):
+// N_j is also summed in float-float, each instance's part N_j^(l) formed again
+// from its observations, and the difference taken in float-float (the FP32
+// difference would cancel when the other sub-blocks' observations are
+// down-weighted).
+__device__ inline void isect_obs_acc(const View &v, int j, int k, float N[6], float g[3], bool &behind) {
+  ProjJac<float> pj;
+  float z;
+  obs_proj<float>(v, v.obs_cam[k], nullptr, v.X_hi + 3 * (size_t)j, v.X_lo + 3 * (size_t)j, pj, z);
+  if (!(z > 0.f)) { behind = true; return; }
+  ObsT<float> ob;
+  load_obs<float>(v, k, ob);
+  float r0 = pj.u - ob.x, r1 = pj.v - ob.y, a0[3], a1[3];
+  for (int c = 0; c < 3; c++) {
+    a0[c] = ob.w * (ob.W[0] * pj.Jx[c] + ob.W[1] * pj.Jx[3 + c]);
+    a1[c] = ob.w * (ob.W[1] * pj.Jx[c] + ob.W[2] * pj.Jx[3 + c]);
+  }
+  for (int r = 0; r < 3; r++) {
+    for (int c = r; c < 3; c++) N[s3idx(r, c)] += pj.Jx[r] * a0[c] + pj.Jx[3 + r] * a1[c];
+    g[r] += a0[r] * r0 + a1[r] * r1;
+  }
+}
+
+__global__ void k_isect_fused_f(View v, int *state, int *iter, int max_iter, double tol, double px_tol,
+                                double cond_max, int last) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= v.N || state[j] != 1) return;
+  int q0 = v.pt_inst_ptr[j], q1 = v.pt_inst_ptr[j + 1];
+  float N[6] = {0, 0, 0, 0, 0, 0}, g[3] = {0, 0, 0};
+  float Nh[6] = {0, 0, 0, 0, 0, 0}, Nl[6] = {0, 0, 0, 0, 0, 0};  // N_j in float-float
+  bool behind = false;
+  float nobs = 0.f;
+  for (int a = q0; a < q1; a++) {
+    int q = v.pt_inst[a];
+    float Nq[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = v.inst_obs_ptr[q]; k < v.inst_obs_ptr[q + 1]; k++) isect_obs_acc(v, j, k, Nq, g, behind);
+    for (int e = 0; e < 6; e++) { N[e] += Nq[e]; ff_acc(Nh[e], Nl[e], Nq[e]); }
+    nobs += (float)(v.inst_obs_ptr[q + 1] - v.inst_obs_ptr[q]);
+  }
+  bool fail = behind;
+  float df[3] = {0.f, 0.f, 0.f};
+  float nd2 = -1.f;        // d^T N d (FP32 solve)
+  double nd2_img = 0.0;    // d^T N d (FP64 re-formation)
+  if (!fail) {
+    float inv[6];
+    float det = sym3_inv<float>(N, inv);
+    float cond = sym3_frob<float>(N) * sym3_frob<float>(inv);
+    if (!(cond <= 1e6f)) {
+      double Nimg[6], gd[3], invd[6];
+      fail = !point_normal_fp64(v, j, Nimg, gd);
+      double detd = sym3_inv<double>(Nimg, invd);
+      fail = fail || !(detd > 0.0) || !(sym3_frob<double>(Nimg) * sym3_frob<double>(invd) <= cond_max);
+      double d[3];
+      for (int r = 0; r < 3; r++) {
+        d[r] = invd[s3idx(r, 0)] * gd[0] + invd[s3idx(r, 1)] * gd[1] + invd[s3idx(r, 2)] * gd[2];
+        df[r] = (float)d[r];
+      }
+      if (px_tol > 0.0) {
+        double Nd3[3];
+        for (int r = 0; r < 3; r++) Nd3[r] = Nimg[s3idx(r, 0)] * d[0] + Nimg[s3idx(r, 1)] * d[1] + Nimg[s3idx(r, 2)] * d[2];
+        nd2_img = d[0] * Nd3[0] + d[1] * Nd3[1] + d[2] * Nd3[2];
+      }
+    } else {
+      fail = !(det > 0.f) || !(cond <= (float)cond_max);
+      for (int r = 0; r < 3; r++) df[r] = inv[s3idx(r, 0)] * g[0] + inv[s3idx(r, 1)] * g[1] + inv[s3idx(r, 2)] * g[2];
+      if (px_tol > 0.0) {
+        float Nd3[3];
+        for (int r = 0; r < 3; r++) Nd3[r] = N[s3idx(r, 0)] * df[0] + N[s3idx(r, 1)] * df[1] + N[s3idx(r, 2)] * df[2];
+        nd2 = df[0] * Nd3[0] + df[1] * Nd3[1] + df[2] * Nd3[2];
+      }
+    }
+  }
+  bool conv = false;
+  if (!fail) {
+    float *xh = v.X_hi + 3 * (size_t)j, *xl = v.X_lo + 3 * (size_t)j;
+    for (int r = 0; r < 3; r++) {
+      float2 xn = ff_add(make_float2(xh[r], xl[r]), make_float2(-df[r], 0.f));
+      xh[r] = xn.x;
+      xl[r] = xn.y;
+      v.X[3 * (size_t)j + r] = ff_to_double(xn);
+    }
+    float nd = sqrtf(df[0] * df[0] + df[1] * df[1] + df[2] * df[2]);
+    float nx = sqrtf(xh[0] * xh[0] + xh[1] * xh[1] + xh[2] * xh[2]);
+    conv = nd <= (float)tol * (1.f + nx);
+    if (!conv && px_tol > 0.0)
+      conv = nd2 >= 0.f ? nd2 <= (float)(px_tol * px_tol) * nobs : nd2_img <= px_tol * px_tol * (double)nobs;
+  }
+  int it = ++iter[j];
+  if (!fail && !conv && (it >= max_iter || last)) fail = true;
+  if (fail) {
+    state[j] = 3;
+    v.active[j] = 0;
+    for (int a = q0; a < q1; a++)
+      for (int e = 0; e < 6; e++) {
+        v.Wl[6 * (size_t)v.pt_inst[a] + e] = 0.0;
+        v.Wl32[6 * (size_t)v.pt_inst[a] + e] = 0.f;
+      }
+  } else if (conv) {
+    state[j] = 2;
+    bool tp = (q1 - q0) >= 2;
+    for (int a = q0; a < q1; a++) {
+      int q = v.pt_inst[a];
+      if (!tp) {
+        for (int e = 0; e < 6; e++) { v.Wl[6 * (size_t)q + e] = 0.0; v.Wl32[6 * (size_t)q + e] = 0.f; }
+        continue;
+      }
+      // this instance's part at the same (pre-step) X: the hi/lo words moved,
+      // so re-form it from the position before the update
+      float Nq[6] = {0, 0, 0, 0, 0, 0}, gq[3] = {0, 0, 0};
+      bool bq = false;
+      float *xh = v.X_hi + 3 * (size_t)j, *xl = v.X_lo + 3 * (size_t)j;
+      float sh[3], sl[3];
+      for (int r = 0; r < 3; r++) {
+        sh[r] = xh[r]; sl[r] = xl[r];
+        float2 xo = ff_add(make_float2(xh[r], xl[r]), make_float2(df[r], 0.f));
+        xh[r] = xo.x; xl[r] = xo.y;
+      }
+      for (int k = v.inst_obs_ptr[q]; k < v.inst_obs_ptr[q + 1]; k++) isect_obs_acc(v, j, k, Nq, gq, bq);
+      for (int r = 0; r < 3; r++) { xh[r] = sh[r]; xl[r] = sl[r]; }
+      for (int e = 0; e < 6; e++) {
+        float2 w = ff_add(make_float2(Nh[e], Nl[e]), make_float2(-Nq[e], 0.f));
+        v.Wl[6 * (size_t)q + e] = ff_to_double(w);
+        v.Wl32[6 * (size_t)q + e] = __fadd_rn(w.x, w.y);
+      }
+    }
+  }
+}
+
 __global__ void k_isect_start(View v, int *state, int *iter, int tp_only, int *count) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= v.N) return;
@@ -612,11 +744,8 @@ rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped, bool fp64) {
   double px_tol = ctx->opt.isect_px_tol;
   for (int it = 0; it < maxit; it++) {
     if (ctx->opt.precision == 1 && !fp64) {
-      float *part = (float *)ctx->isect_N;
-      RPBA_KERNEL(ctx, "k_isect_inst", k_isect_inst<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(
-                                           v, ctx->isect_state, part));
-      RPBA_KERNEL(ctx, "k_isect_point", k_isect_point<float><<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(
-                                            v, ctx->isect_state, ctx->isect_iter, part, maxit, tol, px_tol,
+      RPBA_KERNEL(ctx, "k_isect_point", k_isect_fused_f<<<nblk(ctx->N, 128), 128, 0, ctx->stream>>>(
+                                            v, ctx->isect_state, ctx->isect_iter, maxit, tol, px_tol,
                                             ctx->opt.cond_max, it == maxit - 1));
     } else {
       RPBA_KERNEL(ctx, "k_isect_inst", k_isect_inst<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(

@@ -92,7 +92,9 @@ def test_intersection_covariance_and_refined_weights(name, precision):
     if precision == 0:
         assert err.max() <= 1e-9
     else:
-        assert np.quantile(err, 0.99) <= 2e-5
+        # the stop (a step moving the image by < 1e-3 px per observation) resolves
+        # positions to ~1e-3 px x 30 m / 1000 px = 3e-5 m on these blocks
+        assert np.quantile(err, 0.99) <= 3e-5
         # both sides stop once a step moves the image by < 1e-3 px per observation,
         # possibly at different iterations: a slowly converging point may then still
         # differ along a weakly determined direction. In image space, with
