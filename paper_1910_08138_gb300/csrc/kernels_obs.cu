@@ -343,8 +343,45 @@ __global__ void k_obs_sigma_f(View v, double *part) {
       n3++;
     }
   }
-  double acc[5] = {(double)sh + (double)sl, (double)n1, (double)rh + (double)rl, (double)n3, (double)np};
-  block_reduce_store<5>(acc, part + 5 * blockIdx.x);
+  // CTA sums in float-float and integers (off the FP64 pipe); thread 0 writes the doubles
+  __shared__ float2 wf[2][32];
+  __shared__ int wi[3][32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float e;
+    float oh = __shfl_down_sync(0xffffffffu, sh, o), ol = __shfl_down_sync(0xffffffffu, sl, o);
+    sh = ff_two_sum(sh, oh, e);
+    sl = __fadd_rn(sl, __fadd_rn(e, ol));
+    oh = __shfl_down_sync(0xffffffffu, rh, o);
+    ol = __shfl_down_sync(0xffffffffu, rl, o);
+    rh = ff_two_sum(rh, oh, e);
+    rl = __fadd_rn(rl, __fadd_rn(e, ol));
+    n1 += __shfl_down_sync(0xffffffffu, n1, o);
+    n3 += __shfl_down_sync(0xffffffffu, n3, o);
+    np += __shfl_down_sync(0xffffffffu, np, o);
+  }
+  if (lane == 0) {
+    wf[0][wid] = make_float2(sh, sl);
+    wf[1][wid] = make_float2(rh, rl);
+    wi[0][wid] = n1; wi[1][wid] = n3; wi[2][wid] = np;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float2 a = wf[0][0], b = wf[1][0];
+    long long c1 = wi[0][0], c3 = wi[1][0], cp = wi[2][0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+      a = ff_add(a, wf[0][w]);
+      b = ff_add(b, wf[1][w]);
+      c1 += wi[0][w]; c3 += wi[1][w]; cp += wi[2][w];
+    }
+    double *o = part + 5 * blockIdx.x;
+    o[0] = ff_to_double(a);
+    o[1] = (double)c1;
+    o[2] = ff_to_double(b);
+    o[3] = (double)c3;
+    o[4] = (double)cp;
+  }
 }
 
 // the sigma_0 sums of the current state into pinned host memory (no
