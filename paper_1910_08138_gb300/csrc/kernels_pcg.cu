@@ -185,11 +185,13 @@ __global__ void __launch_bounds__(256) k_pcg_split(const double *S, const long l
 // FP32 form: q += S p in float-float, summed over the tiles with FP64
 // atomics. p^T S p is left to the step kernel (p . q over the sub-block):
 // one atomic per tile on a single per-sub-block word serialises hundreds of
-// CTAs.
-__global__ void __launch_bounds__(256) k_pcg_symv_ff(const float2 *__restrict__ Sff, const long long *S_off,
-                                                     const int *npad, const int *voff, const int *live,
-                                                     const int *sched_tiles, int L, const float2 *__restrict__ p,
-                                                     double *q) {
+// CTAs. 128 threads: warps 0-1 form the row sums, warps 2-3 the column sums
+// (off-diagonal tiles), two threads per row or column with 16 entries each.
+#define SYMV_THREADS 128
+__global__ void __launch_bounds__(SYMV_THREADS) k_pcg_symv_ff(const float2 *__restrict__ Sff, const long long *S_off,
+                                                              const int *npad, const int *voff, const int *live,
+                                                              const int *sched_tiles, int L,
+                                                              const float2 *__restrict__ p, double *q) {
   int l, a, b;
   tile_of(blockIdx.x, sched_tiles, L, l, a, b);
   if (!live[l]) return;
@@ -200,31 +202,38 @@ __global__ void __launch_bounds__(256) k_pcg_symv_ff(const float2 *__restrict__ 
   __shared__ float2 blk[PT][PLD];
   __shared__ float2 pI[PT], pJ[PT];
   int tid = threadIdx.x;
-  if (tid < PT) {
-    pI[tid] = pl[a * PT + tid];
-    pJ[tid] = pl[b * PT + tid];
+  if (tid < PT) pI[tid] = pl[a * PT + tid];
+  else if (tid < 2 * PT) pJ[tid - PT] = pl[b * PT + tid - PT];
+  float2 v[8];
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    int e = tid + SYMV_THREADS * k, r = e / PT, c = e - r * PT;
+    v[k] = (a == b && c > r) ? A[(size_t)(a * PT + c) * np + b * PT + r] : A[(size_t)(a * PT + r) * np + b * PT + c];
   }
-  for (int e = tid; e < PT * PT; e += blockDim.x) {
-    int r = e / PT, c = e - r * PT;
-    float2 v = A[(size_t)(a * PT + r) * np + b * PT + c];
-    if (a == b && c > r) v = A[(size_t)(a * PT + c) * np + b * PT + r];
-    blk[r][c] = v;
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    int e = tid + SYMV_THREADS * k, r = e / PT, c = e - r * PT;
+    blk[r][c] = v[k];
   }
   __syncthreads();
-  if (tid < 2 * PT && (tid < PT || a != b)) {
-    bool col = tid >= PT;
-    int t = col ? tid - PT : tid;
-    float sh = 0.f, sl = 0.f;
-    for (int k = 0; k < PT; k++) {
-      float2 m = col ? blk[k][t] : blk[t][k];
-      float2 x = col ? pI[k] : pJ[k];
-      float e;
-      float pr = ff_two_prod(m.x, x.x, e);
-      ff_acc(sh, sl, pr);
-      sl = __fadd_rn(sl, __fmaf_rn(m.y, x.x, __fmaf_rn(m.x, x.y, e)));
-    }
-    atomicAdd(ql + (col ? b : a) * PT + t, ff_to_double(make_float2(sh, sl)));
+  bool col = tid >= 2 * PT;
+  int u = tid & 63, t = u >> 1, h = u & 1;  // row (or column) t, entries 16h .. 16h+15
+  if (col && a == b) return;                // the diagonal tile's columns are its rows
+  float sh = 0.f, sl = 0.f;
+#pragma unroll
+  for (int k = 16 * h; k < 16 * h + 16; k++) {
+    float2 m = col ? blk[k][t] : blk[t][k];
+    float2 x = col ? pI[k] : pJ[k];
+    float e;
+    float pr = ff_two_prod(m.x, x.x, e);
+    ff_acc(sh, sl, pr);
+    sl = __fadd_rn(sl, __fmaf_rn(m.y, x.x, __fmaf_rn(m.x, x.y, e)));
   }
+  float oh = __shfl_xor_sync(0xffffffffu, sh, 1), ol = __shfl_xor_sync(0xffffffffu, sl, 1);
+  float e;
+  sh = ff_two_sum(sh, oh, e);
+  sl = __fadd_rn(sl, __fadd_rn(e, ol));
+  if (h == 0) atomicAdd(ql + (col ? b : a) * PT + t, ff_to_double(make_float2(sh, sl)));
 }
 
 // FP32 form start: x = 0, r = y, z = M^-1 r (FP32), p = z; rz, |y|
@@ -817,7 +826,7 @@ rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai, int *iters) {
   for (int it = 0; it < maxit; it++) {
     RPBA_CUDA(cudaMemsetAsync(ctx->pcg_q, 0, ctx->ytot * sizeof(double), st));
     if (!fsai && ff_pcg(ctx)) {
-      RPBA_KERNEL(ctx, "k_pcg_symv", k_pcg_symv_ff<<<tiles, 256, 0, st>>>(
+      RPBA_KERNEL(ctx, "k_pcg_symv", k_pcg_symv_ff<<<tiles, SYMV_THREADS, 0, st>>>(
                                          ctx->pcg_Sff, ctx->S_off, ctx->npad, ctx->ycam_off, ctx->pcg_live,
                                          ctx->pcg_tiles, L, ctx->pcg_fp, ctx->pcg_q));
       RPBA_KERNEL(ctx, "k_pcg_step", k_pcg_step_ff<<<L, PCG_THREADS, ctx->pcg_ff_smem, st>>>(
