@@ -328,7 +328,7 @@ __device__ inline void ff_cta_sum(float (&h)[NV], float (&l)[NV], float2 (*sh)[3
 __global__ void __launch_bounds__(PCG_THREADS) k_pcg_step_ff(const int *sub_cam_ptr, const int *voff,
                                                              const float *__restrict__ Minv32, double tol,
                                                              float2 *__restrict__ x, float2 *__restrict__ r,
-                                                             float2 *__restrict__ p, const double *__restrict__ q,
+                                                             float2 *__restrict__ p, double *__restrict__ q,
                                                              double *st, int *live) {
   extern __shared__ float2 rs[];  // r (n), then z as floats (n)
   __shared__ float2 red[2][32];
@@ -355,6 +355,12 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_step_ff(const int *sub_cam_
   for (int k = 0; k < PCGF_PER; k++) {
     int e = threadIdx.x + k * PCG_THREADS;
     if (e < n) { pv[k] = p[o + e]; xv[k] = x[o + e]; rv[k] = r[o + e]; qv[k] = ff_split_bits(q[o + e]); }
+  }
+  // q is consumed: zero it for the next product (padding rows only ever get +0)
+#pragma unroll
+  for (int k = 0; k < PCGF_PER; k++) {
+    int e = threadIdx.x + k * PCG_THREADS;
+    if (e < n) q[o + e] = 0.0;
   }
   float ph[1] = {0.f}, pl[1] = {0.f};  // p . q
 #pragma unroll
@@ -786,6 +792,7 @@ rpba_status pcg_init(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiAppl
   int L = ctx->L;
   cudaStream_t st = ctx->stream;
   if (!fsai && ff_pcg(ctx)) {
+    RPBA_CUDA(cudaMemsetAsync(ctx->pcg_q, 0, ctx->ytot * sizeof(double), st));
     RPBA_KERNEL(ctx, "k_pcg_init", k_pcg_init_ff<<<L, PCG_THREADS, 0, st>>>(
                                        run_dev, fail_dev, ctx->sub_cam_ptr, ctx->ycam_off, ctx->npad, ctx->pcg_Minv32,
                                        ctx->y, ctx->pcg_fx, ctx->pcg_fr, ctx->pcg_fz, ctx->pcg_fp, ctx->pcg_st,
@@ -824,8 +831,7 @@ rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai, int *iters) {
   // took (launches for converged sub-blocks return at once), then every 8
   int next_check = std::min(maxit, std::max(8, ctx->pcg_pred));
   for (int it = 0; it < maxit; it++) {
-    RPBA_CUDA(cudaMemsetAsync(ctx->pcg_q, 0, ctx->ytot * sizeof(double), st));
-    if (!fsai && ff_pcg(ctx)) {
+    if (!fsai && ff_pcg(ctx)) {  // q starts at zero (init) and the step zeroes what it consumed
       RPBA_KERNEL(ctx, "k_pcg_symv", k_pcg_symv_ff<<<tiles, SYMV_THREADS, 0, st>>>(
                                          ctx->pcg_Sff, ctx->S_off, ctx->npad, ctx->ycam_off, ctx->pcg_live,
                                          ctx->pcg_tiles, L, ctx->pcg_fp, ctx->pcg_q));
@@ -834,6 +840,7 @@ rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai, int *iters) {
                                          ctx->pcg_fx, ctx->pcg_fr, ctx->pcg_fp, ctx->pcg_q, ctx->pcg_st,
                                          ctx->pcg_live));
     } else {
+      RPBA_CUDA(cudaMemsetAsync(ctx->pcg_q, 0, ctx->ytot * sizeof(double), st));
       RPBA_CUDA(cudaMemsetAsync(ctx->pcg_pq, 0, L * sizeof(double), st));
       RPBA_KERNEL(ctx, "k_pcg_symv", k_pcg_symv<<<tiles, 256, 0, st>>>(
                                          ctx->S, ctx->S_off, ctx->npad, ctx->ycam_off, ctx->pcg_live, ctx->pcg_tiles,

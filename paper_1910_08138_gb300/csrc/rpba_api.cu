@@ -535,7 +535,8 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
     RPBA_TRY(upload(ctx, &ctx->sub_chunk_ptr, cp.data(), cp.size()));
     RPBA_TRY(alloc_n(ctx, &ctx->chunk_part, (size_t)std::max(ctx->n_chunks, 1)));
   }
-  RPBA_TRY(alloc_n(ctx, &ctx->obs_cost, (size_t)K));
+  if (ctx->opt.precision != 1)  // the FP32 form sums its cost terms per chunk
+    RPBA_TRY(alloc_n(ctx, &ctx->obs_cost, (size_t)K));
   if (ctx->opt.precision == 1) {
     // FP32 form: inputs rounded once (observations relative to the principal point)
     std::vector<float> xy32(2 * (size_t)K), w32((size_t)K, 1.0f), wi32(ctx->has_winv ? 3 * (size_t)K : 0);
