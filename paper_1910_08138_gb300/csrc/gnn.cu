@@ -965,7 +965,7 @@ rpba_status learned_setup(Ctx *ctx, const int *run_dev, int *fail_dev, FsaiApply
   return RPBA_OK;
 }
 
-// judge: a sub-block the learned preconditioner did not bring to pcg_tol is
+// fallback: a sub-block the learned preconditioner did not bring to pcg_tol is
 // solved again with block-Jacobi PCG (reads a count on the host)
 rpba_status learned_fallback(Ctx *ctx, const int *run_dev, int *fail_dev) {
   cudaStream_t st = ctx->stream;

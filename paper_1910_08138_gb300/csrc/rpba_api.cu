@@ -1134,7 +1134,7 @@ static rpba_status lm_pre_pcg(Ctx *ctx) {
   return pcg_init(ctx, ctx->lm_run, ctx->lm_cholfail, nullptr);
 }
 
-// PCG solvers: the CG loop and the solution (and solver 3's block-Jacobi judge)
+// PCG solvers: the CG loop and the solution (and solver 3's block-Jacobi check)
 static rpba_status lm_cg(Ctx *ctx) {
   const FsaiApply *f = ctx->opt.solver == 3 ? &ctx->fsai : nullptr;
   int iters = 0;
