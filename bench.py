@@ -280,6 +280,20 @@ def oracle_step_sample(prob, budget_s=None):
     return dt, k_act
 
 
+def replicas_aggregate(total_ms, obs_per_step, steps, world, device):
+    """N independent replicas of the block (weak scaling, no collective on the
+    data path): the job's time is the slowest rank's, its work that of all
+    ranks. Returns (total_ms, obs/s)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    return total_ms, world * obs_per_step * steps / (total_ms / 1e3)
+
+
 def run_reference(args, rank, world):
     from paper_1910_08138_gb300 import synth
     if rank != 0:
@@ -373,14 +387,8 @@ def run_ours(args, rank, world):
     prof, launches = ctx.profile_read()
     ctx.profile_enable(False)
     ctx.profile_select(None)
-    total_ms = float(np.sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        torch.distributed.barrier()
+    total_ms, value = replicas_aggregate(float(np.sum(times)), k_act, args.steps, world, "cuda")
     ms = total_ms / args.steps
-    value = world * k_act * args.steps / (total_ms / 1e3)
     # algorithmic bytes of the HBM-bound kernels per launch (FP32 form: 20 B/obs
     # of observation data + per-observation 3x6 blocks written and read)
     K = k_act
@@ -529,7 +537,8 @@ def main():
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        if args.impl == "ours":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
     if args.impl == "reference":
         run_reference(args, rank, world)
