@@ -8,7 +8,13 @@
 //   trial update, robust weights (Sec. 5.3).
 //
 // Compute precision T is double for the all-FP64 form and float for the
-// mixed form; positions, rotations, costs and the RCS stay double.
+// FP32 form; the FP64 master state (positions, rotations) and the RCS stay
+// double. The FP32 form runs no FP64 arithmetic per observation, point or
+// instance: residuals for the cost, sigma_0, the MAD and the robust test in
+// float-float (ffloat.cuh), Jacobians and normal equations in FP32 on hi + lo
+// position words, the per-observation N_XC and Z blocks in registers only,
+// format changes by integer bit operations, and FP64 only for sums over
+// blocks of terms and for the rare ill-conditioned 3x3 point systems.
 #include <cuda_runtime.h>
 #include <math.h>
 

@@ -22,7 +22,11 @@
 // preconditioner is applied in FP32 (it needs no more). The product keeps
 // ~1e-13 relative accuracy, far below the 1e-8 residual the loop stops at; on
 // this GPU the FP64 pipe runs at 1/64 of the FP32 rate, so the FP64 loop is
-// bound by its FP64 instructions and this one by memory and latency.
+// bound by its FP64 instructions and this one by memory and latency. The
+// float-float step forms p.Sp itself (p . q), keeps its block sums in
+// float-float, runs the scalar FP64 arithmetic in one thread and zeroes the q
+// it has read; the product uses 128-thread CTAs (two threads per row and per
+// column of a tile).
 #include <cuda_runtime.h>
 #include <math.h>
 

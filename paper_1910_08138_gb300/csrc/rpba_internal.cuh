@@ -5,18 +5,26 @@
 // Data layout in HBM (all arrays device-resident for the life of a context):
 //   cameras (M):   R (9 f64), t (3 f64), intrinsics (3 f64), trial R/t,
 //                  sub-block id, position inside the sub-block (RCS row / 6)
-//   points (N):    X (3 f64), active flag (u8), CSR point -> instances
+//   points (N):    X (3 f64), active flag (u8), CSR point -> instances;
+//                  numbered internally by (sub-block of the first camera,
+//                  first camera, caller's id), translated at the boundary
 //   instances (P): sorted by (sub-block l, point j); X^l (3 f64), trial X^l,
 //                  W^l (sym3 f64), damped inverse point block Ninv (sym3),
 //                  point gradient gX (3), TP flag = point has >= 2 instances
 //   observations (K): sorted by instance (so every instance and every
 //                  sub-block is a contiguous segment), structure of arrays:
 //                  cam (i32), inst (i32), xy (2 f64), C^-1 (3 f64), robust
-//                  weight w (f64), user index (i32); per-LM-step N_XC (3x6)
-//                  and Z = Ninv N_XC (3x6) in the compute precision
+//                  weight w (f64), user index (i32); FP64 form: per-LM-step
+//                  N_XC (3x6) and Z = Ninv N_XC (3x6)
+//   FP32 form:     camera records (R, C, f as hi + lo, t; 128 B each) of the
+//                  current and trial state, X, X^l and trial X^l as hi + lo
+//                  words, observations relative to the principal point as
+//                  hi + lo, C^-1, w and W^l in FP32
 //   camera order:  CSR camera -> observation positions (gather list)
 //   Schur pairs:   (a, b) observation positions of one instance whose cameras
-//                  differ, local(cam a) > local(cam b): lower-triangle blocks
+//                  differ, local(cam a) > local(cam b): lower-triangle blocks;
+//                  FP32 form: sorted by (camera of a, camera of b, a) with
+//                  their instance and camera-pair segment
 //   RCS:           per sub-block a dense n_pad x n_pad f64 matrix (row-major,
 //                  n_pad = 32 * ceil(6 M_l / 32), padding = identity), rhs;
 //                  inverted 32 x 32 diagonal tiles of the factor; for the
