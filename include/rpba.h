@@ -95,9 +95,12 @@ typedef struct {
   double isect_px_tol;   /* ... or a step that moves the image residuals by less than this per
                             observation (dX^T N dX <= px_tol^2 n_obs), 1e-3 px */
   double cond_max;       /* Frobenius condition number that drops a point, 1e12 */
-  int32_t precision;     /* 0: all FP64 ("plain"); 1: FP32 bulk, FP64 solve/reductions */
-  int32_t solver;        /* RCS solve: 0 FP64 Cholesky; 1 FP64 PCG with block-Jacobi
-                            preconditioning (Sec. 5.5) to pcg_tol; 2 FP32 Cholesky of the
+  int32_t precision;     /* 0: all FP64 ("plain"); 1: FP32 bulk (float-float residuals for
+                            the cost, sigma_0 and robust tests), FP64 reductions */
+  int32_t solver;        /* RCS solve: 0 FP64 Cholesky; 1 PCG with block-Jacobi
+                            preconditioning (Sec. 5.5) to pcg_tol (FP64 vectors; with
+                            precision 1 float-float vectors and products for sub-blocks of
+                            up to 2048 unknowns, FP64 above); 2 FP32 Cholesky of the
                             Jacobi-scaled RCS with FP64 iterative refinement; 3 FP64 PCG
                             with the learned preconditioner (rpba_set_gnn_weights),
                             block-Jacobi PCG again for a sub-block it leaves above pcg_tol;
