@@ -627,8 +627,8 @@ __global__ void k_isect_point(View v, int *state, int *iter, const T *part, int 
   }
 }
 
-// FP32 form, one Gauss-Newton iteration of Eq. bars in one kernel, one thread
-// per running point: N_j and g_j over all the point's observations at the
+// FP32 form, one Gauss-Newton iteration of Eq. bars for one point (the
+// kernel below runs them all in one launch): N_j and g_j over all the point's observations at the
 // current X_j (hi + lo), the FP32 solve with the same checks, FP64
 // re-formation and convergence tests as k_isect_point, the position update
 // in float-float. On convergence the refined weights W^l = N_j - N_j^(l):
@@ -654,10 +654,8 @@ __device__ inline void isect_obs_acc(const View &v, int j, int k, float N[6], fl
   }
 }
 
-__global__ void k_isect_fused_f(View v, int *state, int *iter, int max_iter, double tol, double px_tol,
-                                double cond_max, int last) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= v.N || state[j] != 1) return;
+__device__ static void isect_fused_step(const View &v, int j, int *state, int *iter, int max_iter, double tol,
+                                        double px_tol, double cond_max, int last) {
   int q0 = v.pt_inst_ptr[j], q1 = v.pt_inst_ptr[j + 1];
   float N[6] = {0, 0, 0, 0, 0, 0}, g[3] = {0, 0, 0};
   float Nh[6] = {0, 0, 0, 0, 0, 0}, Nl[6] = {0, 0, 0, 0, 0, 0};  // N_j in float-float
@@ -759,6 +757,16 @@ __global__ void k_isect_fused_f(View v, int *state, int *iter, int max_iter, dou
   }
 }
 
+// the points are independent (cameras fixed): each thread runs its point's
+// Gauss-Newton iterations to convergence or failure in one launch
+__global__ void k_isect_fused_f(View v, int *state, int *iter, int max_iter, double tol, double px_tol,
+                                double cond_max) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= v.N) return;
+  for (int pass = 0; pass < max_iter && state[j] == 1; pass++)
+    isect_fused_step(v, j, state, iter, max_iter, tol, px_tol, cond_max, pass == max_iter - 1);
+}
+
 __global__ void k_isect_start(View v, int *state, int *iter, int tp_only, int *count) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= v.N) return;
@@ -785,12 +793,12 @@ rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped, bool fp64) {
   int maxit = ctx->opt.isect_max_iter;
   double tol = ctx->opt.isect_tol;
   double px_tol = ctx->opt.isect_px_tol;
-  for (int it = 0; it < maxit; it++) {
-    if (ctx->opt.precision == 1 && !fp64) {
-      RPBA_KERNEL(ctx, "k_isect_point", k_isect_fused_f<<<nblk(ctx->N, 128), 128, 0, ctx->stream>>>(
-                                            v, ctx->isect_state, ctx->isect_iter, maxit, tol, px_tol,
-                                            ctx->opt.cond_max, it == maxit - 1));
-    } else {
+  if (ctx->opt.precision == 1 && !fp64) {  // FP32 form: every point's iterations in one launch
+    RPBA_KERNEL(ctx, "k_isect_point", k_isect_fused_f<<<nblk(ctx->N, 128), 128, 0, ctx->stream>>>(
+                                          v, ctx->isect_state, ctx->isect_iter, maxit, tol, px_tol,
+                                          ctx->opt.cond_max));
+  } else {
+    for (int it = 0; it < maxit; it++) {
       RPBA_KERNEL(ctx, "k_isect_inst", k_isect_inst<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(
                                            v, ctx->isect_state, ctx->isect_N));
       RPBA_KERNEL(ctx, "k_isect_point", k_isect_point<double><<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(
