@@ -335,10 +335,12 @@ __global__ void k_camera_mad(int M, MadIn in, const uint8_t *active, const int *
 rpba_status launch_camera_scale(Ctx *ctx) {
   if (ctx->M == 0) return RPBA_OK;
   bool f32 = ctx->opt.precision == 1;
-  size_t ks = f32 ? sizeof(unsigned) : sizeof(unsigned long long);
   int n2 = 64;
   while (n2 < 2 * ctx->max_cam_obs) n2 <<= 1;
-  size_t smem = (size_t)n2 * ks;
+  // FP32 form: 32-bit keys, radix select (no padding); FP64 form: 64-bit keys
+  // padded to a power of two for the bitonic sort
+  size_t smem = f32 ? (size_t)std::max(2 * ctx->max_cam_obs, 1) * sizeof(unsigned)
+                    : (size_t)n2 * sizeof(unsigned long long);
   if (smem > 200 * 1024) {
     ctx->err = "camera with too many observations for the shared-memory median";
     return RPBA_ERR_INVALID_ARG;
@@ -347,7 +349,6 @@ rpba_status launch_camera_scale(Ctx *ctx) {
            ctx->camff, ctx->X_hi, ctx->X_lo, ctx->obs_xy32, ctx->obs_xylo, ctx->obs_whiten32};
   int threads = std::min(1024, std::max(32, n2 / 2));  // one thread per compare-exchange of a pass
   if (f32) {
-    smem = (size_t)std::max(2 * ctx->max_cam_obs, 1) * sizeof(unsigned);  // radix select: no padding
     // two observations per thread (up to 1024 threads): the residual phase is
     // a chain of dependent gathers, so it wants many threads in flight
     threads = std::min(1024, std::max(64, 32 * ((ctx->max_cam_obs + 63) / 64)));  // two observations per thread
