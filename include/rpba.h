@@ -329,12 +329,15 @@ rpba_status rpba_check_formats(const double *x, const float *f, int32_t n, float
 #define RPBA_NOALLOC_MAX_OBS (8192 * 256)
 #define RPBA_NOALLOC_MAX_POINTS (8192 * 256)
 
-/* sigma_0 and RMS as rpba_sigma0 computes them (Eq. sigma0: sum w v^T C^-1 v
- * over observations of active points / (2 K - 6 M - 3 N + 7); RMS over
+/* sigma_0 and RMS as rpba_sigma0 computes them (sigma_0 squared: the sum of
+ * w v^T C^-1 v over the observations of active points, divided by
+ * 2 K - 6 M - 3 N + 7 with K active observations, M cameras and N active
+ * points; RMS: the root mean square of the residual components over the
  * observations with w == 1), for a block given entirely in caller-owned DEVICE
- * memory, without allocating any device memory. The paper has no counterpart;
- * it exists for callers that cannot allocate device memory per call (a fixed
- * device-memory budget, an allocator owned by another framework).
+ * memory, without allocating any device memory. The paper has no counterpart
+ * to this entry point; it exists for callers that cannot allocate device
+ * memory per call (a fixed device-memory budget, an allocator owned by another
+ * framework).
  *   R n_cams x 9 (row-major rotation, X_c = R X + t), t n_cams x 3, intr
  *   n_cams x 3 (f, cx, cy), X n_points x 3, active n_points (NULL: all),
  *   obs_cam / obs_point n_obs, obs_xy n_obs x 2, obs_winv n_obs x 3 (NULL:
@@ -345,8 +348,9 @@ rpba_status rpba_check_formats(const double *x, const float *f, int32_t n, float
  * Scratch: one file-scope device array shared by every call; its device
  * address is looked up on the first call on each device (make that first call
  * before any stream capture). Calls that overlap on the GPU race on it.
- * Errors: INVALID_ARG for negative sizes, sizes above the limits, or missing
- * arrays; CUDA for a failed launch or copy. */
+ * Errors: INVALID_ARG for negative sizes, sizes above the limits, missing
+ * arrays, or observations without any camera or point; CUDA for a failed
+ * launch or copy. */
 rpba_status rpba_sigma0_noalloc(int32_t n_cams, int32_t n_points, int32_t n_obs, const double *R,
                                 const double *t, const double *intr, const double *X,
                                 const uint8_t *active, const int32_t *obs_cam,

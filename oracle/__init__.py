@@ -100,6 +100,12 @@ def lib():
         L.orc_lm_step.restype = C.c_int
         L.orc_sub_lm.argtypes = [C.c_void_p, C.c_int, C.POINTER(Options)]
         L.orc_sub_lm.restype = C.c_int
+        L.orc_sub_lm_trace.argtypes = [C.c_void_p, C.c_int, C.POINTER(Options), _dp, _dp, _ip, C.c_int]
+        L.orc_sub_lm_trace.restype = C.c_int
+        L.orc_lambda_next.argtypes = [C.c_double, C.c_int, C.c_double]
+        L.orc_lambda_next.restype = C.c_double
+        L.orc_ratio_rule.argtypes = [C.POINTER(C.c_double), C.c_double, C.c_double, C.POINTER(C.c_int)]
+        L.orc_ratio_rule.restype = C.c_int
         L.orc_run.argtypes = [C.c_void_p, C.POINTER(Options), C.POINTER(Report)]
         L.orc_default_options.argtypes = [C.POINTER(Options)]
         _lib = L
@@ -140,6 +146,21 @@ def project(R, t, intr, X):
     uv, Jc, Jx = np.zeros(2), np.zeros(12), np.zeros(6)
     z = lib().orc_project(_f64(R).reshape(-1), _f64(t), _f64(intr), _f64(X), uv, Jc, Jx)
     return uv, Jc.reshape(2, 6), Jx.reshape(2, 3), z
+
+
+def lambda_next(lam, accepted, lambda0):
+    return lib().orc_lambda_next(float(lam), int(accepted), float(lambda0))
+
+
+def ratio_rule_sequence(values, stop_ratio=1.01, grace=1):
+    """Feeds values[1:] to the oracle's stop rule, starting from best =
+    values[0]; returns the index (into values) of the value that stopped the
+    loop, or None."""
+    best, g = C.c_double(float(values[0])), C.c_int(int(grace))
+    for i, v in enumerate(values[1:], start=1):
+        if lib().orc_ratio_rule(C.byref(best), float(v), float(stop_ratio), C.byref(g)):
+            return i
+    return None
 
 
 def median(a):
@@ -273,6 +294,15 @@ class Oracle:
     def sub_lm(self, l, **opts):
         o = default_options(**opts)
         return lib().orc_sub_lm(self._h, l, C.byref(o))
+
+    def sub_lm_trace(self, l, cap=64, **opts):
+        """The LM loop of sub-block l with its trace: (iterations, lambda used,
+        result of each step, F_l after each step)."""
+        o = default_options(**opts)
+        F, lam, acc = np.zeros(cap), np.zeros(cap), np.zeros(cap, np.int32)
+        it = lib().orc_sub_lm_trace(self._h, l, C.byref(o), F, lam, acc, cap)
+        n = min(it, cap)
+        return it, lam[:n], acc[:n], F[:n]
 
     def run(self, **opts):
         o = default_options(**opts)

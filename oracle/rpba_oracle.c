@@ -874,11 +874,36 @@ int orc_lm_step(orc_ctx *c, int l, double lambda, double *F_before, double *F_tr
   return result;
 }
 
+/* LM damping after a step. The paper keeps lambda fixed (Sec. 5.5) and is
+ * silent on a rejected step; the reading taken here: x10 after a rejected
+ * step, /10 floored at lambda0 after an accepted one. */
+double orc_lambda_next(double lambda, int accepted, double lambda0) {
+  if (!accepted) return lambda * 10.0;
+  return lambda / 10.0 > lambda0 ? lambda / 10.0 : lambda0;
+}
+
+/* The stop rule of the inner (F_l) and the outer (sigma_0) loop (Sec. 5.5):
+ * after a new value v, ratio = best / v with best the smallest value before
+ * v; best then becomes min(best, v). A ratio below stop_ratio uses up one
+ * grace iteration if one is left, and otherwise ends the loop (returns 1). */
+int orc_ratio_rule(double *best, double v, double stop_ratio, int *grace) {
+  double ratio = *best / (v > 1e-300 ? v : 1e-300);
+  if (v < *best) *best = v;
+  if (ratio >= stop_ratio) return 0;
+  if (*grace > 0) {
+    (*grace)--;
+    return 0;
+  }
+  return 1;
+}
+
 /* the LM loop of one sub-block (one solution of Eq. bact). A rejected step
  * raises lambda and retries; the best/current ratio rule (Sec. 5.5) is
  * applied to accepted steps; more than max_reject rejections in a row end the
- * loop. */
-int orc_sub_lm(orc_ctx *c, int l, const orc_options *o) {
+ * loop. With a trace (cap > 0), iteration it records the damping it used,
+ * whether its step was accepted and the cost F_l after it. */
+int orc_sub_lm_trace(orc_ctx *c, int l, const orc_options *o, double *F_hist, double *lambda_hist,
+                     int *acc_hist, int cap) {
   if (c->sub_cam_ptr[l + 1] == c->sub_cam_ptr[l]) return 0;
   double lambda = o->lambda0;
   double F = orc_sub_cost(c, l);
@@ -887,25 +912,29 @@ int orc_sub_lm(orc_ctx *c, int l, const orc_options *o) {
   int rejects = 0;
   int it = 0;
   while (it < o->max_inner) {
-    it++;
     double Fb, Ft;
     int r = orc_lm_step(c, l, lambda, &Fb, &Ft, NULL, NULL);
+    if (it < cap) {
+      lambda_hist[it] = lambda;
+      acc_hist[it] = r;
+      F_hist[it] = r == 1 ? Ft : F;
+    }
+    it++;
     if (r != 1) {
-      lambda *= 10.0;
+      lambda = orc_lambda_next(lambda, 0, o->lambda0);
       if (++rejects > o->max_reject) break;
       continue;
     }
     rejects = 0;
     F = Ft;
-    lambda = lambda / 10.0 > o->lambda0 ? lambda / 10.0 : o->lambda0;
-    double ratio = best / (F > 1e-300 ? F : 1e-300);
-    if (F < best) best = F;
-    if (ratio < o->stop_ratio) {
-      if (grace > 0) grace--;
-      else break;
-    }
+    lambda = orc_lambda_next(lambda, 1, o->lambda0);
+    if (orc_ratio_rule(&best, F, o->stop_ratio, &grace)) break;
   }
   return it;
+}
+
+int orc_sub_lm(orc_ctx *c, int l, const orc_options *o) {
+  return orc_sub_lm_trace(c, l, o, NULL, NULL, NULL, 0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -955,10 +984,7 @@ void orc_run(orc_ctx *c, const orc_options *o, orc_report *r) {
     s = orc_sigma0(c);
     if (r->outer < 128) r->sigma0_hist[r->outer] = s;
     r->outer++;
-    double ratio = best / (s > 1e-300 ? s : 1e-300);
-    if (s < best) best = s;
-    if (ratio < o->stop_ratio) {
-      if (grace > 0) { grace--; continue; }
+    if (orc_ratio_rule(&best, s, o->stop_ratio, &grace)) {
       if (o->robust && !robust_on) {
         robust_on = 1;
         r->robust_started_at = r->outer;

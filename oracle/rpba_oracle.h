@@ -131,6 +131,16 @@ int orc_lm_step(orc_ctx *c, int l, double lambda, double *F_before, double *F_tr
                 double *dc, double *dx);
 /* the LM loop of sub-block l (one bact); returns the number of iterations */
 int orc_sub_lm(orc_ctx *c, int l, const orc_options *o);
+/* the same loop; iteration it < cap records the damping it used, its result
+ * (as orc_lm_step) and the cost F_l after it */
+int orc_sub_lm_trace(orc_ctx *c, int l, const orc_options *o, double *F_hist, double *lambda_hist,
+                     int *acc_hist, int cap);
+/* the damping after a step: x10 after a rejection, /10 floored at lambda0
+ * after an acceptance (reading of Sec. 5.5) */
+double orc_lambda_next(double lambda, int accepted, double lambda0);
+/* the stop rule of both loops (Sec. 5.5): ratio = best / v, best = min(best,
+ * v); below stop_ratio one grace iteration, then stop (returns 1) */
+int orc_ratio_rule(double *best, double v, double stop_ratio, int *grace);
 
 /* whole method: initial intersection, bact/bars iterations, robust stage */
 void orc_run(orc_ctx *c, const orc_options *o, orc_report *r);

@@ -354,14 +354,14 @@ rpba_status launch_camera_scale(Ctx *ctx) {
     threads = std::min(1024, std::max(64, 32 * ((ctx->max_cam_obs + 63) / 64)));  // two observations per thread
     if (smem > 48 * 1024)
       RPBA_CUDA(cudaFuncSetAttribute(k_camera_mad<unsigned>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    RPBA_KERNEL(ctx, "k_camera_mad", k_camera_mad<unsigned><<<ctx->M, threads, smem, ctx->stream>>>(
+    RPBA_KERNEL(ctx, "k_camera_mad_u32", k_camera_mad<unsigned><<<ctx->M, threads, smem, ctx->stream>>>(
                                          ctx->M, in, ctx->active, ctx->cam_obs_ptr, ctx->cam_obs, ctx->obs_pt,
                                          ctx->has_winv, ctx->cam_sigma, ctx->cam_sigma32));
   } else {
     if (smem > 48 * 1024)
       RPBA_CUDA(cudaFuncSetAttribute(k_camera_mad<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-    RPBA_KERNEL(ctx, "k_camera_mad", k_camera_mad<unsigned long long><<<ctx->M, threads, smem, ctx->stream>>>(
+    RPBA_KERNEL(ctx, "k_camera_mad_u64", k_camera_mad<unsigned long long><<<ctx->M, threads, smem, ctx->stream>>>(
                                          ctx->M, in, ctx->active, ctx->cam_obs_ptr, ctx->cam_obs, ctx->obs_pt,
                                          ctx->has_winv, ctx->cam_sigma, nullptr));
   }

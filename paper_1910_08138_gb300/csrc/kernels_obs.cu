@@ -396,7 +396,7 @@ rpba_status sigma0_launch(Ctx *ctx) {
   View v = make_view(ctx);
   int nb = ctx->red_blocks;
   if (ctx->opt.precision == 1) {
-    RPBA_KERNEL(ctx, "k_obs_sigma", k_obs_sigma_f<<<nb, 256, 0, ctx->stream>>>(v, ctx->red));
+    RPBA_KERNEL(ctx, "k_obs_sigma_f", k_obs_sigma_f<<<nb, 256, 0, ctx->stream>>>(v, ctx->red));
   } else {
     RPBA_KERNEL(ctx, "k_obs_sigma", k_obs_sigma<<<nb, 256, 0, ctx->stream>>>(v, ctx->red));
   }
@@ -794,7 +794,7 @@ rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped, bool fp64) {
   double tol = ctx->opt.isect_tol;
   double px_tol = ctx->opt.isect_px_tol;
   if (ctx->opt.precision == 1 && !fp64) {  // FP32 form: every point's iterations in one launch
-    RPBA_KERNEL(ctx, "k_isect_point", k_isect_fused_f<<<nblk(ctx->N, 128), 128, 0, ctx->stream>>>(
+    RPBA_KERNEL(ctx, "k_isect_fused_f", k_isect_fused_f<<<nblk(ctx->N, 128), 128, 0, ctx->stream>>>(
                                           v, ctx->isect_state, ctx->isect_iter, maxit, tol, px_tol,
                                           ctx->opt.cond_max));
   } else {
@@ -905,7 +905,7 @@ rpba_status launch_robust_weights(Ctx *ctx, int *n_down) {
   RPBA_TRY(launch_camera_scale(ctx));
   RPBA_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(int), ctx->stream));
   if (ctx->K && ctx->opt.precision == 1)
-    RPBA_KERNEL(ctx, "k_robust_weights", k_robust_weights_f<<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(
+    RPBA_KERNEL(ctx, "k_robust_weights_f", k_robust_weights_f<<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(
                                              make_view(ctx), ctx->cam_sigma32, (float)ctx->opt.t_v, ctx->opt.downweight,
                                              ctx->counters));
   else if (ctx->K)
@@ -1074,11 +1074,11 @@ static rpba_status sub_costs_impl(Ctx *ctx, int trial, const int *run, double *F
   View v = make_view(ctx);
   if (ctx->opt.precision == 1) {
     if (ctx->n_chunks)
-      RPBA_KERNEL(ctx, "k_obs_cost", k_cost_chunks_f<<<ctx->n_chunks, 256, 0, ctx->stream>>>(
+      RPBA_KERNEL(ctx, "k_cost_chunks_f", k_cost_chunks_f<<<ctx->n_chunks, 256, 0, ctx->stream>>>(
                                          v, trial, run, ctx->chunk_sub, ctx->chunk_start, ctx->sub_obs_ptr,
                                          ctx->chunk_part));
     if (ctx->L)
-      RPBA_KERNEL(ctx, "k_cost_sub", k_cost_sub_f<<<ctx->L, 256, 0, ctx->stream>>>(ctx->L, run, ctx->sub_chunk_ptr,
+      RPBA_KERNEL(ctx, "k_cost_sub_f", k_cost_sub_f<<<ctx->L, 256, 0, ctx->stream>>>(ctx->L, run, ctx->sub_chunk_ptr,
                                                                                    ctx->chunk_part, F_dev));
     return RPBA_OK;
   }
@@ -1451,9 +1451,9 @@ rpba_status launch_build_rcs(Ctx *ctx, const double *lambda_dev, const int *run_
   RPBA_KERNEL(ctx, "k_rcs_clear", k_rcs_clear<<<gclr, 256, 0, ctx->stream>>>(v, run_dev, ctx->L));
   if (ctx->P == 0) return RPBA_OK;
   if (ctx->opt.precision == 1) {
-    RPBA_KERNEL(ctx, "k_linearize", k_linearize<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(
+    RPBA_KERNEL(ctx, "k_linearize_f32", k_linearize<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(
                                         v, lambda_dev, run_dev, nullptr, nullptr, (float *)ctx->Ninv, (float *)ctx->gX));
-    RPBA_KERNEL(ctx, "k_camera_blocks", k_camera_blocks<float><<<ctx->M, CB_THREADS, 0, ctx->stream>>>(
+    RPBA_KERNEL(ctx, "k_camera_blocks_f32", k_camera_blocks<float><<<ctx->M, CB_THREADS, 0, ctx->stream>>>(
         v, lambda_dev, run_dev, nullptr, nullptr, (const float *)ctx->gX, (const float *)ctx->Ninv));
     if (ctx->n_pairs)
       RPBA_KERNEL(ctx, "k_schur_seg", k_schur_seg<<<nblk(ctx->n_pairs, SC_THREADS), SC_THREADS, 0, ctx->stream>>>(
@@ -1461,9 +1461,9 @@ rpba_status launch_build_rcs(Ctx *ctx, const double *lambda_dev, const int *run_
                                           ctx->spair_seg, ctx->seg_cam, ctx->seg_nb, (const float *)ctx->Ninv));
   } else {
     double *NXC = (double *)ctx->NXC, *Z = (double *)ctx->Z;
-    RPBA_KERNEL(ctx, "k_linearize", k_linearize<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, lambda_dev, run_dev, NXC, Z,
+    RPBA_KERNEL(ctx, "k_linearize_f64", k_linearize<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, lambda_dev, run_dev, NXC, Z,
                                                                     (double *)ctx->Ninv, (double *)ctx->gX));
-    RPBA_KERNEL(ctx, "k_camera_blocks", k_camera_blocks<double><<<ctx->M, CB_THREADS, 0, ctx->stream>>>(
+    RPBA_KERNEL(ctx, "k_camera_blocks_f64", k_camera_blocks<double><<<ctx->M, CB_THREADS, 0, ctx->stream>>>(
         v, lambda_dev, run_dev, NXC, Z, (const double *)ctx->gX, (const double *)ctx->Ninv));
     if (ctx->n_pairs)
       RPBA_KERNEL(ctx, "k_schur_pairs", k_schur_pairs<double><<<nblk(ctx->n_pairs * 6, 256), 256, 0, ctx->stream>>>(
@@ -1570,10 +1570,10 @@ rpba_status launch_backsub_trial(Ctx *ctx, const int *run_dev) {
     RPBA_KERNEL(ctx, "k_to_float", k_to_float<<<nblk(ctx->ytot, 256), 256, 0, ctx->stream>>>(ctx->dC, ctx->dC32, ctx->ytot));
   if (ctx->P) {
     if (ctx->opt.precision == 1)
-      RPBA_KERNEL(ctx, "k_backsub", k_backsub<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, run_dev, nullptr,
+      RPBA_KERNEL(ctx, "k_backsub_f32", k_backsub<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, run_dev, nullptr,
                                                                    (const float *)ctx->Ninv, (const float *)ctx->gX));
     else
-      RPBA_KERNEL(ctx, "k_backsub", k_backsub<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, run_dev, (const double *)ctx->NXC,
+      RPBA_KERNEL(ctx, "k_backsub_f64", k_backsub<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, run_dev, (const double *)ctx->NXC,
                                                                     (const double *)ctx->Ninv, (const double *)ctx->gX));
   }
   if (ctx->M) RPBA_KERNEL(ctx, "k_cam_trial", k_cam_trial<<<nblk(ctx->M, 128), 128, 0, ctx->stream>>>(v, run_dev));

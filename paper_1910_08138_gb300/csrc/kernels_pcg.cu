@@ -797,7 +797,7 @@ rpba_status pcg_init(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiAppl
   cudaStream_t st = ctx->stream;
   if (!fsai && ff_pcg(ctx)) {
     RPBA_CUDA(cudaMemsetAsync(ctx->pcg_q, 0, ctx->ytot * sizeof(double), st));
-    RPBA_KERNEL(ctx, "k_pcg_init", k_pcg_init_ff<<<L, PCG_THREADS, 0, st>>>(
+    RPBA_KERNEL(ctx, "k_pcg_init_ff", k_pcg_init_ff<<<L, PCG_THREADS, 0, st>>>(
                                        run_dev, fail_dev, ctx->sub_cam_ptr, ctx->ycam_off, ctx->npad, ctx->pcg_Minv32,
                                        ctx->y, ctx->pcg_fx, ctx->pcg_fr, ctx->pcg_fz, ctx->pcg_fp, ctx->pcg_st,
                                        ctx->pcg_live));
@@ -836,10 +836,10 @@ rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai, int *iters) {
   int next_check = std::min(maxit, std::max(8, ctx->pcg_pred));
   for (int it = 0; it < maxit; it++) {
     if (!fsai && ff_pcg(ctx)) {  // q starts at zero (init) and the step zeroes what it consumed
-      RPBA_KERNEL(ctx, "k_pcg_symv", k_pcg_symv_ff<<<tiles, SYMV_THREADS, 0, st>>>(
+      RPBA_KERNEL(ctx, "k_pcg_symv_ff", k_pcg_symv_ff<<<tiles, SYMV_THREADS, 0, st>>>(
                                          ctx->pcg_Sff, ctx->S_off, ctx->npad, ctx->ycam_off, ctx->pcg_live,
                                          ctx->pcg_tiles, L, ctx->pcg_fp, ctx->pcg_q));
-      RPBA_KERNEL(ctx, "k_pcg_step", k_pcg_step_ff<<<L, PCG_THREADS, ctx->pcg_ff_smem, st>>>(
+      RPBA_KERNEL(ctx, "k_pcg_step_ff", k_pcg_step_ff<<<L, PCG_THREADS, ctx->pcg_ff_smem, st>>>(
                                          ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_Minv32, ctx->opt.pcg_tol,
                                          ctx->pcg_fx, ctx->pcg_fr, ctx->pcg_fp, ctx->pcg_q, ctx->pcg_st,
                                          ctx->pcg_live));
@@ -887,7 +887,7 @@ rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai, int *iters) {
 rpba_status pcg_out(Ctx *ctx, const int *run_dev, const int *fail_dev) {
   int L = ctx->L;
   if (ff_pcg(ctx)) {
-    RPBA_KERNEL(ctx, "k_pcg_out", k_pcg_out_ff<<<dim3(8, L), 256, 0, ctx->stream>>>(
+    RPBA_KERNEL(ctx, "k_pcg_out_ff", k_pcg_out_ff<<<dim3(8, L), 256, 0, ctx->stream>>>(
                                       run_dev, fail_dev, ctx->ycam_off, ctx->npad, L, ctx->pcg_fx, ctx->dC));
     return RPBA_OK;
   }

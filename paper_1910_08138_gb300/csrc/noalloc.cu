@@ -124,6 +124,9 @@ extern "C" rpba_status rpba_sigma0_noalloc(int32_t n_cams, int32_t n_points, int
   if (n_obs > RPBA_NOALLOC_MAX_OBS || n_points > RPBA_NOALLOC_MAX_POINTS) return RPBA_ERR_INVALID_ARG;
   if ((n_cams && (!R || !t || !intr)) || (n_points && !X) || (n_obs && (!obs_cam || !obs_point || !obs_xy)))
     return RPBA_ERR_INVALID_ARG;
+  // observations index cameras and points: a block with observations but no
+  // cameras or no points has nothing valid for them to reference
+  if (n_obs && (!n_cams || !n_points)) return RPBA_ERR_INVALID_ARG;
   double *scratch = nullptr;
   rpba_status st = scratch_for_current_device(&scratch);
   if (st != RPBA_OK) return st;

@@ -185,6 +185,64 @@ def test_lm_step(name, form):
     np.testing.assert_allclose(g.cameras(), o.cameras(), atol=1e-8 if precision == 0 else 1e-4)
 
 
+# the FP32 form's iterative solvers: float-float block-Jacobi PCG (1), the auto
+# choice the benchmark runs (4, which resolves to 1 on these blocks) and the
+# learned preconditioner (3)
+PCG_FORMS = [(1, 1), (1, 4), (1, 3)]
+
+
+@pytest.mark.parametrize("name", list(PROBS))
+@pytest.mark.parametrize("form", PCG_FORMS)
+def test_lm_step_pcg_forms(name, form):
+    """PCG on the RCS (block-Jacobi as in Sec. 5.5, or the learned
+    preconditioner) in the FP32 form, at one shared state.
+
+    The solver is judged on the system it was given: the GPU's own assembled
+    RCS (rpba_rcs at the same damping), against which the returned camera step
+    must have a true relative residual of at most pcg_tol = 1e-8 plus the
+    float-float product's rounding (hi + lo words carry ~2^-48 relative; 1e-12
+    of |S| |dc| covers the sum over a row). The step itself must then match the
+    oracle's Cholesky step within the FP32 assembly's error, the tolerance of
+    the FP32 form with the direct solve (5e-3 of the largest entry; the RCS
+    differs from the oracle's by up to 2e-5 of its largest entry, amplified by
+    its condition number)."""
+    precision, solver = form
+    prob, o, g = _state_after_intersection(name, precision, weights=(name == "tiny3w"), solver=solver)
+    if solver == 3:
+        G = rpba.Gnn(seed=0)  # untrained weights: SPD by construction all the same
+        g.set_gnn_weights(G.weights())
+        G.close()
+    assert g.resolved_options().solver in (1, 3)
+    lam = 1e-4
+    pcg_tol = g.options.pcg_tol
+    systems = []
+    for l in range(g.L):
+        S, y = g.rcs(l, lam)
+        systems.append((np.tril(S) + np.tril(S, -1).T, y))
+    acc, Fb, Ft, dc, dx = g.lm_step(lam)
+    it, rr = g.solver_stats()
+    assert np.all(it > 0) and np.all(rr <= pcg_tol)
+    off = 0
+    _, isub = o.instances()
+    for l in range(o.L):
+        S, y = systems[l]
+        n = y.size
+        dcl = dc[off:off + n]
+        res = np.linalg.norm(S @ dcl - y) / np.linalg.norm(y)
+        fp = 1e-12 * np.linalg.norm(np.abs(S) @ np.abs(dcl)) / np.linalg.norm(y)
+        assert res <= pcg_tol + fp, (l, res, fp)
+        r, fb, ft, dco, dxo = o.lm_step(l, lam)
+        np.testing.assert_allclose(Fb[l], fb, rtol=1e-6)
+        sc = max(np.abs(dco).max(), 1e-12)
+        assert np.abs(dcl - dco).max() <= 5e-3 * sc
+        sx = max(np.abs(dxo).max(), 1e-12)
+        assert np.abs(dx[isub == l] - dxo).max() <= 5e-3 * sx
+        np.testing.assert_allclose(Ft[l], ft, rtol=1e-4)
+        assert acc[l] == r
+        off += n
+    np.testing.assert_allclose(g.cameras(), o.cameras(), atol=1e-4)
+
+
 @pytest.mark.parametrize("name", list(PROBS))
 def test_fp32_form_sigma0_from_float_float_residuals(name):
     """The FP32 form's sigma_0 and RMS (Eq. sigma0) come from float-float

@@ -1,0 +1,198 @@
+"""GPU path against the FP64 CPU oracle on the benchmark's own block sizes.
+
+The small-block parity tests cover every kernel at a few thousand
+observations; the paths below only run on larger inputs:
+
+* the 1,000-camera / 100k-point / 600k-observation block with 8 uneven
+  sub-blocks (60..200 cameras, RCS sizes up to 1,200 unknowns: 38 tiles of
+  32 per side), where every per-observation kernel spans thousands of CTAs
+  and the Schur kernel its full segment machinery;
+* cameras with more observations than 48 KB of shared memory holds in the
+  per-camera median (the opt-in dynamic shared-memory launch), and cameras
+  above the median's shared-memory limit, which must be refused with a status.
+
+Every comparison starts both sides from the same state. Tolerances are those
+of the small-block tests (FP32 form: Jacobians 1e-5 relative, covariance 1e-4
+relative Frobenius, RCS 2e-5 of its largest entry, costs, sigma_0 and camera
+scales 1e-6 relative).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1910_08138_gb300 import rpba, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_frob(a, b, axis):
+    return np.linalg.norm(a - b, axis=axis) / np.maximum(np.linalg.norm(b, axis=axis), 1e-300)
+
+
+def sync_state(o, g):
+    g.set_cameras(o.cameras())
+    X, a = o.points()
+    g.set_points(X, a)
+    Xl, Wl = o.instance_state()
+    g.set_instance_state(Xl, Wl)
+    g.set_weights(o.weights())
+
+
+@pytest.fixture(scope="module")
+def block1000():
+    """The 1,000-camera block after the oracle's first intersection, sub-block
+    copies moved by 2 cm and 2 % of the observations down-weighted (the state
+    of an iteration in the robust stage)."""
+    prob = synth.config(2)
+    o = oracle.Oracle(prob)
+    o.intersect()
+    rng = np.random.default_rng(11)
+    Xl, Wl = o.instance_state()
+    o.set_instance_state(Xl + rng.normal(0, 0.02, Xl.shape), Wl)
+    o.set_weights(np.where(rng.random(o.K) < 0.02, 1e-4, 1.0))
+    return prob, o
+
+
+def test_block1000_residuals_jacobians_costs_sigma0(block1000):
+    prob, o = block1000
+    g = rpba.Rpba(prob, precision=1)
+    sync_state(o, g)
+    np.testing.assert_allclose(g.residuals(), o.residuals(), rtol=0, atol=1e-9)
+    Jc_o, Jx_o = o.jacobians()
+    Jc_g, Jx_g = g.jacobians()
+    assert rel_frob(Jc_g, Jc_o, (1, 2)).max() <= 1e-5
+    assert rel_frob(Jx_g, Jx_o, (1, 2)).max() <= 1e-5
+    Fo = np.array([o.sub_cost(l) for l in range(o.L)])
+    np.testing.assert_allclose(g.sub_costs(), Fo, rtol=1e-6)
+    s_g, rms_g = g.sigma0()
+    assert s_g == pytest.approx(o.sigma0(), rel=1e-6)
+    assert rms_g == pytest.approx(o.rms(), rel=1e-6)
+    g.close()
+
+
+def test_block1000_reduced_camera_systems(block1000):
+    """Every sub-block's RCS (60..200 cameras) and right-hand side."""
+    prob, o = block1000
+    g = rpba.Rpba(prob, precision=1)
+    sync_state(o, g)
+    for l in range(o.L):
+        So, yo = o.rcs(l, 1e-4)
+        Sg, yg = g.rcs(l, 1e-4)
+        low = np.tril(np.ones_like(So, dtype=bool))
+        assert np.abs(Sg[low] - So[low]).max() <= 2e-5 * np.abs(So).max(), l
+        assert np.abs(yg - yo).max() <= 2e-4 * np.abs(yo).max(), l
+    g.close()
+
+
+def test_block1000_lm_step_chosen_solver(block1000):
+    """The benchmark's form (FP32 bulk, auto solver = float-float block-Jacobi
+    PCG on 8 sub-blocks): camera and point steps against the oracle's Cholesky
+    step at the FP32 assembly's tolerance, the true relative residual of each
+    sub-block's PCG solution against the GPU's own RCS at pcg_tol plus the
+    float-float rounding, and the same accept/reject decisions."""
+    prob, o = block1000
+    g = rpba.Rpba(prob, precision=1, solver=4)
+    assert g.resolved_options().solver == 1
+    sync_state(o, g)
+    lam = 1e-4
+    systems = []
+    for l in range(g.L):
+        S, y = g.rcs(l, lam)
+        systems.append((np.tril(S) + np.tril(S, -1).T, y))
+    acc, Fb, Ft, dc, dx = g.lm_step(lam)
+    it, rr = g.solver_stats()
+    assert np.all(it > 0) and np.all(rr <= g.options.pcg_tol)
+    off = 0
+    _, isub = o.instances()
+    o2 = oracle.Oracle(prob)  # lm_step moves the oracle's state: use a copy per call
+    for l in range(o.L):
+        S, y = systems[l]
+        n = y.size
+        dcl = dc[off:off + n]
+        res = np.linalg.norm(S @ dcl - y) / np.linalg.norm(y)
+        fp = 1e-12 * np.linalg.norm(np.abs(S) @ np.abs(dcl)) / np.linalg.norm(y)
+        assert res <= g.options.pcg_tol + fp, (l, res, fp)
+        o2.set_cameras(o.cameras())
+        X, a = o.points()
+        o2.set_points(X, a)
+        o2.set_instance_state(*o.instance_state())
+        o2.set_weights(o.weights())
+        r, fb, ft, dco, dxo = o2.lm_step(l, lam)
+        np.testing.assert_allclose(Fb[l], fb, rtol=1e-6)
+        assert np.abs(dcl - dco).max() <= 5e-3 * np.abs(dco).max(), l
+        assert np.abs(dx[isub == l] - dxo).max() <= 5e-3 * np.abs(dxo).max(), l
+        np.testing.assert_allclose(Ft[l], ft, rtol=1e-4)
+        assert acc[l] == r
+        off += n
+    g.close()
+
+
+def test_block1000_intersection_covariance_and_scales(block1000):
+    prob, o0 = block1000
+    o = oracle.Oracle(prob)
+    g = rpba.Rpba(prob, precision=1)
+    o.set_cameras(o0.cameras())
+    X, a = o0.points()
+    o.set_points(X, a)
+    o.set_instance_state(*o0.instance_state())
+    o.set_weights(o0.weights())
+    sync_state(o, g)
+    # per-camera robust scale at the shared state
+    so = o.camera_scale()
+    np.testing.assert_allclose(g.camera_scale(), so, rtol=1e-6, atol=1e-12)
+    # TP intersection from the shared state (Eq. bars)
+    o.intersect(tp_only=True)
+    g.intersect_points(True)
+    Xo, ao = o.points()
+    Xg, ag = g.points()
+    assert (ao != ag).mean() <= 0.001
+    act = (ao == 1) & (ag == 1)
+    err = np.abs(Xg[act] - Xo[act]).max(1)
+    assert np.quantile(err, 0.99) <= 3e-5
+    # covariance of every active point at the oracle's state
+    sync_state(o, g)
+    ids = np.nonzero(ao == 1)[0]
+    Co = o.covariance(ids)
+    Cg = g.covariance(ids)
+    assert rel_frob(Cg, Co, (1, 2)).max() <= 1e-4
+    g.close()
+
+
+def _many_obs_per_camera(n_points):
+    # 6 cameras that all see the whole scene, each point in 4 of them: every
+    # camera holds about 2/3 of the observations
+    return synth.tiny(seed=21, nx=3, ny=2, n_points=n_points, opp=4, runs=[3, 3])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_camera_scale_above_48kb_of_shared_memory(precision):
+    """About 8,000 observations per camera: 16,000 whitened components, i.e.
+    64 KB of 32-bit keys (FP32 form) and 128 KB of padded 64-bit keys (FP64
+    form), both above the 48 KB default and launched with opt-in shared
+    memory."""
+    prob = _many_obs_per_camera(12000)
+    per_cam = np.bincount(prob["obs_cam"])
+    assert per_cam.max() > 6144
+    o = oracle.Oracle(prob)
+    o.intersect()
+    g = rpba.Rpba(prob, precision=precision)
+    sync_state(o, g)
+    so = o.camera_scale()
+    np.testing.assert_allclose(g.camera_scale(), so, rtol=1e-12 if precision == 0 else 1e-6, atol=1e-12)
+    g.close()
+
+
+@pytest.mark.parametrize("precision,n_points", [(0, 16000), (1, 40000)])
+def test_camera_scale_refuses_cameras_beyond_its_shared_memory(precision, n_points):
+    """Above 200 KB of keys (FP64 form: more than 8,192 observations on one
+    camera; FP32 form: more than 25,600) the per-camera median is refused with
+    RPBA_ERR_INVALID_ARG before any launch, and the context stays usable."""
+    prob = _many_obs_per_camera(n_points)
+    g = rpba.Rpba(prob, precision=precision)
+    with pytest.raises(rpba.RpbaError) as e:
+        g.camera_scale()
+    assert e.value.status == 1
+    s0, _ = g.sigma0()
+    assert np.isfinite(s0)
+    g.close()

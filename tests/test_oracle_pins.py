@@ -533,6 +533,135 @@ def test_single_subblock_is_ordinary_bundle_adjustment():
     assert np.abs(g).max() < 1e-6 * np.abs(Na).max()
 
 
+def test_lambda_policy_hand_cases():
+    """Reading of Sec. 5.5 (lambda fixed in the paper, silent on rejection):
+    x10 after a rejected step, /10 after an accepted one, never below lambda0."""
+    assert oracle.lambda_next(1e-4, 0, 1e-4) == pytest.approx(1e-3, rel=1e-15)
+    assert oracle.lambda_next(1e-2, 0, 1e-4) == pytest.approx(1e-1, rel=1e-15)
+    assert oracle.lambda_next(1e-2, 1, 1e-4) == pytest.approx(1e-3, rel=1e-15)
+    assert oracle.lambda_next(1e-4, 1, 1e-4) == 1e-4
+    assert oracle.lambda_next(5e-4, 1, 1e-4) == 1e-4  # 5e-5 is floored at lambda0
+    assert oracle.lambda_next(1e-3, 1, 1e-3) == 1e-3
+
+
+@pytest.mark.parametrize("values,grace,stop", [
+    ([10.0, 5.0, 4.99, 4.98], 1, 3),          # one grace iteration, then stop
+    ([10.0, 5.0, 4.99, 4.0, 3.99], 1, 4),     # the grace is not given back by a later improvement
+    ([10.0, 9.95], 0, 1),                     # no grace: the first small ratio stops
+    ([10.0, 10.5, 10.6], 1, 2),               # a worse value is a ratio below 1 (best stays 10)
+    ([10.0, 10.5, 9.0, 8.95], 1, 3),          # ... and the best so far, not the last value, is the reference
+    ([10.0, 9.0, 8.0, 7.0], 1, None),         # ratios of 1.11..1.14 never stop
+    ([1.01, 1.0, 0.9999], 0, 2),              # a ratio of exactly 1.01 is not below 1.01; 1.0001 is
+])
+def test_ratio_rule_hand_sequences(values, grace, stop):
+    """The stop rule of Sec. 5.5 for the inner (F_l) and the outer (sigma_0)
+    loop on hand-worked sequences: ratio = best so far / new value, below
+    1.01 spends the one grace iteration, then stops."""
+    assert oracle.ratio_rule_sequence(values, 1.01, grace) == stop
+
+
+def _dense_lm_loop(o2, prob, lambda0=1e-4, stop_ratio=1.01, grace=1, max_inner=20, max_reject=6):
+    """An LM loop over one sub-block written with dense numpy algebra: the
+    normal equations J^T W J of all unknowns (cameras and points), the damping
+    lambda diag(N), np.linalg.solve, the trial update R <- exp([dw]x) R (scipy),
+    the cost of Eq. bact in numpy, acceptance on a decrease, and the damping
+    and stop rules of Sec. 5.5 as read (x10 on reject, /10 floored at lambda0
+    on accept; best/current below 1.01 after one grace iteration). o2 only
+    holds the state and projects points (its projection is pinned above)."""
+    lam, best, g_left, rejects = lambda0, None, grace, 0
+    F = sub_cost_numpy(o2, prob, 0, o2.cameras(), o2.instance_state()[0])
+    best = F
+    lams, accs, Fs = [], [], []
+    it = 0
+    while it < max_inner:
+        it += 1
+        Na, g, nC = dense_subblock_system(o2, prob, 0, lam)
+        delta = np.linalg.solve(Na, -g)
+        poses0 = o2.cameras()
+        Xl0, Wl = o2.instance_state()
+        poses_t = poses0.copy()
+        for n, i in enumerate(o2.sub_cameras(0)):
+            Rt = Rotation.from_rotvec(delta[6 * n:6 * n + 3]).as_matrix() @ pose_R(poses0[i])
+            poses_t[i, :3] = Rotation.from_matrix(Rt).as_rotvec()
+            poses_t[i, 3:] = poses0[i, 3:] + delta[6 * n + 3:6 * n + 6]
+        Xl_t = Xl0 + delta[nC:].reshape(-1, 3)
+        Ft = sub_cost_numpy(o2, prob, 0, poses_t, Xl_t)
+        lams.append(lam)
+        accepted = Ft < F
+        accs.append(int(accepted))
+        Fs.append(Ft if accepted else F)
+        if not accepted:
+            lam *= 10.0
+            rejects += 1
+            if rejects > max_reject:
+                break
+            continue
+        rejects = 0
+        o2.set_cameras(poses_t)
+        o2.set_instance_state(Xl_t, Wl)
+        F = Ft
+        lam = max(lam / 10.0, lambda0)
+        ratio = best / F
+        best = min(best, F)
+        if ratio < stop_ratio:
+            if g_left > 0:
+                g_left -= 1
+            else:
+                break
+    return it, np.array(lams), np.array(accs), np.array(Fs)
+
+
+@pytest.mark.parametrize("seed,rot_sigma,pos_sigma,lambda0,rejects", [
+    (42, 0.01, 0.3, 1e-4, False),
+    (43, 0.01, 0.3, 1e-4, False),
+    # far from the minimum with little damping: rejected steps raise lambda
+    # four times in a row, then accepted steps lower it again
+    (50, 0.1, 2.0, 1e-6, True),
+])
+def test_single_subblock_lm_loop_equals_dense_lm(seed, rot_sigma, pos_sigma, lambda0, rejects):
+    """L = 1 (no TPs): the oracle's whole LM loop (orc_sub_lm) is ordinary
+    bundle adjustment. It takes the same number of iterations, the same
+    damping sequence and the same accept/reject decisions as a dense numpy LM
+    loop with the same policy, and its cost after every step agrees to 1e-10
+    (at lambda0 = 1e-4; scaled by 1e-4 / lambda0 below it).
+    Parameters are compared to 1e-6: with L = 1 the 7-DoF gauge is left to the
+    damping alone (cond ~ 1e8), so rounding moves them along the gauge
+    without changing the cost."""
+    prob = with_weights(synth.tiny(seed=seed, runs=[6], n_points=40, rot_sigma=rot_sigma, pos_sigma=pos_sigma,
+                                   pt_sigma=max(0.1, pos_sigma)), seed)
+    o = oracle.Oracle(prob)
+    o.intersect()
+    o2 = oracle.Oracle(prob)
+    o2.intersect()
+    _, Wl = o.instance_state()
+    assert o.L == 1 and np.all(Wl == 0.0)
+    it, lam, acc, F = o.sub_lm_trace(0, lambda0=lambda0)
+    it_d, lam_d, acc_d, F_d = _dense_lm_loop(o2, prob, lambda0=lambda0)
+    assert it == it_d and it >= 3
+    assert bool((acc != 1).any()) == rejects
+    np.testing.assert_array_equal(acc == 1, acc_d == 1)
+    np.testing.assert_allclose(lam, lam_d, rtol=1e-15)
+    # the gauge's eigenvalues of the damped system scale with lambda0, so the
+    # rounding in the step grows with 1 / lambda0: 1e-10 at the default 1e-4
+    np.testing.assert_allclose(F, F_d, rtol=1e-10 * (1e-4 / lambda0))
+    np.testing.assert_allclose(o.cameras(), o2.cameras(), atol=1e-6)
+    np.testing.assert_allclose(o.instance_state()[0], o2.instance_state()[0], atol=1e-6)
+
+
+def test_outer_loop_stops_where_the_ratio_rule_says():
+    """The outer loop of orc_run (Sec. 5.5) stops at the first sigma_0 the
+    stop rule rejects, counted on its own sigma_0 history from sigma_0 after
+    the first intersection (robust stage off, so no restart)."""
+    prob = synth.config(1)
+    keep = ~prob["outlier"]
+    for k in ("obs_cam", "obs_point", "obs_xy"):
+        prob[k] = prob[k][keep]
+    rep = oracle.Oracle(prob).run(robust=0)
+    seq = [rep["sigma0_initial"]] + rep["sigma0_hist"]
+    stop = oracle.ratio_rule_sequence(seq, 1.01, 1)
+    assert stop == rep["outer"] and rep["outer"] < 30
+
+
 def test_robust_stage_finds_injected_outliers():
     prob = synth.config(1)
     o = oracle.Oracle(prob)

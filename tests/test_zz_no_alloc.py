@@ -58,3 +58,15 @@ def test_sigma0_noalloc_rejects_blocks_above_its_limit():
     with pytest.raises(rpba.RpbaError) as e:
         rpba.rpba_sigma0_noalloc(1, 1, MAX_OBS + 1, 1, 1, 1, 1, None, 1, 1, 1)
     assert e.value.status == 1  # RPBA_ERR_INVALID_ARG, nothing launched
+    # observations that reference no camera or no point: rejected on the host.
+    # Every array is a real device buffer large enough for one camera, point
+    # and observation, so no launch could read outside memory it owns.
+    import torch
+    dev = torch.device("cuda")
+    buf = torch.zeros(64, dtype=torch.float64, device=dev)
+    idx = torch.zeros(4, dtype=torch.int32, device=dev)
+    for n_cams, n_points in ((0, 1), (1, 0)):
+        with pytest.raises(rpba.RpbaError) as e:
+            rpba.rpba_sigma0_noalloc(n_cams, n_points, 1, buf.data_ptr(), buf.data_ptr(), buf.data_ptr(),
+                                     buf.data_ptr(), None, idx.data_ptr(), idx.data_ptr(), buf.data_ptr())
+        assert e.value.status == 1
