@@ -1,27 +1,32 @@
 #!/usr/bin/env python
 """Benchmark of the RPBA hot path on GB300 (one JSON line on stdout).
 
-Workload: the 1,000-camera / 100k-point / ~600k-observation block with 8
-uneven sub-blocks (60..200 cameras), nadir + 30 deg oblique views, 0.5 px
-noise, 2 % outliers (seeded synthetic data).
+Workload (default): the 10,000-camera / 4M-point / 20M-observation block with
+64 sub-blocks, nadir + 45 deg oblique wide-baseline views, 1 px noise, 5 %
+outliers (seeded synthetic data; --config selects the smaller blocks).
 
-A step is one pass of the whole hot path over that block: one lock-step
-Levenberg-Marquardt iteration of every sub-block (residuals, Jacobians,
-normal equations with the TP control term, Schur complement, RCS solve,
-back-substitution, trial cost, accept/reject), the exchange, the robust
-weights (per-camera MAD) and the intersection of all tie points with their
-covariance-derived weights. value = observations processed per second per
-LM iteration.
+A step is one pass of the whole hot path over that block: one steady-state
+outer iteration of the method, i.e. one lock-step Levenberg-Marquardt
+iteration of every sub-block (residuals, Jacobians, normal equations with the
+TP control term, Schur complement, RCS solve, back-substitution, trial cost,
+accept/reject), the exchange, the robust weights (per-camera MAD) and the
+intersection of all tie points with their covariance-derived weights, and
+sigma_0. value = observations per second per LM iteration, where the
+observations counted are those active after the first (FP64) intersection,
+the same number in both arms.
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload instead.
+workload instead (one LM iteration of as many sub-blocks as there are host
+cores, one thread per sub-block, per step).
 """
 
 from __future__ import annotations
 
 import argparse
+import concurrent.futures as cf
 import json
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -38,24 +43,47 @@ WORKLOADS = {
     2: "rpba-1000cam-100kpt-600kobs-8sub (25x40 grid, nadir+30deg oblique, 0.5px, 2% outliers)",
     3: "rpba-64blocks-7748cam-222kpt-1.0Mobs-304sub (20..400 cams/block, 2..8 sub-blocks, 0.5px, 2% outliers)",
     4: "rpba-5000cam-1Mpt-3.4Mobs-32sub (50x100 strips, 60% forward / 30% side overlap, 0.5px, 5% outliers)",
-    5: "rpba-10000cam-4Mpt-20Mobs-64sub (100x100 grid, nadir+45deg oblique, 1px, 5% outliers)",
+    5: "rpba-10000cam-4Mpt-20Mobs-64sub (100x100 grid, nadir+45deg oblique wide baseline, 1px, 5% outliers)",
 }
-# a bounded sample of the oracle's work on the large blocks (seconds of CPU)
-CPU_SAMPLE_BUDGET_S = {4: 15.0, 5: 15.0}
+DEFAULT_CONFIG = 5
 TARGETS = os.path.join(ROOT, "tests", "golden", "oracle_targets.json")
+FORMS = {"chosen": (1, 4), "plain": (0, 0)}  # (precision, solver); solver 4 = auto
+TTR_REPEATS = 3  # fresh runs per form for the time to the oracle's RMS (median reported)
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--config", type=int, default=2)
+    p.add_argument("--config", type=int, default=DEFAULT_CONFIG)
     p.add_argument("--precision", type=int, default=1)
     p.add_argument("--solver", type=int, default=4)
+    p.add_argument("--chol-tc", type=int, default=1, help="direct solver's FP32 factorisation on the tensor cores")
     p.add_argument("--no-extras", action="store_true", help="skip e2e / time-to-RMS / cpu legs")
     return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# host description
+# ---------------------------------------------------------------------------
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
 
 
 # ---------------------------------------------------------------------------
@@ -66,8 +94,9 @@ class ClockSampler:
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index=0):
+    def __init__(self, index=0, interval_ms=50):
         self.index = index
+        self.interval_ms = interval_ms
         self.proc = None
         self.lines = []
 
@@ -75,7 +104,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.interval_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
@@ -93,105 +122,42 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 7:
-                continue
-            try:
-                sm.append(float(f[0])); smax.append(float(f[1]))
-            except ValueError:
-                continue
-            for n, v in zip(names, f[3:7]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        return {"sm_mhz": float(np.median(sm)) if sm else None,
-                "sm_max_mhz": float(max(smax)) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return summarise_clocks(self.lines)
+
+
+def summarise_clocks(lines):
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 7:
+            continue
+        try:
+            sm.append(float(f[0]))
+            smax.append(float(f[1]))
+        except ValueError:
+            continue
+        for n, v in zip(names, f[3:7]):
+            if v.lower() == "active":
+                reasons.add(n)
+    return {"sm_mhz": float(np.median(sm)) if sm else None,
+            "sm_max_mhz": float(max(smax)) if smax else None,
+            "reasons": sorted(reasons), "samples": len(sm)}
 
 
 # ---------------------------------------------------------------------------
 # roofline bookkeeping
 # ---------------------------------------------------------------------------
-def fp64_peak_gflops():
-    """Nominal dense FP64 rate of a GB300 (1.25 TFLOP/s, 152 SMs at 2.07 GHz)."""
-    return 1250.0
-
-
-def cholesky_update_flops(sub_sizes, tile=32):
-    """Algorithmic flops of the trailing updates of one blocked factorisation
-    of every sub-block RCS: sum_k tile * m_k (m_k + 1), m_k = n - tile (k + 1)."""
-    tot = 0
-    for n in sub_sizes:
-        k = 0
-        while n - tile * (k + 1) > 0:
-            m = n - tile * (k + 1)
-            tot += tile * m * (m + 1)
-            k += 1
-    return tot
-
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+FP32_PEAK_SOURCE = "FP32 CUDA-core rate from 152 SMs x 128 lanes x 2 flops x 2070 MHz"
 
 # DRAM bytes per unit of work from the ncu captures summarised under profiles/
-# (dram__bytes_read.sum + dram__bytes_write.sum); None once a kernel has changed
-NCU_TRAFFIC_PER_TILE = {
-    # profiles/k_chol_update_f32_cfg3_64blocks.md: 2.81 MB over 543 tiles
-    "k_chol_update_f32": 2.809088e6 / 543,
+# (dram__bytes_read.sum + dram__bytes_write.sum); a kernel is removed from this
+# table when it changes after its capture
+NCU_TRAFFIC_PER_UNIT = {
+    # profiles/k_pcg_symv_ff_cfg4_5000cam.md: 118.88 + 3.13 MB over 14,688 lower tiles
+    "k_pcg_symv_ff": ((118.880768 + 3.132160) * 1e6 / 14688, "tile", "profiles/k_pcg_symv_ff_cfg4_5000cam.md"),
 }
-
-
-def update_tiles(sub_sizes, tile=32):
-    """Trailing-update tiles (CTAs) of one factorisation of every sub-block RCS."""
-    tot = 0
-    for n in sub_sizes:
-        T = (n + tile - 1) // tile
-        for k in range(T - 1):
-            rem = T - k - 1
-            tot += rem * (rem + 1) // 2
-    return tot
-
-
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
-
-
-def roofline(prof, steps, n_sub_sizes, K, peaks, mem_bound_bytes, symv_flops=0.0, alu_flops=None):
-    # the dominant kernel, event-timed over the timed region
-    name, (launches, ms) = max(prof.items(), key=lambda kv: kv[1][1])
-    per_launch_s = ms / 1e3 / max(launches, 1)
-    if alu_flops and name in alu_flops:
-        achieved = alu_flops[name] / per_launch_s / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP32 CUDA-core rate from 152 SMs x 128 lanes x 2 flops x 2070 MHz",
-                "launches": launches, "avg_launch_ms": per_launch_s * 1e3}
-    if name == "k_pcg_symv" and symv_flops > 0 and name not in mem_bound_bytes:
-        achieved = symv_flops / max(launches, 1) / per_launch_s / 1e12
-        peak = fp64_peak_gflops() / 1e3
-        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": "nominal FP64 rate (1.25 TFLOP/s); FMA-chain probe 1.2 TFLOP/s",
-                "launches": launches, "avg_launch_ms": per_launch_s * 1e3}
-    if name in ("k_chol_update_f64", "k_chol_update_f32"):
-        work = cholesky_update_flops(n_sub_sizes) * steps / max(launches, 1)
-        achieved = work / per_launch_s / 1e12
-        f64 = name.endswith("f64")
-        peak = fp64_peak_gflops() / 1e3 if f64 else 74.6
-        traffic = None
-        if name in NCU_TRAFFIC_PER_TILE:
-            traffic = NCU_TRAFFIC_PER_TILE[name] * update_tiles(n_sub_sizes) * steps / max(launches, 1)
-        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "traffic_note": "ncu DRAM bytes per tile scaled to the average launch" if traffic else None,
-                "peak_source": "FP64 1.2 / FP32 74.6 TFLOP/s measured by an FMA-chain probe on this GB300",
-                "launches": launches, "avg_launch_ms": per_launch_s * 1e3}
-    bytes_per_launch = mem_bound_bytes.get(name)
-    if bytes_per_launch is None:
-        return {"kernel": name, "bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": None, "traffic": None, "launches": launches, "avg_launch_ms": per_launch_s * 1e3}
-    achieved = bytes_per_launch / per_launch_s / 1e9
-    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": "measured",
-            "launches": launches, "avg_launch_ms": per_launch_s * 1e3}
 
 
 def schur_pairs(prob):
@@ -201,6 +167,49 @@ def schur_pairs(prob):
     key = np.asarray(prob["obs_point"]).astype(np.int64) * (int(sub.max()) + 1) + sub
     _, n = np.unique(key, return_counts=True)
     return float(np.sum(n * (n - 1) // 2))
+
+
+def obs_stream_bytes(has_winv):
+    """Bytes per observation every FP32-form per-observation pass streams: the
+    point and camera indices (4 + 4), the position hi + lo (8 + 8), the robust
+    weight (4) and C^-1 when given (12)."""
+    return 28 + (12 if has_winv else 0)
+
+
+def kernel_models(K, N, P, M, has_winv, pairs):
+    """Algorithmic bytes (HBM-bound kernels) or flops (ALU-bound) of one launch
+    of each FP32-form kernel of the step, from the data it must read and write
+    once: K observations, N points, P instances, M cameras. Camera records are
+    128 B each. Lower bounds: a kernel that gathers the same word twice is
+    charged once."""
+    ob = obs_stream_bytes(has_winv)
+    return {
+        "k_obs_sigma_f": ("hbm", K * ob + N * 25 + M * 128),
+        "k_cost_chunks_f": ("hbm", K * ob + P * 72 + M * 128),
+        "k_robust_weights_f": ("hbm", K * (ob + 4) + N * 25 + M * 132),
+        "k_camera_mad_u32": ("hbm", K * ob + N * 25 + M * 136),
+        "k_isect_fused_f": ("hbm", K * ob + N * 48 + P * 24 + M * 128),
+        "k_camera_blocks_f32": ("hbm", K * ob + P * 60 + M * (128 + 432)),
+        "k_linearize_f32": ("hbm", K * ob + P * 132 + M * 128),
+        "k_backsub_f32": ("hbm", K * ob + P * 72 + M * 152),
+        # 6x6 product N_XC,a^T (Ninv N_XC,b) per point pair, Z = Ninv N_XC once per observation
+        "k_schur_seg": ("alu", 216.0 * pairs + 108.0 * K),
+    }
+
+
+def roofline_entry(name, launches, ms, bound, work, peaks, traffic=None, traffic_note=None):
+    per_launch_s = ms / 1e3 / max(launches, 1)
+    if bound == "alu":
+        achieved = work / per_launch_s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "peak_source": FP32_PEAK_SOURCE,
+                "launches": launches, "avg_launch_ms": per_launch_s * 1e3}
+    achieved = work / per_launch_s / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "traffic_note": traffic_note,
+            "algorithmic_bytes": work,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if not peaks.get("fallback") else "fallback",
+            "launches": launches, "avg_launch_ms": per_launch_s * 1e3}
 
 
 def load_peaks():
@@ -239,47 +248,105 @@ def train_preconditioner(stream):
     return w, time.perf_counter() - t0
 
 
-FORMS = {"chosen": (1, 4), "plain": (0, 0)}  # (precision, solver); solver 4 = auto
-TTR_REPEATS = 3  # fresh runs per form for the time to the oracle's RMS (median reported)
+def counted_obs(prob, active):
+    """Observations of active points: the work unit of the metric."""
+    return int(np.asarray(active)[np.asarray(prob["obs_point"])].astype(bool).sum())
 
 
 # ---------------------------------------------------------------------------
-# reference arm: the FP64 CPU oracle
+# the FP64 CPU oracle (reference arm and CPU baseline)
 # ---------------------------------------------------------------------------
-def oracle_step_sample(prob, budget_s=None):
-    """One bounded sample of the step on the CPU oracle: one LM iteration of
-    every sub-block, the exchange, robust weights and the TP intersection.
-    With a budget (large blocks): the LM iterations of the first sub-blocks
-    until the budget is spent, and the observations of those sub-blocks.
-    Returns (seconds, observations)."""
+def oracle_setup(prob):
+    """The oracle after its first intersection (untimed) and the observations
+    of active points per sub-block."""
     import oracle
     o = oracle.Oracle(prob)
     o.intersect()
     _, act = o.points()
-    if budget_s is not None:
-        sub_of_cam = np.asarray(prob["cam_subblock"])
-        obs_sub = sub_of_cam[np.asarray(prob["obs_cam"])]
-        active_obs = act[np.asarray(prob["obs_point"])] == 1
-        dt, kk = 0.0, 0
-        for l in range(o.L):
-            t0 = time.perf_counter()
-            o.lm_step(l, 1e-4)
-            dt += time.perf_counter() - t0
-            kk += int(np.sum(active_obs & (obs_sub == l)))
-            if dt > budget_s:
-                break
-        return dt, kk
+    sub_of_obs = np.asarray(prob["cam_subblock"])[np.asarray(prob["obs_cam"])]
+    active_obs = act[np.asarray(prob["obs_point"])] == 1
+    per_sub = np.bincount(sub_of_obs[active_obs], minlength=o.L)
+    return o, per_sub, int(active_obs.sum())
+
+
+def oracle_lm_iteration(o, subs, threads, lam=1e-4):
+    """One LM iteration of the listed sub-blocks, one host thread per
+    sub-block (the paper's scheme; the oracle's step of sub-block l touches
+    only l's cameras and instances, so the result equals the sequential
+    run's). Returns seconds."""
     t0 = time.perf_counter()
-    for l in range(o.L):
-        o.lm_step(l, 1e-4)
+    if threads <= 1 or len(subs) <= 1:
+        for l in subs:
+            o.lm_step(int(l), lam)
+    else:
+        with cf.ThreadPoolExecutor(max_workers=min(threads, len(subs))) as ex:
+            list(ex.map(lambda l: o.lm_step(int(l), lam), subs))
+    return time.perf_counter() - t0
+
+
+def run_reference(args, rank, world):
+    from paper_1910_08138_gb300 import synth
+    if rank != 0:
+        return
+    prob = synth.config(args.config)
+    o, per_sub, k_work = oracle_setup(prob)
+    threads = host_cores()
+    # each step: one LM iteration of `threads` sub-blocks in parallel, cycling
+    # through the block's sub-blocks from step to step
+    order = [l for l in range(o.L) if per_sub[l] > 0]
+    pos = 0
+
+    def step():
+        nonlocal pos
+        subs = [order[(pos + a) % len(order)] for a in range(min(threads, len(order)))]
+        pos = (pos + len(subs)) % len(order)
+        return oracle_lm_iteration(o, subs, threads), int(sum(per_sub[l] for l in subs))
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    times, kk = [], []
+    for _ in range(args.steps):
+        dt, k = step()
+        times.append(dt)
+        kk.append(k)
+    ms = 1e3 * float(np.mean(times))
+    value = float(np.sum(kk)) / float(np.sum(times))
+    sample = (f"per step one LM iteration of {min(threads, len(order))} of the {len(order)} sub-blocks "
+              f"(one host thread each, cycling through the block), FP64 oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "obs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.config], "n_obs_block": k_work, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "obs/s", "cores": min(threads, len(order)), "kind": "oracle",
+                             "sample": sample, "nproc": host_cores(), "cpu_model": cpu_model()},
+            "e2e": {"value": value, "unit": "obs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def oracle_full_step(prob, threads):
+    """The CPU baseline in our arm: the oracle's whole step on the same block
+    (one LM iteration of every sub-block, one host thread per sub-block up to
+    the core count; then the robust weights, the TP intersection and sigma_0,
+    single-threaded as the oracle is written). Returns (seconds, observations,
+    description)."""
+    o, per_sub, k_work = oracle_setup(prob)
+    subs = [l for l in range(o.L) if per_sub[l] > 0]
+    t0 = time.perf_counter()
+    oracle_lm_iteration(o, subs, threads)
+    t_lm = time.perf_counter() - t0
     o.robust_weights()
     o.intersect(tp_only=True)
+    o.sigma0()
     dt = time.perf_counter() - t0
-    _, act = o.points()
-    k_act = int(act[prob["obs_point"]].sum())
-    return dt, k_act
+    what = (f"one whole step of the FP64 oracle: LM iteration of all {len(subs)} sub-blocks on "
+            f"{min(threads, len(subs))} threads ({t_lm:.1f} s), then robust weights, TP intersection and "
+            f"sigma_0 on one thread ({dt - t_lm:.1f} s)")
+    return dt, k_work, what
 
 
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
 def replicas_aggregate(total_ms, obs_per_step, steps, world, device):
     """N independent replicas of the block (weak scaling, no collective on the
     data path): the job's time is the slowest rank's, its work that of all
@@ -294,34 +361,20 @@ def replicas_aggregate(total_ms, obs_per_step, steps, world, device):
     return total_ms, world * obs_per_step * steps / (total_ms / 1e3)
 
 
-def run_reference(args, rank, world):
-    from paper_1910_08138_gb300 import synth
-    if rank != 0:
-        return
-    prob = synth.config(args.config)
-    budget = CPU_SAMPLE_BUDGET_S.get(args.config)
-    for _ in range(max(args.warmup, 0) and 1):
-        oracle_step_sample(prob, budget)
-    times, kk = [], 0
-    for _ in range(args.steps):
-        dt, kk = oracle_step_sample(prob, budget)
-        times.append(dt)
-    ms = 1e3 * float(np.mean(times))
-    value = kk / (ms / 1e3)
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "obs/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.config], "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": "obs/s", "cores": 1, "kind": "oracle",
-                             "sample": "one LM iteration of all sub-blocks + robust weights + TP intersection, "
-                                       "whole block, single thread, per step"},
-            "e2e": {"value": value, "unit": "obs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+def symv_work(ctx, pcg_iters, n_sub):
+    """Algorithmic bytes of the float-float symmetric RCS product per launch:
+    8 B (hi + lo) per stored lower-tile entry of the live sub-blocks; during the
+    last LM iteration of a step sub-block l was live in iters[l] launches.
+    Returns (bytes per launch, live tiles per launch)."""
+    npad = [32 * ((n + 31) // 32) for n in n_sub]
+    tiles = [(n // 32) * (n // 32 + 1) // 2 for n in npad]
+    launches = sum(int(np.max(it)) for it in pcg_iters)
+    live_tiles = sum(float(np.dot(it, tiles)) for it in pcg_iters)
+    if not launches:
+        return None, None
+    return live_tiles * 1024 * 8 / launches, live_tiles / launches
 
 
-# ---------------------------------------------------------------------------
-# our arm
-# ---------------------------------------------------------------------------
 def run_ours(args, rank, world):
     import torch
 
@@ -333,33 +386,38 @@ def run_ours(args, rank, world):
     prob = synth.config(args.config)
     peaks = load_peaks()
     gnn_w, gnn_s = (train_preconditioner(stream) if args.solver == 3 else (None, None))
-    ctx = rpba.Rpba(prob, stream=stream, **bench_options(args.precision, args.solver, 1))
+    ctx = rpba.Rpba(prob, stream=stream, chol_tc=args.chol_tc, **bench_options(args.precision, args.solver, 1))
     if gnn_w is not None:
         ctx.set_gnn_weights(gnn_w)
     ctx.intersect()
-    solver = ctx.resolved_options().solver  # auto (4) resolved by the library
+    _, act0 = ctx.points()
+    K = counted_obs(prob, act0)  # the same count as the oracle's after its first intersection
     n_sub = [6 * len(ctx.sub_cameras(l)) for l in range(ctx.L)]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def step():
+        return ctx.outer_iteration(robust=True)
+
     # the last warm-up step times every kernel (the breakdown and the dominant
     # kernel); the timed steps time only the dominant kernel, so that event
     # records stay out of the rest of the step
     for _ in range(max(args.warmup - 2, 0)):
-        ctx.iterate(1)
+        step()
     ctx.profile_enable(True)
     flush.fill_(-1.0)
-    ctx.iterate(1)
-    prof_all, launches_all = ctx.profile_read()
+    step()
+    prof_all, _ = ctx.profile_read()
     ctx.profile_enable(False)
     dominant = max(prof_all.items(), key=lambda kv: kv[1][1])[0]
-    # the last warm-up step already runs with the timed steps' profiling, so
+    # the next warm-up step already runs with the timed steps' profiling, so
     # that the graphs it captures (event nodes for the dominant kernel only)
     # are the ones the timed steps replay
     ctx.profile_enable(True)
     ctx.profile_select(dominant)
     if args.warmup >= 2:
         flush.fill_(-2.0)
-        ctx.iterate(1)
-    solver = ctx.resolved_options().solver  # auto may have moved to the direct solve
+        step()
+    solver = ctx.resolved_options().solver
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -368,18 +426,16 @@ def run_ours(args, rank, world):
     clocks = ClockSampler(dev)
     clocks.start()
     times = []
-    k_act = None
     pcg_iters = []
     for s in range(args.steps):
         flush.fill_(float(s))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        rep = ctx.iterate(1)
+        step()
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
-        k_act = rep["active_obs"]
         if solver in (1, 3):
             pcg_iters.append(ctx.solver_stats()[0])
             solver = ctx.resolved_options().solver
@@ -387,61 +443,58 @@ def run_ours(args, rank, world):
     prof, launches = ctx.profile_read()
     ctx.profile_enable(False)
     ctx.profile_select(None)
-    total_ms, value = replicas_aggregate(float(np.sum(times)), k_act, args.steps, world, "cuda")
+    total_ms, value = replicas_aggregate(float(np.sum(times)), K, args.steps, world, "cuda")
     ms = total_ms / args.steps
-    # algorithmic bytes of the HBM-bound kernels per launch (FP32 form: 20 B/obs
-    # of observation data + per-observation 3x6 blocks written and read)
-    K = k_act
-    rs = 4 if args.precision == 1 else 8
-    mem_bytes = {
-        "k_linearize": K * (4 + 4 + 16 + 8 + 2 * 18 * rs),
-        "k_camera_blocks": K * (4 + 4 + 16 + 8 + 2 * 18 * rs + 24),
-        "k_inst_cost": K * (4 + 16 + 8) + ctx.P * 24,
-        "k_backsub": K * (4 + 18 * rs) + ctx.P * (24 * 2 + 9 * rs),
-    }
-    # symmetric RCS product of the PCG solvers: 2 n_pad^2 flops per live
-    # sub-block and launch; the last LM iteration of every step ran
-    # iters[l] launches for sub-block l
-    symv_flops = 0.0
-    if pcg_iters:
-        npad = [32 * ((n + 31) // 32) for n in n_sub]
-        symv_flops = sum(float(np.dot(it, np.square(npad))) * 2.0 for it in pcg_iters)
-        # CG step (block-Jacobi): per live sub-block of size n, x r p q read, x r
-        # written, z written, z p read and p written (10 n doubles) and the 6x6
-        # inverse blocks (48 B per entry)
-        step_bytes = sum(float(np.dot(it, n_sub)) * (10 * 8 + 48) for it in pcg_iters)
-        iters = sum(int(np.max(it)) for it in pcg_iters)
-        if iters and args.precision == 1 and solver == 1:
-            # float-float form: x, r, p pairs (8 B) read and written, q (8 B)
-            # read, z (4 B) written and read, the FP32 inverse blocks (24 B per
-            # entry); the product reads 8 B (hi + lo) per stored lower-tile entry
-            step_bytes = sum(float(np.dot(it, n_sub)) * (3 * 16 + 8 + 8 + 24) for it in pcg_iters)
-            tiles = [(n // 32) * (n // 32 + 1) // 2 for n in npad]
-            mem_bytes["k_pcg_symv"] = sum(float(np.dot(it, tiles)) * 1024 * 8 for it in pcg_iters) / iters
-        if iters:
-            mem_bytes["k_pcg_step"] = step_bytes / iters
-    # robust scale: per observation its indices, xy, the point and its active flag
-    mem_bytes["k_camera_mad"] = K * (4 + 4 + 16 + 24 + 1) + ctx.M * 9 * 8
-    # off-diagonal Schur blocks (FP32 form): per point pair the 6x6 product
-    # N_XC,a^T (Ninv N_XC,b), 216 flops, plus Z = Ninv N_XC once per observation,
-    # 108 flops (pairs of the active instances at the start of the step)
-    alu_flops = {"k_schur_seg": 216.0 * schur_pairs(prob) + 108.0 * K} if args.precision == 1 else None
-    roof = roofline({dominant: prof.get(dominant, (0, 0.0))}, args.steps, n_sub, K, peaks, mem_bytes,
-                    symv_flops=symv_flops, alu_flops=alu_flops)
+
+    # rooflines: the dominant kernel over the timed region; the other hot
+    # kernels from the fully event-timed last warm-up step
+    has_winv = prob.get("obs_winv") is not None
+    models = kernel_models(K, ctx.N, ctx.P, ctx.M, has_winv, schur_pairs(prob)) if args.precision == 1 else {}
+    sbytes, live_tiles = symv_work(ctx, pcg_iters, n_sub) if pcg_iters else (None, None)
+    if sbytes is not None:
+        models["k_pcg_symv_ff" if args.precision == 1 else "k_pcg_symv"] = ("hbm", sbytes)
+
+    def entry(name, launches_, ms_):
+        if name not in models:
+            return {"kernel": name, "bound": None, "achieved": None, "frac": None, "launches": launches_,
+                    "avg_launch_ms": ms_ / max(launches_, 1)}
+        bound, work = models[name]
+        traffic, note = None, None
+        if name in NCU_TRAFFIC_PER_UNIT and name == "k_pcg_symv_ff" and live_tiles:
+            per, unit, src = NCU_TRAFFIC_PER_UNIT[name]
+            traffic = per * live_tiles
+            note = f"ncu DRAM bytes per {unit} ({src}) x {live_tiles:.0f} live tiles per launch"
+        return roofline_entry(name, launches_, ms_, bound, work, peaks, traffic, note)
+
+    roof = entry(dominant, *prof.get(dominant, (0, 0.0)))
+    step_ms_all = sum(v[1] for v in prof_all.values())
+    hot = []
+    for name, (la, kms) in sorted(prof_all.items(), key=lambda kv: -kv[1][1]):
+        if kms < 0.02 * step_ms_all:
+            continue
+        e = entry(name, la, kms)
+        e["share"] = kms / step_ms_all
+        hot.append(e)
     kernels = {k: {"launches": v[0], "ms": round(v[1], 4)}
                for k, v in sorted(prof_all.items(), key=lambda kv: -kv[1][1])}
+    solver_names = {0: "FP64 Cholesky", 1: "block-Jacobi PCG" + (" (float-float)" if args.precision == 1 else " (FP64)"),
+                    2: "FP32 Cholesky + FP64 refinement", 3: "PCG, learned preconditioner"}
     line = {"metric": METRIC, "value": value, "unit": "obs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == 1 else "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.config], "precision": "mixed FP32/FP64" if args.precision == 1 else "FP64",
-                       "solver": {0: "FP64 Cholesky", 1: "FP64 PCG, block-Jacobi", 2: "FP32 Cholesky + FP64 refinement",
-                                  3: "FP64 PCG, learned preconditioner"}.get(solver)
+            "config": {"workload": WORKLOADS[args.config],
+                       "precision": "mixed FP32/FP64" if args.precision == 1 else "FP64",
+                       "solver": solver_names.get(solver)
                        + (" (auto: PCG for up to 64 sub-blocks while a solve takes at most 48 CG iterations,"
                           " else the direct solve)" if args.solver == 4 else ""),
-                       "l2": "flushed between steps (256 MB write)", "n_obs": K, "subblocks": ctx.L,
-                       "step": "1 LM iteration of all sub-blocks + exchange + robust weights + TP intersection",
+                       "l2": "flushed between steps (256 MB write)", "n_obs": K,
+                       "n_obs_note": "observations of points active after the first (FP64) intersection; the "
+                                     "reference arm counts the same",
+                       "subblocks": ctx.L,
+                       "step": "1 steady-state outer iteration: 1 LM iteration of all sub-blocks + exchange + "
+                               "robust weights + TP intersection + sigma_0",
                        "parallelism": f"replicas x{world}"},
-            "roofline": roof, "gpu_launches": launches,
+            "roofline": roof, "hot_kernels": hot, "gpu_launches": launches,
             "gpu_launches_per_step": launches / args.steps, "clocks": clk,
             "kernels_last_warmup_step": kernels}
     if gnn_w is not None:
@@ -462,12 +515,12 @@ def extras(args, prob, ctx, stream, K, gnn_w=None):
     cams = np.ascontiguousarray(ctx.cameras())
     X, act = ctx.points()
     times = []
-    for s in range(max(3, args.steps // 2)):
+    for s in range(max(3, min(args.steps, 20) // 2)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx.set_cameras(cams)
         ctx.set_points(X, act)
-        rep = ctx.iterate(1)
+        ctx.outer_iteration(robust=True)
         cams = ctx.cameras()
         X, act = ctx.points()
         torch.cuda.synchronize()
@@ -484,7 +537,7 @@ def extras(args, prob, ctx, stream, K, gnn_w=None):
         pass
     ttr = {}
     if target is None:
-        out["time_to_oracle_rms"] = {"skipped": "no stored oracle RMS for this block (the oracle's whole run is too long)"}
+        out["time_to_oracle_rms"] = {"skipped": "no stored oracle RMS for this block"}
     for form, (prec, solver) in (() if target is None else
                                  (("chosen", (args.precision, args.solver)), ("plain", FORMS["plain"]))):
         runs = []
@@ -520,13 +573,12 @@ def extras(args, prob, ctx, stream, K, gnn_w=None):
         if ttr["plain"]["seconds"] > 0:
             ttr["chosen_speedup_vs_plain"] = ttr["plain"]["seconds"] / ttr["chosen"]["seconds"]
         out["time_to_oracle_rms"] = ttr
-    # CPU oracle on a bounded sample of the same workload
-    budget = CPU_SAMPLE_BUDGET_S.get(args.config)
-    dt, kk = oracle_step_sample(prob, budget)
-    what = ("LM iterations of the first sub-blocks" if budget else
-            "one LM iteration of all sub-blocks + robust weights + TP intersection")
-    out["cpu_baseline"] = {"value": kk / dt, "unit": "obs/s", "cores": 1, "kind": "oracle",
-                           "sample": f"{what} ({kk} obs), single thread, {dt:.1f} s"}
+    # CPU oracle: one whole step of the same block on the host cores
+    threads = host_cores()
+    dt, kk, what = oracle_full_step(prob, threads)
+    out["cpu_baseline"] = {"value": kk / dt, "unit": "obs/s", "cores": min(threads, ctx.L), "kind": "oracle",
+                           "sample": f"{what}; {kk} observations, {dt:.1f} s",
+                           "nproc": host_cores(), "cpu_model": cpu_model()}
     return out
 
 

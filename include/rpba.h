@@ -110,6 +110,10 @@ typedef struct {
   double pcg_tol;        /* relative residual of the PCG solve, 1e-8 */
   int32_t pcg_max_iter;  /* PCG iteration cap, 500 */
   int32_t ir_steps;      /* refinement passes of solver 2 after the first solve, 2 */
+  int32_t chol_tc;       /* solver 2's FP32 factorisation: 1 (default) left-looking with its
+                            updates on the tensor cores (tcgen05.mma kind::tf32, each factor
+                            entry split into three TF32 pieces, six products: FP32 accuracy),
+                            operands staged by TMA; 0 right-looking on the CUDA cores */
   /* optional device allocator (NULL: cudaMalloc / cudaFree) */
   void *(*dev_alloc)(size_t bytes, void *user);
   void (*dev_free)(void *ptr, void *user);
@@ -156,6 +160,31 @@ rpba_status rpba_intersect(rpba_ctx *ctx);
  * rpba_intersect first if it has not been run. `report` may be NULL. */
 rpba_status rpba_iterate(rpba_ctx *ctx, int32_t max_outer, rpba_report *report);
 
+/* One outer iteration of the RPBA loop (Sec. 5) in steady state: the LM
+ * adjustment of every sub-block (Eq. bact, up to options.max_inner lock-step
+ * LM iterations), the exchange of cameras and single-sub-block points, the
+ * robust weights from the per-camera scale when `robust` is nonzero (Sec.
+ * 5.3), the intersection of the tie points with their refined weights (Eq.
+ * bars, Sec. 5.1) and sigma_0 (Eq. sigma0). Unlike rpba_iterate it evaluates
+ * no start or final sigma_0, applies no stop rule and eliminates no point: the
+ * caller owns the loop. Runs rpba_intersect first if it has not been run.
+ * Outputs (nullable): sigma0 after the iteration, lm_launches = lock-step LM
+ * iterations it ran. Errors: NOT_CONVERGED if the LM loop does not end,
+ * CUDA. */
+rpba_status rpba_outer_iteration(rpba_ctx *ctx, int32_t robust, double *sigma0, int32_t *lm_launches);
+
+/* Sharded runs (the sub-blocks of one block spread over processes, each with
+ * its own context holding the whole block; Sec. 5's exchange between them).
+ * rpba_set_subblock_mask: the LM adjustment of rpba_bact, rpba_iterate and
+ * rpba_outer_iteration moves only the sub-blocks l with mask[l] != 0
+ * (n_subblocks bytes, host, read during the call; NULL restores all, the
+ * default). rpba_set_point_mask: the intersections (rpba_intersect_points
+ * and those inside the iteration) handle only the points j with mask[j] != 0
+ * (n_points bytes in the caller's numbering; NULL: all). Both persist until
+ * changed. Errors: CUDA. */
+rpba_status rpba_set_subblock_mask(rpba_ctx *ctx, const uint8_t *mask);
+rpba_status rpba_set_point_mask(rpba_ctx *ctx, const uint8_t *mask);
+
 /* C_j = N_j^-1 of the listed points at the current state (Eq. bars), out is
  * n x 9 row-major; inactive points give NaN. */
 rpba_status rpba_covariance(rpba_ctx *ctx, const int32_t *point_ids, int32_t n, double *out9);
@@ -172,6 +201,12 @@ rpba_status rpba_get_options(rpba_ctx *ctx, rpba_options *out);
 /* cameras of sub-block l in RCS row order (ascending global id); n_out = count */
 rpba_status rpba_sub_cameras(rpba_ctx *ctx, int32_t l, int32_t *cams, int32_t *n_out);
 rpba_status rpba_set_cameras(rpba_ctx *ctx, const double *pose);
+/* the camera state as held, without the angle-axis conversion: R (n_cams x 9,
+ * row-major, X_c = R X + t) and t (n_cams x 3), host buffers. A sharded run's
+ * exchange moves cameras through these, bit for bit. Errors: INVALID_ARG for
+ * a NULL buffer, CUDA. */
+rpba_status rpba_get_camera_rt(rpba_ctx *ctx, double *R, double *t);
+rpba_status rpba_set_camera_rt(rpba_ctx *ctx, const double *R, const double *t);
 rpba_status rpba_set_points(rpba_ctx *ctx, const double *X, const uint8_t *active /* nullable */);
 /* instances sorted by (sub-block, point): point id, sub-block id, X^l (P x 3),
  * W^l (P x 6 sym3); any output may be NULL */

@@ -67,6 +67,8 @@ def lib():
         L.orc_sub_cameras.restype = C.c_int
         L.orc_get_cameras.argtypes = [C.c_void_p, _dp]
         L.orc_set_cameras.argtypes = [C.c_void_p, _dp]
+        L.orc_get_camera_rt.argtypes = [C.c_void_p, _dp, _dp]
+        L.orc_set_camera_rt.argtypes = [C.c_void_p, _dp, _dp]
         L.orc_get_points.argtypes = [C.c_void_p, _dp, _up]
         L.orc_set_points.argtypes = [C.c_void_p, _dp, C.c_void_p]
         L.orc_get_instances.argtypes = [C.c_void_p, _dp, _dp]
@@ -91,6 +93,10 @@ def lib():
         L.orc_robust_weights.restype = C.c_int
         L.orc_intersect.argtypes = [C.c_void_p, C.POINTER(Options), C.c_int]
         L.orc_intersect.restype = C.c_int
+        L.orc_intersect_points.argtypes = [C.c_void_p, C.POINTER(Options), _ip, C.c_int, C.c_int]
+        L.orc_intersect_points.restype = C.c_int
+        L.orc_robust_weights_cams.argtypes = [C.c_void_p, _ip, C.c_int, C.c_double, C.c_double]
+        L.orc_robust_weights_cams.restype = C.c_int
         L.orc_sub_cost.argtypes = [C.c_void_p, C.c_int]
         L.orc_sub_cost.restype = C.c_double
         L.orc_rcs.argtypes = [C.c_void_p, C.c_int, C.c_double, _dp, _dp]
@@ -211,6 +217,17 @@ class Oracle:
     def set_cameras(self, pose):
         lib().orc_set_cameras(self._h, _f64(pose, (self.M, 6)))
 
+    def camera_rt(self):
+        """(M, 12): the rotation matrix (row-major) and translation of every
+        camera, as held."""
+        R, t = np.zeros((self.M, 9)), np.zeros((self.M, 3))
+        lib().orc_get_camera_rt(self._h, R, t)
+        return np.concatenate([R, t], axis=1)
+
+    def set_camera_rt(self, Rt):
+        Rt = _f64(Rt, (self.M, 12))
+        lib().orc_set_camera_rt(self._h, np.ascontiguousarray(Rt[:, :9]), np.ascontiguousarray(Rt[:, 9:]))
+
     def points(self):
         X, a = np.zeros((self.N, 3)), np.zeros(self.N, np.uint8)
         lib().orc_get_points(self._h, X, a)
@@ -272,6 +289,17 @@ class Oracle:
     def intersect(self, tp_only=False, **opts):
         o = default_options(**opts)
         return lib().orc_intersect(self._h, C.byref(o), int(tp_only))
+
+    def intersect_points(self, ids, tp_only=False, **opts):
+        """Eq. bars for the listed points only."""
+        o = default_options(**opts)
+        ids = _i32(ids)
+        return lib().orc_intersect_points(self._h, C.byref(o), ids, ids.size, int(tp_only))
+
+    def robust_weights_cams(self, cams, t_v=4.0, downweight=1e-4):
+        """Robust weights of the observations of the listed cameras only."""
+        cams = _i32(cams)
+        return lib().orc_robust_weights_cams(self._h, cams, cams.size, t_v, downweight)
 
     def sub_cost(self, l):
         return lib().orc_sub_cost(self._h, l)

@@ -421,6 +421,16 @@ void orc_set_cameras(orc_ctx *c, const double *pose) {
   }
 }
 
+void orc_get_camera_rt(const orc_ctx *c, double *R, double *t) {
+  memcpy(R, c->R, sizeof(double) * 9 * c->M);
+  memcpy(t, c->t, sizeof(double) * 3 * c->M);
+}
+
+void orc_set_camera_rt(orc_ctx *c, const double *R, const double *t) {
+  memcpy(c->R, R, sizeof(double) * 9 * c->M);
+  memcpy(c->t, t, sizeof(double) * 3 * c->M);
+}
+
 void orc_get_points(const orc_ctx *c, double *X, unsigned char *active) {
   if (X) memcpy(X, c->X, sizeof(double) * 3 * c->N);
   if (active) memcpy(active, c->active, (size_t)c->N);
@@ -546,45 +556,69 @@ static void whiten(const double W[3], const double v[2], double e[2]) {
   e[1] = sqrt(W[2] - W[1] * W[1] / W[0]) * v[1];
 }
 
-/* per camera: 1.4826 * median |e - median(e)| over its whitened components (Sec. 5.3) */
+/* camera i: 1.4826 * median |e - median(e)| over its whitened components
+ * (Sec. 5.3); buf holds at least 2 K_i doubles */
+static double camera_scale_one(const orc_ctx *c, int i, double *buf) {
+  double v[2], e[2];
+  int n = 0;
+  for (int p = c->cam_obs_ptr[i]; p < c->cam_obs_ptr[i + 1]; p++) {
+    int k = c->cam_obs[p];
+    int j = c->obs_pt[k];
+    if (!c->active[j]) continue;
+    obs_residual(c, k, c->R, c->t, c->X + 3 * j, v, NULL, NULL);
+    whiten(c->obs_winv + 3 * k, v, e);
+    buf[n++] = e[0];
+    buf[n++] = e[1];
+  }
+  if (n == 0) return 0.0;
+  double med = orc_median(buf, n);
+  for (int a = 0; a < n; a++) buf[a] = fabs(buf[a] - med);
+  return 1.4826 * orc_median(buf, n);
+}
+
 void orc_camera_scale(const orc_ctx *c, double *sigma) {
   double *buf = (double *)malloc(sizeof(double) * (size_t)(2 * c->K + 2));
-  double v[2], e[2];
-  for (int i = 0; i < c->M; i++) {
-    int n = 0;
-    for (int p = c->cam_obs_ptr[i]; p < c->cam_obs_ptr[i + 1]; p++) {
-      int k = c->cam_obs[p];
-      int j = c->obs_pt[k];
-      if (!c->active[j]) continue;
-      obs_residual(c, k, c->R, c->t, c->X + 3 * j, v, NULL, NULL);
-      whiten(c->obs_winv + 3 * k, v, e);
-      buf[n++] = e[0];
-      buf[n++] = e[1];
-    }
-    if (n == 0) { sigma[i] = 0.0; continue; }
-    double med = orc_median(buf, n);
-    for (int a = 0; a < n; a++) buf[a] = fabs(buf[a] - med);
-    sigma[i] = 1.4826 * orc_median(buf, n);
-  }
+  for (int i = 0; i < c->M; i++) sigma[i] = camera_scale_one(c, i, buf);
   free(buf);
+}
+
+/* observation k's robust weight from its camera's scale s: down-weighted when
+ * sqrt(v^T C^-1 v) / s > t_v (Sec. 5.3); returns 1 when down-weighted */
+static int robust_weight_one(orc_ctx *c, int k, double s, double t_v, double downweight) {
+  double v[2];
+  int j = c->obs_pt[k];
+  obs_residual(c, k, c->R, c->t, c->X + 3 * j, v, NULL, NULL);
+  double nr = sqrt(quad_w(c->obs_winv + 3 * k, v));
+  int out = (s > 0.0) && (nr / s > t_v);
+  c->w[k] = out ? downweight : 1.0;
+  return out;
 }
 
 int orc_robust_weights(orc_ctx *c, double t_v, double downweight) {
   double *sigma = (double *)malloc(sizeof(double) * (size_t)(c->M > 0 ? c->M : 1));
   orc_camera_scale(c, sigma);
   int nd = 0;
-  double v[2];
   for (int k = 0; k < c->K; k++) {
-    int j = c->obs_pt[k];
-    if (!c->active[j]) continue;
-    obs_residual(c, k, c->R, c->t, c->X + 3 * j, v, NULL, NULL);
-    double s = sigma[c->obs_cam[k]];
-    double nr = sqrt(quad_w(c->obs_winv + 3 * k, v));
-    int out = (s > 0.0) && (nr / s > t_v);
-    c->w[k] = out ? downweight : 1.0;
-    nd += out;
+    if (!c->active[c->obs_pt[k]]) continue;
+    nd += robust_weight_one(c, k, sigma[c->obs_cam[k]], t_v, downweight);
   }
   free(sigma);
+  return nd;
+}
+
+int orc_robust_weights_cams(orc_ctx *c, const int *cams, int n, double t_v, double downweight) {
+  double *buf = (double *)malloc(sizeof(double) * (size_t)(2 * c->K + 2));
+  int nd = 0;
+  for (int a = 0; a < n; a++) {
+    int i = cams[a];
+    double s = camera_scale_one(c, i, buf);
+    for (int p = c->cam_obs_ptr[i]; p < c->cam_obs_ptr[i + 1]; p++) {
+      int k = c->cam_obs[p];
+      if (!c->active[c->obs_pt[k]]) continue;
+      nd += robust_weight_one(c, k, s, t_v, downweight);
+    }
+  }
+  free(buf);
   return nd;
 }
 
@@ -638,32 +672,49 @@ static int intersect_point(const orc_ctx *c, const orc_options *o, int j, double
   return 0;
 }
 
-int orc_intersect(orc_ctx *c, const orc_options *o, int tp_only) {
-  int dropped = 0;
+/* Eq. bars for point j (skipped when inactive, or a single-instance point
+ * with tp_only): X_j, or the point dropped; W^l of its instances (Sec. 5.1).
+ * Returns 1 when it drops the point. */
+static int intersect_one(orc_ctx *c, const orc_options *o, int j, int tp_only, double *Nl) {
+  if (!c->active[j]) return 0;
+  int q0 = c->pt_inst_ptr[j], nq = c->pt_inst_ptr[j + 1] - q0;
+  if (tp_only && nq < 2) return 0;
+  double X[3] = {c->X[3 * j], c->X[3 * j + 1], c->X[3 * j + 2]};
+  double Ntot[6];
+  if (!intersect_point(c, o, j, X, Ntot, Nl)) {
+    c->active[j] = 0;
+    for (int qi = 0; qi < nq; qi++) memset(c->Wl + 6 * c->pt_inst[q0 + qi], 0, 6 * sizeof(double));
+    return 1;
+  }
+  for (int e = 0; e < 3; e++) c->X[3 * j + e] = X[e];
+  for (int qi = 0; qi < nq; qi++) {
+    double *W = c->Wl + 6 * c->pt_inst[q0 + qi];
+    for (int e = 0; e < 6; e++) W[e] = (nq >= 2) ? Ntot[e] - Nl[6 * qi + e] : 0.0;
+  }
+  return 0;
+}
+
+static double *instance_scratch(const orc_ctx *c) {
   int maxq = 1;
   for (int j = 0; j < c->N; j++) {
     int nq = c->pt_inst_ptr[j + 1] - c->pt_inst_ptr[j];
     if (nq > maxq) maxq = nq;
   }
-  double *Nl = (double *)malloc(sizeof(double) * 6 * (size_t)maxq);
-  for (int j = 0; j < c->N; j++) {
-    if (!c->active[j]) continue;
-    int q0 = c->pt_inst_ptr[j], nq = c->pt_inst_ptr[j + 1] - q0;
-    if (tp_only && nq < 2) continue;
-    double X[3] = {c->X[3 * j], c->X[3 * j + 1], c->X[3 * j + 2]};
-    double Ntot[6];
-    if (!intersect_point(c, o, j, X, Ntot, Nl)) {
-      c->active[j] = 0;
-      dropped++;
-      for (int qi = 0; qi < nq; qi++) memset(c->Wl + 6 * c->pt_inst[q0 + qi], 0, 6 * sizeof(double));
-      continue;
-    }
-    for (int e = 0; e < 3; e++) c->X[3 * j + e] = X[e];
-    for (int qi = 0; qi < nq; qi++) {
-      double *W = c->Wl + 6 * c->pt_inst[q0 + qi];
-      for (int e = 0; e < 6; e++) W[e] = (nq >= 2) ? Ntot[e] - Nl[6 * qi + e] : 0.0;
-    }
-  }
+  return (double *)malloc(sizeof(double) * 6 * (size_t)maxq);
+}
+
+int orc_intersect(orc_ctx *c, const orc_options *o, int tp_only) {
+  int dropped = 0;
+  double *Nl = instance_scratch(c);
+  for (int j = 0; j < c->N; j++) dropped += intersect_one(c, o, j, tp_only, Nl);
+  free(Nl);
+  return dropped;
+}
+
+int orc_intersect_points(orc_ctx *c, const orc_options *o, const int *ids, int n, int tp_only) {
+  int dropped = 0;
+  double *Nl = instance_scratch(c);
+  for (int a = 0; a < n; a++) dropped += intersect_one(c, o, ids[a], tp_only, Nl);
   free(Nl);
   return dropped;
 }
@@ -835,13 +886,12 @@ int orc_lm_step(orc_ctx *c, int l, double lambda, double *F_before, double *F_tr
       }
       sym3_mul_vec(Ninv + 6 * (q - q0), rhs, dx + 3 * (q - q0));
     }
-    /* trial state */
+    /* trial state: only the cameras and instances of sub-block l are set and
+     * read (its observations see only its cameras), so sub-blocks can take
+     * their steps on separate threads */
     double *Rt = (double *)malloc(sizeof(double) * 9 * c->M);
     double *tt = (double *)malloc(sizeof(double) * 3 * c->M);
     double *Xt = (double *)malloc(sizeof(double) * 3 * (size_t)(c->P > 0 ? c->P : 1));
-    memcpy(Rt, c->R, sizeof(double) * 9 * c->M);
-    memcpy(tt, c->t, sizeof(double) * 3 * c->M);
-    memcpy(Xt, c->Xl, sizeof(double) * 3 * c->P);
     for (int li = 0; li < Ml; li++) {
       int i = c->sub_cam[c0 + li];
       double dR[9];
@@ -861,9 +911,12 @@ int orc_lm_step(orc_ctx *c, int l, double lambda, double *F_before, double *F_tr
     if (dc_out) memcpy(dc_out, y, sizeof(double) * n);
     if (dx_out) memcpy(dx_out, dx, sizeof(double) * 3 * nP);
     if (F1 < F0) {
-      memcpy(c->R, Rt, sizeof(double) * 9 * c->M);
-      memcpy(c->t, tt, sizeof(double) * 3 * c->M);
-      memcpy(c->Xl, Xt, sizeof(double) * 3 * c->P);
+      for (int li = 0; li < Ml; li++) {
+        int i = c->sub_cam[c0 + li];
+        memcpy(c->R + 9 * i, Rt + 9 * i, sizeof(double) * 9);
+        memcpy(c->t + 3 * i, tt + 3 * i, sizeof(double) * 3);
+      }
+      memcpy(c->Xl + 3 * (size_t)q0, Xt + 3 * (size_t)q0, sizeof(double) * 3 * nP);
       result = 1;
     } else {
       result = 0;

@@ -87,6 +87,9 @@ int orc_sub_cameras(const orc_ctx *c, int l, int *cams);
 /* state */
 void orc_get_cameras(const orc_ctx *c, double *pose);
 void orc_set_cameras(orc_ctx *c, const double *pose);
+/* the rotation matrices (9 per camera, row-major) and translations as held */
+void orc_get_camera_rt(const orc_ctx *c, double *R, double *t);
+void orc_set_camera_rt(orc_ctx *c, const double *R, const double *t);
 void orc_get_points(const orc_ctx *c, double *X, unsigned char *active);
 void orc_set_points(orc_ctx *c, const double *X, const unsigned char *active);
 void orc_get_instances(const orc_ctx *c, double *Xl, double *Wl);
@@ -112,12 +115,16 @@ void orc_camera_scale(const orc_ctx *c, double *sigma);
 double orc_median(double *a, int n); /* sorts a */
 /* robust weights from the per-camera scale; returns the number down-weighted */
 int orc_robust_weights(orc_ctx *c, double t_v, double downweight);
+/* the same for the observations of the listed cameras only */
+int orc_robust_weights_cams(orc_ctx *c, const int *cams, int n, double t_v, double downweight);
 
 /* intersection (Eq. bars) of all active points (tp_only = 0) or of the tie
  * points only (tp_only = 1), starting at the current X. Writes X, the
  * per-instance weights W^l (Sec. 5.1) and drops points that fail. Returns the
  * number of points dropped. */
 int orc_intersect(orc_ctx *c, const orc_options *o, int tp_only);
+/* the same for the listed points only */
+int orc_intersect_points(orc_ctx *c, const orc_options *o, const int *ids, int n, int tp_only);
 
 /* sub-block l: cost F_l (Eq. bact) at the current sub-block state */
 double orc_sub_cost(const orc_ctx *c, int l);

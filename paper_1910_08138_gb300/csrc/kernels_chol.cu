@@ -27,7 +27,10 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <vector>
+
 #include "rpba_internal.cuh"
+#include "tc_sm100.cuh"
 
 namespace rpba {
 
@@ -246,6 +249,215 @@ __global__ void __launch_bounds__(256, 3) k_chol_update(T *S, T *Linv, CholView 
     return;
   }
   store_diag<T>(A, np, k + 1, P, Q, Linv + cv.linv_off[l] + (size_t)(k + 1) * CT * CT);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 factorisation with the updates on the tensor cores (chol_tc)
+//
+// Left-looking, one launch per block column J of 32: the CTA of (sub-block
+// l, row block i) gathers the 128 rows {diagonal rows 32J .. 32J+31} and
+// {96 rows below, from 32J + 32 + 96 i} of every finished block column k < J
+// and accumulates in tensor memory
+//     U = sum_k P_k[rows] P_k[32J .. 32J+31]^T          (128 x 32, K = 32 J)
+// with tcgen05.mma kind::tf32: each factor entry is held as three TF32 pieces
+// h + m + l (h, m rounded to TF32, l the exact FP32 remainder) and the six
+// products hh, hm, mh, hl, lh, mm are accumulated, which keeps the update at
+// FP32 accuracy (the dropped products are below 2^-31 relative). Operands
+// arrive by TMA (128-byte swizzle) in a two-stage ring; one thread issues the
+// TMA loads and the MMAs, tcgen05.commit frees a stage. Then every CTA of the
+// step factors the updated diagonal tile A_JJ - U[0:32] itself (one warp; the
+// result is the same in every CTA) and solves its rows:
+//     L_iJ = (A_iJ - U_i) L_JJ^-T,
+// writing them to the row-major factor (read by the triangular solves) and
+// as TF32 pieces to block column J's panel (read by the later steps). The
+// CTA of row block 0 also stores L_JJ and its inverse. Every wait is bounded
+// (tc::mbar_wait); on a timeout the CTA records it in err, marks the
+// sub-block failed, waits (bounded) for its own MMAs and frees its TMEM.
+// ---------------------------------------------------------------------------
+#define TC_ROWS 128                            // rows of one MMA (M)
+#define TC_BELOW 96                            // rows below the diagonal tile per CTA
+#define TC_PIECE_BYTES (TC_ROWS * CT * 4)      // one piece of one stage: 16 KB
+#define TC_STAGE_BYTES (3 * TC_PIECE_BYTES)    // three pieces: 48 KB
+#define TC_STAGES 2
+#define TC_SMEM (TC_STAGES * TC_STAGE_BYTES + 1024)
+#define TC_WAIT_NS 200000000ull                // 0.2 s: no wait of a healthy launch comes near it
+
+struct TcView {
+  float *S;                 // FP32 factor storage (row-major, the layout of S32)
+  const long long *off;
+  const int *npad;
+  float *Linv;
+  const int *linv_off;
+  const int *run;
+  int *fail;
+  float *P0, *P1, *P2;      // panel pieces
+  const long long *prow;
+  const int *sched;         // this step's L+1 prefix sums of CTAs
+  int L;
+  int *err;
+};
+
+__device__ inline void tc_split3(float x, float &h, float &m, float &l) {
+  h = tc::tf32_round(x);
+  float r = x - h;  // exact
+  m = tc::tf32_round(r);
+  l = r - m;        // exact
+}
+
+__global__ void __launch_bounds__(128) k_chol_tc(const __grid_constant__ CUtensorMap tm0,
+                                                 const __grid_constant__ CUtensorMap tm1,
+                                                 const __grid_constant__ CUtensorMap tm2, TcView v, int J) {
+  extern __shared__ uint8_t tc_smem_raw[];
+  __shared__ __align__(8) uint64_t bar_full[TC_STAGES], bar_empty[TC_STAGES], bar_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ float Ls[CT * CLD], Xs[CT * CLD];
+  __shared__ int sh_ok, sh_bad;
+  int loc;
+  int l = sched_find(v.sched, v.L, blockIdx.x, &loc);
+  if (!v.run[l] || v.fail[l]) return;  // CTA-uniform
+  int np = v.npad[l];
+  if (32 * J >= np) return;
+  const int d0 = 32 * J, r0 = d0 + 32 + TC_BELOW * loc;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float *A = v.S + v.off[l];
+  float acc[32];
+#pragma unroll
+  for (int c = 0; c < 32; c++) acc[c] = 0.f;
+
+  if (J > 0) {
+    uint8_t *base = (uint8_t *)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+    if (tid == 0) {
+      for (int s = 0; s < TC_STAGES; s++) {
+        tc::mbar_init(&bar_full[s], 1);
+        tc::mbar_init(&bar_empty[s], 1);
+      }
+      tc::mbar_init(&bar_done, 1);
+      tc::fence_mbar_init();
+      tc::prefetch_tmap(&tm0);
+      tc::prefetch_tmap(&tm1);
+      tc::prefetch_tmap(&tm2);
+    }
+    if (warp == 0) {
+      tc::tmem_alloc(&tmem_base, 32);
+      tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    if (tid == 0) {
+      bool ok = true;
+      const long long prow = v.prow[l];
+      const CUtensorMap *maps[3] = {&tm0, &tm1, &tm2};
+      auto load = [&](int k, int s) {
+        uint8_t *st = base + s * TC_STAGE_BYTES;
+        tc::mbar_arrive_expect_tx(&bar_full[s], TC_STAGE_BYTES);
+        int y = (int)(prow + (long long)k * np);
+        for (int p = 0; p < 3; p++) {
+          uint8_t *pb = st + p * TC_PIECE_BYTES;
+          tc::tma_load_2d(pb, maps[p], 0, y + d0, &bar_full[s]);
+          for (int b = 0; b < 3; b++) tc::tma_load_2d(pb + (1 + b) * 32 * 128, maps[p], 0, y + r0 + 32 * b, &bar_full[s]);
+        }
+      };
+      const uint32_t idesc = tc::idesc_tf32(TC_ROWS, CT);
+      // products of the pieces (A piece, B piece): hh hm mh hl lh mm
+      const int pa[6] = {0, 0, 1, 0, 2, 1}, pb[6] = {0, 1, 0, 2, 0, 1};
+      int issued_loads = 0;
+      for (int k = 0; k < J && k < TC_STAGES; k++) {
+        load(k, k);
+        issued_loads++;
+      }
+      int k = 0;
+      for (; k < J; k++) {
+        int s = k % TC_STAGES;
+        uint32_t ph = (uint32_t)(k / TC_STAGES) & 1u;
+        if (!tc::mbar_wait(&bar_full[s], ph, TC_WAIT_NS)) { ok = false; break; }
+        tc::tc_fence_after();
+        uint32_t sa = tc::smem_u32(base + s * TC_STAGE_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < 4; kk++) {  // K = 8 TF32 (32 bytes) per MMA
+          uint64_t d[3];
+#pragma unroll
+          for (int p = 0; p < 3; p++) d[p] = tc::desc_sw128_kmajor(sa + p * TC_PIECE_BYTES + kk * 32);
+#pragma unroll
+          for (int t = 0; t < 6; t++)  // B = the diagonal rows: the first 32 rows of its piece
+            tc::mma_tf32(tmem, d[pa[t]], d[pb[t]], idesc, (k > 0 || kk > 0 || t > 0) ? 1u : 0u);
+        }
+        tc::mma_commit(&bar_empty[s]);
+        if (k + TC_STAGES < J) {
+          if (!tc::mbar_wait(&bar_empty[s], ph, TC_WAIT_NS)) { ok = false; k++; break; }
+          load(k + TC_STAGES, s);
+          issued_loads++;
+        }
+      }
+      // every MMA issued so far completes before bar_done's arrival
+      tc::mma_commit(&bar_done);
+      bool done = tc::mbar_wait(&bar_done, 0, TC_WAIT_NS);
+      if (!ok) {
+        // loads still in flight land in this CTA's shared memory: wait for
+        // them (bounded) before leaving
+        for (int q = k; q < issued_loads; q++)
+          tc::mbar_wait(&bar_full[q % TC_STAGES], (uint32_t)(q / TC_STAGES) & 1u, TC_WAIT_NS);
+      }
+      sh_ok = ok && done;
+    }
+    __syncthreads();
+    tc::tc_fence_after();
+    if (sh_ok) tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), acc);
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 32);
+    if (!sh_ok) {
+      if (tid == 0) {
+        atomicExch(v.err, 1);
+        v.fail[l] = 1;
+      }
+      return;
+    }
+  }
+
+  // diagonal tile: A_JJ - U[0:32] (lower part), factored and inverted by warp 0
+  if (warp == 0) {
+    float x[CT];
+#pragma unroll
+    for (int c = 0; c < CT; c++) x[c] = (c <= lane) ? A[(size_t)(d0 + lane) * np + d0 + c] - acc[c] : 0.f;
+    bool okp = warp_potrf_inv<float>(x, Ls, Xs);
+    if (lane == 0) sh_bad = !okp;
+  }
+  __syncthreads();
+  if (sh_bad) {
+    if (tid == 0 && loc == 0) v.fail[l] = 1;
+    return;
+  }
+  if (warp == 0 && loc == 0) {
+    float *Li = v.Linv + v.linv_off[l] + (size_t)J * CT * CT;
+    for (int c = 0; c < CT; c++) {
+      if (c <= lane) A[(size_t)(d0 + lane) * np + d0 + c] = Ls[lane * CLD + c];
+      Li[lane * CT + c] = Xs[lane * CLD + c];
+    }
+  }
+  // rows below: L_iJ = (A_iJ - U_i) L_JJ^-T (L_JJ^-1 lower triangular)
+  if (warp > 0) {
+    int r = r0 + 32 * (warp - 1) + lane;
+    if (r < np) {
+      float crow[CT];
+#pragma unroll
+      for (int c = 0; c < CT; c++) crow[c] = A[(size_t)r * np + d0 + c] - acc[c];
+      long long pr = (v.prow[l] + (long long)J * np + r) * CT;
+#pragma unroll
+      for (int c = 0; c < CT; c++) {
+        float s = 0.f;
+#pragma unroll
+        for (int e = 0; e <= c; e++) s = fmaf(crow[e], Xs[c * CLD + e], s);
+        A[(size_t)r * np + d0 + c] = s;
+        float h, m, lo;
+        tc_split3(s, h, m, lo);
+        v.P0[pr + c] = h;
+        v.P1[pr + c] = m;
+        v.P2[pr + c] = lo;
+      }
+    }
+  }
 }
 
 // forward L z = r and backward L^T x = z (r in, x out, may alias), one thread
@@ -501,6 +713,87 @@ __global__ void k_mixed_update(const int *run, const int *fail, const int *voff,
   }
 }
 
+// the panel layout, per-step schedule and TMA tensor maps of the
+// tensor-core factorisation (once per context)
+rpba_status tc_chol_setup(Ctx *ctx) {
+  int L = ctx->L, steps = ctx->max_tiles;
+  if (L == 0 || steps == 0) return RPBA_OK;
+  std::vector<long long> prow(L);
+  long long rows = 0;
+  for (int l = 0; l < L; l++) {
+    prow[l] = rows;
+    rows += (long long)(ctx->h_npad[l] / CT) * ctx->h_npad[l];
+  }
+  if (rows + TC_ROWS >= (1LL << 31)) {
+    ctx->err = "RCS too large for the tensor-core factorisation's 32-bit panel rows";
+    return RPBA_ERR_INVALID_ARG;
+  }
+  std::vector<int> sched((size_t)steps * (L + 1), 0);
+  ctx->h_tc_ctas.assign(steps, 0);
+  for (int J = 0; J < steps; J++) {
+    int *pb = &sched[(size_t)J * (L + 1)];
+    for (int l = 0; l < L; l++) {
+      int np = ctx->h_npad[l], below = np - CT * J - CT;
+      int c = (CT * J < np) ? 1 + (below > 0 ? (below + TC_BELOW - 1) / TC_BELOW : 0) : 0;
+      pb[l + 1] = pb[l] + c;
+    }
+    ctx->h_tc_ctas[J] = pb[L];
+  }
+  for (int p = 0; p < 3; p++) {
+    RPBA_TRY(ctx_alloc(ctx, (void **)&ctx->tc_panel[p], (size_t)(rows + TC_ROWS) * CT * sizeof(float)));
+    RPBA_CUDA(cudaMemsetAsync(ctx->tc_panel[p], 0, (size_t)(rows + TC_ROWS) * CT * sizeof(float), ctx->stream));
+  }
+  RPBA_TRY(ctx_alloc(ctx, (void **)&ctx->tc_prow, sizeof(long long) * L));
+  RPBA_CUDA(cudaMemcpyAsync(ctx->tc_prow, prow.data(), sizeof(long long) * L, cudaMemcpyHostToDevice, ctx->stream));
+  RPBA_TRY(ctx_alloc(ctx, (void **)&ctx->tc_sched, sizeof(int) * sched.size()));
+  RPBA_CUDA(cudaMemcpyAsync(ctx->tc_sched, sched.data(), sizeof(int) * sched.size(), cudaMemcpyHostToDevice,
+                            ctx->stream));
+  RPBA_TRY(ctx_alloc(ctx, (void **)&ctx->tc_err, sizeof(int)));
+  RPBA_CUDA(cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), ctx->stream));
+  // cuTensorMapEncodeTiled through the runtime (no link against the driver library)
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    ctx->err = "cuTensorMapEncodeTiled is not available";
+    return RPBA_ERR_CUDA;
+  }
+  auto encode = (CUresult(*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                             const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                             CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill))fn;
+  // 2-D: 32 floats (128 B) per row, all panel rows; boxes of 32 rows, 128-byte swizzle
+  cuuint64_t dims[2] = {(cuuint64_t)CT, (cuuint64_t)(rows + TC_ROWS)};
+  cuuint64_t strides[1] = {(cuuint64_t)CT * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)CT, 32};
+  cuuint32_t estr[2] = {1, 1};
+  for (int p = 0; p < 3; p++) {
+    CUresult r = encode(&ctx->tc_map[p], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ctx->tc_panel[p], dims, strides, box,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      ctx->err = "cuTensorMapEncodeTiled failed for the factor panels";
+      return RPBA_ERR_CUDA;
+    }
+  }
+  RPBA_CUDA(cudaFuncSetAttribute(k_chol_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  ctx->tc_ready = true;
+  return RPBA_OK;
+}
+
+// the FP32 factorisation of every running sub-block on the tensor cores
+static rpba_status factor_tc(Ctx *ctx, float *S, float *Linv, const long long *off, const int *run, int *fail) {
+  TcView tv{S, off, ctx->npad, Linv, ctx->linv_off, run, fail, ctx->tc_panel[0], ctx->tc_panel[1],
+            ctx->tc_panel[2], ctx->tc_prow, nullptr, ctx->L, ctx->tc_err};
+  for (int J = 0; J < ctx->max_tiles; J++) {
+    int n = ctx->h_tc_ctas[J];
+    if (n == 0) break;
+    tv.sched = ctx->tc_sched + (size_t)J * (ctx->L + 1);
+    RPBA_KERNEL(ctx, "k_chol_tc", k_chol_tc<<<n, 128, TC_SMEM, ctx->stream>>>(ctx->tc_map[0], ctx->tc_map[1],
+                                                                                ctx->tc_map[2], tv, J));
+  }
+  return RPBA_OK;
+}
+
 rpba_status launch_solve_rcs(Ctx *ctx, const int *run_dev, int *fail_dev) {
   if (ctx->opt.solver == 1) return launch_pcg_blockjacobi(ctx, run_dev, fail_dev);
   if (ctx->opt.solver == 3) return launch_pcg_learned(ctx, run_dev, fail_dev);
@@ -526,7 +819,10 @@ rpba_status launch_solve_rcs(Ctx *ctx, const int *run_dev, int *fail_dev) {
                                                                          ctx->npad, ctx->ycam_off, run_dev,
                                                                          ctx->ir_d));
   CholView cv{ctx->S32_off, ctx->npad, ctx->linv_off, run_dev, fail_dev, ctx->sched, ctx->L};
-  RPBA_TRY(factor<float>(ctx, ctx->S32, ctx->Linv32, cv, T_max));
+  if (ctx->opt.chol_tc && ctx->tc_ready)
+    RPBA_TRY(factor_tc(ctx, ctx->S32, ctx->Linv32, ctx->S32_off, run_dev, fail_dev));
+  else
+    RPBA_TRY(factor<float>(ctx, ctx->S32, ctx->Linv32, cv, T_max));
   int passes = 1 + ctx->opt.ir_steps;
   for (int it = 0; it < passes; it++) {
     if (it > 0) {

@@ -767,11 +767,11 @@ __global__ void k_isect_fused_f(View v, int *state, int *iter, int max_iter, dou
     isect_fused_step(v, j, state, iter, max_iter, tol, px_tol, cond_max, pass == max_iter - 1);
 }
 
-__global__ void k_isect_start(View v, int *state, int *iter, int tp_only, int *count) {
+__global__ void k_isect_start(View v, const uint8_t *pt_mask, int *state, int *iter, int tp_only, int *count) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= v.N) return;
   int nq = v.pt_inst_ptr[j + 1] - v.pt_inst_ptr[j];
-  int s = (v.active[j] && (!tp_only || nq >= 2)) ? 1 : 0;
+  int s = (v.active[j] && (!tp_only || nq >= 2) && pt_mask[j]) ? 1 : 0;
   state[j] = s;
   iter[j] = 0;
   if (s) atomicAdd(count, 1);
@@ -789,7 +789,7 @@ rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped, bool fp64) {
   if (ctx->N == 0) { if (n_dropped) *n_dropped = 0; return RPBA_OK; }
   RPBA_CUDA(cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(int), ctx->stream));
   RPBA_KERNEL(ctx, "k_isect_start", k_isect_start<<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(
-                                        v, ctx->isect_state, ctx->isect_iter, tp_only, ctx->counters));
+                                        v, ctx->pt_mask, ctx->isect_state, ctx->isect_iter, tp_only, ctx->counters));
   int maxit = ctx->opt.isect_max_iter;
   double tol = ctx->opt.isect_tol;
   double px_tol = ctx->opt.isect_px_tol;
@@ -1583,7 +1583,7 @@ rpba_status launch_backsub_trial(Ctx *ctx, const int *run_dev) {
 // ---------------------------------------------------------------------------
 // LM control per sub-block (Sec. 5.5 and the stopping reading)
 // ---------------------------------------------------------------------------
-__global__ void k_lm_init(View v, const int *sub_nc, double lambda0, int grace, double *lam, double *F,
+__global__ void k_lm_init(View v, const uint8_t *sub_mask, double lambda0, int grace, double *lam, double *F,
                           double *best, int *gr, int *rej, int *it, int *run, const double *F0) {
   int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= v.L) return;
@@ -1593,7 +1593,7 @@ __global__ void k_lm_init(View v, const int *sub_nc, double lambda0, int grace, 
   gr[l] = grace;
   rej[l] = 0;
   it[l] = 0;
-  run[l] = (v.sub_cam_ptr[l + 1] - v.sub_cam_ptr[l]) > 0;
+  run[l] = (v.sub_cam_ptr[l + 1] - v.sub_cam_ptr[l]) > 0 && sub_mask[l];
 }
 
 __global__ void k_lm_decide(int L, double lambda0, double stop_ratio, int max_inner, int max_reject,
@@ -1660,7 +1660,7 @@ rpba_status launch_lm_apply(Ctx *ctx, const int *acc_dev) {
 
 rpba_status launch_lm_init(Ctx *ctx) {
   RPBA_TRY(sub_costs_impl(ctx, 0, nullptr, ctx->lm_Ft));
-  RPBA_KERNEL(ctx, "k_lm_init", k_lm_init<<<nblk(ctx->L, 128), 128, 0, ctx->stream>>>(make_view(ctx), nullptr, ctx->opt.lambda0, ctx->opt.grace,
+  RPBA_KERNEL(ctx, "k_lm_init", k_lm_init<<<nblk(ctx->L, 128), 128, 0, ctx->stream>>>(make_view(ctx), ctx->sub_mask, ctx->opt.lambda0, ctx->opt.grace,
                                                         ctx->lm_lambda, ctx->lm_F, ctx->lm_best, ctx->lm_grace,
                                                         ctx->lm_rej, ctx->lm_it, ctx->lm_run, ctx->lm_Ft));
   return RPBA_OK;

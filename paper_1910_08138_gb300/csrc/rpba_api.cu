@@ -177,6 +177,7 @@ extern "C" void rpba_default_options(rpba_options *o) {
   o->pcg_tol = 1e-8;
   o->pcg_max_iter = 500;
   o->ir_steps = 2;
+  o->chol_tc = 1;
 }
 
 extern "C" const char *rpba_last_error(const rpba_ctx *ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
@@ -665,7 +666,12 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
     RPBA_TRY(alloc_n(ctx, &ctx->ir_rs, (size_t)std::max(yt, 1)));
     RPBA_TRY(alloc_n(ctx, &ctx->ir_x, (size_t)std::max(yt, 1)));
     RPBA_TRY(alloc_n(ctx, &ctx->ir_t, (size_t)std::max(yt, 1)));
+    if (ctx->opt.chol_tc) RPBA_TRY(tc_chol_setup(ctx));
   }
+  RPBA_TRY(alloc_n(ctx, &ctx->sub_mask, (size_t)std::max(L, 1)));
+  RPBA_CUDA(cudaMemsetAsync(ctx->sub_mask, 1, (size_t)std::max(L, 1), ctx->stream));
+  RPBA_TRY(alloc_n(ctx, &ctx->pt_mask, (size_t)std::max(N, 1)));
+  RPBA_CUDA(cudaMemsetAsync(ctx->pt_mask, 1, (size_t)std::max(N, 1), ctx->stream));
   RPBA_TRY(alloc_n(ctx, &ctx->lm_lambda, (size_t)L));
   RPBA_TRY(alloc_n(ctx, &ctx->lm_F, (size_t)L));
   RPBA_TRY(alloc_n(ctx, &ctx->lm_Ft, (size_t)L));
@@ -792,6 +798,21 @@ extern "C" rpba_status rpba_set_cameras(rpba_ctx *h, const double *pose) {
   return sync(ctx);
 }
 
+extern "C" rpba_status rpba_get_camera_rt(rpba_ctx *h, double *R, double *t) {
+  CTX_OR_FAIL;
+  if (!R || !t) return RPBA_ERR_INVALID_ARG;
+  RPBA_CUDA(cudaMemcpyAsync(R, ctx->R, 9 * (size_t)ctx->M * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  RPBA_CUDA(cudaMemcpyAsync(t, ctx->t, 3 * (size_t)ctx->M * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return sync(ctx);
+}
+extern "C" rpba_status rpba_set_camera_rt(rpba_ctx *h, const double *R, const double *t) {
+  CTX_OR_FAIL;
+  if (!R || !t) return RPBA_ERR_INVALID_ARG;
+  RPBA_CUDA(cudaMemcpyAsync(ctx->R, R, 9 * (size_t)ctx->M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  RPBA_CUDA(cudaMemcpyAsync(ctx->t, t, 3 * (size_t)ctx->M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  RPBA_TRY(sync_mirrors(ctx));
+  return sync(ctx);
+}
 extern "C" rpba_status rpba_get_cameras(rpba_ctx *h, double *pose) {
   CTX_OR_FAIL;
   if (!pose) return RPBA_ERR_INVALID_ARG;
@@ -1344,6 +1365,38 @@ extern "C" rpba_status rpba_bact(rpba_ctx *h, int32_t *iters) {
     RPBA_CUDA(cudaMemcpyAsync(iters, ctx->lm_it, ctx->L * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     RPBA_TRY(sync(ctx));
   }
+  return RPBA_OK;
+}
+
+extern "C" rpba_status rpba_set_subblock_mask(rpba_ctx *h, const uint8_t *mask) {
+  CTX_OR_FAIL;
+  if (ctx->L == 0) return RPBA_OK;
+  std::vector<uint8_t> m(ctx->L, 1);
+  if (mask)
+    for (int l = 0; l < ctx->L; l++) m[l] = mask[l] ? 1 : 0;
+  RPBA_CUDA(cudaMemcpyAsync(ctx->sub_mask, m.data(), m.size(), cudaMemcpyHostToDevice, ctx->stream));
+  return sync(ctx);
+}
+
+extern "C" rpba_status rpba_set_point_mask(rpba_ctx *h, const uint8_t *mask) {
+  CTX_OR_FAIL;
+  if (ctx->N == 0) return RPBA_OK;
+  std::vector<uint8_t> m(ctx->N, 1);
+  if (mask)  // caller's numbering -> internal
+    for (int j = 0; j < ctx->N; j++) m[ctx->h_pt_perm[j]] = mask[j] ? 1 : 0;
+  RPBA_CUDA(cudaMemcpyAsync(ctx->pt_mask, m.data(), m.size(), cudaMemcpyHostToDevice, ctx->stream));
+  return sync(ctx);
+}
+
+extern "C" rpba_status rpba_outer_iteration(rpba_ctx *h, int32_t robust, double *sigma0, int32_t *lm_launches) {
+  CTX_OR_FAIL;
+  if (!ctx->intersected) RPBA_TRY(rpba_intersect(h));
+  int inner = 0, launches = 0;
+  RPBA_TRY(run_bact(ctx, &inner, &launches));
+  double s = 0.0;
+  RPBA_TRY(outer_tail(ctx, robust != 0, &s));
+  if (sigma0) *sigma0 = s;
+  if (lm_launches) *lm_launches = launches;
   return RPBA_OK;
 }
 

@@ -39,6 +39,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "../../include/rpba.h"
 #include "ffloat.cuh"
 
@@ -271,6 +273,21 @@ struct Ctx {
   float *S32 = nullptr, *Linv32 = nullptr, *ir_r32 = nullptr;
   long long *S32_off = nullptr;
   double *ir_d = nullptr, *ir_rs = nullptr, *ir_x = nullptr, *ir_t = nullptr;
+  // FP32 factorisation on the tensor cores (chol_tc): the factor's block
+  // columns of 32 as three TF32 pieces in panel-major order (block column k
+  // of sub-block l is npad_l rows of 32 floats from row tc_prow[l] + k npad_l),
+  // a TMA tensor map per piece, per step the CTA prefix sums over the
+  // sub-blocks, and a flag that a bounded wait gave up
+  float *tc_panel[3] = {nullptr, nullptr, nullptr};
+  long long *tc_prow = nullptr;
+  int *tc_sched = nullptr;
+  std::vector<int> h_tc_ctas;  // CTAs of each step
+  CUtensorMap tc_map[3];
+  int *tc_err = nullptr;
+  bool tc_ready = false;
+  // which sub-blocks the LM adjustment moves and which points the
+  // intersection handles (all by default; a share of them in sharded runs)
+  uint8_t *sub_mask = nullptr, *pt_mask = nullptr;
   // LM control per sub-block
   double *lm_lambda = nullptr, *lm_F = nullptr, *lm_Ft = nullptr, *lm_best = nullptr;
   int *lm_grace = nullptr, *lm_rej = nullptr, *lm_it = nullptr, *lm_run = nullptr;
@@ -428,6 +445,7 @@ rpba_status launch_eliminate(Ctx *ctx);
 rpba_status launch_sub_costs(Ctx *ctx, int trial, double *F_dev);
 rpba_status launch_build_rcs(Ctx *ctx, const double *lambda_dev, const int *run_dev);
 rpba_status launch_solve_rcs(Ctx *ctx, const int *run_dev, int *fail_dev);
+rpba_status tc_chol_setup(Ctx *ctx);
 rpba_status launch_pcg_blockjacobi(Ctx *ctx, const int *run_dev, int *fail_dev);
 rpba_status launch_pcg_learned(Ctx *ctx, const int *run_dev, int *fail_dev);
 void build_camera_graph(Ctx *ctx, const std::vector<int> &inst_obs_ptr, const std::vector<int> &obs_cam_sorted,

@@ -41,7 +41,7 @@ class Options(C.Structure):
                 ("isect_tol", C.c_double), ("isect_px_tol", C.c_double), ("cond_max", C.c_double),
                 ("precision", C.c_int32),
                 ("solver", C.c_int32), ("pcg_tol", C.c_double), ("pcg_max_iter", C.c_int32),
-                ("ir_steps", C.c_int32),
+                ("ir_steps", C.c_int32), ("chol_tc", C.c_int32),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", C.c_void_p)]
 
 
@@ -113,6 +113,11 @@ def load(build_if_missing: bool = True):
         "rpba_bact": (C.c_int, [vp, _ip]),
         "rpba_profile_enable": (C.c_int, [vp, C.c_int32]),
         "rpba_profile_select": (C.c_int, [vp, C.c_char_p]),
+        "rpba_get_camera_rt": (C.c_int, [vp, _dp, _dp]),
+        "rpba_set_camera_rt": (C.c_int, [vp, _dp, _dp]),
+        "rpba_set_subblock_mask": (C.c_int, [vp, C.c_void_p]),
+        "rpba_set_point_mask": (C.c_int, [vp, C.c_void_p]),
+        "rpba_outer_iteration": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
         "rpba_profile_read": (C.c_int, [vp, C.c_int32, C.c_char_p, _dp, C.POINTER(C.c_int64), _ip,
                                         C.POINTER(C.c_int64)]),
         "rpba_solver_stats": (C.c_int, [vp, _ip, _dp]),
@@ -311,6 +316,13 @@ class Rpba:
                 "active_obs": r.active_obs, "robust_started_at": r.robust_started_at,
                 "sigma0_hist": list(r.sigma0_hist[:min(r.outer, 128)])}
 
+    def outer_iteration(self, robust=True):
+        """One steady-state outer iteration (bact, exchange, robust weights,
+        TP intersection, sigma_0); returns (sigma_0, lock-step LM iterations)."""
+        s, n = C.c_double(), C.c_int32()
+        self._c(load().rpba_outer_iteration(self._h, int(bool(robust)), C.byref(s), C.byref(n)))
+        return s.value, n.value
+
     def covariance(self, ids):
         ids = _i32(ids)
         out = np.zeros((ids.size, 9))
@@ -410,6 +422,29 @@ class Rpba:
         dc, dx = np.zeros(6 * self.M), np.zeros((self.P, 3))
         self._c(load().rpba_lm_step(self._h, float(lam), _i(acc), _d(Fb), _d(Ft), _d(dc), _d(dx)))
         return acc, Fb, Ft, dc, dx
+
+    def camera_rt(self):
+        """(M, 12): rotation matrix (row-major) and translation per camera, as held."""
+        R, t = np.zeros((self.M, 9)), np.zeros((self.M, 3))
+        self._c(load().rpba_get_camera_rt(self._h, _d(R), _d(t)))
+        return np.concatenate([R, t], axis=1)
+
+    def set_camera_rt(self, Rt):
+        Rt = _f64(Rt, (self.M, 12))
+        self._c(load().rpba_set_camera_rt(self._h, _d(np.ascontiguousarray(Rt[:, :9])),
+                                          _d(np.ascontiguousarray(Rt[:, 9:]))))
+
+    def set_subblock_mask(self, mask=None):
+        """LM adjustment only of the sub-blocks with mask[l] != 0 (None: all)."""
+        m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+        assert m is None or m.size == self.L
+        self._c(load().rpba_set_subblock_mask(self._h, None if m is None else m.ctypes.data_as(C.c_void_p)))
+
+    def set_point_mask(self, mask=None):
+        """Intersections only of the points with mask[j] != 0 (None: all)."""
+        m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+        assert m is None or m.size == self.N
+        self._c(load().rpba_set_point_mask(self._h, None if m is None else m.ctypes.data_as(C.c_void_p)))
 
     def bact(self):
         it = np.zeros(self.L, np.int32)

@@ -90,7 +90,7 @@ def _assign_observations(rng, R, t, foot, X, opp, chunk=200_000):
     for s in range(0, X.shape[0], chunk):
         Xs = X[s:s + chunk]
         n = Xs.shape[0]
-        _, idx = tree.query(Xs[:, :2], k=kq)
+        _, idx = tree.query(Xs[:, :2], k=kq, workers=-1)  # parallel over query points; same result
         idx = np.asarray(idx).reshape(n, kq)
         Rc = R[idx.reshape(-1)]
         tc = t[idx.reshape(-1)]

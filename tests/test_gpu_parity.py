@@ -304,6 +304,35 @@ def test_whole_iteration_final_rms(precision, robust, outliers, solver):
         assert abs(rg["deleted_points"] - ro["deleted_points"]) <= max(3, 0.15 * ro["deleted_points"])
 
 
+def test_outer_iteration_is_one_iteration_of_the_loop():
+    """rpba_outer_iteration (the benchmark's step) is one outer iteration of
+    rpba_iterate's loop without its start and final sigma_0, stop rule or
+    elimination: with the robust stage off the two leave the same state
+    (FP64 form, same kernels: to rounding), and sigma_0 after it is the
+    oracle's after its first outer iteration."""
+    prob = synth.config(1)
+    ro = oracle.Oracle(prob).run(max_outer=1, robust=0)
+    g1 = rpba.Rpba(prob, precision=0, robust=0)
+    r1 = g1.iterate(1)
+    g2 = rpba.Rpba(prob, precision=0, robust=0)
+    s2, n2 = g2.outer_iteration(robust=False)
+    assert n2 == r1["lm_launches"] and n2 > 0
+    # the FP64 form sums the Schur blocks with atomics: two runs agree to rounding
+    assert s2 == pytest.approx(r1["sigma0_hist"][0], rel=1e-12)
+    np.testing.assert_allclose(g1.cameras(), g2.cameras(), rtol=0, atol=1e-9)
+    # weakly determined far points carry the rounding of their large coordinates
+    np.testing.assert_allclose(g1.points()[0], g2.points()[0], rtol=1e-5, atol=1e-9)
+    assert s2 == pytest.approx(ro["sigma0_hist"][0], rel=1e-9)
+    # with the robust stage on, the FP32 form's steady-state step stays within
+    # the oracle's robust trajectory to the FP32 form's sigma_0 tolerance
+    g3 = rpba.Rpba(prob, precision=1, solver=4, robust=1, robust_from_start=1)
+    o3 = oracle.Oracle(prob).run(max_outer=1, robust=1, robust_from_start=1)
+    s3, _ = g3.outer_iteration(robust=True)
+    assert s3 == pytest.approx(o3["sigma0_hist"][0], rel=1e-3)
+    for g in (g1, g2, g3):
+        g.close()
+
+
 def test_empty_subblock_single_observation_point_and_errors():
     prob = synth.tiny(seed=9, runs=[3, 3])
     prob["cam_subblock"] = np.where(prob["cam_subblock"] == 1, 2, 0).astype(np.int32)  # id 1 unused

@@ -196,3 +196,49 @@ def test_camera_scale_refuses_cameras_beyond_its_shared_memory(precision, n_poin
     s0, _ = g.sigma0()
     assert np.isfinite(s0)
     g.close()
+
+
+def _large_subblock_state(precision, **opts):
+    """400 cameras in two sub-blocks of 350 and 50: the first RCS has 2,100
+    unknowns (66 tiles of 32), so its factorisation runs 66 steps with up to
+    22 row blocks each; state after the oracle's first intersection, copies
+    moved by 2 cm."""
+    prob = synth.tiny(seed=31, nx=20, ny=20, n_points=6000, opp=4, runs=[350, 50],
+                      extent=(-38.0, 38.0, -38.0, 38.0))
+    o = oracle.Oracle(prob)
+    o.intersect()
+    rng = np.random.default_rng(7)
+    Xl, Wl = o.instance_state()
+    o.set_instance_state(Xl + rng.normal(0, 0.02, Xl.shape), Wl)
+    g = rpba.Rpba(prob, precision=precision, **opts)
+    sync_state(o, g)
+    return prob, o, g
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_direct_solver_on_a_2100_unknown_subblock(precision):
+    """Solver 2 (FP32 factorisation of the Jacobi-scaled RCS with its updates
+    on the tensor cores, FP64 iterative refinement) against the oracle's FP64
+    Cholesky step (Sec. 2) on a sub-block above 2,000 unknowns, and against the
+    same solver with the CUDA-core factorisation: both refine to the FP64
+    solution of the same system, so they agree far below the oracle tolerance."""
+    prob, o, g = _large_subblock_state(precision, solver=2, chol_tc=1)
+    n0 = 6 * len(o.sub_cameras(0))
+    assert n0 > 2000
+    _, _, g2 = _large_subblock_state(precision, solver=2, chol_tc=0)
+    acc, Fb, Ft, dc, dx = g.lm_step(1e-4)
+    acc2, _, _, dc2, _ = g2.lm_step(1e-4)
+    assert np.all(acc >= 0) and np.all(acc2 >= 0)  # no failed factorisation
+    np.testing.assert_allclose(dc, dc2, rtol=0, atol=1e-6 * np.abs(dc2).max())
+    off = 0
+    _, isub = o.instances()
+    for l in range(o.L):
+        r, fb, ft, dco, dxo = o.lm_step(l, 1e-4)
+        n = dco.size
+        tol = 1e-7 if precision == 0 else 5e-3
+        assert np.abs(dc[off:off + n] - dco).max() <= tol * np.abs(dco).max(), l
+        assert np.abs(dx[isub == l] - dxo).max() <= tol * np.abs(dxo).max(), l
+        assert acc[l] == r
+        off += n
+    for c in (g, g2):
+        c.close()
