@@ -60,7 +60,8 @@ def parse():
     p.add_argument("--config", type=int, default=DEFAULT_CONFIG)
     p.add_argument("--precision", type=int, default=1)
     p.add_argument("--solver", type=int, default=4)
-    p.add_argument("--chol-tc", type=int, default=1, help="direct solver's FP32 factorisation on the tensor cores")
+    p.add_argument("--chol-tc", type=int, default=0,
+                   help="direct solver's FP32 factorisation: 0 CUDA cores, 1 tensor cores per step, 2 persistent")
     p.add_argument("--no-extras", action="store_true", help="skip e2e / time-to-RMS / cpu legs")
     return p.parse_args()
 
@@ -186,7 +187,7 @@ def kernel_models(K, N, P, M, has_winv, pairs):
     return {
         "k_obs_sigma_f": ("hbm", K * ob + N * 25 + M * 128),
         "k_cost_chunks_f": ("hbm", K * ob + P * 72 + M * 128),
-        "k_robust_weights_f": ("hbm", K * (ob + 4) + N * 25 + M * 132),
+        "k_robust_weights_f": ("hbm", K * (ob + 12) + N * 25 + M * 132),
         "k_camera_mad_u32": ("hbm", K * ob + N * 25 + M * 136),
         "k_isect_fused_f": ("hbm", K * ob + N * 48 + P * 24 + M * 128),
         "k_camera_blocks_f32": ("hbm", K * ob + P * 60 + M * (128 + 432)),

@@ -90,6 +90,16 @@ typedef struct {
   int32_t max_reject;    /* rejected LM steps in a row that end a bact, 6 */
   int32_t robust;        /* 1: robust stage (Sec. 5.3, parallel variant) */
   int32_t robust_from_start; /* 1: robust weights from the first intersection on */
+  int32_t weight_mode;   /* the TPs' weight W^l in the other sub-blocks: 0 the refined weight of
+                            Sec. 5.1 (the point's normal matrix without sub-block l), 1 the
+                            normal matrix of all cameras, 2 a scalar rho I with rho = rho0 at
+                            the first intersection, times 1.01 per outer iteration (the
+                            ablation variants of Sec. 6.4) */
+  double rho0;           /* weight_mode 2: the first rho, 200 (Sec. 6.3, simulated data) */
+  int32_t robust_serial; /* end of the robust stage: 0 the parallel variant (eliminate every
+                            point with a down-weighted observation), 1 the serial variant of
+                            Sec. 5.3 (delete the down-weighted observations: weight 0, then
+                            eliminate points left with fewer than two; use with t_v = 3) */
   int32_t isect_max_iter;/* Gauss-Newton iterations of the intersection, 10 */
   double isect_tol;      /* ||dX|| <= tol (1 + ||X||) ends it, 1e-10 */
   double isect_px_tol;   /* ... or a step that moves the image residuals by less than this per
@@ -110,10 +120,17 @@ typedef struct {
   double pcg_tol;        /* relative residual of the PCG solve, 1e-8 */
   int32_t pcg_max_iter;  /* PCG iteration cap, 500 */
   int32_t ir_steps;      /* refinement passes of solver 2 after the first solve, 2 */
-  int32_t chol_tc;       /* solver 2's FP32 factorisation: 1 (default) left-looking with its
-                            updates on the tensor cores (tcgen05.mma kind::tf32, each factor
-                            entry split into three TF32 pieces, six products: FP32 accuracy),
-                            operands staged by TMA; 0 right-looking on the CUDA cores */
+  int32_t chol_tc;       /* solver 2's FP32 factorisation: 0 (default) right-looking on the
+                            CUDA cores; left-looking with its updates on the tensor cores
+                            (tcgen05.mma kind::tf32, each factor entry split into three TF32
+                            pieces, six products: FP32 accuracy), operands staged by TMA, as
+                            2 one persistent launch over every step of every sub-block or 1
+                            one launch per step. Same results to rounding; rpba_tune picks
+                            the fastest for a workload */
+  const char *tune_cache; /* NULL, or a file of tuned launch shapes (JSON lines, one object per
+                            workload: cameras, points, observations, sub-blocks, precision,
+                            solver and SM count): the entry of this workload, if any, is
+                            applied at create; rpba_tune writes it (the string is copied) */
   /* optional device allocator (NULL: cudaMalloc / cudaFree) */
   void *(*dev_alloc)(size_t bytes, void *user);
   void (*dev_free)(void *ptr, void *user);
@@ -159,6 +176,20 @@ rpba_status rpba_intersect(rpba_ctx *ctx);
  * (Eq. bars), with the robust stage of Sec. 5.3 when enabled. Runs
  * rpba_intersect first if it has not been run. `report` may be NULL. */
 rpba_status rpba_iterate(rpba_ctx *ctx, int32_t max_outer, rpba_report *report);
+
+/* Autotuner: times candidate launch shapes on the context's own data with
+ * CUDA events (5 runs each after one untimed run) and keeps the fastest: the
+ * CTA sizes of the intersection (64/128/256 points), the linearisation and the
+ * back-substitution (64/128/256 instances) and the robust weights (128/256/512
+ * observations), and, for the direct solver, the tensor-core factorisation's
+ * launch form (chol_tc 1 or 2). These kernels give every thread one
+ * independent item, so the choice changes timing, not results. The state is
+ * unchanged (the intersection's timing restores it). With cache_path (or the
+ * context's tune_cache when NULL) the choice is written there for the
+ * workload. chosen (nullable, 5 values): isect, lin, backsub, robust,
+ * chol_tc. Not a step of the paper's method. Errors: INVALID_ARG for an
+ * unwritable cache, CUDA. */
+rpba_status rpba_tune(rpba_ctx *ctx, const char *cache_path, int32_t *chosen);
 
 /* One outer iteration of the RPBA loop (Sec. 5) in steady state: the LM
  * adjustment of every sub-block (Eq. bact, up to options.max_inner lock-step

@@ -27,7 +27,9 @@ class Options(C.Structure):
                 ("stop_ratio", C.c_double), ("grace", C.c_int), ("max_outer", C.c_int),
                 ("max_inner", C.c_int), ("max_reject", C.c_int), ("robust", C.c_int),
                 ("robust_from_start", C.c_int), ("isect_max_iter", C.c_int),
-                ("isect_tol", C.c_double), ("isect_px_tol", C.c_double), ("cond_max", C.c_double)]
+                ("isect_tol", C.c_double), ("isect_px_tol", C.c_double), ("cond_max", C.c_double),
+                ("robust_serial", C.c_int), ("weight_mode", C.c_int), ("rho0", C.c_double),
+                ("rho", C.c_double)]
 
 
 class Report(C.Structure):
@@ -123,6 +125,8 @@ def default_options(**kw) -> Options:
     lib().orc_default_options(C.byref(o))
     for k, v in kw.items():
         setattr(o, k, v)
+    if "rho0" in kw and "rho" not in kw:
+        o.rho = o.rho0
     return o
 
 

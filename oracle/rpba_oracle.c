@@ -266,6 +266,10 @@ void orc_default_options(orc_options *o) {
   o->isect_tol = 1e-10;
   o->isect_px_tol = 1e-3;
   o->cond_max = 1e12;
+  o->robust_serial = 0;
+  o->weight_mode = 0;
+  o->rho0 = 200.0;
+  o->rho = 200.0;
 }
 
 static int cmp_ll(const void *a, const void *b) {
@@ -491,7 +495,7 @@ double orc_sigma0(const orc_ctx *c) {
   for (int j = 0; j < c->N; j++) nact += c->active[j];
   for (int k = 0; k < c->K; k++) {
     int j = c->obs_pt[k];
-    if (!c->active[j]) continue;
+    if (!c->active[j] || c->w[k] == 0.0) continue;  /* w = 0: deleted (serial robust variant) */
     obs_residual(c, k, c->R, c->t, c->X + 3 * j, v, NULL, NULL);
     sum += c->w[k] * quad_w(c->obs_winv + 3 * k, v);
     kact++;
@@ -689,7 +693,13 @@ static int intersect_one(orc_ctx *c, const orc_options *o, int j, int tp_only, d
   for (int e = 0; e < 3; e++) c->X[3 * j + e] = X[e];
   for (int qi = 0; qi < nq; qi++) {
     double *W = c->Wl + 6 * c->pt_inst[q0 + qi];
-    for (int e = 0; e < 6; e++) W[e] = (nq >= 2) ? Ntot[e] - Nl[6 * qi + e] : 0.0;
+    for (int e = 0; e < 6; e++) {
+      double refined = Ntot[e] - Nl[6 * qi + e];           /* Sec. 5.1 */
+      double all = Ntot[e];                                /* all cameras (Sec. 6.4) */
+      double scalar = (e == 0 || e == 3 || e == 5) ? o->rho : 0.0;  /* rho I (Sec. 6.4) */
+      double val = o->weight_mode == 1 ? all : (o->weight_mode == 2 ? scalar : refined);
+      W[e] = (nq >= 2) ? val : 0.0;
+    }
   }
   return 0;
 }
@@ -1003,7 +1013,12 @@ static void tp_copies_from_points(orc_ctx *c, int tp_only) {
   }
 }
 
-void orc_run(orc_ctx *c, const orc_options *o, orc_report *r) {
+void orc_run(orc_ctx *c, const orc_options *o_in, orc_report *r) {
+  /* rho of the scalar weight: rho0 at the first intersection, times 1.01
+   * for every outer iteration after it */
+  orc_options oo = *o_in;
+  orc_options *o = &oo;
+  o->rho = o->rho0;
   memset(r, 0, sizeof(*r));
   r->robust_started_at = -1;
   int n_start = 0;
@@ -1032,6 +1047,7 @@ void orc_run(orc_ctx *c, const orc_options *o, orc_report *r) {
     }
     if (robust_on) orc_robust_weights(c, o->t_v, o->downweight);
     /* bars: intersection of the TPs with all cameras fixed */
+    o->rho *= 1.01;
     orc_intersect(c, o, 1);
     tp_copies_from_points(c, 1);
     s = orc_sigma0(c);
@@ -1051,8 +1067,21 @@ void orc_run(orc_ctx *c, const orc_options *o, orc_report *r) {
       break;
     }
   }
-  if (robust_on) {
-    /* eliminate every point with a down-weighted observation (Sec. 5.3) */
+  if (robust_on && o->robust_serial) {
+    /* serial variant (Sec. 5.3): the down-weighted observations are deleted
+     * (weight 0); a point seen by fewer than two cameras afterwards is
+     * eliminated */
+    int *cnt = (int *)calloc((size_t)(c->N > 0 ? c->N : 1), sizeof(int));
+    for (int k = 0; k < c->K; k++) {
+      if (c->w[k] != 1.0) c->w[k] = 0.0;
+      else cnt[c->obs_pt[k]]++;
+    }
+    for (int j = 0; j < c->N; j++)
+      if (cnt[j] < 2) c->active[j] = 0;
+    free(cnt);
+  } else if (robust_on) {
+    /* parallel variant: eliminate every point with a down-weighted
+     * observation (Sec. 5.3) */
     for (int k = 0; k < c->K; k++)
       if (c->w[k] != 1.0) c->active[c->obs_pt[k]] = 0;
   }

@@ -54,6 +54,16 @@ typedef struct {
   double isect_tol;    /* ||dX|| <= tol (1 + ||X||) ends the intersection, 1e-10 */
   double isect_px_tol; /* or a step moving the image residuals by < this per observation, 1e-3 px */
   double cond_max;     /* Frobenius condition number above which a point is dropped, 1e12 */
+  int robust_serial;   /* 1: the serial variant of Sec. 5.3 at the end of the robust stage
+                          (delete the down-weighted observations, eliminate points left with
+                          fewer than two); 0: the parallel variant (eliminate every point with a
+                          down-weighted observation) */
+  int weight_mode;     /* the TPs' weight W^l in the other sub-blocks: 0 the refined weight of
+                          Sec. 5.1 (normal matrix without sub-block l), 1 the normal matrix of all
+                          cameras, 2 a scalar rho I (the ablations of Sec. 6.4) */
+  double rho0;         /* weight_mode 2: rho of the first intersection, times 1.01 per outer
+                          iteration (the plain approach's schedule, Sec. 6.3; 200) */
+  double rho;          /* the rho in effect (set by orc_run; for a direct orc_intersect, rho0) */
 } orc_options;
 
 typedef struct {

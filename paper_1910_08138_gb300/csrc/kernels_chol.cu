@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "rpba_internal.cuh"
@@ -254,28 +255,36 @@ __global__ void __launch_bounds__(256, 3) k_chol_update(T *S, T *Linv, CholView 
 // ---------------------------------------------------------------------------
 // FP32 factorisation with the updates on the tensor cores (chol_tc)
 //
-// Left-looking, one launch per block column J of 32: the CTA of (sub-block
-// l, row block i) gathers the 128 rows {diagonal rows 32J .. 32J+31} and
-// {96 rows below, from 32J + 32 + 96 i} of every finished block column k < J
-// and accumulates in tensor memory
+// Left-looking over block columns J of 32. A task (sub-block l, step J, row
+// block i) gathers the 128 rows {diagonal rows 32J .. 32J+31} and {96 rows
+// below, from 32J + 32 + 96 i} of every finished block column k < J and
+// accumulates in tensor memory
 //     U = sum_k P_k[rows] P_k[32J .. 32J+31]^T          (128 x 32, K = 32 J)
 // with tcgen05.mma kind::tf32: each factor entry is held as three TF32 pieces
 // h + m + l (h, m rounded to TF32, l the exact FP32 remainder) and the six
 // products hh, hm, mh, hl, lh, mm are accumulated, which keeps the update at
 // FP32 accuracy (the dropped products are below 2^-31 relative). Operands
 // arrive by TMA (128-byte swizzle) in a two-stage ring; one thread issues the
-// TMA loads and the MMAs, tcgen05.commit frees a stage. Then every CTA of the
+// TMA loads and the MMAs, tcgen05.commit frees a stage. Then every task of the
 // step factors the updated diagonal tile A_JJ - U[0:32] itself (one warp; the
-// result is the same in every CTA) and solves its rows:
+// result is the same in every task) and solves its rows:
 //     L_iJ = (A_iJ - U_i) L_JJ^-T,
-// writing them to the row-major factor (read by the triangular solves) and
-// as TF32 pieces to block column J's panel (read by the later steps). The
-// CTA of row block 0 also stores L_JJ and its inverse. Every wait is bounded
-// (tc::mbar_wait); on a timeout the CTA records it in err, marks the
-// sub-block failed, waits (bounded) for its own MMAs and frees its TMEM.
+// writing them to the row-major factor (read by the triangular solves, which
+// take the diagonal steps from the inverted tiles, so A_JJ itself is only
+// read here) and as TF32 pieces to block column J's panel (read by the later
+// steps). The task of row block 0 stores L_JJ^-1. Every wait is bounded
+// (tc::mbar_wait); on a timeout the task records it in err, marks the
+// sub-block failed, waits (bounded) for its own MMAs and loads.
+//
+// Two launch forms: one launch per step (k_chol_tc), or one persistent
+// cooperative launch (k_chol_tc_persistent) whose CTAs take the tasks of all
+// steps of all sub-blocks from a queue ordered by step (within a step the
+// larger sub-blocks first); a task waits (bounded) until every task of its
+// sub-block's previous step has finished, so sub-blocks of uneven size
+// advance independently instead of in lock step.
 // ---------------------------------------------------------------------------
 #define TC_ROWS 128                            // rows of one MMA (M)
-#define TC_BELOW 96                            // rows below the diagonal tile per CTA
+#define TC_BELOW 96                            // rows below the diagonal tile per task
 #define TC_PIECE_BYTES (TC_ROWS * CT * 4)      // one piece of one stage: 16 KB
 #define TC_STAGE_BYTES (3 * TC_PIECE_BYTES)    // three pieces: 48 KB
 #define TC_STAGES 2
@@ -292,9 +301,17 @@ struct TcView {
   int *fail;
   float *P0, *P1, *P2;      // panel pieces
   const long long *prow;
-  const int *sched;         // this step's L+1 prefix sums of CTAs
+  const int *sched;         // per-step launch: this step's L+1 prefix sums of CTAs
   int L;
   int *err;
+  // persistent launch: the task queue (l, J, i) and its head, the finished
+  // tasks per (sub-block, step), the task count per (sub-block, step)
+  const int4 *tasks;
+  int n_tasks;
+  int *head;
+  int *done;
+  const int *need;
+  int T_max;
 };
 
 __device__ inline void tc_split3(float x, float &h, float &m, float &l) {
@@ -304,76 +321,69 @@ __device__ inline void tc_split3(float x, float &h, float &m, float &l) {
   l = r - m;        // exact
 }
 
-__global__ void __launch_bounds__(128) k_chol_tc(const __grid_constant__ CUtensorMap tm0,
-                                                 const __grid_constant__ CUtensorMap tm1,
-                                                 const __grid_constant__ CUtensorMap tm2, TcView v, int J) {
-  extern __shared__ uint8_t tc_smem_raw[];
-  __shared__ __align__(8) uint64_t bar_full[TC_STAGES], bar_empty[TC_STAGES], bar_done;
-  __shared__ uint32_t tmem_base;
-  __shared__ float Ls[CT * CLD], Xs[CT * CLD];
-  __shared__ int sh_ok, sh_bad;
-  int loc;
-  int l = sched_find(v.sched, v.L, blockIdx.x, &loc);
-  if (!v.run[l] || v.fail[l]) return;  // CTA-uniform
-  int np = v.npad[l];
-  if (32 * J >= np) return;
+// what a CTA keeps across the tasks it runs: its barriers, TMEM, and the
+// count of stage fills and accumulations (the barriers' phase parities)
+struct TcCta {
+  uint64_t *full, *empty, *done;
+  uint32_t tmem;
+  uint8_t *base;
+  uint32_t fills;  // stage fills so far (stage = fills % TC_STAGES)
+  uint32_t dones;  // accumulations completed so far
+};
+
+struct TcShared {
+  float Ls[CT * CLD], Xs[CT * CLD];
+  int ok, bad;
+};
+
+// one task: the update of (l, J, loc), the diagonal factor, the rows' solve.
+// Returns false when a bounded wait gave up (the sub-block is marked failed).
+__device__ bool tc_task(const CUtensorMap *tm0, const CUtensorMap *tm1, const CUtensorMap *tm2, const TcView &v,
+                        int l, int J, int loc, TcCta &c, TcShared &sh) {
+  const int np = v.npad[l];
   const int d0 = 32 * J, r0 = d0 + 32 + TC_BELOW * loc;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   float *A = v.S + v.off[l];
   float acc[32];
 #pragma unroll
-  for (int c = 0; c < 32; c++) acc[c] = 0.f;
+  for (int q = 0; q < 32; q++) acc[q] = 0.f;
 
   if (J > 0) {
-    uint8_t *base = (uint8_t *)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
-    if (tid == 0) {
-      for (int s = 0; s < TC_STAGES; s++) {
-        tc::mbar_init(&bar_full[s], 1);
-        tc::mbar_init(&bar_empty[s], 1);
-      }
-      tc::mbar_init(&bar_done, 1);
-      tc::fence_mbar_init();
-      tc::prefetch_tmap(&tm0);
-      tc::prefetch_tmap(&tm1);
-      tc::prefetch_tmap(&tm2);
-    }
-    if (warp == 0) {
-      tc::tmem_alloc(&tmem_base, 32);
-      tc::tmem_relinquish();
-    }
-    tc::tc_fence_before();
-    __syncthreads();
-    tc::tc_fence_after();
-    const uint32_t tmem = tmem_base;
     if (tid == 0) {
       bool ok = true;
       const long long prow = v.prow[l];
-      const CUtensorMap *maps[3] = {&tm0, &tm1, &tm2};
-      auto load = [&](int k, int s) {
-        uint8_t *st = base + s * TC_STAGE_BYTES;
-        tc::mbar_arrive_expect_tx(&bar_full[s], TC_STAGE_BYTES);
+      const CUtensorMap *maps[3] = {tm0, tm1, tm2};
+      const uint32_t f0 = c.fills;
+      auto load = [&](int k) {
+        uint32_t f = f0 + (uint32_t)k;
+        int s = (int)(f % TC_STAGES);
+        uint8_t *st = c.base + s * TC_STAGE_BYTES;
+        tc::mbar_arrive_expect_tx(&c.full[s], TC_STAGE_BYTES);
         int y = (int)(prow + (long long)k * np);
         for (int p = 0; p < 3; p++) {
           uint8_t *pb = st + p * TC_PIECE_BYTES;
-          tc::tma_load_2d(pb, maps[p], 0, y + d0, &bar_full[s]);
-          for (int b = 0; b < 3; b++) tc::tma_load_2d(pb + (1 + b) * 32 * 128, maps[p], 0, y + r0 + 32 * b, &bar_full[s]);
+          tc::tma_load_2d(pb, maps[p], 0, y + d0, &c.full[s]);
+          for (int b = 0; b < 3; b++) tc::tma_load_2d(pb + (1 + b) * 32 * 128, maps[p], 0, y + r0 + 32 * b, &c.full[s]);
         }
       };
       const uint32_t idesc = tc::idesc_tf32(TC_ROWS, CT);
       // products of the pieces (A piece, B piece): hh hm mh hl lh mm
       const int pa[6] = {0, 0, 1, 0, 2, 1}, pb[6] = {0, 1, 0, 2, 0, 1};
-      int issued_loads = 0;
+      int issued = 0;
       for (int k = 0; k < J && k < TC_STAGES; k++) {
-        load(k, k);
-        issued_loads++;
+        // a stage is reused only after the MMAs that read it completed: the
+        // previous task's accumulation finished before its epilogue
+        load(k);
+        issued++;
       }
       int k = 0;
       for (; k < J; k++) {
-        int s = k % TC_STAGES;
-        uint32_t ph = (uint32_t)(k / TC_STAGES) & 1u;
-        if (!tc::mbar_wait(&bar_full[s], ph, TC_WAIT_NS)) { ok = false; break; }
+        uint32_t f = f0 + (uint32_t)k;
+        int s = (int)(f % TC_STAGES);
+        uint32_t ph = (f / TC_STAGES) & 1u;
+        if (!tc::mbar_wait(&c.full[s], ph, TC_WAIT_NS)) { ok = false; break; }
         tc::tc_fence_after();
-        uint32_t sa = tc::smem_u32(base + s * TC_STAGE_BYTES);
+        uint32_t sa = tc::smem_u32(c.base + s * TC_STAGE_BYTES);
 #pragma unroll
         for (int kk = 0; kk < 4; kk++) {  // K = 8 TF32 (32 bytes) per MMA
           uint64_t d[3];
@@ -381,38 +391,41 @@ __global__ void __launch_bounds__(128) k_chol_tc(const __grid_constant__ CUtenso
           for (int p = 0; p < 3; p++) d[p] = tc::desc_sw128_kmajor(sa + p * TC_PIECE_BYTES + kk * 32);
 #pragma unroll
           for (int t = 0; t < 6; t++)  // B = the diagonal rows: the first 32 rows of its piece
-            tc::mma_tf32(tmem, d[pa[t]], d[pb[t]], idesc, (k > 0 || kk > 0 || t > 0) ? 1u : 0u);
+            tc::mma_tf32(c.tmem, d[pa[t]], d[pb[t]], idesc, (k > 0 || kk > 0 || t > 0) ? 1u : 0u);
         }
-        tc::mma_commit(&bar_empty[s]);
+        tc::mma_commit(&c.empty[s]);
         if (k + TC_STAGES < J) {
-          if (!tc::mbar_wait(&bar_empty[s], ph, TC_WAIT_NS)) { ok = false; k++; break; }
-          load(k + TC_STAGES, s);
-          issued_loads++;
+          if (!tc::mbar_wait(&c.empty[s], ph, TC_WAIT_NS)) { ok = false; k++; break; }
+          load(k + TC_STAGES);
+          issued++;
         }
       }
-      // every MMA issued so far completes before bar_done's arrival
-      tc::mma_commit(&bar_done);
-      bool done = tc::mbar_wait(&bar_done, 0, TC_WAIT_NS);
+      // every MMA issued so far completes before this arrival
+      tc::mma_commit(c.done);
+      bool fin = tc::mbar_wait(c.done, c.dones & 1u, TC_WAIT_NS);
       if (!ok) {
         // loads still in flight land in this CTA's shared memory: wait for
-        // them (bounded) before leaving
-        for (int q = k; q < issued_loads; q++)
-          tc::mbar_wait(&bar_full[q % TC_STAGES], (uint32_t)(q / TC_STAGES) & 1u, TC_WAIT_NS);
+        // them (bounded) before going on
+        for (int q = k; q < issued; q++) {
+          uint32_t f = f0 + (uint32_t)q;
+          tc::mbar_wait(&c.full[f % TC_STAGES], (f / TC_STAGES) & 1u, TC_WAIT_NS);
+        }
       }
-      sh_ok = ok && done;
+      sh.ok = ok && fin;
     }
+    c.fills += (uint32_t)J;
+    c.dones += 1;
     __syncthreads();
     tc::tc_fence_after();
-    if (sh_ok) tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), acc);
+    if (sh.ok) tc::tmem_ld32(c.tmem + ((uint32_t)(32 * warp) << 16), acc);
     tc::tc_fence_before();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, 32);
-    if (!sh_ok) {
+    if (!sh.ok) {
       if (tid == 0) {
         atomicExch(v.err, 1);
         v.fail[l] = 1;
       }
-      return;
+      return false;
     }
   }
 
@@ -420,21 +433,18 @@ __global__ void __launch_bounds__(128) k_chol_tc(const __grid_constant__ CUtenso
   if (warp == 0) {
     float x[CT];
 #pragma unroll
-    for (int c = 0; c < CT; c++) x[c] = (c <= lane) ? A[(size_t)(d0 + lane) * np + d0 + c] - acc[c] : 0.f;
-    bool okp = warp_potrf_inv<float>(x, Ls, Xs);
-    if (lane == 0) sh_bad = !okp;
+    for (int q = 0; q < CT; q++) x[q] = (q <= lane) ? A[(size_t)(d0 + lane) * np + d0 + q] - acc[q] : 0.f;
+    bool okp = warp_potrf_inv<float>(x, sh.Ls, sh.Xs);
+    if (lane == 0) sh.bad = !okp;
   }
   __syncthreads();
-  if (sh_bad) {
+  if (sh.bad) {
     if (tid == 0 && loc == 0) v.fail[l] = 1;
-    return;
+    return true;
   }
   if (warp == 0 && loc == 0) {
     float *Li = v.Linv + v.linv_off[l] + (size_t)J * CT * CT;
-    for (int c = 0; c < CT; c++) {
-      if (c <= lane) A[(size_t)(d0 + lane) * np + d0 + c] = Ls[lane * CLD + c];
-      Li[lane * CT + c] = Xs[lane * CLD + c];
-    }
+    for (int q = 0; q < CT; q++) Li[lane * CT + q] = sh.Xs[lane * CLD + q];
   }
   // rows below: L_iJ = (A_iJ - U_i) L_JJ^-T (L_JJ^-1 lower triangular)
   if (warp > 0) {
@@ -442,22 +452,146 @@ __global__ void __launch_bounds__(128) k_chol_tc(const __grid_constant__ CUtenso
     if (r < np) {
       float crow[CT];
 #pragma unroll
-      for (int c = 0; c < CT; c++) crow[c] = A[(size_t)r * np + d0 + c] - acc[c];
+      for (int q = 0; q < CT; q++) crow[q] = A[(size_t)r * np + d0 + q] - acc[q];
       long long pr = (v.prow[l] + (long long)J * np + r) * CT;
 #pragma unroll
-      for (int c = 0; c < CT; c++) {
+      for (int q = 0; q < CT; q++) {
         float s = 0.f;
 #pragma unroll
-        for (int e = 0; e <= c; e++) s = fmaf(crow[e], Xs[c * CLD + e], s);
-        A[(size_t)r * np + d0 + c] = s;
+        for (int e = 0; e <= q; e++) s = fmaf(crow[e], sh.Xs[q * CLD + e], s);
+        A[(size_t)r * np + d0 + q] = s;
         float h, m, lo;
         tc_split3(s, h, m, lo);
-        v.P0[pr + c] = h;
-        v.P1[pr + c] = m;
-        v.P2[pr + c] = lo;
+        v.P0[pr + q] = h;
+        v.P1[pr + q] = m;
+        v.P2[pr + q] = lo;
       }
     }
   }
+  return true;
+}
+
+// barriers and TMEM of a CTA (128 threads)
+__device__ inline void tc_cta_init(TcCta &c, uint64_t *full, uint64_t *empty, uint64_t *done, uint32_t *tmem_slot,
+                                   uint8_t *raw, const CUtensorMap *tm0, const CUtensorMap *tm1,
+                                   const CUtensorMap *tm2) {
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < TC_STAGES; s++) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(done, 1);
+    tc::fence_mbar_init();
+    tc::prefetch_tmap(tm0);
+    tc::prefetch_tmap(tm1);
+    tc::prefetch_tmap(tm2);
+  }
+  if ((tid >> 5) == 0) {
+    tc::tmem_alloc(tmem_slot, 32);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  c.full = full;
+  c.empty = empty;
+  c.done = done;
+  c.tmem = *tmem_slot;
+  c.base = (uint8_t *)(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
+  c.fills = 0;
+  c.dones = 0;
+}
+
+__device__ inline void tc_cta_fini(TcCta &c) {
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(c.tmem, 32);
+}
+
+__global__ void __launch_bounds__(128) k_chol_tc(const __grid_constant__ CUtensorMap tm0,
+                                                 const __grid_constant__ CUtensorMap tm1,
+                                                 const __grid_constant__ CUtensorMap tm2, TcView v, int J) {
+  extern __shared__ uint8_t tc_smem_raw[];
+  __shared__ __align__(8) uint64_t bar_full[TC_STAGES], bar_empty[TC_STAGES], bar_done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ TcShared sh;
+  int loc;
+  int l = sched_find(v.sched, v.L, blockIdx.x, &loc);
+  if (!v.run[l] || v.fail[l]) return;  // CTA-uniform
+  if (32 * J >= v.npad[l]) return;
+  if (J == 0) {  // no update: no barriers, no TMEM
+    TcCta c{};
+    tc_task(&tm0, &tm1, &tm2, v, l, J, loc, c, sh);
+    return;
+  }
+  TcCta c;
+  tc_cta_init(c, bar_full, bar_empty, &bar_done, &tmem_slot, tc_smem_raw, &tm0, &tm1, &tm2);
+  tc_task(&tm0, &tm1, &tm2, v, l, J, loc, c, sh);
+  tc_cta_fini(c);
+}
+
+// acquire load of a completion counter
+__device__ inline int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__global__ void __launch_bounds__(128) k_chol_tc_persistent(const __grid_constant__ CUtensorMap tm0,
+                                                            const __grid_constant__ CUtensorMap tm1,
+                                                            const __grid_constant__ CUtensorMap tm2, TcView v) {
+  extern __shared__ uint8_t tc_smem_raw[];
+  __shared__ __align__(8) uint64_t bar_full[TC_STAGES], bar_empty[TC_STAGES], bar_done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ TcShared sh;
+  __shared__ int cur, go;
+  TcCta c;
+  tc_cta_init(c, bar_full, bar_empty, &bar_done, &tmem_slot, tc_smem_raw, &tm0, &tm1, &tm2);
+  for (;;) {
+    if (threadIdx.x == 0) cur = atomicAdd(v.head, 1);
+    __syncthreads();
+    const int t = cur;
+    if (t >= v.n_tasks) break;
+    const int4 task = v.tasks[t];
+    const int l = task.x, J = task.y, loc = task.z;
+    if (threadIdx.x == 0) {
+      // every task of the previous step of this sub-block has finished: the
+      // queue holds all of them before this one, and they run on CTAs that
+      // are resident (cooperative launch), so the wait ends
+      bool ok = true;
+      if (J > 0) {
+        const int *cnt = v.done + (size_t)l * v.T_max + (J - 1);
+        const int want = v.need[(size_t)l * v.T_max + (J - 1)];
+        if (ld_acquire(cnt) < want) {
+          uint64_t t0 = tc::global_ns();
+          while (ld_acquire(cnt) < want) {
+            __nanosleep(200);
+            if (tc::global_ns() - t0 > TC_WAIT_NS) { ok = false; break; }
+          }
+        }
+        // the panels that task wrote with generic stores are read by TMA
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+      }
+      if (!ok) {
+        atomicExch(v.err, 1);
+        v.fail[l] = 1;
+      }
+      // after any error the remaining tasks are only counted, so that no
+      // task waits on work that will not come
+      go = ok && v.run[l] && !v.fail[l] && !*(volatile int *)v.err;
+    }
+    __syncthreads();
+    if (go) tc_task(&tm0, &tm1, &tm2, v, l, J, loc, c, sh);
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(v.done + (size_t)l * v.T_max + J, 1);
+    }
+  }
+  tc_cta_fini(c);
 }
 
 // forward L z = r and backward L^T x = z (r in, x out, may alias), one thread
@@ -776,6 +910,39 @@ rpba_status tc_chol_setup(Ctx *ctx) {
     }
   }
   RPBA_CUDA(cudaFuncSetAttribute(k_chol_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  RPBA_CUDA(cudaFuncSetAttribute(k_chol_tc_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  // the persistent form's queue: every (sub-block, step, row block) task,
+  // ordered by step, within a step the larger sub-blocks first
+  {
+    std::vector<int4> tasks;
+    std::vector<int> need((size_t)L * steps, 0);
+    std::vector<int> order(L);
+    for (int l = 0; l < L; l++) order[l] = l;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ctx->h_npad[a] > ctx->h_npad[b]; });
+    for (int J = 0; J < steps; J++)
+      for (int l : order) {
+        int np = ctx->h_npad[l], below = np - CT * J - CT;
+        if (CT * J >= np) continue;
+        int c = 1 + (below > 0 ? (below + TC_BELOW - 1) / TC_BELOW : 0);
+        need[(size_t)l * steps + J] = c;
+        for (int i = 0; i < c; i++) tasks.push_back(make_int4(l, J, i, 0));
+      }
+    ctx->tc_n_tasks = (int)tasks.size();
+    RPBA_TRY(ctx_alloc(ctx, (void **)&ctx->tc_tasks, sizeof(int4) * std::max<size_t>(tasks.size(), 1)));
+    RPBA_CUDA(cudaMemcpyAsync(ctx->tc_tasks, tasks.data(), sizeof(int4) * tasks.size(), cudaMemcpyHostToDevice,
+                              ctx->stream));
+    RPBA_TRY(ctx_alloc(ctx, (void **)&ctx->tc_need, sizeof(int) * need.size()));
+    RPBA_CUDA(cudaMemcpyAsync(ctx->tc_need, need.data(), sizeof(int) * need.size(), cudaMemcpyHostToDevice,
+                              ctx->stream));
+    // counters: the queue head, then the finished tasks per (sub-block, step)
+    RPBA_TRY(ctx_alloc(ctx, (void **)&ctx->tc_count, sizeof(int) * (1 + need.size())));
+    int per_sm = 0, sms = 0, dev = 0;
+    RPBA_CUDA(cudaGetDevice(&dev));
+    RPBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    RPBA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_tc_persistent, 128, TC_SMEM));
+    ctx->tc_grid = std::max(1, std::min(ctx->tc_n_tasks, std::max(per_sm, 1) * sms));
+    RPBA_CUDA(cudaStreamSynchronize(ctx->stream));  // the host vectors go out of scope
+  }
   ctx->tc_ready = true;
   return RPBA_OK;
 }
@@ -783,7 +950,25 @@ rpba_status tc_chol_setup(Ctx *ctx) {
 // the FP32 factorisation of every running sub-block on the tensor cores
 static rpba_status factor_tc(Ctx *ctx, float *S, float *Linv, const long long *off, const int *run, int *fail) {
   TcView tv{S, off, ctx->npad, Linv, ctx->linv_off, run, fail, ctx->tc_panel[0], ctx->tc_panel[1],
-            ctx->tc_panel[2], ctx->tc_prow, nullptr, ctx->L, ctx->tc_err};
+            ctx->tc_panel[2], ctx->tc_prow, nullptr, ctx->L, ctx->tc_err,
+            ctx->tc_tasks, ctx->tc_n_tasks, ctx->tc_count, ctx->tc_count + 1, ctx->tc_need, ctx->max_tiles};
+  if (ctx->opt.chol_tc == 2) {  // one persistent cooperative launch
+    RPBA_CUDA(cudaMemsetAsync(ctx->tc_count, 0, sizeof(int) * (1 + (size_t)ctx->L * ctx->max_tiles), ctx->stream));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ctx->tc_grid);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = TC_SMEM;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    RPBA_KERNEL(ctx, "k_chol_tc_persistent",
+                RPBA_CUDA(cudaLaunchKernelEx(&cfg, k_chol_tc_persistent, ctx->tc_map[0], ctx->tc_map[1],
+                                             ctx->tc_map[2], tv)));
+    return RPBA_OK;
+  }
   for (int J = 0; J < ctx->max_tiles; J++) {
     int n = ctx->h_tc_ctas[J];
     if (n == 0) break;

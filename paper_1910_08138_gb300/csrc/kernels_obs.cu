@@ -53,7 +53,20 @@ struct View {
   const float *obs_xylo;
   float *Xlt_hi, *Xlt_lo;
   float *Wl32;
+  // the TPs' weight: 0 refined (Sec. 5.1), 1 all cameras, 2 rho I with rho
+  // read from device memory (it grows per outer iteration: graphs replay)
+  int wmode;
+  const double *wrho;
 };
+
+// the weight W^l written for a TP instance under the weight mode (the
+// ablations of Sec. 6.4): element e of the sym3 from the refined value and
+// the point's full normal matrix
+__device__ inline double tp_weight(const View &v, int e, double refined, double full) {
+  if (v.wmode == 1) return full;
+  if (v.wmode == 2) return (e == 0 || e == 3 || e == 5) ? *v.wrho : 0.0;
+  return refined;
+}
 
 static View make_view(Ctx *c) {
   View v;
@@ -73,6 +86,8 @@ static View make_view(Ctx *c) {
   v.dC32 = c->dC32;
   v.camff = c->camff; v.camff_t = c->camff_t; v.obs_xylo = c->obs_xylo;
   v.Xlt_hi = c->Xlt_hi; v.Xlt_lo = c->Xlt_lo; v.Wl32 = c->Wl32;
+  v.wmode = c->opt.weight_mode;
+  v.wrho = c->wrho;
   return v;
 }
 
@@ -314,6 +329,7 @@ __global__ void k_obs_sigma(View v, double *part) {
     double W0 = 1, W1 = 0, W2 = 1;
     if (v.has_winv) { W0 = v.obs_winv[3 * k]; W1 = v.obs_winv[3 * k + 1]; W2 = v.obs_winv[3 * k + 2]; }
     double w = v.obs_w[k];
+    if (w == 0.0) continue;  // deleted by the serial robust variant
     acc[0] += w * (W0 * r0 * r0 + 2.0 * W1 * r0 * r1 + W2 * r1 * r1);
     acc[1] += 1.0;
     if (w == 1.0) {
@@ -326,6 +342,28 @@ __global__ void k_obs_sigma(View v, double *part) {
 
 // FP32 form: the same sums from float-float residuals (Eq. ta) formed in
 // FP32, each thread accumulating float-float (TwoSum), the blocks in FP64
+__device__ void sigma_cta_sums(float sh, float sl, float rh, float rl, int n1, int n3, int np, double *o);
+
+// one observation's sigma_0 terms from its float-float residual (FP32 form)
+__device__ inline void sigma_obs_terms(const View &v, int k, int i, int j, float &sh, float &sl, float &rh,
+                                       float &rl, int &n1, int &n3) {
+  if (v.obs_w32[k] == 0.f) return;  // deleted by the serial robust variant
+  float r0, r1;
+  ff_residual(v.camff + FF_CAM * (size_t)i, v.X_hi + 3 * (size_t)j, v.X_lo + 3 * (size_t)j, v.obs_xy32[2 * k],
+              v.obs_xylo[2 * k], v.obs_xy32[2 * k + 1], v.obs_xylo[2 * k + 1], r0, r1);
+  float W0 = 1.f, W1 = 0.f, W2 = 1.f;
+  if (v.has_winv) { W0 = v.obs_winv32[3 * k]; W1 = v.obs_winv32[3 * k + 1]; W2 = v.obs_winv32[3 * k + 2]; }
+  float w = v.obs_w32[k], e;
+  sh = ff_two_sum(sh, w * (W0 * r0 * r0 + 2.f * W1 * r0 * r1 + W2 * r1 * r1), e);
+  sl += e;
+  n1++;
+  if (w == 1.f) {
+    rh = ff_two_sum(rh, r0 * r0 + r1 * r1, e);
+    rl += e;
+    n3++;
+  }
+}
+
 __global__ void k_obs_sigma_f(View v, double *part) {
   float sh = 0.f, sl = 0.f, rh = 0.f, rl = 0.f;
   int n1 = 0, n3 = 0, np = 0;
@@ -333,23 +371,15 @@ __global__ void k_obs_sigma_f(View v, double *part) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < v.K; k += gridDim.x * blockDim.x) {
     int j = v.obs_pt[k];
     if (!v.active[j]) continue;
-    int i = v.obs_cam[k];
-    float r0, r1;
-    ff_residual(v.camff + FF_CAM * (size_t)i, v.X_hi + 3 * (size_t)j, v.X_lo + 3 * (size_t)j, v.obs_xy32[2 * k],
-                v.obs_xylo[2 * k], v.obs_xy32[2 * k + 1], v.obs_xylo[2 * k + 1], r0, r1);
-    float W0 = 1.f, W1 = 0.f, W2 = 1.f;
-    if (v.has_winv) { W0 = v.obs_winv32[3 * k]; W1 = v.obs_winv32[3 * k + 1]; W2 = v.obs_winv32[3 * k + 2]; }
-    float w = v.obs_w32[k], e;
-    sh = ff_two_sum(sh, w * (W0 * r0 * r0 + 2.f * W1 * r0 * r1 + W2 * r1 * r1), e);
-    sl += e;
-    n1++;
-    if (w == 1.f) {
-      rh = ff_two_sum(rh, r0 * r0 + r1 * r1, e);
-      rl += e;
-      n3++;
-    }
+    sigma_obs_terms(v, k, v.obs_cam[k], j, sh, sl, rh, rl, n1, n3);
   }
-  // CTA sums in float-float and integers (off the FP64 pipe); thread 0 writes the doubles
+  sigma_cta_sums(sh, sl, rh, rl, n1, n3, np, part + 5 * blockIdx.x);
+}
+
+// the sigma_0 sums of a CTA in float-float and integers (off the FP64 pipe):
+// sum w v^T W v, active observations, sum |v|^2 and count of w == 1, active
+// points; thread 0 writes them as 5 doubles to o
+__device__ void sigma_cta_sums(float sh, float sl, float rh, float rl, int n1, int n3, int np, double *o) {
   __shared__ float2 wf[2][32];
   __shared__ int wi[3][32];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -381,7 +411,6 @@ __global__ void k_obs_sigma_f(View v, double *part) {
       b = ff_add(b, wf[1][w]);
       c1 += wi[0][w]; c3 += wi[1][w]; cp += wi[2][w];
     }
-    double *o = part + 5 * blockIdx.x;
     o[0] = ff_to_double(a);
     o[1] = (double)c1;
     o[2] = ff_to_double(b);
@@ -615,13 +644,16 @@ __global__ void k_isect_point(View v, int *state, int *iter, const T *part, int 
         }
         for (int e = 0; e < 6; e++) {
           float2 w = make_float2(Wh[e], Wlo[e]);
-          v.Wl[6 * (size_t)q + e] = tp ? ff_to_double(w) : 0.0;
-          v.Wl32[6 * (size_t)q + e] = tp ? __fadd_rn(Wh[e], Wlo[e]) : 0.f;
+          double wd = tp_weight(v, e, ff_to_double(w), (double)N[e]);
+          v.Wl[6 * (size_t)q + e] = tp ? wd : 0.0;
+          v.Wl32[6 * (size_t)q + e] = tp ? (v.wmode ? (float)wd : __fadd_rn(Wh[e], Wlo[e])) : 0.f;
         }
       } else {
-        for (int e = 0; e < 6; e++) v.Wl[6 * (size_t)q + e] = tp ? (double)(N[e] - o[e]) : 0.0;
+        for (int e = 0; e < 6; e++)
+          v.Wl[6 * (size_t)q + e] = tp ? tp_weight(v, e, (double)(N[e] - o[e]), (double)N[e]) : 0.0;
         if (v.Wl32)
-          for (int e = 0; e < 6; e++) v.Wl32[6 * (size_t)q + e] = tp ? (float)(N[e] - o[e]) : 0.f;
+          for (int e = 0; e < 6; e++)
+            v.Wl32[6 * (size_t)q + e] = tp ? (float)tp_weight(v, e, (double)(N[e] - o[e]), (double)N[e]) : 0.f;
       }
     }
   }
@@ -750,8 +782,14 @@ __device__ static void isect_fused_step(const View &v, int j, int *state, int *i
       for (int r = 0; r < 3; r++) { xh[r] = sh[r]; xl[r] = sl[r]; }
       for (int e = 0; e < 6; e++) {
         float2 w = ff_add(make_float2(Nh[e], Nl[e]), make_float2(-Nq[e], 0.f));
-        v.Wl[6 * (size_t)q + e] = ff_to_double(w);
-        v.Wl32[6 * (size_t)q + e] = __fadd_rn(w.x, w.y);
+        if (v.wmode) {
+          double wd = tp_weight(v, e, 0.0, ff_to_double(make_float2(Nh[e], Nl[e])));
+          v.Wl[6 * (size_t)q + e] = wd;
+          v.Wl32[6 * (size_t)q + e] = (float)wd;
+        } else {
+          v.Wl[6 * (size_t)q + e] = ff_to_double(w);
+          v.Wl32[6 * (size_t)q + e] = __fadd_rn(w.x, w.y);
+        }
       }
     }
   }
@@ -794,7 +832,7 @@ rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped, bool fp64) {
   double tol = ctx->opt.isect_tol;
   double px_tol = ctx->opt.isect_px_tol;
   if (ctx->opt.precision == 1 && !fp64) {  // FP32 form: every point's iterations in one launch
-    RPBA_KERNEL(ctx, "k_isect_fused_f", k_isect_fused_f<<<nblk(ctx->N, 128), 128, 0, ctx->stream>>>(
+    RPBA_KERNEL(ctx, "k_isect_fused_f", k_isect_fused_f<<<nblk(ctx->N, ctx->tune.isect), ctx->tune.isect, 0, ctx->stream>>>(
                                           v, ctx->isect_state, ctx->isect_iter, maxit, tol, px_tol,
                                           ctx->opt.cond_max));
   } else {
@@ -881,7 +919,10 @@ __global__ void k_robust_weights(View v, const double *sigma, double t_v, double
   if (out) atomicAdd(count, 1);
 }
 
-// FP32 form: float-float residual, the test |v|_W > t_v sigma_i in FP32
+// FP32 form: float-float residual, the test |v|_W > t_v sigma_i in FP32.
+// A separate pass in observation order: written from the per-camera scale
+// kernel the weights would scatter over the observation-ordered arrays
+// (measured slower on the 20M-observation block).
 __global__ void k_robust_weights_f(View v, const float *sigma, float t_v, double dw, int *count) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= v.K) return;
@@ -905,11 +946,11 @@ rpba_status launch_robust_weights(Ctx *ctx, int *n_down) {
   RPBA_TRY(launch_camera_scale(ctx));
   RPBA_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(int), ctx->stream));
   if (ctx->K && ctx->opt.precision == 1)
-    RPBA_KERNEL(ctx, "k_robust_weights_f", k_robust_weights_f<<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(
+    RPBA_KERNEL(ctx, "k_robust_weights_f", k_robust_weights_f<<<nblk(ctx->K, ctx->tune.robust), ctx->tune.robust, 0, ctx->stream>>>(
                                              make_view(ctx), ctx->cam_sigma32, (float)ctx->opt.t_v, ctx->opt.downweight,
                                              ctx->counters));
   else if (ctx->K)
-    RPBA_KERNEL(ctx, "k_robust_weights", k_robust_weights<<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(make_view(ctx), ctx->cam_sigma, ctx->opt.t_v,
+    RPBA_KERNEL(ctx, "k_robust_weights", k_robust_weights<<<nblk(ctx->K, ctx->tune.robust), ctx->tune.robust, 0, ctx->stream>>>(make_view(ctx), ctx->cam_sigma, ctx->opt.t_v,
                                                                 ctx->opt.downweight, ctx->counters));
   if (n_down) {
     RPBA_CUDA(cudaMemcpyAsync(ctx->h_pinned_counter, ctx->counters, sizeof(int), cudaMemcpyDeviceToHost,
@@ -926,8 +967,38 @@ __global__ void k_eliminate(View v) {
   if (v.obs_w[k] != 1.0) v.active[v.obs_pt[k]] = 0;
 }
 
+// serial robust variant (Sec. 5.3): the down-weighted observations are
+// deleted (weight 0)
+__global__ void k_delete_obs(View v) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= v.K) return;
+  if (v.obs_w[k] != 1.0) {
+    v.obs_w[k] = 0.0;
+    if (v.obs_w32) v.obs_w32[k] = 0.f;
+  }
+}
+
+// ... and a point seen by fewer than two cameras afterwards is eliminated
+__global__ void k_eliminate_thin(View v) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= v.N || !v.active[j]) return;
+  int kept = 0;
+  for (int a = v.pt_inst_ptr[j]; a < v.pt_inst_ptr[j + 1]; a++) {
+    int q = v.pt_inst[a];
+    for (int k = v.inst_obs_ptr[q]; k < v.inst_obs_ptr[q + 1]; k++) kept += v.obs_w[k] == 1.0 ? 1 : 0;
+  }
+  if (kept < 2) v.active[j] = 0;
+}
+
 rpba_status launch_eliminate(Ctx *ctx) {
   if (!ctx->K) return RPBA_OK;
+  if (ctx->opt.robust_serial) {
+    RPBA_KERNEL(ctx, "k_delete_obs", k_delete_obs<<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(make_view(ctx)));
+    if (ctx->N)
+      RPBA_KERNEL(ctx, "k_eliminate_thin",
+                  k_eliminate_thin<<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(make_view(ctx)));
+    return RPBA_OK;
+  }
   RPBA_KERNEL(ctx, "k_eliminate", k_eliminate<<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(make_view(ctx)));
   return RPBA_OK;
 }
@@ -1451,7 +1522,7 @@ rpba_status launch_build_rcs(Ctx *ctx, const double *lambda_dev, const int *run_
   RPBA_KERNEL(ctx, "k_rcs_clear", k_rcs_clear<<<gclr, 256, 0, ctx->stream>>>(v, run_dev, ctx->L));
   if (ctx->P == 0) return RPBA_OK;
   if (ctx->opt.precision == 1) {
-    RPBA_KERNEL(ctx, "k_linearize_f32", k_linearize<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(
+    RPBA_KERNEL(ctx, "k_linearize_f32", k_linearize<float><<<nblk(ctx->P, ctx->tune.lin), ctx->tune.lin, 0, ctx->stream>>>(
                                         v, lambda_dev, run_dev, nullptr, nullptr, (float *)ctx->Ninv, (float *)ctx->gX));
     RPBA_KERNEL(ctx, "k_camera_blocks_f32", k_camera_blocks<float><<<ctx->M, CB_THREADS, 0, ctx->stream>>>(
         v, lambda_dev, run_dev, nullptr, nullptr, (const float *)ctx->gX, (const float *)ctx->Ninv));
@@ -1461,7 +1532,7 @@ rpba_status launch_build_rcs(Ctx *ctx, const double *lambda_dev, const int *run_
                                           ctx->spair_seg, ctx->seg_cam, ctx->seg_nb, (const float *)ctx->Ninv));
   } else {
     double *NXC = (double *)ctx->NXC, *Z = (double *)ctx->Z;
-    RPBA_KERNEL(ctx, "k_linearize_f64", k_linearize<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, lambda_dev, run_dev, NXC, Z,
+    RPBA_KERNEL(ctx, "k_linearize_f64", k_linearize<double><<<nblk(ctx->P, ctx->tune.lin), ctx->tune.lin, 0, ctx->stream>>>(v, lambda_dev, run_dev, NXC, Z,
                                                                     (double *)ctx->Ninv, (double *)ctx->gX));
     RPBA_KERNEL(ctx, "k_camera_blocks_f64", k_camera_blocks<double><<<ctx->M, CB_THREADS, 0, ctx->stream>>>(
         v, lambda_dev, run_dev, NXC, Z, (const double *)ctx->gX, (const double *)ctx->Ninv));
@@ -1570,10 +1641,10 @@ rpba_status launch_backsub_trial(Ctx *ctx, const int *run_dev) {
     RPBA_KERNEL(ctx, "k_to_float", k_to_float<<<nblk(ctx->ytot, 256), 256, 0, ctx->stream>>>(ctx->dC, ctx->dC32, ctx->ytot));
   if (ctx->P) {
     if (ctx->opt.precision == 1)
-      RPBA_KERNEL(ctx, "k_backsub_f32", k_backsub<float><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, run_dev, nullptr,
+      RPBA_KERNEL(ctx, "k_backsub_f32", k_backsub<float><<<nblk(ctx->P, ctx->tune.backsub), ctx->tune.backsub, 0, ctx->stream>>>(v, run_dev, nullptr,
                                                                    (const float *)ctx->Ninv, (const float *)ctx->gX));
     else
-      RPBA_KERNEL(ctx, "k_backsub_f64", k_backsub<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(v, run_dev, (const double *)ctx->NXC,
+      RPBA_KERNEL(ctx, "k_backsub_f64", k_backsub<double><<<nblk(ctx->P, ctx->tune.backsub), ctx->tune.backsub, 0, ctx->stream>>>(v, run_dev, (const double *)ctx->NXC,
                                                                     (const double *)ctx->Ninv, (const double *)ctx->gX));
   }
   if (ctx->M) RPBA_KERNEL(ctx, "k_cam_trial", k_cam_trial<<<nblk(ctx->M, 128), 128, 0, ctx->stream>>>(v, run_dev));

@@ -113,6 +113,7 @@ __global__ void k_covariance(int n, const int *ids, const double *R, const doubl
 // helpers
 // ---------------------------------------------------------------------------
 static void free_graph(GraphRec *g);
+static bool tune_load(Ctx *ctx, const char *path);
 static rpba_status dev_alloc(Ctx *ctx, void **p, size_t bytes) {
   if (bytes == 0) bytes = 16;
   bytes = (bytes + 255) & ~(size_t)255;
@@ -168,6 +169,8 @@ extern "C" void rpba_default_options(rpba_options *o) {
   o->max_reject = 6;
   o->robust = 0;
   o->robust_from_start = 0;
+  o->weight_mode = 0;
+  o->rho0 = 200.0;
   o->isect_max_iter = 10;
   o->isect_tol = 1e-10;
   o->isect_px_tol = 1e-3;
@@ -177,7 +180,7 @@ extern "C" void rpba_default_options(rpba_options *o) {
   o->pcg_tol = 1e-8;
   o->pcg_max_iter = 500;
   o->ir_steps = 2;
-  o->chol_tc = 1;
+  o->chol_tc = 0;
 }
 
 extern "C" const char *rpba_last_error(const rpba_ctx *ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
@@ -666,8 +669,10 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
     RPBA_TRY(alloc_n(ctx, &ctx->ir_rs, (size_t)std::max(yt, 1)));
     RPBA_TRY(alloc_n(ctx, &ctx->ir_x, (size_t)std::max(yt, 1)));
     RPBA_TRY(alloc_n(ctx, &ctx->ir_t, (size_t)std::max(yt, 1)));
-    if (ctx->opt.chol_tc) RPBA_TRY(tc_chol_setup(ctx));
+    RPBA_TRY(tc_chol_setup(ctx));  // the tensor-core forms, for chol_tc and the autotuner
   }
+  RPBA_TRY(alloc_n(ctx, &ctx->wrho, 1));
+  RPBA_CUDA(cudaMemcpyAsync(ctx->wrho, &ctx->opt.rho0, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   RPBA_TRY(alloc_n(ctx, &ctx->sub_mask, (size_t)std::max(L, 1)));
   RPBA_CUDA(cudaMemsetAsync(ctx->sub_mask, 1, (size_t)std::max(L, 1), ctx->stream));
   RPBA_TRY(alloc_n(ctx, &ctx->pt_mask, (size_t)std::max(N, 1)));
@@ -716,7 +721,9 @@ extern "C" rpba_status rpba_create(const rpba_problem *prob, const rpba_options 
   if (opt) ctx->opt = *opt;
   else rpba_default_options(&ctx->opt);
   if ((ctx->opt.precision != 0 && ctx->opt.precision != 1) || ctx->opt.solver < 0 || ctx->opt.solver > 4 ||
-      ctx->opt.ir_steps < 0 || ctx->opt.ir_steps > 20 || ctx->opt.pcg_max_iter < 1 || !(ctx->opt.pcg_tol > 0.0)) {
+      ctx->opt.ir_steps < 0 || ctx->opt.ir_steps > 20 || ctx->opt.pcg_max_iter < 1 || !(ctx->opt.pcg_tol > 0.0) ||
+      ctx->opt.chol_tc < 0 || ctx->opt.chol_tc > 2 || ctx->opt.weight_mode < 0 || ctx->opt.weight_mode > 2 ||
+      !(ctx->opt.rho0 > 0.0)) {
     ctx->err = "invalid precision / solver / ir_steps option";
     *out = h;
     return RPBA_ERR_INVALID_ARG;
@@ -736,7 +743,13 @@ extern "C" rpba_status rpba_create(const rpba_problem *prob, const rpba_options 
     return RPBA_ERR_CUDA;
   }
   RPBA_CUDA(cudaGetDevice(&ctx->dev));
-  return build(ctx, prob);
+  if (ctx->opt.tune_cache) {  // kept by the context: the caller's string may go
+    ctx->tune_cache_path = ctx->opt.tune_cache;
+    ctx->opt.tune_cache = ctx->tune_cache_path.c_str();
+  }
+  RPBA_TRY(build(ctx, prob));
+  if (ctx->opt.tune_cache && *ctx->opt.tune_cache) tune_load(ctx, ctx->opt.tune_cache);
+  return RPBA_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1320,6 +1333,12 @@ static rpba_status outer_tail_body(Ctx *ctx, bool robust) {
 }
 
 static rpba_status outer_tail(Ctx *ctx, bool robust, double *sigma0) {
+  // the scalar TP weight's rho for this outer iteration's intersection
+  ctx->outer_done++;
+  if (ctx->opt.weight_mode == 2) {
+    ctx->h_pinned_d[8] = ctx->opt.rho0 * pow(1.01, (double)ctx->outer_done);
+    RPBA_CUDA(cudaMemcpyAsync(ctx->wrho, ctx->h_pinned_d + 8, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  }
   GraphRec *&g = ctx->outer_graph[robust ? 1 : 0];
   if (g && (g->with_events != ctx->prof_enabled || g->prof_only != ctx->prof_only)) {
     free_graph(g);  // timing nodes only while profiling
@@ -1386,6 +1405,187 @@ extern "C" rpba_status rpba_set_point_mask(rpba_ctx *h, const uint8_t *mask) {
     for (int j = 0; j < ctx->N; j++) m[ctx->h_pt_perm[j]] = mask[j] ? 1 : 0;
   RPBA_CUDA(cudaMemcpyAsync(ctx->pt_mask, m.data(), m.size(), cudaMemcpyHostToDevice, ctx->stream));
   return sync(ctx);
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: launch shapes timed on the context's own data, cached per workload
+// ---------------------------------------------------------------------------
+static std::string tune_signature(const Ctx *ctx) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  char b[160];
+  snprintf(b, sizeof(b), "M%d_N%d_K%d_L%d_P%d_prec%d_solver%d_sm%d", ctx->M, ctx->N, ctx->K, ctx->L, ctx->P,
+           ctx->opt.precision, ctx->opt.solver, sms);
+  return b;
+}
+
+// one cache line (JSON object): {"sig": "...", "isect": 128, "lin": 128, "backsub": 128, "robust": 256, "chol_tc": 2}
+static std::string tune_line(const Ctx *ctx) {
+  char b[320];
+  snprintf(b, sizeof(b), "{\"sig\": \"%s\", \"isect\": %d, \"lin\": %d, \"backsub\": %d, \"robust\": %d, \"chol_tc\": %d}",
+           tune_signature(ctx).c_str(), ctx->tune.isect, ctx->tune.lin, ctx->tune.backsub, ctx->tune.robust,
+           ctx->opt.chol_tc);
+  return b;
+}
+
+static bool json_int(const std::string &line, const char *key, int *out) {
+  std::string k = std::string("\"") + key + "\":";
+  size_t p = line.find(k);
+  if (p == std::string::npos) return false;
+  return sscanf(line.c_str() + p + k.size(), " %d", out) == 1;
+}
+
+static bool tune_valid(int threads) { return threads >= 32 && threads <= 1024 && threads % 32 == 0; }
+
+// the context's workload in the cache: applies its values; false if absent
+static bool tune_load(Ctx *ctx, const char *path) {
+  FILE *f = fopen(path, "r");
+  if (!f) return false;
+  std::string want = "\"sig\": \"" + tune_signature(ctx) + "\"";
+  char buf[1024];
+  bool found = false;
+  while (fgets(buf, sizeof(buf), f)) {
+    std::string line(buf);
+    if (line.find(want) == std::string::npos) continue;
+    Tuning t;
+    int chol = ctx->opt.chol_tc;
+    bool ok = json_int(line, "isect", &t.isect) && json_int(line, "lin", &t.lin) &&
+              json_int(line, "backsub", &t.backsub) && json_int(line, "robust", &t.robust) &&
+              json_int(line, "chol_tc", &chol);
+    if (ok && tune_valid(t.isect) && tune_valid(t.lin) && tune_valid(t.backsub) && tune_valid(t.robust) &&
+        chol >= 0 && chol <= 2) {
+      ctx->tune = t;
+      if (ctx->tc_ready || chol == 0) ctx->opt.chol_tc = chol;
+      found = true;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+// rewrite the cache with this workload's line replaced (or appended)
+static rpba_status tune_store(Ctx *ctx, const char *path) {
+  std::vector<std::string> keep;
+  std::string want = "\"sig\": \"" + tune_signature(ctx) + "\"";
+  if (FILE *f = fopen(path, "r")) {
+    char buf[1024];
+    while (fgets(buf, sizeof(buf), f)) {
+      std::string line(buf);
+      if (line.find(want) == std::string::npos && line.find("\"sig\"") != std::string::npos) keep.push_back(line);
+    }
+    fclose(f);
+  }
+  FILE *f = fopen(path, "w");
+  if (!f) {
+    ctx->err = std::string("cannot write the tune cache ") + path;
+    return RPBA_ERR_INVALID_ARG;
+  }
+  for (auto &l : keep) fputs(l.c_str(), f);
+  fprintf(f, "%s\n", tune_line(ctx).c_str());
+  fclose(f);
+  return RPBA_OK;
+}
+
+// mean time of reps calls of fn after one untimed call (CUDA events on the
+// context's stream)
+template <class F>
+static rpba_status time_phase(Ctx *ctx, int reps, float *ms, F fn) {
+  RPBA_TRY(fn());
+  cudaEvent_t a, b;
+  RPBA_CUDA(cudaEventCreate(&a));
+  RPBA_CUDA(cudaEventCreate(&b));
+  RPBA_CUDA(cudaEventRecord(a, ctx->stream));
+  for (int r = 0; r < reps; r++) RPBA_TRY(fn());
+  RPBA_CUDA(cudaEventRecord(b, ctx->stream));
+  RPBA_CUDA(cudaEventSynchronize(b));
+  float t = 0.f;
+  RPBA_CUDA(cudaEventElapsedTime(&t, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *ms = t / (float)reps;
+  return RPBA_OK;
+}
+
+template <class F>
+static rpba_status pick(Ctx *ctx, int *param, const std::vector<int> &cand, F fn) {
+  int best = *param;
+  float best_ms = 1e30f;
+  for (int c : cand) {
+    *param = c;
+    float ms = 0.f;
+    RPBA_TRY(time_phase(ctx, 5, &ms, fn));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  *param = best;
+  return RPBA_OK;
+}
+
+extern "C" rpba_status rpba_tune(rpba_ctx *h, const char *cache_path, int32_t *chosen) {
+  CTX_OR_FAIL;
+  if (!ctx->intersected) RPBA_TRY(rpba_intersect(h));
+  bool saved_graphs = ctx->use_graphs, saved_prof = ctx->prof_enabled;
+  ctx->prof_enabled = false;
+  // the robust weights and the TP intersection change the state: it is saved
+  // here and restored after their timings
+  std::vector<double> X(3 * (size_t)ctx->N), Xl(3 * (size_t)ctx->P), Wl(6 * (size_t)ctx->P), w(ctx->K);
+  std::vector<uint8_t> act(ctx->N);
+  RPBA_TRY(rpba_get_points(h, X.data(), act.data()));
+  RPBA_TRY(rpba_get_instances(h, nullptr, nullptr, Xl.data(), Wl.data()));
+  RPBA_TRY(rpba_get_weights(h, w.data()));
+  auto restore = [&]() -> rpba_status {
+    RPBA_TRY(rpba_set_points(h, X.data(), act.data()));
+    RPBA_TRY(rpba_set_instances(h, Xl.data(), Wl.data()));
+    return rpba_set_weights(h, w.data());
+  };
+  RPBA_TRY(pick(ctx, &ctx->tune.robust, {128, 256, 512}, [&] { return launch_robust_weights(ctx, nullptr); }));
+  RPBA_TRY(restore());
+  // the RCS assembly (linearisation), then the back-substitution with trial:
+  // per-LM-step scratch only, the state is unchanged
+  RPBA_TRY(launch_lm_init(ctx));
+  RPBA_TRY(pick(ctx, &ctx->tune.lin, {64, 128, 256},
+                [&] { return launch_build_rcs(ctx, ctx->lm_lambda, ctx->lm_run); }));
+  RPBA_TRY(launch_solve_rcs(ctx, ctx->lm_run, ctx->lm_cholfail));
+  RPBA_TRY(pick(ctx, &ctx->tune.backsub, {64, 128, 256}, [&] { return launch_backsub_trial(ctx, ctx->lm_run); }));
+  // the direct solve's factorisation: persistent or one launch per step
+  if ((ctx->opt.solver == 2 || ctx->auto_solver) && ctx->tc_ready) {
+    int s = ctx->opt.solver;
+    ctx->opt.solver = 2;
+    rpba_status st = pick(ctx, &ctx->opt.chol_tc, {0, 1, 2}, [&] { return launch_solve_rcs(ctx, ctx->lm_run, ctx->lm_cholfail); });
+    ctx->opt.solver = s;
+    RPBA_TRY(st);
+  }
+  // the TP intersection from the saved state every time
+  {
+    rpba_status st = pick(ctx, &ctx->tune.isect, {64, 128, 256}, [&]() -> rpba_status {
+      RPBA_TRY(restore());
+      return launch_intersect(ctx, 1, nullptr);
+    });
+    RPBA_TRY(restore());
+    RPBA_TRY(st);
+  }
+  ctx->use_graphs = saved_graphs;
+  ctx->prof_enabled = saved_prof;
+  free_lm_graphs(ctx);  // captured graphs carry the old launch shapes
+  for (auto &g : ctx->outer_graph)
+    if (g) {
+      free_graph(g);
+      g = nullptr;
+    }
+  RPBA_TRY(sync(ctx));
+  if (chosen) {
+    chosen[0] = ctx->tune.isect;
+    chosen[1] = ctx->tune.lin;
+    chosen[2] = ctx->tune.backsub;
+    chosen[3] = ctx->tune.robust;
+    chosen[4] = ctx->opt.chol_tc;
+  }
+  const char *path = cache_path ? cache_path : ctx->opt.tune_cache;
+  if (path && *path) RPBA_TRY(tune_store(ctx, path));
+  return RPBA_OK;
 }
 
 extern "C" rpba_status rpba_outer_iteration(rpba_ctx *h, int32_t robust, double *sigma0, int32_t *lm_launches) {

@@ -172,8 +172,19 @@ struct DevBuf {
 
 struct GraphRec;
 
+// launch shapes the autotuner picks (rpba_tune): block sizes of kernels that
+// give every thread one independent item, so they change timing, not results
+struct Tuning {
+  int isect = 128;    // k_isect_fused_f: points per CTA
+  int lin = 128;      // k_linearize: instances per CTA
+  int backsub = 128;  // k_backsub: instances per CTA
+  int robust = 256;   // k_robust_weights(_f): observations per CTA
+};
+
 struct Ctx {
   rpba_options opt;
+  Tuning tune;
+  std::string tune_cache_path;  // the context's copy of opt.tune_cache
   cudaStream_t stream = nullptr;
   std::string err;
   int dev = 0;
@@ -285,9 +296,18 @@ struct Ctx {
   CUtensorMap tc_map[3];
   int *tc_err = nullptr;
   bool tc_ready = false;
+  // persistent form: the task queue, tasks per (sub-block, step), the queue
+  // head and finished-task counters, the grid (resident CTAs)
+  int4 *tc_tasks = nullptr;
+  int *tc_need = nullptr, *tc_count = nullptr;
+  int tc_n_tasks = 0, tc_grid = 0;
   // which sub-blocks the LM adjustment moves and which points the
   // intersection handles (all by default; a share of them in sharded runs)
   uint8_t *sub_mask = nullptr, *pt_mask = nullptr;
+  // the scalar TP weight's rho (weight_mode 2) on the device, and the outer
+  // iterations run so far (rho = rho0 1.01^t)
+  double *wrho = nullptr;
+  int outer_done = 0;
   // LM control per sub-block
   double *lm_lambda = nullptr, *lm_F = nullptr, *lm_Ft = nullptr, *lm_best = nullptr;
   int *lm_grace = nullptr, *lm_rej = nullptr, *lm_it = nullptr, *lm_run = nullptr;

@@ -37,11 +37,12 @@ class Options(C.Structure):
     _fields_ = [("lambda0", C.c_double), ("t_v", C.c_double), ("downweight", C.c_double),
                 ("stop_ratio", C.c_double), ("grace", C.c_int32), ("max_outer", C.c_int32),
                 ("max_inner", C.c_int32), ("max_reject", C.c_int32), ("robust", C.c_int32),
-                ("robust_from_start", C.c_int32), ("isect_max_iter", C.c_int32),
+                ("robust_from_start", C.c_int32), ("weight_mode", C.c_int32), ("rho0", C.c_double),
+                ("robust_serial", C.c_int32), ("isect_max_iter", C.c_int32),
                 ("isect_tol", C.c_double), ("isect_px_tol", C.c_double), ("cond_max", C.c_double),
                 ("precision", C.c_int32),
                 ("solver", C.c_int32), ("pcg_tol", C.c_double), ("pcg_max_iter", C.c_int32),
-                ("ir_steps", C.c_int32), ("chol_tc", C.c_int32),
+                ("ir_steps", C.c_int32), ("chol_tc", C.c_int32), ("tune_cache", C.c_char_p),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", C.c_void_p)]
 
 
@@ -113,6 +114,7 @@ def load(build_if_missing: bool = True):
         "rpba_bact": (C.c_int, [vp, _ip]),
         "rpba_profile_enable": (C.c_int, [vp, C.c_int32]),
         "rpba_profile_select": (C.c_int, [vp, C.c_char_p]),
+        "rpba_tune": (C.c_int, [vp, C.c_char_p, _ip]),
         "rpba_get_camera_rt": (C.c_int, [vp, _dp, _dp]),
         "rpba_set_camera_rt": (C.c_int, [vp, _dp, _dp]),
         "rpba_set_subblock_mask": (C.c_int, [vp, C.c_void_p]),
@@ -213,6 +215,8 @@ def rpba_default_options(**overrides) -> Options:
     o = Options()
     load().rpba_default_options(C.byref(o))
     for k, v in overrides.items():
+        if k == "tune_cache" and isinstance(v, str):
+            v = v.encode()
         setattr(o, k, v)
     return o
 
@@ -422,6 +426,14 @@ class Rpba:
         dc, dx = np.zeros(6 * self.M), np.zeros((self.P, 3))
         self._c(load().rpba_lm_step(self._h, float(lam), _i(acc), _d(Fb), _d(Ft), _d(dc), _d(dx)))
         return acc, Fb, Ft, dc, dx
+
+    def tune(self, cache_path=None):
+        """Autotune the launch shapes on this context's data; returns the
+        choice {isect, lin, backsub, robust, chol_tc} (written to cache_path,
+        or to the context's tune_cache, when given)."""
+        out = np.zeros(5, np.int32)
+        self._c(load().rpba_tune(self._h, None if cache_path is None else str(cache_path).encode(), _i(out)))
+        return dict(zip(("isect", "lin", "backsub", "robust", "chol_tc"), (int(x) for x in out)))
 
     def camera_rt(self):
         """(M, 12): rotation matrix (row-major) and translation per camera, as held."""

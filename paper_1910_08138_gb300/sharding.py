@@ -368,7 +368,10 @@ class RpbaEngine:
         mask = np.zeros(self.ctx.N, np.uint8)
         mask[np.asarray(ids, dtype=np.int64)] = 1
         self.ctx.set_point_mask(mask)
-        self.ctx.intersect_points(tp_only)
+        if tp_only:
+            self.ctx.intersect_points(True)
+        else:
+            self.ctx.intersect()  # the first intersection: FP64 in every form
         self.ctx.set_point_mask(None)
 
     def bact(self, subs):

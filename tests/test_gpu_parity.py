@@ -333,6 +333,50 @@ def test_outer_iteration_is_one_iteration_of_the_loop():
         g.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_serial_robust_variant(precision):
+    """The serial robust variant of Sec. 5.3 (t_v = 3, the down-weighted
+    observations deleted, then points with fewer than two eliminated) on the
+    one-block case L = 1: the FP64 form reproduces the oracle's run (same
+    deletions, RMS and sigma_0 to rounding), the FP32 form its RMS to 1e-3 px."""
+    prob = dict(synth.config(1))
+    prob["cam_subblock"] = np.zeros_like(prob["cam_subblock"])
+    opts = dict(robust=1, robust_from_start=1, robust_serial=1, t_v=3.0)
+    o = oracle.Oracle(prob)
+    ro = o.run(**opts)
+    g = rpba.Rpba(prob, precision=precision, **opts)
+    rg = g.iterate()
+    assert abs(rg["rms"] - ro["rms"]) <= (1e-9 if precision == 0 else 1e-3)
+    wg, wo = g.weights(), o.weights()
+    assert set(np.unique(wg)) <= {0.0, 1.0}
+    if precision == 0:
+        assert rg["outer"] == ro["outer"] and rg["deleted_points"] == ro["deleted_points"]
+        np.testing.assert_array_equal(wg, wo)
+        assert rg["sigma0"] == pytest.approx(ro["sigma0"], rel=1e-9)
+    else:
+        assert abs(rg["deleted_points"] - ro["deleted_points"]) <= max(3, 0.05 * ro["deleted_points"])
+        assert rg["sigma0"] == pytest.approx(ro["sigma0"], rel=1e-3)
+    g.close()
+
+
+@pytest.mark.parametrize("precision,mode", [(0, 1), (0, 2), (1, 1), (1, 2)])
+def test_ablation_weight_modes(precision, mode):
+    """The TPs' weight from all cameras (1) or as rho I with the 1.01 schedule
+    (2), the ablations of Sec. 6.4: whole runs against the oracle; the FP64
+    form reproduces its trajectory."""
+    prob = synth.config(1)
+    opts = dict(robust=1, robust_from_start=1, weight_mode=mode)
+    ro = oracle.Oracle(prob).run(**opts)
+    g = rpba.Rpba(prob, precision=precision, **opts)
+    rg = g.iterate()
+    assert abs(rg["rms"] - ro["rms"]) <= (1e-9 if precision == 0 else 1e-3)
+    if precision == 0:
+        assert rg["outer"] == ro["outer"] and rg["inner_total"] == ro["inner_total"]
+        assert rg["deleted_points"] == ro["deleted_points"]
+        np.testing.assert_allclose(rg["sigma0_hist"], ro["sigma0_hist"], rtol=1e-6)
+    g.close()
+
+
 def test_empty_subblock_single_observation_point_and_errors():
     prob = synth.tiny(seed=9, runs=[3, 3])
     prob["cam_subblock"] = np.where(prob["cam_subblock"] == 1, 2, 0).astype(np.int32)  # id 1 unused

@@ -215,14 +215,16 @@ def _large_subblock_state(precision, **opts):
     return prob, o, g
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_direct_solver_on_a_2100_unknown_subblock(precision):
+@pytest.mark.parametrize("precision,chol_tc", [(0, 2), (1, 2), (0, 1)])
+def test_direct_solver_on_a_2100_unknown_subblock(precision, chol_tc):
     """Solver 2 (FP32 factorisation of the Jacobi-scaled RCS with its updates
     on the tensor cores, FP64 iterative refinement) against the oracle's FP64
     Cholesky step (Sec. 2) on a sub-block above 2,000 unknowns, and against the
     same solver with the CUDA-core factorisation: both refine to the FP64
-    solution of the same system, so they agree far below the oracle tolerance."""
-    prob, o, g = _large_subblock_state(precision, solver=2, chol_tc=1)
+    solution of the same system, so they agree far below the oracle tolerance.
+    chol_tc 2 is the persistent launch (all steps of both sub-blocks from one
+    queue), 1 one launch per step."""
+    prob, o, g = _large_subblock_state(precision, solver=2, chol_tc=chol_tc)
     n0 = 6 * len(o.sub_cameras(0))
     assert n0 > 2000
     _, _, g2 = _large_subblock_state(precision, solver=2, chol_tc=0)

@@ -662,6 +662,44 @@ def test_outer_loop_stops_where_the_ratio_rule_says():
     assert stop == rep["outer"] and rep["outer"] < 30
 
 
+def test_ablation_weights_all_cameras_and_scalar():
+    """The ablation variants of Sec. 6.4 for the TPs' weight W^l. All cameras:
+    the point's full normal matrix N_j for every instance; since the refined
+    weights N_j - N_j^(l) of a point's n instances sum to (n - 1) N_j, it must
+    equal that sum / (n - 1). Scalar: rho I, rho0 at the first intersection
+    and 1.01 times more per outer iteration (the plain approach's schedule,
+    Sec. 6.3); single-sub-block points get no weight in either."""
+    prob = synth.tiny(seed=6, nx=4, ny=3, n_points=120, runs=[4, 4, 4], oblique_deg=30, nadir_every=3)
+    o0 = oracle.Oracle(prob)
+    o0.intersect()
+    o1 = oracle.Oracle(prob)
+    o1.intersect(weight_mode=1)
+    ip, _ = o0.instances()
+    _, W0 = o0.instance_state()
+    _, W1 = o1.instance_state()
+    n = np.bincount(ip, minlength=o0.N)
+    tp = n[ip] >= 2
+    assert tp.any() and (~tp).any()
+    full = np.zeros((o0.N, 6))
+    np.add.at(full, ip[tp], W0[tp])
+    full[n >= 2] /= (n[n >= 2] - 1)[:, None]
+    np.testing.assert_allclose(W1[tp], full[ip[tp]], rtol=1e-10, atol=1e-12 * np.abs(full).max())
+    assert np.all(W1[~tp] == 0.0)
+    o2 = oracle.Oracle(prob)
+    o2.intersect(weight_mode=2, rho0=50.0)
+    _, W2 = o2.instance_state()
+    eye = np.array([1.0, 0, 0, 1.0, 0, 1.0])
+    np.testing.assert_array_equal(W2[tp], np.tile(50.0 * eye, (int(tp.sum()), 1)))
+    assert np.all(W2[~tp] == 0.0)
+    o3 = oracle.Oracle(prob)
+    rep = o3.run(weight_mode=2, rho0=50.0, max_outer=2)
+    _, W3 = o3.instance_state()
+    _, a3 = o3.points()
+    live = tp & (a3[ip] == 1)
+    np.testing.assert_allclose(W3[live], np.tile(50.0 * 1.01 ** rep["outer"] * eye, (int(live.sum()), 1)),
+                               rtol=1e-15)
+
+
 def test_robust_stage_finds_injected_outliers():
     prob = synth.config(1)
     o = oracle.Oracle(prob)
@@ -673,6 +711,32 @@ def test_robust_stage_finds_injected_outliers():
     good = np.setdiff1d(np.arange(o.N), bad)
     assert (act[good] == 0).mean() < 0.06
     assert 0.45 < rep["sigma0"] < 0.55
+
+
+@pytest.mark.parametrize("single_subblock", [True, False])
+def test_serial_robust_stage_deletes_the_outliers(single_subblock):
+    """Serial variant of Sec. 5.3 (t_v = 3): the down-weighted observations are
+    deleted at the end and points left with fewer than two observations are
+    eliminated. No injected outlier survives among the kept observations of
+    the kept points, every kept point keeps at least two observations, and
+    sigma_0 after the deletion is the noise level (0.5 px)."""
+    prob = synth.config(1)
+    if single_subblock:  # the serial case proper: one block, L = 1
+        prob = dict(prob)
+        prob["cam_subblock"] = np.zeros_like(prob["cam_subblock"])
+    o = oracle.Oracle(prob)
+    rep = o.run(robust=1, robust_from_start=1, robust_serial=1, t_v=3.0)
+    _, act = o.points()
+    w = o.weights()
+    out = prob["outlier"]
+    kept = (act[prob["obs_point"]] == 1) & (w == 1.0)
+    assert set(np.unique(w)) <= {0.0, 1.0}  # deleted or kept, nothing in between
+    assert not (kept & out).any()
+    per_point = np.bincount(prob["obs_point"][kept], minlength=o.N)
+    assert per_point[act == 1].min() >= 2
+    assert 0.45 < rep["sigma0"] < 0.55
+    # sigma_0 counts only the kept observations (a deleted one has weight 0)
+    assert rep["active_points"] == int(act.sum())
 
 
 def test_robust_stage_without_outliers_deletes_little():
