@@ -387,6 +387,27 @@ rpba_status rpba_profile_read(rpba_ctx *ctx, int32_t max_kernels, char *names, d
 rpba_status rpba_check_formats(const double *x, const float *f, int32_t n, float *hi, float *lo, double *back,
                                double *fd);
 
+/* ---- sub-block construction ----------------------------------------------- */
+
+/* Sub-blocks from the visibility graph (Sec. 5.2): the cameras are split into
+ * n_parts parts by recursive bisection of the graph whose nodes are the
+ * cameras and whose edges join cameras that observe a common point (weight:
+ * the number of such points), each camera weighted by the cube root of the sum,
+ * over the points it sees, of their observation counts; every bisection
+ * balances the weight (each side within 2 % of its share) and keeps the cut
+ * weight small (greedy
+ * graph growing, then Fiduccia-Mattheyses passes). The paper uses METIS here;
+ * this partitioner is the library's own. Host computation, no GPU.
+ *   obs_cam / obs_point: n_obs observations (host), as in rpba_problem.
+ *   cam_subblock: n_cams outputs in [0, n_parts), usable as
+ *   rpba_problem.cam_subblock. node_weight (nullable, n_cams): the weights
+ *   used. edge_cut (nullable): the total weight of the edges between parts.
+ * Deterministic for the same input. Errors: INVALID_ARG for sizes out of range
+ * (1 <= n_parts <= n_cams) or an index outside the cameras or points. */
+rpba_status rpba_partition(int32_t n_cams, int32_t n_points, int32_t n_obs, const int32_t *obs_cam,
+                           const int32_t *obs_point, int32_t n_parts, int32_t *cam_subblock,
+                           double *node_weight, double *edge_cut);
+
 /* ---- a variant that allocates no device memory --------------------------- */
 
 /* Largest block rpba_sigma0_noalloc accepts (its fixed scratch: 8192 partial

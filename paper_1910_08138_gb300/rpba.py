@@ -115,6 +115,8 @@ def load(build_if_missing: bool = True):
         "rpba_profile_enable": (C.c_int, [vp, C.c_int32]),
         "rpba_profile_select": (C.c_int, [vp, C.c_char_p]),
         "rpba_tune": (C.c_int, [vp, C.c_char_p, _ip]),
+        "rpba_partition": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _ip, _ip, C.c_int32, _ip, _dp,
+                                     C.POINTER(C.c_double)]),
         "rpba_get_camera_rt": (C.c_int, [vp, _dp, _dp]),
         "rpba_set_camera_rt": (C.c_int, [vp, _dp, _dp]),
         "rpba_set_subblock_mask": (C.c_int, [vp, C.c_void_p]),
@@ -194,6 +196,21 @@ def rpba_sigma0_noalloc(n_cams, n_points, n_obs, R, t, intr, X, active, obs_cam,
     if st != 0:
         raise RpbaError(st, "rpba_sigma0_noalloc failed")
     return s0.value, rms.value, sums
+
+
+def rpba_partition(n_cams, n_points, obs_cam, obs_point, n_parts):
+    """Sub-blocks from the visibility graph (Sec. 5.2): returns (cam_subblock,
+    node_weight, edge_cut)."""
+    oc = np.ascontiguousarray(obs_cam, dtype=np.int32)
+    op = np.ascontiguousarray(obs_point, dtype=np.int32)
+    part = np.zeros(int(n_cams), np.int32)
+    w = np.zeros(int(n_cams))
+    cut = C.c_double()
+    st = load().rpba_partition(int(n_cams), int(n_points), int(oc.size), _i(oc), _i(op), int(n_parts), _i(part),
+                               _d(w), C.byref(cut))
+    if st != 0:
+        raise RpbaError(st, "rpba_partition failed")
+    return part, w, cut.value
 
 
 def rpba_check_formats(x, f):
