@@ -62,6 +62,7 @@ def parse():
     p.add_argument("--solver", type=int, default=4)
     p.add_argument("--chol-tc", type=int, default=0,
                    help="direct solver's FP32 factorisation: 0 CUDA cores, 1 tensor cores per step, 2 persistent")
+    p.add_argument("--tune", action="store_true", help="autotune the launch shapes on the block before timing")
     p.add_argument("--no-extras", action="store_true", help="skip e2e / time-to-RMS / cpu legs")
     return p.parse_args()
 
@@ -391,6 +392,7 @@ def run_ours(args, rank, world):
     if gnn_w is not None:
         ctx.set_gnn_weights(gnn_w)
     ctx.intersect()
+    tuned = ctx.tune() if args.tune else None
     _, act0 = ctx.points()
     K = counted_obs(prob, act0)  # the same count as the oracle's after its first intersection
     n_sub = [6 * len(ctx.sub_cameras(l)) for l in range(ctx.L)]
@@ -500,6 +502,8 @@ def run_ours(args, rank, world):
             "kernels_last_warmup_step": kernels}
     if gnn_w is not None:
         line["config"]["preconditioner_training_s"] = round(gnn_s, 2)
+    if tuned is not None:
+        line["config"]["tuned_launch_shapes"] = tuned
     if rank == 0 and not args.no_extras:
         line.update(extras(args, prob, ctx, stream, K, gnn_w))
     ctx.close()
@@ -512,9 +516,13 @@ def extras(args, prob, ctx, stream, K, gnn_w=None):
 
     from paper_1910_08138_gb300 import rpba
     out = {}
-    # e2e through the C ABI with host buffers: state H2D, one step, state D2H
-    cams = np.ascontiguousarray(ctx.cameras())
-    X, act = ctx.points()
+    # e2e through the C ABI with host buffers in pinned memory: the state (poses,
+    # points, active flags) H2D, one step, the state D2H
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
+    cams = pin((ctx.M, 6), torch.float64)
+    X, act = pin((ctx.N, 3), torch.float64), pin((ctx.N,), torch.uint8)
+    ctx.cameras(out=cams)
+    ctx.points(out=(X, act))
     times = []
     for s in range(max(3, min(args.steps, 20) // 2)):
         torch.cuda.synchronize()
@@ -522,14 +530,15 @@ def extras(args, prob, ctx, stream, K, gnn_w=None):
         ctx.set_cameras(cams)
         ctx.set_points(X, act)
         ctx.outer_iteration(robust=True)
-        cams = ctx.cameras()
-        X, act = ctx.points()
+        ctx.cameras(out=cams)
+        ctx.points(out=(X, act))
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
     h2d = cams.nbytes + X.nbytes + act.nbytes
     d2h = h2d
     out["e2e"] = {"value": K / float(np.mean(times)), "unit": "obs/s", "h2d_bytes_per_step": int(h2d),
-                  "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * float(np.mean(times))}
+                  "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * float(np.mean(times)),
+                  "host_buffers": "pinned"}
     # time to the oracle's final RMS, chosen form vs plain all-FP64 form
     target = None
     try:

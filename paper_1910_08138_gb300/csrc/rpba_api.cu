@@ -516,7 +516,8 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   // or per-instance array at a time)
   RPBA_TRY(upload(ctx, &ctx->d_pt_inv, ctx->h_pt_inv.data(), (size_t)N));
   RPBA_TRY(upload(ctx, &ctx->d_inst_canon, ctx->h_inst_canon.data(), (size_t)P));
-  RPBA_TRY(alloc_n(ctx, &ctx->perm_scratch, std::max<size_t>(std::max(3 * (size_t)N, 6 * (size_t)P), 1)));
+  ctx->perm_scratch_n = std::max<size_t>(std::max(3 * (size_t)N, 6 * (size_t)P), 1);
+  RPBA_TRY(alloc_n(ctx, &ctx->perm_scratch, ctx->perm_scratch_n));
   RPBA_TRY(upload(ctx, &ctx->pt_inst, pin.data(), (size_t)P));
   RPBA_TRY(upload(ctx, &ctx->inst_pt, inst_pt.data(), (size_t)P));
   RPBA_TRY(upload(ctx, &ctx->inst_sub, inst_sub.data(), (size_t)P));
@@ -800,13 +801,26 @@ extern "C" rpba_status rpba_sub_cameras(rpba_ctx *h, int32_t l, int32_t *cams, i
   return RPBA_OK;
 }
 
+// device staging for n doubles: the persistent permutation scratch when it is
+// large enough (no allocation per call), else a temporary buffer
+static rpba_status staging(Ctx *ctx, Tmp &d, size_t n, double **out) {
+  if (n <= ctx->perm_scratch_n) {
+    *out = ctx->perm_scratch;
+    return RPBA_OK;
+  }
+  RPBA_TRY(d.alloc(n * sizeof(double)));
+  *out = (double *)d.p;
+  return RPBA_OK;
+}
+
 extern "C" rpba_status rpba_set_cameras(rpba_ctx *h, const double *pose) {
   CTX_OR_FAIL;
   if (!pose) return RPBA_ERR_INVALID_ARG;
   Tmp d(ctx);
-  RPBA_TRY(d.alloc(6 * (size_t)ctx->M * sizeof(double)));
-  RPBA_CUDA(cudaMemcpyAsync(d.p, pose, 6 * (size_t)ctx->M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-  if (ctx->M) RPBA_KERNEL(ctx, "k_pose_to_R", k_pose_to_R<<<nblk(ctx->M, 128), 128, 0, ctx->stream>>>(ctx->M, (double *)d.p, ctx->R, ctx->t));
+  double *buf = nullptr;
+  RPBA_TRY(staging(ctx, d, 6 * (size_t)ctx->M, &buf));
+  RPBA_CUDA(cudaMemcpyAsync(buf, pose, 6 * (size_t)ctx->M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  if (ctx->M) RPBA_KERNEL(ctx, "k_pose_to_R", k_pose_to_R<<<nblk(ctx->M, 128), 128, 0, ctx->stream>>>(ctx->M, buf, ctx->R, ctx->t));
   RPBA_TRY(sync_mirrors(ctx));
   return sync(ctx);
 }
@@ -830,9 +844,10 @@ extern "C" rpba_status rpba_get_cameras(rpba_ctx *h, double *pose) {
   CTX_OR_FAIL;
   if (!pose) return RPBA_ERR_INVALID_ARG;
   Tmp d(ctx);
-  RPBA_TRY(d.alloc(6 * (size_t)ctx->M * sizeof(double)));
-  if (ctx->M) RPBA_KERNEL(ctx, "k_R_to_pose", k_R_to_pose<<<nblk(ctx->M, 128), 128, 0, ctx->stream>>>(ctx->M, ctx->R, ctx->t, (double *)d.p));
-  RPBA_CUDA(cudaMemcpyAsync(pose, d.p, 6 * (size_t)ctx->M * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  double *buf = nullptr;
+  RPBA_TRY(staging(ctx, d, 6 * (size_t)ctx->M, &buf));
+  if (ctx->M) RPBA_KERNEL(ctx, "k_R_to_pose", k_R_to_pose<<<nblk(ctx->M, 128), 128, 0, ctx->stream>>>(ctx->M, ctx->R, ctx->t, buf));
+  RPBA_CUDA(cudaMemcpyAsync(pose, buf, 6 * (size_t)ctx->M * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   return sync(ctx);
 }
 

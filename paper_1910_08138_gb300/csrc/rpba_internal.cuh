@@ -208,6 +208,7 @@ struct Ctx {
   std::vector<int> h_pt_perm, h_pt_inv, h_inst_canon;
   int *d_pt_inv = nullptr, *d_inst_canon = nullptr;  // the same maps on the device
   double *perm_scratch = nullptr;                      // one per-point or per-instance array
+  size_t perm_scratch_n = 0;                           // its length in doubles
   int n_active_start = 0;
   std::vector<long long> h_S_off;   // L: offset (doubles) of the RCS of l
   std::vector<int> h_npad;          // L: padded RCS size

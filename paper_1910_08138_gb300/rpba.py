@@ -350,13 +350,18 @@ class Rpba:
         self._c(load().rpba_covariance(self._h, _i(ids), ids.size, _d(out)))
         return out.reshape(-1, 3, 3)
 
-    def cameras(self):
-        out = np.zeros((self.M, 6))
+    def cameras(self, out=None):
+        """Poses (n_cams x 6); into `out` (C-contiguous float64) when given."""
+        out = np.zeros((self.M, 6)) if out is None else out
+        assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == 6 * self.M
         self._c(load().rpba_get_cameras(self._h, _d(out)))
         return out
 
-    def points(self):
-        X, a = np.zeros((self.N, 3)), np.zeros(self.N, np.uint8)
+    def points(self, out=None):
+        """(X n_points x 3, active); into `out` = (X, active) when given."""
+        X, a = (np.zeros((self.N, 3)), np.zeros(self.N, np.uint8)) if out is None else out
+        assert X.dtype == np.float64 and X.flags.c_contiguous and X.size == 3 * self.N
+        assert a.dtype == np.uint8 and a.flags.c_contiguous and a.size == self.N
         self._c(load().rpba_get_points(self._h, _d(X), a.ctypes.data_as(_u8)))
         return X, a
 
