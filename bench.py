@@ -171,6 +171,19 @@ def schur_pairs(prob):
     return float(np.sum(n * (n - 1) // 2))
 
 
+def tie_point_counts(prob, active):
+    """Active tie points (points seen in two or more sub-blocks), their
+    observations and their instances: what the TP intersection reads."""
+    cam_sub = np.asarray(prob["cam_subblock"]).astype(np.int64)
+    op = np.asarray(prob["obs_point"]).astype(np.int64)
+    sub = cam_sub[np.asarray(prob["obs_cam"])]
+    N = int(np.asarray(prob["points"]).shape[0])
+    key = np.unique(op * (int(sub.max()) + 1) + sub)
+    n_inst = np.bincount(key // (int(sub.max()) + 1), minlength=N)
+    tp = (n_inst >= 2) & (np.asarray(active) == 1)
+    return int(tp.sum()), int(tp[op].sum()), int(n_inst[tp].sum())
+
+
 def obs_stream_bytes(has_winv):
     """Bytes per observation every FP32-form per-observation pass streams: the
     point and camera indices (4 + 4), the position hi + lo (8 + 8), the robust
@@ -178,7 +191,7 @@ def obs_stream_bytes(has_winv):
     return 28 + (12 if has_winv else 0)
 
 
-def kernel_models(K, N, P, M, has_winv, pairs):
+def kernel_models(K, N, P, M, has_winv, pairs, tps=None):
     """Algorithmic bytes (HBM-bound kernels) or flops (ALU-bound) of one launch
     of each FP32-form kernel of the step, from the data it must read and write
     once: K observations, N points, P instances, M cameras. Camera records are
@@ -190,7 +203,9 @@ def kernel_models(K, N, P, M, has_winv, pairs):
         "k_cost_chunks_f": ("hbm", K * ob + P * 72 + M * 128),
         "k_robust_weights_f": ("hbm", K * (ob + 12) + N * 25 + M * 132),
         "k_camera_mad_u32": ("hbm", K * ob + N * 25 + M * 136),
-        "k_isect_fused_f": ("hbm", K * ob + N * 48 + P * 24 + M * 128),
+        # the TP intersection: the tie points' observations, positions and instances
+        "k_isect_fused_f": ("hbm", (tps[1] * ob + tps[0] * 48 + tps[2] * 24 if tps else K * ob + N * 48 + P * 24)
+                            + M * 128),
         "k_camera_blocks_f32": ("hbm", K * ob + P * 60 + M * (128 + 432)),
         "k_linearize_f32": ("hbm", K * ob + P * 132 + M * 128),
         "k_backsub_f32": ("hbm", K * ob + P * 72 + M * 152),
@@ -452,7 +467,8 @@ def run_ours(args, rank, world):
     # rooflines: the dominant kernel over the timed region; the other hot
     # kernels from the fully event-timed last warm-up step
     has_winv = prob.get("obs_winv") is not None
-    models = kernel_models(K, ctx.N, ctx.P, ctx.M, has_winv, schur_pairs(prob)) if args.precision == 1 else {}
+    models = (kernel_models(K, ctx.N, ctx.P, ctx.M, has_winv, schur_pairs(prob), tie_point_counts(prob, act0))
+              if args.precision == 1 else {})
     sbytes, live_tiles = symv_work(ctx, pcg_iters, n_sub) if pcg_iters else (None, None)
     if sbytes is not None:
         models["k_pcg_symv_ff" if args.precision == 1 else "k_pcg_symv"] = ("hbm", sbytes)

@@ -796,11 +796,14 @@ __device__ static void isect_fused_step(const View &v, int j, int *state, int *i
 }
 
 // the points are independent (cameras fixed): each thread runs its point's
-// Gauss-Newton iterations to convergence or failure in one launch
-__global__ void k_isect_fused_f(View v, int *state, int *iter, int max_iter, double tol, double px_tol,
-                                double cond_max) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= v.N) return;
+// Gauss-Newton iterations to convergence or failure in one launch. With a
+// list (the TP intersection) the threads cover the listed points only, so no
+// warp lane idles on a point that is not intersected.
+__global__ void k_isect_fused_f(View v, const int *list, int n, int *state, int *iter, int max_iter, double tol,
+                                double px_tol, double cond_max) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int j = list ? list[t] : t;
   for (int pass = 0; pass < max_iter && state[j] == 1; pass++)
     isect_fused_step(v, j, state, iter, max_iter, tol, px_tol, cond_max, pass == max_iter - 1);
 }
@@ -832,9 +835,12 @@ rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped, bool fp64) {
   double tol = ctx->opt.isect_tol;
   double px_tol = ctx->opt.isect_px_tol;
   if (ctx->opt.precision == 1 && !fp64) {  // FP32 form: every point's iterations in one launch
-    RPBA_KERNEL(ctx, "k_isect_fused_f", k_isect_fused_f<<<nblk(ctx->N, ctx->tune.isect), ctx->tune.isect, 0, ctx->stream>>>(
-                                          v, ctx->isect_state, ctx->isect_iter, maxit, tol, px_tol,
-                                          ctx->opt.cond_max));
+    const int *list = tp_only ? ctx->tp_list : nullptr;
+    int n = tp_only ? ctx->n_tp : ctx->N;
+    if (n)
+      RPBA_KERNEL(ctx, "k_isect_fused_f", k_isect_fused_f<<<nblk(n, ctx->tune.isect), ctx->tune.isect, 0, ctx->stream>>>(
+                                            v, list, n, ctx->isect_state, ctx->isect_iter, maxit, tol, px_tol,
+                                            ctx->opt.cond_max));
   } else {
     for (int it = 0; it < maxit; it++) {
       RPBA_KERNEL(ctx, "k_isect_inst", k_isect_inst<double><<<nblk(ctx->P, 128), 128, 0, ctx->stream>>>(
@@ -1045,10 +1051,20 @@ __global__ void k_obs_cost(View v, int trial, const int *run, double *cost) {
   cost[k] = F;
 }
 
+// the sigma_0 sums of one thread (FP32 form): sum w v^T W v and sum |v|^2
+// (w == 1) in float-float, the counts of active and of w == 1 observations
+struct SigmaAcc {
+  float sh = 0.f, sl = 0.f, rh = 0.f, rl = 0.f;
+  int n1 = 0, n3 = 0;
+};
+
 // FP32 form: the observation's term from its float-float residual, formed
 // in FP32 and stored in FP64 for the FP64 sum; the TP control term from the
-// float-float difference X^l - X_TP and W^l in FP32
-__device__ inline float obs_cost_term_f(const View &v, int trial, int k) {
+// float-float difference X^l - X_TP and W^l in FP32. With SIG the same
+// residual also feeds the observation's sigma_0 terms (Eq. sigma0: every
+// observation of an active point that is not deleted, whatever its depth)
+template <bool SIG = false>
+__device__ inline float obs_cost_term_f(const View &v, int trial, int k, SigmaAcc *sig = nullptr) {
   int q = v.obs_inst[k];
   int j = v.inst_pt[q];
   if (!v.active[j]) return 0.f;
@@ -1058,13 +1074,29 @@ __device__ inline float obs_cost_term_f(const View &v, int trial, int k) {
   const float *Xw = (trial ? v.Xlt_lo : v.Xl_lo) + 3 * (size_t)q;
   float r0, r1;
   float F;
-  if (!ff_residual(cf, Xh, Xw, v.obs_xy32[2 * k], v.obs_xylo[2 * k], v.obs_xy32[2 * k + 1], v.obs_xylo[2 * k + 1],
-                   r0, r1)) {
+  bool front = ff_residual(cf, Xh, Xw, v.obs_xy32[2 * k], v.obs_xylo[2 * k], v.obs_xy32[2 * k + 1],
+                           v.obs_xylo[2 * k + 1], r0, r1);
+  if (!front && !SIG) {
     F = INFINITY;
   } else {
     float W0 = 1.f, W1 = 0.f, W2 = 1.f;
     if (v.has_winv) { W0 = v.obs_winv32[3 * k]; W1 = v.obs_winv32[3 * k + 1]; W2 = v.obs_winv32[3 * k + 2]; }
-    F = v.obs_w32[k] * (W0 * r0 * r0 + 2.f * W1 * r0 * r1 + W2 * r1 * r1);
+    float w = v.obs_w32[k];
+    F = w * (W0 * r0 * r0 + 2.f * W1 * r0 * r1 + W2 * r1 * r1);
+    if constexpr (SIG) {
+      if (w != 0.f) {  // w = 0: deleted by the serial robust variant
+        float e;
+        sig->sh = ff_two_sum(sig->sh, F, e);
+        sig->sl += e;
+        sig->n1++;
+        if (w == 1.f) {
+          sig->rh = ff_two_sum(sig->rh, r0 * r0 + r1 * r1, e);
+          sig->rl += e;
+          sig->n3++;
+        }
+      }
+      if (!front) F = INFINITY;
+    }
   }
   if (k == v.inst_obs_ptr[q]) {
     const float *W = v.Wl32 + 6 * (size_t)q;
@@ -1079,14 +1111,19 @@ __device__ inline float obs_cost_term_f(const View &v, int trial, int k) {
 
 // FP32 form, F_l in two deterministic stages without a per-observation array:
 // one CTA per chunk (<= 256 observations of one sub-block, one per thread)
-// writes its sum, then one CTA per sub-block adds its chunks' sums in order
+// writes its sum, then one CTA per sub-block adds its chunks' sums in order.
+// With SIG (at a state where every X^l equals its X) the chunk also writes
+// its 5 sigma_0 sums to sig (the active points counted over a grid stride)
+template <bool SIG>
 __global__ void __launch_bounds__(256) k_cost_chunks_f(View v, int trial, const int *run, const int *chunk_sub,
-                                                       const int *chunk_start, const int *sub_obs_ptr, double *part) {
+                                                       const int *chunk_start, const int *sub_obs_ptr, double *part,
+                                                       double *sig) {
   __shared__ float2 ws[8];
   int c = blockIdx.x, l = chunk_sub[c];
   if (run && !run[l]) return;
   int k = chunk_start[c] + threadIdx.x;
-  float F = k < sub_obs_ptr[l + 1] ? obs_cost_term_f(v, trial, k) : 0.f;
+  SigmaAcc acc;
+  float F = k < sub_obs_ptr[l + 1] ? obs_cost_term_f<SIG>(v, trial, k, &acc) : 0.f;
   // a point behind its camera makes the sum +inf (TwoSum would turn it into NaN)
   int any_inf = __syncthreads_or(isinf(F));
   float h = any_inf ? 0.f : F, lo = 0.f;  // float-float sum: off the FP64 pipe
@@ -1104,14 +1141,29 @@ __global__ void __launch_bounds__(256) k_cost_chunks_f(View v, int trial, const 
     for (int w = 1; w < (int)(blockDim.x >> 5); w++) t = ff_add(t, ws[w]);
     part[c] = any_inf ? (double)INFINITY : ff_to_double(t);
   }
+  if constexpr (SIG) {
+    int np = 0;
+    for (int j = c * blockDim.x + threadIdx.x; j < v.N; j += gridDim.x * blockDim.x) np += v.active[j] ? 1 : 0;
+    sigma_cta_sums(acc.sh, acc.sl, acc.rh, acc.rl, acc.n1, acc.n3, np, sig + 5 * (size_t)c);
+  }
 }
 
-__global__ void k_cost_sub_f(int L, const int *run, const int *sub_chunk_ptr, const double *part, double *F) {
+// F_l from its chunks in order; with SIG also its chunks' sigma_0 sums
+template <bool SIG>
+__global__ void k_cost_sub_f(int L, const int *run, const int *sub_chunk_ptr, const double *part, double *F,
+                             const double *sig, double *sig_sub) {
   int l = blockIdx.x;
   if (l >= L || (run && !run[l])) return;
   double acc[1] = {0.0};
   for (int c = sub_chunk_ptr[l] + threadIdx.x; c < sub_chunk_ptr[l + 1]; c += blockDim.x) acc[0] += part[c];
   block_reduce_store<1>(acc, F + l);
+  if constexpr (SIG) {
+    double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int c = sub_chunk_ptr[l] + threadIdx.x; c < sub_chunk_ptr[l + 1]; c += blockDim.x)
+#pragma unroll
+      for (int e = 0; e < 5; e++) s[e] += sig[5 * (size_t)c + e];
+    block_reduce_store<5>(s, sig_sub + 5 * (size_t)l);
+  }
 }
 
 #define SEG_CHUNKS 32
@@ -1145,12 +1197,12 @@ static rpba_status sub_costs_impl(Ctx *ctx, int trial, const int *run, double *F
   View v = make_view(ctx);
   if (ctx->opt.precision == 1) {
     if (ctx->n_chunks)
-      RPBA_KERNEL(ctx, "k_cost_chunks_f", k_cost_chunks_f<<<ctx->n_chunks, 256, 0, ctx->stream>>>(
+      RPBA_KERNEL(ctx, "k_cost_chunks_f", k_cost_chunks_f<false><<<ctx->n_chunks, 256, 0, ctx->stream>>>(
                                          v, trial, run, ctx->chunk_sub, ctx->chunk_start, ctx->sub_obs_ptr,
-                                         ctx->chunk_part));
+                                         ctx->chunk_part, nullptr));
     if (ctx->L)
-      RPBA_KERNEL(ctx, "k_cost_sub_f", k_cost_sub_f<<<ctx->L, 256, 0, ctx->stream>>>(ctx->L, run, ctx->sub_chunk_ptr,
-                                                                                   ctx->chunk_part, F_dev));
+      RPBA_KERNEL(ctx, "k_cost_sub_f", k_cost_sub_f<false><<<ctx->L, 256, 0, ctx->stream>>>(
+                                        ctx->L, run, ctx->sub_chunk_ptr, ctx->chunk_part, F_dev, nullptr, nullptr));
     return RPBA_OK;
   }
   if (ctx->K) {
@@ -1164,6 +1216,28 @@ static rpba_status sub_costs_impl(Ctx *ctx, int trial, const int *run, double *F
 
 rpba_status launch_sub_costs(Ctx *ctx, int trial, double *F_dev) {
   return sub_costs_impl(ctx, trial, trial ? ctx->lm_run : nullptr, F_dev);
+}
+
+// FP32 form, at the end of the outer iteration's tail (after the exchange
+// and the TP copies every instance's X^l equals its point's X, so the TP
+// control terms vanish and F_l is the image part of sigma_0's sum over the
+// sub-block): one pass over the observations gives every sub-block's cost
+// (into f0_cache, for the next bact's start) and the sigma_0 sums (5 doubles
+// into pinned host memory, like sigma0_launch). Capturable, no synchronisation.
+rpba_status cost_sigma0_launch(Ctx *ctx) {
+  if (ctx->opt.precision != 1 || !ctx->n_chunks || !ctx->L) return sigma0_launch(ctx);
+  View v = make_view(ctx);
+  double *sig_chunk = ctx->sigma0_part, *sig_sub = sig_chunk + 5 * (size_t)ctx->n_chunks;
+  double *sig_tot = sig_sub + 5 * (size_t)ctx->L;
+  RPBA_KERNEL(ctx, "k_cost_chunks_f", k_cost_chunks_f<true><<<ctx->n_chunks, 256, 0, ctx->stream>>>(
+                                       v, 0, nullptr, ctx->chunk_sub, ctx->chunk_start, ctx->sub_obs_ptr,
+                                       ctx->chunk_part, sig_chunk));
+  RPBA_KERNEL(ctx, "k_cost_sub_f", k_cost_sub_f<true><<<ctx->L, 256, 0, ctx->stream>>>(
+                                    ctx->L, nullptr, ctx->sub_chunk_ptr, ctx->chunk_part, ctx->f0_cache, sig_chunk,
+                                    sig_sub));
+  RPBA_KERNEL(ctx, "k_sum_partials", k_sum_partials<5><<<1, 256, 0, ctx->stream>>>(sig_sub, ctx->L, sig_tot));
+  RPBA_CUDA(cudaMemcpyAsync(ctx->h_pinned_d, sig_tot, 5 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return RPBA_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1729,11 +1803,17 @@ rpba_status launch_lm_apply(Ctx *ctx, const int *acc_dev) {
   return RPBA_OK;
 }
 
+// the costs F_l at the start of a bact: those the outer iteration's tail left
+// when nothing has changed the state since (cost_sigma0_launch), else
+// evaluated here
 rpba_status launch_lm_init(Ctx *ctx) {
-  RPBA_TRY(sub_costs_impl(ctx, 0, nullptr, ctx->lm_Ft));
+  const double *F0 = ctx->lm_Ft;
+  if (ctx->f0_valid) F0 = ctx->f0_cache;
+  else RPBA_TRY(sub_costs_impl(ctx, 0, nullptr, ctx->lm_Ft));
+  ctx->f0_valid = false;  // the bact changes the state
   RPBA_KERNEL(ctx, "k_lm_init", k_lm_init<<<nblk(ctx->L, 128), 128, 0, ctx->stream>>>(make_view(ctx), ctx->sub_mask, ctx->opt.lambda0, ctx->opt.grace,
                                                         ctx->lm_lambda, ctx->lm_F, ctx->lm_best, ctx->lm_grace,
-                                                        ctx->lm_rej, ctx->lm_it, ctx->lm_run, ctx->lm_Ft));
+                                                        ctx->lm_rej, ctx->lm_it, ctx->lm_run, F0));
   return RPBA_OK;
 }
 

@@ -512,6 +512,14 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   RPBA_TRY(upload(ctx, &ctx->X, pb->points, 3 * (size_t)N));
   RPBA_TRY(upload(ctx, &ctx->active, active.data(), (size_t)N));
   RPBA_TRY(upload(ctx, &ctx->pt_inst_ptr, pip.data(), (size_t)N + 1));
+  {  // the tie points (points in two or more sub-blocks), for the TP intersection's launch
+    std::vector<int> tps;
+    for (int j = 0; j < N; j++)
+      if (pip[j + 1] - pip[j] >= 2) tps.push_back(j);
+    ctx->n_tp = (int)tps.size();
+    if (tps.empty()) tps.push_back(0);  // a one-element buffer; the launch covers n_tp = 0 items
+    RPBA_TRY(upload(ctx, &ctx->tp_list, tps.data(), tps.size()));
+  }
   // index maps of the boundary translation and their scratch (one per-point
   // or per-instance array at a time)
   RPBA_TRY(upload(ctx, &ctx->d_pt_inv, ctx->h_pt_inv.data(), (size_t)N));
@@ -539,6 +547,10 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
     RPBA_TRY(upload(ctx, &ctx->chunk_start, cst.data(), cst.size()));
     RPBA_TRY(upload(ctx, &ctx->sub_chunk_ptr, cp.data(), cp.size()));
     RPBA_TRY(alloc_n(ctx, &ctx->chunk_part, (size_t)std::max(ctx->n_chunks, 1)));
+    if (ctx->opt.precision == 1) {
+      RPBA_TRY(alloc_n(ctx, &ctx->f0_cache, (size_t)std::max(L, 1)));
+      RPBA_TRY(alloc_n(ctx, &ctx->sigma0_part, 5 * ((size_t)ctx->n_chunks + L + 1)));
+    }
   }
   if (ctx->opt.precision != 1)  // the FP32 form sums its cost terms per chunk
     RPBA_TRY(alloc_n(ctx, &ctx->obs_cost, (size_t)K));
@@ -756,9 +768,15 @@ extern "C" rpba_status rpba_create(const rpba_problem *prob, const rpba_options 
 // ---------------------------------------------------------------------------
 // state access
 // ---------------------------------------------------------------------------
-#define CTX_OR_FAIL                          \
+// every entry point may change the state, which ends the validity of the
+// sub-block costs the outer iteration's tail left (f0_valid); those that only
+// read it, and rpba_outer_iteration, which uses them, take CTX_KEEP_COSTS
+#define CTX_KEEP_COSTS                       \
   if (!h) return RPBA_ERR_INVALID_ARG;       \
   Ctx *ctx = &h->c;
+#define CTX_OR_FAIL \
+  CTX_KEEP_COSTS    \
+  ctx->f0_valid = false;
 
 // temporary device buffer for host transfers (freed at return)
 struct Tmp {
@@ -786,14 +804,14 @@ struct Tmp {
 };
 
 extern "C" rpba_status rpba_info(rpba_ctx *h, int32_t *L, int32_t *P) {
-  CTX_OR_FAIL;
+  CTX_KEEP_COSTS;
   if (L) *L = ctx->L;
   if (P) *P = ctx->P;
   return RPBA_OK;
 }
 
 extern "C" rpba_status rpba_sub_cameras(rpba_ctx *h, int32_t l, int32_t *cams, int32_t *n) {
-  CTX_OR_FAIL;
+  CTX_KEEP_COSTS;
   if (l < 0 || l >= ctx->L) { ctx->err = "sub-block index out of range"; return RPBA_ERR_STATE; }
   int a = ctx->h_sub_cam_ptr[l], b = ctx->h_sub_cam_ptr[l + 1];
   if (cams) for (int p = a; p < b; p++) cams[p - a] = ctx->h_sub_cam[p];
@@ -826,7 +844,7 @@ extern "C" rpba_status rpba_set_cameras(rpba_ctx *h, const double *pose) {
 }
 
 extern "C" rpba_status rpba_get_camera_rt(rpba_ctx *h, double *R, double *t) {
-  CTX_OR_FAIL;
+  CTX_KEEP_COSTS;
   if (!R || !t) return RPBA_ERR_INVALID_ARG;
   RPBA_CUDA(cudaMemcpyAsync(R, ctx->R, 9 * (size_t)ctx->M * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   RPBA_CUDA(cudaMemcpyAsync(t, ctx->t, 3 * (size_t)ctx->M * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -841,7 +859,7 @@ extern "C" rpba_status rpba_set_camera_rt(rpba_ctx *h, const double *R, const do
   return sync(ctx);
 }
 extern "C" rpba_status rpba_get_cameras(rpba_ctx *h, double *pose) {
-  CTX_OR_FAIL;
+  CTX_KEEP_COSTS;
   if (!pose) return RPBA_ERR_INVALID_ARG;
   Tmp d(ctx);
   double *buf = nullptr;
@@ -919,7 +937,7 @@ extern "C" rpba_status rpba_set_points(rpba_ctx *h, const double *X, const uint8
 }
 
 extern "C" rpba_status rpba_get_points(rpba_ctx *h, double *X, uint8_t *active) {
-  CTX_OR_FAIL;
+  CTX_KEEP_COSTS;
   if (X) RPBA_TRY(rows_out(ctx, ctx->X, X, ctx->N, 3, ctx->d_pt_inv));
   if (active) RPBA_TRY(rows_out(ctx, ctx->active, active, ctx->N, 1, ctx->d_pt_inv));
   return sync(ctx);
@@ -927,7 +945,7 @@ extern "C" rpba_status rpba_get_points(rpba_ctx *h, double *X, uint8_t *active) 
 
 // instances leave and enter in the canonical order (sub-block, caller's point id)
 extern "C" rpba_status rpba_get_instances(rpba_ctx *h, int32_t *ip, int32_t *is, double *Xl, double *Wl) {
-  CTX_OR_FAIL;
+  CTX_KEEP_COSTS;
   const std::vector<int> &canon = ctx->h_inst_canon;
   for (size_t c = 0; c < (size_t)ctx->P; c++) {
     int q = canon[c];
@@ -954,7 +972,7 @@ extern "C" rpba_status rpba_set_instances(rpba_ctx *h, const double *Xl, const d
 }
 
 extern "C" rpba_status rpba_get_weights(rpba_ctx *h, double *w) {
-  CTX_OR_FAIL;
+  CTX_KEEP_COSTS;
   if (!w) return RPBA_ERR_INVALID_ARG;
   std::vector<double> g(ctx->K);
   if (ctx->K) RPBA_CUDA(cudaMemcpyAsync(g.data(), ctx->obs_w, ctx->K * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1000,7 +1018,7 @@ extern "C" rpba_status rpba_jacobians(rpba_ctx *h, double *Jc, double *Jx) {
 }
 
 extern "C" rpba_status rpba_sigma0(rpba_ctx *h, double *s0, double *rms) {
-  CTX_OR_FAIL;
+  CTX_KEEP_COSTS;
   return launch_sigma0(ctx, s0, rms);
 }
 
@@ -1344,7 +1362,7 @@ static rpba_status outer_tail_body(Ctx *ctx, bool robust) {
   if (robust) RPBA_TRY(launch_robust_weights(ctx, nullptr));
   RPBA_TRY(launch_intersect(ctx, 1, nullptr));
   RPBA_TRY(launch_tp_copies(ctx, 1));
-  return sigma0_launch(ctx);
+  return cost_sigma0_launch(ctx);
 }
 
 static rpba_status outer_tail(Ctx *ctx, bool robust, double *sigma0) {
@@ -1369,6 +1387,8 @@ static rpba_status outer_tail(Ctx *ctx, bool robust, double *sigma0) {
     RPBA_TRY(sync(ctx));
   }
   sigma0_finish(ctx, sigma0, nullptr, nullptr, nullptr);
+  // the FP32 form's tail left the sub-block costs of this state for the next bact
+  ctx->f0_valid = ctx->opt.precision == 1 && ctx->n_chunks > 0 && ctx->L > 0;
   return RPBA_OK;
 }
 
@@ -1604,7 +1624,7 @@ extern "C" rpba_status rpba_tune(rpba_ctx *h, const char *cache_path, int32_t *c
 }
 
 extern "C" rpba_status rpba_outer_iteration(rpba_ctx *h, int32_t robust, double *sigma0, int32_t *lm_launches) {
-  CTX_OR_FAIL;
+  CTX_KEEP_COSTS;
   if (!ctx->intersected) RPBA_TRY(rpba_intersect(h));
   int inner = 0, launches = 0;
   RPBA_TRY(run_bact(ctx, &inner, &launches));
@@ -1645,6 +1665,7 @@ extern "C" rpba_status rpba_iterate(rpba_ctx *h, int32_t max_outer, rpba_report 
       if (o.robust && !robust_on) {
         robust_on = true;
         r.robust_started_at = r.outer;
+        ctx->f0_valid = false;
         RPBA_TRY(launch_robust_weights(ctx, nullptr));
         RPBA_TRY(launch_intersect(ctx, 1, nullptr));
         RPBA_TRY(launch_tp_copies(ctx, 1));
@@ -1670,7 +1691,7 @@ extern "C" rpba_status rpba_iterate(rpba_ctx *h, int32_t max_outer, rpba_report 
 // profiling
 // ---------------------------------------------------------------------------
 extern "C" rpba_status rpba_profile_enable(rpba_ctx *h, int32_t enable) {
-  CTX_OR_FAIL;
+  CTX_KEEP_COSTS;
   RPBA_TRY(sync(ctx));
   for (auto &r : ctx->prof_recs) {
     cudaEventDestroy(r.a);
@@ -1686,7 +1707,7 @@ extern "C" rpba_status rpba_profile_enable(rpba_ctx *h, int32_t enable) {
 
 extern "C" rpba_status rpba_profile_read(rpba_ctx *h, int32_t max_kernels, char *names, double *ms,
                                          int64_t *launches, int32_t *n_kernels, int64_t *total_launches) {
-  CTX_OR_FAIL;
+  CTX_KEEP_COSTS;
   RPBA_TRY(sync(ctx));
   for (auto &r : ctx->prof_recs) {
     float t = 0.f;
@@ -1714,7 +1735,7 @@ extern "C" rpba_status rpba_profile_read(rpba_ctx *h, int32_t max_kernels, char 
 }
 
 extern "C" rpba_status rpba_solver_stats(rpba_ctx *h, int32_t *iters, double *relres) {
-  CTX_OR_FAIL;
+  CTX_KEEP_COSTS;
   if (!ctx->pcg_st) {
     ctx->err = "solver statistics exist for the PCG solvers only";
     return RPBA_ERR_STATE;
@@ -1730,14 +1751,14 @@ extern "C" rpba_status rpba_solver_stats(rpba_ctx *h, int32_t *iters, double *re
 }
 
 extern "C" rpba_status rpba_solver_fallbacks(rpba_ctx *h, int64_t *n) {
-  CTX_OR_FAIL;
+  CTX_KEEP_COSTS;
   if (!n) return RPBA_ERR_INVALID_ARG;
   *n = ctx->gnn_fallbacks;
   return RPBA_OK;
 }
 
 extern "C" rpba_status rpba_profile_select(rpba_ctx *h, const char *kernel) {
-  CTX_OR_FAIL;
+  CTX_KEEP_COSTS;
   ctx->prof_only = kernel ? std::string(kernel) : std::string();
   return RPBA_OK;
 }
@@ -1786,7 +1807,7 @@ extern "C" rpba_status rpba_check_formats(const double *x, const float *f, int32
 }
 
 extern "C" rpba_status rpba_get_options(rpba_ctx *h, rpba_options *out) {
-  CTX_OR_FAIL;
+  CTX_KEEP_COSTS;
   if (!out) return RPBA_ERR_INVALID_ARG;
   *out = ctx->opt;
   return RPBA_OK;

@@ -226,6 +226,8 @@ struct Ctx {
   double *X = nullptr;
   uint8_t *active = nullptr;
   int *pt_inst_ptr = nullptr, *pt_inst = nullptr;
+  int *tp_list = nullptr;  // the tie points (>= 2 instances), internal numbering
+  int n_tp = 0;
   // instances
   int *inst_pt = nullptr, *inst_sub = nullptr, *inst_obs_ptr = nullptr, *sub_inst_ptr = nullptr;
   double *Xl = nullptr, *Xlt = nullptr, *Wl = nullptr, *inst_cost = nullptr;
@@ -279,6 +281,12 @@ struct Ctx {
   int *chunk_sub = nullptr, *chunk_start = nullptr, *sub_chunk_ptr = nullptr;
   int n_chunks = 0;
   double *chunk_part = nullptr;
+  // FP32 form: the outer iteration's tail evaluates the sub-block costs with
+  // the sigma_0 sums in one pass (every X^l equals its X there); the next
+  // bact starts from these costs while no entry point has changed the state
+  // since. sigma0_part: 5 sums per chunk, then per sub-block, then the total
+  double *f0_cache = nullptr, *sigma0_part = nullptr;
+  bool f0_valid = false;
   std::vector<int> h_sched;  // per factorisation step: prefix sums of panel and update tiles
   int *sched = nullptr;
   double *Linv64 = nullptr;
@@ -449,6 +457,7 @@ rpba_status launch_jacobians(Ctx *ctx, double *Jc_dev, double *Jx_dev);
 // sigma_0 in two halves: the sums into pinned memory (capturable), and the
 // values from them after a synchronisation
 rpba_status sigma0_launch(Ctx *ctx);
+rpba_status cost_sigma0_launch(Ctx *ctx);
 void sigma0_finish(const Ctx *ctx, double *sigma0, double *rms, long long *n_obs, long long *n_points);
 rpba_status launch_sigma0(Ctx *ctx, double *sigma0, double *rms, long long *n_obs = nullptr,
                           long long *n_points = nullptr);

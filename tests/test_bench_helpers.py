@@ -106,3 +106,16 @@ def test_reference_arm_prints_one_line_with_the_contract_keys():
     o = oracle.Oracle(synth.config(1))
     o.intersect()
     assert d["config"]["n_obs_block"] == bench.counted_obs(synth.config(1), o.points()[1])
+
+
+def test_tie_point_counts_by_brute_force():
+    prob = synth.config(1)
+    rng = np.random.default_rng(1)
+    act = (rng.random(prob["points"].shape[0]) < 0.8).astype(np.uint8)
+    subs_of = {}
+    for c, j in zip(prob["obs_cam"], prob["obs_point"]):
+        subs_of.setdefault(int(j), set()).add(int(prob["cam_subblock"][c]))
+    tps = {j for j, s in subs_of.items() if len(s) >= 2 and act[j]}
+    n_obs = sum(1 for j in prob["obs_point"] if int(j) in tps)
+    n_inst = sum(len(subs_of[j]) for j in tps)
+    assert bench.tie_point_counts(prob, act) == (len(tps), n_obs, n_inst)
