@@ -693,11 +693,17 @@ __device__ static void isect_fused_step(const View &v, int j, int *state, int *i
   float Nh[6] = {0, 0, 0, 0, 0, 0}, Nl[6] = {0, 0, 0, 0, 0, 0};  // N_j in float-float
   bool behind = false;
   float nobs = 0.f;
+  const bool tp = (q1 - q0) >= 2;
   for (int a = q0; a < q1; a++) {
     int q = v.pt_inst[a];
     float Nq[6] = {0, 0, 0, 0, 0, 0};
     for (int k = v.inst_obs_ptr[q]; k < v.inst_obs_ptr[q + 1]; k++) isect_obs_acc(v, j, k, Nq, g, behind);
     for (int e = 0; e < 6; e++) { N[e] += Nq[e]; ff_acc(Nh[e], Nl[e], Nq[e]); }
+    // each instance's part N_j^(l) waits in its W^l slot (this point's thread
+    // alone touches it) until the refined weight is formed at convergence;
+    // every point leaves the launch converged or failed, which overwrites it
+    if (tp)
+      for (int e = 0; e < 6; e++) v.Wl32[6 * (size_t)q + e] = Nq[e];
     nobs += (float)(v.inst_obs_ptr[q + 1] - v.inst_obs_ptr[q]);
   }
   bool fail = behind;
@@ -760,26 +766,16 @@ __device__ static void isect_fused_step(const View &v, int j, int *state, int *i
       }
   } else if (conv) {
     state[j] = 2;
-    bool tp = (q1 - q0) >= 2;
     for (int a = q0; a < q1; a++) {
       int q = v.pt_inst[a];
       if (!tp) {
         for (int e = 0; e < 6; e++) { v.Wl[6 * (size_t)q + e] = 0.0; v.Wl32[6 * (size_t)q + e] = 0.f; }
         continue;
       }
-      // this instance's part at the same (pre-step) X: the hi/lo words moved,
-      // so re-form it from the position before the update
-      float Nq[6] = {0, 0, 0, 0, 0, 0}, gq[3] = {0, 0, 0};
-      bool bq = false;
-      float *xh = v.X_hi + 3 * (size_t)j, *xl = v.X_lo + 3 * (size_t)j;
-      float sh[3], sl[3];
-      for (int r = 0; r < 3; r++) {
-        sh[r] = xh[r]; sl[r] = xl[r];
-        float2 xo = ff_add(make_float2(xh[r], xl[r]), make_float2(df[r], 0.f));
-        xh[r] = xo.x; xl[r] = xo.y;
-      }
-      for (int k = v.inst_obs_ptr[q]; k < v.inst_obs_ptr[q + 1]; k++) isect_obs_acc(v, j, k, Nq, gq, bq);
-      for (int r = 0; r < 3; r++) { xh[r] = sh[r]; xl[r] = sl[r]; }
+      // this instance's part at the same (pre-step) X as N_j: the one this
+      // pass left in the W^l slot
+      float Nq[6];
+      for (int e = 0; e < 6; e++) Nq[e] = v.Wl32[6 * (size_t)q + e];
       for (int e = 0; e < 6; e++) {
         float2 w = ff_add(make_float2(Nh[e], Nl[e]), make_float2(-Nq[e], 0.f));
         if (v.wmode) {
@@ -1513,40 +1509,46 @@ __global__ void k_schur_pairs(View v, const int *run, const int *pa, const int *
   }
 }
 
-// FP32 form, off-diagonal Schur blocks: one thread per point pair (a seen
-// by camera i, b seen by camera i', the same instance, local(i) > local(i')),
+// FP32 form, off-diagonal Schur blocks: point pairs (a seen by camera i, b
+// seen by camera i', the same instance, local(i) > local(i')),
 //   S[6 li + r, 6 li' + c] -= sum_e N_XC,a[e][r] Z_b[e][c],
 // the blocks formed in FP32 registers. The pairs are sorted by camera pair
-// (segment), so a warp's 32 pairs cover few segments: a segmented warp
-// reduction sums each segment's part and its first lane adds the 36 values
-// to S (FP64 atomics, one set per segment piece instead of one per pair).
+// (segment) and cut into items of at most SC_ITEM consecutive pairs of one
+// segment; a thread sums its item's blocks in registers, then a segmented
+// warp reduction (items sorted, so a segment is a run of lanes) sums each
+// segment's part and its first lane adds the 36 values to S (FP64 atomics,
+// one set per segment piece instead of one per pair).
 #define SC_THREADS 256
-__global__ void __launch_bounds__(SC_THREADS) k_schur_seg(View v, const int *run, long long npairs,
-                                                          const int *spa, const int *spb, const int *spq,
-                                                          const int *sps, const int *seg_cam, const int *seg_nb,
-                                                          const float *Ninv) {
-  long long p = (long long)blockIdx.x * SC_THREADS + threadIdx.x;
+__global__ void __launch_bounds__(SC_THREADS, 2) k_schur_seg(View v, const int *run, long long nitems,
+                                                             const int *item, const int *spa, const int *spb,
+                                                             const int *spq, const int *sps, const int *seg_cam,
+                                                             const int *seg_nb, const float *Ninv) {
+  long long it = (long long)blockIdx.x * SC_THREADS + threadIdx.x;
   int lane = threadIdx.x & 31;
   int sg = -1;
   float acc[36];
 #pragma unroll
   for (int e = 0; e < 36; e++) acc[e] = 0.f;
-  if (p < npairs) {
-    sg = sps[p];
-    int i = seg_cam[sg], ib = seg_nb[sg], q = spq[p];
-    if (run[v.cam_sub[i]] && v.active[v.inst_pt[q]]) {
-      float A[18], B[18], Zb[18];
-      nxc_f(v, i, spa[p], q, A);
-      nxc_f(v, ib, spb[p], q, B);
-      const float *iv = Ninv + 6 * (size_t)q;
-      float inv[6] = {iv[0], iv[1], iv[2], iv[3], iv[4], iv[5]};
-      z_of(inv, B, Zb);
+  if (it < nitems) {
+    int t0 = item[it], t1 = item[it + 1];
+    sg = sps[t0];
+    int i = seg_cam[sg], ib = seg_nb[sg];
+    if (run[v.cam_sub[i]])
+      for (int t = t0; t < t1; t++) {
+        int q = spq[t];
+        if (!v.active[v.inst_pt[q]]) continue;
+        float A[18], B[18], Zb[18];
+        nxc_f(v, i, spa[t], q, A);
+        nxc_f(v, ib, spb[t], q, B);
+        const float *iv = Ninv + 6 * (size_t)q;
+        float inv[6] = {iv[0], iv[1], iv[2], iv[3], iv[4], iv[5]};
+        z_of(inv, B, Zb);
 #pragma unroll
-      for (int r = 0; r < 6; r++)
+        for (int r = 0; r < 6; r++)
 #pragma unroll
-        for (int c = 0; c < 6; c++)
-          acc[6 * r + c] = A[r] * Zb[c] + A[6 + r] * Zb[6 + c] + A[12 + r] * Zb[12 + c];
-    }
+          for (int c = 0; c < 6; c++)
+            acc[6 * r + c] += A[r] * Zb[c] + A[6 + r] * Zb[6 + c] + A[12 + r] * Zb[12 + c];
+      }
   }
   // segments are contiguous runs of lanes: after the steps, a lane holds the
   // sum over itself and the following lanes of its run
@@ -1601,9 +1603,10 @@ rpba_status launch_build_rcs(Ctx *ctx, const double *lambda_dev, const int *run_
     RPBA_KERNEL(ctx, "k_camera_blocks_f32", k_camera_blocks<float><<<ctx->M, CB_THREADS, 0, ctx->stream>>>(
         v, lambda_dev, run_dev, nullptr, nullptr, (const float *)ctx->gX, (const float *)ctx->Ninv));
     if (ctx->n_pairs)
-      RPBA_KERNEL(ctx, "k_schur_seg", k_schur_seg<<<nblk(ctx->n_pairs, SC_THREADS), SC_THREADS, 0, ctx->stream>>>(
-                                          v, run_dev, ctx->n_pairs, ctx->spair_a, ctx->spair_b, ctx->spair_q,
-                                          ctx->spair_seg, ctx->seg_cam, ctx->seg_nb, (const float *)ctx->Ninv));
+      RPBA_KERNEL(ctx, "k_schur_seg", k_schur_seg<<<nblk(ctx->n_items, SC_THREADS), SC_THREADS, 0, ctx->stream>>>(
+                                          v, run_dev, ctx->n_items, ctx->sitem, ctx->spair_a, ctx->spair_b,
+                                          ctx->spair_q, ctx->spair_seg, ctx->seg_cam, ctx->seg_nb,
+                                          (const float *)ctx->Ninv));
   } else {
     double *NXC = (double *)ctx->NXC, *Z = (double *)ctx->Z;
     RPBA_KERNEL(ctx, "k_linearize_f64", k_linearize<double><<<nblk(ctx->P, ctx->tune.lin), ctx->tune.lin, 0, ctx->stream>>>(v, lambda_dev, run_dev, NXC, Z,

@@ -3,6 +3,7 @@
 // the host driver of the iteration of Sec. 5 (bact of all sub-blocks in lock
 // step, exchange, bars, convergence, robust stage).
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <math.h>
 #include <string.h>
 
@@ -387,9 +388,13 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   // segment per camera pair (i, i')), then by position: camera i owns the
   // off-diagonal blocks S_{i,i'} with local(i) > local(i'), each the sum over
   // one segment
-  std::vector<int> spa, spb, spq, sps, seg_cam, seg_nb;
+  std::vector<int> spa, spb, spq, sps, seg_cam, seg_nb, sitem;
   if (ctx->opt.precision == 1) {
     long long np = ctx->n_pairs;
+    if (np >= INT_MAX) {  // pair positions and items are 32-bit
+      ctx->err = "more than 2^31 - 1 Schur pairs";
+      return RPBA_ERR_INVALID_ARG;
+    }
     std::vector<long long> by_b(np), cnt(M + 1, 0);
     auto cam_of = [&](int pos) { return pb->obs_cam[order[pos]]; };
     for (long long e = 0; e < np; e++) cnt[cam_of(pb_[e]) + 1]++;
@@ -423,6 +428,14 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
       sps[t] = (int)seg_cam.size() - 1;
     }
     ctx->n_segs = (long long)seg_nb.size();
+    for (long long t = 0; t < np;) {  // items: up to SC_ITEM pairs of one segment
+      sitem.push_back((int)t);
+      long long e = t + 1;
+      while (e < np && e - t < SC_ITEM && sps[e] == sps[t]) e++;
+      t = e;
+    }
+    ctx->n_items = (long long)sitem.size();
+    sitem.push_back((int)np);
     pa.clear(); pa.shrink_to_fit();
     pb_.clear(); pb_.shrink_to_fit();
   }
@@ -631,6 +644,7 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
     RPBA_TRY(upload(ctx, &ctx->spair_seg, sps.data(), sps.size()));
     RPBA_TRY(upload(ctx, &ctx->seg_cam, seg_cam.data(), seg_cam.size()));
     RPBA_TRY(upload(ctx, &ctx->seg_nb, seg_nb.data(), seg_nb.size()));
+    RPBA_TRY(upload(ctx, &ctx->sitem, sitem.data(), sitem.size()));
   } else {
     RPBA_TRY(upload(ctx, &ctx->pair_a, pa.data(), pa.size()));
     RPBA_TRY(upload(ctx, &ctx->pair_b, pb_.data(), pb_.size()));

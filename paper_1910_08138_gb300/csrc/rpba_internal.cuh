@@ -174,6 +174,9 @@ struct GraphRec;
 
 // launch shapes the autotuner picks (rpba_tune): block sizes of kernels that
 // give every thread one independent item, so they change timing, not results
+// the FP32 Schur kernel's pairs per thread (consecutive pairs of one segment)
+#define SC_ITEM 8
+
 struct Tuning {
   int isect = 128;    // k_isect_fused_f: points per CTA
   int lin = 128;      // k_linearize: instances per CTA
@@ -248,6 +251,10 @@ struct Ctx {
   int *spair_a = nullptr, *spair_b = nullptr, *spair_q = nullptr, *spair_seg = nullptr;
   int *seg_cam = nullptr, *seg_nb = nullptr;
   long long n_segs = 0;
+  // items: runs of at most SC_ITEM consecutive pairs of one segment, one per
+  // thread of the Schur kernel (first pair of each item, then n_pairs)
+  int *sitem = nullptr;
+  long long n_items = 0;
   // FP32 form, block-Jacobi PCG in float-float: the RCS as hi + lo pairs (the
   // layout of S), the vectors x, r, p as pairs and z in FP32, M^-1 in FP32
   float2 *pcg_Sff = nullptr, *pcg_fx = nullptr, *pcg_fr = nullptr, *pcg_fp = nullptr;
