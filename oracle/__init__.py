@@ -81,6 +81,13 @@ def lib():
         L.orc_rotation_log.argtypes = [_dp, _dp]
         L.orc_project.argtypes = [_dp, _dp, _dp, _dp, _dp, _dp, _dp]
         L.orc_project.restype = C.c_double
+        L.orc_project_k1.argtypes = [_dp, _dp, _dp, C.c_double, _dp, _dp, _dp, _dp]
+        L.orc_project_k1.restype = C.c_double
+        L.orc_enable_intrinsics.argtypes = [C.c_void_p, C.c_void_p]
+        L.orc_camera_dim.argtypes = [C.c_void_p]
+        L.orc_camera_dim.restype = C.c_int
+        L.orc_get_intrinsics.argtypes = [C.c_void_p, _dp]
+        L.orc_set_intrinsics.argtypes = [C.c_void_p, _dp]
         L.orc_residuals.argtypes = [C.c_void_p, _dp]
         L.orc_jacobians.argtypes = [C.c_void_p, _dp, _dp]
         L.orc_sigma0.argtypes = [C.c_void_p]
@@ -158,6 +165,13 @@ def project(R, t, intr, X):
     return uv, Jc.reshape(2, 6), Jx.reshape(2, 3), z
 
 
+def project_k1(R, t, intr, k1, X):
+    """With the radial parameter k1: returns (uv, Jc 2x8, Jx 2x3, depth)."""
+    uv, Jc, Jx = np.zeros(2), np.zeros(16), np.zeros(6)
+    z = lib().orc_project_k1(_f64(R).reshape(-1), _f64(t), _f64(intr), float(k1), _f64(X), uv, Jc, Jx)
+    return uv, Jc.reshape(2, 8), Jx.reshape(2, 3), z
+
+
 def lambda_next(lam, accepted, lambda0):
     return lib().orc_lambda_next(float(lam), int(accepted), float(lambda0))
 
@@ -179,9 +193,12 @@ def median(a):
 
 
 class Oracle:
-    """One oracle context over a problem dict (see paper_1910_08138_gb300.synth)."""
+    """One oracle context over a problem dict (see paper_1910_08138_gb300.synth).
+    With intrinsics (default: the problem's "intrinsics" entry) the focal
+    length and the radial parameter of every camera are unknowns too, starting
+    from cam_intr's f and the problem's "cam_k1" (0 when absent)."""
 
-    def __init__(self, prob):
+    def __init__(self, prob, intrinsics=None):
         L = lib()
         self.M = int(prob["cam_pose"].shape[0])
         self.N = int(prob["points"].shape[0])
@@ -195,6 +212,13 @@ class Oracle:
                                _i32(prob["cam_subblock"]))
         self.L = L.orc_num_subblocks(self._h)
         self.P = L.orc_num_instances(self._h)
+        if intrinsics is None:
+            intrinsics = bool(prob.get("intrinsics", False))
+        if intrinsics:
+            k1 = prob.get("cam_k1")
+            self._k1 = None if k1 is None else _f64(k1, (self.M,))
+            L.orc_enable_intrinsics(self._h, None if self._k1 is None else self._k1.ctypes.data_as(C.c_void_p))
+        self.cd = L.orc_camera_dim(self._h)
 
     def __del__(self):
         if getattr(self, "_h", None):
@@ -232,6 +256,15 @@ class Oracle:
         Rt = _f64(Rt, (self.M, 12))
         lib().orc_set_camera_rt(self._h, np.ascontiguousarray(Rt[:, :9]), np.ascontiguousarray(Rt[:, 9:]))
 
+    def intrinsics(self):
+        """(M, 2): focal length and radial parameter k1 of every camera."""
+        fk = np.zeros((self.M, 2))
+        lib().orc_get_intrinsics(self._h, fk)
+        return fk
+
+    def set_intrinsics(self, fk):
+        lib().orc_set_intrinsics(self._h, _f64(fk, (self.M, 2)))
+
     def points(self):
         X, a = np.zeros((self.N, 3)), np.zeros(self.N, np.uint8)
         lib().orc_get_points(self._h, X, a)
@@ -266,9 +299,9 @@ class Oracle:
         return v
 
     def jacobians(self):
-        Jc, Jx = np.zeros((self.K, 12)), np.zeros((self.K, 6))
+        Jc, Jx = np.zeros((self.K, 2 * self.cd)), np.zeros((self.K, 6))
         lib().orc_jacobians(self._h, Jc, Jx)
-        return Jc.reshape(self.K, 2, 6), Jx.reshape(self.K, 2, 3)
+        return Jc.reshape(self.K, 2, self.cd), Jx.reshape(self.K, 2, 3)
 
     def sigma0(self):
         return lib().orc_sigma0(self._h)
@@ -309,13 +342,13 @@ class Oracle:
         return lib().orc_sub_cost(self._h, l)
 
     def rcs(self, l, lam):
-        n = 6 * len(self.sub_cameras(l))
+        n = self.cd * len(self.sub_cameras(l))
         S, y = np.zeros((n, n)), np.zeros(n)
         lib().orc_rcs(self._h, l, lam, S, y)
         return S, y
 
     def lm_step(self, l, lam):
-        n = 6 * len(self.sub_cameras(l))
+        n = self.cd * len(self.sub_cameras(l))
         _, s = self.instances()
         nP = int((s == l).sum())
         dc, dx = np.zeros(max(n, 1)), np.zeros((max(nP, 1), 3))

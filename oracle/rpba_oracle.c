@@ -43,7 +43,13 @@
  *    with a down-weighted observation is eliminated.
  *  - an LM trial with any observation behind its camera is rejected.
  *  - redundancy of sigma_0: 2 K - 6 M - 3 N + 7 over the active observations
- *    and points (free network).
+ *    and points (free network); with per-camera intrinsics 2 K - 8 M - 3 N + 7.
+ *  - per-camera intrinsics (the Final data sets of Sec. 6: focal length and
+ *    the first radial distortion parameter estimated per camera): the radial
+ *    polynomial acts on the normalised image coordinates p = (x_c/z_c, y_c/z_c),
+ *    u = f (1 + k1 |p|^2) p_x + cx, v = f (1 + k1 |p|^2) p_y + cy, with the
+ *    principal point fixed; the camera unknowns are (dw, dt, df, dk1), f and
+ *    k1 updated additively.
  */
 #include "rpba_oracle.h"
 
@@ -53,7 +59,9 @@
 
 struct orc_ctx {
   int M, N, K, L, P;
-  double *intr;
+  int cd;       /* camera unknowns: 6 (pose) or 8 (pose, f, k1) */
+  double *intr; /* (f, cx, cy) per camera; f is estimated when cd = 8 */
+  double *k1;   /* radial parameter per camera (0 unless cd = 8) */
   int *cam_sub;
   int *obs_cam, *obs_pt;
   double *obs_xy, *obs_winv;
@@ -247,6 +255,56 @@ double orc_project(const double R[9], const double t[3], const double intr[3],
   return Xc[2];
 }
 
+/* g_k with the first radial distortion parameter (the Final data sets of
+ * Sec. 6): p = (x_c/z_c, y_c/z_c), d = 1 + k1 |p|^2, (u, v) = f d p + (cx, cy).
+ * Jc (2 x 8) = d(u,v)/d(dw, dt, df, dk1) with the rotation convention of
+ * orc_project; Jx = d(u,v)/dX. */
+double orc_project_k1(const double R[9], const double t[3], const double intr[3], double k1,
+                      const double X[3], double uv[2], double Jc[16], double Jx[6]) {
+  double RX[3], Xc[3];
+  for (int r = 0; r < 3; r++) {
+    RX[r] = R[r * 3 + 0] * X[0] + R[r * 3 + 1] * X[1] + R[r * 3 + 2] * X[2];
+    Xc[r] = RX[r] + t[r];
+  }
+  double f = intr[0];
+  double iz = 1.0 / Xc[2];
+  double px = Xc[0] * iz, py = Xc[1] * iz;
+  double r2 = px * px + py * py;
+  double d = 1.0 + k1 * r2;
+  if (uv) {
+    uv[0] = f * d * px + intr[1];
+    uv[1] = f * d * py + intr[2];
+  }
+  if (Jc || Jx) {
+    /* d(u,v)/dp = f (d I + 2 k1 p p^T); dp/dXc = (1/z) [I2 | -p] */
+    double D[4] = {f * (d + 2.0 * k1 * px * px), f * 2.0 * k1 * px * py,
+                   f * 2.0 * k1 * px * py, f * (d + 2.0 * k1 * py * py)};
+    double Q[6] = {iz, 0.0, -px * iz, 0.0, iz, -py * iz};
+    double P[6]; /* d(u,v)/dXc = D Q */
+    for (int r = 0; r < 2; r++)
+      for (int c = 0; c < 3; c++) P[r * 3 + c] = D[r * 2 + 0] * Q[c] + D[r * 2 + 1] * Q[3 + c];
+    if (Jx)
+      for (int r = 0; r < 2; r++)
+        for (int c = 0; c < 3; c++)
+          Jx[r * 3 + c] = P[r * 3 + 0] * R[0 * 3 + c] + P[r * 3 + 1] * R[1 * 3 + c] +
+                          P[r * 3 + 2] * R[2 * 3 + c];
+    if (Jc) {
+      double M[9] = {0.0, RX[2], -RX[1], -RX[2], 0.0, RX[0], RX[1], -RX[0], 0.0};
+      double pp[2] = {px, py};
+      for (int r = 0; r < 2; r++) {
+        for (int c = 0; c < 3; c++) {
+          Jc[r * 8 + c] = P[r * 3 + 0] * M[0 * 3 + c] + P[r * 3 + 1] * M[1 * 3 + c] +
+                          P[r * 3 + 2] * M[2 * 3 + c];
+          Jc[r * 8 + 3 + c] = P[r * 3 + c];
+        }
+        Jc[r * 8 + 6] = d * pp[r];      /* d/df */
+        Jc[r * 8 + 7] = f * r2 * pp[r]; /* d/dk1 */
+      }
+    }
+  }
+  return Xc[2];
+}
+
 /* ------------------------------------------------------------------------ */
 /* construction                                                              */
 /* ------------------------------------------------------------------------ */
@@ -301,8 +359,10 @@ orc_ctx *orc_create(int M, int N, int K, const double *cam_pose, const double *c
                     const double *obs_xy, const double *obs_winv, const int *cam_sub) {
   orc_ctx *c = (orc_ctx *)calloc(1, sizeof(orc_ctx));
   c->M = M; c->N = N; c->K = K;
-  c->intr = (double *)malloc(sizeof(double) * 3 * M);
+  c->cd = 6;
+  c->intr = (double *)malloc(sizeof(double) * 3 * (M > 0 ? M : 1));
   memcpy(c->intr, cam_intr, sizeof(double) * 3 * M);
+  c->k1 = (double *)calloc((size_t)(M > 0 ? M : 1), sizeof(double));
   c->cam_sub = (int *)malloc(sizeof(int) * M);
   memcpy(c->cam_sub, cam_sub, sizeof(int) * M);
   int L = 0;
@@ -385,7 +445,7 @@ orc_ctx *orc_create(int M, int N, int K, const double *cam_pose, const double *c
 
 void orc_destroy(orc_ctx *c) {
   if (!c) return;
-  free(c->intr); free(c->cam_sub); free(c->obs_cam); free(c->obs_pt); free(c->obs_xy);
+  free(c->intr); free(c->k1); free(c->cam_sub); free(c->obs_cam); free(c->obs_pt); free(c->obs_xy);
   free(c->obs_winv); free(c->obs_inst); free(c->inst_pt); free(c->inst_sub);
   free(c->inst_obs_ptr); free(c->inst_obs); free(c->pt_inst_ptr); free(c->pt_inst);
   free(c->pt_obs_ptr); free(c->pt_obs); free(c->cam_obs_ptr); free(c->cam_obs);
@@ -435,6 +495,27 @@ void orc_set_camera_rt(orc_ctx *c, const double *R, const double *t) {
   memcpy(c->t, t, sizeof(double) * 3 * c->M);
 }
 
+void orc_enable_intrinsics(orc_ctx *c, const double *k1) {
+  c->cd = 8;
+  for (int i = 0; i < c->M; i++) c->k1[i] = k1 ? k1[i] : 0.0;
+}
+
+int orc_camera_dim(const orc_ctx *c) { return c->cd; }
+
+void orc_get_intrinsics(const orc_ctx *c, double *fk) {
+  for (int i = 0; i < c->M; i++) {
+    fk[2 * i] = c->intr[3 * i];
+    fk[2 * i + 1] = c->k1[i];
+  }
+}
+
+void orc_set_intrinsics(orc_ctx *c, const double *fk) {
+  for (int i = 0; i < c->M; i++) {
+    c->intr[3 * i] = fk[2 * i];
+    c->k1[i] = fk[2 * i + 1];
+  }
+}
+
 void orc_get_points(const orc_ctx *c, double *X, unsigned char *active) {
   if (X) memcpy(X, c->X, sizeof(double) * 3 * c->N);
   if (active) memcpy(active, c->active, (size_t)c->N);
@@ -462,14 +543,23 @@ void orc_set_weights(orc_ctx *c, const double *w) { memcpy(c->w, w, sizeof(doubl
 /* evaluations at the global state                                          */
 /* ------------------------------------------------------------------------ */
 
-static double obs_residual(const orc_ctx *c, int k, const double *R, const double *t,
-                           const double *X, double v[2], double Jc[12], double Jx[6]) {
+/* residual of observation k for the camera arrays R, t, intr, k1 (global
+ * indexing); Jc is 2 x cd */
+static double obs_residual_at(const orc_ctx *c, int k, const double *R, const double *t,
+                              const double *intr, const double *k1, const double *X, double v[2],
+                              double *Jc, double Jx[6]) {
   int i = c->obs_cam[k];
   double uv[2];
-  double z = orc_project(R + 9 * i, t + 3 * i, c->intr + 3 * i, X, uv, Jc, Jx);
+  double z = c->cd == 8 ? orc_project_k1(R + 9 * i, t + 3 * i, intr + 3 * i, k1[i], X, uv, Jc, Jx)
+                        : orc_project(R + 9 * i, t + 3 * i, intr + 3 * i, X, uv, Jc, Jx);
   v[0] = uv[0] - c->obs_xy[2 * k + 0];
   v[1] = uv[1] - c->obs_xy[2 * k + 1];
   return z;
+}
+
+static double obs_residual(const orc_ctx *c, int k, const double *R, const double *t,
+                           const double *X, double v[2], double *Jc, double Jx[6]) {
+  return obs_residual_at(c, k, R, t, c->intr, c->k1, X, v, Jc, Jx);
 }
 
 static double quad_w(const double W[3], const double v[2]) {
@@ -484,7 +574,7 @@ void orc_residuals(const orc_ctx *c, double *v) {
 void orc_jacobians(const orc_ctx *c, double *Jc, double *Jx) {
   double v[2];
   for (int k = 0; k < c->K; k++)
-    obs_residual(c, k, c->R, c->t, c->X + 3 * c->obs_pt[k], v, Jc + 12 * k, Jx + 6 * k);
+    obs_residual(c, k, c->R, c->t, c->X + 3 * c->obs_pt[k], v, Jc + 2 * (size_t)c->cd * k, Jx + 6 * k);
 }
 
 /* sigma_0 (Eq. sigma0, with C^-1 as in Eq. normalw) over the active points */
@@ -500,7 +590,7 @@ double orc_sigma0(const orc_ctx *c) {
     sum += c->w[k] * quad_w(c->obs_winv + 3 * k, v);
     kact++;
   }
-  double red = 2.0 * (double)kact - 6.0 * c->M - 3.0 * (double)nact + 7.0;
+  double red = 2.0 * (double)kact - (double)c->cd * c->M - 3.0 * (double)nact + 7.0;
   if (red < 1.0) red = 1.0;
   return sqrt(sum / red);
 }
@@ -735,14 +825,14 @@ int orc_intersect_points(orc_ctx *c, const orc_options *o, const int *ids, int n
 
 /* F_l for given camera arrays (global indexing) and instance positions */
 static double sub_cost_at(const orc_ctx *c, int l, const double *R, const double *t,
-                          const double *Xl) {
+                          const double *intr, const double *k1, const double *Xl) {
   double F = 0.0, v[2];
   for (int q = c->sub_inst_ptr[l]; q < c->sub_inst_ptr[l + 1]; q++) {
     int j = c->inst_pt[q];
     if (!c->active[j]) continue;
     for (int p = c->inst_obs_ptr[q]; p < c->inst_obs_ptr[q + 1]; p++) {
       int k = c->inst_obs[p];
-      double z = obs_residual(c, k, R, t, Xl + 3 * q, v, NULL, NULL);
+      double z = obs_residual_at(c, k, R, t, intr, k1, Xl + 3 * q, v, NULL, NULL);
       if (!(z > 0.0)) return INFINITY;
       F += c->w[k] * quad_w(c->obs_winv + 3 * k, v);
     }
@@ -754,23 +844,24 @@ static double sub_cost_at(const orc_ctx *c, int l, const double *R, const double
   return F;
 }
 
-double orc_sub_cost(const orc_ctx *c, int l) { return sub_cost_at(c, l, c->R, c->t, c->Xl); }
+double orc_sub_cost(const orc_ctx *c, int l) { return sub_cost_at(c, l, c->R, c->t, c->intr, c->k1, c->Xl); }
 
 /* Normal equations of sub-block l, damped, reduced to the cameras (Sec. 2,
  * Sec. 5.5). For every instance q of l also returns Ninv (inverse of the
  * damped point block, sym3) and gX (the point gradient). */
 static int rcs_build(const orc_ctx *c, int l, double lambda, double *S, double *y,
                      double *Ninv, double *gX) {
+  const int cd = c->cd;
   int c0 = c->sub_cam_ptr[l], Ml = c->sub_cam_ptr[l + 1] - c0;
-  int n = 6 * Ml;
+  int n = cd * Ml;
   memset(S, 0, sizeof(double) * (size_t)n * n);
   memset(y, 0, sizeof(double) * n);
-  double *NCC = (double *)calloc((size_t)36 * (Ml > 0 ? Ml : 1), sizeof(double));
-  double *gC = (double *)calloc((size_t)6 * (Ml > 0 ? Ml : 1), sizeof(double));
+  double *NCC = (double *)calloc((size_t)cd * cd * (Ml > 0 ? Ml : 1), sizeof(double));
+  double *gC = (double *)calloc((size_t)cd * (Ml > 0 ? Ml : 1), sizeof(double));
   int mmax = c->max_inst_obs;
-  double *NXC = (double *)malloc(sizeof(double) * 18 * mmax);
+  double *NXC = (double *)malloc(sizeof(double) * 3 * cd * mmax);
   int *loc = (int *)malloc(sizeof(int) * mmax);
-  double v[2], Jc[12], Jx[6];
+  double v[2], Jc[16], Jx[6];
   int q0 = c->sub_inst_ptr[l];
   for (int q = q0; q < c->sub_inst_ptr[l + 1]; q++) {
     int j = c->inst_pt[q];
@@ -788,12 +879,12 @@ static int rcs_build(const orc_ctx *c, int l, double lambda, double *S, double *
       obs_residual(c, k, c->R, c->t, c->Xl + 3 * q, v, Jc, Jx);
       const double *W = c->obs_winv + 3 * k;
       double wk = c->w[k];
-      add_AtWB(Jc, 6, Jc, 6, W, wk, NCC + 36 * li);   /* N_CC block of camera i */
-      add_AtWB(Jc, 6, v, 1, W, wk, gC + 6 * li);      /* camera gradient */
-      add_AtWB(Jx, 3, Jx, 3, W, wk, NXX);             /* N_XX */
-      add_AtWB(Jx, 3, v, 1, W, wk, g);                /* point gradient */
-      memset(NXC + 18 * m, 0, 18 * sizeof(double));
-      add_AtWB(Jx, 3, Jc, 6, W, wk, NXC + 18 * m);    /* N_XC block (3 x 6) */
+      add_AtWB(Jc, cd, Jc, cd, W, wk, NCC + cd * cd * li); /* N_CC block of camera i */
+      add_AtWB(Jc, cd, v, 1, W, wk, gC + cd * li);         /* camera gradient */
+      add_AtWB(Jx, 3, Jx, 3, W, wk, NXX);                  /* N_XX */
+      add_AtWB(Jx, 3, v, 1, W, wk, g);                     /* point gradient */
+      memset(NXC + 3 * cd * m, 0, 3 * cd * sizeof(double));
+      add_AtWB(Jx, 3, Jc, cd, W, wk, NXC + 3 * cd * m);    /* N_XC block (3 x cd) */
     }
     /* TP as control point: + (X^l - X_TP)^T W^l (X^l - X_TP) */
     const double *Wl = c->Wl + 6 * q;
@@ -813,37 +904,37 @@ static int rcs_build(const orc_ctx *c, int l, double lambda, double *S, double *
     double Ng[3];
     sym3_mul_vec(Ni, g, Ng);
     for (int a = 0; a < m; a++) {
-      const double *Ba = NXC + 18 * a;
-      for (int r = 0; r < 6; r++) {
+      const double *Ba = NXC + 3 * cd * a;
+      for (int r = 0; r < cd; r++) {
         double acc = 0.0;
-        for (int e = 0; e < 3; e++) acc += Ba[e * 6 + r] * Ng[e];
-        y[6 * loc[a] + r] += acc;
+        for (int e = 0; e < 3; e++) acc += Ba[e * cd + r] * Ng[e];
+        y[cd * loc[a] + r] += acc;
       }
       for (int b = 0; b < m; b++) {
-        const double *Bb = NXC + 18 * b;
-        double NB[18]; /* Ninv * N_XC,b */
+        const double *Bb = NXC + 3 * cd * b;
+        double NB[24]; /* Ninv * N_XC,b */
         for (int e = 0; e < 3; e++)
-          for (int s = 0; s < 6; s++) {
+          for (int s = 0; s < cd; s++) {
             double acc = 0.0;
-            for (int f = 0; f < 3; f++) acc += Ni[s3(e, f)] * Bb[f * 6 + s];
-            NB[e * 6 + s] = acc;
+            for (int f = 0; f < 3; f++) acc += Ni[s3(e, f)] * Bb[f * cd + s];
+            NB[e * cd + s] = acc;
           }
-        for (int r = 0; r < 6; r++)
-          for (int s = 0; s < 6; s++) {
+        for (int r = 0; r < cd; r++)
+          for (int s = 0; s < cd; s++) {
             double acc = 0.0;
-            for (int e = 0; e < 3; e++) acc += Ba[e * 6 + r] * NB[e * 6 + s];
-            S[(size_t)(6 * loc[a] + r) * n + 6 * loc[b] + s] -= acc;
+            for (int e = 0; e < 3; e++) acc += Ba[e * cd + r] * NB[e * cd + s];
+            S[(size_t)(cd * loc[a] + r) * n + cd * loc[b] + s] -= acc;
           }
       }
     }
   }
   /* camera blocks, damped, and the camera gradient */
   for (int li = 0; li < Ml; li++)
-    for (int r = 0; r < 6; r++) {
-      y[6 * li + r] -= gC[6 * li + r];
-      for (int s = 0; s < 6; s++) {
-        double nv = NCC[36 * li + r * 6 + s];
-        S[(size_t)(6 * li + r) * n + 6 * li + s] += nv + (r == s ? lambda * nv : 0.0);
+    for (int r = 0; r < cd; r++) {
+      y[cd * li + r] -= gC[cd * li + r];
+      for (int s = 0; s < cd; s++) {
+        double nv = NCC[cd * cd * li + r * cd + s];
+        S[(size_t)(cd * li + r) * n + cd * li + s] += nv + (r == s ? lambda * nv : 0.0);
       }
     }
   free(NCC); free(gC); free(NXC); free(loc);
@@ -861,9 +952,10 @@ int orc_rcs(const orc_ctx *c, int l, double lambda, double *S, double *y) {
 
 int orc_lm_step(orc_ctx *c, int l, double lambda, double *F_before, double *F_trial,
                 double *dc_out, double *dx_out) {
+  const int cd = c->cd;
   int c0 = c->sub_cam_ptr[l], Ml = c->sub_cam_ptr[l + 1] - c0;
   int q0 = c->sub_inst_ptr[l], nP = c->sub_inst_ptr[l + 1] - q0;
-  int n = 6 * Ml;
+  int n = cd * Ml;
   double F0 = orc_sub_cost(c, l);
   if (F_before) *F_before = F0;
   if (F_trial) *F_trial = F0;
@@ -878,7 +970,7 @@ int orc_lm_step(orc_ctx *c, int l, double lambda, double *F_before, double *F_tr
   if (cholesky(S, n)) {
     cholesky_solve(S, n, y); /* y now holds the camera update d_C */
     /* back-substitution: dX = Ninv (-g_X - sum_k N_XC,k dC_i(k)) */
-    double v[2], Jc[12], Jx[6];
+    double v[2], Jc[16], Jx[6];
     for (int q = q0; q < q0 + nP; q++) {
       int j = c->inst_pt[q];
       if (!c->active[j]) continue;
@@ -888,11 +980,11 @@ int orc_lm_step(orc_ctx *c, int l, double lambda, double *F_before, double *F_tr
         int k = c->inst_obs[p];
         int li = c->cam_local[c->obs_cam[k]];
         obs_residual(c, k, c->R, c->t, c->Xl + 3 * q, v, Jc, Jx);
-        double B[18];
+        double B[24];
         memset(B, 0, sizeof(B));
-        add_AtWB(Jx, 3, Jc, 6, c->obs_winv + 3 * k, c->w[k], B);
+        add_AtWB(Jx, 3, Jc, cd, c->obs_winv + 3 * k, c->w[k], B);
         for (int e = 0; e < 3; e++)
-          for (int s = 0; s < 6; s++) rhs[e] -= B[e * 6 + s] * y[6 * li + s];
+          for (int s = 0; s < cd; s++) rhs[e] -= B[e * cd + s] * y[cd * li + s];
       }
       sym3_mul_vec(Ninv + 6 * (q - q0), rhs, dx + 3 * (q - q0));
     }
@@ -901,22 +993,30 @@ int orc_lm_step(orc_ctx *c, int l, double lambda, double *F_before, double *F_tr
      * their steps on separate threads */
     double *Rt = (double *)malloc(sizeof(double) * 9 * c->M);
     double *tt = (double *)malloc(sizeof(double) * 3 * c->M);
+    double *it = (double *)malloc(sizeof(double) * 3 * c->M);
+    double *kt = (double *)malloc(sizeof(double) * (c->M > 0 ? c->M : 1));
     double *Xt = (double *)malloc(sizeof(double) * 3 * (size_t)(c->P > 0 ? c->P : 1));
     for (int li = 0; li < Ml; li++) {
       int i = c->sub_cam[c0 + li];
       double dR[9];
-      orc_rodrigues(y + 6 * li, dR);
+      orc_rodrigues(y + cd * li, dR);
       for (int r = 0; r < 3; r++)
         for (int s = 0; s < 3; s++) {
           double acc = 0.0;
           for (int m = 0; m < 3; m++) acc += dR[r * 3 + m] * c->R[9 * i + m * 3 + s];
           Rt[9 * i + r * 3 + s] = acc;
         }
-      for (int e = 0; e < 3; e++) tt[3 * i + e] = c->t[3 * i + e] + y[6 * li + 3 + e];
+      for (int e = 0; e < 3; e++) tt[3 * i + e] = c->t[3 * i + e] + y[cd * li + 3 + e];
+      for (int e = 0; e < 3; e++) it[3 * i + e] = c->intr[3 * i + e];
+      kt[i] = c->k1[i];
+      if (cd == 8) {
+        it[3 * i] += y[cd * li + 6];
+        kt[i] += y[cd * li + 7];
+      }
     }
     for (int q = q0; q < q0 + nP; q++)
       for (int e = 0; e < 3; e++) Xt[3 * q + e] = c->Xl[3 * q + e] + dx[3 * (q - q0) + e];
-    double F1 = sub_cost_at(c, l, Rt, tt, Xt);
+    double F1 = sub_cost_at(c, l, Rt, tt, it, kt, Xt);
     if (F_trial) *F_trial = F1;
     if (dc_out) memcpy(dc_out, y, sizeof(double) * n);
     if (dx_out) memcpy(dx_out, dx, sizeof(double) * 3 * nP);
@@ -925,13 +1025,15 @@ int orc_lm_step(orc_ctx *c, int l, double lambda, double *F_before, double *F_tr
         int i = c->sub_cam[c0 + li];
         memcpy(c->R + 9 * i, Rt + 9 * i, sizeof(double) * 9);
         memcpy(c->t + 3 * i, tt + 3 * i, sizeof(double) * 3);
+        c->intr[3 * i] = it[3 * i];
+        c->k1[i] = kt[i];
       }
       memcpy(c->Xl + 3 * (size_t)q0, Xt + 3 * (size_t)q0, sizeof(double) * 3 * nP);
       result = 1;
     } else {
       result = 0;
     }
-    free(Rt); free(tt); free(Xt);
+    free(Rt); free(tt); free(it); free(kt); free(Xt);
   }
   free(S); free(y); free(Ninv); free(gX); free(dx);
   return result;

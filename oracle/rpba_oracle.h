@@ -25,6 +25,7 @@
  *   sym3    : 6 doubles (a00, a01, a02, a11, a12, a22)
  *   winv    : (w11, w12, w22) of C_k^-1 per observation (NULL = identity)
  *   Jc      : 2x6 row-major d(u,v)/d(dw, dt), dw a left-multiplied incremental rotation
+ *             (2x8 with per-camera intrinsics: (dw, dt, df, dk1))
  *   Jx      : 2x3 row-major d(u,v)/dX
  *   instance: a (point j, sub-block l) pair for every sub-block l whose cameras
  *             observe j, in canonical order sorted by (l, j). A tie point (TP) is
@@ -114,6 +115,20 @@ void orc_rotation_log(const double R[9], double w[3]);
 double orc_project(const double R[9], const double t[3], const double intr[3],
                    const double X[3], double uv[2], double Jc[12], double Jx[6]);
 
+/* the same with the first radial distortion parameter k1 (Sec. 6, the Final
+ * data sets): p = (x_c, y_c)/z_c, (u, v) = f (1 + k1 |p|^2) p + (cx, cy);
+ * Jc is 2x8 row-major d(u,v)/d(dw, dt, df, dk1) */
+double orc_project_k1(const double R[9], const double t[3], const double intr[3], double k1,
+                      const double X[3], double uv[2], double Jc[16], double Jx[6]);
+
+/* per-camera intrinsics: from this call on, f and k1 of every camera are
+ * unknowns (8 per camera) and the projection includes k1 (initial values k1,
+ * or 0 when NULL) */
+void orc_enable_intrinsics(orc_ctx *c, const double *k1);
+int orc_camera_dim(const orc_ctx *c); /* 6, or 8 with intrinsics */
+void orc_get_intrinsics(const orc_ctx *c, double *fk); /* (f, k1) per camera */
+void orc_set_intrinsics(orc_ctx *c, const double *fk);
+
 /* evaluations at the global state (cameras, points X) */
 void orc_residuals(const orc_ctx *c, double *v);
 void orc_jacobians(const orc_ctx *c, double *Jc, double *Jx);
@@ -139,7 +154,8 @@ int orc_intersect_points(orc_ctx *c, const orc_options *o, const int *ids, int n
 /* sub-block l: cost F_l (Eq. bact) at the current sub-block state */
 double orc_sub_cost(const orc_ctx *c, int l);
 /* damped reduced camera system of sub-block l at the current state;
- * S is n x n row-major (n = 6 * cameras in l), y has n entries. Returns n. */
+ * S is n x n row-major (n = 6 * cameras in l, 8 * with intrinsics), y has n
+ * entries. Returns n. */
 int orc_rcs(const orc_ctx *c, int l, double lambda, double *S, double *y);
 /* one LM iteration of sub-block l with damping lambda: solve, trial, accept if
  * the cost decreases. Returns 1 accepted, 0 rejected, -1 solve failed.

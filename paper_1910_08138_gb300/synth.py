@@ -317,6 +317,97 @@ def tiny(seed=0, nx=3, ny=2, n_points=30, opp=4, runs=None, sigma_px=0.5, outlie
                       runs=runs, rot_sigma=rot_sigma, pos_sigma=pos_sigma, pt_sigma=pt_sigma)
 
 
+# --------------------------------------------------------------------------
+# photo-collection blocks with per-camera intrinsics (the Final data sets of
+# Sec. 6: focal length and first radial parameter estimated per camera)
+# --------------------------------------------------------------------------
+def _image_radial(R, t, f, k1, X):
+    """Imaging with a radial polynomial on the normalised coordinates:
+    p = (x_c, y_c)/z_c, (u, v) = f (1 + k1 |p|^2) p + (CX, CY)."""
+    xc = np.einsum("nab,nb->na", R, X) + t
+    z = xc[:, 2]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        p = xc[:, :2] / z[:, None]
+    d = 1.0 + k1 * np.sum(p * p, axis=1)
+    uv = (f * d)[:, None] * p + np.array([CX, CY])
+    return uv, z
+
+
+def ring_block(rng, n_cams, n_points, mean_track, n_sub, sigma_px=1.0, outlier_frac=0.02,
+               radius=9.0, f_range=(850.0, 1250.0), k1_range=(-0.08, 0.08), f_sigma_rel=0.01,
+               rot_sigma=0.002, pos_sigma=0.03, pt_sigma=0.03):
+    """Cameras on a ring around an object, each with its own focal length and
+    radial parameter; points on the object, each seen by a random subset of
+    the cameras facing its side (track lengths 2 + geometric, mean
+    `mean_track`); sub-blocks are contiguous arcs of the ring. The initial
+    values perturb the poses and points and the focal lengths (relative
+    sigma `f_sigma_rel`) and start every k1 at 0."""
+    M = n_cams
+    az = 2.0 * np.pi * (np.arange(M) + rng.uniform(-0.3, 0.3, M)) / M
+    centers = np.stack([radius * np.cos(az), radius * np.sin(az), rng.uniform(1.0, 4.0, M)], axis=1)
+    target = np.array([0.0, 0.0, 2.5]) + rng.normal(0.0, 0.3, (M, 3))
+    c2w = np.empty((M, 3, 3))
+    for i in range(M):
+        zc = target[i] - centers[i]
+        zc /= np.linalg.norm(zc)
+        xc = np.cross(zc, np.array([0.0, 0.0, 1.0]))
+        xc /= np.linalg.norm(xc)
+        yc = np.cross(zc, xc)
+        roll = Rotation.from_rotvec(zc * rng.normal(0.0, 0.05)).as_matrix()
+        c2w[i] = roll @ np.stack([xc, yc, zc], axis=1)
+    R, t = _rig(centers, c2w)
+    f = rng.uniform(*f_range, M)
+    k1 = rng.uniform(*k1_range, M)
+    # points on the object (a cylinder of radius 4.5, 0..5 high), each facing outward
+    n_try = int(n_points * 1.2) + 16
+    paz = rng.uniform(0.0, 2.0 * np.pi, n_try)
+    pr = 4.5 * np.sqrt(rng.uniform(0.3, 1.0, n_try))
+    X = np.stack([pr * np.cos(paz), pr * np.sin(paz), rng.uniform(0.0, 5.0, n_try)], axis=1)
+    want = 2 + rng.geometric(1.0 / max(mean_track - 1.0, 1.0), n_try) - 1
+    half = int(M * 65 / 360)  # cameras within 65 degrees of the point's side
+    centre_cam = np.round(paz / (2.0 * np.pi) * M).astype(np.int64)
+    oc, op, ouv = [], [], []
+    for j in range(n_try):
+        cand = (centre_cam[j] + np.arange(-half, half + 1)) % M
+        take = rng.permutation(cand)[:min(int(want[j]), cand.size)]
+        uv, z = _image_radial(R[take], t[take], f[take], k1[take], np.repeat(X[j][None], take.size, 0))
+        ok = (z > 0.5) & (uv[:, 0] >= 0) & (uv[:, 0] < IMG_W) & (uv[:, 1] >= 0) & (uv[:, 1] < IMG_H)
+        if ok.sum() >= 2:
+            oc.append(take[ok])
+            op.append(np.full(int(ok.sum()), j))
+            ouv.append(uv[ok])
+    oc, op, ouv = np.concatenate(oc).astype(np.int32), np.concatenate(op), np.concatenate(ouv)
+    blk = _finish_block(rng, R, t, centers, X, oc, op, ouv, sigma_px, outlier_frac,
+                        rot_sigma, pos_sigma, pt_sigma, n_points=n_points)
+    f0 = f * (1.0 + rng.normal(0.0, f_sigma_rel, M))
+    blk["cam_intr"] = np.stack([f0, np.full(M, CX), np.full(M, CY)], axis=1)
+    blk["cam_k1"] = np.zeros(M)
+    blk["intrinsics"] = True
+    blk["gt_cam_intr"] = np.stack([f, np.full(M, CX), np.full(M, CY)], axis=1)
+    blk["gt_cam_k1"] = k1
+    blk["cam_subblock"] = (np.arange(M) * n_sub // M).astype(np.int32)
+    blk["cam_block"] = np.zeros(M, dtype=np.int32)
+    return blk
+
+
+def bal_config(scale: float = 1.0):
+    """Stand-in for the Final 961 data set of Sec. 6 (Table datasets: 961
+    cameras, 187,103 points, 3,385,950 observations, focal length and k1 per
+    camera): a seeded ring block of the same size, 18 observations per point
+    on average, 12 sub-blocks of about 80 cameras (the paper's minimum is 70),
+    sigma 1 px, 2 % outliers."""
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 961))
+    return ring_block(rng, 961, int(187_103 * scale), 18.1, 12)
+
+
+def tiny_intrinsics(seed=0, n_cams=24, n_points=300, mean_track=6.0, n_sub=3, sigma_px=0.5,
+                    outlier_frac=0.0, **kw):
+    """A small ring block with per-camera intrinsics for brute-force checks."""
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 29 + seed))
+    return ring_block(rng, n_cams, n_points, mean_track, n_sub, sigma_px=sigma_px,
+                      outlier_frac=outlier_frac, **kw)
+
+
 PROBLEM_KEYS = ("cam_pose", "cam_intr", "points", "obs_cam", "obs_point", "obs_xy",
                 "obs_winv", "cam_subblock", "cam_block")
 
