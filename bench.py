@@ -44,6 +44,8 @@ WORKLOADS = {
     3: "rpba-64blocks-7748cam-222kpt-1.0Mobs-304sub (20..400 cams/block, 2..8 sub-blocks, 0.5px, 2% outliers)",
     4: "rpba-5000cam-1Mpt-3.4Mobs-32sub (50x100 strips, 60% forward / 30% side overlap, 0.5px, 5% outliers)",
     5: "rpba-10000cam-4Mpt-20Mobs-64sub (100x100 grid, nadir+45deg oblique wide baseline, 1px, 5% outliers)",
+    6: "rpba-961cam-187kpt-3.4Mobs-12sub-intrinsics (ring around an object, focal length and k1 per camera, "
+       "18 obs/point, 1px, 2% outliers; stand-in for Final 961)",
 }
 DEFAULT_CONFIG = 5
 TARGETS = os.path.join(ROOT, "tests", "golden", "oracle_targets.json")
@@ -191,12 +193,12 @@ def obs_stream_bytes(has_winv):
     return 28 + (12 if has_winv else 0)
 
 
-def kernel_models(K, N, P, M, has_winv, pairs, tps=None):
+def kernel_models(K, N, P, M, has_winv, pairs, tps=None, cd=6):
     """Algorithmic bytes (HBM-bound kernels) or flops (ALU-bound) of one launch
     of each FP32-form kernel of the step, from the data it must read and write
-    once: K observations, N points, P instances, M cameras. Camera records are
-    128 B each. Lower bounds: a kernel that gathers the same word twice is
-    charged once."""
+    once: K observations, N points, P instances, M cameras with cd unknowns
+    each (6, or 8 with per-camera intrinsics). Camera records are 128 B each.
+    Lower bounds: a kernel that gathers the same word twice is charged once."""
     ob = obs_stream_bytes(has_winv)
     return {
         "k_obs_sigma_f": ("hbm", K * ob + N * 25 + M * 128),
@@ -206,11 +208,11 @@ def kernel_models(K, N, P, M, has_winv, pairs, tps=None):
         # the TP intersection: the tie points' observations, positions and instances
         "k_isect_fused_f": ("hbm", (tps[1] * ob + tps[0] * 48 + tps[2] * 24 if tps else K * ob + N * 48 + P * 24)
                             + M * 128),
-        "k_camera_blocks_f32": ("hbm", K * ob + P * 60 + M * (128 + 432)),
+        "k_camera_blocks_f32": ("hbm", K * ob + P * 60 + M * (128 + 12 * cd * cd)),
         "k_linearize_f32": ("hbm", K * ob + P * 132 + M * 128),
-        "k_backsub_f32": ("hbm", K * ob + P * 72 + M * 152),
-        # 6x6 product N_XC,a^T (Ninv N_XC,b) per point pair, Z = Ninv N_XC once per observation
-        "k_schur_seg": ("alu", 216.0 * pairs + 108.0 * K),
+        "k_backsub_f32": ("hbm", K * ob + P * 72 + M * (128 + 4 * cd)),
+        # cd x cd product N_XC,a^T (Ninv N_XC,b) per point pair, Z = Ninv N_XC once per observation
+        "k_schur_seg": ("alu", 6.0 * cd * cd * pairs + 18.0 * cd * K),
     }
 
 
@@ -467,7 +469,8 @@ def run_ours(args, rank, world):
     # rooflines: the dominant kernel over the timed region; the other hot
     # kernels from the fully event-timed last warm-up step
     has_winv = prob.get("obs_winv") is not None
-    models = (kernel_models(K, ctx.N, ctx.P, ctx.M, has_winv, schur_pairs(prob), tie_point_counts(prob, act0))
+    models = (kernel_models(K, ctx.N, ctx.P, ctx.M, has_winv, schur_pairs(prob), tie_point_counts(prob, act0),
+                            cd=ctx.cd)
               if args.precision == 1 else {})
     sbytes, live_tiles = symv_work(ctx, pcg_iters, n_sub) if pcg_iters else (None, None)
     if sbytes is not None:

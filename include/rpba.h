@@ -69,6 +69,8 @@ typedef struct {
   const double *obs_winv;
   const int32_t *cam_subblock;
   const int32_t *cam_block;
+  const double *cam_k1;  /* n_cams initial radial parameters, read with options.intrinsics = 1
+                            (NULL: 0) */
 } rpba_problem;
 
 /* solver 4 (auto) starts with block-Jacobi PCG for at most this many
@@ -127,6 +129,13 @@ typedef struct {
                             2 one persistent launch over every step of every sub-block or 1
                             one launch per step. Same results to rounding; rpba_tune picks
                             the fastest for a workload */
+  int32_t intrinsics;    /* 1: per-camera intrinsics as in the Final data sets of Sec. 6: the
+                            focal length f (cam_intr[0]) and the first radial parameter k1
+                            (cam_k1) of every camera are estimated with its pose, 8 unknowns
+                            per camera; the projection applies 1 + k1 |p|^2 to the normalised
+                            coordinates p = (x_c, y_c)/z_c; the principal point stays fixed.
+                            Solvers 0 and 2 (4 resolves to 2); 1 and 3 give INVALID_ARG.
+                            0 (default): intrinsics known, pinhole, 6 unknowns per camera */
   const char *tune_cache; /* NULL, or a file of tuned launch shapes (JSON lines, one object per
                             workload: cameras, points, observations, sub-blocks, precision,
                             solver and SM count): the entry of this workload, if any, is
@@ -239,6 +248,12 @@ rpba_status rpba_set_cameras(rpba_ctx *ctx, const double *pose);
 rpba_status rpba_get_camera_rt(rpba_ctx *ctx, double *R, double *t);
 rpba_status rpba_set_camera_rt(rpba_ctx *ctx, const double *R, const double *t);
 rpba_status rpba_set_points(rpba_ctx *ctx, const double *X, const uint8_t *active /* nullable */);
+/* per-camera intrinsics (options.intrinsics = 1): fk is n_cams x 2, the focal
+ * length and the radial parameter k1 of every camera (Sec. 6, Final data
+ * sets), host buffer. Without intrinsics get returns (f, 0) and set accepts
+ * only (f, 0) with the creation's f: anything else gives INVALID_ARG. */
+rpba_status rpba_get_intrinsics(rpba_ctx *ctx, double *fk);
+rpba_status rpba_set_intrinsics(rpba_ctx *ctx, const double *fk);
 /* instances sorted by (sub-block, point): point id, sub-block id, X^l (P x 3),
  * W^l (P x 6 sym3); any output may be NULL */
 rpba_status rpba_get_instances(rpba_ctx *ctx, int32_t *inst_point, int32_t *inst_sub, double *Xl,
@@ -249,7 +264,8 @@ rpba_status rpba_get_weights(rpba_ctx *ctx, double *w);
 rpba_status rpba_set_weights(rpba_ctx *ctx, const double *w);
 /* v_k = g_k(P_i, X_j) - x_k at the global state (Sec. 2), n_obs x 2 */
 rpba_status rpba_residuals(rpba_ctx *ctx, double *v);
-/* Jc (n_obs x 2 x 6, d/d(dw, dt), dw left-multiplied) and Jx (n_obs x 2 x 3) (Eq. ta) */
+/* Jc (n_obs x 2 x 6, d/d(dw, dt), dw left-multiplied; n_obs x 2 x 8 with
+ * intrinsics, d/d(dw, dt, df, dk1)) and Jx (n_obs x 2 x 3) (Eq. ta) */
 rpba_status rpba_jacobians(rpba_ctx *ctx, double *Jc, double *Jx);
 /* sigma_0 (Eq. sigma0) and RMS at the global state */
 rpba_status rpba_sigma0(rpba_ctx *ctx, double *sigma0, double *rms);
@@ -262,12 +278,13 @@ rpba_status rpba_intersect_points(rpba_ctx *ctx, int32_t tp_only, int32_t *n_dro
 /* F_l of every sub-block at the current state (Eq. bact), n_subblocks values */
 rpba_status rpba_sub_costs(rpba_ctx *ctx, double *F);
 /* damped RCS of sub-block l (Sec. 2, 5.5): S (n x n, lower triangle valid,
- * n = 6 x cameras of l) and y (n), at the current state */
+ * n = 6 x cameras of l, 8 x with intrinsics) and y (n), at the current state */
 rpba_status rpba_rcs(rpba_ctx *ctx, int32_t l, double lambda, double *S, double *y);
 /* one LM step of every sub-block with damping lambda: solve, trial, accept
  * if F_l decreases. Outputs per sub-block (nullable): accepted (1/0/-1 solve
  * failed), F before, F of the trial; dc = camera updates in RCS order of all
- * sub-blocks concatenated (6 x n_cams), dx = instance updates (P x 3). */
+ * sub-blocks concatenated (6 x n_cams, 8 x with intrinsics), dx = instance
+ * updates (P x 3). */
 rpba_status rpba_lm_step(rpba_ctx *ctx, double lambda, int32_t *accepted, double *F_before,
                          double *F_trial, double *dc, double *dx);
 /* the LM adjustment of every sub-block to its own stop (Eq. bact, with the

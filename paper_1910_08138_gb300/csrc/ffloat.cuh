@@ -141,19 +141,21 @@ __host__ __device__ __forceinline__ void ff_split(double x, float &hi, float &lo
 // Camera record of the FP32 form, FF_CAM floats (128 bytes, read as float4):
 //   [0, 9) R hi (row-major)   [9, 12) centre C = -R^T t hi   [12, 15) C lo
 //   [15] f hi                 [16, 25) R lo                   [25] f lo
-//   [26, 29) zero             [29, 32) t rounded to FP32
-// The FP32 projection and Jacobians read floats [0, 16) and [28, 32); the
-// float-float residual reads [0, 28).
+//   [26] k1 hi  [27] k1 lo    [28] zero                       [29, 32) t rounded to FP32
+// (k1: the first radial parameter of per-camera intrinsics, 0 without.)
+// The FP32 projection and Jacobians read floats [0, 16), [24, 28) for k1 and
+// [28, 32); the float-float residual reads [0, 28).
 #define FF_CAM 32
 
-__host__ __device__ inline void ff_camera_record(const double *R, const double *t, double f, float *o) {
+__host__ __device__ inline void ff_camera_record(const double *R, const double *t, double f, double k1, float *o) {
   for (int e = 0; e < 9; e++) ff_split(R[e], o[e], o[16 + e]);
   for (int c = 0; c < 3; c++) {
     double C = -(R[c] * t[0] + R[3 + c] * t[1] + R[6 + c] * t[2]);
     ff_split(C, o[9 + c], o[12 + c]);
   }
   ff_split(f, o[15], o[25]);
-  for (int e = 26; e < 29; e++) o[e] = 0.f;
+  ff_split(k1, o[26], o[27]);
+  o[28] = 0.f;
   for (int e = 0; e < 3; e++) o[29 + e] = (float)t[e];
 }
 
@@ -174,9 +176,11 @@ __device__ __forceinline__ void ff_load_record(const float *cf, float (&c)[4 * N
 // division with one remainder correction, f times the quotient, and the
 // subtraction of the observation, whose leading parts cancel exactly. The
 // residual is returned in FP32 (it is small: its leading bits are exact).
-// Returns z_c > 0; the residual is computed either way, as in FP64.
+// Returns z_c > 0; the residual is computed either way, as in FP64. With
+// k1on (per-camera intrinsics) f is replaced by f (1 + k1 |q|^2), q the
+// normalised coordinates, all in float-float.
 __device__ __forceinline__ bool ff_residual(const float *cf, const float *Xh, const float *Xl, float oxh, float oxl,
-                                            float oyh, float oyl, float &r0, float &r1) {
+                                            float oyh, float oyl, float &r0, float &r1, bool k1on = false) {
   float c[28];
   ff_load_record<7>(cf, c);
   float dh[3], dl[3];
@@ -195,6 +199,25 @@ __device__ __forceinline__ bool ff_residual(const float *cf, const float *Xh, co
   float qx = ff_div(xh, xl, zh, zl, rz, qxl);
   float qy = ff_div(yh, yl, zh, zl, rz, qyl);
   float fh = c[15], fl = c[25];
+  if (k1on) {
+    // f (1 + k1 |q|^2) in float-float: |q|^2 from the quotients and their
+    // remainders, then k1 |q|^2, 1 + that, and the product with f
+    float e1, e2, e3, te, se, ge;
+    float r2h = ff_two_prod(qx, qx, e1);
+    e1 = __fmaf_rn(2.f * qx, qxl, e1);
+    float r2b = ff_two_prod(qy, qy, e2);
+    e2 = __fmaf_rn(2.f * qy, qyl, e2);
+    r2h = ff_two_sum(r2h, r2b, e3);
+    float r2l = __fadd_rn(__fadd_rn(e1, e2), e3);
+    float kh = c[26], kl = c[27];
+    float th = ff_two_prod(kh, r2h, te);
+    te = __fmaf_rn(kl, r2h, __fmaf_rn(kh, r2l, te));
+    float sh = ff_two_sum(1.f, th, se);
+    float sl = __fadd_rn(se, te);
+    float gh = ff_two_prod(fh, sh, ge);
+    ge = __fmaf_rn(fl, sh, __fmaf_rn(fh, sl, ge));
+    fh = ff_two_sum(gh, ge, fl);
+  }
   float ue, ve;
   float uh = ff_two_prod(fh, qx, ue);
   ue = __fmaf_rn(fl, qx, __fmaf_rn(fh, qxl, ue));

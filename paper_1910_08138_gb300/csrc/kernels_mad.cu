@@ -228,9 +228,10 @@ __device__ static float2 radix_median(const unsigned *a, int n, SelScratch &S) {
 struct MadIn {
   const double *R, *t, *intr, *X, *obs_xy, *whiten;
   const float *camff, *Xh, *Xl, *oxy, *oxylo, *whiten32;
+  const double *k1;  // per-camera radial parameter (NULL without intrinsics)
 };
 
-template <typename Key>
+template <typename Key, bool K1>
 __global__ void k_camera_mad(int M, MadIn in, const uint8_t *active, const int *cam_obs_ptr, const int *cam_obs,
                              const int *obs_pt, int has_winv, double *sigma, float *sigma32) {
   extern __shared__ __align__(16) unsigned char sh_raw[];
@@ -249,7 +250,7 @@ __global__ void k_camera_mad(int M, MadIn in, const uint8_t *active, const int *
     if constexpr (sizeof(Key) == 4) {  // keys straight from the FP32 components
       float r0, r1;
       ff_residual(in.camff + FF_CAM * (size_t)i, in.Xh + 3 * (size_t)j, in.Xl + 3 * (size_t)j, in.oxy[2 * k],
-                  in.oxylo[2 * k], in.oxy[2 * k + 1], in.oxylo[2 * k + 1], r0, r1);
+                  in.oxylo[2 * k], in.oxy[2 * k + 1], in.oxylo[2 * k + 1], r0, r1, K1);
       if (has_winv) {
         const float *F = in.whiten32 + 3 * (size_t)k;
         float a = F[0] * r0 + F[1] * r1, b = F[2] * r1;
@@ -259,13 +260,11 @@ __global__ void k_camera_mad(int M, MadIn in, const uint8_t *active, const int *
       k0 = fkey(r0);
       k1 = fkey(r1);
     } else {
-      const double *Ri = in.R + 9 * i, *ti = in.t + 3 * i, *Xj = in.X + 3 * j;
-      double f = in.intr[3 * i], cx = in.intr[3 * i + 1], cy = in.intr[3 * i + 2];
-      double Xc[3];
-      for (int r = 0; r < 3; r++) Xc[r] = Ri[3 * r] * Xj[0] + Ri[3 * r + 1] * Xj[1] + Ri[3 * r + 2] * Xj[2] + ti[r];
-      double iz = 1.0 / Xc[2];
-      double r0 = f * Xc[0] * iz + cx - in.obs_xy[2 * k];
-      double r1 = f * Xc[1] * iz + cy - in.obs_xy[2 * k + 1];
+      double pu, pv;
+      proj64(in.R + 9 * i, in.t + 3 * i, in.intr[3 * i], in.k1 ? in.k1[i] : 0.0, in.intr[3 * i + 1],
+             in.intr[3 * i + 2], in.X + 3 * j, pu, pv);
+      double r0 = pu - in.obs_xy[2 * k];
+      double r1 = pv - in.obs_xy[2 * k + 1];
       double e0 = r0, e1 = r1;
       if (has_winv) {  // upper Cholesky factor of C^-1, precomputed: (sqrt(w11), w12/sqrt(w11), sqrt(w22 - w12^2/w11))
         const double *F = in.whiten + 3 * k;
@@ -346,22 +345,24 @@ rpba_status launch_camera_scale(Ctx *ctx) {
     return RPBA_ERR_INVALID_ARG;
   }
   MadIn in{ctx->R, ctx->t, ctx->intr, ctx->X, ctx->obs_xy, ctx->obs_whiten,
-           ctx->camff, ctx->X_hi, ctx->X_lo, ctx->obs_xy32, ctx->obs_xylo, ctx->obs_whiten32};
+           ctx->camff, ctx->X_hi, ctx->X_lo, ctx->obs_xy32, ctx->obs_xylo, ctx->obs_whiten32,
+           ctx->cd == 8 ? ctx->k1 : nullptr};
   int threads = std::min(1024, std::max(32, n2 / 2));  // one thread per compare-exchange of a pass
   if (f32) {
     // two observations per thread (up to 1024 threads): the residual phase is
     // a chain of dependent gathers, so it wants many threads in flight
     threads = std::min(1024, std::max(64, 32 * ((ctx->max_cam_obs + 63) / 64)));  // two observations per thread
+    auto kern = ctx->cd == 8 ? k_camera_mad<unsigned, true> : k_camera_mad<unsigned, false>;
     if (smem > 48 * 1024)
-      RPBA_CUDA(cudaFuncSetAttribute(k_camera_mad<unsigned>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    RPBA_KERNEL(ctx, "k_camera_mad_u32", k_camera_mad<unsigned><<<ctx->M, threads, smem, ctx->stream>>>(
+      RPBA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RPBA_KERNEL(ctx, "k_camera_mad_u32", kern<<<ctx->M, threads, smem, ctx->stream>>>(
                                          ctx->M, in, ctx->active, ctx->cam_obs_ptr, ctx->cam_obs, ctx->obs_pt,
                                          ctx->has_winv, ctx->cam_sigma, ctx->cam_sigma32));
   } else {
+    auto kern = k_camera_mad<unsigned long long, false>;  // the FP64 path reads k1 from in.k1
     if (smem > 48 * 1024)
-      RPBA_CUDA(cudaFuncSetAttribute(k_camera_mad<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-    RPBA_KERNEL(ctx, "k_camera_mad_u64", k_camera_mad<unsigned long long><<<ctx->M, threads, smem, ctx->stream>>>(
+      RPBA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RPBA_KERNEL(ctx, "k_camera_mad_u64", kern<<<ctx->M, threads, smem, ctx->stream>>>(
                                          ctx->M, in, ctx->active, ctx->cam_obs_ptr, ctx->cam_obs, ctx->obs_pt,
                                          ctx->has_winv, ctx->cam_sigma, nullptr));
   }

@@ -27,8 +27,13 @@ namespace rpba {
 // ---------------------------------------------------------------------------
 struct View {
   int M, N, K, L, P, has_winv;
-  const double *R, *t, *intr;
+  const double *R, *t;
+  double *intr;
   double *Rt, *tt;
+  // per-camera intrinsics: cd = 8 camera unknowns, k1 (NULL without), trial
+  // f and k1; k1on: the projections include the radial term
+  int cd, k1on;
+  double *k1, *ft, *k1t;
   const int *cam_sub, *cam_local, *sub_cam_ptr, *sub_cam, *cam_obs_ptr, *cam_obs;
   double *X;
   uint8_t *active;
@@ -88,6 +93,7 @@ static View make_view(Ctx *c) {
   v.Xlt_hi = c->Xlt_hi; v.Xlt_lo = c->Xlt_lo; v.Wl32 = c->Wl32;
   v.wmode = c->opt.weight_mode;
   v.wrho = c->wrho;
+  v.cd = c->cd; v.k1on = c->cd == 8; v.k1 = c->k1; v.ft = c->ft; v.k1t = c->k1t;
   return v;
 }
 
@@ -112,7 +118,7 @@ static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 // FP32 rate, so the FP32 form rounds every input once per pass instead.
 template <typename T>
 struct CamPt {
-  T R[9], Xc[3], RX[3], f, cx, cy;
+  T R[9], Xc[3], RX[3], f, k1, cx, cy;
 };
 
 __device__ inline void cam_point_d(const View &v, int i, const double X[3], CamPt<double> &o) {
@@ -124,6 +130,7 @@ __device__ inline void cam_point_d(const View &v, int i, const double X[3], CamP
   }
   for (int e = 0; e < 9; e++) o.R[e] = R[e];
   o.f = v.intr[3 * i]; o.cx = v.intr[3 * i + 1]; o.cy = v.intr[3 * i + 2];
+  o.k1 = v.k1 ? v.k1[i] : 0.0;
 }
 
 __device__ inline void cam_point_f(const View &v, int i, const float *Xh, const float *Xlw, CamPt<float> &o) {
@@ -144,6 +151,7 @@ __device__ inline void cam_point_f(const View &v, int i, const float *Xh, const 
     o.RX[r] = o.Xc[r] - t[r];
   }
   o.f = c[15]; o.cx = 0.f; o.cy = 0.f;
+  o.k1 = v.k1on ? __ldg(p + 6).z : 0.f;  // record float 26
 }
 
 __device__ inline void split(double x, float &hi, float &lo) {
@@ -155,7 +163,7 @@ __device__ inline void split(double x, float &hi, float &lo) {
 __global__ void k_cam_prep(View v) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= v.M) return;
-  ff_camera_record(v.R + 9 * i, v.t + 3 * i, v.intr[3 * i], v.camff + FF_CAM * (size_t)i);
+  ff_camera_record(v.R + 9 * i, v.t + 3 * i, v.intr[3 * i], v.k1 ? v.k1[i] : 0.0, v.camff + FF_CAM * (size_t)i);
 }
 
 // hi/lo pairs of the sub-block copies (which = 0) or of the points (which = 1)
@@ -218,15 +226,39 @@ __device__ inline void load_obs(const View &v, int k, ObsT<T> &o) {
 }
 
 // projection (relative to the principal point) and Jacobians of camera i at
-// a point given in FP64 (Xd) or as FP32 hi/lo pairs (Xh, Xlw)
-template <typename T>
+// a point given in FP64 (Xd) or as FP32 hi/lo pairs (Xh, Xlw); CD = 8 with
+// per-camera intrinsics (camera Jacobian 2 x 8), else 6
+template <typename T, int CD>
 __device__ inline void obs_proj(const View &v, int i, const double *Xd, const float *Xh, const float *Xlw,
-                                ProjJac<T> &pj, T &z) {
+                                ProjJac<T, CD> &pj, T &z) {
   CamPt<T> cp;
   if constexpr (sizeof(T) == sizeof(float)) cam_point_f(v, i, Xh, Xlw, cp);
   else cam_point_d(v, i, Xd, cp);
   z = cp.Xc[2];
-  project_jac<T>(cp.R, cp.Xc, cp.RX, cp.f, T(0), T(0), pj);
+  project_jac<T, CD>(cp.R, cp.Xc, cp.RX, cp.f, cp.k1, T(0), T(0), pj);
+}
+
+// the projection and the point Jacobian only (intersection, point blocks),
+// with or without the radial term
+template <typename T>
+struct ProjX {
+  T u, v, Jx[6];
+};
+
+template <typename T>
+__device__ inline void proj_x(const View &v, int i, const double *Xd, const float *Xh, const float *Xlw,
+                              ProjX<T> &o, T &z) {
+  if (v.k1on) {
+    ProjJac<T, 8> pj;
+    obs_proj<T, 8>(v, i, Xd, Xh, Xlw, pj, z);
+    o.u = pj.u; o.v = pj.v;
+    for (int e = 0; e < 6; e++) o.Jx[e] = pj.Jx[e];
+  } else {
+    ProjJac<T, 6> pj;
+    obs_proj<T, 6>(v, i, Xd, Xh, Xlw, pj, z);
+    o.u = pj.u; o.v = pj.v;
+    for (int e = 0; e < 6; e++) o.Jx[e] = pj.Jx[e];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -236,25 +268,24 @@ __global__ void k_residuals(View v, double *out) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= v.K) return;
   int i = v.obs_cam[k], j = v.obs_pt[k];
-  const double *R = v.R + 9 * i, *t = v.t + 3 * i, *X = v.X + 3 * j;
-  double Xc[3];
-  for (int r = 0; r < 3; r++) Xc[r] = R[3 * r] * X[0] + R[3 * r + 1] * X[1] + R[3 * r + 2] * X[2] + t[r];
-  double f = v.intr[3 * i], iz = 1.0 / Xc[2];
+  double pu, pv;
+  proj64(v.R + 9 * i, v.t + 3 * i, v.intr[3 * i], v.k1 ? v.k1[i] : 0.0, v.intr[3 * i + 1], v.intr[3 * i + 2],
+         v.X + 3 * j, pu, pv);
   int u = v.obs_user[k];
-  out[2 * u] = f * Xc[0] * iz + v.intr[3 * i + 1] - v.obs_xy[2 * k];
-  out[2 * u + 1] = f * Xc[1] * iz + v.intr[3 * i + 2] - v.obs_xy[2 * k + 1];
+  out[2 * u] = pu - v.obs_xy[2 * k];
+  out[2 * u + 1] = pv - v.obs_xy[2 * k + 1];
 }
 
-template <typename T>
+template <typename T, int CD>
 __global__ void k_jacobians(View v, double *Jc, double *Jx) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= v.K) return;
   int i = v.obs_cam[k], j = v.obs_pt[k];
-  ProjJac<T> pj;
+  ProjJac<T, CD> pj;
   T z;
-  obs_proj<T>(v, i, v.X + 3 * j, v.X_hi + 3 * j, v.X_lo + 3 * j, pj, z);
+  obs_proj<T, CD>(v, i, v.X + 3 * j, v.X_hi + 3 * j, v.X_lo + 3 * j, pj, z);
   int u = v.obs_user[k];
-  for (int e = 0; e < 12; e++) Jc[12 * u + e] = (double)pj.Jc[e];
+  for (int e = 0; e < 2 * CD; e++) Jc[2 * CD * (size_t)u + e] = (double)pj.Jc[e];
   for (int e = 0; e < 6; e++) Jx[6 * u + e] = (double)pj.Jx[e];
 }
 
@@ -266,10 +297,15 @@ rpba_status launch_residuals(Ctx *ctx, double *v_dev) {
 
 rpba_status launch_jacobians(Ctx *ctx, double *Jc, double *Jx) {
   if (ctx->K == 0) return RPBA_OK;
-  if (ctx->opt.precision == 1)
-    RPBA_KERNEL(ctx, "k_jacobians", k_jacobians<float><<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(make_view(ctx), Jc, Jx));
+  dim3 g(nblk(ctx->K, 256)), b(256);
+  if (ctx->opt.precision == 1 && ctx->cd == 8)
+    RPBA_KERNEL(ctx, "k_jacobians", k_jacobians<float, 8><<<g, b, 0, ctx->stream>>>(make_view(ctx), Jc, Jx));
+  else if (ctx->opt.precision == 1)
+    RPBA_KERNEL(ctx, "k_jacobians", k_jacobians<float, 6><<<g, b, 0, ctx->stream>>>(make_view(ctx), Jc, Jx));
+  else if (ctx->cd == 8)
+    RPBA_KERNEL(ctx, "k_jacobians", k_jacobians<double, 8><<<g, b, 0, ctx->stream>>>(make_view(ctx), Jc, Jx));
   else
-    RPBA_KERNEL(ctx, "k_jacobians", k_jacobians<double><<<nblk(ctx->K, 256), 256, 0, ctx->stream>>>(make_view(ctx), Jc, Jx));
+    RPBA_KERNEL(ctx, "k_jacobians", k_jacobians<double, 6><<<g, b, 0, ctx->stream>>>(make_view(ctx), Jc, Jx));
   return RPBA_OK;
 }
 
@@ -320,12 +356,11 @@ __global__ void k_obs_sigma(View v, double *part) {
     int j = v.obs_pt[k];
     if (!v.active[j]) continue;
     int i = v.obs_cam[k];
-    const double *R = v.R + 9 * i, *t = v.t + 3 * i, *X = v.X + 3 * j;
-    double Xc[3];
-    for (int r = 0; r < 3; r++) Xc[r] = R[3 * r] * X[0] + R[3 * r + 1] * X[1] + R[3 * r + 2] * X[2] + t[r];
-    double f = v.intr[3 * i], iz = 1.0 / Xc[2];
-    double r0 = f * Xc[0] * iz + v.intr[3 * i + 1] - v.obs_xy[2 * k];
-    double r1 = f * Xc[1] * iz + v.intr[3 * i + 2] - v.obs_xy[2 * k + 1];
+    double pu, pv;
+    proj64(v.R + 9 * i, v.t + 3 * i, v.intr[3 * i], v.k1 ? v.k1[i] : 0.0, v.intr[3 * i + 1], v.intr[3 * i + 2],
+           v.X + 3 * j, pu, pv);
+    double r0 = pu - v.obs_xy[2 * k];
+    double r1 = pv - v.obs_xy[2 * k + 1];
     double W0 = 1, W1 = 0, W2 = 1;
     if (v.has_winv) { W0 = v.obs_winv[3 * k]; W1 = v.obs_winv[3 * k + 1]; W2 = v.obs_winv[3 * k + 2]; }
     double w = v.obs_w[k];
@@ -345,12 +380,13 @@ __global__ void k_obs_sigma(View v, double *part) {
 __device__ void sigma_cta_sums(float sh, float sl, float rh, float rl, int n1, int n3, int np, double *o);
 
 // one observation's sigma_0 terms from its float-float residual (FP32 form)
+template <bool K1>
 __device__ inline void sigma_obs_terms(const View &v, int k, int i, int j, float &sh, float &sl, float &rh,
                                        float &rl, int &n1, int &n3) {
   if (v.obs_w32[k] == 0.f) return;  // deleted by the serial robust variant
   float r0, r1;
   ff_residual(v.camff + FF_CAM * (size_t)i, v.X_hi + 3 * (size_t)j, v.X_lo + 3 * (size_t)j, v.obs_xy32[2 * k],
-              v.obs_xylo[2 * k], v.obs_xy32[2 * k + 1], v.obs_xylo[2 * k + 1], r0, r1);
+              v.obs_xylo[2 * k], v.obs_xy32[2 * k + 1], v.obs_xylo[2 * k + 1], r0, r1, K1);
   float W0 = 1.f, W1 = 0.f, W2 = 1.f;
   if (v.has_winv) { W0 = v.obs_winv32[3 * k]; W1 = v.obs_winv32[3 * k + 1]; W2 = v.obs_winv32[3 * k + 2]; }
   float w = v.obs_w32[k], e;
@@ -364,6 +400,7 @@ __device__ inline void sigma_obs_terms(const View &v, int k, int i, int j, float
   }
 }
 
+template <bool K1>
 __global__ void k_obs_sigma_f(View v, double *part) {
   float sh = 0.f, sl = 0.f, rh = 0.f, rl = 0.f;
   int n1 = 0, n3 = 0, np = 0;
@@ -371,7 +408,7 @@ __global__ void k_obs_sigma_f(View v, double *part) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < v.K; k += gridDim.x * blockDim.x) {
     int j = v.obs_pt[k];
     if (!v.active[j]) continue;
-    sigma_obs_terms(v, k, v.obs_cam[k], j, sh, sl, rh, rl, n1, n3);
+    sigma_obs_terms<K1>(v, k, v.obs_cam[k], j, sh, sl, rh, rl, n1, n3);
   }
   sigma_cta_sums(sh, sl, rh, rl, n1, n3, np, part + 5 * blockIdx.x);
 }
@@ -425,7 +462,8 @@ rpba_status sigma0_launch(Ctx *ctx) {
   View v = make_view(ctx);
   int nb = ctx->red_blocks;
   if (ctx->opt.precision == 1) {
-    RPBA_KERNEL(ctx, "k_obs_sigma_f", k_obs_sigma_f<<<nb, 256, 0, ctx->stream>>>(v, ctx->red));
+    if (ctx->cd == 8) RPBA_KERNEL(ctx, "k_obs_sigma_f", k_obs_sigma_f<true><<<nb, 256, 0, ctx->stream>>>(v, ctx->red));
+    else RPBA_KERNEL(ctx, "k_obs_sigma_f", k_obs_sigma_f<false><<<nb, 256, 0, ctx->stream>>>(v, ctx->red));
   } else {
     RPBA_KERNEL(ctx, "k_obs_sigma", k_obs_sigma<<<nb, 256, 0, ctx->stream>>>(v, ctx->red));
   }
@@ -439,7 +477,7 @@ rpba_status sigma0_launch(Ctx *ctx) {
 // sigma0_launch, after the stream has been synchronised
 void sigma0_finish(const Ctx *ctx, double *sigma0, double *rms, long long *n_obs, long long *n_points) {
   const double *h = ctx->h_pinned_d;
-  double red = 2.0 * h[1] - 6.0 * ctx->M - 3.0 * h[4] + 7.0;
+  double red = 2.0 * h[1] - (double)ctx->cd * ctx->M - 3.0 * h[4] + 7.0;
   if (red < 1.0) red = 1.0;
   if (sigma0) *sigma0 = sqrt(h[0] / red);
   if (rms) *rms = h[3] > 0 ? sqrt(h[2] / (2.0 * h[3])) : 0.0;
@@ -466,9 +504,9 @@ __device__ __noinline__ bool point_normal_fp64(const View &v, int j, double *N, 
   for (int a = v.pt_inst_ptr[j]; a < v.pt_inst_ptr[j + 1]; a++) {
     int q = v.pt_inst[a];
     for (int k = v.inst_obs_ptr[q]; k < v.inst_obs_ptr[q + 1]; k++) {
-      ProjJac<double> pj;
+      ProjX<double> pj;
       double z;
-      obs_proj<double>(v, v.obs_cam[k], v.X + 3 * (size_t)j, nullptr, nullptr, pj, z);
+      proj_x<double>(v, v.obs_cam[k], v.X + 3 * (size_t)j, nullptr, nullptr, pj, z);
       if (!(z > 0.0)) { ok = false; continue; }
       ObsT<double> ob;
       load_obs<double>(v, k, ob);
@@ -498,9 +536,9 @@ __global__ void k_isect_inst(View v, const int *state, T *part) {
   bool behind = false;
   for (int k = v.inst_obs_ptr[q]; k < v.inst_obs_ptr[q + 1]; k++) {
     int i = v.obs_cam[k];
-    ProjJac<T> pj;
+    ProjX<T> pj;
     T z;
-    obs_proj<T>(v, i, v.X + 3 * j, v.X_hi + 3 * j, v.X_lo + 3 * j, pj, z);
+    proj_x<T>(v, i, v.X + 3 * j, v.X_hi + 3 * j, v.X_lo + 3 * j, pj, z);
     if (!(z > T(0))) { behind = true; continue; }
     ObsT<T> ob;
     load_obs<T>(v, k, ob);
@@ -669,9 +707,9 @@ __global__ void k_isect_point(View v, int *state, int *iter, const T *part, int 
 // difference would cancel when the other sub-blocks' observations are
 // down-weighted).
 __device__ inline void isect_obs_acc(const View &v, int j, int k, float N[6], float g[3], bool &behind) {
-  ProjJac<float> pj;
+  ProjX<float> pj;
   float z;
-  obs_proj<float>(v, v.obs_cam[k], nullptr, v.X_hi + 3 * (size_t)j, v.X_lo + 3 * (size_t)j, pj, z);
+  proj_x<float>(v, v.obs_cam[k], nullptr, v.X_hi + 3 * (size_t)j, v.X_lo + 3 * (size_t)j, pj, z);
   if (!(z > 0.f)) { behind = true; return; }
   ObsT<float> ob;
   load_obs<float>(v, k, ob);
@@ -905,12 +943,11 @@ __global__ void k_robust_weights(View v, const double *sigma, double t_v, double
   int j = v.obs_pt[k];
   if (!v.active[j]) return;
   int i = v.obs_cam[k];
-  const double *R = v.R + 9 * i, *t = v.t + 3 * i, *X = v.X + 3 * j;
-  double Xc[3];
-  for (int r = 0; r < 3; r++) Xc[r] = R[3 * r] * X[0] + R[3 * r + 1] * X[1] + R[3 * r + 2] * X[2] + t[r];
-  double f = v.intr[3 * i], iz = 1.0 / Xc[2];
-  double r0 = f * Xc[0] * iz + v.intr[3 * i + 1] - v.obs_xy[2 * k];
-  double r1 = f * Xc[1] * iz + v.intr[3 * i + 2] - v.obs_xy[2 * k + 1];
+  double pu, pv;
+  proj64(v.R + 9 * i, v.t + 3 * i, v.intr[3 * i], v.k1 ? v.k1[i] : 0.0, v.intr[3 * i + 1], v.intr[3 * i + 2],
+         v.X + 3 * j, pu, pv);
+  double r0 = pu - v.obs_xy[2 * k];
+  double r1 = pv - v.obs_xy[2 * k + 1];
   double W0 = 1, W1 = 0, W2 = 1;
   if (v.has_winv) { W0 = v.obs_winv[3 * k]; W1 = v.obs_winv[3 * k + 1]; W2 = v.obs_winv[3 * k + 2]; }
   double nr = sqrt(W0 * r0 * r0 + 2.0 * W1 * r0 * r1 + W2 * r1 * r1);
@@ -925,6 +962,7 @@ __global__ void k_robust_weights(View v, const double *sigma, double t_v, double
 // A separate pass in observation order: written from the per-camera scale
 // kernel the weights would scatter over the observation-ordered arrays
 // (measured slower on the 20M-observation block).
+template <bool K1>
 __global__ void k_robust_weights_f(View v, const float *sigma, float t_v, double dw, int *count) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= v.K) return;
@@ -933,7 +971,7 @@ __global__ void k_robust_weights_f(View v, const float *sigma, float t_v, double
   int i = v.obs_cam[k];
   float r0, r1;
   ff_residual(v.camff + FF_CAM * (size_t)i, v.X_hi + 3 * (size_t)j, v.X_lo + 3 * (size_t)j, v.obs_xy32[2 * k],
-              v.obs_xylo[2 * k], v.obs_xy32[2 * k + 1], v.obs_xylo[2 * k + 1], r0, r1);
+              v.obs_xylo[2 * k], v.obs_xy32[2 * k + 1], v.obs_xylo[2 * k + 1], r0, r1, K1);
   float W0 = 1.f, W1 = 0.f, W2 = 1.f;
   if (v.has_winv) { W0 = v.obs_winv32[3 * k]; W1 = v.obs_winv32[3 * k + 1]; W2 = v.obs_winv32[3 * k + 2]; }
   float nr = sqrtf(W0 * r0 * r0 + 2.f * W1 * r0 * r1 + W2 * r1 * r1);
@@ -947,10 +985,17 @@ __global__ void k_robust_weights_f(View v, const float *sigma, float t_v, double
 rpba_status launch_robust_weights(Ctx *ctx, int *n_down) {
   RPBA_TRY(launch_camera_scale(ctx));
   RPBA_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(int), ctx->stream));
-  if (ctx->K && ctx->opt.precision == 1)
-    RPBA_KERNEL(ctx, "k_robust_weights_f", k_robust_weights_f<<<nblk(ctx->K, ctx->tune.robust), ctx->tune.robust, 0, ctx->stream>>>(
-                                             make_view(ctx), ctx->cam_sigma32, (float)ctx->opt.t_v, ctx->opt.downweight,
-                                             ctx->counters));
+  if (ctx->K && ctx->opt.precision == 1) {
+    dim3 g(nblk(ctx->K, ctx->tune.robust)), b(ctx->tune.robust);
+    if (ctx->cd == 8)
+      RPBA_KERNEL(ctx, "k_robust_weights_f", k_robust_weights_f<true><<<g, b, 0, ctx->stream>>>(
+                                               make_view(ctx), ctx->cam_sigma32, (float)ctx->opt.t_v,
+                                               ctx->opt.downweight, ctx->counters));
+    else
+      RPBA_KERNEL(ctx, "k_robust_weights_f", k_robust_weights_f<false><<<g, b, 0, ctx->stream>>>(
+                                               make_view(ctx), ctx->cam_sigma32, (float)ctx->opt.t_v,
+                                               ctx->opt.downweight, ctx->counters));
+  }
   else if (ctx->K)
     RPBA_KERNEL(ctx, "k_robust_weights", k_robust_weights<<<nblk(ctx->K, ctx->tune.robust), ctx->tune.robust, 0, ctx->stream>>>(make_view(ctx), ctx->cam_sigma, ctx->opt.t_v,
                                                                 ctx->opt.downweight, ctx->counters));
@@ -1024,15 +1069,16 @@ __global__ void k_obs_cost(View v, int trial, const int *run, double *cost) {
   const double *R = (trial ? v.Rt : v.R) + 9 * i;
   const double *t = (trial ? v.tt : v.t) + 3 * i;
   const double *Xq = (trial ? v.Xlt : v.Xl) + 3 * (size_t)q;
-  double Xc[3];
-  for (int r = 0; r < 3; r++) Xc[r] = R[3 * r] * Xq[0] + R[3 * r + 1] * Xq[1] + R[3 * r + 2] * Xq[2] + t[r];
+  double f = (trial && v.ft) ? v.ft[i] : v.intr[3 * i];
+  double k1 = v.k1 ? (trial ? v.k1t[i] : v.k1[i]) : 0.0;
+  double pu, pv;
+  double zc = proj64(R, t, f, k1, v.intr[3 * i + 1], v.intr[3 * i + 2], Xq, pu, pv);
   double F;
-  if (!(Xc[2] > 0.0)) {
+  if (!(zc > 0.0)) {
     F = INFINITY;
   } else {
-    double f = v.intr[3 * i], iz = 1.0 / Xc[2];
-    double r0 = f * Xc[0] * iz + v.intr[3 * i + 1] - v.obs_xy[2 * k];
-    double r1 = f * Xc[1] * iz + v.intr[3 * i + 2] - v.obs_xy[2 * k + 1];
+    double r0 = pu - v.obs_xy[2 * k];
+    double r1 = pv - v.obs_xy[2 * k + 1];
     double W0 = 1, W1 = 0, W2 = 1;
     if (v.has_winv) { W0 = v.obs_winv[3 * k]; W1 = v.obs_winv[3 * k + 1]; W2 = v.obs_winv[3 * k + 2]; }
     F = v.obs_w[k] * (W0 * r0 * r0 + 2.0 * W1 * r0 * r1 + W2 * r1 * r1);
@@ -1059,7 +1105,7 @@ struct SigmaAcc {
 // float-float difference X^l - X_TP and W^l in FP32. With SIG the same
 // residual also feeds the observation's sigma_0 terms (Eq. sigma0: every
 // observation of an active point that is not deleted, whatever its depth)
-template <bool SIG = false>
+template <bool SIG, bool K1>
 __device__ inline float obs_cost_term_f(const View &v, int trial, int k, SigmaAcc *sig = nullptr) {
   int q = v.obs_inst[k];
   int j = v.inst_pt[q];
@@ -1071,7 +1117,7 @@ __device__ inline float obs_cost_term_f(const View &v, int trial, int k, SigmaAc
   float r0, r1;
   float F;
   bool front = ff_residual(cf, Xh, Xw, v.obs_xy32[2 * k], v.obs_xylo[2 * k], v.obs_xy32[2 * k + 1],
-                           v.obs_xylo[2 * k + 1], r0, r1);
+                           v.obs_xylo[2 * k + 1], r0, r1, K1);
   if (!front && !SIG) {
     F = INFINITY;
   } else {
@@ -1110,7 +1156,7 @@ __device__ inline float obs_cost_term_f(const View &v, int trial, int k, SigmaAc
 // writes its sum, then one CTA per sub-block adds its chunks' sums in order.
 // With SIG (at a state where every X^l equals its X) the chunk also writes
 // its 5 sigma_0 sums to sig (the active points counted over a grid stride)
-template <bool SIG>
+template <bool SIG, bool K1>
 __global__ void __launch_bounds__(256) k_cost_chunks_f(View v, int trial, const int *run, const int *chunk_sub,
                                                        const int *chunk_start, const int *sub_obs_ptr, double *part,
                                                        double *sig) {
@@ -1119,7 +1165,7 @@ __global__ void __launch_bounds__(256) k_cost_chunks_f(View v, int trial, const 
   if (run && !run[l]) return;
   int k = chunk_start[c] + threadIdx.x;
   SigmaAcc acc;
-  float F = k < sub_obs_ptr[l + 1] ? obs_cost_term_f<SIG>(v, trial, k, &acc) : 0.f;
+  float F = k < sub_obs_ptr[l + 1] ? obs_cost_term_f<SIG, K1>(v, trial, k, &acc) : 0.f;
   // a point behind its camera makes the sum +inf (TwoSum would turn it into NaN)
   int any_inf = __syncthreads_or(isinf(F));
   float h = any_inf ? 0.f : F, lo = 0.f;  // float-float sum: off the FP64 pipe
@@ -1192,8 +1238,12 @@ __global__ void k_seg_final(int L, const int *run, const double *part, double *F
 static rpba_status sub_costs_impl(Ctx *ctx, int trial, const int *run, double *F_dev) {
   View v = make_view(ctx);
   if (ctx->opt.precision == 1) {
-    if (ctx->n_chunks)
-      RPBA_KERNEL(ctx, "k_cost_chunks_f", k_cost_chunks_f<false><<<ctx->n_chunks, 256, 0, ctx->stream>>>(
+    if (ctx->n_chunks && ctx->cd == 8)
+      RPBA_KERNEL(ctx, "k_cost_chunks_f", k_cost_chunks_f<false, true><<<ctx->n_chunks, 256, 0, ctx->stream>>>(
+                                         v, trial, run, ctx->chunk_sub, ctx->chunk_start, ctx->sub_obs_ptr,
+                                         ctx->chunk_part, nullptr));
+    else if (ctx->n_chunks)
+      RPBA_KERNEL(ctx, "k_cost_chunks_f", k_cost_chunks_f<false, false><<<ctx->n_chunks, 256, 0, ctx->stream>>>(
                                          v, trial, run, ctx->chunk_sub, ctx->chunk_start, ctx->sub_obs_ptr,
                                          ctx->chunk_part, nullptr));
     if (ctx->L)
@@ -1225,9 +1275,14 @@ rpba_status cost_sigma0_launch(Ctx *ctx) {
   View v = make_view(ctx);
   double *sig_chunk = ctx->sigma0_part, *sig_sub = sig_chunk + 5 * (size_t)ctx->n_chunks;
   double *sig_tot = sig_sub + 5 * (size_t)ctx->L;
-  RPBA_KERNEL(ctx, "k_cost_chunks_f", k_cost_chunks_f<true><<<ctx->n_chunks, 256, 0, ctx->stream>>>(
-                                       v, 0, nullptr, ctx->chunk_sub, ctx->chunk_start, ctx->sub_obs_ptr,
-                                       ctx->chunk_part, sig_chunk));
+  if (ctx->cd == 8)
+    RPBA_KERNEL(ctx, "k_cost_chunks_f", k_cost_chunks_f<true, true><<<ctx->n_chunks, 256, 0, ctx->stream>>>(
+                                         v, 0, nullptr, ctx->chunk_sub, ctx->chunk_start, ctx->sub_obs_ptr,
+                                         ctx->chunk_part, sig_chunk));
+  else
+    RPBA_KERNEL(ctx, "k_cost_chunks_f", k_cost_chunks_f<true, false><<<ctx->n_chunks, 256, 0, ctx->stream>>>(
+                                         v, 0, nullptr, ctx->chunk_sub, ctx->chunk_start, ctx->sub_obs_ptr,
+                                         ctx->chunk_part, sig_chunk));
   RPBA_KERNEL(ctx, "k_cost_sub_f", k_cost_sub_f<true><<<ctx->L, 256, 0, ctx->stream>>>(
                                     ctx->L, nullptr, ctx->sub_chunk_ptr, ctx->chunk_part, ctx->f0_cache, sig_chunk,
                                     sig_sub));
@@ -1246,9 +1301,9 @@ __device__ __noinline__ void instance_normal_fp64(const View &v, int q, double l
   for (int e = 0; e < 6; e++) N[e] = 0.0;
   for (int e = 0; e < 3; e++) g[e] = 0.0;
   for (int k = v.inst_obs_ptr[q]; k < v.inst_obs_ptr[q + 1]; k++) {
-    ProjJac<double> pj;
+    ProjX<double> pj;
     double z;
-    obs_proj<double>(v, v.obs_cam[k], Xd, nullptr, nullptr, pj, z);
+    proj_x<double>(v, v.obs_cam[k], Xd, nullptr, nullptr, pj, z);
     ObsT<double> ob;
     load_obs<double>(v, k, ob);
     double r0 = pj.u - ob.x, r1 = pj.v - ob.y, a0[3], a1[3];
@@ -1275,7 +1330,7 @@ __device__ __noinline__ void instance_normal_fp64(const View &v, int q, double l
 // form: when the FP32 N_XX has a Frobenius condition number above 1e5, N_XX
 // and g_X are formed again in FP64 and the FP64 inverse is rounded to FP32 (an
 // FP32 inverse would be wrong in the weak direction).
-template <typename T>
+template <typename T, int CD>
 __global__ void k_linearize(View v, const double *lambda, const int *run, T *NXC, T *Z, T *Ninv_out,
                             T *gX_out) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1290,7 +1345,7 @@ __global__ void k_linearize(View v, const double *lambda, const int *run, T *NXC
     for (int e = 0; e < 3; e++) gX_out[3 * (size_t)q + e] = 0;
     if (kStore)
       for (int k = k0; k < k1; k++)
-        for (int e = 0; e < 18; e++) { NXC[18 * (size_t)k + e] = 0; Z[18 * (size_t)k + e] = 0; }
+        for (int e = 0; e < 3 * CD; e++) { NXC[3 * CD * (size_t)k + e] = 0; Z[3 * CD * (size_t)k + e] = 0; }
     return;
   }
   const double *Xd = v.Xl + 3 * (size_t)q;
@@ -1298,9 +1353,9 @@ __global__ void k_linearize(View v, const double *lambda, const int *run, T *NXC
   T N[6] = {0, 0, 0, 0, 0, 0}, g[3] = {0, 0, 0};
   for (int k = k0; k < k1; k++) {
     int i = v.obs_cam[k];
-    ProjJac<T> pj;
+    ProjJac<T, CD> pj;
     T z;
-    obs_proj<T>(v, i, Xd, Xh, Xw, pj, z);
+    obs_proj<T, CD>(v, i, Xd, Xh, Xw, pj, z);
     ObsT<T> ob;
     load_obs<T>(v, k, ob);
     T r0 = pj.u - ob.x, r1 = pj.v - ob.y;
@@ -1315,9 +1370,9 @@ __global__ void k_linearize(View v, const double *lambda, const int *run, T *NXC
     }
     if (kStore) {
       // N_XC = (w W A_X)^T A_C : row r (point coord) = a0[r] Jc[0,:] + a1[r] Jc[1,:]
-      T *o = NXC + 18 * (size_t)k;
+      T *o = NXC + 3 * CD * (size_t)k;
       for (int r = 0; r < 3; r++)
-        for (int c = 0; c < 6; c++) o[6 * r + c] = a0[r] * pj.Jc[c] + a1[r] * pj.Jc[6 + c];
+        for (int c = 0; c < CD; c++) o[CD * r + c] = a0[r] * pj.Jc[c] + a1[r] * pj.Jc[CD + c];
     }
   }
   // TP control term
@@ -1353,20 +1408,21 @@ __global__ void k_linearize(View v, const double *lambda, const int *run, T *NXC
   for (int e = 0; e < 3; e++) gX_out[3 * (size_t)q + e] = g[e];
   if (kStore)
   for (int k = k0; k < k1; k++) {
-    const T *B = NXC + 18 * (size_t)k;
-    T *o = Z + 18 * (size_t)k;
+    const T *B = NXC + 3 * CD * (size_t)k;
+    T *o = Z + 3 * CD * (size_t)k;
     for (int r = 0; r < 3; r++)
-      for (int c = 0; c < 6; c++)
-        o[6 * r + c] = inv[s3idx(r, 0)] * B[c] + inv[s3idx(r, 1)] * B[6 + c] + inv[s3idx(r, 2)] * B[12 + c];
+      for (int c = 0; c < CD; c++)
+        o[CD * r + c] = inv[s3idx(r, 0)] * B[c] + inv[s3idx(r, 1)] * B[CD + c] + inv[s3idx(r, 2)] * B[2 * CD + c];
   }
 }
 
 // FP32 form: N_XC = (w W A_X)^T A_C of observation k (camera i, instance q)
 // in registers, with the projection at the instance's X^l
-__device__ inline void nxc_f(const View &v, int i, int k, int q, float B[18]) {
-  ProjJac<float> pj;
+template <int CD>
+__device__ inline void nxc_f(const View &v, int i, int k, int q, float B[3 * CD]) {
+  ProjJac<float, CD> pj;
   float z;
-  obs_proj<float>(v, i, nullptr, v.Xl_hi + 3 * (size_t)q, v.Xl_lo + 3 * (size_t)q, pj, z);
+  obs_proj<float, CD>(v, i, nullptr, v.Xl_hi + 3 * (size_t)q, v.Xl_lo + 3 * (size_t)q, pj, z);
   float w = v.obs_w32[k], W0 = 1.f, W1 = 0.f, W2 = 1.f;
   if (v.has_winv) { W0 = v.obs_winv32[3 * k]; W1 = v.obs_winv32[3 * k + 1]; W2 = v.obs_winv32[3 * k + 2]; }
 #pragma unroll
@@ -1374,137 +1430,140 @@ __device__ inline void nxc_f(const View &v, int i, int k, int q, float B[18]) {
     float a0 = w * (W0 * pj.Jx[r] + W1 * pj.Jx[3 + r]);
     float a1 = w * (W1 * pj.Jx[r] + W2 * pj.Jx[3 + r]);
 #pragma unroll
-    for (int c = 0; c < 6; c++) B[6 * r + c] = a0 * pj.Jc[c] + a1 * pj.Jc[6 + c];
+    for (int c = 0; c < CD; c++) B[CD * r + c] = a0 * pj.Jc[c] + a1 * pj.Jc[CD + c];
   }
 }
 
-// Z = Ninv N_XC (3x6) with Ninv a packed symmetric 3x3
-__device__ inline void z_of(const float inv[6], const float B[18], float Zk[18]) {
+// Z = Ninv N_XC (3 x CD) with Ninv a packed symmetric 3x3
+template <int CD>
+__device__ inline void z_of(const float inv[6], const float B[3 * CD], float Zk[3 * CD]) {
 #pragma unroll
   for (int r = 0; r < 3; r++)
 #pragma unroll
-    for (int c = 0; c < 6; c++)
-      Zk[6 * r + c] = inv[s3idx(r, 0)] * B[c] + inv[s3idx(r, 1)] * B[6 + c] + inv[s3idx(r, 2)] * B[12 + c];
+    for (int c = 0; c < CD; c++)
+      Zk[CD * r + c] = inv[s3idx(r, 0)] * B[c] + inv[s3idx(r, 1)] * B[CD + c] + inv[s3idx(r, 2)] * B[2 * CD + c];
 }
 
 // one CTA (CB_THREADS threads) per camera of a running sub-block: diagonal RCS block
 //   S_ii = U_ii + lambda diag(U_ii) - sum_k N_XC,k^T Z_k,  U_ii = sum_k w A_C^T W A_C
 // and right-hand side y_i = -sum_k w A_C^T W v + sum_k Z_k^T g_X
 #define CB_THREADS 128
-template <typename T>
+template <typename T, int CD>
 __global__ void __launch_bounds__(CB_THREADS) k_camera_blocks(View v, const double *lambda, const int *run,
                                                               const T *NXC, const T *Z, const T *gX,
                                                               const T *Ninv) {
+  constexpr int NU = CD * (CD + 1) / 2;  // upper triangle of a CD x CD block
+  constexpr int NA = 2 * NU + 2 * CD;    // U, SZ, gc, yz
   int i = blockIdx.x;
   if (i >= v.M) return;
   int l = v.cam_sub[i];
   if (!run[l]) return;
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  T acc[54];  // U (21), SZ (21), gc (6), yz (6)
+  T acc[NA];
 #pragma unroll
-  for (int e = 0; e < 54; e++) acc[e] = 0;
+  for (int e = 0; e < NA; e++) acc[e] = 0;
   for (int p = v.cam_obs_ptr[i] + threadIdx.x; p < v.cam_obs_ptr[i + 1]; p += CB_THREADS) {
     int k = v.cam_obs[p];
     int q = v.obs_inst[k];
     int j = v.inst_pt[q];
     if (!v.active[j]) continue;
-    ProjJac<T> pj;
+    ProjJac<T, CD> pj;
     T z;
-    obs_proj<T>(v, i, v.Xl + 3 * (size_t)q, v.Xl_hi + 3 * (size_t)q, v.Xl_lo + 3 * (size_t)q, pj, z);
+    obs_proj<T, CD>(v, i, v.Xl + 3 * (size_t)q, v.Xl_hi + 3 * (size_t)q, v.Xl_lo + 3 * (size_t)q, pj, z);
     ObsT<T> ob;
     load_obs<T>(v, k, ob);
     T r0 = pj.u - ob.x, r1 = pj.v - ob.y;
-    T b0[6], b1[6];  // w W A_C
+    T b0[CD], b1[CD];  // w W A_C
 #pragma unroll
-    for (int c = 0; c < 6; c++) {
-      b0[c] = ob.w * (ob.W[0] * pj.Jc[c] + ob.W[1] * pj.Jc[6 + c]);
-      b1[c] = ob.w * (ob.W[1] * pj.Jc[c] + ob.W[2] * pj.Jc[6 + c]);
+    for (int c = 0; c < CD; c++) {
+      b0[c] = ob.w * (ob.W[0] * pj.Jc[c] + ob.W[1] * pj.Jc[CD + c]);
+      b1[c] = ob.w * (ob.W[1] * pj.Jc[c] + ob.W[2] * pj.Jc[CD + c]);
     }
     const T *gq = gX + 3 * (size_t)q;
-    T Bl[18], Zl[18], g3[3] = {gq[0], gq[1], gq[2]};
+    T Bl[3 * CD], Zl[3 * CD], g3[3] = {gq[0], gq[1], gq[2]};
     if constexpr (sizeof(T) == sizeof(float)) {  // N_XC and Z in registers
 #pragma unroll
       for (int r = 0; r < 3; r++)
 #pragma unroll
-        for (int c = 0; c < 6; c++) {
+        for (int c = 0; c < CD; c++) {
           T a0 = ob.w * (ob.W[0] * pj.Jx[r] + ob.W[1] * pj.Jx[3 + r]);
           T a1 = ob.w * (ob.W[1] * pj.Jx[r] + ob.W[2] * pj.Jx[3 + r]);
-          Bl[6 * r + c] = a0 * pj.Jc[c] + a1 * pj.Jc[6 + c];
+          Bl[CD * r + c] = a0 * pj.Jc[c] + a1 * pj.Jc[CD + c];
         }
       const float *iv = Ninv + 6 * (size_t)q;
       float inv[6] = {iv[0], iv[1], iv[2], iv[3], iv[4], iv[5]};
-      z_of(inv, Bl, Zl);
+      z_of<CD>(inv, Bl, Zl);
     } else {
-      const T *B = NXC + 18 * (size_t)k, *Zk = Z + 18 * (size_t)k;
+      const T *B = NXC + 3 * CD * (size_t)k, *Zk = Z + 3 * CD * (size_t)k;
 #pragma unroll
-      for (int e = 0; e < 18; e++) { Bl[e] = B[e]; Zl[e] = Zk[e]; }
+      for (int e = 0; e < 3 * CD; e++) { Bl[e] = B[e]; Zl[e] = Zk[e]; }
     }
     int e = 0;
 #pragma unroll
-    for (int r = 0; r < 6; r++) {
-      acc[42 + r] += b0[r] * r0 + b1[r] * r1;
-      acc[48 + r] += Zl[r] * g3[0] + Zl[6 + r] * g3[1] + Zl[12 + r] * g3[2];
+    for (int r = 0; r < CD; r++) {
+      acc[2 * NU + r] += b0[r] * r0 + b1[r] * r1;
+      acc[2 * NU + CD + r] += Zl[r] * g3[0] + Zl[CD + r] * g3[1] + Zl[2 * CD + r] * g3[2];
 #pragma unroll
-      for (int c = r; c < 6; c++, e++) {
-        acc[e] += pj.Jc[r] * b0[c] + pj.Jc[6 + r] * b1[c];
-        acc[21 + e] += Bl[r] * Zl[c] + Bl[6 + r] * Zl[6 + c] + Bl[12 + r] * Zl[12 + c];
+      for (int c = r; c < CD; c++, e++) {
+        acc[e] += pj.Jc[r] * b0[c] + pj.Jc[CD + r] * b1[c];
+        acc[NU + e] += Bl[r] * Zl[c] + Bl[CD + r] * Zl[CD + c] + Bl[2 * CD + r] * Zl[2 * CD + c];
       }
     }
   }
   // warp reduction, then across the CTA's warps
-  __shared__ T red[CB_THREADS / 32][54];
+  __shared__ T red[CB_THREADS / 32][NA];
 #pragma unroll
-  for (int e = 0; e < 54; e++) {
+  for (int e = 0; e < NA; e++) {
     T x = acc[e];
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     if (lane == 0) red[wid][e] = x;
   }
   __syncthreads();
-  if (threadIdx.x < 54) {
+  if (threadIdx.x < NA) {
     T x = 0;
     for (int w = 0; w < CB_THREADS / 32; w++) x += red[w][threadIdx.x];
     red[0][threadIdx.x] = x;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const T *U = red[0], *SZ = red[0] + 21, *gc = red[0] + 42, *yz = red[0] + 48;
+    const T *U = red[0], *SZ = red[0] + NU, *gc = red[0] + 2 * NU, *yz = red[0] + 2 * NU + CD;
     double lam = lambda[l];
     int li = v.cam_local[i];
     int np = v.npad[l];
     double *S = v.S + v.S_off[l];
     int e = 0;
-    for (int r = 0; r < 6; r++)
-      for (int c = r; c < 6; c++, e++) {
+    for (int r = 0; r < CD; r++)
+      for (int c = r; c < CD; c++, e++) {
         double val = (double)U[e] - (double)SZ[e];
         if (r == c) val += lam * (double)U[e];
-        S[(size_t)(6 * li + r) * np + 6 * li + c] = val;
-        S[(size_t)(6 * li + c) * np + 6 * li + r] = val;
+        S[(size_t)(CD * li + r) * np + CD * li + c] = val;
+        S[(size_t)(CD * li + c) * np + CD * li + r] = val;
       }
     double *yv = v.y + v.ycam_off[l];
-    for (int r = 0; r < 6; r++) yv[6 * li + r] = -(double)gc[r] + (double)yz[r];
+    for (int r = 0; r < CD; r++) yv[CD * li + r] = -(double)gc[r] + (double)yz[r];
   }
 }
 
 // off-diagonal Schur blocks: one thread per (pair, row r):
-//   S[(6 ia + r), 6 ib + c] -= sum_e N_XC,a[e][r] Z_b[e][c]    (ia > ib)
-template <typename T>
+//   S[(CD ia + r), CD ib + c] -= sum_e N_XC,a[e][r] Z_b[e][c]    (ia > ib)
+template <typename T, int CD>
 __global__ void k_schur_pairs(View v, const int *run, const int *pa, const int *pb, long long npairs,
                               const T *NXC, const T *Z) {
   long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= npairs * 6) return;
-  long long p = tid / 6;
-  int r = (int)(tid - p * 6);
+  if (tid >= npairs * CD) return;
+  long long p = tid / CD;
+  int r = (int)(tid - p * CD);
   int a = pa[p], b = pb[p];
   int q = v.obs_inst[a];
   int l = v.inst_sub[q];
   if (!run[l] || !v.active[v.inst_pt[q]]) return;
   int ia = v.cam_local[v.obs_cam[a]], ib = v.cam_local[v.obs_cam[b]];
-  const T *A = NXC + 18 * (size_t)a, *Zb = Z + 18 * (size_t)b;
-  T x0 = A[r], x1 = A[6 + r], x2 = A[12 + r];
-  double *row = v.S + v.S_off[l] + (size_t)(6 * ia + r) * v.npad[l] + 6 * ib;
+  const T *A = NXC + 3 * CD * (size_t)a, *Zb = Z + 3 * CD * (size_t)b;
+  T x0 = A[r], x1 = A[CD + r], x2 = A[2 * CD + r];
+  double *row = v.S + v.S_off[l] + (size_t)(CD * ia + r) * v.npad[l] + CD * ib;
 #pragma unroll
-  for (int c = 0; c < 6; c++) {
-    T val = x0 * Zb[c] + x1 * Zb[6 + c] + x2 * Zb[12 + c];
+  for (int c = 0; c < CD; c++) {
+    T val = x0 * Zb[c] + x1 * Zb[CD + c] + x2 * Zb[2 * CD + c];
     atomicAdd(row + c, -(double)val);
   }
 }
@@ -1516,19 +1575,20 @@ __global__ void k_schur_pairs(View v, const int *run, const int *pa, const int *
 // (segment) and cut into items of at most SC_ITEM consecutive pairs of one
 // segment; a thread sums its item's blocks in registers, then a segmented
 // warp reduction (items sorted, so a segment is a run of lanes) sums each
-// segment's part and its first lane adds the 36 values to S (FP64 atomics,
+// segment's part and its first lane adds the CD x CD values to S (FP64 atomics,
 // one set per segment piece instead of one per pair).
 #define SC_THREADS 256
-__global__ void __launch_bounds__(SC_THREADS, 2) k_schur_seg(View v, const int *run, long long nitems,
+template <int CD>
+__global__ void __launch_bounds__(SC_THREADS, CD == 6 ? 2 : 1) k_schur_seg(View v, const int *run, long long nitems,
                                                              const int *item, const int *spa, const int *spb,
                                                              const int *spq, const int *sps, const int *seg_cam,
                                                              const int *seg_nb, const float *Ninv) {
   long long it = (long long)blockIdx.x * SC_THREADS + threadIdx.x;
   int lane = threadIdx.x & 31;
   int sg = -1;
-  float acc[36];
+  float acc[CD * CD];
 #pragma unroll
-  for (int e = 0; e < 36; e++) acc[e] = 0.f;
+  for (int e = 0; e < CD * CD; e++) acc[e] = 0.f;
   if (it < nitems) {
     int t0 = item[it], t1 = item[it + 1];
     sg = sps[t0];
@@ -1537,17 +1597,17 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_schur_seg(View v, const int *
       for (int t = t0; t < t1; t++) {
         int q = spq[t];
         if (!v.active[v.inst_pt[q]]) continue;
-        float A[18], B[18], Zb[18];
-        nxc_f(v, i, spa[t], q, A);
-        nxc_f(v, ib, spb[t], q, B);
+        float A[3 * CD], B[3 * CD], Zb[3 * CD];
+        nxc_f<CD>(v, i, spa[t], q, A);
+        nxc_f<CD>(v, ib, spb[t], q, B);
         const float *iv = Ninv + 6 * (size_t)q;
         float inv[6] = {iv[0], iv[1], iv[2], iv[3], iv[4], iv[5]};
-        z_of(inv, B, Zb);
+        z_of<CD>(inv, B, Zb);
 #pragma unroll
-        for (int r = 0; r < 6; r++)
+        for (int r = 0; r < CD; r++)
 #pragma unroll
-          for (int c = 0; c < 6; c++)
-            acc[6 * r + c] += A[r] * Zb[c] + A[6 + r] * Zb[6 + c] + A[12 + r] * Zb[12 + c];
+          for (int c = 0; c < CD; c++)
+            acc[CD * r + c] += A[r] * Zb[c] + A[CD + r] * Zb[CD + c] + A[2 * CD + r] * Zb[2 * CD + c];
       }
   }
   // segments are contiguous runs of lanes: after the steps, a lane holds the
@@ -1557,7 +1617,7 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_schur_seg(View v, const int *
     int so = __shfl_down_sync(0xffffffffu, sg, o);
     bool take = (lane + o < 32) && so == sg;
 #pragma unroll
-    for (int e = 0; e < 36; e++) {
+    for (int e = 0; e < CD * CD; e++) {
       float y = __shfl_down_sync(0xffffffffu, acc[e], o);
       if (take) acc[e] += y;
     }
@@ -1568,11 +1628,11 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_schur_seg(View v, const int *
   int l = v.cam_sub[i];
   if (!run[l]) return;
   int np = v.npad[l];
-  double *row = v.S + v.S_off[l] + (size_t)(6 * v.cam_local[i]) * np + 6 * v.cam_local[ib];
+  double *row = v.S + v.S_off[l] + (size_t)(CD * v.cam_local[i]) * np + CD * v.cam_local[ib];
 #pragma unroll
-  for (int r = 0; r < 6; r++)
+  for (int r = 0; r < CD; r++)
 #pragma unroll
-    for (int c = 0; c < 6; c++) atomicAdd(row + (size_t)r * np + c, f2d(-acc[6 * r + c]));
+    for (int c = 0; c < CD; c++) atomicAdd(row + (size_t)r * np + c, f2d(-acc[CD * r + c]));
 }
 
 // zero the RCS of running sub-blocks, identity on the padding
@@ -1580,7 +1640,7 @@ __global__ void k_rcs_clear(View v, const int *run, int L) {
   int l = blockIdx.y;
   if (l >= L || !run[l]) return;
   int np = v.npad[l];
-  int n = 6 * (v.sub_cam_ptr[l + 1] - v.sub_cam_ptr[l]);
+  int n = v.cd * (v.sub_cam_ptr[l + 1] - v.sub_cam_ptr[l]);
   double *S = v.S + v.S_off[l];
   size_t tot = (size_t)np * np;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
@@ -1592,29 +1652,38 @@ __global__ void k_rcs_clear(View v, const int *run, int L) {
     if (e >= n) yv[e] = 0.0;
 }
 
+template <int CD>
+static rpba_status build_rcs_cd(Ctx *ctx, const View &v, const double *lambda_dev, const int *run_dev);
+
 rpba_status launch_build_rcs(Ctx *ctx, const double *lambda_dev, const int *run_dev) {
   View v = make_view(ctx);
   dim3 gclr(64, ctx->L);
   RPBA_KERNEL(ctx, "k_rcs_clear", k_rcs_clear<<<gclr, 256, 0, ctx->stream>>>(v, run_dev, ctx->L));
   if (ctx->P == 0) return RPBA_OK;
+  if (ctx->cd == 8) return build_rcs_cd<8>(ctx, v, lambda_dev, run_dev);
+  return build_rcs_cd<6>(ctx, v, lambda_dev, run_dev);
+}
+
+template <int CD>
+static rpba_status build_rcs_cd(Ctx *ctx, const View &v, const double *lambda_dev, const int *run_dev) {
   if (ctx->opt.precision == 1) {
-    RPBA_KERNEL(ctx, "k_linearize_f32", k_linearize<float><<<nblk(ctx->P, ctx->tune.lin), ctx->tune.lin, 0, ctx->stream>>>(
+    RPBA_KERNEL(ctx, "k_linearize_f32", k_linearize<float, CD><<<nblk(ctx->P, ctx->tune.lin), ctx->tune.lin, 0, ctx->stream>>>(
                                         v, lambda_dev, run_dev, nullptr, nullptr, (float *)ctx->Ninv, (float *)ctx->gX));
-    RPBA_KERNEL(ctx, "k_camera_blocks_f32", k_camera_blocks<float><<<ctx->M, CB_THREADS, 0, ctx->stream>>>(
+    RPBA_KERNEL(ctx, "k_camera_blocks_f32", k_camera_blocks<float, CD><<<ctx->M, CB_THREADS, 0, ctx->stream>>>(
         v, lambda_dev, run_dev, nullptr, nullptr, (const float *)ctx->gX, (const float *)ctx->Ninv));
     if (ctx->n_pairs)
-      RPBA_KERNEL(ctx, "k_schur_seg", k_schur_seg<<<nblk(ctx->n_items, SC_THREADS), SC_THREADS, 0, ctx->stream>>>(
+      RPBA_KERNEL(ctx, "k_schur_seg", k_schur_seg<CD><<<nblk(ctx->n_items, SC_THREADS), SC_THREADS, 0, ctx->stream>>>(
                                           v, run_dev, ctx->n_items, ctx->sitem, ctx->spair_a, ctx->spair_b,
                                           ctx->spair_q, ctx->spair_seg, ctx->seg_cam, ctx->seg_nb,
                                           (const float *)ctx->Ninv));
   } else {
     double *NXC = (double *)ctx->NXC, *Z = (double *)ctx->Z;
-    RPBA_KERNEL(ctx, "k_linearize_f64", k_linearize<double><<<nblk(ctx->P, ctx->tune.lin), ctx->tune.lin, 0, ctx->stream>>>(v, lambda_dev, run_dev, NXC, Z,
+    RPBA_KERNEL(ctx, "k_linearize_f64", k_linearize<double, CD><<<nblk(ctx->P, ctx->tune.lin), ctx->tune.lin, 0, ctx->stream>>>(v, lambda_dev, run_dev, NXC, Z,
                                                                     (double *)ctx->Ninv, (double *)ctx->gX));
-    RPBA_KERNEL(ctx, "k_camera_blocks_f64", k_camera_blocks<double><<<ctx->M, CB_THREADS, 0, ctx->stream>>>(
+    RPBA_KERNEL(ctx, "k_camera_blocks_f64", k_camera_blocks<double, CD><<<ctx->M, CB_THREADS, 0, ctx->stream>>>(
         v, lambda_dev, run_dev, NXC, Z, (const double *)ctx->gX, (const double *)ctx->Ninv));
     if (ctx->n_pairs)
-      RPBA_KERNEL(ctx, "k_schur_pairs", k_schur_pairs<double><<<nblk(ctx->n_pairs * 6, 256), 256, 0, ctx->stream>>>(
+      RPBA_KERNEL(ctx, "k_schur_pairs", k_schur_pairs<double, CD><<<nblk(ctx->n_pairs * CD, 256), 256, 0, ctx->stream>>>(
           v, run_dev, ctx->pair_a, ctx->pair_b, ctx->n_pairs, NXC, Z));
   }
   return RPBA_OK;
@@ -1624,7 +1693,7 @@ rpba_status launch_build_rcs(Ctx *ctx, const double *lambda_dev, const int *run_
 // back-substitution, trial state
 // ---------------------------------------------------------------------------
 // dX = Ninv (-g_X - sum_k N_XC,k dC_i(k)); X^l trial = X^l + dX
-template <typename T>
+template <typename T, int CD>
 __global__ void k_backsub(View v, const int *run, const T *NXC, const T *Ninv, const T *gX) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= v.P) return;
@@ -1644,27 +1713,27 @@ __global__ void k_backsub(View v, const int *run, const T *NXC, const T *Ninv, c
   T rhs[3] = {-gX[3 * (size_t)q], -gX[3 * (size_t)q + 1], -gX[3 * (size_t)q + 2]};
   for (int k = v.inst_obs_ptr[q]; k < v.inst_obs_ptr[q + 1]; k++) {
     int i = v.obs_cam[k];
-    int off = v.ycam_off[l] + 6 * v.cam_local[i];
+    int off = v.ycam_off[l] + CD * v.cam_local[i];
     if constexpr (sizeof(T) == sizeof(float)) {
       // N_XC dC = (w W A_X)^T (A_C dC), the Jacobians formed again in registers
-      float dc[6];
-      for (int c = 0; c < 6; c++) dc[c] = v.dC32[off + c];
-      ProjJac<float> pj;
+      float dc[CD];
+      for (int c = 0; c < CD; c++) dc[c] = v.dC32[off + c];
+      ProjJac<float, CD> pj;
       float z;
-      obs_proj<float>(v, i, nullptr, v.Xl_hi + 3 * (size_t)q, v.Xl_lo + 3 * (size_t)q, pj, z);
+      obs_proj<float, CD>(v, i, nullptr, v.Xl_hi + 3 * (size_t)q, v.Xl_lo + 3 * (size_t)q, pj, z);
       float w = v.obs_w32[k], W0 = 1.f, W1 = 0.f, W2 = 1.f;
       if (v.has_winv) { W0 = v.obs_winv32[3 * k]; W1 = v.obs_winv32[3 * k + 1]; W2 = v.obs_winv32[3 * k + 2]; }
       float u0 = 0.f, u1 = 0.f;
-      for (int c = 0; c < 6; c++) { u0 += pj.Jc[c] * dc[c]; u1 += pj.Jc[6 + c] * dc[c]; }
+      for (int c = 0; c < CD; c++) { u0 += pj.Jc[c] * dc[c]; u1 += pj.Jc[CD + c] * dc[c]; }
       float e0 = w * (W0 * u0 + W1 * u1), e1 = w * (W1 * u0 + W2 * u1);
       for (int r = 0; r < 3; r++) rhs[r] -= pj.Jx[r] * e0 + pj.Jx[3 + r] * e1;
     } else {
-      T dc[6];
-      for (int c = 0; c < 6; c++) dc[c] = v.dC[off + c];
-      const T *B = NXC + 18 * (size_t)k;
+      T dc[CD];
+      for (int c = 0; c < CD; c++) dc[c] = v.dC[off + c];
+      const T *B = NXC + 3 * CD * (size_t)k;
       for (int r = 0; r < 3; r++) {
         T s = 0;
-        for (int c = 0; c < 6; c++) s += B[6 * r + c] * dc[c];
+        for (int c = 0; c < CD; c++) s += B[CD * r + c] * dc[c];
         rhs[r] -= s;
       }
     }
@@ -1684,27 +1753,36 @@ __global__ void k_backsub(View v, const int *run, const T *NXC, const T *Ninv, c
   }
 }
 
-// trial cameras: R' = exp([dw]x) R, t' = t + dt
+// trial cameras: R' = exp([dw]x) R, t' = t + dt; with per-camera
+// intrinsics f' = f + df, k1' = k1 + dk1
 __global__ void k_cam_trial(View v, const int *run) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= v.M) return;
   int l = v.cam_sub[i];
   const double *R = v.R + 9 * i;
   double *Rt = v.Rt + 9 * i;
+  double f = v.intr[3 * i], k1 = v.k1 ? v.k1[i] : 0.0;
   if (!run[l]) {
     for (int e = 0; e < 9; e++) Rt[e] = R[e];
     for (int e = 0; e < 3; e++) v.tt[3 * i + e] = v.t[3 * i + e];
-    if (v.camff_t) ff_camera_record(Rt, v.tt + 3 * i, v.intr[3 * i], v.camff_t + FF_CAM * (size_t)i);
-    return;
+  } else {
+    const double *dc = v.dC + v.ycam_off[l] + v.cd * v.cam_local[i];
+    double dR[9];
+    rodrigues(dc, dR);
+    for (int r = 0; r < 3; r++)
+      for (int c = 0; c < 3; c++)
+        Rt[3 * r + c] = dR[3 * r] * R[c] + dR[3 * r + 1] * R[3 + c] + dR[3 * r + 2] * R[6 + c];
+    for (int e = 0; e < 3; e++) v.tt[3 * i + e] = v.t[3 * i + e] + dc[3 + e];
+    if (v.cd == 8) {
+      f += dc[6];
+      k1 += dc[7];
+    }
   }
-  const double *dc = v.dC + v.ycam_off[l] + 6 * v.cam_local[i];
-  double dR[9];
-  rodrigues(dc, dR);
-  for (int r = 0; r < 3; r++)
-    for (int c = 0; c < 3; c++)
-      Rt[3 * r + c] = dR[3 * r] * R[c] + dR[3 * r + 1] * R[3 + c] + dR[3 * r + 2] * R[6 + c];
-  for (int e = 0; e < 3; e++) v.tt[3 * i + e] = v.t[3 * i + e] + dc[3 + e];
-  if (v.camff_t) ff_camera_record(Rt, v.tt + 3 * i, v.intr[3 * i], v.camff_t + FF_CAM * (size_t)i);
+  if (v.ft) {
+    v.ft[i] = f;
+    v.k1t[i] = k1;
+  }
+  if (v.camff_t) ff_camera_record(Rt, v.tt + 3 * i, f, k1, v.camff_t + FF_CAM * (size_t)i);
 }
 
 __global__ void k_to_float(const double *a, float *b, int n) {
@@ -1717,12 +1795,17 @@ rpba_status launch_backsub_trial(Ctx *ctx, const int *run_dev) {
   if (ctx->opt.precision == 1 && ctx->ytot)
     RPBA_KERNEL(ctx, "k_to_float", k_to_float<<<nblk(ctx->ytot, 256), 256, 0, ctx->stream>>>(ctx->dC, ctx->dC32, ctx->ytot));
   if (ctx->P) {
-    if (ctx->opt.precision == 1)
-      RPBA_KERNEL(ctx, "k_backsub_f32", k_backsub<float><<<nblk(ctx->P, ctx->tune.backsub), ctx->tune.backsub, 0, ctx->stream>>>(v, run_dev, nullptr,
-                                                                   (const float *)ctx->Ninv, (const float *)ctx->gX));
+    dim3 g(nblk(ctx->P, ctx->tune.backsub)), b(ctx->tune.backsub);
+    const double *nxc = (const double *)ctx->NXC, *ninv = (const double *)ctx->Ninv, *gx = (const double *)ctx->gX;
+    const float *ninv32 = (const float *)ctx->Ninv, *gx32 = (const float *)ctx->gX;
+    if (ctx->opt.precision == 1 && ctx->cd == 8)
+      RPBA_KERNEL(ctx, "k_backsub_f32", k_backsub<float, 8><<<g, b, 0, ctx->stream>>>(v, run_dev, nullptr, ninv32, gx32));
+    else if (ctx->opt.precision == 1)
+      RPBA_KERNEL(ctx, "k_backsub_f32", k_backsub<float, 6><<<g, b, 0, ctx->stream>>>(v, run_dev, nullptr, ninv32, gx32));
+    else if (ctx->cd == 8)
+      RPBA_KERNEL(ctx, "k_backsub_f64", k_backsub<double, 8><<<g, b, 0, ctx->stream>>>(v, run_dev, nxc, ninv, gx));
     else
-      RPBA_KERNEL(ctx, "k_backsub_f64", k_backsub<double><<<nblk(ctx->P, ctx->tune.backsub), ctx->tune.backsub, 0, ctx->stream>>>(v, run_dev, (const double *)ctx->NXC,
-                                                                    (const double *)ctx->Ninv, (const double *)ctx->gX));
+      RPBA_KERNEL(ctx, "k_backsub_f64", k_backsub<double, 6><<<g, b, 0, ctx->stream>>>(v, run_dev, nxc, ninv, gx));
   }
   if (ctx->M) RPBA_KERNEL(ctx, "k_cam_trial", k_cam_trial<<<nblk(ctx->M, 128), 128, 0, ctx->stream>>>(v, run_dev));
   return sub_costs_impl(ctx, 1, run_dev, ctx->lm_Ft);
@@ -1784,6 +1867,10 @@ __global__ void k_lm_apply_cams(View v, const int *acc) {
   double *t = const_cast<double *>(v.t) + 3 * i;
   for (int e = 0; e < 9; e++) R[e] = v.Rt[9 * i + e];
   for (int e = 0; e < 3; e++) t[e] = v.tt[3 * i + e];
+  if (v.ft) {
+    v.intr[3 * i] = v.ft[i];
+    v.k1[i] = v.k1t[i];
+  }
   if (v.camff)
     for (int e = 0; e < FF_CAM; e++) v.camff[FF_CAM * (size_t)i + e] = v.camff_t[FF_CAM * (size_t)i + e];
 }

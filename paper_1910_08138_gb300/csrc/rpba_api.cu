@@ -68,7 +68,7 @@ __global__ void k_R_to_pose(int M, const double *R, const double *t, double *pos
 
 // C_j = N_j^-1 with N_j = sum_k w A_X^T W A_X over all observations of j
 __global__ void k_covariance(int n, const int *ids, const double *R, const double *t, const double *intr,
-                             const double *X, const uint8_t *active, const int *pt_inst_ptr, const int *pt_inst,
+                             const double *k1, const double *X, const uint8_t *active, const int *pt_inst_ptr, const int *pt_inst,
                              const int *inst_obs_ptr, const int *obs_cam, const double *obs_winv, int has_winv,
                              const double *obs_w, int N, double *out) {
   int a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -89,15 +89,23 @@ __global__ void k_covariance(int n, const int *ids, const double *R, const doubl
           Xc[r] = RX[r] + t[3 * i + r];
         }
         if (!(Xc[2] > 0.0)) { ok = false; break; }
-        ProjJac<double> pj;
-        project_jac<double>(Rl, Xc, RX, intr[3 * i], intr[3 * i + 1], intr[3 * i + 2], pj);
+        double Jx[6];
+        if (k1) {  // per-camera intrinsics: the radial term
+          ProjJac<double, 8> pj;
+          project_jac<double, 8>(Rl, Xc, RX, intr[3 * i], k1[i], intr[3 * i + 1], intr[3 * i + 2], pj);
+          for (int e = 0; e < 6; e++) Jx[e] = pj.Jx[e];
+        } else {
+          ProjJac<double, 6> pj;
+          project_jac<double, 6>(Rl, Xc, RX, intr[3 * i], 0.0, intr[3 * i + 1], intr[3 * i + 2], pj);
+          for (int e = 0; e < 6; e++) Jx[e] = pj.Jx[e];
+        }
         double W0 = 1, W1 = 0, W2 = 1;
         if (has_winv) { W0 = obs_winv[3 * k]; W1 = obs_winv[3 * k + 1]; W2 = obs_winv[3 * k + 2]; }
         double w = obs_w[k];
         for (int r = 0; r < 3; r++)
           for (int c = r; c < 3; c++) {
-            double a0 = W0 * pj.Jx[c] + W1 * pj.Jx[3 + c], a1 = W1 * pj.Jx[c] + W2 * pj.Jx[3 + c];
-            Nm[s3idx(r, c)] += w * (pj.Jx[r] * a0 + pj.Jx[3 + r] * a1);
+            double a0 = W0 * Jx[c] + W1 * Jx[3 + c], a1 = W1 * Jx[c] + W2 * Jx[3 + c];
+            Nm[s3idx(r, c)] += w * (Jx[r] * a0 + Jx[3 + r] * a1);
           }
       }
     }
@@ -228,7 +236,10 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   // solver 4 (auto): lock-step PCG runs as many iterations as its slowest
   // sub-block needs, a maximum that grows with the number of sub-blocks; the
   // direct solve's critical path is set by the largest sub-block alone
-  if (ctx->opt.solver == 4) {
+  ctx->cd = ctx->opt.intrinsics ? 8 : 6;
+  if (ctx->opt.solver == 4 && ctx->cd == 8) {
+    ctx->opt.solver = 2;  // the PCG solvers take 6 x 6 camera blocks
+  } else if (ctx->opt.solver == 4) {
     ctx->auto_solver = true;
     ctx->opt.solver = L <= RPBA_AUTO_PCG_MAX_SUBBLOCKS ? 1 : 2;
   }
@@ -450,7 +461,7 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   long long stot = 0;
   int yt = 0, maxT = 0;
   for (int l = 0; l < L; l++) {
-    int n = 6 * (scp[l + 1] - scp[l]);
+    int n = ctx->cd * (scp[l + 1] - scp[l]);
     int T = (n + RPBA_TILE - 1) / RPBA_TILE;
     npad[l] = T * RPBA_TILE;
     ntiles[l] = T;
@@ -515,6 +526,14 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   RPBA_TRY(alloc_n(ctx, &ctx->Rt, 9 * (size_t)M));
   RPBA_TRY(alloc_n(ctx, &ctx->tt, 3 * (size_t)M));
   RPBA_TRY(upload(ctx, &ctx->intr, pb->cam_intr, 3 * (size_t)M));
+  if (ctx->cd == 8) {  // per-camera intrinsics: k1 and the trial f, k1
+    std::vector<double> k1(std::max(M, 1), 0.0);
+    if (pb->cam_k1)
+      for (int i = 0; i < M; i++) k1[i] = pb->cam_k1[i];
+    RPBA_TRY(upload(ctx, &ctx->k1, k1.data(), k1.size()));
+    RPBA_TRY(alloc_n(ctx, &ctx->ft, (size_t)std::max(M, 1)));
+    RPBA_TRY(alloc_n(ctx, &ctx->k1t, (size_t)std::max(M, 1)));
+  }
   RPBA_TRY(upload(ctx, &ctx->cam_sub, pb->cam_subblock, (size_t)M));
   RPBA_TRY(upload(ctx, &ctx->cam_local, cam_local.data(), (size_t)M));
   RPBA_TRY(upload(ctx, &ctx->sub_cam_ptr, scp.data(), (size_t)L + 1));
@@ -634,8 +653,8 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   }
   RPBA_TRY(alloc_n(ctx, &ctx->obs_w, (size_t)K));
   if (ctx->opt.precision != 1) {  // the FP32 form keeps the Jacobian blocks in registers
-    RPBA_TRY(dev_alloc(ctx, &ctx->NXC, 18 * (size_t)K * rs));
-    RPBA_TRY(dev_alloc(ctx, &ctx->Z, 18 * (size_t)K * rs));
+    RPBA_TRY(dev_alloc(ctx, &ctx->NXC, 3 * (size_t)ctx->cd * K * rs));
+    RPBA_TRY(dev_alloc(ctx, &ctx->Z, 3 * (size_t)ctx->cd * K * rs));
   }
   if (ctx->opt.precision == 1) {
     RPBA_TRY(upload(ctx, &ctx->spair_a, spa.data(), spa.size()));
@@ -750,8 +769,9 @@ extern "C" rpba_status rpba_create(const rpba_problem *prob, const rpba_options 
   if ((ctx->opt.precision != 0 && ctx->opt.precision != 1) || ctx->opt.solver < 0 || ctx->opt.solver > 4 ||
       ctx->opt.ir_steps < 0 || ctx->opt.ir_steps > 20 || ctx->opt.pcg_max_iter < 1 || !(ctx->opt.pcg_tol > 0.0) ||
       ctx->opt.chol_tc < 0 || ctx->opt.chol_tc > 2 || ctx->opt.weight_mode < 0 || ctx->opt.weight_mode > 2 ||
-      !(ctx->opt.rho0 > 0.0)) {
-    ctx->err = "invalid precision / solver / ir_steps option";
+      !(ctx->opt.rho0 > 0.0) || ctx->opt.intrinsics < 0 || ctx->opt.intrinsics > 1 ||
+      (ctx->opt.intrinsics && (ctx->opt.solver == 1 || ctx->opt.solver == 3))) {
+    ctx->err = "invalid precision / solver / ir_steps / intrinsics option";
     *out = h;
     return RPBA_ERR_INVALID_ARG;
   }
@@ -950,6 +970,49 @@ extern "C" rpba_status rpba_set_points(rpba_ctx *h, const double *X, const uint8
   return sync(ctx);
 }
 
+extern "C" rpba_status rpba_get_intrinsics(rpba_ctx *h, double *fk) {
+  CTX_KEEP_COSTS;
+  if (!fk) return RPBA_ERR_INVALID_ARG;
+  const int M = ctx->M;
+  std::vector<double> intr(3 * (size_t)M), k1(M, 0.0);
+  if (M) RPBA_CUDA(cudaMemcpyAsync(intr.data(), ctx->intr, intr.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+  if (M && ctx->k1)
+    RPBA_CUDA(cudaMemcpyAsync(k1.data(), ctx->k1, M * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  RPBA_TRY(sync(ctx));
+  for (int i = 0; i < M; i++) {
+    fk[2 * i] = intr[3 * (size_t)i];
+    fk[2 * i + 1] = k1[i];
+  }
+  return RPBA_OK;
+}
+
+// sets f and k1 of every camera; the FP32 form's camera records follow
+extern "C" rpba_status rpba_set_intrinsics(rpba_ctx *h, const double *fk) {
+  CTX_OR_FAIL;
+  if (!fk) return RPBA_ERR_INVALID_ARG;
+  const int M = ctx->M;
+  std::vector<double> intr(3 * (size_t)M), k1(M);
+  if (M) RPBA_CUDA(cudaMemcpyAsync(intr.data(), ctx->intr, intr.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+  RPBA_TRY(sync(ctx));
+  for (int i = 0; i < M; i++) {
+    if (!(fk[2 * i] > 0.0) || !isfinite(fk[2 * i + 1]) ||
+        (ctx->cd == 6 && (fk[2 * i] != intr[3 * (size_t)i] || fk[2 * i + 1] != 0.0))) {
+      ctx->err = "intrinsics: f must be positive and k1 finite; without the intrinsics option they are fixed";
+      return RPBA_ERR_INVALID_ARG;
+    }
+    intr[3 * (size_t)i] = fk[2 * i];
+    k1[i] = fk[2 * i + 1];
+  }
+  if (M) RPBA_CUDA(cudaMemcpyAsync(ctx->intr, intr.data(), intr.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+  if (M && ctx->k1)
+    RPBA_CUDA(cudaMemcpyAsync(ctx->k1, k1.data(), M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  RPBA_TRY(sync_mirrors(ctx));
+  return sync(ctx);
+}
+
 extern "C" rpba_status rpba_get_points(rpba_ctx *h, double *X, uint8_t *active) {
   CTX_KEEP_COSTS;
   if (X) RPBA_TRY(rows_out(ctx, ctx->X, X, ctx->N, 3, ctx->d_pt_inv));
@@ -1023,10 +1086,11 @@ extern "C" rpba_status rpba_jacobians(rpba_ctx *h, double *Jc, double *Jx) {
   CTX_OR_FAIL;
   if (!Jc || !Jx) return RPBA_ERR_INVALID_ARG;
   Tmp a(ctx), b(ctx);
-  RPBA_TRY(a.alloc(12 * (size_t)ctx->K * sizeof(double)));
+  RPBA_TRY(a.alloc(2 * (size_t)ctx->cd * ctx->K * sizeof(double)));
   RPBA_TRY(b.alloc(6 * (size_t)ctx->K * sizeof(double)));
   RPBA_TRY(launch_jacobians(ctx, (double *)a.p, (double *)b.p));
-  RPBA_CUDA(cudaMemcpyAsync(Jc, a.p, 12 * (size_t)ctx->K * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  RPBA_CUDA(cudaMemcpyAsync(Jc, a.p, 2 * (size_t)ctx->cd * ctx->K * sizeof(double), cudaMemcpyDeviceToHost,
+                            ctx->stream));
   RPBA_CUDA(cudaMemcpyAsync(Jx, b.p, 6 * (size_t)ctx->K * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   return sync(ctx);
 }
@@ -1085,7 +1149,7 @@ extern "C" rpba_status rpba_covariance(rpba_ctx *h, const int32_t *ids, int32_t 
     idi[e] = ctx->h_pt_perm[ids[e]];
   }
   RPBA_CUDA(cudaMemcpyAsync(di.p, idi.data(), n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
-  RPBA_KERNEL(ctx, "k_covariance", k_covariance<<<nblk(n, 128), 128, 0, ctx->stream>>>(n, (const int *)di.p, ctx->R, ctx->t, ctx->intr, ctx->X,
+  RPBA_KERNEL(ctx, "k_covariance", k_covariance<<<nblk(n, 128), 128, 0, ctx->stream>>>(n, (const int *)di.p, ctx->R, ctx->t, ctx->intr, ctx->cd == 8 ? ctx->k1 : nullptr, ctx->X,
                                                      ctx->active, ctx->pt_inst_ptr, ctx->pt_inst, ctx->inst_obs_ptr,
                                                      ctx->obs_cam, ctx->obs_winv, ctx->has_winv, ctx->obs_w, ctx->N,
                                                      (double *)dout.p));
@@ -1107,7 +1171,7 @@ extern "C" rpba_status rpba_rcs(rpba_ctx *h, int32_t l, double lambda, double *S
   RPBA_TRY(launch_fill_int(ctx, ctx->lm_run, ctx->L, 0));
   RPBA_TRY(launch_fill_int(ctx, ctx->lm_run + l, 1, 1));
   RPBA_TRY(launch_build_rcs(ctx, ctx->lm_lambda, ctx->lm_run));
-  int n = 6 * (ctx->h_sub_cam_ptr[l + 1] - ctx->h_sub_cam_ptr[l]);
+  int n = ctx->cd * (ctx->h_sub_cam_ptr[l + 1] - ctx->h_sub_cam_ptr[l]);
   int np = ctx->h_npad[l];
   std::vector<double> full((size_t)np * np), yf(np);
   if (np) {
@@ -1169,7 +1233,7 @@ extern "C" rpba_status rpba_lm_step(rpba_ctx *h, double lambda, int32_t *accepte
   if (dc) {
     int o = 0, yo = 0;
     for (int l = 0; l < L; l++) {
-      int n = 6 * (ctx->h_sub_cam_ptr[l + 1] - ctx->h_sub_cam_ptr[l]);
+      int n = ctx->cd * (ctx->h_sub_cam_ptr[l + 1] - ctx->h_sub_cam_ptr[l]);
       for (int r = 0; r < n; r++) dc[o + r] = dCh[yo + r];
       o += n;
       yo += ctx->h_npad[l];
@@ -1464,8 +1528,8 @@ static std::string tune_signature(const Ctx *ctx) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   char b[160];
-  snprintf(b, sizeof(b), "M%d_N%d_K%d_L%d_P%d_prec%d_solver%d_sm%d", ctx->M, ctx->N, ctx->K, ctx->L, ctx->P,
-           ctx->opt.precision, ctx->opt.solver, sms);
+  snprintf(b, sizeof(b), "M%d_N%d_K%d_L%d_P%d_prec%d_solver%d_cd%d_sm%d", ctx->M, ctx->N, ctx->K, ctx->L,
+           ctx->P, ctx->opt.precision, ctx->opt.solver, ctx->cd, sms);
   return b;
 }
 

@@ -104,38 +104,87 @@ __device__ inline void rodrigues(const double w[3], double R[9]) {
 // Projection g_k (Sec. 2) of a camera-frame point Xc and its Jacobians.
 // RX = R X (camera frame before the translation) enters the rotation part:
 // d Xc / d dw = -[R X]x for R' = exp([dw]x) R; d Xc / dt = I; d Xc / dX = R.
-template <typename T>
+// CD = 6: pinhole, camera unknowns (dw, dt). CD = 8: per-camera intrinsics
+// (the Final data sets of Sec. 6), the first radial parameter on the
+// normalised coordinates p = (x_c, y_c)/z_c, (u, v) = f (1 + k1 |p|^2) p +
+// (cx, cy), camera unknowns (dw, dt, df, dk1). Jc is 2 x CD row-major.
+template <typename T, int CD = 6>
 struct ProjJac {
-  T u, v;     // projection
-  T Jc[12];   // 2x6
-  T Jx[6];    // 2x3
+  T u, v;          // projection
+  T Jc[2 * CD];    // 2 x CD
+  T Jx[6];         // 2 x 3
 };
 
-template <typename T>
-__device__ inline void project_jac(const T R[9], const T Xc[3], const T RX[3], T f, T cx, T cy,
-                                   ProjJac<T> &o) {
+template <typename T, int CD = 6>
+__device__ inline void project_jac(const T R[9], const T Xc[3], const T RX[3], T f, T k1, T cx, T cy,
+                                   ProjJac<T, CD> &o) {
   T iz = T(1) / Xc[2];
-  T fx = f * iz;
   T px = Xc[0] * iz, py = Xc[1] * iz;
-  o.u = fx * Xc[0] + cx;
-  o.v = fx * Xc[1] + cy;
-  // P = d(u,v)/dXc = fx [[1, 0, -px], [0, 1, -py]]
-  // Jx = P R
-  for (int c = 0; c < 3; c++) {
-    o.Jx[c] = fx * (R[c] - px * R[6 + c]);
-    o.Jx[3 + c] = fx * (R[3 + c] - py * R[6 + c]);
-  }
-  // rotation part: P * (-[RX]x); -[a]x = [[0, a2, -a1], [-a2, 0, a0], [a1, -a0, 0]]
   T a0 = RX[0], a1 = RX[1], a2 = RX[2];
-  o.Jc[0] = fx * (0 - px * a1);
-  o.Jc[1] = fx * (a2 + px * a0);
-  o.Jc[2] = fx * (-a1);
-  o.Jc[6] = fx * (-a2 - py * a1);
-  o.Jc[7] = fx * (py * a0);
-  o.Jc[8] = fx * (a0);
-  // translation part: P
-  o.Jc[3] = fx; o.Jc[4] = 0; o.Jc[5] = -fx * px;
-  o.Jc[9] = 0; o.Jc[10] = fx; o.Jc[11] = -fx * py;
+  if constexpr (CD == 6) {
+    T fx = f * iz;
+    o.u = fx * Xc[0] + cx;
+    o.v = fx * Xc[1] + cy;
+    // P = d(u,v)/dXc = fx [[1, 0, -px], [0, 1, -py]]
+    // Jx = P R
+    for (int c = 0; c < 3; c++) {
+      o.Jx[c] = fx * (R[c] - px * R[6 + c]);
+      o.Jx[3 + c] = fx * (R[3 + c] - py * R[6 + c]);
+    }
+    // rotation part: P * (-[RX]x); -[a]x = [[0, a2, -a1], [-a2, 0, a0], [a1, -a0, 0]]
+    o.Jc[0] = fx * (0 - px * a1);
+    o.Jc[1] = fx * (a2 + px * a0);
+    o.Jc[2] = fx * (-a1);
+    o.Jc[6] = fx * (-a2 - py * a1);
+    o.Jc[7] = fx * (py * a0);
+    o.Jc[8] = fx * (a0);
+    // translation part: P
+    o.Jc[3] = fx; o.Jc[4] = 0; o.Jc[5] = -fx * px;
+    o.Jc[9] = 0; o.Jc[10] = fx; o.Jc[11] = -fx * py;
+  } else {
+    T r2 = px * px + py * py;
+    T d = T(1) + k1 * r2;
+    T fd = f * d;
+    o.u = fd * px + cx;
+    o.v = fd * py + cy;
+    // d(u,v)/dp = f (d I + 2 k1 p p^T) = [[D00, D01], [D01, D11]]
+    T a = T(2) * k1 * f;
+    T D00 = fd + a * px * px, D01 = a * px * py, D11 = fd + a * py * py;
+    // P = d(u,v)/dXc = D (1/z) [[1, 0, -px], [0, 1, -py]]
+    T P[6] = {iz * D00, iz * D01, -iz * (D00 * px + D01 * py),
+              iz * D01, iz * D11, -iz * (D01 * px + D11 * py)};
+    for (int r = 0; r < 2; r++) {
+      const T *Pr = P + 3 * r;
+      for (int c = 0; c < 3; c++) o.Jx[3 * r + c] = Pr[0] * R[c] + Pr[1] * R[3 + c] + Pr[2] * R[6 + c];
+      T *J = o.Jc + CD * r;
+      J[0] = Pr[1] * (-a2) + Pr[2] * a1;
+      J[1] = Pr[0] * a2 - Pr[2] * a0;
+      J[2] = -Pr[0] * a1 + Pr[1] * a0;
+      J[3] = Pr[0]; J[4] = Pr[1]; J[5] = Pr[2];
+      T pr = r == 0 ? px : py;
+      J[6] = d * pr;       // d/df
+      J[7] = f * r2 * pr;  // d/dk1
+    }
+  }
+}
+
+// FP64 projection of X by camera (R, t, f, k1, cx, cy); returns z_c. With
+// k1 = 0 the pinhole expression (f x_c / z_c + cx) as written everywhere else.
+__device__ inline double proj64(const double *R, const double *t, double f, double k1, double cx, double cy,
+                                const double *X, double &u, double &v) {
+  double Xc[3];
+  for (int r = 0; r < 3; r++) Xc[r] = R[3 * r] * X[0] + R[3 * r + 1] * X[1] + R[3 * r + 2] * X[2] + t[r];
+  double iz = 1.0 / Xc[2];
+  if (k1 == 0.0) {
+    u = f * Xc[0] * iz + cx;
+    v = f * Xc[1] * iz + cy;
+  } else {
+    double px = Xc[0] * iz, py = Xc[1] * iz;
+    double fd = f * (1.0 + k1 * (px * px + py * py));
+    u = fd * px + cx;
+    v = fd * py + cy;
+  }
+  return Xc[2];
 }
 
 // ---------------------------------------------------------------------------
@@ -222,6 +271,10 @@ struct Ctx {
 
   // cameras
   double *R = nullptr, *t = nullptr, *intr = nullptr, *Rt = nullptr, *tt = nullptr;
+  // per-camera intrinsics (opt.intrinsics): cd = 8 camera unknowns, the
+  // radial parameter k1 (and f in intr) estimated, trial f and k1
+  int cd = 6;
+  double *k1 = nullptr, *ft = nullptr, *k1t = nullptr;
   int *cam_sub = nullptr, *cam_local = nullptr, *sub_cam_ptr = nullptr, *sub_cam = nullptr;
   int *cam_obs_ptr = nullptr, *cam_obs = nullptr;
   double *cam_sigma = nullptr;

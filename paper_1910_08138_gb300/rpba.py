@@ -30,7 +30,7 @@ class Problem(C.Structure):
     _fields_ = [("n_cams", C.c_int32), ("n_points", C.c_int32), ("n_obs", C.c_int32),
                 ("cam_pose", _dp), ("cam_intr", _dp), ("points", _dp), ("obs_cam", _ip),
                 ("obs_point", _ip), ("obs_xy", _dp), ("obs_winv", _dp), ("cam_subblock", _ip),
-                ("cam_block", _ip)]
+                ("cam_block", _ip), ("cam_k1", _dp)]
 
 
 class Options(C.Structure):
@@ -42,7 +42,8 @@ class Options(C.Structure):
                 ("isect_tol", C.c_double), ("isect_px_tol", C.c_double), ("cond_max", C.c_double),
                 ("precision", C.c_int32),
                 ("solver", C.c_int32), ("pcg_tol", C.c_double), ("pcg_max_iter", C.c_int32),
-                ("ir_steps", C.c_int32), ("chol_tc", C.c_int32), ("tune_cache", C.c_char_p),
+                ("ir_steps", C.c_int32), ("chol_tc", C.c_int32), ("intrinsics", C.c_int32),
+                ("tune_cache", C.c_char_p),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", C.c_void_p)]
 
 
@@ -118,6 +119,8 @@ def load(build_if_missing: bool = True):
         "rpba_partition": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _ip, _ip, C.c_int32, _ip, _dp,
                                      C.POINTER(C.c_double)]),
         "rpba_get_camera_rt": (C.c_int, [vp, _dp, _dp]),
+        "rpba_get_intrinsics": (C.c_int, [vp, _dp]),
+        "rpba_set_intrinsics": (C.c_int, [vp, _dp]),
         "rpba_set_camera_rt": (C.c_int, [vp, _dp, _dp]),
         "rpba_set_subblock_mask": (C.c_int, [vp, C.c_void_p]),
         "rpba_set_point_mask": (C.c_int, [vp, C.c_void_p]),
@@ -272,10 +275,12 @@ def rpba_create(problem: dict, options: Options | None = None, stream=None, torc
     arrs["obs_winv"] = None if winv is None else _f64(winv, (K, 3))
     blk = problem.get("cam_block")
     arrs["cam_block"] = None if blk is None else _i32(blk)
+    k1 = problem.get("cam_k1")
+    arrs["cam_k1"] = None if k1 is None else _f64(k1, (M,))
     keep["arrs"] = arrs
     pb = Problem(M, N, K, _d(arrs["cam_pose"]), _d(arrs["cam_intr"]), _d(arrs["points"]),
                  _i(arrs["obs_cam"]), _i(arrs["obs_point"]), _d(arrs["obs_xy"]), _d(arrs["obs_winv"]),
-                 _i(arrs["cam_subblock"]), _i(arrs["cam_block"]))
+                 _i(arrs["cam_subblock"]), _i(arrs["cam_block"]), _d(arrs["cam_k1"]))
     opt = options if options is not None else rpba_default_options()
     if torch_alloc:
         import torch
@@ -298,10 +303,13 @@ def rpba_create(problem: dict, options: Options | None = None, stream=None, torc
 
 
 class Rpba:
-    """One library context over a problem dict (same keys as the C struct)."""
+    """One library context over a problem dict (same keys as the C struct).
+    The intrinsics option defaults to the problem's "intrinsics" entry."""
 
     def __init__(self, problem, stream=None, torch_alloc=False, **options):
+        options.setdefault("intrinsics", int(bool(problem.get("intrinsics", False))))
         self.options = rpba_default_options(**options)
+        self.cd = 8 if self.options.intrinsics else 6
         self._h, self._keep = rpba_create(problem, self.options, stream=stream, torch_alloc=torch_alloc)
         self.M = int(problem["cam_pose"].shape[0])
         self.N = int(problem["points"].shape[0])
@@ -375,6 +383,15 @@ class Rpba:
     def set_cameras(self, pose):
         self._c(load().rpba_set_cameras(self._h, _d(_f64(pose, (self.M, 6)))))
 
+    def intrinsics(self):
+        """(n_cams x 2): focal length and radial parameter k1 of every camera."""
+        fk = np.zeros((self.M, 2))
+        self._c(load().rpba_get_intrinsics(self._h, _d(fk)))
+        return fk
+
+    def set_intrinsics(self, fk):
+        self._c(load().rpba_set_intrinsics(self._h, _d(_f64(fk, (self.M, 2)))))
+
     def set_points(self, X, active=None):
         a = None if active is None else np.ascontiguousarray(active, dtype=np.uint8)
         self._c(load().rpba_set_points(self._h, _d(_f64(X, (self.N, 3))),
@@ -407,9 +424,9 @@ class Rpba:
         return v
 
     def jacobians(self):
-        Jc, Jx = np.zeros((self.K, 12)), np.zeros((self.K, 6))
+        Jc, Jx = np.zeros((self.K, 2 * self.cd)), np.zeros((self.K, 6))
         self._c(load().rpba_jacobians(self._h, _d(Jc), _d(Jx)))
-        return Jc.reshape(self.K, 2, 6), Jx.reshape(self.K, 2, 3)
+        return Jc.reshape(self.K, 2, self.cd), Jx.reshape(self.K, 2, 3)
 
     def sigma0(self):
         s, r = C.c_double(), C.c_double()
@@ -437,7 +454,7 @@ class Rpba:
         return F
 
     def rcs(self, l, lam):
-        n = 6 * len(self.sub_cameras(l))
+        n = self.cd * len(self.sub_cameras(l))
         S, y = np.zeros((n, n)), np.zeros(n)
         self._c(load().rpba_rcs(self._h, l, float(lam), _d(S), _d(y)))
         return S, y
@@ -445,7 +462,7 @@ class Rpba:
     def lm_step(self, lam):
         acc = np.zeros(self.L, np.int32)
         Fb, Ft = np.zeros(self.L), np.zeros(self.L)
-        dc, dx = np.zeros(6 * self.M), np.zeros((self.P, 3))
+        dc, dx = np.zeros(self.cd * self.M), np.zeros((self.P, 3))
         self._c(load().rpba_lm_step(self._h, float(lam), _i(acc), _d(Fb), _d(Ft), _d(dc), _d(dx)))
         return acc, Fb, Ft, dc, dx
 

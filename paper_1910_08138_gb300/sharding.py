@@ -43,6 +43,9 @@ class ShardPlan:
 
     def __init__(self, prob, world: int, rank: int, inst_point=None, inst_sub=None):
         self.world, self.rank = int(world), int(rank)
+        # camera unknowns: 6, or 8 with per-camera intrinsics (f and k1 travel
+        # with each camera's rotation and translation)
+        self.cd = 8 if prob.get("intrinsics", False) else 6
         cam_sub = np.asarray(prob["cam_subblock"], dtype=np.int64)
         obs_cam = np.asarray(prob["obs_cam"], dtype=np.int64)
         obs_pt = np.asarray(prob["obs_point"], dtype=np.int64)
@@ -52,7 +55,7 @@ class ShardPlan:
         # sub-blocks to ranks: cost ~ observations + (6 M_l)^3 / 3 of its solve
         m_l = np.bincount(cam_sub, minlength=self.L).astype(np.float64)
         k_l = np.bincount(obs_sub, minlength=self.L).astype(np.float64)
-        cost = k_l * 1000.0 + (6.0 * m_l) ** 3 / 3.0
+        cost = k_l * 1000.0 + (float(self.cd) * m_l) ** 3 / 3.0
         load = np.zeros(self.world)
         self.sub_rank = np.zeros(self.L, dtype=np.int64)
         for l in sorted(range(self.L), key=lambda x: (-cost[x], x)):
@@ -115,10 +118,11 @@ class ShardPlan:
 
     def exchange_bytes(self):
         """Bytes this rank sends per outer iteration: its cameras (rotation
-        matrix and translation, 12 doubles) to every other rank, its TPs' records (X_TP and the active flag: 4
+        matrix and translation, 12 doubles, with intrinsics also f and k1) to
+        every other rank, its TPs' records (X_TP and the active flag: 4
         doubles, W^l: 6 per receiving instance) and the robust weights of TP
         observations (1 double each)."""
-        b = 8 * 12 * self.own_cams.size * (self.world - 1)
+        b = 8 * (12 + self.cd - 6) * self.own_cams.size * (self.world - 1)
         for d in self.tp_send:
             b += 8 * (4 * self.tp_send[d].size + 6 * self.tpi_send[d].size + self.w_send[d].size)
         return b
@@ -188,14 +192,16 @@ class SoloComm:
 # ---------------------------------------------------------------------------
 def _exchange_cameras(engine, plan, comm):
     """All-gather of the cameras as held: rotation matrix and translation
-    (12 doubles each), so that every rank holds the same bits."""
+    (12 doubles each; with intrinsics 14: f and k1 too), so that every rank
+    holds the same bits."""
     rt = engine.cameras()
+    width = rt.shape[1]
     send = {d: rt[plan.own_cams].reshape(-1) for d in range(plan.world) if d != plan.rank}
-    sizes = {s: 12 * plan.cams_of[s].size for s in range(plan.world) if s != plan.rank}
+    sizes = {s: width * plan.cams_of[s].size for s in range(plan.world) if s != plan.rank}
     got = comm.exchange(send, sizes)
     for s, a in got.items():
         if a.size:
-            rt[plan.cams_of[s]] = a.reshape(-1, 12)
+            rt[plan.cams_of[s]] = a.reshape(-1, width)
     engine.set_cameras(rt)
 
 
@@ -254,7 +260,7 @@ def _sigma0(engine, plan, comm):
     """sigma_0 (Eq. sigma0, weights C^-1): the weighted square sum over the
     observations of active points and their count, each rank over the
     observations of its cameras, the active points counted by their owners;
-    r = 2 K - 6 M - 3 N + 7."""
+    r = 2 K - 6 M - 3 N + 7 (8 M with per-camera intrinsics)."""
     v = engine.residuals()
     w = engine.weights()
     _, act = engine.points()
@@ -270,7 +276,7 @@ def _sigma0(engine, plan, comm):
         q = Wk[:, 0] * vv[:, 0] * vv[:, 0] + 2.0 * Wk[:, 1] * vv[:, 0] * vv[:, 1] + Wk[:, 2] * vv[:, 1] * vv[:, 1]
     part = np.array([float(np.sum(w[k] * q)), float(k.size), float(np.sum(act[plan.own_pts] == 1))])
     tot = comm.allreduce_sum(part)
-    red = max(2.0 * tot[1] - 6.0 * plan.M - 3.0 * tot[2] + 7.0, 1.0)
+    red = max(2.0 * tot[1] - float(plan.cd) * plan.M - 3.0 * tot[2] + 7.0, 1.0)
     return float(np.sqrt(tot[0] / red))
 
 
@@ -387,10 +393,17 @@ class RpbaEngine:
         self.ctx.robust_weights()
 
     def cameras(self):
-        return self.ctx.camera_rt()
+        """(M, 12) rotation and translation as held; (M, 14) with f and k1
+        when the context estimates intrinsics."""
+        rt = self.ctx.camera_rt()
+        if self.ctx.options.intrinsics:
+            rt = np.concatenate([rt, self.ctx.intrinsics()], axis=1)
+        return rt
 
     def set_cameras(self, rt):
-        self.ctx.set_camera_rt(rt)
+        self.ctx.set_camera_rt(np.ascontiguousarray(rt[:, :12]))
+        if rt.shape[1] == 14:
+            self.ctx.set_intrinsics(np.ascontiguousarray(rt[:, 12:]))
 
     def points(self):
         return self.ctx.points()

@@ -250,7 +250,12 @@ def config(c: int, scale: float = 1.0, n_blocks: int = 64):
        5 obs/point, 32 sub-blocks, 5 % outliers.
     5: 100x100 positions, nadir and 45 deg obliques, 4M points, 5 obs/point,
        64 sub-blocks, sigma 1 px, 5 % outliers.
+    6: the photo-collection block with per-camera intrinsics (bal_config):
+       961 cameras on a ring, 187,103 points, 18 obs/point, 12 sub-blocks,
+       focal length and k1 estimated per camera, sigma 1 px, 2 % outliers.
     """
+    if c == 6:
+        return bal_config(scale)
     rng = np.random.Generator(np.random.PCG64(SEED_BASE + 100 * c))
     if c == 1:
         return grid_block(rng, 10, 5, 4.0, 30.0, int(2000 * scale), 4, 0.5, 0.02,

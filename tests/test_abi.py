@@ -3,6 +3,7 @@
 import ctypes
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -31,11 +32,30 @@ def test_default_options_are_the_papers_values():
     assert o.stop_ratio == 1.01 and o.grace == 1
 
 
-def test_struct_layouts_match_header():
-    # pointer-sized fields at the end of rpba_options: ctypes and C agree on size
-    assert ctypes.sizeof(rpba.Options) % 8 == 0
-    assert ctypes.sizeof(rpba.Problem) == 3 * 4 + 4 + 9 * 8
-    assert ctypes.sizeof(rpba.Report) == 3 * 8 + 7 * 4 + 4 + 128 * 8
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors of rpba_problem, rpba_options and rpba_report have
+    the size and the field offsets the C compiler gives the header's structs."""
+    structs = {"rpba_problem": rpba.Problem, "rpba_options": rpba.Options, "rpba_report": rpba.Report}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "rpba.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in cls._fields_:
+            lines.append(f'  printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            a, b, c = line.split()
+            got[(a, b)] = int(c)
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for f in cls._fields_:
+            assert got[(cname, f[0])] == getattr(cls, f[0]).offset, (cname, f[0])
 
 
 def test_create_fails_loudly_without_gpu():

@@ -22,7 +22,7 @@ TARGETS = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "orac
 FORMS = {"chosen": (1, 4), "plain": (0, 0)}
 
 
-@pytest.fixture(scope="module", params=[2, 3, 4, 5])
+@pytest.fixture(scope="module", params=[2, 3, 4, 5, 6])
 def block(request):
     return request.param, synth.config(request.param)
 

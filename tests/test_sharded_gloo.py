@@ -48,10 +48,15 @@ class OracleEngine:
         self.o.robust_weights_cams(np.asarray(cams, dtype=np.int32), t_v, downweight)
 
     def cameras(self):
-        return self.o.camera_rt()
+        rt = self.o.camera_rt()
+        if self.o.cd == 8:  # per-camera intrinsics travel with the camera
+            rt = np.concatenate([rt, self.o.intrinsics()], axis=1)
+        return rt
 
     def set_cameras(self, rt):
-        self.o.set_camera_rt(rt)
+        self.o.set_camera_rt(rt[:, :12])
+        if rt.shape[1] == 14:
+            self.o.set_intrinsics(rt[:, 12:])
 
     def points(self):
         return self.o.points()
@@ -80,6 +85,9 @@ PROBS = {
     # four uneven sub-blocks, oblique views and 3 % outliers
     "tiny4": lambda: synth.tiny(seed=8, nx=6, ny=4, n_points=300, opp=4, runs=[8, 6, 6, 4], oblique_deg=30,
                                 nadir_every=3, outlier_frac=0.03, extent=(-12.0, 12.0, -8.0, 8.0)),
+    # per-camera intrinsics (8 unknowns per camera), 4 arcs of a ring
+    "ring4": lambda: synth.tiny_intrinsics(seed=8, n_cams=20, n_points=250, mean_track=5.0, n_sub=4,
+                                           outlier_frac=0.02),
 }
 
 
@@ -131,7 +139,7 @@ def _assemble(res):
     return cams, X, act
 
 
-@pytest.mark.parametrize("name,world", [("cfg1", 2), ("tiny4", 2), ("tiny4", 3)])
+@pytest.mark.parametrize("name,world", [("cfg1", 2), ("tiny4", 2), ("tiny4", 3), ("ring4", 2)])
 def test_sharded_run_equals_single_process_run(name, world):
     opts = dict(robust=True, robust_from_start=True)
     prob = PROBS[name]()
@@ -140,7 +148,8 @@ def test_sharded_run_equals_single_process_run(name, world):
     Xo, ao = o.points()
     res = _run_ranks(world, name, opts)
     cams, X, act = _assemble(res)
-    np.testing.assert_array_equal(cams, o.camera_rt())
+    exp = o.camera_rt() if o.cd == 6 else np.concatenate([o.camera_rt(), o.intrinsics()], axis=1)
+    np.testing.assert_array_equal(cams, exp)
     np.testing.assert_array_equal(act, ao)
     np.testing.assert_array_equal(X[ao == 1], Xo[ao == 1])
     for r in res:
