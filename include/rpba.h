@@ -134,7 +134,8 @@ typedef struct {
                             (cam_k1) of every camera are estimated with its pose, 8 unknowns
                             per camera; the projection applies 1 + k1 |p|^2 to the normalised
                             coordinates p = (x_c, y_c)/z_c; the principal point stays fixed.
-                            Solvers 0 and 2 (4 resolves to 2); 1 and 3 give INVALID_ARG.
+                            Solvers 0, 1, 2 and 4; 3 (the learned preconditioner, built on
+                            6 x 6 camera blocks) gives INVALID_ARG.
                             0 (default): intrinsics known, pinhole, 6 unknowns per camera */
   const char *tune_cache; /* NULL, or a file of tuned launch shapes (JSON lines, one object per
                             workload: cameras, points, observations, sub-blocks, precision,

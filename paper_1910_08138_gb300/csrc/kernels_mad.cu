@@ -245,12 +245,14 @@ __global__ void k_camera_mad(int M, MadIn in, const uint8_t *active, const int *
   for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
     int k = cam_obs[p];
     int j = obs_pt[k];
-    if (!active[j]) continue;
     Key k0, k1;
     if constexpr (sizeof(Key) == 4) {  // keys straight from the FP32 components
+      // the active flag is read beside the residual's gathers, not before them
+      const bool act = active[j] != 0;
       float r0, r1;
       ff_residual(in.camff + FF_CAM * (size_t)i, in.Xh + 3 * (size_t)j, in.Xl + 3 * (size_t)j, in.oxy[2 * k],
                   in.oxylo[2 * k], in.oxy[2 * k + 1], in.oxylo[2 * k + 1], r0, r1, K1);
+      if (!act) continue;
       if (has_winv) {
         const float *F = in.whiten32 + 3 * (size_t)k;
         float a = F[0] * r0 + F[1] * r1, b = F[2] * r1;
@@ -260,6 +262,7 @@ __global__ void k_camera_mad(int M, MadIn in, const uint8_t *active, const int *
       k0 = fkey(r0);
       k1 = fkey(r1);
     } else {
+      if (!active[j]) continue;
       double pu, pv;
       proj64(in.R + 9 * i, in.t + 3 * i, in.intr[3 * i], in.k1 ? in.k1[i] : 0.0, in.intr[3 * i + 1],
              in.intr[3 * i + 2], in.X + 3 * j, pu, pv);

@@ -725,7 +725,7 @@ __device__ inline void isect_obs_acc(const View &v, int j, int k, float N[6], fl
 }
 
 __device__ static void isect_fused_step(const View &v, int j, int *state, int *iter, int max_iter, double tol,
-                                        double px_tol, double cond_max, int last) {
+                                        double px_tol, double cond_max, int last, int copies) {
   int q0 = v.pt_inst_ptr[j], q1 = v.pt_inst_ptr[j + 1];
   float N[6] = {0, 0, 0, 0, 0, 0}, g[3] = {0, 0, 0};
   float Nh[6] = {0, 0, 0, 0, 0, 0}, Nl[6] = {0, 0, 0, 0, 0, 0};  // N_j in float-float
@@ -825,6 +825,12 @@ __device__ static void isect_fused_step(const View &v, int j, int *state, int *i
           v.Wl32[6 * (size_t)q + e] = __fadd_rn(w.x, w.y);
         }
       }
+      if (copies)  // the TP copies restart at X_TP (as k_tp_copies writes them)
+        for (int e = 0; e < 3; e++) {
+          v.Xl[3 * (size_t)q + e] = v.X[3 * (size_t)j + e];
+          v.Xl_hi[3 * (size_t)q + e] = v.X_hi[3 * (size_t)j + e];
+          v.Xl_lo[3 * (size_t)q + e] = v.X_lo[3 * (size_t)j + e];
+        }
     }
   }
 }
@@ -832,14 +838,21 @@ __device__ static void isect_fused_step(const View &v, int j, int *state, int *i
 // the points are independent (cameras fixed): each thread runs its point's
 // Gauss-Newton iterations to convergence or failure in one launch. With a
 // list (the TP intersection) the threads cover the listed points only, so no
-// warp lane idles on a point that is not intersected.
-__global__ void k_isect_fused_f(View v, const int *list, int n, int *state, int *iter, int max_iter, double tol,
-                                double px_tol, double cond_max) {
+// warp lane idles on a point that is not intersected; pt_mask given: the
+// listed points (all TPs) set their own start state, in place of
+// k_isect_start. copies: a converged TP also restarts its sub-block copies
+// X^l at X_TP, in place of k_tp_copies.
+__global__ void k_isect_fused_f(View v, const int *list, int n, const uint8_t *pt_mask, int copies, int *state,
+                                int *iter, int max_iter, double tol, double px_tol, double cond_max) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   int j = list ? list[t] : t;
+  if (pt_mask) {
+    state[j] = (v.active[j] && pt_mask[j]) ? 1 : 0;
+    iter[j] = 0;
+  }
   for (int pass = 0; pass < max_iter && state[j] == 1; pass++)
-    isect_fused_step(v, j, state, iter, max_iter, tol, px_tol, cond_max, pass == max_iter - 1);
+    isect_fused_step(v, j, state, iter, max_iter, tol, px_tol, cond_max, pass == max_iter - 1, copies);
 }
 
 __global__ void k_isect_start(View v, const uint8_t *pt_mask, int *state, int *iter, int tp_only, int *count) {
@@ -859,21 +872,28 @@ __global__ void k_isect_count(const int *state, int n, int *running, int *failed
   if (state[j] == 3) atomicAdd(failed, 1);
 }
 
-rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped, bool fp64) {
+rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped, bool fp64, bool tp_copies) {
   View v = make_view(ctx);
   if (ctx->N == 0) { if (n_dropped) *n_dropped = 0; return RPBA_OK; }
-  RPBA_CUDA(cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(int), ctx->stream));
-  RPBA_KERNEL(ctx, "k_isect_start", k_isect_start<<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(
-                                        v, ctx->pt_mask, ctx->isect_state, ctx->isect_iter, tp_only, ctx->counters));
+  const bool fused = ctx->opt.precision == 1 && !fp64;
+  // the TP list launch sets its points' start states itself unless the
+  // dropped points are counted afterwards (that count reads every state)
+  const bool own_start = fused && tp_only && !n_dropped;
+  if (!own_start) {
+    RPBA_CUDA(cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(int), ctx->stream));
+    RPBA_KERNEL(ctx, "k_isect_start", k_isect_start<<<nblk(ctx->N, 256), 256, 0, ctx->stream>>>(
+                                          v, ctx->pt_mask, ctx->isect_state, ctx->isect_iter, tp_only, ctx->counters));
+  }
   int maxit = ctx->opt.isect_max_iter;
   double tol = ctx->opt.isect_tol;
   double px_tol = ctx->opt.isect_px_tol;
-  if (ctx->opt.precision == 1 && !fp64) {  // FP32 form: every point's iterations in one launch
+  if (fused) {  // FP32 form: every point's iterations in one launch
     const int *list = tp_only ? ctx->tp_list : nullptr;
     int n = tp_only ? ctx->n_tp : ctx->N;
     if (n)
       RPBA_KERNEL(ctx, "k_isect_fused_f", k_isect_fused_f<<<nblk(n, ctx->tune.isect), ctx->tune.isect, 0, ctx->stream>>>(
-                                            v, list, n, ctx->isect_state, ctx->isect_iter, maxit, tol, px_tol,
+                                            v, list, n, own_start ? ctx->pt_mask : nullptr, tp_copies && tp_only ? 1 : 0,
+                                            ctx->isect_state, ctx->isect_iter, maxit, tol, px_tol,
                                             ctx->opt.cond_max));
   } else {
     for (int it = 0; it < maxit; it++) {
@@ -967,11 +987,12 @@ __global__ void k_robust_weights_f(View v, const float *sigma, float t_v, double
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= v.K) return;
   int j = v.obs_pt[k];
-  if (!v.active[j]) return;
   int i = v.obs_cam[k];
+  const bool act = v.active[j] != 0;  // read beside the residual's gathers, not before them
   float r0, r1;
   ff_residual(v.camff + FF_CAM * (size_t)i, v.X_hi + 3 * (size_t)j, v.X_lo + 3 * (size_t)j, v.obs_xy32[2 * k],
               v.obs_xylo[2 * k], v.obs_xy32[2 * k + 1], v.obs_xylo[2 * k + 1], r0, r1, K1);
+  if (!act) return;
   float W0 = 1.f, W1 = 0.f, W2 = 1.f;
   if (v.has_winv) { W0 = v.obs_winv32[3 * k]; W1 = v.obs_winv32[3 * k + 1]; W2 = v.obs_winv32[3 * k + 2]; }
   float nr = sqrtf(W0 * r0 * r0 + 2.f * W1 * r0 * r1 + W2 * r1 * r1);
@@ -1105,12 +1126,16 @@ struct SigmaAcc {
 // float-float difference X^l - X_TP and W^l in FP32. With SIG the same
 // residual also feeds the observation's sigma_0 terms (Eq. sigma0: every
 // observation of an active point that is not deleted, whatever its depth)
+// The loads do not wait for the point's active flag: the observation's point,
+// camera and instance come from its own streams, so every gather of the term
+// issues after one dependent load; an inactive point's term is dropped at the
+// end.
 template <bool SIG, bool K1>
 __device__ inline float obs_cost_term_f(const View &v, int trial, int k, SigmaAcc *sig = nullptr) {
   int q = v.obs_inst[k];
-  int j = v.inst_pt[q];
-  if (!v.active[j]) return 0.f;
+  int j = v.obs_pt[k];  // = inst_pt[q]
   int i = v.obs_cam[k];
+  const bool act = v.active[j] != 0;
   const float *cf = (trial ? v.camff_t : v.camff) + FF_CAM * (size_t)i;
   const float *Xh = (trial ? v.Xlt_hi : v.Xl_hi) + 3 * (size_t)q;
   const float *Xw = (trial ? v.Xlt_lo : v.Xl_lo) + 3 * (size_t)q;
@@ -1126,7 +1151,7 @@ __device__ inline float obs_cost_term_f(const View &v, int trial, int k, SigmaAc
     float w = v.obs_w32[k];
     F = w * (W0 * r0 * r0 + 2.f * W1 * r0 * r1 + W2 * r1 * r1);
     if constexpr (SIG) {
-      if (w != 0.f) {  // w = 0: deleted by the serial robust variant
+      if (act && w != 0.f) {  // w = 0: deleted by the serial robust variant
         float e;
         sig->sh = ff_two_sum(sig->sh, F, e);
         sig->sl += e;
@@ -1148,7 +1173,7 @@ __device__ inline float obs_cost_term_f(const View &v, int trial, int k, SigmaAc
     F += W[0] * d[0] * d[0] + W[3] * d[1] * d[1] + W[5] * d[2] * d[2] +
          2.f * (W[1] * d[0] * d[1] + W[2] * d[0] * d[2] + W[4] * d[1] * d[2]);
   }
-  return F;
+  return act ? F : 0.f;
 }
 
 // FP32 form, F_l in two deterministic stages without a per-observation array:
@@ -1448,6 +1473,57 @@ __device__ inline void z_of(const float inv[6], const float B[3 * CD], float Zk[
 //   S_ii = U_ii + lambda diag(U_ii) - sum_k N_XC,k^T Z_k,  U_ii = sum_k w A_C^T W A_C
 // and right-hand side y_i = -sum_k w A_C^T W v + sum_k Z_k^T g_X
 #define CB_THREADS 128
+// one observation k (instance q) of camera i: its terms of U, SZ, gc and yz
+// added to acc when act (the point is active)
+template <typename T, int CD>
+__device__ __forceinline__ void cb_obs(const View &v, int i, int k, int q, bool act, const T *NXC, const T *Z,
+                                       const T *gX, const T *Ninv, T *acc) {
+  constexpr int NU = CD * (CD + 1) / 2;
+  ProjJac<T, CD> pj;
+  T z;
+  obs_proj<T, CD>(v, i, v.Xl + 3 * (size_t)q, v.Xl_hi + 3 * (size_t)q, v.Xl_lo + 3 * (size_t)q, pj, z);
+  ObsT<T> ob;
+  load_obs<T>(v, k, ob);
+  T r0 = pj.u - ob.x, r1 = pj.v - ob.y;
+  T b0[CD], b1[CD];  // w W A_C
+#pragma unroll
+  for (int c = 0; c < CD; c++) {
+    b0[c] = ob.w * (ob.W[0] * pj.Jc[c] + ob.W[1] * pj.Jc[CD + c]);
+    b1[c] = ob.w * (ob.W[1] * pj.Jc[c] + ob.W[2] * pj.Jc[CD + c]);
+  }
+  const T *gq = gX + 3 * (size_t)q;
+  T Bl[3 * CD], Zl[3 * CD], g3[3] = {gq[0], gq[1], gq[2]};
+  if constexpr (sizeof(T) == sizeof(float)) {  // N_XC and Z in registers
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+      for (int c = 0; c < CD; c++) {
+        T a0 = ob.w * (ob.W[0] * pj.Jx[r] + ob.W[1] * pj.Jx[3 + r]);
+        T a1 = ob.w * (ob.W[1] * pj.Jx[r] + ob.W[2] * pj.Jx[3 + r]);
+        Bl[CD * r + c] = a0 * pj.Jc[c] + a1 * pj.Jc[CD + c];
+      }
+    const float *iv = Ninv + 6 * (size_t)q;
+    float inv[6] = {iv[0], iv[1], iv[2], iv[3], iv[4], iv[5]};
+    z_of<CD>(inv, Bl, Zl);
+  } else {
+    const T *B = NXC + 3 * CD * (size_t)k, *Zk = Z + 3 * CD * (size_t)k;
+#pragma unroll
+    for (int e = 0; e < 3 * CD; e++) { Bl[e] = B[e]; Zl[e] = Zk[e]; }
+  }
+  if (!act) return;
+  int e = 0;
+#pragma unroll
+  for (int r = 0; r < CD; r++) {
+    acc[2 * NU + r] += b0[r] * r0 + b1[r] * r1;
+    acc[2 * NU + CD + r] += Zl[r] * g3[0] + Zl[CD + r] * g3[1] + Zl[2 * CD + r] * g3[2];
+#pragma unroll
+    for (int c = r; c < CD; c++, e++) {
+      acc[e] += pj.Jc[r] * b0[c] + pj.Jc[CD + r] * b1[c];
+      acc[NU + e] += Bl[r] * Zl[c] + Bl[CD + r] * Zl[CD + c] + Bl[2 * CD + r] * Zl[2 * CD + c];
+    }
+  }
+}
+
 template <typename T, int CD>
 __global__ void __launch_bounds__(CB_THREADS) k_camera_blocks(View v, const double *lambda, const int *run,
                                                               const T *NXC, const T *Z, const T *gX,
@@ -1462,52 +1538,28 @@ __global__ void __launch_bounds__(CB_THREADS) k_camera_blocks(View v, const doub
   T acc[NA];
 #pragma unroll
   for (int e = 0; e < NA; e++) acc[e] = 0;
-  for (int p = v.cam_obs_ptr[i] + threadIdx.x; p < v.cam_obs_ptr[i + 1]; p += CB_THREADS) {
-    int k = v.cam_obs[p];
-    int q = v.obs_inst[k];
-    int j = v.inst_pt[q];
-    if (!v.active[j]) continue;
-    ProjJac<T, CD> pj;
-    T z;
-    obs_proj<T, CD>(v, i, v.Xl + 3 * (size_t)q, v.Xl_hi + 3 * (size_t)q, v.Xl_lo + 3 * (size_t)q, pj, z);
-    ObsT<T> ob;
-    load_obs<T>(v, k, ob);
-    T r0 = pj.u - ob.x, r1 = pj.v - ob.y;
-    T b0[CD], b1[CD];  // w W A_C
-#pragma unroll
-    for (int c = 0; c < CD; c++) {
-      b0[c] = ob.w * (ob.W[0] * pj.Jc[c] + ob.W[1] * pj.Jc[CD + c]);
-      b1[c] = ob.w * (ob.W[1] * pj.Jc[c] + ob.W[2] * pj.Jc[CD + c]);
+  const int p1 = v.cam_obs_ptr[i + 1];
+  if constexpr (sizeof(T) == sizeof(float)) {
+    // the observation list walked one element ahead: the next observation's
+    // position and instance load while this one's arithmetic runs, and the
+    // point's active flag is read beside this one's gathers, not before them
+    int p = v.cam_obs_ptr[i] + threadIdx.x;
+    int k = p < p1 ? v.cam_obs[p] : 0;
+    int q = p < p1 ? v.obs_inst[k] : 0;
+    for (; p < p1; p += CB_THREADS) {
+      const int pn = p + CB_THREADS;
+      const int kn = pn < p1 ? v.cam_obs[pn] : 0;
+      const bool act = v.active[v.obs_pt[k]] != 0;
+      cb_obs<T, CD>(v, i, k, q, act, NXC, Z, gX, Ninv, acc);
+      k = kn;
+      q = pn < p1 ? v.obs_inst[kn] : 0;
     }
-    const T *gq = gX + 3 * (size_t)q;
-    T Bl[3 * CD], Zl[3 * CD], g3[3] = {gq[0], gq[1], gq[2]};
-    if constexpr (sizeof(T) == sizeof(float)) {  // N_XC and Z in registers
-#pragma unroll
-      for (int r = 0; r < 3; r++)
-#pragma unroll
-        for (int c = 0; c < CD; c++) {
-          T a0 = ob.w * (ob.W[0] * pj.Jx[r] + ob.W[1] * pj.Jx[3 + r]);
-          T a1 = ob.w * (ob.W[1] * pj.Jx[r] + ob.W[2] * pj.Jx[3 + r]);
-          Bl[CD * r + c] = a0 * pj.Jc[c] + a1 * pj.Jc[CD + c];
-        }
-      const float *iv = Ninv + 6 * (size_t)q;
-      float inv[6] = {iv[0], iv[1], iv[2], iv[3], iv[4], iv[5]};
-      z_of<CD>(inv, Bl, Zl);
-    } else {
-      const T *B = NXC + 3 * CD * (size_t)k, *Zk = Z + 3 * CD * (size_t)k;
-#pragma unroll
-      for (int e = 0; e < 3 * CD; e++) { Bl[e] = B[e]; Zl[e] = Zk[e]; }
-    }
-    int e = 0;
-#pragma unroll
-    for (int r = 0; r < CD; r++) {
-      acc[2 * NU + r] += b0[r] * r0 + b1[r] * r1;
-      acc[2 * NU + CD + r] += Zl[r] * g3[0] + Zl[CD + r] * g3[1] + Zl[2 * CD + r] * g3[2];
-#pragma unroll
-      for (int c = r; c < CD; c++, e++) {
-        acc[e] += pj.Jc[r] * b0[c] + pj.Jc[CD + r] * b1[c];
-        acc[NU + e] += Bl[r] * Zl[c] + Bl[CD + r] * Zl[CD + c] + Bl[2 * CD + r] * Zl[2 * CD + c];
-      }
+  } else {
+    for (int p = v.cam_obs_ptr[i] + threadIdx.x; p < p1; p += CB_THREADS) {
+      int k = v.cam_obs[p];
+      int q = v.obs_inst[k];
+      if (!v.active[v.inst_pt[q]]) continue;
+      cb_obs<T, CD>(v, i, k, q, true, NXC, Z, gX, Ninv, acc);
     }
   }
   // warp reduction, then across the CTA's warps

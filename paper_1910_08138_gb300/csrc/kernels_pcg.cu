@@ -1,7 +1,8 @@
 // kernels_pcg.cu -- preconditioned conjugate gradients on the reduced camera
 // systems S_l dC_l = y_l of all running sub-blocks at once (Sec. 5.5: the RCS
 // is solved by CG with block-Jacobi preconditioning, i.e. the inverses of the
-// 6x6 diagonal camera blocks). FP64 vectors and FP64 matrix-vector products,
+// diagonal camera blocks, 6x6 or 8x8 with per-camera intrinsics). FP64 vectors
+// and FP64 matrix-vector products,
 // so that the relative residual can reach 1e-8.
 //
 // Per iteration: k_pcg_symv (one CTA per 32x32 lower tile of every running
@@ -42,8 +43,10 @@ namespace rpba {
 
 static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 
-// M_i^-1 for every camera of a running sub-block: inverse of S_ii (6x6, FP64,
-// Gauss-Jordan on the SPD block); stored row-major, 36 per camera
+// M_i^-1 for every camera of a running sub-block: inverse of S_ii (CD x CD,
+// CD = 6, or 8 with per-camera intrinsics; FP64 Gauss-Jordan on the SPD
+// block); stored row-major, CD^2 per camera
+template <int CD>
 __global__ void k_pcg_bj_setup(int M, const int *cam_sub, const int *cam_local, const int *sub_cam_ptr, const int *run,
                                const double *S, const long long *S_off, const int *npad, double *Minv, int *fail,
                                float *Minv32) {
@@ -53,34 +56,34 @@ __global__ void k_pcg_bj_setup(int M, const int *cam_sub, const int *cam_local, 
   if (!run[l]) return;
   int np = npad[l], li = cam_local[i];
   const double *A = S + S_off[l];
-  double a[6][12];
-  for (int r = 0; r < 6; r++)
-    for (int c = 0; c < 6; c++) {
+  double a[CD][2 * CD];
+  for (int r = 0; r < CD; r++)
+    for (int c = 0; c < CD; c++) {
       int rr = r >= c ? r : c, cc = r >= c ? c : r;  // lower triangle holds the block
-      a[r][c] = A[(size_t)(6 * li + rr) * np + 6 * li + cc];
-      a[r][6 + c] = (r == c) ? 1.0 : 0.0;
+      a[r][c] = A[(size_t)(CD * li + rr) * np + CD * li + cc];
+      a[r][CD + c] = (r == c) ? 1.0 : 0.0;
     }
-  for (int c = 0; c < 6; c++) {
+  for (int c = 0; c < CD; c++) {
     double piv = a[c][c];
     if (!(piv > 0.0)) {
       atomicExch(fail + l, 1);
       return;
     }
     double ip = 1.0 / piv;
-    for (int e = 0; e < 12; e++) a[c][e] *= ip;
-    for (int r = 0; r < 6; r++) {
+    for (int e = 0; e < 2 * CD; e++) a[c][e] *= ip;
+    for (int r = 0; r < CD; r++) {
       if (r == c) continue;
       double f = a[r][c];
-      for (int e = 0; e < 12; e++) a[r][e] -= f * a[c][e];
+      for (int e = 0; e < 2 * CD; e++) a[r][e] -= f * a[c][e];
     }
   }
-  double *o = Minv + 36 * (size_t)(sub_cam_ptr[l] + li);  // cameras in sub-block order
-  for (int r = 0; r < 6; r++)
-    for (int c = 0; c < 6; c++) o[6 * r + c] = a[r][6 + c];
+  double *o = Minv + CD * CD * (size_t)(sub_cam_ptr[l] + li);  // cameras in sub-block order
+  for (int r = 0; r < CD; r++)
+    for (int c = 0; c < CD; c++) o[CD * r + c] = a[r][CD + c];
   if (Minv32) {
-    float *o32 = Minv32 + 36 * (size_t)(sub_cam_ptr[l] + li);
-    for (int r = 0; r < 6; r++)
-      for (int c = 0; c < 6; c++) o32[6 * r + c] = (float)a[r][6 + c];
+    float *o32 = Minv32 + CD * CD * (size_t)(sub_cam_ptr[l] + li);
+    for (int r = 0; r < CD; r++)
+      for (int c = 0; c < CD; c++) o32[CD * r + c] = (float)a[r][CD + c];
   }
 }
 
@@ -241,6 +244,7 @@ __global__ void __launch_bounds__(SYMV_THREADS) k_pcg_symv_ff(const float2 *__re
 }
 
 // FP32 form start: x = 0, r = y, z = M^-1 r (FP32), p = z; rz, |y|
+template <int CD>
 __global__ void __launch_bounds__(PCG_THREADS) k_pcg_init_ff(const int *run, const int *fail, const int *sub_cam_ptr,
                                                              const int *voff, const int *npad, const float *Minv32,
                                                              const double *y, float2 *x, float2 *r, float *z,
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_init_ff(const int *run, con
   }
   if (!ok) return;
   int g0 = sub_cam_ptr[l], ncam = sub_cam_ptr[l + 1] - g0;
-  int n = 6 * ncam, o = voff[l];
+  int n = CD * ncam, o = voff[l];
   double v[2] = {0.0, 0.0};
   const float2 zero = make_float2(0.f, 0.f);
   for (int e = threadIdx.x; e < npad[l]; e += blockDim.x) {  // padding stays zero
@@ -266,13 +270,13 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_init_ff(const int *run, con
   __syncthreads();
   float rzh = 0.f, rzl = 0.f;
   for (int c = threadIdx.x; c < ncam; c += blockDim.x) {
-    const float *Mi = Minv32 + 36 * (size_t)(g0 + c);
-    const float2 *rc = r + o + 6 * c;
-    for (int a = 0; a < 6; a++) {
+    const float *Mi = Minv32 + CD * CD * (size_t)(g0 + c);
+    const float2 *rc = r + o + CD * c;
+    for (int a = 0; a < CD; a++) {
       float t = 0.f;
-      for (int b = 0; b < 6; b++) t += Mi[6 * a + b] * rc[b].x;
-      z[o + 6 * c + a] = t;
-      p[o + 6 * c + a] = make_float2(t, 0.f);
+      for (int b = 0; b < CD; b++) t += Mi[CD * a + b] * rc[b].x;
+      z[o + CD * c + a] = t;
+      p[o + CD * c + a] = make_float2(t, 0.f);
       float e;
       float pr = ff_two_prod(rc[a].x, t, e);
       ff_acc(rzh, rzl, pr);
@@ -329,6 +333,7 @@ __device__ inline void ff_cta_sum(float (&h)[NV], float (&l)[NV], float2 (*sh)[3
 // arithmetic (alpha, beta, the statistics) runs in thread 0 alone: on this GPU
 // one SM's FP64 unit would serialise it across the block.
 #define PCGF_PER 8
+template <int CD>
 __global__ void __launch_bounds__(PCG_THREADS) k_pcg_step_ff(const int *sub_cam_ptr, const int *voff,
                                                              const float *__restrict__ Minv32, double tol,
                                                              float2 *__restrict__ x, float2 *__restrict__ r,
@@ -341,15 +346,16 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_step_ff(const int *sub_cam_
   int l = blockIdx.x;
   if (!live[l]) return;
   int g0 = sub_cam_ptr[l], ncam = sub_cam_ptr[l + 1] - g0;
-  int n = 6 * ncam, o = voff[l];
+  int n = CD * ncam, o = voff[l];
   float *zs = reinterpret_cast<float *>(rs + n);
   // the thread's inverse block, independent of this iteration's data
-  float m[36];
+  constexpr int M4 = CD * CD / 4;
+  float m[CD * CD];
   int c0 = threadIdx.x;
   if (c0 < ncam) {
-    const float4 *Mi = reinterpret_cast<const float4 *>(Minv32 + 36 * (size_t)(g0 + c0));
+    const float4 *Mi = reinterpret_cast<const float4 *>(Minv32 + CD * CD * (size_t)(g0 + c0));
 #pragma unroll
-    for (int k = 0; k < 9; k++) {
+    for (int k = 0; k < M4; k++) {
       float4 w = __ldg(Mi + k);
       m[4 * k] = w.x; m[4 * k + 1] = w.y; m[4 * k + 2] = w.z; m[4 * k + 3] = w.w;
     }
@@ -403,22 +409,22 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_step_ff(const int *sub_cam_
   float vh[2] = {rr, 0.f}, vl[2] = {0.f, 0.f};  // r.r (FP32 is enough for the test), r.z
   for (int c = threadIdx.x; c < ncam; c += PCG_THREADS) {
     if (c != c0) {  // more cameras than threads: load this block too
-      const float4 *Mi = reinterpret_cast<const float4 *>(Minv32 + 36 * (size_t)(g0 + c));
+      const float4 *Mi = reinterpret_cast<const float4 *>(Minv32 + CD * CD * (size_t)(g0 + c));
 #pragma unroll
-      for (int k = 0; k < 9; k++) {
+      for (int k = 0; k < M4; k++) {
         float4 w = __ldg(Mi + k);
         m[4 * k] = w.x; m[4 * k + 1] = w.y; m[4 * k + 2] = w.z; m[4 * k + 3] = w.w;
       }
     }
-    float rh[6], rl[6];
+    float rh[CD], rl[CD];
 #pragma unroll
-    for (int b2 = 0; b2 < 6; b2++) { rh[b2] = rs[6 * c + b2].x; rl[b2] = rs[6 * c + b2].y; }
+    for (int b2 = 0; b2 < CD; b2++) { rh[b2] = rs[CD * c + b2].x; rl[b2] = rs[CD * c + b2].y; }
 #pragma unroll
-    for (int a2 = 0; a2 < 6; a2++) {
+    for (int a2 = 0; a2 < CD; a2++) {
       float t = 0.f;
 #pragma unroll
-      for (int b2 = 0; b2 < 6; b2++) t += m[6 * a2 + b2] * rh[b2];
-      zs[6 * c + a2] = t;
+      for (int b2 = 0; b2 < CD; b2++) t += m[CD * a2 + b2] * rh[b2];
+      zs[CD * c + a2] = t;
       float e;
       float pr = ff_two_prod(rh[a2], t, e);
       ff_acc(vh[1], vl[1], pr);
@@ -453,19 +459,21 @@ __global__ void k_pcg_out_ff(const int *run, const int *fail, const int *voff, c
     dC[voff[l] + e] = ff_to_double(x[voff[l] + e]);
 }
 
-// z = M^-1 r for the cameras of sub-block l (block rows of 6)
+// z = M^-1 r for the cameras of sub-block l (block rows of CD)
+template <int CD>
 __device__ inline void apply_precond(int n_cam, const double *Minv_l, const double *r, double *z) {
   for (int c = threadIdx.x; c < n_cam; c += blockDim.x) {
-    const double *Mi = Minv_l + 36 * (size_t)c;
-    for (int a = 0; a < 6; a++) {
+    const double *Mi = Minv_l + CD * CD * (size_t)c;
+    for (int a = 0; a < CD; a++) {
       double s = 0.0;
-      for (int b = 0; b < 6; b++) s += Mi[6 * a + b] * r[6 * c + b];
-      z[6 * c + a] = s;
+      for (int b = 0; b < CD; b++) s += Mi[CD * a + b] * r[CD * c + b];
+      z[CD * c + a] = s;
     }
   }
 }
 
 // start: x = 0, r = y, z = M^-1 r, p = z; rz, |y|
+template <int CD>
 __global__ void __launch_bounds__(PCG_THREADS) k_pcg_init(const int *run, const int *fail, const int *sub_cam_ptr,
                                                   const int *voff, const int *npad, const double *Minv_sub,
                                                   const double *y, double *x, double *r, double *z, double *p,
@@ -478,7 +486,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_init(const int *run, const 
   }
   if (!ok) return;
   int ncam = sub_cam_ptr[l + 1] - sub_cam_ptr[l];
-  int n = 6 * ncam;
+  int n = CD * ncam;
   int o = voff[l];
   for (int e = threadIdx.x; e < npad[l]; e += blockDim.x) {  // padding stays zero
     x[o + e] = 0.0;
@@ -487,7 +495,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_init(const int *run, const 
     p[o + e] = 0.0;
   }
   __syncthreads();
-  apply_precond(ncam, Minv_sub + 36 * (size_t)sub_cam_ptr[l], r + o, z + o);
+  apply_precond<CD>(ncam, Minv_sub + CD * CD * (size_t)sub_cam_ptr[l], r + o, z + o);
   __syncthreads();
   double v[2] = {0.0, 0.0};
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
@@ -662,6 +670,7 @@ rpba_status fsai_apply(Ctx *ctx, const FsaiApply &F, const int *live, const doub
 // ---- the CG step, one CTA per sub-block ----
 // block-Jacobi step: alpha = rz / p.Sp, x += alpha p, r -= alpha q, z = M^-1 r,
 // beta = rz' / rz, p = z + beta p, convergence ||r|| <= tol ||y||
+template <int CD>
 __global__ void __launch_bounds__(PCG_THREADS) k_pcg_step(const int *sub_cam_ptr, const int *voff,
                                                           const double *Minv_sub, double tol, double *x, double *r,
                                                           double *z, double *p, const double *q, const double *pq,
@@ -674,7 +683,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_step(const int *sub_cam_ptr
     return;
   }
   int g0 = sub_cam_ptr[l], ncam = sub_cam_ptr[l + 1] - g0;
-  int n = 6 * ncam, o = voff[l];
+  int n = CD * ncam, o = voff[l];
   double alpha = rz_old / pql;
   double v[2] = {0.0, 0.0};
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
@@ -685,12 +694,12 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_step(const int *sub_cam_ptr
   }
   __syncthreads();
   for (int c = threadIdx.x; c < ncam; c += blockDim.x) {
-    const double *Mi = Minv_sub + 36 * (size_t)(g0 + c);
-    const double *rc = r + o + 6 * c;
-    double *zc = z + o + 6 * c;
-    for (int a = 0; a < 6; a++) {
+    const double *Mi = Minv_sub + CD * CD * (size_t)(g0 + c);
+    const double *rc = r + o + CD * c;
+    double *zc = z + o + CD * c;
+    for (int a = 0; a < CD; a++) {
       double t = 0.0;
-      for (int b = 0; b < 6; b++) t += Mi[6 * a + b] * rc[b];
+      for (int b = 0; b < CD; b++) t += Mi[CD * a + b] * rc[b];
       zc[a] = t;
       v[1] += rc[a] * t;
     }
@@ -797,7 +806,8 @@ rpba_status pcg_init(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiAppl
   cudaStream_t st = ctx->stream;
   if (!fsai && ff_pcg(ctx)) {
     RPBA_CUDA(cudaMemsetAsync(ctx->pcg_q, 0, ctx->ytot * sizeof(double), st));
-    RPBA_KERNEL(ctx, "k_pcg_init_ff", k_pcg_init_ff<<<L, PCG_THREADS, 0, st>>>(
+    auto init_ff = ctx->cd == 8 ? k_pcg_init_ff<8> : k_pcg_init_ff<6>;
+    RPBA_KERNEL(ctx, "k_pcg_init_ff", init_ff<<<L, PCG_THREADS, 0, st>>>(
                                        run_dev, fail_dev, ctx->sub_cam_ptr, ctx->ycam_off, ctx->npad, ctx->pcg_Minv32,
                                        ctx->y, ctx->pcg_fx, ctx->pcg_fr, ctx->pcg_fz, ctx->pcg_fp, ctx->pcg_st,
                                        ctx->pcg_live));
@@ -817,7 +827,8 @@ rpba_status pcg_init(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiAppl
                                                                     ctx->pcg_z, ctx->pcg_p, ctx->pcg_st,
                                                                     ctx->pcg_live));
   } else {
-    RPBA_KERNEL(ctx, "k_pcg_init", k_pcg_init<<<L, PCG_THREADS, 0, st>>>(
+    auto init = ctx->cd == 8 ? k_pcg_init<8> : k_pcg_init<6>;
+    RPBA_KERNEL(ctx, "k_pcg_init", init<<<L, PCG_THREADS, 0, st>>>(
                                        run_dev, fail_dev, ctx->sub_cam_ptr, ctx->ycam_off, ctx->npad, ctx->pcg_Minv,
                                        ctx->y, ctx->pcg_x, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, ctx->pcg_st,
                                        ctx->pcg_live));
@@ -834,12 +845,14 @@ rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai, int *iters) {
   // the first convergence read after as many iterations as the previous solve
   // took (launches for converged sub-blocks return at once), then every 8
   int next_check = std::min(maxit, std::max(8, ctx->pcg_pred));
+  auto step_ff = ctx->cd == 8 ? k_pcg_step_ff<8> : k_pcg_step_ff<6>;
+  auto step64 = ctx->cd == 8 ? k_pcg_step<8> : k_pcg_step<6>;
   for (int it = 0; it < maxit; it++) {
     if (!fsai && ff_pcg(ctx)) {  // q starts at zero (init) and the step zeroes what it consumed
       RPBA_KERNEL(ctx, "k_pcg_symv_ff", k_pcg_symv_ff<<<tiles, SYMV_THREADS, 0, st>>>(
                                          ctx->pcg_Sff, ctx->S_off, ctx->npad, ctx->ycam_off, ctx->pcg_live,
                                          ctx->pcg_tiles, L, ctx->pcg_fp, ctx->pcg_q));
-      RPBA_KERNEL(ctx, "k_pcg_step_ff", k_pcg_step_ff<<<L, PCG_THREADS, ctx->pcg_ff_smem, st>>>(
+      RPBA_KERNEL(ctx, "k_pcg_step_ff", step_ff<<<L, PCG_THREADS, ctx->pcg_ff_smem, st>>>(
                                          ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_Minv32, ctx->opt.pcg_tol,
                                          ctx->pcg_fx, ctx->pcg_fr, ctx->pcg_fp, ctx->pcg_q, ctx->pcg_st,
                                          ctx->pcg_live));
@@ -859,7 +872,7 @@ rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai, int *iters) {
                                            ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p,
                                            ctx->pcg_st, ctx->pcg_live));
       } else {
-        RPBA_KERNEL(ctx, "k_pcg_step", k_pcg_step<<<L, PCG_THREADS, 0, st>>>(
+        RPBA_KERNEL(ctx, "k_pcg_step", step64<<<L, PCG_THREADS, 0, st>>>(
                                            ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_Minv, ctx->opt.pcg_tol,
                                            ctx->pcg_x, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, ctx->pcg_q, ctx->pcg_pq,
                                            ctx->pcg_st, ctx->pcg_live));
@@ -902,11 +915,11 @@ rpba_status pcg_iterate(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiA
   return pcg_out(ctx, run_dev, fail_dev);
 }
 
-// block-Jacobi: the inverse 6x6 camera blocks (failure flags reset first)
+// block-Jacobi: the inverse camera blocks (failure flags reset first)
 rpba_status pcg_bj_setup(Ctx *ctx, const int *run_dev, int *fail_dev) {
   RPBA_CUDA(cudaMemsetAsync(fail_dev, 0, ctx->L * sizeof(int), ctx->stream));
   if (ctx->M)
-    RPBA_KERNEL(ctx, "k_pcg_bj_setup", k_pcg_bj_setup<<<nblk(ctx->M, 128), 128, 0, ctx->stream>>>(
+    RPBA_KERNEL(ctx, "k_pcg_bj_setup", (ctx->cd == 8 ? k_pcg_bj_setup<8> : k_pcg_bj_setup<6>)<<<nblk(ctx->M, 128), 128, 0, ctx->stream>>>(
                                            ctx->M, ctx->cam_sub, ctx->cam_local, ctx->sub_cam_ptr, run_dev, ctx->S,
                                            ctx->S_off, ctx->npad, ctx->pcg_Minv, fail_dev,
                                            ff_pcg(ctx) ? ctx->pcg_Minv32 : nullptr));

@@ -237,9 +237,7 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   // sub-block needs, a maximum that grows with the number of sub-blocks; the
   // direct solve's critical path is set by the largest sub-block alone
   ctx->cd = ctx->opt.intrinsics ? 8 : 6;
-  if (ctx->opt.solver == 4 && ctx->cd == 8) {
-    ctx->opt.solver = 2;  // the PCG solvers take 6 x 6 camera blocks
-  } else if (ctx->opt.solver == 4) {
+  if (ctx->opt.solver == 4) {
     ctx->auto_solver = true;
     ctx->opt.solver = L <= RPBA_AUTO_PCG_MAX_SUBBLOCKS ? 1 : 2;
   }
@@ -679,7 +677,7 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   RPBA_TRY(upload(ctx, &ctx->sched, ctx->h_sched.data(), ctx->h_sched.size()));
   RPBA_TRY(alloc_n(ctx, &ctx->Linv64, (size_t)std::max(ltot, 1)));
   if (ctx->opt.solver == 1 || ctx->opt.solver == 3 || ctx->auto_solver) {
-    RPBA_TRY(alloc_n(ctx, &ctx->pcg_Minv, 36 * (size_t)std::max(M, 1)));
+    RPBA_TRY(alloc_n(ctx, &ctx->pcg_Minv, (size_t)ctx->cd * ctx->cd * std::max(M, 1)));
     RPBA_TRY(alloc_n(ctx, &ctx->pcg_x, (size_t)std::max(yt, 1)));
     RPBA_TRY(alloc_n(ctx, &ctx->pcg_r, (size_t)std::max(yt, 1)));
     RPBA_TRY(alloc_n(ctx, &ctx->pcg_z, (size_t)std::max(yt, 1)));
@@ -689,7 +687,7 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
     RPBA_TRY(alloc_n(ctx, &ctx->pcg_pq, (size_t)std::max(L, 1)));
     RPBA_TRY(alloc_n(ctx, &ctx->pcg_live, (size_t)std::max(L, 1)));
     int max_n = 0;
-    for (int l = 0; l < L; l++) max_n = std::max(max_n, 6 * (scp[l + 1] - scp[l]));
+    for (int l = 0; l < L; l++) max_n = std::max(max_n, ctx->cd * (scp[l + 1] - scp[l]));
     // solver 1 or auto's PCG in the FP32 form: float-float, for sub-blocks of
     // up to RPBA_PCG_FF_MAX_N unknowns (the step kernel's register batches)
     if (ctx->opt.precision == 1 && ctx->opt.solver == 1 && max_n <= RPBA_PCG_FF_MAX_N) {
@@ -699,7 +697,7 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
       RPBA_TRY(alloc_n(ctx, &ctx->pcg_fr, (size_t)std::max(yt, 1)));
       RPBA_TRY(alloc_n(ctx, &ctx->pcg_fp, (size_t)std::max(yt, 1)));
       RPBA_TRY(alloc_n(ctx, &ctx->pcg_fz, (size_t)std::max(yt, 1)));
-      RPBA_TRY(alloc_n(ctx, &ctx->pcg_Minv32, 36 * (size_t)std::max(M, 1)));
+      RPBA_TRY(alloc_n(ctx, &ctx->pcg_Minv32, (size_t)ctx->cd * ctx->cd * std::max(M, 1)));
     }
     std::vector<int> pt(L + 1, 0);
     for (int l = 0; l < L; l++) pt[l + 1] = pt[l] + ntiles[l] * (ntiles[l] + 1) / 2;
@@ -770,7 +768,7 @@ extern "C" rpba_status rpba_create(const rpba_problem *prob, const rpba_options 
       ctx->opt.ir_steps < 0 || ctx->opt.ir_steps > 20 || ctx->opt.pcg_max_iter < 1 || !(ctx->opt.pcg_tol > 0.0) ||
       ctx->opt.chol_tc < 0 || ctx->opt.chol_tc > 2 || ctx->opt.weight_mode < 0 || ctx->opt.weight_mode > 2 ||
       !(ctx->opt.rho0 > 0.0) || ctx->opt.intrinsics < 0 || ctx->opt.intrinsics > 1 ||
-      (ctx->opt.intrinsics && (ctx->opt.solver == 1 || ctx->opt.solver == 3))) {
+      (ctx->opt.intrinsics && ctx->opt.solver == 3)) {
     ctx->err = "invalid precision / solver / ir_steps / intrinsics option";
     *out = h;
     return RPBA_ERR_INVALID_ARG;
@@ -1438,8 +1436,10 @@ static rpba_status lm_step_run(Ctx *ctx) {
 static rpba_status outer_tail_body(Ctx *ctx, bool robust) {
   RPBA_TRY(launch_exchange(ctx));
   if (robust) RPBA_TRY(launch_robust_weights(ctx, nullptr));
-  RPBA_TRY(launch_intersect(ctx, 1, nullptr));
-  RPBA_TRY(launch_tp_copies(ctx, 1));
+  // the FP32 form's TP intersection restarts the converged TPs' copies itself
+  const bool fused_copies = ctx->opt.precision == 1;
+  RPBA_TRY(launch_intersect(ctx, 1, nullptr, false, fused_copies));
+  if (!fused_copies) RPBA_TRY(launch_tp_copies(ctx, 1));
   return cost_sigma0_launch(ctx);
 }
 

@@ -522,8 +522,10 @@ void sigma0_finish(const Ctx *ctx, double *sigma0, double *rms, long long *n_obs
 rpba_status launch_sigma0(Ctx *ctx, double *sigma0, double *rms, long long *n_obs = nullptr,
                           long long *n_points = nullptr);
 // Eq. bars for all points (tp_only = 0) or the tie points; fp64 forces the
-// FP64 kernels in the FP32 form
-rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped, bool fp64 = false);
+// FP64 kernels in the FP32 form. tp_copies: the FP32 form's TP intersection
+// also restarts the converged TPs' copies X^l at X_TP (a later
+// launch_tp_copies is then not needed for them)
+rpba_status launch_intersect(Ctx *ctx, int tp_only, int *n_dropped, bool fp64 = false, bool tp_copies = false);
 rpba_status launch_exchange(Ctx *ctx);
 rpba_status launch_tp_copies(Ctx *ctx, int tp_only);
 rpba_status launch_camera_scale(Ctx *ctx);

@@ -55,7 +55,7 @@ def _state(precision, seed=5, **opts):
 def test_intrinsics_state_options_and_refusals():
     prob = _prob()
     g = rpba.Rpba(prob, precision=1, solver=4)
-    assert g.cd == 8 and g.resolved_options().solver == 2  # auto resolves to the direct solve
+    assert g.cd == 8 and g.resolved_options().solver == 1  # auto: PCG on 3 sub-blocks
     fk = g.intrinsics()
     np.testing.assert_array_equal(fk[:, 0], prob["cam_intr"][:, 0])
     np.testing.assert_array_equal(fk[:, 1], prob["cam_k1"])
@@ -65,9 +65,8 @@ def test_intrinsics_state_options_and_refusals():
     with pytest.raises(rpba.RpbaError):
         g.set_intrinsics(fk2 * np.array([-1.0, 1.0]))  # a negative focal length
     g.close()
-    for solver in (1, 3):  # the PCG solvers take 6 x 6 camera blocks
-        with pytest.raises(rpba.RpbaError):
-            rpba.Rpba(prob, precision=1, solver=solver)
+    with pytest.raises(rpba.RpbaError):  # the learned preconditioner is built on 6 x 6 camera blocks
+        rpba.Rpba(prob, precision=1, solver=3)
     # without the option the intrinsics are fixed and k1 is 0
     g6 = rpba.Rpba(prob, precision=0, intrinsics=0)
     fk6 = g6.intrinsics()
@@ -162,6 +161,41 @@ def test_lm_step_with_intrinsics(form):
     fg, fo = g.intrinsics(), o.intrinsics()
     np.testing.assert_allclose(fg[:, 0], fo[:, 0], rtol=1e-9 if precision == 0 else 1e-5)
     assert np.abs(fg[:, 1] - fo[:, 1]).max() <= (1e-7 if precision == 0 else 5e-3) * dk1 + 1e-15
+
+
+@pytest.mark.parametrize("form", [(1, 1), (1, 4), (0, 1)])
+def test_lm_step_pcg_with_intrinsics(form):
+    """Block-Jacobi PCG with 8 x 8 camera blocks: the returned camera step
+    solves the GPU's own RCS to pcg_tol (plus the product's rounding), and
+    matches the oracle's Cholesky step within the form's tolerance."""
+    precision, solver = form
+    prob, o, g = _state(precision, solver=solver)
+    assert g.resolved_options().solver == 1
+    lam = 1e-4
+    systems = []
+    for l in range(g.L):
+        S, y = g.rcs(l, lam)
+        systems.append((np.tril(S) + np.tril(S, -1).T, y))
+    acc, Fb, Ft, dc, dx = g.lm_step(lam)
+    it, rr = g.solver_stats()
+    assert np.all(it > 0) and np.all(rr <= g.options.pcg_tol)
+    off = 0
+    _, isub = o.instances()
+    for l in range(o.L):
+        S, y = systems[l]
+        n = y.size
+        dcl = dc[off:off + n]
+        res = np.linalg.norm(S @ dcl - y) / np.linalg.norm(y)
+        fp = 1e-12 * np.linalg.norm(np.abs(S) @ np.abs(dcl)) / np.linalg.norm(y)
+        assert res <= g.options.pcg_tol + fp, (l, res, fp)
+        r, fb, ft, dco, dxo = o.lm_step(l, lam)
+        tol = 1e-5 if precision == 0 else 5e-3
+        d_g, d_o = dcl.reshape(-1, 8), dco.reshape(-1, 8)
+        for cols in (slice(0, 6), slice(6, 7), slice(7, 8)):
+            sc = max(np.abs(d_o[:, cols]).max(), 1e-12)
+            assert np.abs(d_g[:, cols] - d_o[:, cols]).max() <= tol * sc
+        np.testing.assert_allclose(Ft[l], ft, rtol=1e-6 if precision == 0 else 1e-4)
+        off += n
 
 
 @pytest.mark.parametrize("precision", [0, 1])
