@@ -98,27 +98,35 @@ class ClockSampler:
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index=0, interval_ms=50):
+    def __init__(self, index=0, interval_ms=10):
         self.index = index
         self.interval_ms = interval_ms
         self.proc = None
-        self.lines = []
+        self.lines = []  # (host time, line)
 
     def start(self):
+        """Starts the query loop and returns once its first sample arrived
+        (nvidia-smi takes a moment to start), so that the timed region that
+        follows is sampled from its beginning."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-lms", str(self.interval_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t_end = time.perf_counter() + 3.0
+            while not self.lines and time.perf_counter() < t_end:
+                time.sleep(0.005)
         except Exception:
             self.proc = None
 
     def _read(self):
         for ln in self.proc.stdout:
-            self.lines.append(ln.strip())
+            self.lines.append((time.perf_counter(), ln.strip()))
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
+        """Summary of the samples taken between host times t0 and t1 (all
+        when not given)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -126,7 +134,9 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        return summarise_clocks(self.lines)
+        lo = -np.inf if t0 is None else t0
+        hi = np.inf if t1 is None else t1 + self.interval_ms / 1e3
+        return summarise_clocks([ln for t, ln in self.lines if lo <= t <= hi])
 
 
 def summarise_clocks(lines):
@@ -447,6 +457,7 @@ def run_ours(args, rank, world):
     clocks.start()
     times = []
     pcg_iters = []
+    t_timed0 = time.perf_counter()
     for s in range(args.steps):
         flush.fill_(float(s))
         e0 = torch.cuda.Event(enable_timing=True)
@@ -459,7 +470,7 @@ def run_ours(args, rank, world):
         if solver in (1, 3):
             pcg_iters.append(ctx.solver_stats()[0])
             solver = ctx.resolved_options().solver
-    clk = clocks.stop()
+    clk = clocks.stop(t_timed0, time.perf_counter())
     prof, launches = ctx.profile_read()
     ctx.profile_enable(False)
     ctx.profile_select(None)
