@@ -169,8 +169,6 @@ FP32_PEAK_SOURCE = "FP32 CUDA-core rate from 152 SMs x 128 lanes x 2 flops x 207
 # (dram__bytes_read.sum + dram__bytes_write.sum); a kernel is removed from this
 # table when it changes after its capture
 NCU_TRAFFIC_PER_UNIT = {
-    # profiles/k_pcg_symv_ff_cfg4_5000cam.md: 118.88 + 3.13 MB over 14,688 lower tiles
-    "k_pcg_symv_ff": ((118.880768 + 3.132160) * 1e6 / 14688, "tile", "profiles/k_pcg_symv_ff_cfg4_5000cam.md"),
 }
 
 
@@ -390,18 +388,28 @@ def replicas_aggregate(total_ms, obs_per_step, steps, world, device):
     return total_ms, world * obs_per_step * steps / (total_ms / 1e3)
 
 
-def symv_work(ctx, pcg_iters, n_sub):
-    """Algorithmic bytes of the float-float symmetric RCS product per launch:
-    8 B (hi + lo) per stored lower-tile entry of the live sub-blocks; during the
-    last LM iteration of a step sub-block l was live in iters[l] launches.
-    Returns (bytes per launch, live tiles per launch)."""
+def pcg_work(ctx, n_sub, precision):
+    """Algorithmic bytes of the RCS products in the context's last PCG solve,
+    per kernel: {kernel: (bytes, lower-tile reads)}. In the FP32 form the CG
+    product reads S rounded to FP32 (4 B per stored lower-tile entry) of every
+    live sub-block once per CG step, and the refinement product reads the hi
+    and lo planes (8 B) once per stage; the FP64 form's product reads the FP64
+    S (8 B) once per CG step."""
     npad = [32 * ((n + 31) // 32) for n in n_sub]
-    tiles = [(n // 32) * (n // 32 + 1) // 2 for n in npad]
-    launches = sum(int(np.max(it)) for it in pcg_iters)
-    live_tiles = sum(float(np.dot(it, tiles)) for it in pcg_iters)
-    if not launches:
-        return None, None
-    return live_tiles * 1024 * 8 / launches, live_tiles / launches
+    tiles = np.array([(n // 32) * (n // 32 + 1) // 2 for n in npad], dtype=np.float64)
+    it = ctx.solver_stats()[0].astype(np.float64)
+    if precision == 1:
+        t32 = float(np.dot(it, tiles))
+        tff = float(np.dot(ctx.solver_stages().astype(np.float64), tiles))
+        return {"k_pcg_symv32": (t32 * 1024 * 4, t32), "k_pcg_symv_ff": (tff * 1024 * 8, tff)}
+    t = float(np.dot(it, tiles))
+    return {"k_pcg_symv": (t * 1024 * 8, t)}
+
+
+def add_work(acc, work):
+    for k, (b, t) in work.items():
+        b0, t0 = acc.get(k, (0.0, 0.0))
+        acc[k] = (b0 + b, t0 + t)
 
 
 def run_ours(args, rank, world):
@@ -422,7 +430,7 @@ def run_ours(args, rank, world):
     tuned = ctx.tune() if args.tune else None
     _, act0 = ctx.points()
     K = counted_obs(prob, act0)  # the same count as the oracle's after its first intersection
-    n_sub = [6 * len(ctx.sub_cameras(l)) for l in range(ctx.L)]
+    n_sub = [ctx.cd * len(ctx.sub_cameras(l)) for l in range(ctx.L)]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
     def step():
@@ -438,6 +446,8 @@ def run_ours(args, rank, world):
     step()
     prof_all, _ = ctx.profile_read()
     ctx.profile_enable(False)
+    solver = ctx.resolved_options().solver
+    work_warm = pcg_work(ctx, n_sub, args.precision) if solver in (1, 3) else {}
     dominant = max(prof_all.items(), key=lambda kv: kv[1][1])[0]
     # the next warm-up step already runs with the timed steps' profiling, so
     # that the graphs it captures (event nodes for the dominant kernel only)
@@ -456,7 +466,7 @@ def run_ours(args, rank, world):
     clocks = ClockSampler(dev)
     clocks.start()
     times = []
-    pcg_iters = []
+    work_timed = {}
     t_timed0 = time.perf_counter()
     for s in range(args.steps):
         flush.fill_(float(s))
@@ -468,7 +478,7 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
         if solver in (1, 3):
-            pcg_iters.append(ctx.solver_stats()[0])
+            add_work(work_timed, pcg_work(ctx, n_sub, args.precision))
             solver = ctx.resolved_options().solver
     clk = clocks.stop(t_timed0, time.perf_counter())
     prof, launches = ctx.profile_read()
@@ -483,34 +493,38 @@ def run_ours(args, rank, world):
     models = (kernel_models(K, ctx.N, ctx.P, ctx.M, has_winv, schur_pairs(prob), tie_point_counts(prob, act0),
                             cd=ctx.cd)
               if args.precision == 1 else {})
-    sbytes, live_tiles = symv_work(ctx, pcg_iters, n_sub) if pcg_iters else (None, None)
-    if sbytes is not None:
-        models["k_pcg_symv_ff" if args.precision == 1 else "k_pcg_symv"] = ("hbm", sbytes)
 
-    def entry(name, launches_, ms_):
-        if name not in models:
+    def entry(name, launches_, ms_, work=None):
+        # work: {kernel: (bytes, tile reads)} of the PCG products over the
+        # launches timed (their bytes per launch follow from the launch count)
+        if work and name in work:
+            b, t = work[name]
+            model, tiles_per = ("hbm", b / max(launches_, 1)), t / max(launches_, 1)
+        else:
+            model, tiles_per = models.get(name), None
+        if model is None:
             return {"kernel": name, "bound": None, "achieved": None, "frac": None, "launches": launches_,
                     "avg_launch_ms": ms_ / max(launches_, 1)}
-        bound, work = models[name]
+        bound, per_launch = model
         traffic, note = None, None
-        if name in NCU_TRAFFIC_PER_UNIT and name == "k_pcg_symv_ff" and live_tiles:
+        if name in NCU_TRAFFIC_PER_UNIT and tiles_per:
             per, unit, src = NCU_TRAFFIC_PER_UNIT[name]
-            traffic = per * live_tiles
-            note = f"ncu DRAM bytes per {unit} ({src}) x {live_tiles:.0f} live tiles per launch"
-        return roofline_entry(name, launches_, ms_, bound, work, peaks, traffic, note)
+            traffic = per * tiles_per
+            note = f"ncu DRAM bytes per {unit} ({src}) x {tiles_per:.0f} live tiles per launch"
+        return roofline_entry(name, launches_, ms_, bound, per_launch, peaks, traffic, note)
 
-    roof = entry(dominant, *prof.get(dominant, (0, 0.0)))
+    roof = entry(dominant, *prof.get(dominant, (0, 0.0)), work=work_timed)
     step_ms_all = sum(v[1] for v in prof_all.values())
     hot = []
     for name, (la, kms) in sorted(prof_all.items(), key=lambda kv: -kv[1][1]):
         if kms < 0.02 * step_ms_all:
             continue
-        e = entry(name, la, kms)
+        e = entry(name, la, kms, work=work_warm)
         e["share"] = kms / step_ms_all
         hot.append(e)
     kernels = {k: {"launches": v[0], "ms": round(v[1], 4)}
                for k, v in sorted(prof_all.items(), key=lambda kv: -kv[1][1])}
-    solver_names = {0: "FP64 Cholesky", 1: "block-Jacobi PCG" + (" (float-float)" if args.precision == 1 else " (FP64)"),
+    solver_names = {0: "FP64 Cholesky", 1: "block-Jacobi PCG" + (" (FP32 CG stages, float-float refinement)" if args.precision == 1 else " (FP64)"),
                     2: "FP32 Cholesky + FP64 refinement", 3: "PCG, learned preconditioner"}
     line = {"metric": METRIC, "value": value, "unit": "obs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -79,6 +79,7 @@ typedef struct {
  * lock-step iterations (one iteration costs ~1/50 of a direct solve) */
 #define RPBA_AUTO_PCG_MAX_SUBBLOCKS 64
 #define RPBA_AUTO_PCG_MAX_ITER 48
+#define RPBA_AUTO_PCG_MAX_ITER_FP32 80 /* precision 1: its CG steps cost about half as much */
 
 /* Options; rpba_default_options fills the paper's values (Sec. 5.3, 5.5). */
 typedef struct {
@@ -111,14 +112,16 @@ typedef struct {
                             the cost, sigma_0 and robust tests), FP64 reductions */
   int32_t solver;        /* RCS solve: 0 FP64 Cholesky; 1 PCG with block-Jacobi
                             preconditioning (Sec. 5.5) to pcg_tol (FP64 vectors; with
-                            precision 1 float-float vectors and products for sub-blocks of
-                            up to 2048 unknowns, FP64 above); 2 FP32 Cholesky of the
+                            precision 1, for sub-blocks of up to 2048 unknowns, FP32 CG
+                            stages on S rounded to FP32, each refined by the float-float
+                            residual y - S x, FP64 above); 2 FP32 Cholesky of the
                             Jacobi-scaled RCS with FP64 iterative refinement; 3 FP64 PCG
                             with the learned preconditioner (rpba_set_gnn_weights),
                             block-Jacobi PCG again for a sub-block it leaves above pcg_tol;
                             4 auto: 1 for at most RPBA_AUTO_PCG_MAX_SUBBLOCKS sub-blocks,
                             else 2; 1 becomes 2 after a solve of more than
-                            RPBA_AUTO_PCG_MAX_ITER iterations (rpba_get_options) */
+                            RPBA_AUTO_PCG_MAX_ITER iterations (RPBA_AUTO_PCG_MAX_ITER_FP32
+                            with precision 1) (rpba_get_options) */
   double pcg_tol;        /* relative residual of the PCG solve, 1e-8 */
   int32_t pcg_max_iter;  /* PCG iteration cap, 500 */
   int32_t ir_steps;      /* refinement passes of solver 2 after the first solve, 2 */
@@ -278,7 +281,7 @@ rpba_status rpba_robust_weights(rpba_ctx *ctx, int32_t *n_down);
 rpba_status rpba_intersect_points(rpba_ctx *ctx, int32_t tp_only, int32_t *n_dropped);
 /* F_l of every sub-block at the current state (Eq. bact), n_subblocks values */
 rpba_status rpba_sub_costs(rpba_ctx *ctx, double *F);
-/* damped RCS of sub-block l (Sec. 2, 5.5): S (n x n, lower triangle valid,
+/* damped RCS of sub-block l (Sec. 2, 5.5): S (n x n, symmetric, row-major;
  * n = 6 x cameras of l, 8 x with intrinsics) and y (n), at the current state */
 rpba_status rpba_rcs(rpba_ctx *ctx, int32_t l, double lambda, double *S, double *y);
 /* one LM step of every sub-block with damping lambda: solve, trial, accept
@@ -299,9 +302,15 @@ rpba_status rpba_bact(rpba_ctx *ctx, int32_t *iters);
 
 /* PCG solvers (solver = 1, 3, or 4 while or after it used PCG): iterations
  * and final relative residual ||r|| / ||y|| of every sub-block in the last PCG
- * pass (n_subblocks values each, nullable). Errors: STATE when the context
- * has no PCG state. */
+ * pass (n_subblocks values each, nullable; with precision 1 the CG steps of
+ * all refinement stages and the float-float residual of the returned
+ * solution). Errors: STATE when the context has no PCG state. */
 rpba_status rpba_solver_stats(rpba_ctx *ctx, int32_t *iters, double *relres);
+/* precision 1 with block-Jacobi PCG: the refinement stages of every
+ * sub-block in the last solve (n_subblocks values; each stage is one FP32 CG
+ * run and one float-float product S x); zeros for the other solvers and
+ * forms. Errors: INVALID_ARG for a NULL stages. */
+rpba_status rpba_solver_stages(rpba_ctx *ctx, int32_t *stages);
 /* solver 3: number of sub-block solves, since create, that the learned
  * preconditioner left above pcg_tol and block-Jacobi PCG solved again */
 rpba_status rpba_solver_fallbacks(rpba_ctx *ctx, int64_t *n);

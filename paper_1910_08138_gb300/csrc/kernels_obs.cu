@@ -1687,17 +1687,22 @@ __global__ void __launch_bounds__(SC_THREADS, CD == 6 ? 2 : 1) k_schur_seg(View 
     for (int c = 0; c < CD; c++) atomicAdd(row + (size_t)r * np + c, f2d(-acc[CD * r + c]));
 }
 
-// zero the RCS of running sub-blocks, identity on the padding
+// zero the lower 32 x 32 tiles of the RCS of running sub-blocks, identity on
+// the padding. The strictly upper tiles are left as they are: every reader of
+// S (the factorisations, the products, the preconditioners, rpba_rcs) takes
+// the matrix from its lower triangle, and the Schur kernels write the upper
+// triangle only inside the diagonal camera blocks. One CTA per row, the row
+// through the end of its diagonal tile (np is a multiple of 32).
 __global__ void k_rcs_clear(View v, const int *run, int L) {
   int l = blockIdx.y;
   if (l >= L || !run[l]) return;
   int np = v.npad[l];
   int n = v.cd * (v.sub_cam_ptr[l + 1] - v.sub_cam_ptr[l]);
   double *S = v.S + v.S_off[l];
-  size_t tot = (size_t)np * np;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
-    size_t r = e / np, c = e - r * np;
-    S[e] = (r == c && (int)r >= n) ? 1.0 : 0.0;
+  for (int r = blockIdx.x; r < np; r += gridDim.x) {
+    double *row = S + (size_t)r * np;
+    int lim = (r | 31) + 1;
+    for (int c = threadIdx.x; c < lim; c += blockDim.x) row[c] = (r == c && r >= n) ? 1.0 : 0.0;
   }
   double *yv = v.y + v.ycam_off[l];
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < np; e += gridDim.x * blockDim.x)
@@ -1709,8 +1714,8 @@ static rpba_status build_rcs_cd(Ctx *ctx, const View &v, const double *lambda_de
 
 rpba_status launch_build_rcs(Ctx *ctx, const double *lambda_dev, const int *run_dev) {
   View v = make_view(ctx);
-  dim3 gclr(64, ctx->L);
-  RPBA_KERNEL(ctx, "k_rcs_clear", k_rcs_clear<<<gclr, 256, 0, ctx->stream>>>(v, run_dev, ctx->L));
+  dim3 gclr(256, ctx->L);
+  RPBA_KERNEL(ctx, "k_rcs_clear", k_rcs_clear<<<gclr, 128, 0, ctx->stream>>>(v, run_dev, ctx->L));
   if (ctx->P == 0) return RPBA_OK;
   if (ctx->cd == 8) return build_rcs_cd<8>(ctx, v, lambda_dev, run_dev);
   return build_rcs_cd<6>(ctx, v, lambda_dev, run_dev);

@@ -16,18 +16,21 @@
 // The preconditioner is the inverse of the diagonal camera blocks
 // (block-Jacobi), or the learned factorised inverse G^T G (solver 3).
 //
-// FP32 form, block-Jacobi: the same iteration without FP64 arithmetic in the
-// loop. Once per solve the RCS is split into hi + lo float pairs (2^-48
-// relative); the product S p runs in float-float on the FP32 pipes (TwoProduct
-// and TwoSum per entry), x, r and p are float-float vectors, and the
-// preconditioner is applied in FP32 (it needs no more). The product keeps
-// ~1e-13 relative accuracy, far below the 1e-8 residual the loop stops at; on
-// this GPU the FP64 pipe runs at 1/64 of the FP32 rate, so the FP64 loop is
-// bound by its FP64 instructions and this one by memory and latency. The
-// float-float step forms p.Sp itself (p . q), keeps its block sums in
-// float-float, runs the scalar FP64 arithmetic in one thread and zeroes the q
-// it has read; the product uses 128-thread CTAs (two threads per row and per
-// column of a tile).
+// FP32 form, block-Jacobi: mixed-precision refinement around FP32 CG. Once
+// per solve the RCS is split into a hi plane (S rounded to FP32) and a lo
+// plane (hi + lo = S to 2^-48 relative). A stage runs FP32 CG on
+// S_hi d = r, with r the current residual rounded to FP32, until
+// ||r_k|| <= 1e-4 ||r_0|| (k_pcg_symv32 reads 4 B per stored entry, one warp
+// per tile with plain FMAs; k_pcg_step32 is the FP32 step); then
+// X += d in float-float and the true residual R = y - S X is formed in
+// float-float from both planes (k_pcg_symv_ff, TwoProduct and TwoSum per
+// entry, ~1e-13 relative) by k_pcg_stage, which ends the solve at
+// ||R|| <= pcg_tol ||y|| or starts the next stage. The entrywise rounding of
+// S_hi is a relative perturbation of 2^-24, so a stage reduces the residual
+// by about max(1e-4, 2^-24 cond) with cond the condition of the Jacobi-scaled
+// RCS; at the benchmark sizes two stages reach 1e-8. The CG steps thus read
+// half the bytes and run no float-float arithmetic, and the stopping test is
+// on the float-float true residual, not on a recurrence.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -175,47 +178,85 @@ __device__ inline void tile_of(int idx, const int *sched_tiles, int L, int &l, i
   b = loc - a * (a + 1) / 2;
 }
 
-// FP32 form: the lower tiles of the live sub-blocks as hi + lo pairs
+// Per-sub-block words of the FP32 form's refinement (PCG_S32_WORDS floats
+// each): rz, the stage's ||r_0|| and tolerance, the last relative true
+// residual, the stage count, a bound on max |p|, the exponent of the
+// fixed-point product and max |S_hi| (as float bits, for atomicMax)
+#define PCG_S32 PCG_S32_WORDS
+enum {
+  S32_RZ = 0, S32_RN0 = 1, S32_TOL = 2, S32_PREV = 3, S32_STAGES = PCG_S32_STAGES, S32_PMAX = 5, S32_QEXP = 6,
+  S32_SMAX = 7
+};
+
+// FP32 form: the lower tiles of the running sub-blocks as hi + lo floats, in
+// two planes with the layout of S (hi: S rounded to 24 bits; hi + lo: S to
+// 2^-48 relative), and max |S_hi| per sub-block (its word zeroed before)
 __global__ void __launch_bounds__(256) k_pcg_split(const double *S, const long long *S_off, const int *npad,
-                                                   const int *live, const int *sched_tiles, int L, float2 *Sff) {
+                                                   const int *run, const int *fail, const int *sched_tiles, int L,
+                                                   float *Shi, float *Slo, float *s32) {
   int l, a, b;
   tile_of(blockIdx.x, sched_tiles, L, l, a, b);
-  if (!live[l]) return;
+  if (!run[l] || fail[l]) return;
   int np = npad[l];
+  float mx = 0.f;
   for (int e = threadIdx.x; e < PT * PT; e += blockDim.x) {
     int r = e / PT, c = e - r * PT;
     size_t idx = (size_t)S_off[l] + (size_t)(a * PT + r) * np + b * PT + c;
-    Sff[idx] = ff_split_bits(S[idx]);
+    float2 v = ff_split_bits(S[idx]);
+    Shi[idx] = v.x;
+    Slo[idx] = v.y;
+    mx = fmaxf(mx, fabsf(v.x));
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(s32 + PCG_S32 * l + S32_SMAX), __float_as_int(mx));
 }
 
-// FP32 form: q += S p in float-float, summed over the tiles with FP64
-// atomics. p^T S p is left to the step kernel (p . q over the sub-block):
-// one atomic per tile on a single per-sub-block word serialises hundreds of
-// CTAs. 128 threads: warps 0-1 form the row sums, warps 2-3 the column sums
+// Exponent s of the FP32 form's fixed-point product: every partial sum of
+// S_hi p (and their total) is below np max|S_hi| max|p| < 2^61 2^-s, so the
+// partials scaled by 2^s fit 64-bit integers, whose sums are exact and do not
+// depend on the order of the atomics. Computed from the exponents alone.
+__device__ inline int fixed_exp(int np, float smax, float pmax) {
+  if (!(smax > 0.f) || !(pmax > 0.f) || isinf(smax) || isinf(pmax)) return 0;
+  int e1, e2, e3;
+  frexpf((float)np, &e1);
+  frexpf(smax, &e2);
+  frexpf(pmax, &e3);
+  return 61 - (e1 + e2 + e3);
+}
+
+// FP32 form, refinement residual: q += S (X + dx) in float-float over the
+// lower tiles of the active sub-blocks (X float-float, dx the FP32 solution of
+// the stage just ended), summed over the tiles with FP64 atomics. 128
+// threads: warps 0-1 form the row sums, warps 2-3 the column sums
 // (off-diagonal tiles), two threads per row or column with 16 entries each.
 #define SYMV_THREADS 128
-__global__ void __launch_bounds__(SYMV_THREADS) k_pcg_symv_ff(const float2 *__restrict__ Sff, const long long *S_off,
-                                                              const int *npad, const int *voff, const int *live,
+__global__ void __launch_bounds__(SYMV_THREADS) k_pcg_symv_ff(const float *__restrict__ Shi,
+                                                              const float *__restrict__ Slo, const long long *S_off,
+                                                              const int *npad, const int *voff, const int *act,
                                                               const int *sched_tiles, int L,
-                                                              const float2 *__restrict__ p, double *q) {
+                                                              const float2 *__restrict__ X,
+                                                              const float *__restrict__ dx, double *q) {
   int l, a, b;
   tile_of(blockIdx.x, sched_tiles, L, l, a, b);
-  if (!live[l]) return;
+  if (!act[l]) return;
   int np = npad[l];
-  const float2 *A = Sff + S_off[l];
-  const float2 *pl = p + voff[l];
+  size_t base = (size_t)S_off[l];
+  const float2 *Xl = X + voff[l];
+  const float *dxl = dx + voff[l];
   double *ql = q + voff[l];
   __shared__ float2 blk[PT][PLD];
   __shared__ float2 pI[PT], pJ[PT];
   int tid = threadIdx.x;
-  if (tid < PT) pI[tid] = pl[a * PT + tid];
-  else if (tid < 2 * PT) pJ[tid - PT] = pl[b * PT + tid - PT];
+  if (tid < PT) pI[tid] = ff_add(Xl[a * PT + tid], make_float2(dxl[a * PT + tid], 0.f));
+  else if (tid < 2 * PT) pJ[tid - PT] = ff_add(Xl[b * PT + tid - PT], make_float2(dxl[b * PT + tid - PT], 0.f));
   float2 v[8];
 #pragma unroll
   for (int k = 0; k < 8; k++) {
     int e = tid + SYMV_THREADS * k, r = e / PT, c = e - r * PT;
-    v[k] = (a == b && c > r) ? A[(size_t)(a * PT + c) * np + b * PT + r] : A[(size_t)(a * PT + r) * np + b * PT + c];
+    size_t idx = base + ((a == b && c > r) ? (size_t)(a * PT + c) * np + b * PT + r
+                                           : (size_t)(a * PT + r) * np + b * PT + c);
+    v[k] = make_float2(Shi[idx], Slo[idx]);
   }
 #pragma unroll
   for (int k = 0; k < 8; k++) {
@@ -243,112 +284,281 @@ __global__ void __launch_bounds__(SYMV_THREADS) k_pcg_symv_ff(const float2 *__re
   if (h == 0) atomicAdd(ql + (col ? b : a) * PT + t, ff_to_double(make_float2(sh, sl)));
 }
 
-// FP32 form start: x = 0, r = y, z = M^-1 r (FP32), p = z; rz, |y|
-template <int CD>
-__global__ void __launch_bounds__(PCG_THREADS) k_pcg_init_ff(const int *run, const int *fail, const int *sub_cam_ptr,
-                                                             const int *voff, const int *npad, const float *Minv32,
-                                                             const double *y, float2 *x, float2 *r, float *z,
-                                                             float2 *p, double *st, int *live) {
-  int l = blockIdx.x;
-  int ok = run[l] && !fail[l];
-  if (threadIdx.x == 0) {
-    live[l] = ok;
-    if (!ok) st[4 * l + 3] = 0.0;  // no iterations in this solve
-  }
-  if (!ok) return;
-  int g0 = sub_cam_ptr[l], ncam = sub_cam_ptr[l + 1] - g0;
-  int n = CD * ncam, o = voff[l];
-  double v[2] = {0.0, 0.0};
-  const float2 zero = make_float2(0.f, 0.f);
-  for (int e = threadIdx.x; e < npad[l]; e += blockDim.x) {  // padding stays zero
-    x[o + e] = zero;
-    r[o + e] = e < n ? ff_split_bits(y[o + e]) : zero;
-    z[o + e] = 0.f;
-    p[o + e] = zero;
-    if (e < n) v[1] += y[o + e] * y[o + e];
-  }
-  __syncthreads();
-  float rzh = 0.f, rzl = 0.f;
-  for (int c = threadIdx.x; c < ncam; c += blockDim.x) {
-    const float *Mi = Minv32 + CD * CD * (size_t)(g0 + c);
-    const float2 *rc = r + o + CD * c;
-    for (int a = 0; a < CD; a++) {
-      float t = 0.f;
-      for (int b = 0; b < CD; b++) t += Mi[CD * a + b] * rc[b].x;
-      z[o + CD * c + a] = t;
-      p[o + CD * c + a] = make_float2(t, 0.f);
-      float e;
-      float pr = ff_two_prod(rc[a].x, t, e);
-      ff_acc(rzh, rzl, pr);
-      rzl = __fadd_rn(rzl, __fmaf_rn(rc[a].y, t, e));
+// Sums over the warp's lanes of 32 values at once: on return lane i holds
+// the sum over all lanes of t[i]. Five halving exchange steps (16 + 8 + 4 + 2
+// + 1 shuffles): at the step of width o a lane keeps the half of its values
+// whose index has bit o equal to its own lane bit o, sends the other half to
+// lane ^ o and adds what it receives.
+__device__ __forceinline__ float warp_transpose_sum(float (&t)[PT], int lane) {
+#pragma unroll
+  for (int o = PT / 2; o >= 1; o >>= 1) {
+    bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; i++) {
+      float send = up ? t[i] : t[i + o];
+      float keep = up ? t[i + o] : t[i];
+      t[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
     }
   }
-  v[0] = (double)rzh + (double)rzl;
-  double s[2];
-  cta_sum<2>(v, s);
-  if (threadIdx.x == 0) {
-    st[4 * l + 0] = s[0];                    // rz
-    st[4 * l + 1] = sqrt(s[1]);              // |y|
-    st[4 * l + 2] = s[1] > 0.0 ? 1.0 : 0.0;  // relative residual
-    st[4 * l + 3] = 0.0;                     // iterations
-    if (!(s[1] > 0.0)) live[l] = 0;
-  }
+  return t[0];
 }
 
-// float-float sum over a warp (lane 0 holds the result)
-__device__ inline void ff_warp_sum(float &h, float &l) {
+// FP32 form, inner CG product: q += S_hi p over the lower tiles of the live
+// sub-blocks, one warp per tile and no shared memory. Lane c reads column c
+// of the tile one row at a time (each load a 128-byte row of the warp), adds
+// S_rc p_I[r] to the transposed product in a register and keeps the 32 row
+// terms S_rc p_J[c]; warp_transpose_sum leaves row r's sum in lane r. On a
+// diagonal tile only the entries on and below the diagonal are used. The two
+// sums of a lane (formed in a fixed order) are added to q as 64-bit fixed-point
+// integers (scale 2^s, fixed_exp), so q does not depend on the order of the
+// atomics and two runs give the same CG iterates.
+#define SYMV32_WARPS 8
+__global__ void __launch_bounds__(32 * SYMV32_WARPS) k_pcg_symv32(const float *__restrict__ Shi,
+                                                                  const long long *S_off, const int *npad,
+                                                                  const int *voff, const int *live,
+                                                                  const int *sched_tiles, int L, int tiles,
+                                                                  const float *__restrict__ s32,
+                                                                  const float *__restrict__ p,
+                                                                  unsigned long long *q) {
+  int lane = threadIdx.x & 31;
+  int idx = blockIdx.x * SYMV32_WARPS + (threadIdx.x >> 5);
+  if (idx >= tiles) return;
+  int l, a, b;
+  tile_of(idx, sched_tiles, L, l, a, b);
+  if (!live[l]) return;
+  int np = npad[l];
+  int sc = (int)s32[PCG_S32 * l + S32_QEXP];
+  const float *A = Shi + S_off[l] + (size_t)(a * PT) * np + b * PT + lane;
+  const float *pl = p + voff[l];
+  float pIc = pl[a * PT + lane], pJc = pl[b * PT + lane];
+  float t[PT];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    float oh = __shfl_down_sync(0xffffffffu, h, o), ol = __shfl_down_sync(0xffffffffu, l, o);
-    float e;
-    h = ff_two_sum(h, oh, e);
-    l = __fadd_rn(l, __fadd_rn(e, ol));
+  for (int r = 0; r < PT; r++) t[r] = __ldg(A + (size_t)r * np);
+  float col = 0.f;
+  if (a != b) {
+#pragma unroll
+    for (int r = 0; r < PT; r++) {
+      col = __fmaf_rn(t[r], __shfl_sync(0xffffffffu, pIc, r), col);
+      t[r] = __fmul_rn(t[r], pJc);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < PT; r++) {
+      float m = lane <= r ? t[r] : 0.f;  // row r, columns 0 .. r
+      col = __fmaf_rn(lane < r ? m : 0.f, __shfl_sync(0xffffffffu, pIc, r), col);
+      t[r] = __fmul_rn(m, pJc);
+    }
+  }
+  float row = warp_transpose_sum(t, lane);
+  unsigned long long *ql = q + voff[l];
+  long long vr = __float2ll_rn(scalbnf(row, sc)), vc = __float2ll_rn(scalbnf(col, sc));
+  if (a != b) {
+    atomicAdd(ql + a * PT + lane, (unsigned long long)vr);
+    atomicAdd(ql + b * PT + lane, (unsigned long long)vc);
+  } else {
+    atomicAdd(ql + a * PT + lane, (unsigned long long)(vr + vc));
   }
 }
 
-// float-float sums of NV values over the CTA; thread 0 gets the totals (as
-// doubles). sh: [NV][32] float2 scratch
+// q[e] (fixed point, scale 2^s) as a float
+__device__ __forceinline__ float fixed_to_float(unsigned long long v, int sc) {
+  return scalbnf(__ll2float_rn((long long)v), -sc);
+}
+
+// FP32 sums of NV values over the CTA; every thread gets the totals
 template <int NV>
-__device__ inline void ff_cta_sum(float (&h)[NV], float (&l)[NV], float2 (*sh)[32], double (&tot)[NV]) {
+__device__ inline void f_cta_sum(float (&v)[NV], float (&out)[NV]) {
+  __shared__ float sh[NV][32];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int k = 0; k < NV; k++) {
-    ff_warp_sum(h[k], l[k]);
-    if (lane == 0) sh[k][wid] = make_float2(h[k], l[k]);
+    float x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[k][wid] = x;
   }
   __syncthreads();
-  if (threadIdx.x == 0)
-    for (int k = 0; k < NV; k++) {
-      float2 t = sh[k][0];
-      for (int w = 1; w < nw; w++) t = ff_add(t, sh[k][w]);
-      tot[k] = ff_to_double(t);
-    }
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    float s = 0.f;
+    for (int w = 0; w < nw; w++) s += sh[k][w];
+    out[k] = s;
+  }
+  __syncthreads();
 }
 
-// FP32 form step: p.Sp = p.q, alpha = rz / p.Sp, x += alpha p, r -= alpha q
-// (float-float), z = M^-1 r (FP32), rz' = r.z, beta = rz' / rz, p = z + beta p.
-// Each thread loads all of its elements at once (up to PCGF_PER) so that each
-// phase waits for one memory latency; r and z pass between the phases in
-// shared memory. The block sums are float-float and the scalar FP64
-// arithmetic (alpha, beta, the statistics) runs in thread 0 alone: on this GPU
-// one SM's FP64 unit would serialise it across the block.
+
+// FP32 sums of NV values and the maximum of one more over the CTA; every
+// thread gets the results
+template <int NV>
+__device__ inline void f_cta_sum_max(float (&v)[NV], float m, float (&out)[NV], float &mout) {
+  __shared__ float sh[NV + 1][32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    float x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[k][wid] = x;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) sh[NV][wid] = m;
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    float t = 0.f;
+    for (int w = 0; w < nw; w++) t += sh[k][w];
+    out[k] = t;
+  }
+  float mm = 0.f;
+  for (int w = 0; w < nw; w++) mm = fmaxf(mm, sh[NV][w]);
+  mout = mm;
+  __syncthreads();
+}
+
+// FP32 form: start of a refinement stage, one CTA per active sub-block.
+// first: X = 0 and R = y (every running sub-block becomes active); otherwise
+// X += x, the FP32 solution of the stage just ended, and R = y - q with
+// q = S X from k_pcg_symv_ff (q is zeroed once read). The solve of the
+// sub-block ends when ||R|| <= tol ||y||, when a stage has not halved ||R||,
+// after max_stage stages, or when final is set (the CG iteration cap);
+// otherwise the FP32 CG restarts on S_hi d = R rounded to FP32: x = 0,
+// z = M^-1 r, p = z, stopping at ||r|| <= max(tol_in, 0.3 tol ||y|| / ||R||)
+// ||R||. st[4l + 2] is the relative true residual ||R|| / ||y||.
+template <int CD>
+__global__ void __launch_bounds__(PCG_THREADS) k_pcg_stage(
+    int first, int final_stage, const int *run, const int *fail, const int *sub_cam_ptr, const int *voff,
+    const int *npad, const float *__restrict__ Minv32, const double *__restrict__ y, double *qd, float2 *X,
+    float *x, float *r, float *z, float *p, unsigned long long *q, double *st, float *s32, int *act, int *live,
+    double tol, double tol_in, int max_stage) {
+  __shared__ int stop;
+  int l = blockIdx.x;
+  int stage;
+  if (first) {
+    int ok = run[l] && !fail[l];
+    if (threadIdx.x == 0) {
+      act[l] = ok;
+      live[l] = 0;
+      st[4 * l + 3] = 0.0;  // CG iterations of this solve
+      st[4 * l + 2] = ok ? 1.0 : 0.0;
+      s32[PCG_S32 * l + S32_STAGES] = 0.f;
+    }
+    if (!ok) return;
+    stage = 0;
+  } else {
+    stage = act[l];
+    if (!stage) return;
+  }
+  int g0 = sub_cam_ptr[l], ncam = sub_cam_ptr[l + 1] - g0;
+  int n = CD * ncam, o = voff[l], np = npad[l];
+  float rr = 0.f;             // ||R||^2: FP32 terms and per-thread sums, FP64 across the CTA
+  double v[2] = {0.0, 0.0};  // ||R||^2, ||y||^2
+  for (int e = threadIdx.x; e < np; e += blockDim.x) {
+    float re = 0.f;
+    if (e < n) {
+      float2 yf = ff_split_bits(y[o + e]);
+      float2 R = yf;
+      if (first) {
+        X[o + e] = make_float2(0.f, 0.f);
+        v[1] += y[o + e] * y[o + e];
+      } else {
+        X[o + e] = ff_add(X[o + e], make_float2(x[o + e], 0.f));
+        float2 qf = ff_split_bits(qd[o + e]);
+        R = ff_add(yf, make_float2(-qf.x, -qf.y));
+      }
+      rr = __fmaf_rn(R.x, R.x, rr);
+      re = R.x;
+    } else if (first) {
+      X[o + e] = make_float2(0.f, 0.f);
+    }
+    qd[o + e] = 0.0;
+    r[o + e] = re;
+    x[o + e] = 0.f;
+    z[o + e] = 0.f;
+    p[o + e] = 0.f;
+    q[o + e] = 0ull;
+  }
+  v[0] = f2d(rr);
+  double s[2];
+  cta_sum<2>(v, s);  // its barriers also order the r writes before the reads below
+  if (threadIdx.x == 0) {
+    double ny = first ? sqrt(s[1]) : st[4 * l + 1];
+    double nr = sqrt(s[0]);
+    double rel = ny > 0.0 ? nr / ny : 0.0;
+    if (first) st[4 * l + 1] = ny;
+    st[4 * l + 2] = rel;
+    float *w = s32 + PCG_S32 * l;
+    bool done = !(ny > 0.0) || rel <= tol || final_stage || stage >= max_stage ||
+                (!first && !(rel <= 0.5 * (double)w[S32_PREV]));
+    if (done) {
+      act[l] = 0;
+      live[l] = 0;
+    } else {
+      act[l] = stage + 1;
+      live[l] = 1;
+      w[S32_RN0] = (float)nr;
+      w[S32_TOL] = (float)fmax(tol_in, 0.3 * tol / rel);
+      w[S32_PREV] = (float)rel;
+      w[S32_STAGES] = (float)(stage + 1);
+    }
+    stop = done;
+  }
+  __syncthreads();
+  if (stop) return;
+  float rz = 0.f, zmax = 0.f;
+  for (int c = threadIdx.x; c < ncam; c += blockDim.x) {
+    const float *Mi = Minv32 + CD * CD * (size_t)(g0 + c);
+    const float *rc = r + o + CD * c;
+    float rl[CD];
+#pragma unroll
+    for (int b = 0; b < CD; b++) rl[b] = rc[b];
+#pragma unroll
+    for (int a = 0; a < CD; a++) {
+      float t = 0.f;
+#pragma unroll
+      for (int b = 0; b < CD; b++) t = __fmaf_rn(Mi[CD * a + b], rl[b], t);
+      z[o + CD * c + a] = t;
+      p[o + CD * c + a] = t;
+      rz = __fmaf_rn(rl[a], t, rz);
+      zmax = fmaxf(zmax, fabsf(t));
+    }
+  }
+  float v1[1] = {rz}, t1[1], pmax;
+  f_cta_sum_max<1>(v1, zmax, t1, pmax);
+  if (threadIdx.x == 0) {
+    float *w = s32 + PCG_S32 * l;
+    w[S32_RZ] = t1[0];
+    w[S32_PMAX] = pmax;
+    w[S32_QEXP] = (float)fixed_exp(np, w[S32_SMAX], pmax);
+  }
+}
+
+// FP32 form, inner CG step of a refinement stage (one CTA per live
+// sub-block): alpha = rz / p.q, x += alpha p, r -= alpha q, z = M^-1 r,
+// beta = r.z / rz, p = z + beta p; the stage ends when ||r|| <= tol_s ||r_0||.
+// FP32 throughout, block sums included (the stage needs ~1e-4 of its right-hand
+// side; the refinement's float-float residual corrects the rest). Each thread
+// loads all of its elements at once (up to PCGF_PER) so that each phase waits
+// for one memory latency; r and z pass between the phases in shared memory;
+// q is zeroed once read.
 #define PCGF_PER 8
 template <int CD>
-__global__ void __launch_bounds__(PCG_THREADS) k_pcg_step_ff(const int *sub_cam_ptr, const int *voff,
-                                                             const float *__restrict__ Minv32, double tol,
-                                                             float2 *__restrict__ x, float2 *__restrict__ r,
-                                                             float2 *__restrict__ p, double *__restrict__ q,
-                                                             double *st, int *live) {
-  extern __shared__ float2 rs[];  // r (n), then z as floats (n)
-  __shared__ float2 red[2][32];
-  __shared__ float2 bc;           // broadcast scalar (alpha, then beta) as a pair
-  __shared__ int stop;
+__global__ void __launch_bounds__(PCG_THREADS) k_pcg_step32(const int *sub_cam_ptr, const int *voff,
+                                                            const float *__restrict__ Minv32,
+                                                            const int *npad, float *__restrict__ x,
+                                                            float *__restrict__ r, float *__restrict__ p,
+                                                            unsigned long long *__restrict__ q, double *st,
+                                                            float *s32, int *live) {
+  extern __shared__ float rzs[];  // r (n), then z (n)
   int l = blockIdx.x;
   if (!live[l]) return;
   int g0 = sub_cam_ptr[l], ncam = sub_cam_ptr[l + 1] - g0;
   int n = CD * ncam, o = voff[l];
-  float *zs = reinterpret_cast<float *>(rs + n);
-  // the thread's inverse block, independent of this iteration's data
+  float *rs = rzs, *zs = rzs + n;
+  float *w = s32 + PCG_S32 * l;
+  float rz_old = w[S32_RZ], rn0 = w[S32_RN0], tol_s = w[S32_TOL], pmax_old = w[S32_PMAX];
+  int sc = (int)w[S32_QEXP];
   constexpr int M4 = CD * CD / 4;
   float m[CD * CD];
   int c0 = threadIdx.x;
@@ -356,97 +566,84 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_step_ff(const int *sub_cam_
     const float4 *Mi = reinterpret_cast<const float4 *>(Minv32 + CD * CD * (size_t)(g0 + c0));
 #pragma unroll
     for (int k = 0; k < M4; k++) {
-      float4 w = __ldg(Mi + k);
-      m[4 * k] = w.x; m[4 * k + 1] = w.y; m[4 * k + 2] = w.z; m[4 * k + 3] = w.w;
+      float4 u = __ldg(Mi + k);
+      m[4 * k] = u.x; m[4 * k + 1] = u.y; m[4 * k + 2] = u.z; m[4 * k + 3] = u.w;
     }
   }
-  float2 pv[PCGF_PER], xv[PCGF_PER], rv[PCGF_PER], qv[PCGF_PER];
+  float pv[PCGF_PER], xv[PCGF_PER], rv[PCGF_PER], qv[PCGF_PER];
 #pragma unroll
   for (int k = 0; k < PCGF_PER; k++) {
     int e = threadIdx.x + k * PCG_THREADS;
-    if (e < n) { pv[k] = p[o + e]; xv[k] = x[o + e]; rv[k] = r[o + e]; qv[k] = ff_split_bits(q[o + e]); }
+    if (e < n) { pv[k] = p[o + e]; xv[k] = x[o + e]; rv[k] = r[o + e]; qv[k] = fixed_to_float(q[o + e], sc); }
   }
-  // q is consumed: zero it for the next product (padding rows only ever get +0)
-#pragma unroll
-  for (int k = 0; k < PCGF_PER; k++) {
-    int e = threadIdx.x + k * PCG_THREADS;
-    if (e < n) q[o + e] = 0.0;
-  }
-  float ph[1] = {0.f}, pl[1] = {0.f};  // p . q
+  float pq = 0.f;
 #pragma unroll
   for (int k = 0; k < PCGF_PER; k++) {
     int e = threadIdx.x + k * PCG_THREADS;
     if (e < n) {
-      float er;
-      float pr = ff_two_prod(pv[k].x, qv[k].x, er);
-      ff_acc(ph[0], pl[0], pr);
-      pl[0] = __fadd_rn(pl[0], __fmaf_rn(pv[k].y, qv[k].x, __fmaf_rn(pv[k].x, qv[k].y, er)));
+      q[o + e] = 0ull;
+      pq = __fmaf_rn(pv[k], qv[k], pq);
     }
   }
-  double pqt[1];
-  ff_cta_sum<1>(ph, pl, red, pqt);
-  if (threadIdx.x == 0) {
-    stop = !(pqt[0] > 0.0);  // breakdown: keep the current iterate
-    if (stop) live[l] = 0;
-    else bc = ff_of(st[4 * l] / pqt[0]);
+  float v1[1] = {pq}, t1[1];
+  f_cta_sum<1>(v1, t1);
+  if (!(t1[0] > 0.f)) {  // breakdown: the stage keeps its current iterate
+    if (threadIdx.x == 0) live[l] = 0;
+    return;
   }
-  __syncthreads();
-  if (stop) return;
-  float2 af = bc, naf = make_float2(-af.x, -af.y);
+  float alpha = rz_old / t1[0];
   float rr = 0.f;
 #pragma unroll
   for (int k = 0; k < PCGF_PER; k++) {
     int e = threadIdx.x + k * PCG_THREADS;
     if (e < n) {
-      x[o + e] = ff_add(xv[k], ff_mul(af, pv[k]));
-      float2 re = ff_add(rv[k], ff_mul(naf, qv[k]));
+      x[o + e] = __fmaf_rn(alpha, pv[k], xv[k]);
+      float re = __fmaf_rn(-alpha, qv[k], rv[k]);
       r[o + e] = re;
       rs[e] = re;
-      rr += re.x * re.x;
+      rr = __fmaf_rn(re, re, rr);
     }
   }
   __syncthreads();
-  float vh[2] = {rr, 0.f}, vl[2] = {0.f, 0.f};  // r.r (FP32 is enough for the test), r.z
+  float rz = 0.f, zmax = 0.f;
   for (int c = threadIdx.x; c < ncam; c += PCG_THREADS) {
     if (c != c0) {  // more cameras than threads: load this block too
       const float4 *Mi = reinterpret_cast<const float4 *>(Minv32 + CD * CD * (size_t)(g0 + c));
 #pragma unroll
       for (int k = 0; k < M4; k++) {
-        float4 w = __ldg(Mi + k);
-        m[4 * k] = w.x; m[4 * k + 1] = w.y; m[4 * k + 2] = w.z; m[4 * k + 3] = w.w;
+        float4 u = __ldg(Mi + k);
+        m[4 * k] = u.x; m[4 * k + 1] = u.y; m[4 * k + 2] = u.z; m[4 * k + 3] = u.w;
       }
     }
-    float rh[CD], rl[CD];
+    float rl[CD];
 #pragma unroll
-    for (int b2 = 0; b2 < CD; b2++) { rh[b2] = rs[CD * c + b2].x; rl[b2] = rs[CD * c + b2].y; }
+    for (int b2 = 0; b2 < CD; b2++) rl[b2] = rs[CD * c + b2];
 #pragma unroll
     for (int a2 = 0; a2 < CD; a2++) {
       float t = 0.f;
 #pragma unroll
-      for (int b2 = 0; b2 < CD; b2++) t += m[CD * a2 + b2] * rh[b2];
+      for (int b2 = 0; b2 < CD; b2++) t = __fmaf_rn(m[CD * a2 + b2], rl[b2], t);
       zs[CD * c + a2] = t;
-      float e;
-      float pr = ff_two_prod(rh[a2], t, e);
-      ff_acc(vh[1], vl[1], pr);
-      vl[1] = __fadd_rn(vl[1], __fmaf_rn(rl[a2], t, e));
+      rz = __fmaf_rn(rl[a2], t, rz);
+      zmax = fmaxf(zmax, fabsf(t));
     }
   }
-  double tot[2];
-  ff_cta_sum<2>(vh, vl, red, tot);  // its barrier also orders the z writes before the reads below
+  float v2[2] = {rr, rz}, t2[2], zm;
+  f_cta_sum_max<2>(v2, zmax, t2, zm);  // its barrier also orders the z writes before the reads below
+  float beta = t2[1] / rz_old;
   if (threadIdx.x == 0) {
-    bc = ff_of(tot[1] / st[4 * l]);
-    st[4 * l] = tot[1];
-    double rel = sqrt(tot[0]) / st[4 * l + 1];
-    st[4 * l + 2] = rel;
+    w[S32_RZ] = t2[1];
+    // max |z + beta p| <= max |z| + |beta| max |p|: the next product's scale
+    float pmax = zm + fabsf(beta) * pmax_old;
+    w[S32_PMAX] = pmax;
+    w[S32_QEXP] = (float)fixed_exp(npad[l], w[S32_SMAX], pmax);
     st[4 * l + 3] += 1.0;
-    if (rel <= tol) live[l] = 0;
+    if (sqrtf(t2[0]) <= tol_s * rn0) live[l] = 0;
   }
-  __syncthreads();
-  float2 bf = bc;
 #pragma unroll
   for (int k = 0; k < PCGF_PER; k++) {
     int e = threadIdx.x + k * PCG_THREADS;
-    if (e < n) p[o + e] = ff_add(make_float2(zs[e], 0.f), ff_mul(bf, pv[k]));
+    if (e < n) p[o + e] = __fmaf_rn(beta, pv[k], zs[e]);
   }
 }
 
@@ -805,16 +1002,18 @@ rpba_status pcg_init(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiAppl
   int L = ctx->L;
   cudaStream_t st = ctx->stream;
   if (!fsai && ff_pcg(ctx)) {
-    RPBA_CUDA(cudaMemsetAsync(ctx->pcg_q, 0, ctx->ytot * sizeof(double), st));
-    auto init_ff = ctx->cd == 8 ? k_pcg_init_ff<8> : k_pcg_init_ff<6>;
-    RPBA_KERNEL(ctx, "k_pcg_init_ff", init_ff<<<L, PCG_THREADS, 0, st>>>(
-                                       run_dev, fail_dev, ctx->sub_cam_ptr, ctx->ycam_off, ctx->npad, ctx->pcg_Minv32,
-                                       ctx->y, ctx->pcg_fx, ctx->pcg_fr, ctx->pcg_fz, ctx->pcg_fp, ctx->pcg_st,
-                                       ctx->pcg_live));
+    RPBA_CUDA(cudaMemsetAsync(ctx->pcg_s32, 0, (size_t)PCG_S32_WORDS * L * sizeof(float), st));
     if (ctx->pcg_tiles_total)
       RPBA_KERNEL(ctx, "k_pcg_split", k_pcg_split<<<ctx->pcg_tiles_total, 256, 0, st>>>(
-                                          ctx->S, ctx->S_off, ctx->npad, ctx->pcg_live, ctx->pcg_tiles, L,
-                                          ctx->pcg_Sff));
+                                          ctx->S, ctx->S_off, ctx->npad, run_dev, fail_dev, ctx->pcg_tiles, L,
+                                          ctx->pcg_Shi, ctx->pcg_Slo, ctx->pcg_s32));
+    auto stage = ctx->cd == 8 ? k_pcg_stage<8> : k_pcg_stage<6>;
+    RPBA_KERNEL(ctx, "k_pcg_stage", stage<<<L, PCG_THREADS, 0, st>>>(
+                                        1, 0, run_dev, fail_dev, ctx->sub_cam_ptr, ctx->ycam_off, ctx->npad,
+                                        ctx->pcg_Minv32, ctx->y, ctx->pcg_q, ctx->pcg_fx, ctx->pcg_x32, ctx->pcg_r32,
+                                        ctx->pcg_z32, ctx->pcg_p32, ctx->pcg_qi, ctx->pcg_st, ctx->pcg_s32,
+                                        ctx->pcg_act, ctx->pcg_live, ctx->opt.pcg_tol, RPBA_PCG_INNER_TOL,
+                                        RPBA_PCG_MAX_STAGES));
     return RPBA_OK;
   }
   if (fsai) {
@@ -836,7 +1035,78 @@ rpba_status pcg_init(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiAppl
   return RPBA_OK;
 }
 
+// count[0] = sub-blocks whose flag is set, count[1] = the most CG iterations
+// any ran; read on the host (synchronising the stream)
+static rpba_status pcg_read_count(Ctx *ctx, const int *flags, int *n_set, int *ran) {
+  cudaStream_t st = ctx->stream;
+  RPBA_CUDA(cudaMemsetAsync(ctx->counters + 8, 0, 2 * sizeof(int), st));
+  RPBA_KERNEL(ctx, "k_pcg_live_count", k_pcg_live_count<<<nblk(ctx->L, 128), 128, 0, st>>>(
+                                           ctx->L, flags, ctx->pcg_st, ctx->counters + 8));
+  RPBA_CUDA(cudaMemcpyAsync(ctx->h_pinned_counter + 8, ctx->counters + 8, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                            st));
+  RPBA_CUDA(cudaStreamSynchronize(st));
+  *n_set = ctx->h_pinned_counter[8];
+  *ran = ctx->h_pinned_counter[9];
+  return RPBA_OK;
+}
+
+// FP32 form: the stages of the refinement after k_pcg_stage's start. Per
+// stage, FP32 CG steps (k_pcg_symv32 + k_pcg_step32) until no sub-block is
+// live, then the float-float residual (k_pcg_symv_ff + k_pcg_stage), which
+// ends the solve of a sub-block or starts its next stage. The live count is
+// read after as many steps as the same stage took in the previous solve,
+// then every 4; the active count after every stage. pcg_max_iter caps the CG
+// steps of all stages together.
+static rpba_status pcg_loop_refined(Ctx *ctx, int *iters) {
+  int L = ctx->L;
+  cudaStream_t st = ctx->stream;
+  int tiles = ctx->pcg_tiles_total;
+  int maxit = ctx->opt.pcg_max_iter;
+  auto step32 = ctx->cd == 8 ? k_pcg_step32<8> : k_pcg_step32<6>;
+  auto stage_k = ctx->cd == 8 ? k_pcg_stage<8> : k_pcg_stage<6>;
+  int it = 0, ran = 0;
+  for (int stage = 0; stage < RPBA_PCG_MAX_STAGES; stage++) {
+    int it0 = it;
+    int next_check = std::min(maxit, it + std::max(2, ctx->pcg_pred_stage[stage]));
+    for (; it < maxit; it++) {
+      RPBA_KERNEL(ctx, "k_pcg_symv32", k_pcg_symv32<<<nblk(tiles, SYMV32_WARPS), 32 * SYMV32_WARPS, 0, st>>>(
+                                           ctx->pcg_Shi, ctx->S_off, ctx->npad, ctx->ycam_off, ctx->pcg_live,
+                                           ctx->pcg_tiles, L, tiles, ctx->pcg_s32, ctx->pcg_p32, ctx->pcg_qi));
+      RPBA_KERNEL(ctx, "k_pcg_step32", step32<<<L, PCG_THREADS, ctx->pcg_ff_smem, st>>>(
+                                           ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_Minv32, ctx->npad,
+                                           ctx->pcg_x32, ctx->pcg_r32, ctx->pcg_p32, ctx->pcg_qi, ctx->pcg_st,
+                                           ctx->pcg_s32, ctx->pcg_live));
+      if (it + 1 == next_check || it == maxit - 1) {
+        int n_live;
+        RPBA_TRY(pcg_read_count(ctx, ctx->pcg_live, &n_live, &ran));
+        if (n_live == 0) {
+          it++;
+          break;
+        }
+        next_check = std::min(maxit, it + 1 + 4);
+      }
+    }
+    ctx->pcg_pred_stage[stage] = it - it0;
+    bool last = it >= maxit || stage + 1 == RPBA_PCG_MAX_STAGES;
+    RPBA_KERNEL(ctx, "k_pcg_symv_ff", k_pcg_symv_ff<<<tiles, SYMV_THREADS, 0, st>>>(
+                                          ctx->pcg_Shi, ctx->pcg_Slo, ctx->S_off, ctx->npad, ctx->ycam_off,
+                                          ctx->pcg_act, ctx->pcg_tiles, L, ctx->pcg_fx, ctx->pcg_x32, ctx->pcg_q));
+    RPBA_KERNEL(ctx, "k_pcg_stage", stage_k<<<L, PCG_THREADS, 0, st>>>(
+                                        0, last ? 1 : 0, nullptr, nullptr, ctx->sub_cam_ptr, ctx->ycam_off,
+                                        ctx->npad, ctx->pcg_Minv32, ctx->y, ctx->pcg_q, ctx->pcg_fx, ctx->pcg_x32,
+                                        ctx->pcg_r32, ctx->pcg_z32, ctx->pcg_p32, ctx->pcg_qi, ctx->pcg_st,
+                                        ctx->pcg_s32, ctx->pcg_act, ctx->pcg_live, ctx->opt.pcg_tol,
+                                        RPBA_PCG_INNER_TOL, RPBA_PCG_MAX_STAGES));
+    int n_act;
+    RPBA_TRY(pcg_read_count(ctx, ctx->pcg_act, &n_act, &ran));
+    if (n_act == 0) break;
+  }
+  if (iters) *iters = ran;
+  return RPBA_OK;
+}
+
 rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai, int *iters) {
+  if (!fsai && ff_pcg(ctx)) return pcg_loop_refined(ctx, iters);
   int L = ctx->L;
   if (iters) *iters = 0;
   cudaStream_t st = ctx->stream;
@@ -845,49 +1115,33 @@ rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai, int *iters) {
   // the first convergence read after as many iterations as the previous solve
   // took (launches for converged sub-blocks return at once), then every 8
   int next_check = std::min(maxit, std::max(8, ctx->pcg_pred));
-  auto step_ff = ctx->cd == 8 ? k_pcg_step_ff<8> : k_pcg_step_ff<6>;
   auto step64 = ctx->cd == 8 ? k_pcg_step<8> : k_pcg_step<6>;
   for (int it = 0; it < maxit; it++) {
-    if (!fsai && ff_pcg(ctx)) {  // q starts at zero (init) and the step zeroes what it consumed
-      RPBA_KERNEL(ctx, "k_pcg_symv_ff", k_pcg_symv_ff<<<tiles, SYMV_THREADS, 0, st>>>(
-                                         ctx->pcg_Sff, ctx->S_off, ctx->npad, ctx->ycam_off, ctx->pcg_live,
-                                         ctx->pcg_tiles, L, ctx->pcg_fp, ctx->pcg_q));
-      RPBA_KERNEL(ctx, "k_pcg_step_ff", step_ff<<<L, PCG_THREADS, ctx->pcg_ff_smem, st>>>(
-                                         ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_Minv32, ctx->opt.pcg_tol,
-                                         ctx->pcg_fx, ctx->pcg_fr, ctx->pcg_fp, ctx->pcg_q, ctx->pcg_st,
-                                         ctx->pcg_live));
+    RPBA_CUDA(cudaMemsetAsync(ctx->pcg_q, 0, ctx->ytot * sizeof(double), st));
+    RPBA_CUDA(cudaMemsetAsync(ctx->pcg_pq, 0, L * sizeof(double), st));
+    RPBA_KERNEL(ctx, "k_pcg_symv", k_pcg_symv<<<tiles, 256, 0, st>>>(
+                                       ctx->S, ctx->S_off, ctx->npad, ctx->ycam_off, ctx->pcg_live, ctx->pcg_tiles,
+                                       L, ctx->pcg_p, ctx->pcg_q, ctx->pcg_pq));
+    if (fsai) {
+      RPBA_KERNEL(ctx, "k_pcg_alpha", k_pcg_alpha<<<L, PCG_THREADS, 0, st>>>(
+                                          ctx->sub_cam_ptr, ctx->ycam_off, ctx->opt.pcg_tol, ctx->pcg_x,
+                                          ctx->pcg_r, ctx->pcg_p, ctx->pcg_q, ctx->pcg_pq, ctx->pcg_st,
+                                          ctx->pcg_live, fsai->P.Li, fsai->rh));
+      RPBA_TRY(fsai_apply(ctx, *fsai, ctx->pcg_live, ctx->pcg_r, ctx->pcg_z, /*skip_first=*/true));
+      RPBA_KERNEL(ctx, "k_pcg_beta", k_pcg_beta<<<L, PCG_THREADS, 0, st>>>(
+                                         ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p,
+                                         ctx->pcg_st, ctx->pcg_live));
     } else {
-      RPBA_CUDA(cudaMemsetAsync(ctx->pcg_q, 0, ctx->ytot * sizeof(double), st));
-      RPBA_CUDA(cudaMemsetAsync(ctx->pcg_pq, 0, L * sizeof(double), st));
-      RPBA_KERNEL(ctx, "k_pcg_symv", k_pcg_symv<<<tiles, 256, 0, st>>>(
-                                         ctx->S, ctx->S_off, ctx->npad, ctx->ycam_off, ctx->pcg_live, ctx->pcg_tiles,
-                                         L, ctx->pcg_p, ctx->pcg_q, ctx->pcg_pq));
-      if (fsai) {
-        RPBA_KERNEL(ctx, "k_pcg_alpha", k_pcg_alpha<<<L, PCG_THREADS, 0, st>>>(
-                                            ctx->sub_cam_ptr, ctx->ycam_off, ctx->opt.pcg_tol, ctx->pcg_x,
-                                            ctx->pcg_r, ctx->pcg_p, ctx->pcg_q, ctx->pcg_pq, ctx->pcg_st,
-                                            ctx->pcg_live, fsai->P.Li, fsai->rh));
-        RPBA_TRY(fsai_apply(ctx, *fsai, ctx->pcg_live, ctx->pcg_r, ctx->pcg_z, /*skip_first=*/true));
-        RPBA_KERNEL(ctx, "k_pcg_beta", k_pcg_beta<<<L, PCG_THREADS, 0, st>>>(
-                                           ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p,
-                                           ctx->pcg_st, ctx->pcg_live));
-      } else {
-        RPBA_KERNEL(ctx, "k_pcg_step", step64<<<L, PCG_THREADS, 0, st>>>(
-                                           ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_Minv, ctx->opt.pcg_tol,
-                                           ctx->pcg_x, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, ctx->pcg_q, ctx->pcg_pq,
-                                           ctx->pcg_st, ctx->pcg_live));
-      }
+      RPBA_KERNEL(ctx, "k_pcg_step", step64<<<L, PCG_THREADS, 0, st>>>(
+                                         ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_Minv, ctx->opt.pcg_tol,
+                                         ctx->pcg_x, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, ctx->pcg_q, ctx->pcg_pq,
+                                         ctx->pcg_st, ctx->pcg_live));
     }
     if (it + 1 == next_check || it == maxit - 1) {
-      RPBA_CUDA(cudaMemsetAsync(ctx->counters + 8, 0, 2 * sizeof(int), st));
-      RPBA_KERNEL(ctx, "k_pcg_live_count", k_pcg_live_count<<<nblk(L, 128), 128, 0, st>>>(
-                                               L, ctx->pcg_live, ctx->pcg_st, ctx->counters + 8));
-      RPBA_CUDA(cudaMemcpyAsync(ctx->h_pinned_counter + 8, ctx->counters + 8, 2 * sizeof(int),
-                                cudaMemcpyDeviceToHost, st));
-      RPBA_CUDA(cudaStreamSynchronize(st));
-      int ran = ctx->h_pinned_counter[9];  // iterations of the slowest sub-block so far
+      int n_live, ran;  // ran: iterations of the slowest sub-block so far
+      RPBA_TRY(pcg_read_count(ctx, ctx->pcg_live, &n_live, &ran));
       if (iters) *iters = ran;
-      if (ctx->h_pinned_counter[8] == 0) {
+      if (n_live == 0) {
         ctx->pcg_pred = ran;
         break;
       }

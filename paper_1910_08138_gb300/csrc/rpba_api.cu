@@ -691,12 +691,15 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
     // solver 1 or auto's PCG in the FP32 form: float-float, for sub-blocks of
     // up to RPBA_PCG_FF_MAX_N unknowns (the step kernel's register batches)
     if (ctx->opt.precision == 1 && ctx->opt.solver == 1 && max_n <= RPBA_PCG_FF_MAX_N) {
-      ctx->pcg_ff_smem = (size_t)std::max(max_n, 1) * (sizeof(float2) + sizeof(float));
-      RPBA_TRY(alloc_n(ctx, &ctx->pcg_Sff, (size_t)std::max(stot, 1LL)));
+      ctx->pcg_ff_smem = (size_t)std::max(max_n, 1) * 2 * sizeof(float);
+      RPBA_TRY(alloc_n(ctx, &ctx->pcg_Shi, (size_t)std::max(stot, 1LL)));
+      RPBA_TRY(alloc_n(ctx, &ctx->pcg_Slo, (size_t)std::max(stot, 1LL)));
       RPBA_TRY(alloc_n(ctx, &ctx->pcg_fx, (size_t)std::max(yt, 1)));
-      RPBA_TRY(alloc_n(ctx, &ctx->pcg_fr, (size_t)std::max(yt, 1)));
-      RPBA_TRY(alloc_n(ctx, &ctx->pcg_fp, (size_t)std::max(yt, 1)));
-      RPBA_TRY(alloc_n(ctx, &ctx->pcg_fz, (size_t)std::max(yt, 1)));
+      for (float **v : {&ctx->pcg_x32, &ctx->pcg_r32, &ctx->pcg_z32, &ctx->pcg_p32})
+        RPBA_TRY(alloc_n(ctx, v, (size_t)std::max(yt, 1)));
+      RPBA_TRY(alloc_n(ctx, &ctx->pcg_qi, (size_t)std::max(yt, 1)));
+      RPBA_TRY(alloc_n(ctx, &ctx->pcg_s32, (size_t)PCG_S32_WORDS * std::max(L, 1)));
+      RPBA_TRY(alloc_n(ctx, &ctx->pcg_act, (size_t)std::max(L, 1)));
       RPBA_TRY(alloc_n(ctx, &ctx->pcg_Minv32, (size_t)ctx->cd * ctx->cd * std::max(M, 1)));
     }
     std::vector<int> pt(L + 1, 0);
@@ -1180,8 +1183,10 @@ extern "C" rpba_status rpba_rcs(rpba_ctx *h, int32_t l, double lambda, double *S
     RPBA_CUDA(cudaMemcpyAsync(yf.data(), ctx->y + yoff, np * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   }
   RPBA_TRY(sync(ctx));
+  // the device keeps the lower triangle; the caller gets the symmetric matrix
   for (int r = 0; r < n; r++) {
-    if (S) for (int c = 0; c < n; c++) S[(size_t)r * n + c] = full[(size_t)r * np + c];
+    if (S)
+      for (int c = 0; c < n; c++) S[(size_t)r * n + c] = c <= r ? full[(size_t)r * np + c] : full[(size_t)c * np + r];
     if (y) y[r] = yf[r];
   }
   return RPBA_OK;
@@ -1285,7 +1290,8 @@ static rpba_status lm_cg(Ctx *ctx) {
   // solver 4 (auto): a solve that needed more lock-step iterations than the
   // direct solve is worth moves the context to the direct solver, from the
   // next LM step on
-  if (ctx->auto_solver && iters > RPBA_AUTO_PCG_MAX_ITER) ctx->auto_switch = true;
+  if (ctx->auto_solver && iters > (ff_pcg(ctx) ? RPBA_AUTO_PCG_MAX_ITER_FP32 : RPBA_AUTO_PCG_MAX_ITER))
+    ctx->auto_switch = true;
   RPBA_TRY(pcg_out(ctx, ctx->lm_run, ctx->lm_cholfail));
   if (ctx->opt.solver == 3) RPBA_TRY(learned_fallback(ctx, ctx->lm_run, ctx->lm_cholfail));
   return RPBA_OK;
@@ -1825,6 +1831,21 @@ extern "C" rpba_status rpba_solver_stats(rpba_ctx *h, int32_t *iters, double *re
     if (iters) iters[l] = (int32_t)st[4 * l + 3];
     if (relres) relres[l] = st[4 * l + 2];
   }
+  return RPBA_OK;
+}
+
+extern "C" rpba_status rpba_solver_stages(rpba_ctx *h, int32_t *stages) {
+  CTX_KEEP_COSTS;
+  if (!stages) return RPBA_ERR_INVALID_ARG;
+  if (!ff_pcg(ctx)) {
+    for (int l = 0; l < ctx->L; l++) stages[l] = 0;
+    return RPBA_OK;
+  }
+  std::vector<float> w((size_t)PCG_S32_WORDS * ctx->L);
+  if (ctx->L)
+    RPBA_CUDA(cudaMemcpyAsync(w.data(), ctx->pcg_s32, w.size() * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+  RPBA_TRY(sync(ctx));
+  for (int l = 0; l < ctx->L; l++) stages[l] = (int32_t)w[(size_t)PCG_S32_WORDS * l + PCG_S32_STAGES];
   return RPBA_OK;
 }
 

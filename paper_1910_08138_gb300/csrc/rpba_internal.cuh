@@ -308,12 +308,19 @@ struct Ctx {
   // thread of the Schur kernel (first pair of each item, then n_pairs)
   int *sitem = nullptr;
   long long n_items = 0;
-  // FP32 form, block-Jacobi PCG in float-float: the RCS as hi + lo pairs (the
-  // layout of S), the vectors x, r, p as pairs and z in FP32, M^-1 in FP32
-  float2 *pcg_Sff = nullptr, *pcg_fx = nullptr, *pcg_fr = nullptr, *pcg_fp = nullptr;
-  float *pcg_fz = nullptr, *pcg_Minv32 = nullptr;
-  size_t pcg_ff_smem = 0;
-  int pcg_pred = 8;        // CG iterations of the previous solve: the first convergence read  // the float-float step's shared memory: r and z of the largest sub-block
+  // FP32 form, block-Jacobi PCG by refinement: the RCS as hi and lo planes
+  // (the layout of S), the solution X in float-float, the FP32 CG vectors of
+  // a stage (x, r, z, p) and its product q, M^-1 in FP32, per-sub-block stage
+  // words and the active flags (stage number + 1 while the solve runs)
+  float *pcg_Shi = nullptr, *pcg_Slo = nullptr;
+  float2 *pcg_fx = nullptr;
+  float *pcg_x32 = nullptr, *pcg_r32 = nullptr, *pcg_z32 = nullptr, *pcg_p32 = nullptr;
+  unsigned long long *pcg_qi = nullptr;  // the CG product S_hi p in 64-bit fixed point
+  float *pcg_Minv32 = nullptr, *pcg_s32 = nullptr;
+  int *pcg_act = nullptr;
+  size_t pcg_ff_smem = 0;  // the FP32 step's shared memory: r and z of the largest sub-block
+  int pcg_pred = 8;        // CG iterations of the previous solve: the first convergence read
+  int pcg_pred_stage[8] = {8, 8, 8, 8, 8, 8, 8, 8};  // the same per refinement stage
   // RCS
   double *S = nullptr, *y = nullptr, *dC = nullptr;  // y, dC: sum of n_pad over l
   long long *S_off = nullptr;
@@ -545,12 +552,19 @@ void build_camera_graph(Ctx *ctx, const std::vector<int> &inst_obs_ptr, const st
 rpba_status pcg_iterate(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiApply *fsai);
 // the phases of pcg_iterate, and the preconditioner set-ups
 rpba_status pcg_init(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiApply *fsai);
-// the FP32 form's block-Jacobi PCG runs in float-float (solver 1, also when
-// chosen by solver 4) when no sub-block has more than RPBA_PCG_FF_MAX_N
-// unknowns (256 threads x 8 elements in registers; r and z, 12 B each, then
-// take at most 24 KB of shared memory)
+// the FP32 form's block-Jacobi PCG runs as FP32 CG stages refined by
+// float-float residuals (solver 1, also when chosen by solver 4) when no
+// sub-block has more than RPBA_PCG_FF_MAX_N unknowns (256 threads x 8
+// elements in registers; r and z, 4 B each, then take at most 16 KB of shared
+// memory). A stage stops at RPBA_PCG_INNER_TOL of its right-hand side (or
+// sooner, where the final tolerance asks for less); at most
+// RPBA_PCG_MAX_STAGES stages per solve.
 #define RPBA_PCG_FF_MAX_N 2048
-inline bool ff_pcg(const Ctx *ctx) { return ctx->pcg_Sff != nullptr && ctx->opt.solver == 1; }
+#define RPBA_PCG_INNER_TOL 1e-4
+#define RPBA_PCG_MAX_STAGES 8
+#define PCG_S32_WORDS 8  // per-sub-block FP32 words of the refinement (pcg_s32)
+#define PCG_S32_STAGES 4 // the word counting the stages of the last solve
+inline bool ff_pcg(const Ctx *ctx) { return ctx->pcg_Shi != nullptr && ctx->opt.solver == 1; }
 rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai, int *iters /* lock-step iterations run, nullable */);
 rpba_status pcg_out(Ctx *ctx, const int *run_dev, const int *fail_dev);
 rpba_status pcg_bj_setup(Ctx *ctx, const int *run_dev, int *fail_dev);

@@ -128,6 +128,7 @@ def load(build_if_missing: bool = True):
         "rpba_profile_read": (C.c_int, [vp, C.c_int32, C.c_char_p, _dp, C.POINTER(C.c_int64), _ip,
                                         C.POINTER(C.c_int64)]),
         "rpba_solver_stats": (C.c_int, [vp, _ip, _dp]),
+        "rpba_solver_stages": (C.c_int, [vp, _ip]),
         "rpba_solver_fallbacks": (C.c_int, [vp, C.POINTER(C.c_int64)]),
         "rpba_gnn_param_count": (C.c_int32, []),
         "rpba_set_gnn_weights": (C.c_int, [vp, _fp, C.c_int32]),
@@ -512,6 +513,13 @@ class Rpba:
         it, rr = np.zeros(self.L, np.int32), np.zeros(self.L)
         self._c(load().rpba_solver_stats(self._h, _i(it), _d(rr)))
         return it, rr
+
+    def solver_stages(self):
+        """Refinement stages of every sub-block in the last FP32-form
+        block-Jacobi PCG solve (zeros for the other solvers)."""
+        n = np.zeros(self.L, np.int32)
+        self._c(load().rpba_solver_stages(self._h, _i(n)))
+        return n
 
     def solver_fallbacks(self):
         n = C.c_int64()

@@ -42,24 +42,42 @@ def test_counted_observations_are_those_of_active_points():
 
 
 class _Ctx:
-    pass
+    """solver_stats / solver_stages of a context, from given arrays."""
+
+    def __init__(self, iters, stages):
+        self.iters, self.stages = np.asarray(iters, np.int32), np.asarray(stages, np.int32)
+
+    def solver_stats(self):
+        return self.iters, np.zeros(self.iters.size)
+
+    def solver_stages(self):
+        return self.stages
 
 
-def test_symv_bytes_are_the_stored_lower_tiles_of_live_sub_blocks():
-    """8 B (hi + lo) per entry of every 32 x 32 lower tile (diagonal included)
-    of the padded RCS, counted over the launches each sub-block was live in."""
-    n_sub = [6 * 25, 6 * 7, 6 * 40]
-    iters = [np.array([5, 2, 9]), np.array([3, 3, 1])]
-    brute_bytes = 0
-    for it in iters:
-        for l, n in enumerate(n_sub):
-            T = -(-n // 32)
-            tiles = sum(1 for a in range(T) for b in range(T) if b <= a)
-            brute_bytes += int(it[l]) * tiles * 32 * 32 * 8
-    launches = sum(int(it.max()) for it in iters)
-    per_launch, live = bench.symv_work(_Ctx(), iters, n_sub)
-    assert per_launch == brute_bytes / launches
-    assert live * 32 * 32 * 8 == per_launch
+def _brute_tiles(n):
+    T = -(-n // 32)
+    return sum(1 for a in range(T) for b in range(T) if b <= a)
+
+
+def test_pcg_bytes_are_the_stored_lower_tiles_of_live_sub_blocks():
+    """Every 32 x 32 lower tile (diagonal included) of the padded RCS of a
+    sub-block is read once per CG step it ran (FP32 form: 4 B per entry, S
+    rounded to FP32; FP64 form: 8 B) and, in the FP32 form, once per
+    refinement stage in hi + lo (8 B per entry)."""
+    n_sub = [6 * 25, 6 * 7, 8 * 40]
+    iters, stages = [5, 2, 9], [2, 1, 3]
+    ctx = _Ctx(iters, stages)
+    w = bench.pcg_work(ctx, n_sub, 1)
+    t32 = sum(i * _brute_tiles(n) for i, n in zip(iters, n_sub))
+    tff = sum(s * _brute_tiles(n) for s, n in zip(stages, n_sub))
+    assert w["k_pcg_symv32"] == (t32 * 32 * 32 * 4, t32)
+    assert w["k_pcg_symv_ff"] == (tff * 32 * 32 * 8, tff)
+    w64 = bench.pcg_work(ctx, n_sub, 0)
+    assert w64 == {"k_pcg_symv": (t32 * 32 * 32 * 8, t32)}
+    acc = {}
+    bench.add_work(acc, w)
+    bench.add_work(acc, w)
+    assert acc["k_pcg_symv32"] == (2 * t32 * 32 * 32 * 4, 2 * t32)
 
 
 def test_clock_summary_median_max_and_reasons():

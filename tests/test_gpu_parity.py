@@ -222,6 +222,11 @@ def test_lm_step_pcg_forms(name, form):
     acc, Fb, Ft, dc, dx = g.lm_step(lam)
     it, rr = g.solver_stats()
     assert np.all(it > 0) and np.all(rr <= pcg_tol)
+    stages = g.solver_stages()
+    # the FP32 form's block-Jacobi PCG refines FP32 CG stages by float-float
+    # residuals: at least one stage, and the reported residual is the true one
+    refined = g.resolved_options().solver == 1
+    assert np.all(stages >= 1) if refined else np.all(stages == 0)
     off = 0
     _, isub = o.instances()
     for l in range(o.L):
@@ -231,6 +236,8 @@ def test_lm_step_pcg_forms(name, form):
         res = np.linalg.norm(S @ dcl - y) / np.linalg.norm(y)
         fp = 1e-12 * np.linalg.norm(np.abs(S) @ np.abs(dcl)) / np.linalg.norm(y)
         assert res <= pcg_tol + fp, (l, res, fp)
+        if refined:
+            assert abs(rr[l] - res) <= 1e-3 * res + 2 * fp, (l, rr[l], res, fp)
         r, fb, ft, dco, dxo = o.lm_step(l, lam)
         np.testing.assert_allclose(Fb[l], fb, rtol=1e-6)
         sc = max(np.abs(dco).max(), 1e-12)
