@@ -171,7 +171,7 @@ __device__ __forceinline__ void ff_load_record(const float *cf, float (&c)[4 * N
 }
 
 // Reprojection residual (Eq. ta) of a point X = Xh + Xl in the camera of
-// record cf against an observation given relative to the principal point as
+// record c (floats [0, 28) of it, in registers) against an observation given relative to the principal point as
 // (oxh + oxl, oyh + oyl): X_c = R (X - C) as float-float, the perspective
 // division with one remainder correction, f times the quotient, and the
 // subtraction of the observation, whose leading parts cancel exactly. The
@@ -179,10 +179,9 @@ __device__ __forceinline__ void ff_load_record(const float *cf, float (&c)[4 * N
 // Returns z_c > 0; the residual is computed either way, as in FP64. With
 // k1on (per-camera intrinsics) f is replaced by f (1 + k1 |q|^2), q the
 // normalised coordinates, all in float-float.
-__device__ __forceinline__ bool ff_residual(const float *cf, const float *Xh, const float *Xl, float oxh, float oxl,
-                                            float oyh, float oyl, float &r0, float &r1, bool k1on = false) {
-  float c[28];
-  ff_load_record<7>(cf, c);
+__device__ __forceinline__ bool ff_residual_rec(const float (&c)[28], const float *Xh, const float *Xl, float oxh,
+                                                float oxl, float oyh, float oyl, float &r0, float &r1,
+                                                bool k1on = false) {
   float dh[3], dl[3];
 #pragma unroll
   for (int k = 0; k < 3; k++) {
@@ -226,6 +225,25 @@ __device__ __forceinline__ bool ff_residual(const float *cf, const float *Xh, co
   r0 = __fadd_rn(__fsub_rn(uh, oxh), __fsub_rn(ue, oxl));
   r1 = __fadd_rn(__fsub_rn(vh, oyh), __fsub_rn(ve, oyl));
   return zh > 0.f;
+}
+
+// the same with the record read from global memory
+__device__ __forceinline__ bool ff_residual(const float *cf, const float *Xh, const float *Xl, float oxh, float oxl,
+                                            float oyh, float oyl, float &r0, float &r1, bool k1on = false) {
+  float c[28];
+  ff_load_record<7>(cf, c);
+  return ff_residual_rec(c, Xh, Xl, oxh, oxl, oyh, oyl, r0, r1, k1on);
+}
+
+// Camera records staged in shared memory: FF_CAM_S float4 per record (seven
+// used), the odd stride spreading neighbouring records over the banks
+#define FF_CAM_S 9
+__device__ __forceinline__ void ff_load_record_s(const float4 *p, float (&c)[28]) {
+#pragma unroll
+  for (int e = 0; e < 7; e++) {
+    float4 a = p[e];
+    c[4 * e] = a.x; c[4 * e + 1] = a.y; c[4 * e + 2] = a.z; c[4 * e + 3] = a.w;
+  }
 }
 
 }  // namespace rpba

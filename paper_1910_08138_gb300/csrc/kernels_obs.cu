@@ -35,6 +35,7 @@ struct View {
   int cd, k1on;
   double *k1, *ft, *k1t;
   const int *cam_sub, *cam_local, *sub_cam_ptr, *sub_cam, *cam_obs_ptr, *cam_obs;
+  const uint16_t *obs_camloc;
   double *X;
   uint8_t *active;
   const int *pt_inst_ptr, *pt_inst;
@@ -78,6 +79,7 @@ static View make_view(Ctx *c) {
   v.M = c->M; v.N = c->N; v.K = c->K; v.L = c->L; v.P = c->P; v.has_winv = c->has_winv;
   v.R = c->R; v.t = c->t; v.intr = c->intr; v.Rt = c->Rt; v.tt = c->tt;
   v.cam_sub = c->cam_sub; v.cam_local = c->cam_local; v.sub_cam_ptr = c->sub_cam_ptr;
+  v.obs_camloc = c->obs_camloc;
   v.sub_cam = c->sub_cam; v.cam_obs_ptr = c->cam_obs_ptr; v.cam_obs = c->cam_obs;
   v.X = c->X; v.active = c->active; v.pt_inst_ptr = c->pt_inst_ptr; v.pt_inst = c->pt_inst;
   v.inst_pt = c->inst_pt; v.inst_sub = c->inst_sub; v.inst_obs_ptr = c->inst_obs_ptr;
@@ -1131,18 +1133,22 @@ struct SigmaAcc {
 // issues after one dependent load; an inactive point's term is dropped at the
 // end.
 template <bool SIG, bool K1>
-__device__ inline float obs_cost_term_f(const View &v, int trial, int k, SigmaAcc *sig = nullptr) {
+__device__ inline float obs_cost_term_f(const View &v, int trial, int k, SigmaAcc *sig = nullptr,
+                                       const float4 *cam_s = nullptr) {
   int q = v.obs_inst[k];
   int j = v.obs_pt[k];  // = inst_pt[q]
-  int i = v.obs_cam[k];
   const bool act = v.active[j] != 0;
-  const float *cf = (trial ? v.camff_t : v.camff) + FF_CAM * (size_t)i;
   const float *Xh = (trial ? v.Xlt_hi : v.Xl_hi) + 3 * (size_t)q;
   const float *Xw = (trial ? v.Xlt_lo : v.Xl_lo) + 3 * (size_t)q;
+  float c[28];
+  if (cam_s)  // the sub-block's records staged in shared memory
+    ff_load_record_s(cam_s + FF_CAM_S * (int)v.obs_camloc[k], c);
+  else
+    ff_load_record<7>((trial ? v.camff_t : v.camff) + FF_CAM * (size_t)v.obs_cam[k], c);
   float r0, r1;
   float F;
-  bool front = ff_residual(cf, Xh, Xw, v.obs_xy32[2 * k], v.obs_xylo[2 * k], v.obs_xy32[2 * k + 1],
-                           v.obs_xylo[2 * k + 1], r0, r1, K1);
+  bool front = ff_residual_rec(c, Xh, Xw, v.obs_xy32[2 * k], v.obs_xylo[2 * k], v.obs_xy32[2 * k + 1],
+                               v.obs_xylo[2 * k + 1], r0, r1, K1);
   if (!front && !SIG) {
     F = INFINITY;
   } else {
@@ -1215,6 +1221,62 @@ __global__ void __launch_bounds__(256) k_cost_chunks_f(View v, int trial, const 
   }
 }
 
+// The same sums with the sub-block's camera records staged in shared memory
+// once per CTA: a CTA takes up to RPBA_COST_GROUP consecutive chunks of one
+// sub-block (group_chunk: the first chunk of each group) and writes every
+// chunk's sums as k_cost_chunks_f does, so the results are the same. In the
+// observations' (sub-block, point) order the 32 lanes of a warp read ~32
+// different cameras: gathered from global memory each camera-record load
+// touches 32 cache lines, staged it is one coalesced copy of the sub-block's
+// records (~112 B per camera) per group.
+static_assert(FF_CAM_S * 16 == RPBA_CAM_STAGE_BYTES, "staged camera record size");
+template <bool SIG, bool K1>
+__global__ void __launch_bounds__(256) k_cost_groups_f(View v, int trial, const int *run, const int *group_chunk,
+                                                       const int *chunk_sub, const int *chunk_start,
+                                                       const int *sub_obs_ptr, const int *sub_chunk_ptr,
+                                                       int n_chunks, double *part, double *sig) {
+  extern __shared__ float4 cam_s[];  // the sub-block's records, FF_CAM_S float4 each
+  __shared__ float2 ws[8];
+  int c0 = group_chunk[blockIdx.x], l = chunk_sub[c0];
+  if (run && !run[l]) return;
+  int c1 = min(c0 + RPBA_COST_GROUP, sub_chunk_ptr[l + 1]);
+  int g0 = v.sub_cam_ptr[l], nl = v.sub_cam_ptr[l + 1] - g0;
+  const float *rec = trial ? v.camff_t : v.camff;
+  for (int e = threadIdx.x; e < 7 * nl; e += blockDim.x) {
+    int r = e / 7, p = e - 7 * r;
+    cam_s[FF_CAM_S * r + p] = __ldg(reinterpret_cast<const float4 *>(rec + FF_CAM * (size_t)v.sub_cam[g0 + r]) + p);
+  }
+  __syncthreads();
+  for (int c = c0; c < c1; c++) {
+    int k = chunk_start[c] + threadIdx.x;
+    SigmaAcc acc;
+    float F = k < sub_obs_ptr[l + 1] ? obs_cost_term_f<SIG, K1>(v, trial, k, &acc, cam_s) : 0.f;
+    int any_inf = __syncthreads_or(isinf(F));
+    float h = any_inf ? 0.f : F, lo = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      float oh = __shfl_down_sync(0xffffffffu, h, o), ol = __shfl_down_sync(0xffffffffu, lo, o);
+      float e;
+      h = ff_two_sum(h, oh, e);
+      lo = __fadd_rn(lo, __fadd_rn(e, ol));
+    }
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = make_float2(h, lo);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float2 t = ws[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); w++) t = ff_add(t, ws[w]);
+      part[c] = any_inf ? (double)INFINITY : ff_to_double(t);
+    }
+    if constexpr (SIG) {
+      int np = 0;
+      for (int j = c * 256 + threadIdx.x; j < v.N; j += n_chunks * 256) np += v.active[j] ? 1 : 0;
+      sigma_cta_sums(acc.sh, acc.sl, acc.rh, acc.rl, acc.n1, acc.n3, np, sig + 5 * (size_t)c);
+    } else {
+      __syncthreads();  // ws is written again by the next chunk
+    }
+  }
+}
+
 // F_l from its chunks in order; with SIG also its chunks' sigma_0 sums
 template <bool SIG>
 __global__ void k_cost_sub_f(int L, const int *run, const int *sub_chunk_ptr, const double *part, double *F,
@@ -1260,10 +1322,32 @@ __global__ void k_seg_final(int L, const int *run, const double *part, double *F
 // ~1e-4 px rounding, which hides the last LM improvements. The FP64 form
 // evaluates them in FP64; the FP32 form in float-float on the FP32 pipes
 // (~1e-10 px), with each term then formed in FP32 and all sums in FP64.
+rpba_status cost_groups_setup(Ctx *ctx) {
+  if (ctx->cost_smem > 48 * 1024) {
+    int b = (int)ctx->cost_smem;
+    RPBA_CUDA(cudaFuncSetAttribute(k_cost_groups_f<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+    RPBA_CUDA(cudaFuncSetAttribute(k_cost_groups_f<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+    RPBA_CUDA(cudaFuncSetAttribute(k_cost_groups_f<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+    RPBA_CUDA(cudaFuncSetAttribute(k_cost_groups_f<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+  }
+  return RPBA_OK;
+}
+
+template <bool SIG>
+static rpba_status cost_groups_launch(Ctx *ctx, const View &v, int trial, const int *run, double *sig) {
+  auto kern = ctx->cd == 8 ? k_cost_groups_f<SIG, true> : k_cost_groups_f<SIG, false>;
+  RPBA_KERNEL(ctx, "k_cost_groups_f", kern<<<ctx->n_groups, 256, ctx->cost_smem, ctx->stream>>>(
+                                         v, trial, run, ctx->group_chunk, ctx->chunk_sub, ctx->chunk_start,
+                                         ctx->sub_obs_ptr, ctx->sub_chunk_ptr, ctx->n_chunks, ctx->chunk_part, sig));
+  return RPBA_OK;
+}
+
 static rpba_status sub_costs_impl(Ctx *ctx, int trial, const int *run, double *F_dev) {
   View v = make_view(ctx);
   if (ctx->opt.precision == 1) {
-    if (ctx->n_chunks && ctx->cd == 8)
+    if (ctx->n_groups)
+      RPBA_TRY(cost_groups_launch<false>(ctx, v, trial, run, nullptr));
+    else if (ctx->n_chunks && ctx->cd == 8)
       RPBA_KERNEL(ctx, "k_cost_chunks_f", k_cost_chunks_f<false, true><<<ctx->n_chunks, 256, 0, ctx->stream>>>(
                                          v, trial, run, ctx->chunk_sub, ctx->chunk_start, ctx->sub_obs_ptr,
                                          ctx->chunk_part, nullptr));
@@ -1300,7 +1384,9 @@ rpba_status cost_sigma0_launch(Ctx *ctx) {
   View v = make_view(ctx);
   double *sig_chunk = ctx->sigma0_part, *sig_sub = sig_chunk + 5 * (size_t)ctx->n_chunks;
   double *sig_tot = sig_sub + 5 * (size_t)ctx->L;
-  if (ctx->cd == 8)
+  if (ctx->n_groups)
+    RPBA_TRY(cost_groups_launch<true>(ctx, v, 0, nullptr, sig_chunk));
+  else if (ctx->cd == 8)
     RPBA_KERNEL(ctx, "k_cost_chunks_f", k_cost_chunks_f<true, true><<<ctx->n_chunks, 256, 0, ctx->stream>>>(
                                          v, 0, nullptr, ctx->chunk_sub, ctx->chunk_start, ctx->sub_obs_ptr,
                                          ctx->chunk_part, sig_chunk));

@@ -578,6 +578,19 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
     RPBA_TRY(upload(ctx, &ctx->sub_chunk_ptr, cp.data(), cp.size()));
     RPBA_TRY(alloc_n(ctx, &ctx->chunk_part, (size_t)std::max(ctx->n_chunks, 1)));
     if (ctx->opt.precision == 1) {
+      // camera records of the largest sub-block staged per CTA (144 B each)
+      int max_cams = 0;
+      for (int l = 0; l < L; l++) max_cams = std::max(max_cams, scp[l + 1] - scp[l]);
+      size_t smem = (size_t)max_cams * RPBA_CAM_STAGE_BYTES;
+      if (smem <= RPBA_COST_STAGE_MAX_SMEM) {
+        std::vector<int> gc;
+        for (int l = 0; l < L; l++)
+          for (int c = cp[l]; c < cp[l + 1]; c += RPBA_COST_GROUP) gc.push_back(c);
+        ctx->n_groups = (int)gc.size();
+        ctx->cost_smem = std::max<size_t>(smem, 16);
+        RPBA_TRY(upload(ctx, &ctx->group_chunk, gc.data(), gc.size()));
+        RPBA_TRY(cost_groups_setup(ctx));
+      }
       RPBA_TRY(alloc_n(ctx, &ctx->f0_cache, (size_t)std::max(L, 1)));
       RPBA_TRY(alloc_n(ctx, &ctx->sigma0_part, 5 * ((size_t)ctx->n_chunks + L + 1)));
     }
@@ -629,6 +642,11 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
   RPBA_TRY(alloc_n(ctx, &ctx->isect_state, (size_t)N));
   RPBA_TRY(alloc_n(ctx, &ctx->isect_iter, (size_t)N));
   RPBA_TRY(upload(ctx, &ctx->obs_cam, ocam.data(), (size_t)K));
+  if (ctx->n_groups) {  // the staged cost kernels index the sub-block's records by local camera
+    std::vector<uint16_t> ocl(K);
+    for (int k = 0; k < K; k++) ocl[k] = (uint16_t)cam_local[ocam[k]];
+    RPBA_TRY(upload(ctx, &ctx->obs_camloc, ocl.data(), (size_t)K));
+  }
   RPBA_TRY(upload(ctx, &ctx->obs_inst, obs_inst.data(), (size_t)K));
   RPBA_TRY(upload(ctx, &ctx->obs_user, order.data(), (size_t)K));
   RPBA_TRY(upload(ctx, &ctx->obs_pt, opt.data(), (size_t)K));

@@ -294,6 +294,7 @@ struct Ctx {
   int *isect_iter = nullptr;
   // observations
   int *obs_cam = nullptr, *obs_inst = nullptr, *obs_user = nullptr, *obs_pt = nullptr;
+  uint16_t *obs_camloc = nullptr;  // camera of each observation within its sub-block (staged cost kernels)
   double *obs_xy = nullptr, *obs_winv = nullptr, *obs_w = nullptr;
   void *NXC = nullptr, *Z = nullptr;  // compute precision, K x 18 each
   // Schur pairs
@@ -347,6 +348,12 @@ struct Ctx {
   // observation, chunks per sub-block (CSR), one partial cost per chunk
   int *chunk_sub = nullptr, *chunk_start = nullptr, *sub_chunk_ptr = nullptr;
   int n_chunks = 0;
+  // groups of up to COST_GROUP chunks of one sub-block (first chunk of each)
+  // for the cost kernels that stage the sub-block's camera records in shared
+  // memory (cost_smem bytes per CTA; 0: the records are read from global memory)
+  int *group_chunk = nullptr;
+  int n_groups = 0;
+  size_t cost_smem = 0;
   double *chunk_part = nullptr;
   // FP32 form: the outer iteration's tail evaluates the sub-block costs with
   // the sigma_0 sums in one pass (every X^l equals its X there); the next
@@ -525,6 +532,12 @@ rpba_status launch_jacobians(Ctx *ctx, double *Jc_dev, double *Jx_dev);
 // values from them after a synchronisation
 rpba_status sigma0_launch(Ctx *ctx);
 rpba_status cost_sigma0_launch(Ctx *ctx);
+// the cost kernels with staged camera records: chunks per CTA, bytes per
+// staged record, the largest staging they take (else the global-memory form)
+#define RPBA_COST_GROUP 4
+#define RPBA_CAM_STAGE_BYTES 144
+#define RPBA_COST_STAGE_MAX_SMEM (96 * 1024)  // 682 cameras: local indices fit 16 bits
+rpba_status cost_groups_setup(Ctx *ctx);
 void sigma0_finish(const Ctx *ctx, double *sigma0, double *rms, long long *n_obs, long long *n_points);
 rpba_status launch_sigma0(Ctx *ctx, double *sigma0, double *rms, long long *n_obs = nullptr,
                           long long *n_points = nullptr);
