@@ -66,6 +66,8 @@ def parse():
                    help="direct solver's FP32 factorisation: 0 CUDA cores, 1 tensor cores per step, 2 persistent")
     p.add_argument("--tune", action="store_true", help="autotune the launch shapes on the block before timing")
     p.add_argument("--no-extras", action="store_true", help="skip e2e / time-to-RMS / cpu legs")
+    p.add_argument("--clock-ms", type=int, default=50,
+                   help="nvidia-smi sampling interval during the timed region (0: no sampling)")
     return p.parse_args()
 
 
@@ -108,6 +110,8 @@ class ClockSampler:
         """Starts the query loop and returns once its first sample arrived
         (nvidia-smi takes a moment to start), so that the timed region that
         follows is sampled from its beginning."""
+        if self.interval_ms <= 0:
+            return
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -128,7 +132,8 @@ class ClockSampler:
         """Summary of the samples taken between host times t0 and t1 (all
         when not given)."""
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            why = "not sampled" if self.interval_ms <= 0 else "nvidia-smi unavailable"
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [why]}
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -465,7 +470,7 @@ def run_ours(args, rank, world):
         torch.distributed.barrier()
     ctx.profile_enable(True)  # resets the counters; the selection stays
     ctx.profile_select(dominant)
-    clocks = ClockSampler(dev)
+    clocks = ClockSampler(dev, args.clock_ms)
     clocks.start()
     times = []
     work_timed = {}

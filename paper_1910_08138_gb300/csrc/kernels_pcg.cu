@@ -35,6 +35,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <string>
 
 #include "rpba_internal.cuh"
 
@@ -422,13 +423,15 @@ __device__ inline void f_cta_sum_max(float (&v)[NV], float m, float (&out)[NV], 
 // X += x, the FP32 solution of the stage just ended, and R = y - q with
 // q = S X from k_pcg_symv_ff (q is zeroed once read). The solve of the
 // sub-block ends when ||R|| <= tol ||y||, when a stage has not halved ||R||,
-// after max_stage stages, or when final is set (the CG iteration cap);
+// after max_stage stages, or at the CG step cap (final set, or the device
+// loop's step count loop_cnt[0] at max_iter);
 // otherwise the FP32 CG restarts on S_hi d = R rounded to FP32: x = 0,
 // z = M^-1 r, p = z, stopping at ||r|| <= max(tol_in, 0.3 tol ||y|| / ||R||)
 // ||R||. st[4l + 2] is the relative true residual ||R|| / ||y||.
 template <int CD>
 __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stage(
-    int first, int final_stage, const int *run, const int *fail, const int *sub_cam_ptr, const int *voff,
+    int first, int final_stage, const int *loop_cnt, int max_iter, const int *run, const int *fail,
+    const int *sub_cam_ptr, const int *voff,
     const int *npad, const float *__restrict__ Minv32, const double *__restrict__ y, double *qd, float2 *X,
     float *x, float *r, float *z, float *p, unsigned long long *q, double *st, float *s32, int *act, int *live,
     double tol, double tol_in, int max_stage) {
@@ -489,7 +492,8 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stage(
     if (first) st[4 * l + 1] = ny;
     st[4 * l + 2] = rel;
     float *w = s32 + PCG_S32 * l;
-    bool done = !(ny > 0.0) || rel <= tol || final_stage || stage >= max_stage ||
+    bool fin = final_stage || (loop_cnt && loop_cnt[0] >= max_iter);
+    bool done = !(ny > 0.0) || rel <= tol || fin || stage >= max_stage ||
                 (!first && !(rel <= 0.5 * (double)w[S32_PREV]));
     if (done) {
       act[l] = 0;
@@ -1009,7 +1013,8 @@ rpba_status pcg_init(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiAppl
                                           ctx->pcg_Shi, ctx->pcg_Slo, ctx->pcg_s32));
     auto stage = ctx->cd == 8 ? k_pcg_stage<8> : k_pcg_stage<6>;
     RPBA_KERNEL(ctx, "k_pcg_stage", stage<<<L, PCG_THREADS, 0, st>>>(
-                                        1, 0, run_dev, fail_dev, ctx->sub_cam_ptr, ctx->ycam_off, ctx->npad,
+                                        1, 0, nullptr, 0, run_dev, fail_dev, ctx->sub_cam_ptr, ctx->ycam_off,
+                                        ctx->npad,
                                         ctx->pcg_Minv32, ctx->y, ctx->pcg_q, ctx->pcg_fx, ctx->pcg_x32, ctx->pcg_r32,
                                         ctx->pcg_z32, ctx->pcg_p32, ctx->pcg_qi, ctx->pcg_st, ctx->pcg_s32,
                                         ctx->pcg_act, ctx->pcg_live, ctx->opt.pcg_tol, RPBA_PCG_INNER_TOL,
@@ -1092,7 +1097,7 @@ static rpba_status pcg_loop_refined(Ctx *ctx, int *iters) {
                                           ctx->pcg_Shi, ctx->pcg_Slo, ctx->S_off, ctx->npad, ctx->ycam_off,
                                           ctx->pcg_act, ctx->pcg_tiles, L, ctx->pcg_fx, ctx->pcg_x32, ctx->pcg_q));
     RPBA_KERNEL(ctx, "k_pcg_stage", stage_k<<<L, PCG_THREADS, 0, st>>>(
-                                        0, last ? 1 : 0, nullptr, nullptr, ctx->sub_cam_ptr, ctx->ycam_off,
+                                        0, last ? 1 : 0, nullptr, 0, nullptr, nullptr, ctx->sub_cam_ptr, ctx->ycam_off,
                                         ctx->npad, ctx->pcg_Minv32, ctx->y, ctx->pcg_q, ctx->pcg_fx, ctx->pcg_x32,
                                         ctx->pcg_r32, ctx->pcg_z32, ctx->pcg_p32, ctx->pcg_qi, ctx->pcg_st,
                                         ctx->pcg_s32, ctx->pcg_act, ctx->pcg_live, ctx->opt.pcg_tol,
@@ -1105,8 +1110,145 @@ static rpba_status pcg_loop_refined(Ctx *ctx, int *iters) {
   return RPBA_OK;
 }
 
+// Condition of a while node of the device-driven loop: some sub-block's flag
+// set and the loop's counter below its limit; inc first adds one to the
+// counter (the body's last kernel counts the pass it ends). The counters
+// bound both loops whatever the flags do: at most max_iter CG steps in all
+// and RPBA_PCG_MAX_STAGES stages.
+__global__ void __launch_bounds__(256) k_pcg_cond(cudaGraphConditionalHandle h, int L, const int *flags, int *cnt,
+                                                  int inc, int limit) {
+  int any = 0;
+  for (int l = threadIdx.x; l < L; l += blockDim.x) any |= flags[l] != 0;
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    int c = *cnt + inc;
+    *cnt = c;
+    cudaGraphSetConditional(h, (any && c < limit) ? 1u : 0u);
+  }
+}
+
+static bool pcg_loop_kernel(const std::string &n) {
+  return n == "k_pcg_symv32" || n == "k_pcg_step32" || n == "k_pcg_cond" || n == "k_pcg_symv_ff" ||
+         n == "k_pcg_stage";
+}
+
+bool pcg_device_loop(const Ctx *ctx) {
+  if (!ff_pcg(ctx) || ctx->pcg_no_device_loop || !ctx->pcg_body_stream[0] || !ctx->pcg_body_stream[1])
+    return false;
+  // conditional bodies take no event-record nodes: a loop kernel that is
+  // being timed runs in the host-driven loop
+  return !(ctx->prof_enabled && (ctx->prof_only.empty() || pcg_loop_kernel(ctx->prof_only)));
+}
+
+// a while node after the work captured so far on st, with its handle; the
+// node's body graph is returned for capture
+static rpba_status add_while(Ctx *ctx, cudaStream_t st, cudaGraphConditionalHandle h, cudaGraph_t *body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  RPBA_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive) {
+    ctx->err = "PCG loop: stream not capturing";
+    return RPBA_ERR_CUDA;
+  }
+  cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};  // the other fields zero
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  RPBA_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+  *body = p.conditional.phGraph_out[0];
+  RPBA_CUDA(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return RPBA_OK;
+}
+
+static rpba_status handle_for(Ctx *ctx, cudaStream_t st, cudaGraphConditionalHandle *h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  RPBA_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+  RPBA_CUDA(cudaGraphConditionalHandleCreate(h, g, 0, 0));
+  return RPBA_OK;
+}
+
+// capture fn's launches on stream bs into body, always ending the capture
+template <class F>
+static rpba_status capture_body(Ctx *ctx, cudaStream_t bs, cudaGraph_t body, std::vector<const char *> *names, F fn) {
+  RPBA_CUDA(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  std::vector<const char *> *prev = ctx->capture_list;
+  ctx->capture_list = names;
+  rpba_status st = fn();
+  ctx->capture_list = prev;
+  cudaGraph_t out = nullptr;
+  cudaError_t e = cudaStreamEndCapture(bs, &out);  // out is body, owned by its node
+  if (st != RPBA_OK) return st;
+  RPBA_CUDA(e);
+  return RPBA_OK;
+}
+
+// FP32 form, the refinement loop inside the graph being captured on the
+// context's stream: a while node over the stages whose body holds a while
+// node over the CG steps, so a solve needs no host read. The step and stage
+// counts go to pinned memory (counters PCG_LOOP_COUNTERS, +1) for the launch
+// count and solver 4's switch, read after the step's synchronisation.
+static rpba_status pcg_loop_device(Ctx *ctx) {
+  int L = ctx->L;
+  cudaStream_t st = ctx->stream, bo = ctx->pcg_body_stream[0], bi = ctx->pcg_body_stream[1];
+  int tiles = ctx->pcg_tiles_total;
+  int maxit = ctx->opt.pcg_max_iter;
+  int *cnt = ctx->counters + PCG_LOOP_COUNTERS;  // [0] CG steps, [1] stages
+  auto step32 = ctx->cd == 8 ? k_pcg_step32<8> : k_pcg_step32<6>;
+  auto stage_k = ctx->cd == 8 ? k_pcg_stage<8> : k_pcg_stage<6>;
+  GraphRec *g = ctx->capture;
+  g->pcg_loop = true;
+  RPBA_CUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof(int), st));
+  cudaGraphConditionalHandle h_out, h_in;
+  RPBA_TRY(handle_for(ctx, st, &h_out));
+  RPBA_KERNEL(ctx, "k_pcg_cond", k_pcg_cond<<<1, 256, 0, st>>>(h_out, L, ctx->pcg_act, cnt + 1, 0,
+                                                                  RPBA_PCG_MAX_STAGES));
+  cudaGraph_t body_out, body_in;
+  RPBA_TRY(add_while(ctx, st, h_out, &body_out));
+  RPBA_TRY(capture_body(ctx, bo, body_out, &g->loop_outer, [&]() -> rpba_status {
+    RPBA_TRY(handle_for(ctx, bo, &h_in));
+    RPBA_KERNEL(ctx, "k_pcg_cond", k_pcg_cond<<<1, 256, 0, bo>>>(h_in, L, ctx->pcg_live, cnt, 0, maxit));
+    RPBA_TRY(add_while(ctx, bo, h_in, &body_in));
+    RPBA_TRY(capture_body(ctx, bi, body_in, &g->loop_inner, [&]() -> rpba_status {
+      RPBA_KERNEL(ctx, "k_pcg_symv32", k_pcg_symv32<<<nblk(tiles, SYMV32_WARPS), 32 * SYMV32_WARPS, 0, bi>>>(
+                                           ctx->pcg_Shi, ctx->S_off, ctx->npad, ctx->ycam_off, ctx->pcg_live,
+                                           ctx->pcg_tiles, L, tiles, ctx->pcg_s32, ctx->pcg_p32, ctx->pcg_qi));
+      RPBA_KERNEL(ctx, "k_pcg_step32", step32<<<L, PCG_THREADS, ctx->pcg_ff_smem, bi>>>(
+                                           ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_Minv32, ctx->npad,
+                                           ctx->pcg_x32, ctx->pcg_r32, ctx->pcg_p32, ctx->pcg_qi, ctx->pcg_st,
+                                           ctx->pcg_s32, ctx->pcg_live));
+      RPBA_KERNEL(ctx, "k_pcg_cond", k_pcg_cond<<<1, 256, 0, bi>>>(h_in, L, ctx->pcg_live, cnt, 1, maxit));
+      return RPBA_OK;
+    }));
+    RPBA_KERNEL(ctx, "k_pcg_symv_ff", k_pcg_symv_ff<<<tiles, SYMV_THREADS, 0, bo>>>(
+                                          ctx->pcg_Shi, ctx->pcg_Slo, ctx->S_off, ctx->npad, ctx->ycam_off,
+                                          ctx->pcg_act, ctx->pcg_tiles, L, ctx->pcg_fx, ctx->pcg_x32, ctx->pcg_q));
+    RPBA_KERNEL(ctx, "k_pcg_stage", stage_k<<<L, PCG_THREADS, 0, bo>>>(
+                                        0, 0, cnt, maxit, nullptr, nullptr, ctx->sub_cam_ptr, ctx->ycam_off,
+                                        ctx->npad, ctx->pcg_Minv32, ctx->y, ctx->pcg_q, ctx->pcg_fx, ctx->pcg_x32,
+                                        ctx->pcg_r32, ctx->pcg_z32, ctx->pcg_p32, ctx->pcg_qi, ctx->pcg_st,
+                                        ctx->pcg_s32, ctx->pcg_act, ctx->pcg_live, ctx->opt.pcg_tol,
+                                        RPBA_PCG_INNER_TOL, RPBA_PCG_MAX_STAGES));
+    RPBA_KERNEL(ctx, "k_pcg_cond", k_pcg_cond<<<1, 256, 0, bo>>>(h_out, L, ctx->pcg_act, cnt + 1, 1,
+                                                                    RPBA_PCG_MAX_STAGES));
+    return RPBA_OK;
+  }));
+  RPBA_CUDA(cudaMemcpyAsync(ctx->h_pinned_counter + PCG_LOOP_COUNTERS, cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                            st));
+  return RPBA_OK;
+}
+
 rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai, int *iters) {
-  if (!fsai && ff_pcg(ctx)) return pcg_loop_refined(ctx, iters);
+  if (!fsai && ff_pcg(ctx)) {
+    if (ctx->capture && pcg_device_loop(ctx)) {
+      if (iters) *iters = 0;  // known after the replay (pinned counters)
+      return pcg_loop_device(ctx);
+    }
+    return pcg_loop_refined(ctx, iters);
+  }
   int L = ctx->L;
   if (iters) *iters = 0;
   cudaStream_t st = ctx->stream;

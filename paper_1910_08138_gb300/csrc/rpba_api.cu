@@ -212,6 +212,8 @@ extern "C" void rpba_destroy(rpba_ctx *h) {
     cudaEventDestroy(r.b);
   }
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+  for (cudaStream_t bs : ctx->pcg_body_stream)
+    if (bs) cudaStreamDestroy(bs);
   delete h;
 }
 
@@ -719,6 +721,13 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
       RPBA_TRY(alloc_n(ctx, &ctx->pcg_s32, (size_t)PCG_S32_WORDS * std::max(L, 1)));
       RPBA_TRY(alloc_n(ctx, &ctx->pcg_act, (size_t)std::max(L, 1)));
       RPBA_TRY(alloc_n(ctx, &ctx->pcg_Minv32, (size_t)ctx->cd * ctx->cd * std::max(M, 1)));
+      // streams on which the device-driven loop's bodies are captured (none:
+      // the host-driven loop)
+      for (cudaStream_t &bs : ctx->pcg_body_stream)
+        if (cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) != cudaSuccess) {
+          cudaGetLastError();
+          bs = nullptr;
+        }
     }
     std::vector<int> pt(L + 1, 0);
     for (int l = 0; l < L; l++) pt[l + 1] = pt[l] + ntiles[l] * (ntiles[l] + 1) / 2;
@@ -1308,7 +1317,8 @@ static rpba_status lm_cg(Ctx *ctx) {
   // solver 4 (auto): a solve that needed more lock-step iterations than the
   // direct solve is worth moves the context to the direct solver, from the
   // next LM step on
-  if (ctx->auto_solver && iters > (ff_pcg(ctx) ? RPBA_AUTO_PCG_MAX_ITER_FP32 : RPBA_AUTO_PCG_MAX_ITER))
+  if (!ctx->capture && ctx->auto_solver &&
+      iters > (ff_pcg(ctx) ? RPBA_AUTO_PCG_MAX_ITER_FP32 : RPBA_AUTO_PCG_MAX_ITER))
     ctx->auto_switch = true;
   RPBA_TRY(pcg_out(ctx, ctx->lm_run, ctx->lm_cholfail));
   if (ctx->opt.solver == 3) RPBA_TRY(learned_fallback(ctx, ctx->lm_run, ctx->lm_cholfail));
@@ -1394,6 +1404,17 @@ static rpba_status account(Ctx *ctx, GraphRec *g) {
     ctx->launches++;
     ctx->launch_by_name[k]++;
   }
+  if (g->pcg_loop) {  // the loop bodies ran as often as their counters say
+    long long steps = ctx->h_pinned_counter[PCG_LOOP_COUNTERS], stages = ctx->h_pinned_counter[PCG_LOOP_COUNTERS + 1];
+    for (const char *k : g->loop_inner) {
+      ctx->launches += steps;
+      ctx->launch_by_name[k] += steps;
+    }
+    for (const char *k : g->loop_outer) {
+      ctx->launches += stages;
+      ctx->launch_by_name[k] += stages;
+    }
+  }
   if (ctx->prof_enabled)
     for (auto &ev : g->events) {
       float t = 0.f;
@@ -1404,14 +1425,29 @@ static rpba_status account(Ctx *ctx, GraphRec *g) {
 }
 
 // one lock-step LM iteration, then the host reads the running count. Direct
-// solvers: one captured graph. PCG solvers: a graph up to the CG start, the
-// CG loop run from the host (it stops on a count read every 8 iterations),
-// and a graph from the back-substitution on.
+// solvers, and the FP32 form's block-Jacobi PCG (its loop as conditional
+// graph nodes): one captured graph. Other PCG solvers, or a timed loop
+// kernel: a graph up to the CG start, the CG loop run from the host (it
+// stops on count reads), and a graph from the back-substitution on.
 static rpba_status lm_step_exec(Ctx *ctx) {
   GraphRec *any = ctx->lm_graph ? ctx->lm_graph : ctx->lm_graph_pre;
   if (any && (any->with_events != ctx->prof_enabled || any->prof_only != ctx->prof_only))
     free_lm_graphs(ctx);  // timing nodes only while profiling
   if (pcg_solver(ctx)) {
+    // FP32 form: the whole step, CG loop included, as one graph
+    if (ctx->use_graphs && pcg_device_loop(ctx)) {
+      if (!ctx->lm_graph) {
+        RPBA_TRY(capture_graph(ctx, &ctx->lm_graph, [&] { return lm_step_body(ctx); }));
+        if (!ctx->lm_graph) ctx->pcg_no_device_loop = true;  // the host-driven loop from now on
+      }
+      if (ctx->lm_graph) {
+        RPBA_CUDA(cudaGraphLaunch(ctx->lm_graph->exec, ctx->stream));
+        RPBA_TRY(sync(ctx));
+        if (ctx->auto_solver && ctx->h_pinned_counter[PCG_LOOP_COUNTERS] > RPBA_AUTO_PCG_MAX_ITER_FP32)
+          ctx->auto_switch = true;
+        return account(ctx, ctx->lm_graph);
+      }
+    }
     if (ctx->use_graphs && !ctx->lm_graph_pre) {
       RPBA_TRY(capture_graph(ctx, &ctx->lm_graph_pre, [&] { return lm_pre_pcg(ctx); }));
       if (ctx->lm_graph_pre) RPBA_TRY(capture_graph(ctx, &ctx->lm_graph_post, [&] { return lm_post(ctx); }));

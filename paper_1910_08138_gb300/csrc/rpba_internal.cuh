@@ -322,6 +322,11 @@ struct Ctx {
   size_t pcg_ff_smem = 0;  // the FP32 step's shared memory: r and z of the largest sub-block
   int pcg_pred = 8;        // CG iterations of the previous solve: the first convergence read
   int pcg_pred_stage[8] = {8, 8, 8, 8, 8, 8, 8, 8};  // the same per refinement stage
+  // the loop as conditional graph nodes: two streams on which its bodies are
+  // captured, and the list that receives the body kernels' names meanwhile
+  cudaStream_t pcg_body_stream[2] = {nullptr, nullptr};
+  std::vector<const char *> *capture_list = nullptr;
+  bool pcg_no_device_loop = false;  // its capture failed once: the host-driven loop
   // RCS
   double *S = nullptr, *y = nullptr, *dC = nullptr;  // y, dC: sum of n_pad over l
   long long *S_off = nullptr;
@@ -466,6 +471,11 @@ struct GraphRec {
   bool with_events = false;  // captured with per-kernel event-record nodes
   std::string prof_only;     // ... for this kernel only (empty: all)
   std::vector<const char *> kernels;
+  // the FP32-form PCG loop as conditional while nodes: the kernels of the
+  // inner (CG step) and outer (refinement stage) bodies, counted per replay
+  // from the loop's device counters
+  bool pcg_loop = false;
+  std::vector<const char *> loop_inner, loop_outer;
   struct Ev {
     const char *name;
     cudaEvent_t a, b;
@@ -507,7 +517,9 @@ struct PhaseTimer {
 
 // after every kernel launch: count it and check the launch status
 inline rpba_status post_launch(Ctx *ctx, const char *name) {
-  if (ctx->capture) {
+  if (ctx->capture_list) {
+    ctx->capture_list->push_back(name);
+  } else if (ctx->capture) {
     ctx->capture->kernels.push_back(name);
   } else {
     ctx->launches++;
@@ -579,6 +591,13 @@ rpba_status pcg_init(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiAppl
 #define PCG_S32_STAGES 4 // the word counting the stages of the last solve
 inline bool ff_pcg(const Ctx *ctx) { return ctx->pcg_Shi != nullptr && ctx->opt.solver == 1; }
 rpba_status pcg_loop(Ctx *ctx, const FsaiApply *fsai, int *iters /* lock-step iterations run, nullable */);
+// counters of the device-driven FP32-form loop: lock-step CG steps and
+// refinement stages of the last solve (device counters[12, 14), copied to
+// h_pinned_counter[12, 14) by the captured graph)
+#define PCG_LOOP_COUNTERS 12
+// the FP32-form PCG loop runs as conditional graph nodes when the LM step is
+// captured (the context's body streams exist and no loop kernel is timed)
+bool pcg_device_loop(const Ctx *ctx);
 rpba_status pcg_out(Ctx *ctx, const int *run_dev, const int *fail_dev);
 rpba_status pcg_bj_setup(Ctx *ctx, const int *run_dev, int *fail_dev);
 rpba_status learned_setup(Ctx *ctx, const int *run_dev, int *fail_dev, FsaiApply *F);
