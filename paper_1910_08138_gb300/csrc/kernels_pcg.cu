@@ -313,19 +313,12 @@ __device__ __forceinline__ float warp_transpose_sum(float (&t)[PT], int lane) {
 // sums of a lane (formed in a fixed order) are added to q as 64-bit fixed-point
 // integers (scale 2^s, fixed_exp), so q does not depend on the order of the
 // atomics and two runs give the same CG iterates.
-#define SYMV32_WARPS 8
-__global__ void __launch_bounds__(32 * SYMV32_WARPS) k_pcg_symv32(const float *__restrict__ Shi,
-                                                                  const long long *S_off, const int *npad,
-                                                                  const int *voff, const int *live,
-                                                                  const int *sched_tiles, int L, int tiles,
-                                                                  const float *__restrict__ s32,
-                                                                  const float *__restrict__ p,
-                                                                  unsigned long long *q) {
-  int lane = threadIdx.x & 31;
-  int idx = blockIdx.x * SYMV32_WARPS + (threadIdx.x >> 5);
-  if (idx >= tiles) return;
-  int l, a, b;
-  tile_of(idx, sched_tiles, L, l, a, b);
+// one tile (one warp): tm = (sub-block, a << 16 | b)
+__device__ __forceinline__ void symv32_tile(const float *__restrict__ Shi, const long long *S_off, const int *npad,
+                                            const int *voff, const int *live, int2 tm,
+                                            const float *__restrict__ s32, const float *__restrict__ p,
+                                            unsigned long long *q, int lane) {
+  int l = tm.x, a = tm.y >> 16, b = tm.y & 0xffff;
   if (!live[l]) return;
   int np = npad[l];
   int sc = (int)s32[PCG_S32 * l + S32_QEXP];
@@ -360,6 +353,25 @@ __global__ void __launch_bounds__(32 * SYMV32_WARPS) k_pcg_symv32(const float *_
     atomicAdd(ql + a * PT + lane, (unsigned long long)(vr + vc));
   }
 }
+
+// The warps stride over the tiles (a grid of a few CTAs per SM), each tile's
+// sub-block and position read from a table (tile_map) in one load.
+#define SYMV32_WARPS 8
+__global__ void __launch_bounds__(32 * SYMV32_WARPS) k_pcg_symv32(const float *__restrict__ Shi,
+                                                                  const long long *S_off, const int *npad,
+                                                                  const int *voff, const int *live,
+                                                                  const int2 *__restrict__ tile_map, int tiles,
+                                                                  const float *__restrict__ s32,
+                                                                  const float *__restrict__ p,
+                                                                  unsigned long long *q) {
+  int lane = threadIdx.x & 31;
+  int nw = gridDim.x * SYMV32_WARPS;
+  for (int idx = blockIdx.x * SYMV32_WARPS + (threadIdx.x >> 5); idx < tiles; idx += nw)
+    symv32_tile(Shi, S_off, npad, voff, live, tile_map[idx], s32, p, q, lane);
+}
+
+// four CTAs of eight warps per SM (152 SMs), or one warp per tile if fewer
+static inline int symv32_grid(int tiles) { return std::max(1, std::min(nblk(tiles, SYMV32_WARPS), 4 * 152)); }
 
 // q[e] (fixed point, scale 2^s) as a float
 __device__ __forceinline__ float fixed_to_float(unsigned long long v, int sc) {
@@ -1074,9 +1086,9 @@ static rpba_status pcg_loop_refined(Ctx *ctx, int *iters) {
     int it0 = it;
     int next_check = std::min(maxit, it + std::max(2, ctx->pcg_pred_stage[stage]));
     for (; it < maxit; it++) {
-      RPBA_KERNEL(ctx, "k_pcg_symv32", k_pcg_symv32<<<nblk(tiles, SYMV32_WARPS), 32 * SYMV32_WARPS, 0, st>>>(
+      RPBA_KERNEL(ctx, "k_pcg_symv32", k_pcg_symv32<<<symv32_grid(tiles), 32 * SYMV32_WARPS, 0, st>>>(
                                            ctx->pcg_Shi, ctx->S_off, ctx->npad, ctx->ycam_off, ctx->pcg_live,
-                                           ctx->pcg_tiles, L, tiles, ctx->pcg_s32, ctx->pcg_p32, ctx->pcg_qi));
+                                           ctx->pcg_tile_map, tiles, ctx->pcg_s32, ctx->pcg_p32, ctx->pcg_qi));
       RPBA_KERNEL(ctx, "k_pcg_step32", step32<<<L, PCG_THREADS, ctx->pcg_ff_smem, st>>>(
                                            ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_Minv32, ctx->npad,
                                            ctx->pcg_x32, ctx->pcg_r32, ctx->pcg_p32, ctx->pcg_qi, ctx->pcg_st,
@@ -1213,9 +1225,9 @@ static rpba_status pcg_loop_device(Ctx *ctx) {
     RPBA_KERNEL(ctx, "k_pcg_cond", k_pcg_cond<<<1, 256, 0, bo>>>(h_in, L, ctx->pcg_live, cnt, 0, maxit));
     RPBA_TRY(add_while(ctx, bo, h_in, &body_in));
     RPBA_TRY(capture_body(ctx, bi, body_in, &g->loop_inner, [&]() -> rpba_status {
-      RPBA_KERNEL(ctx, "k_pcg_symv32", k_pcg_symv32<<<nblk(tiles, SYMV32_WARPS), 32 * SYMV32_WARPS, 0, bi>>>(
+      RPBA_KERNEL(ctx, "k_pcg_symv32", k_pcg_symv32<<<symv32_grid(tiles), 32 * SYMV32_WARPS, 0, bi>>>(
                                            ctx->pcg_Shi, ctx->S_off, ctx->npad, ctx->ycam_off, ctx->pcg_live,
-                                           ctx->pcg_tiles, L, tiles, ctx->pcg_s32, ctx->pcg_p32, ctx->pcg_qi));
+                                           ctx->pcg_tile_map, tiles, ctx->pcg_s32, ctx->pcg_p32, ctx->pcg_qi));
       RPBA_KERNEL(ctx, "k_pcg_step32", step32<<<L, PCG_THREADS, ctx->pcg_ff_smem, bi>>>(
                                            ctx->sub_cam_ptr, ctx->ycam_off, ctx->pcg_Minv32, ctx->npad,
                                            ctx->pcg_x32, ctx->pcg_r32, ctx->pcg_p32, ctx->pcg_qi, ctx->pcg_st,

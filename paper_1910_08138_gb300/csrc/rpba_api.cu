@@ -733,6 +733,13 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
     for (int l = 0; l < L; l++) pt[l + 1] = pt[l] + ntiles[l] * (ntiles[l] + 1) / 2;
     ctx->pcg_tiles_total = pt[L];
     RPBA_TRY(upload(ctx, &ctx->pcg_tiles, pt.data(), (size_t)L + 1));
+    if (ctx->pcg_Shi) {  // the FP32 CG product's tile table: (sub-block, a << 16 | b) per lower tile
+      std::vector<int2> tm((size_t)std::max(pt[L], 1));
+      for (int l = 0; l < L; l++)
+        for (int a = 0, t = pt[l]; a < ntiles[l]; a++)
+          for (int b = 0; b <= a; b++, t++) tm[t] = make_int2(l, (a << 16) | b);
+      RPBA_TRY(upload(ctx, &ctx->pcg_tile_map, tm.data(), tm.size()));
+    }
   }
   if (ctx->opt.solver == 2 || ctx->auto_solver) {
     RPBA_TRY(alloc_n(ctx, &ctx->S32, (size_t)std::max(stot, 1LL)));

@@ -317,6 +317,7 @@ struct Ctx {
   float2 *pcg_fx = nullptr;
   float *pcg_x32 = nullptr, *pcg_r32 = nullptr, *pcg_z32 = nullptr, *pcg_p32 = nullptr;
   unsigned long long *pcg_qi = nullptr;  // the CG product S_hi p in 64-bit fixed point
+  int2 *pcg_tile_map = nullptr;           // per lower tile of the running RCS: (sub-block, a << 16 | b)
   float *pcg_Minv32 = nullptr, *pcg_s32 = nullptr;
   int *pcg_act = nullptr;
   size_t pcg_ff_smem = 0;  // the FP32 step's shared memory: r and z of the largest sub-block
