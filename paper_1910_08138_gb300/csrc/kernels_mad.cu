@@ -229,6 +229,9 @@ struct MadIn {
   const double *R, *t, *intr, *X, *obs_xy, *whiten;
   const float *camff, *Xh, *Xl, *oxy, *oxylo, *whiten32;
   const double *k1;  // per-camera radial parameter (NULL without intrinsics)
+  // FP32 form: the observation streams in camera-major order (the order of cam_obs)
+  const int *cm_pt;
+  const float *cm_xy, *cm_xylo, *cm_whiten32;
 };
 
 template <typename Key, bool K1>
@@ -243,18 +246,18 @@ __global__ void k_camera_mad(int M, MadIn in, const uint8_t *active, const int *
   __syncthreads();
   int p0 = cam_obs_ptr[i], p1 = cam_obs_ptr[i + 1];
   for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-    int k = cam_obs[p];
-    int j = obs_pt[k];
     Key k0, k1;
     if constexpr (sizeof(Key) == 4) {  // keys straight from the FP32 components
-      // the active flag is read beside the residual's gathers, not before them
+      // the observation from the camera-major streams (coalesced); the active
+      // flag is read beside the residual's gathers, not before them
+      int j = in.cm_pt[p];
       const bool act = active[j] != 0;
       float r0, r1;
-      ff_residual(in.camff + FF_CAM * (size_t)i, in.Xh + 3 * (size_t)j, in.Xl + 3 * (size_t)j, in.oxy[2 * k],
-                  in.oxylo[2 * k], in.oxy[2 * k + 1], in.oxylo[2 * k + 1], r0, r1, K1);
+      ff_residual(in.camff + FF_CAM * (size_t)i, in.Xh + 3 * (size_t)j, in.Xl + 3 * (size_t)j, in.cm_xy[2 * (size_t)p],
+                  in.cm_xylo[2 * (size_t)p], in.cm_xy[2 * (size_t)p + 1], in.cm_xylo[2 * (size_t)p + 1], r0, r1, K1);
       if (!act) continue;
       if (has_winv) {
-        const float *F = in.whiten32 + 3 * (size_t)k;
+        const float *F = in.cm_whiten32 + 3 * (size_t)p;
         float a = F[0] * r0 + F[1] * r1, b = F[2] * r1;
         r0 = a;
         r1 = b;
@@ -262,6 +265,8 @@ __global__ void k_camera_mad(int M, MadIn in, const uint8_t *active, const int *
       k0 = fkey(r0);
       k1 = fkey(r1);
     } else {
+      int k = cam_obs[p];
+      int j = obs_pt[k];
       if (!active[j]) continue;
       double pu, pv;
       proj64(in.R + 9 * i, in.t + 3 * i, in.intr[3 * i], in.k1 ? in.k1[i] : 0.0, in.intr[3 * i + 1],
@@ -349,7 +354,7 @@ rpba_status launch_camera_scale(Ctx *ctx) {
   }
   MadIn in{ctx->R, ctx->t, ctx->intr, ctx->X, ctx->obs_xy, ctx->obs_whiten,
            ctx->camff, ctx->X_hi, ctx->X_lo, ctx->obs_xy32, ctx->obs_xylo, ctx->obs_whiten32,
-           ctx->cd == 8 ? ctx->k1 : nullptr};
+           ctx->cd == 8 ? ctx->k1 : nullptr, ctx->cm_pt, ctx->cm_xy32, ctx->cm_xylo, ctx->cm_whiten32};
   int threads = std::min(1024, std::max(32, n2 / 2));  // one thread per compare-exchange of a pass
   if (f32) {
     // two observations per thread (up to 1024 threads): the residual phase is

@@ -36,6 +36,8 @@ struct View {
   double *k1, *ft, *k1t;
   const int *cam_sub, *cam_local, *sub_cam_ptr, *sub_cam, *cam_obs_ptr, *cam_obs;
   const uint16_t *obs_camloc;
+  const int *cm_pt, *cm_inst;
+  const float *cm_xy32, *cm_winv32;
   double *X;
   uint8_t *active;
   const int *pt_inst_ptr, *pt_inst;
@@ -80,6 +82,7 @@ static View make_view(Ctx *c) {
   v.R = c->R; v.t = c->t; v.intr = c->intr; v.Rt = c->Rt; v.tt = c->tt;
   v.cam_sub = c->cam_sub; v.cam_local = c->cam_local; v.sub_cam_ptr = c->sub_cam_ptr;
   v.obs_camloc = c->obs_camloc;
+  v.cm_pt = c->cm_pt; v.cm_inst = c->cm_inst; v.cm_xy32 = c->cm_xy32; v.cm_winv32 = c->cm_winv32;
   v.sub_cam = c->sub_cam; v.cam_obs_ptr = c->cam_obs_ptr; v.cam_obs = c->cam_obs;
   v.X = c->X; v.active = c->active; v.pt_inst_ptr = c->pt_inst_ptr; v.pt_inst = c->pt_inst;
   v.inst_pt = c->inst_pt; v.inst_sub = c->inst_sub; v.inst_obs_ptr = c->inst_obs_ptr;
@@ -1322,6 +1325,39 @@ __global__ void k_seg_final(int L, const int *run, const double *part, double *F
 // ~1e-4 px rounding, which hides the last LM improvements. The FP64 form
 // evaluates them in FP64; the FP32 form in float-float on the FP32 pipes
 // (~1e-10 px), with each term then formed in FP32 and all sums in FP64.
+// dst[p] = src[list[p]] for rows of w words
+template <typename T>
+__global__ void k_gather_rows(long long n, int w, const int *list, const T *src, T *dst) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * w) return;
+  long long r = e / w;
+  dst[e] = src[(long long)list[r] * w + (e - r * w)];
+}
+
+rpba_status camera_major_setup(Ctx *ctx) {
+  long long K = ctx->K;
+  if (ctx->opt.precision != 1 || K == 0) return RPBA_OK;
+  RPBA_TRY(ctx_alloc(ctx, (void **)&ctx->cm_pt, K * sizeof(int)));
+  RPBA_TRY(ctx_alloc(ctx, (void **)&ctx->cm_inst, K * sizeof(int)));
+  RPBA_TRY(ctx_alloc(ctx, (void **)&ctx->cm_xy32, 2 * K * sizeof(float)));
+  RPBA_TRY(ctx_alloc(ctx, (void **)&ctx->cm_xylo, 2 * K * sizeof(float)));
+  auto g = [&](auto *src, auto *dst, int w, const char *what) -> rpba_status {
+    RPBA_KERNEL(ctx, what, (k_gather_rows<<<nblk(K * w, 256), 256, 0, ctx->stream>>>(K, w, ctx->cam_obs, src, dst)));
+    return RPBA_OK;
+  };
+  RPBA_TRY(g(ctx->obs_pt, ctx->cm_pt, 1, "k_gather_rows"));
+  RPBA_TRY(g(ctx->obs_inst, ctx->cm_inst, 1, "k_gather_rows"));
+  RPBA_TRY(g(ctx->obs_xy32, ctx->cm_xy32, 2, "k_gather_rows"));
+  RPBA_TRY(g(ctx->obs_xylo, ctx->cm_xylo, 2, "k_gather_rows"));
+  if (ctx->has_winv) {
+    RPBA_TRY(ctx_alloc(ctx, (void **)&ctx->cm_winv32, 3 * K * sizeof(float)));
+    RPBA_TRY(ctx_alloc(ctx, (void **)&ctx->cm_whiten32, 3 * K * sizeof(float)));
+    RPBA_TRY(g(ctx->obs_winv32, ctx->cm_winv32, 3, "k_gather_rows"));
+    RPBA_TRY(g(ctx->obs_whiten32, ctx->cm_whiten32, 3, "k_gather_rows"));
+  }
+  return RPBA_OK;
+}
+
 rpba_status cost_groups_setup(Ctx *ctx) {
   if (ctx->cost_smem > 48 * 1024) {
     int b = (int)ctx->cost_smem;
@@ -1562,14 +1598,31 @@ __device__ inline void z_of(const float inv[6], const float B[3 * CD], float Zk[
 // one observation k (instance q) of camera i: its terms of U, SZ, gc and yz
 // added to acc when act (the point is active)
 template <typename T, int CD>
+__device__ __forceinline__ void cb_obs_body(const View &v, int i, int k, int q, bool act, const ObsT<T> &ob,
+                                            const T *NXC, const T *Z, const T *gX, const T *Ninv, T *acc);
+
+template <typename T, int CD>
 __device__ __forceinline__ void cb_obs(const View &v, int i, int k, int q, bool act, const T *NXC, const T *Z,
                                        const T *gX, const T *Ninv, T *acc) {
+  ObsT<T> ob;
+  load_obs<T>(v, k, ob);
+  cb_obs_body<T, CD>(v, i, k, q, act, ob, NXC, Z, gX, Ninv, acc);
+}
+
+// FP32 form: the observation already loaded (from the camera-major streams)
+template <typename T, int CD>
+__device__ __forceinline__ void cb_obs_ob(const View &v, int i, int q, bool act, const ObsT<T> &ob, const T *Ninv,
+                                          const T *gX, T *acc) {
+  cb_obs_body<T, CD>(v, i, 0, q, act, ob, nullptr, nullptr, gX, Ninv, acc);
+}
+
+template <typename T, int CD>
+__device__ __forceinline__ void cb_obs_body(const View &v, int i, int k, int q, bool act, const ObsT<T> &ob,
+                                            const T *NXC, const T *Z, const T *gX, const T *Ninv, T *acc) {
   constexpr int NU = CD * (CD + 1) / 2;
   ProjJac<T, CD> pj;
   T z;
   obs_proj<T, CD>(v, i, v.Xl + 3 * (size_t)q, v.Xl_hi + 3 * (size_t)q, v.Xl_lo + 3 * (size_t)q, pj, z);
-  ObsT<T> ob;
-  load_obs<T>(v, k, ob);
   T r0 = pj.u - ob.x, r1 = pj.v - ob.y;
   T b0[CD], b1[CD];  // w W A_C
 #pragma unroll
@@ -1626,19 +1679,23 @@ __global__ void __launch_bounds__(CB_THREADS) k_camera_blocks(View v, const doub
   for (int e = 0; e < NA; e++) acc[e] = 0;
   const int p1 = v.cam_obs_ptr[i + 1];
   if constexpr (sizeof(T) == sizeof(float)) {
-    // the observation list walked one element ahead: the next observation's
-    // position and instance load while this one's arithmetic runs, and the
-    // point's active flag is read beside this one's gathers, not before them
-    int p = v.cam_obs_ptr[i] + threadIdx.x;
-    int k = p < p1 ? v.cam_obs[p] : 0;
-    int q = p < p1 ? v.obs_inst[k] : 0;
-    for (; p < p1; p += CB_THREADS) {
-      const int pn = p + CB_THREADS;
-      const int kn = pn < p1 ? v.cam_obs[pn] : 0;
-      const bool act = v.active[v.obs_pt[k]] != 0;
-      cb_obs<T, CD>(v, i, k, q, act, NXC, Z, gX, Ninv, acc);
-      k = kn;
-      q = pn < p1 ? v.obs_inst[kn] : 0;
+    // the camera's observations from the camera-major streams (coalesced);
+    // only the robust weight (it changes) is gathered by observation, and the
+    // point's active flag is read beside the other gathers, not before them
+    for (int p = v.cam_obs_ptr[i] + threadIdx.x; p < p1; p += CB_THREADS) {
+      int q = v.cm_inst[p];
+      const bool act = v.active[v.cm_pt[p]] != 0;
+      ObsT<float> ob;
+      ob.x = v.cm_xy32[2 * (size_t)p];
+      ob.y = v.cm_xy32[2 * (size_t)p + 1];
+      if (v.has_winv) {
+        ob.W[0] = v.cm_winv32[3 * (size_t)p]; ob.W[1] = v.cm_winv32[3 * (size_t)p + 1];
+        ob.W[2] = v.cm_winv32[3 * (size_t)p + 2];
+      } else {
+        ob.W[0] = 1.f; ob.W[1] = 0.f; ob.W[2] = 1.f;
+      }
+      ob.w = v.obs_w32[v.cam_obs[p]];
+      cb_obs_ob<T, CD>(v, i, q, act, ob, Ninv, gX, acc);
     }
   } else {
     for (int p = v.cam_obs_ptr[i] + threadIdx.x; p < p1; p += CB_THREADS) {

@@ -752,6 +752,7 @@ static rpba_status build(Ctx *ctx, const rpba_problem *pb) {
     RPBA_TRY(alloc_n(ctx, &ctx->ir_t, (size_t)std::max(yt, 1)));
     RPBA_TRY(tc_chol_setup(ctx));  // the tensor-core forms, for chol_tc and the autotuner
   }
+  RPBA_TRY(camera_major_setup(ctx));
   RPBA_TRY(alloc_n(ctx, &ctx->wrho, 1));
   RPBA_CUDA(cudaMemcpyAsync(ctx->wrho, &ctx->opt.rho0, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   RPBA_TRY(alloc_n(ctx, &ctx->sub_mask, (size_t)std::max(L, 1)));

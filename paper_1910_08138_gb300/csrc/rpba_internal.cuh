@@ -295,6 +295,11 @@ struct Ctx {
   // observations
   int *obs_cam = nullptr, *obs_inst = nullptr, *obs_user = nullptr, *obs_pt = nullptr;
   uint16_t *obs_camloc = nullptr;  // camera of each observation within its sub-block (staged cost kernels)
+  // FP32 form: the static observation streams in camera-major order (the
+  // order of cam_obs), for the per-camera kernels (MAD, camera blocks): point,
+  // instance, position (hi, lo), C^-1 and its upper Cholesky factor
+  int *cm_pt = nullptr, *cm_inst = nullptr;
+  float *cm_xy32 = nullptr, *cm_xylo = nullptr, *cm_winv32 = nullptr, *cm_whiten32 = nullptr;
   double *obs_xy = nullptr, *obs_winv = nullptr, *obs_w = nullptr;
   void *NXC = nullptr, *Z = nullptr;  // compute precision, K x 18 each
   // Schur pairs
@@ -551,6 +556,8 @@ rpba_status cost_sigma0_launch(Ctx *ctx);
 #define RPBA_CAM_STAGE_BYTES 144
 #define RPBA_COST_STAGE_MAX_SMEM (96 * 1024)  // 682 cameras: local indices fit 16 bits
 rpba_status cost_groups_setup(Ctx *ctx);
+// the camera-major copies (FP32 form), from the observation-order arrays
+rpba_status camera_major_setup(Ctx *ctx);
 void sigma0_finish(const Ctx *ctx, double *sigma0, double *rms, long long *n_obs, long long *n_points);
 rpba_status launch_sigma0(Ctx *ctx, double *sigma0, double *rms, long long *n_obs = nullptr,
                           long long *n_points = nullptr);
