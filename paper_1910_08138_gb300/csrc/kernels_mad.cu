@@ -357,9 +357,10 @@ rpba_status launch_camera_scale(Ctx *ctx) {
            ctx->cd == 8 ? ctx->k1 : nullptr, ctx->cm_pt, ctx->cm_xy32, ctx->cm_xylo, ctx->cm_whiten32};
   int threads = std::min(1024, std::max(32, n2 / 2));  // one thread per compare-exchange of a pass
   if (f32) {
-    // two observations per thread (up to 1024 threads): the residual phase is
-    // a chain of dependent gathers, so it wants many threads in flight
-    threads = std::min(1024, std::max(64, 32 * ((ctx->max_cam_obs + 63) / 64)));  // two observations per thread
+    // two observations per thread, at most 512 threads: with the camera-major
+    // streams the residual phase is no longer a chain of gathers, and the
+    // selects' barriers are cheaper on smaller CTAs (more of them per SM)
+    threads = std::min(512, std::max(64, 32 * ((ctx->max_cam_obs + 63) / 64)));
     auto kern = ctx->cd == 8 ? k_camera_mad<unsigned, true> : k_camera_mad<unsigned, false>;
     if (smem > 48 * 1024)
       RPBA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
