@@ -218,6 +218,8 @@ def kernel_models(K, N, P, M, has_winv, pairs, tps=None, cd=6):
     return {
         "k_obs_sigma_f": ("hbm", K * ob + N * 25 + M * 128),
         "k_cost_chunks_f": ("hbm", K * ob + P * 72 + M * 128),
+        # the same with the sub-block's records staged: plus a 16-bit local camera index per observation
+        "k_cost_groups_f": ("hbm", K * (ob + 2) + P * 72 + M * 128),
         "k_robust_weights_f": ("hbm", K * (ob + 12) + N * 25 + M * 132),
         "k_camera_mad_u32": ("hbm", K * ob + N * 25 + M * 136),
         # the TP intersection: the tie points' observations, positions and instances
@@ -548,6 +550,8 @@ def run_ours(args, rank, world):
                        "step": "1 steady-state outer iteration: 1 LM iteration of all sub-blocks + exchange + "
                                "robust weights + TP intersection + sigma_0",
                        "parallelism": f"replicas x{world}"},
+            "step_ms_spread": {"min": float(np.min(times)), "median": float(np.median(times)),
+                               "max": float(np.max(times))},
             "roofline": roof, "hot_kernels": hot, "gpu_launches": launches,
             "gpu_launches_per_step": launches / args.steps, "clocks": clk,
             "kernels_last_warmup_step": kernels}
