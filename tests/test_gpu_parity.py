@@ -185,7 +185,8 @@ def test_lm_step(name, form):
     np.testing.assert_allclose(g.cameras(), o.cameras(), atol=1e-8 if precision == 0 else 1e-4)
 
 
-# the FP32 form's iterative solvers: float-float block-Jacobi PCG (1), the auto
+# the FP32 form's iterative solvers: block-Jacobi PCG (1, FP32 CG stages refined by float-float
+# residuals), the auto
 # choice the benchmark runs (4, which resolves to 1 on these blocks) and the
 # learned preconditioner (3)
 PCG_FORMS = [(1, 1), (1, 4), (1, 3)]

@@ -86,11 +86,12 @@ def test_block1000_reduced_camera_systems(block1000):
 
 
 def test_block1000_lm_step_chosen_solver(block1000):
-    """The benchmark's form (FP32 bulk, auto solver = float-float block-Jacobi
-    PCG on 8 sub-blocks): camera and point steps against the oracle's Cholesky
-    step at the FP32 assembly's tolerance, the true relative residual of each
-    sub-block's PCG solution against the GPU's own RCS at pcg_tol plus the
-    float-float rounding, and the same accept/reject decisions."""
+    """The benchmark's form (FP32 bulk, auto solver = block-Jacobi PCG on 8
+    sub-blocks, FP32 CG stages refined by float-float residuals): camera and
+    point steps against the oracle's Cholesky step at the FP32 assembly's
+    tolerance, the true relative residual of each sub-block's PCG solution
+    against the GPU's own RCS at pcg_tol plus the float-float rounding, and the
+    same accept/reject decisions."""
     prob, o = block1000
     g = rpba.Rpba(prob, precision=1, solver=4)
     assert g.resolved_options().solver == 1
