@@ -159,6 +159,37 @@ __device__ inline void cam_point_f(const View &v, int i, const float *Xh, const 
   o.k1 = v.k1on ? __ldg(p + 6).z : 0.f;  // record float 26
 }
 
+// the FP32 projection's words of a camera record held in registers (R, C hi
+// and lo, f; t; k1), for a thread that projects many points into one camera
+struct CamRecF {
+  float c[16], t[3], k1;
+};
+
+__device__ inline void load_cam_rec(const View &v, int i, CamRecF &r) {
+  const float4 *p = reinterpret_cast<const float4 *>(v.camff + FF_CAM * (size_t)i);
+#pragma unroll
+  for (int e = 0; e < 4; e++) {
+    float4 a = __ldg(p + e);
+    r.c[4 * e] = a.x; r.c[4 * e + 1] = a.y; r.c[4 * e + 2] = a.z; r.c[4 * e + 3] = a.w;
+  }
+  float4 tt = __ldg(p + 7);
+  r.t[0] = tt.y; r.t[1] = tt.z; r.t[2] = tt.w;
+  r.k1 = v.k1on ? __ldg(p + 6).z : 0.f;  // record float 26
+}
+
+// cam_point_f's arithmetic on a record in registers
+__device__ inline void cam_point_rec(const CamRecF &r, const float *Xh, const float *Xlw, CamPt<float> &o) {
+  float d[3];
+  for (int k = 0; k < 3; k++) d[k] = (Xh[k] - r.c[9 + k]) + (Xlw[k] - r.c[12 + k]);
+  for (int e = 0; e < 9; e++) o.R[e] = r.c[e];
+  for (int k = 0; k < 3; k++) {
+    o.Xc[k] = o.R[3 * k] * d[0] + o.R[3 * k + 1] * d[1] + o.R[3 * k + 2] * d[2];
+    o.RX[k] = o.Xc[k] - r.t[k];
+  }
+  o.f = r.c[15]; o.cx = 0.f; o.cy = 0.f;
+  o.k1 = r.k1;
+}
+
 __device__ inline void split(double x, float &hi, float &lo) {
   hi = (float)x;
   lo = (float)(x - (double)hi);
@@ -1581,6 +1612,24 @@ __device__ inline void nxc_f(const View &v, int i, int k, int q, float B[3 * CD]
   }
 }
 
+// the same with the camera's record in registers
+template <int CD>
+__device__ inline void nxc_f_rec(const View &v, const CamRecF &rec, int k, int q, float B[3 * CD]) {
+  ProjJac<float, CD> pj;
+  CamPt<float> cp;
+  cam_point_rec(rec, v.Xl_hi + 3 * (size_t)q, v.Xl_lo + 3 * (size_t)q, cp);
+  project_jac<float, CD>(cp.R, cp.Xc, cp.RX, cp.f, cp.k1, 0.f, 0.f, pj);
+  float w = v.obs_w32[k], W0 = 1.f, W1 = 0.f, W2 = 1.f;
+  if (v.has_winv) { W0 = v.obs_winv32[3 * k]; W1 = v.obs_winv32[3 * k + 1]; W2 = v.obs_winv32[3 * k + 2]; }
+#pragma unroll
+  for (int r = 0; r < 3; r++) {
+    float a0 = w * (W0 * pj.Jx[r] + W1 * pj.Jx[3 + r]);
+    float a1 = w * (W1 * pj.Jx[r] + W2 * pj.Jx[3 + r]);
+#pragma unroll
+    for (int c = 0; c < CD; c++) B[CD * r + c] = a0 * pj.Jc[c] + a1 * pj.Jc[CD + c];
+  }
+}
+
 // Z = Ninv N_XC (3 x CD) with Ninv a packed symmetric 3x3
 template <int CD>
 __device__ inline void z_of(const float inv[6], const float B[3 * CD], float Zk[3 * CD]) {
@@ -1788,13 +1837,18 @@ __global__ void __launch_bounds__(SC_THREADS, CD == 6 ? 2 : 1) k_schur_seg(View 
     int t0 = item[it], t1 = item[it + 1];
     sg = sps[t0];
     int i = seg_cam[sg], ib = seg_nb[sg];
-    if (run[v.cam_sub[i]])
+    if (run[v.cam_sub[i]]) {
+      // the item's two cameras, read once for its pairs (a warp's lanes read
+      // ~32 different records: per pair that was twice five gathered loads)
+      CamRecF ra, rb;
+      load_cam_rec(v, i, ra);
+      load_cam_rec(v, ib, rb);
       for (int t = t0; t < t1; t++) {
         int q = spq[t];
         if (!v.active[v.inst_pt[q]]) continue;
         float A[3 * CD], B[3 * CD], Zb[3 * CD];
-        nxc_f<CD>(v, i, spa[t], q, A);
-        nxc_f<CD>(v, ib, spb[t], q, B);
+        nxc_f_rec<CD>(v, ra, spa[t], q, A);
+        nxc_f_rec<CD>(v, rb, spb[t], q, B);
         const float *iv = Ninv + 6 * (size_t)q;
         float inv[6] = {iv[0], iv[1], iv[2], iv[3], iv[4], iv[5]};
         z_of<CD>(inv, B, Zb);
@@ -1804,6 +1858,7 @@ __global__ void __launch_bounds__(SC_THREADS, CD == 6 ? 2 : 1) k_schur_seg(View 
           for (int c = 0; c < CD; c++)
             acc[CD * r + c] += A[r] * Zb[c] + A[CD + r] * Zb[CD + c] + A[2 * CD + r] * Zb[2 * CD + c];
       }
+    }
   }
   // segments are contiguous runs of lanes: after the steps, a lane holds the
   // sum over itself and the following lanes of its run
