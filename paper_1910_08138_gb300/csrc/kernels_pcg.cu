@@ -191,26 +191,36 @@ enum {
 
 // FP32 form: the lower tiles of the running sub-blocks as hi + lo floats, in
 // two planes with the layout of S (hi: S rounded to 24 bits; hi + lo: S to
-// 2^-48 relative), and max |S_hi| per sub-block (its word zeroed before)
-__global__ void __launch_bounds__(256) k_pcg_split(const double *S, const long long *S_off, const int *npad,
-                                                   const int *run, const int *fail, const int *sched_tiles, int L,
-                                                   float *Shi, float *Slo, float *s32) {
-  int l, a, b;
-  tile_of(blockIdx.x, sched_tiles, L, l, a, b);
-  if (!run[l] || fail[l]) return;
-  int np = npad[l];
-  float mx = 0.f;
-  for (int e = threadIdx.x; e < PT * PT; e += blockDim.x) {
-    int r = e / PT, c = e - r * PT;
-    size_t idx = (size_t)S_off[l] + (size_t)(a * PT + r) * np + b * PT + c;
-    float2 v = ff_split_bits(S[idx]);
-    Shi[idx] = v.x;
-    Slo[idx] = v.y;
-    mx = fmaxf(mx, fabsf(v.x));
-  }
+// 2^-48 relative), and max |S_hi| per sub-block (its word zeroed before). One
+// warp per tile (lane c: column c, one 256-byte row load per step), the warps
+// striding over the tile table.
+__global__ void __launch_bounds__(256) k_pcg_split(const double *__restrict__ S, const long long *S_off,
+                                                   const int *npad, const int *run, const int *fail,
+                                                   const int2 *__restrict__ tile_map, int tiles, float *Shi,
+                                                   float *Slo, float *s32) {
+  int lane = threadIdx.x & 31;
+  int nw = gridDim.x * (blockDim.x >> 5);
+  for (int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); idx < tiles; idx += nw) {
+    int2 tm = tile_map[idx];
+    int l = tm.x, a = tm.y >> 16, b = tm.y & 0xffff;
+    if (!run[l] || fail[l]) continue;  // the same for the whole warp
+    int np = npad[l];
+    size_t base = (size_t)S_off[l] + (size_t)(a * PT) * np + b * PT + lane;
+    double v[PT];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(s32 + PCG_S32 * l + S32_SMAX), __float_as_int(mx));
+    for (int r = 0; r < PT; r++) v[r] = __ldg(S + base + (size_t)r * np);
+    float mx = 0.f;
+#pragma unroll
+    for (int r = 0; r < PT; r++) {
+      float2 h = ff_split_bits(v[r]);
+      Shi[base + (size_t)r * np] = h.x;
+      Slo[base + (size_t)r * np] = h.y;
+      mx = fmaxf(mx, fabsf(h.x));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) atomicMax(reinterpret_cast<int *>(s32 + PCG_S32 * l + S32_SMAX), __float_as_int(mx));
+  }
 }
 
 // Exponent s of the FP32 form's fixed-point product: every partial sum of
@@ -1020,9 +1030,9 @@ rpba_status pcg_init(Ctx *ctx, const int *run_dev, int *fail_dev, const FsaiAppl
   if (!fsai && ff_pcg(ctx)) {
     RPBA_CUDA(cudaMemsetAsync(ctx->pcg_s32, 0, (size_t)PCG_S32_WORDS * L * sizeof(float), st));
     if (ctx->pcg_tiles_total)
-      RPBA_KERNEL(ctx, "k_pcg_split", k_pcg_split<<<ctx->pcg_tiles_total, 256, 0, st>>>(
-                                          ctx->S, ctx->S_off, ctx->npad, run_dev, fail_dev, ctx->pcg_tiles, L,
-                                          ctx->pcg_Shi, ctx->pcg_Slo, ctx->pcg_s32));
+      RPBA_KERNEL(ctx, "k_pcg_split", k_pcg_split<<<symv32_grid(ctx->pcg_tiles_total), 256, 0, st>>>(
+                                          ctx->S, ctx->S_off, ctx->npad, run_dev, fail_dev, ctx->pcg_tile_map,
+                                          ctx->pcg_tiles_total, ctx->pcg_Shi, ctx->pcg_Slo, ctx->pcg_s32));
     auto stage = ctx->cd == 8 ? k_pcg_stage<8> : k_pcg_stage<6>;
     RPBA_KERNEL(ctx, "k_pcg_stage", stage<<<L, PCG_THREADS, 0, st>>>(
                                         1, 0, nullptr, 0, run_dev, fail_dev, ctx->sub_cam_ptr, ctx->ycam_off,
