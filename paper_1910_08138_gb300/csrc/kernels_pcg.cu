@@ -238,61 +238,74 @@ __device__ inline int fixed_exp(int np, float smax, float pmax) {
 
 // FP32 form, refinement residual: q += S (X + dx) in float-float over the
 // lower tiles of the active sub-blocks (X float-float, dx the FP32 solution of
-// the stage just ended), summed over the tiles with FP64 atomics. 128
-// threads: warps 0-1 form the row sums, warps 2-3 the column sums
-// (off-diagonal tiles), two threads per row or column with 16 entries each.
-#define SYMV_THREADS 128
+// the stage just ended), summed over the tiles with FP64 atomics. One warp per
+// tile, the warps striding over the tile table (as k_pcg_symv32): lane c reads
+// column c's hi and lo words one row at a time, accumulates the transposed
+// product in float-float and keeps the 32 row terms (hi, lo); a transposing
+// butterfly of float-float additions leaves row r's sum in lane r.
+#define SYMV_THREADS 256
+__device__ __forceinline__ float2 warp_transpose_sum_ff(float (&th)[PT], float (&tl)[PT], int lane) {
+#pragma unroll
+  for (int o = PT / 2; o >= 1; o >>= 1) {
+    bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; i++) {
+      float sh = up ? th[i] : th[i + o], sl = up ? tl[i] : tl[i + o];
+      float kh = up ? th[i + o] : th[i], kl = up ? tl[i + o] : tl[i];
+      float2 r = ff_add(make_float2(kh, kl),
+                        make_float2(__shfl_xor_sync(0xffffffffu, sh, o), __shfl_xor_sync(0xffffffffu, sl, o)));
+      th[i] = r.x;
+      tl[i] = r.y;
+    }
+  }
+  return make_float2(th[0], tl[0]);
+}
+
 __global__ void __launch_bounds__(SYMV_THREADS) k_pcg_symv_ff(const float *__restrict__ Shi,
                                                               const float *__restrict__ Slo, const long long *S_off,
                                                               const int *npad, const int *voff, const int *act,
-                                                              const int *sched_tiles, int L,
+                                                              const int2 *__restrict__ tile_map, int tiles,
                                                               const float2 *__restrict__ X,
                                                               const float *__restrict__ dx, double *q) {
-  int l, a, b;
-  tile_of(blockIdx.x, sched_tiles, L, l, a, b);
-  if (!act[l]) return;
-  int np = npad[l];
-  size_t base = (size_t)S_off[l];
-  const float2 *Xl = X + voff[l];
-  const float *dxl = dx + voff[l];
-  double *ql = q + voff[l];
-  __shared__ float2 blk[PT][PLD];
-  __shared__ float2 pI[PT], pJ[PT];
-  int tid = threadIdx.x;
-  if (tid < PT) pI[tid] = ff_add(Xl[a * PT + tid], make_float2(dxl[a * PT + tid], 0.f));
-  else if (tid < 2 * PT) pJ[tid - PT] = ff_add(Xl[b * PT + tid - PT], make_float2(dxl[b * PT + tid - PT], 0.f));
-  float2 v[8];
+  int lane = threadIdx.x & 31;
+  int nw = gridDim.x * (SYMV_THREADS / 32);
+  for (int idx = blockIdx.x * (SYMV_THREADS / 32) + (threadIdx.x >> 5); idx < tiles; idx += nw) {
+    int2 tm = tile_map[idx];
+    int l = tm.x, a = tm.y >> 16, b = tm.y & 0xffff;
+    if (!act[l]) continue;  // the same for the whole warp
+    int np = npad[l];
+    size_t base = (size_t)S_off[l] + (size_t)(a * PT) * np + b * PT + lane;
+    const float2 *Xl = X + voff[l];
+    const float *dxl = dx + voff[l];
+    float2 pI = ff_add(Xl[a * PT + lane], make_float2(dxl[a * PT + lane], 0.f));
+    float2 pJ = ff_add(Xl[b * PT + lane], make_float2(dxl[b * PT + lane], 0.f));
+    float th[PT], tl[PT];
 #pragma unroll
-  for (int k = 0; k < 8; k++) {
-    int e = tid + SYMV_THREADS * k, r = e / PT, c = e - r * PT;
-    size_t idx = base + ((a == b && c > r) ? (size_t)(a * PT + c) * np + b * PT + r
-                                           : (size_t)(a * PT + r) * np + b * PT + c);
-    v[k] = make_float2(Shi[idx], Slo[idx]);
-  }
+    for (int r = 0; r < PT; r++) {
+      th[r] = __ldg(Shi + base + (size_t)r * np);
+      tl[r] = __ldg(Slo + base + (size_t)r * np);
+    }
+    float2 col = make_float2(0.f, 0.f);
+    const bool diag = a == b;
 #pragma unroll
-  for (int k = 0; k < 8; k++) {
-    int e = tid + SYMV_THREADS * k, r = e / PT, c = e - r * PT;
-    blk[r][c] = v[k];
+    for (int r = 0; r < PT; r++) {
+      float2 m = make_float2(th[r], tl[r]);
+      if (diag && lane > r) m = make_float2(0.f, 0.f);  // row r, columns 0 .. r
+      float2 pr = make_float2(__shfl_sync(0xffffffffu, pI.x, r), __shfl_sync(0xffffffffu, pI.y, r));
+      if (!diag || lane < r) col = ff_add(col, ff_mul(m, pr));
+      float2 t = ff_mul(m, pJ);
+      th[r] = t.x;
+      tl[r] = t.y;
+    }
+    float2 row = warp_transpose_sum_ff(th, tl, lane);
+    double *ql = q + voff[l];
+    if (!diag) {
+      atomicAdd(ql + a * PT + lane, ff_to_double(row));
+      atomicAdd(ql + b * PT + lane, ff_to_double(col));
+    } else {
+      atomicAdd(ql + a * PT + lane, ff_to_double(ff_add(row, col)));
+    }
   }
-  __syncthreads();
-  bool col = tid >= 2 * PT;
-  int u = tid & 63, t = u >> 1, h = u & 1;  // row (or column) t, entries 16h .. 16h+15
-  if (col && a == b) return;                // the diagonal tile's columns are its rows
-  float sh = 0.f, sl = 0.f;
-#pragma unroll
-  for (int k = 16 * h; k < 16 * h + 16; k++) {
-    float2 m = col ? blk[k][t] : blk[t][k];
-    float2 x = col ? pI[k] : pJ[k];
-    float e;
-    float pr = ff_two_prod(m.x, x.x, e);
-    ff_acc(sh, sl, pr);
-    sl = __fadd_rn(sl, __fmaf_rn(m.y, x.x, __fmaf_rn(m.x, x.y, e)));
-  }
-  float oh = __shfl_xor_sync(0xffffffffu, sh, 1), ol = __shfl_xor_sync(0xffffffffu, sl, 1);
-  float e;
-  sh = ff_two_sum(sh, oh, e);
-  sl = __fadd_rn(sl, __fadd_rn(e, ol));
-  if (h == 0) atomicAdd(ql + (col ? b : a) * PT + t, ff_to_double(make_float2(sh, sl)));
 }
 
 // Sums over the warp's lanes of 32 values at once: on return lane i holds
@@ -1115,9 +1128,10 @@ static rpba_status pcg_loop_refined(Ctx *ctx, int *iters) {
     }
     ctx->pcg_pred_stage[stage] = it - it0;
     bool last = it >= maxit || stage + 1 == RPBA_PCG_MAX_STAGES;
-    RPBA_KERNEL(ctx, "k_pcg_symv_ff", k_pcg_symv_ff<<<tiles, SYMV_THREADS, 0, st>>>(
+    RPBA_KERNEL(ctx, "k_pcg_symv_ff", k_pcg_symv_ff<<<symv32_grid(tiles), SYMV_THREADS, 0, st>>>(
                                           ctx->pcg_Shi, ctx->pcg_Slo, ctx->S_off, ctx->npad, ctx->ycam_off,
-                                          ctx->pcg_act, ctx->pcg_tiles, L, ctx->pcg_fx, ctx->pcg_x32, ctx->pcg_q));
+                                          ctx->pcg_act, ctx->pcg_tile_map, tiles, ctx->pcg_fx, ctx->pcg_x32,
+                                          ctx->pcg_q));
     RPBA_KERNEL(ctx, "k_pcg_stage", stage_k<<<L, PCG_THREADS, 0, st>>>(
                                         0, last ? 1 : 0, nullptr, 0, nullptr, nullptr, ctx->sub_cam_ptr, ctx->ycam_off,
                                         ctx->npad, ctx->pcg_Minv32, ctx->y, ctx->pcg_q, ctx->pcg_fx, ctx->pcg_x32,
@@ -1245,9 +1259,10 @@ static rpba_status pcg_loop_device(Ctx *ctx) {
       RPBA_KERNEL(ctx, "k_pcg_cond", k_pcg_cond<<<1, 256, 0, bi>>>(h_in, L, ctx->pcg_live, cnt, 1, maxit));
       return RPBA_OK;
     }));
-    RPBA_KERNEL(ctx, "k_pcg_symv_ff", k_pcg_symv_ff<<<tiles, SYMV_THREADS, 0, bo>>>(
+    RPBA_KERNEL(ctx, "k_pcg_symv_ff", k_pcg_symv_ff<<<symv32_grid(tiles), SYMV_THREADS, 0, bo>>>(
                                           ctx->pcg_Shi, ctx->pcg_Slo, ctx->S_off, ctx->npad, ctx->ycam_off,
-                                          ctx->pcg_act, ctx->pcg_tiles, L, ctx->pcg_fx, ctx->pcg_x32, ctx->pcg_q));
+                                          ctx->pcg_act, ctx->pcg_tile_map, tiles, ctx->pcg_fx, ctx->pcg_x32,
+                                          ctx->pcg_q));
     RPBA_KERNEL(ctx, "k_pcg_stage", stage_k<<<L, PCG_THREADS, 0, bo>>>(
                                         0, 0, cnt, maxit, nullptr, nullptr, ctx->sub_cam_ptr, ctx->ycam_off,
                                         ctx->npad, ctx->pcg_Minv32, ctx->y, ctx->pcg_q, ctx->pcg_fx, ctx->pcg_x32,
