@@ -163,22 +163,6 @@ __device__ inline void cta_sum(double (&v)[NV], double (&out)[NV]) {
   __syncthreads();
 }
 
-// CTA -> (sub-block l, lower tile (a, b)) through prefix sums of the
-// per-sub-block tile counts
-__device__ inline void tile_of(int idx, const int *sched_tiles, int L, int &l, int &a, int &b) {
-  int lo = 0, hi = L - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (sched_tiles[mid] <= idx) lo = mid; else hi = mid - 1;
-  }
-  l = lo;
-  int loc = idx - sched_tiles[l];
-  a = (int)((sqrtf(8.0f * (float)loc + 1.0f) - 1.0f) * 0.5f);
-  while ((a + 1) * (a + 2) / 2 <= loc) a++;
-  while (a * (a + 1) / 2 > loc) a--;
-  b = loc - a * (a + 1) / 2;
-}
-
 // Per-sub-block words of the FP32 form's refinement (PCG_S32_WORDS floats
 // each): rz, the stage's ||r_0|| and tolerance, the last relative true
 // residual, the stage count, a bound on max |p|, the exponent of the
